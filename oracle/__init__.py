@@ -1,0 +1,206 @@
+"""CPU oracle for the box-restricted implicit-Euler FV reaction-diffusion step.
+
+TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the CPU-baseline
+leg of bench.py may import this package; the product path (the CUDA library and
+its binding) never does, and this package imports nothing from it.
+
+Plain FP64, single thread.  The arithmetic-heavy parts (CSR assembly, GMRES,
+dense LU, the CNN reference) live in the C files next to this module; the step
+driver below is the plain definition of the method (arXiv 2505.03067):
+
+* Sec. 2.3 (Bounding Box Mesh): the box is the bounding box of every tumour
+  voxel (cell id > 0) widened by a margin and clamped to the lattice.
+* Sec. 2.4 (Implementation): each species is advanced by one implicit-Euler
+  step of Eq. 1-4 discretised by first-order finite volumes on the box mesh
+  and solved with GMRES; the result is mapped back onto the pleural mask, so
+  only in-mask voxels of the box change.
+
+Stopping rule (the paper gives none): true residual ||b - A x||_2 <=
+max(rtol * ||b_mask||_2, atol), norms over the in-mask rows (masked rows are
+identity rows whose residual is zero from the initial guess c^n on).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "lib")
+_SOURCES = ["oracle.c", "cnn_oracle.c"]
+_lib = None
+
+OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into oracle/lib/liboracle.so (plain -O2, no -march)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    so = os.path.join(_LIBDIR, "liboracle.so")
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    if not force and os.path.exists(so) and all(os.path.getmtime(so) >= os.path.getmtime(s) for s in srcs):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
+    os.replace(tmp, so)
+    return so
+
+
+class _Species(C.Structure):
+    _fields_ = [("dt", C.c_double), ("h", C.c_double), ("D", C.c_double), ("mu", C.c_double),
+                ("c_bc", C.c_double), ("bc_box", C.c_int32), ("ncell", C.c_int32),
+                ("k_cell", C.c_void_p), ("q_cell", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_assemble.restype = C.c_int64
+        _lib.orc_gmres.restype = C.c_int
+        _lib.orc_dense_solve.restype = C.c_int
+        _lib.orc_csr_matvec.restype = None
+    return _lib
+
+
+def _p(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else C.c_void_p(0)
+
+
+@dataclasses.dataclass
+class CSR:
+    n: tuple
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def N(self):
+        return len(self.row_ptr) - 1
+
+    def dense(self) -> np.ndarray:
+        A = np.zeros((self.N, self.N))
+        for r in range(self.N):
+            for e in range(self.row_ptr[r], self.row_ptr[r + 1]):
+                A[r, self.col[e]] += self.val[e]
+        return A
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float64).reshape(-1)
+        y = np.empty_like(x)
+        lib().orc_csr_matvec(C.c_int64(self.N), _p(self.row_ptr), _p(self.col), _p(self.val), _p(x), _p(y))
+        return y
+
+
+# ---------------------------------------------------------------- Sec. 2.3: bounding box
+def bbox(cell_id: np.ndarray, margin: int):
+    """Bounding box of all voxels with cell id > 0, widened by `margin` and clamped:
+    lo = max(0, min - margin), hi = min(L, max + margin + 1) per axis (x, y, z).
+    Returns None when there is no tumour voxel."""
+    zz, yy, xx = np.nonzero(cell_id > 0)
+    if len(xx) == 0:
+        return None
+    Lz, Ly, Lx = cell_id.shape
+    lo = [max(0, int(a.min()) - margin) for a in (xx, yy, zz)]
+    hi = [min(L, int(a.max()) + margin + 1) for a, L in ((xx, Lx), (yy, Ly), (zz, Lz))]
+    return tuple(lo), tuple(hi)
+
+
+def box_slices(box):
+    (lx, ly, lz), (hx, hy, hz) = box
+    return (slice(lz, hz), slice(ly, hy), slice(lx, hx))
+
+
+def box_view(a: np.ndarray, box) -> np.ndarray:
+    """Copy of the box region of a lattice array (the gather)."""
+    return np.ascontiguousarray(a[box_slices(box)])
+
+
+# ---------------------------------------------------------------- Sec. 2.4: FV assembly
+def assemble(mask_box, cell_box, c_box, params, s: int, bc_box: int = 0, dfac_box=None):
+    """CSR matrix A and right-hand side b of species s on the box (see oracle.c)."""
+    nz, ny, nx = mask_box.shape
+    N = nx * ny * nz
+    mask_box = np.ascontiguousarray(mask_box, np.uint8)
+    cell_box = np.ascontiguousarray(cell_box, np.int32)
+    c_box = np.ascontiguousarray(c_box, np.float64)
+    k = np.ascontiguousarray(params.k_cell[s], np.float64)
+    q = np.ascontiguousarray(params.q_cell[s], np.float64)
+    df = None if dfac_box is None else np.ascontiguousarray(dfac_box, np.float64)
+    sp = _Species(params.dt, params.h, float(params.D[s]), float(params.mu[s]), float(params.c_bc[s]),
+                  bc_box, params.ncell, k.ctypes.data, q.ctypes.data)
+    n = (C.c_int32 * 3)(nx, ny, nz)
+    rp = np.empty(N + 1, np.int64)
+    col = np.empty(7 * N, np.int32)
+    val = np.empty(7 * N, np.float64)
+    rhs = np.empty(N, np.float64)
+    nnz = lib().orc_assemble(n, _p(mask_box), _p(cell_box), _p(c_box), _p(df), C.byref(sp),
+                             _p(rp), _p(col), _p(val), _p(rhs))
+    if nnz < 0:
+        raise ValueError("cell id outside the rate tables")
+    return CSR((nx, ny, nz), rp, col[:nnz].copy(), val[:nnz].copy()), rhs.reshape(mask_box.shape)
+
+
+def gmres(A: CSR, b, x0, restart: int = 30, tol_abs: float = 1e-12, maxit: int = 10000):
+    """Restarted GMRES(m) with MGS Arnoldi and Givens rotations (oracle.c)."""
+    b = np.ascontiguousarray(b, np.float64).reshape(-1)
+    x = np.array(x0, np.float64).reshape(-1).copy()
+    it = C.c_int32(0)
+    cyc = C.c_int32(0)
+    res = C.c_double(0)
+    st = lib().orc_gmres(C.c_int64(A.N), _p(A.row_ptr), _p(A.col), _p(A.val), _p(b), _p(x),
+                         C.c_int32(restart), C.c_double(tol_abs), C.c_int32(maxit),
+                         C.byref(it), C.byref(cyc), C.byref(res))
+    return x, {"status": st, "iters": it.value, "cycles": cyc.value, "res": res.value}
+
+
+def dense_solve(A: CSR, b):
+    b = np.ascontiguousarray(b, np.float64).reshape(-1)
+    x = np.empty_like(b)
+    st = lib().orc_dense_solve(C.c_int64(A.N), _p(A.row_ptr), _p(A.col), _p(A.val), _p(b), _p(x))
+    if st != OK:
+        raise RuntimeError(f"dense solve failed: {st}")
+    return x
+
+
+# ---------------------------------------------------------------- one step of the method
+def step(lat, params, margin: int, bc_box: int = 0, rtol: float = 1e-12, atol: float = 0.0,
+         restart: int = 30, maxit: int = 10000, solver: str = "gmres", x0=None):
+    """Advance every species of `lat` (a workloads.Lattice, modified in place) by one
+    implicit-Euler step inside the bounding box; returns a report dict.  `x0`
+    optionally gives per-species initial guesses on the box (default c^n)."""
+    box = bbox(lat.cell_id, margin)
+    if box is None:
+        return {"status": ERR_EMPTY, "box": None}
+    sl = box_slices(box)
+    mask_box = box_view(lat.mask, box)
+    cell_box = box_view(lat.cell_id, box)
+    dfac_box = None if lat.dfac is None else box_view(lat.dfac, box)
+    inm = mask_box > 0
+    rep = {"status": OK, "box": box, "iters": [], "cycles": [], "res": [], "bnorm": [],
+           "mask_voxels": int(inm.sum()), "box_voxels": int(mask_box.size)}
+    for s in range(params.nspecies):
+        c_box = box_view(lat.fields[s], box)
+        A, b = assemble(mask_box, cell_box, c_box, params, s, bc_box, dfac_box)
+        bnorm = float(np.sqrt(np.sum(b[inm] ** 2)))
+        tol = max(rtol * bnorm, atol)
+        if solver == "lu":
+            x = dense_solve(A, b)
+            info = {"status": OK, "iters": 0, "cycles": 0,
+                    "res": float(np.linalg.norm(b.reshape(-1) - A.matvec(x)))}
+        else:
+            guess = c_box if x0 is None else x0[s]
+            x, info = gmres(A, b, guess, restart, tol, maxit)
+        x = x.reshape(mask_box.shape)
+        # Sec. 2.4: the solution is mapped onto the pleural mask
+        lat.fields[s][sl][inm] = x[inm]
+        rep["iters"].append(info["iters"])
+        rep["cycles"].append(info["cycles"])
+        rep["res"].append(info["res"])
+        rep["bnorm"].append(bnorm)
+        if info["status"] != OK:
+            rep["status"] = info["status"]
+    return rep
