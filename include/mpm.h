@@ -1,0 +1,216 @@
+/*
+ * mpm.h -- C ABI of the GB300 box-restricted reaction-diffusion solver.
+ *
+ * The library advances the species fields of a Cellular Potts lattice by one
+ * first-order implicit-Euler, first-order finite-volume step of
+ *     dC/dt = D lap(C) - S,       S = k C - q                (Eq. 1-4)
+ * restricted to a bounding box of the tumour cells plus a margin (Sec. 2.3),
+ * solved by restarted GMRES and mapped back onto the pleural mask (Sec. 2.4),
+ * of Dolganov et al., arXiv 2505.03067.  All compute runs in the library's
+ * CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice arrays are dense, x fastest: voxel (i,j,k) is at i + Lx*(j + Ly*k).
+ *  - "device" pointers are CUDA device (or managed) memory owned by the caller;
+ *    the library never frees them.  Buffers of an mpm_subgrid are owned by the
+ *    library and live until mpm_subgrid_destroy / mpm_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Kernels are
+ *    queued on it; calls that must size buffers from device results (extract)
+ *    synchronise that stream.  Asynchronous CUDA errors surface as
+ *    MPM_ERR_CUDA at the next call that synchronises.
+ *  - No call throws, exits or prints; each returns an mpm_status and, on error,
+ *    leaves a message readable with mpm_last_error(ctx).
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPM_MAX_SPECIES 4
+#define MPM_MAX_RESTART 32
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, id outside tables) */
+    MPM_ERR_EMPTY = 2,      /* no tumour voxel (cell id > 0): no box; outputs untouched */
+    MPM_ERR_NOCONV = 3,     /* maxit reached; the best iterate is kept */
+    MPM_ERR_BREAKDOWN = 4,  /* non-finite value or a zero pivot in the least squares */
+    MPM_ERR_TIMEOUT = 5,    /* a bounded inter-CTA wait expired; results are invalid */
+    MPM_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+    MPM_ERR_NOMEM = 7       /* the context's memory cap or the device is exhausted */
+} mpm_status;
+
+typedef struct mpm_ctx mpm_ctx;
+typedef struct mpm_subgrid mpm_subgrid;
+
+/* Bounding box: lo inclusive, hi exclusive, per axis (x, y, z). */
+typedef struct { int32_t lo[3], hi[3]; } mpm_box;
+
+/* The caller's lattice (all device pointers, caller-owned). */
+typedef struct {
+    int32_t dims[3];                    /* Lx, Ly, Lz; Lx*Ly*Lz < 2^31 */
+    const int32_t *cell_id;             /* CPM cell id per voxel, 0 = medium, > 0 = tumour */
+    const uint8_t *mask;                /* 1 = pleural space (solved), 0 = outside */
+    const double *dfac;                 /* nullable: per-voxel diffusivity factor (D_s * dfac) */
+    double *field[MPM_MAX_SPECIES];     /* concentration of each species (FP64) */
+} mpm_lattice;
+
+/* Physical parameters of Eq. 1-4 (host struct; the rate tables are device). */
+typedef struct {
+    int32_t nspecies;                   /* 1..MPM_MAX_SPECIES */
+    int32_t ncell;                      /* entries per species in k_cell / q_cell */
+    double dt, h;                       /* time step, grid spacing */
+    double D[MPM_MAX_SPECIES];          /* diffusivity */
+    double mu[MPM_MAX_SPECIES];         /* uniform first-order decay (Eq. 3-4) */
+    double c_bc[MPM_MAX_SPECIES];       /* Dirichlet value on box faces */
+    const double *k_cell;               /* device [nspecies][ncell]: uptake of cell id */
+    const double *q_cell;               /* device [nspecies][ncell]: source of cell id */
+    int32_t bc_box;                     /* 0: Dirichlet box faces, 1: zero flux */
+} mpm_params;
+
+typedef struct {
+    double rtol;            /* stop when ||b - A x||_2 <= max(rtol*||b||_2, atol) (in-mask rows) */
+    double atol;
+    int32_t restart;        /* GMRES restart length m, 1..MPM_MAX_RESTART */
+    int32_t maxit;          /* total Arnoldi steps per species */
+    int32_t precision;      /* 0: FP64 throughout; 1: FP32 Krylov inside FP64 refinement */
+    double inner_rtol;      /* precision 1: reduction of each FP32 inner cycle (e.g. 1e-5) */
+    int32_t x0_given;       /* 1: the subgrid's current iterate is the initial guess
+                               (set by mpm_subgrid_import); 0: c^n from the extract */
+    int32_t nblocks;        /* 0: automatic; else the persistent grid size (tuning) */
+} mpm_opts;
+
+typedef struct {
+    int32_t iters[MPM_MAX_SPECIES];     /* Arnoldi steps */
+    int32_t cycles[MPM_MAX_SPECIES];    /* restarts (refinement steps for precision 1) */
+    int32_t status[MPM_MAX_SPECIES];    /* mpm_status per species */
+    double res[MPM_MAX_SPECIES];        /* final true residual ||b - A x||_2 (FP64) */
+    double bnorm[MPM_MAX_SPECIES];      /* ||b||_2 over in-mask rows */
+    int64_t box_voxels;                 /* nx*ny*nz */
+    int64_t mask_voxels;                /* in-mask voxels of the box (the unknowns) */
+    int64_t stored_voxels;              /* voxels of the active tiles held in HBM */
+    double solve_ms;                    /* device time of the solve kernel (CUDA events) */
+} mpm_report;
+
+/* Shape of an extracted subgrid (host struct filled by mpm_subgrid_info). */
+typedef struct {
+    mpm_box box;
+    int32_t n[3];               /* box dims */
+    int32_t tile[3];            /* tile dims (powers of two) */
+    int32_t ntiles;             /* tiles covering the box */
+    int32_t nactive;            /* tiles holding at least one in-mask voxel */
+    int64_t stored_voxels;      /* nactive * tile volume */
+    int64_t mask_voxels;
+    int32_t nspecies;
+} mpm_subgrid_desc;
+
+/* What mpm_subgrid_export copies out (box-dense layout, x fastest). */
+typedef enum {
+    MPM_EXPORT_X = 0,       /* current iterate / solution (double), c^n right after extract */
+    MPM_EXPORT_RHS = 1,     /* b (double) */
+    MPM_EXPORT_DIAG = 2,    /* A_PP (double) */
+    MPM_EXPORT_FLAGS = 3,   /* uint8: bits 0-5 open faces -x,+x,-y,+y,-z,+z; bit 6 in mask */
+    MPM_EXPORT_CELL = 4     /* int32 cell id */
+} mpm_export_what;
+
+/* Create a context on the current CUDA device.  workspace_bytes caps the device
+ * memory the library may allocate for subgrids and Krylov bases (0 = no cap).
+ * Errors: MPM_ERR_ARG (ctx NULL), MPM_ERR_CUDA (no device). */
+mpm_status mpm_create(mpm_ctx **ctx, size_t workspace_bytes);
+mpm_status mpm_destroy(mpm_ctx *ctx);
+/* Message of the last error on this context ("" if none); valid until the next call. */
+const char *mpm_last_error(const mpm_ctx *ctx);
+
+mpm_status mpm_subgrid_create(mpm_ctx *ctx, mpm_subgrid **sub);
+mpm_status mpm_subgrid_destroy(mpm_ctx *ctx, mpm_subgrid *sub);
+mpm_status mpm_subgrid_info(const mpm_subgrid *sub, mpm_subgrid_desc *out);
+
+/*
+ * Sec. 2.3 (dynamic bounding box) + the gather: reduce the lattice to the box
+ * of all voxels with cell_id > 0, widened by `margin` and clamped,
+ *     lo = max(0, min - margin),  hi = min(L, max + margin + 1),
+ * split the box into tiles of dims `tile` (powers of two, product 32..1024;
+ * NULL = 8x8x4), keep the tiles that hold an in-mask voxel, and copy the mask,
+ * cell ids, optional dfac and the species fields c^n of those tiles into `sub`
+ * (tile-major, library-owned).  `nspecies` fields are gathered.
+ * Writes the box to *out_box.  Synchronises `stream` (the box size sizes the
+ * buffers).  MPM_ERR_EMPTY if no voxel has cell_id > 0 (sub and out_box are
+ * then unchanged).
+ */
+mpm_status mpm_box_extract(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
+                           const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, void *stream);
+
+/*
+ * Assemble the implicit-Euler FV system of every species on the extracted box
+ * (Eq. 1-4 discretised as in Sec. 2.4).  For an in-mask voxel P:
+ *   A_PP = 1 + dt (mu + k_cell[id]) + (dt/h^2) sum_f w_f D_f
+ *   A_PQ = -(dt/h^2) D_f   for each face to an in-mask neighbour Q in the box
+ *   b_P  = c^n_P + dt q_cell[id] + (dt/h^2) sum_{box faces} 2 D_P c_bc
+ * with D_f the harmonic mean of D_s*dfac at P and Q, w_f = 1 on an open face,
+ * 2 on a Dirichlet box face (half-cell distance; 0 if bc_box = 1), 0 on a face
+ * to a masked voxel.  Masked voxels are identity rows keeping c^n.
+ * Queued on `stream`.  MPM_ERR_ARG on bad parameters; a cell id outside
+ * [0, ncell) is reported by the next solve as MPM_ERR_ARG.
+ */
+mpm_status mpm_assemble_coeffs(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, void *stream);
+
+/*
+ * Solve A c^{n+1} = b for every species of `sub` with restarted GMRES in one
+ * persistent kernel (all species in lock step), starting from c^n (or the
+ * imported guess), stopping on the true FP64 residual.  precision 1 runs the
+ * Krylov basis and operator in FP32 inside FP64 iterative refinement.  If
+ * scatter_to is not NULL, the in-mask box voxels of its fields receive the
+ * solution (Sec. 2.4); other voxels are untouched.  Synchronises `stream`
+ * and fills *rep (may be NULL).  Returns the worst species status.
+ */
+mpm_status mpm_solve_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *scatter_to,
+                          const mpm_opts *opt, mpm_report *rep, void *stream);
+
+/*
+ * Solve nsys independent subgrids (every species of each) in ONE persistent
+ * launch: the grid is split into teams of CTAs, each team takes a list of
+ * systems chosen by a longest-first partition of their sizes.  scatter_to may
+ * be NULL or hold nsys entries (each nullable).  reps may be NULL or hold nsys.
+ */
+mpm_status mpm_solve_batch(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
+                           int32_t nsys, const mpm_opts *opt, mpm_report *reps, void *stream);
+
+/* Copy `what` of species s from the subgrid into dst (device, box-dense,
+ * nx*ny*nz elements of the export type).  Voxels of tiles that hold no
+ * in-mask voxel are not stored: they receive 0 (1 for DIAG).  Queued on
+ * `stream`. */
+mpm_status mpm_subgrid_export(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s,
+                              void *dst, void *stream);
+
+/* Overwrite the iterate of species s with src (device, box-dense doubles) on
+ * the in-mask voxels: the initial guess used when opts.x0_given = 1. */
+mpm_status mpm_subgrid_import(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const double *src, void *stream);
+
+/* y = A x for species s (device, box-dense doubles, FP64 operator of the last
+ * assemble): the matrix-free 7-point operator alone. */
+mpm_status mpm_apply_operator(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const double *x,
+                              double *y, void *stream);
+
+/* Scatter the current iterate to the lattice (in-mask box voxels only). */
+mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, void *stream);
+
+/* Test hooks for failure detection (no GPU fault is ever provoked):
+ *  MPM_DEBUG_TIMEOUT_NS  wall-time limit of every inter-CTA wait of the solver
+ *                        (default 2e9 ns); on expiry the solve returns
+ *                        MPM_ERR_TIMEOUT and the context stays usable.
+ *  MPM_DEBUG_SKIP_BLOCK  CTA index that leaves the solver at once, so that its
+ *                        partners' waits run out (-1 = none, the default). */
+#define MPM_DEBUG_TIMEOUT_NS 1
+#define MPM_DEBUG_SKIP_BLOCK 2
+mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM_H */

@@ -1,0 +1,235 @@
+// api.cu -- the C ABI of include/mpm.h: context and subgrid lifetime, memory
+// accounting, error plumbing.  No exception crosses the ABI; every entry
+// point returns an mpm_status and records a message on the context.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mpm_internal.cuh"
+
+mpm_status mpm_fail(mpm_ctx *ctx, mpm_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+mpm_status mpm_cuda_check(mpm_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return MPM_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return mpm_fail(ctx, MPM_ERR_NOMEM, m);
+    return mpm_fail(ctx, MPM_ERR_CUDA, m);
+}
+
+// Grow-only device buffer under the context's cap; the old contents are not kept.
+mpm_status mpm_grow(mpm_ctx *ctx, void **p, size_t *cap, size_t need, const char *what)
+{
+    if (need <= *cap && *p) return MPM_OK;
+    size_t want = need + need / 4 + 4096;     // head-room for growing boxes
+    if (ctx->cap && ctx->allocated - *cap + want > ctx->cap) {
+        want = need;
+        if (ctx->allocated - *cap + want > ctx->cap)
+            return mpm_fail(ctx, MPM_ERR_NOMEM, std::string(what) + ": workspace cap exceeded");
+    }
+    if (*p) {
+        cudaError_t e = cudaFree(*p);
+        if (e != cudaSuccess) return mpm_cuda_check(ctx, e, "cudaFree");
+        ctx->allocated -= *cap;
+        *p = nullptr;
+        *cap = 0;
+    }
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return mpm_fail(ctx, MPM_ERR_NOMEM, std::string(what) + ": cudaMalloc of " + std::to_string(want) + " bytes failed");
+    }
+    *p = q;
+    *cap = want;
+    ctx->allocated += want;
+    return MPM_OK;
+}
+
+static void free_sub_buffers(mpm_ctx *ctx, mpm_subgrid *sub)
+{
+    void **bufs[3] = {&sub->geo, &sub->elem, &sub->krylov};
+    size_t *caps[3] = {&sub->geo_bytes, &sub->elem_bytes, &sub->krylov_bytes};
+    for (int i = 0; i < 3; ++i) {
+        if (*bufs[i]) {
+            cudaFree(*bufs[i]);
+            if (ctx) ctx->allocated -= *caps[i];
+        }
+        *bufs[i] = nullptr;
+        *caps[i] = 0;
+    }
+}
+
+extern "C" {
+
+mpm_status mpm_create(mpm_ctx **out, size_t workspace_bytes)
+{
+    if (!out) return MPM_ERR_ARG;
+    *out = nullptr;
+    mpm_ctx *ctx = new (std::nothrow) mpm_ctx();
+    if (!ctx) return MPM_ERR_NOMEM;
+    ctx->cap = workspace_bytes;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_box, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_abort, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_abort, 0, 256);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_stage, 1 << 16);
+    if (e == cudaSuccess) ctx->stage_cap = 1 << 16;
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mpm_destroy(ctx);
+        return MPM_ERR_CUDA;
+    }
+    *out = ctx;
+    return MPM_OK;
+}
+
+mpm_status mpm_destroy(mpm_ctx *ctx)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    cudaFree(ctx->d_box);
+    cudaFree(ctx->d_count);
+    cudaFree(ctx->d_err);
+    cudaFree(ctx->d_abort);
+    cudaFree(ctx->d_partials);
+    cudaFree(ctx->d_bar);
+    cudaFree(ctx->d_args);
+    cudaFree(ctx->d_tmp);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return MPM_OK;
+}
+
+const char *mpm_last_error(const mpm_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+mpm_status mpm_subgrid_create(mpm_ctx *ctx, mpm_subgrid **sub)
+{
+    if (!ctx || !sub) return mpm_fail(ctx, MPM_ERR_ARG, "subgrid_create: null argument");
+    *sub = new (std::nothrow) mpm_subgrid();
+    return *sub ? MPM_OK : mpm_fail(ctx, MPM_ERR_NOMEM, "subgrid_create: out of host memory");
+}
+
+mpm_status mpm_subgrid_destroy(mpm_ctx *ctx, mpm_subgrid *sub)
+{
+    if (!sub) return mpm_fail(ctx, MPM_ERR_ARG, "subgrid_destroy: null subgrid");
+    free_sub_buffers(ctx, sub);
+    delete sub;
+    return MPM_OK;
+}
+
+mpm_status mpm_subgrid_info(const mpm_subgrid *sub, mpm_subgrid_desc *out)
+{
+    if (!sub || !out) return MPM_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    if (!sub->extracted) return MPM_ERR_ARG;
+    for (int d = 0; d < 3; ++d) {
+        out->box.lo[d] = sub->lo[d];
+        out->box.hi[d] = sub->hi[d];
+        out->n[d] = sub->n[d];
+        out->tile[d] = 1 << sub->lt[d];
+    }
+    out->ntiles = sub->ntiles;
+    out->nactive = sub->nact;
+    out->stored_voxels = sub->NE;
+    out->mask_voxels = sub->mask_voxels;
+    out->nspecies = sub->nspecies;
+    return MPM_OK;
+}
+
+mpm_status mpm_box_extract(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
+                           const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_extract_impl(ctx, lat, nspecies, margin, tile, out_box, sub, (cudaStream_t)stream);
+}
+
+mpm_status mpm_assemble_coeffs(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_assemble_impl(ctx, sub, prm, (cudaStream_t)stream);
+}
+
+mpm_status mpm_solve_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *scatter_to, const mpm_opts *opt,
+                          mpm_report *rep, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    mpm_subgrid *subs[1] = {sub};
+    const mpm_lattice *sc[1] = {scatter_to};
+    return mpm_solve_impl(ctx, subs, sc, 1, opt, rep, (cudaStream_t)stream);
+}
+
+mpm_status mpm_solve_batch(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
+                           int32_t nsys, const mpm_opts *opt, mpm_report *reps, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_solve_impl(ctx, subs, scatter_to, nsys, opt, reps, (cudaStream_t)stream);
+}
+
+mpm_status mpm_subgrid_export(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_export_impl(ctx, sub, what, s, dst, (cudaStream_t)stream);
+}
+
+mpm_status mpm_subgrid_import(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const double *src, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_import_impl(ctx, sub, s, src, (cudaStream_t)stream);
+}
+
+mpm_status mpm_apply_operator(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const double *x, double *y,
+                              void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_apply_impl(ctx, sub, s, x, y, (cudaStream_t)stream);
+}
+
+mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_scatter_impl(ctx, sub, lat, (cudaStream_t)stream);
+}
+
+mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    switch (key) {
+    case MPM_DEBUG_TIMEOUT_NS:
+        if (value <= 0) return mpm_fail(ctx, MPM_ERR_ARG, "debug: timeout must be > 0");
+        ctx->timeout_ns = (uint64_t)value;
+        return MPM_OK;
+    case MPM_DEBUG_SKIP_BLOCK:
+        ctx->skip_block = (int32_t)value;
+        return MPM_OK;
+    default:
+        return mpm_fail(ctx, MPM_ERR_ARG, "debug: unknown key");
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,559 @@
+// extract.cu -- Sec. 2.3 (dynamic bounding box) and the gather/scatter of the
+// box sub-grid between the caller's lattice and the library's tile-major
+// compact layout (Sec. 2.4: the result is mapped back onto the pleural mask).
+#include <climits>
+#include <cstring>
+
+#include "mpm_internal.cuh"
+
+namespace mpm {
+
+// ---------------------------------------------------------------- bbox reduction
+// Min and max (x, y, z) over voxels with cell_id > 0.  HBM-bound scan of the
+// int32 lattice (4 B/voxel): 16-byte loads, four in flight per thread; the
+// coordinate arithmetic only runs for tumour voxels.  Per-CTA reduction, then
+// six atomics per CTA that found any tumour voxel.
+__device__ __forceinline__ void bbox_upd(uint32_t e, uint32_t Lx, uint32_t Lxy, int (&mn)[3], int (&mx)[3])
+{
+    const uint32_t k = e / Lxy;
+    const uint32_t r = e - k * Lxy;
+    const uint32_t j = r / Lx;
+    const uint32_t i = r - j * Lx;
+    mn[0] = min(mn[0], (int)i); mx[0] = max(mx[0], (int)i);
+    mn[1] = min(mn[1], (int)j); mx[1] = max(mx[1], (int)j);
+    mn[2] = min(mn[2], (int)k); mx[2] = max(mx[2], (int)k);
+}
+
+__global__ void __launch_bounds__(kBlock) k_bbox(const int32_t *__restrict__ cell, uint32_t Lx, uint32_t Lxy,
+                                                 uint32_t ntot, int vec4, int32_t *__restrict__ out)
+{
+    int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {-1, -1, -1};
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nth = gridDim.x * blockDim.x;
+    uint32_t done = 0;
+    if (vec4) {
+        const int4 *c4 = reinterpret_cast<const int4 *>(cell);
+        const uint32_t n4 = ntot / 4;
+        uint32_t q = tid;
+        for (; q + 3 * nth < n4; q += 4 * nth) {
+            int4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldcs(c4 + q + u * nth);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if ((v[u].x > 0) | (v[u].y > 0) | (v[u].z > 0) | (v[u].w > 0)) {
+                    const uint32_t e = 4 * (q + u * nth);
+                    if (v[u].x > 0) bbox_upd(e + 0, Lx, Lxy, mn, mx);
+                    if (v[u].y > 0) bbox_upd(e + 1, Lx, Lxy, mn, mx);
+                    if (v[u].z > 0) bbox_upd(e + 2, Lx, Lxy, mn, mx);
+                    if (v[u].w > 0) bbox_upd(e + 3, Lx, Lxy, mn, mx);
+                }
+            }
+        }
+        for (; q < n4; q += nth) {
+            const int4 v = __ldcs(c4 + q);
+            const uint32_t e = 4 * q;
+            if (v.x > 0) bbox_upd(e + 0, Lx, Lxy, mn, mx);
+            if (v.y > 0) bbox_upd(e + 1, Lx, Lxy, mn, mx);
+            if (v.z > 0) bbox_upd(e + 2, Lx, Lxy, mn, mx);
+            if (v.w > 0) bbox_upd(e + 3, Lx, Lxy, mn, mx);
+        }
+        done = n4 * 4;
+    }
+    for (uint32_t e = done + tid; e < ntot; e += nth)
+        if (__ldcs(cell + e) > 0) bbox_upd(e, Lx, Lxy, mn, mx);
+
+    __shared__ int smn[3][kWarps], smx[3][kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int a = __reduce_min_sync(0xffffffffu, mn[d]);
+        const int b = __reduce_max_sync(0xffffffffu, mx[d]);
+        if (lane == 0) { smn[d][w] = a; smx[d][w] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        int a = INT_MAX, b = -1;
+        for (int i = 0; i < kWarps; ++i) { a = min(a, smn[d][i]); b = max(b, smx[d][i]); }
+        if (b >= 0) { atomicMin(out + d, a); atomicMax(out + 3 + d, b); }
+    }
+}
+
+// ---------------------------------------------------------------- tiles
+struct BoxGeo {
+    int32_t lo[3], n[3], nt[3];
+    int32_t lt[3];
+    uint32_t Lx, Ly;
+};
+
+// Mark tiles holding an in-mask voxel; count the in-mask voxels of the box.
+// One warp per box row (j, k).
+__global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restrict__ mask, BoxGeo g,
+                                                        int8_t *__restrict__ active,
+                                                        unsigned long long *__restrict__ count)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t nwarp = (int64_t)gridDim.x * kWarps;
+    const int64_t nrows = (int64_t)g.n[1] * g.n[2];
+    unsigned long long cnt = 0;
+    for (int64_t row = warp; row < nrows; row += nwarp) {
+        const int by = (int)(row % g.n[1]), bz = (int)(row / g.n[1]);
+        const int64_t L0 = (int64_t)g.lo[0] + (int64_t)g.Lx * ((int64_t)(g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
+        const int64_t trow = ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) * g.nt[0];
+        for (int bx = lane; bx < g.n[0]; bx += 32) {
+            if (__ldg(mask + L0 + bx)) {
+                ++cnt;
+                active[trow + (bx >> g.lt[0])] = 1;
+            }
+        }
+    }
+    cnt = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    if (lane == 0 && cnt) atomicAdd(count, cnt);
+}
+
+// Exclusive scan of the tile activity (one CTA): compact index per tile (-1
+// if inactive), coordinates of each active tile, and the active count.
+__global__ void __launch_bounds__(1024) k_tile_scan(const int8_t *__restrict__ active, int32_t ntiles, BoxGeo g,
+                                                    int32_t *__restrict__ tile_index,
+                                                    int32_t *__restrict__ tile_coord,
+                                                    unsigned long long *__restrict__ nact_out)
+{
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int32_t chunk = (ntiles + 1023) / 1024;
+    const int32_t b = min(ntiles, t * chunk), e = min(ntiles, b + chunk);
+    int32_t c = 0;
+    for (int32_t i = b; i < e; ++i) c += active[i] ? 1 : 0;
+    part[t] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {      // Hillis-Steele inclusive scan
+        const int32_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t idx = part[t] - c;
+    for (int32_t i = b; i < e; ++i) {
+        if (active[i]) {
+            tile_index[i] = idx;
+            const int32_t tx = i % g.nt[0], ty = (i / g.nt[0]) % g.nt[1], tz = i / (g.nt[0] * g.nt[1]);
+            tile_coord[4 * idx + 0] = tx;
+            tile_coord[4 * idx + 1] = ty;
+            tile_coord[4 * idx + 2] = tz;
+            tile_coord[4 * idx + 3] = 0;
+            ++idx;
+        } else {
+            tile_index[i] = -1;
+        }
+    }
+    if (t == 1023) *nact_out = (unsigned long long)part[1023];
+}
+
+__global__ void k_tile_nbr(const int32_t *__restrict__ tile_index, const int32_t *__restrict__ tile_coord,
+                           int32_t nact, BoxGeo g, int32_t *__restrict__ nbr)
+{
+    const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nact) return;
+    const int32_t c[3] = {tile_coord[4 * a], tile_coord[4 * a + 1], tile_coord[4 * a + 2]};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        int32_t q[3] = {c[0], c[1], c[2]};
+        q[d >> 1] += (d & 1) ? 1 : -1;
+        int32_t r = -1;
+        if (q[0] >= 0 && q[0] < g.nt[0] && q[1] >= 0 && q[1] < g.nt[1] && q[2] >= 0 && q[2] < g.nt[2])
+            r = tile_index[(q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]];
+        nbr[6 * a + d] = r;
+    }
+}
+
+// Box coordinates of element e; returns false for tile padding outside the box.
+__device__ __forceinline__ bool elem_box(int64_t e, const BoxGeo &g, const int32_t *__restrict__ tile_coord,
+                                         int &bx, int &by, int &bz)
+{
+    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
+    const int64_t tile = e >> ltv;
+    const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
+    const int4 tc = __ldg(reinterpret_cast<const int4 *>(tile_coord) + tile);
+    bx = (tc.x << g.lt[0]) + (int)(v & ((1u << g.lt[0]) - 1));
+    by = (tc.y << g.lt[1]) + (int)((v >> g.lt[0]) & ((1u << g.lt[1]) - 1));
+    bz = (tc.z << g.lt[2]) + (int)(v >> (g.lt[0] + g.lt[1]));
+    return bx < g.n[0] && by < g.n[1] && bz < g.n[2];
+}
+
+struct GatherArgs {
+    const int32_t *cell_id;
+    const uint8_t *mask;
+    const double *dfac_lat;
+    const double *field[kMaxSpecies];
+    int32_t nspecies;
+    uint8_t *flags;
+    int32_t *cell;
+    double *dfac;
+    double *x[kMaxSpecies];
+    double *cn[kMaxSpecies];
+};
+
+// Copy mask-derived face flags, cell ids, dfac and c^n of every stored element.
+__global__ void __launch_bounds__(kBlock) k_gather(GatherArgs a, BoxGeo g, const int32_t *__restrict__ tile_coord,
+                                                   int64_t NE)
+{
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < NE; e += (int64_t)gridDim.x * kBlock) {
+        int bx, by, bz;
+        if (!elem_box(e, g, tile_coord, bx, by, bz)) {
+            a.flags[e] = 0;
+            a.cell[e] = 0;
+            if (a.dfac) a.dfac[e] = 1.0;
+            for (int s = 0; s < a.nspecies; ++s) { a.x[s][e] = 0.0; a.cn[s][e] = 0.0; }
+            continue;
+        }
+        const int64_t sy = g.Lx, sz = (int64_t)g.Lx * g.Ly;
+        const int64_t L = (int64_t)(g.lo[0] + bx) + sy * (g.lo[1] + by) + sz * (g.lo[2] + bz);
+        uint32_t f = F_BOX;
+        if (__ldg(a.mask + L)) {
+            f |= F_MASK;
+            if (bx > 0 && __ldg(a.mask + L - 1)) f |= F_MX;
+            if (bx < g.n[0] - 1 && __ldg(a.mask + L + 1)) f |= F_PX;
+            if (by > 0 && __ldg(a.mask + L - sy)) f |= F_MY;
+            if (by < g.n[1] - 1 && __ldg(a.mask + L + sy)) f |= F_PY;
+            if (bz > 0 && __ldg(a.mask + L - sz)) f |= F_MZ;
+            if (bz < g.n[2] - 1 && __ldg(a.mask + L + sz)) f |= F_PZ;
+        }
+        a.flags[e] = (uint8_t)f;
+        a.cell[e] = __ldg(a.cell_id + L);
+        if (a.dfac) a.dfac[e] = __ldg(a.dfac_lat + L);
+        for (int s = 0; s < a.nspecies; ++s) {
+            const double c = __ldg(a.field[s] + L);
+            a.x[s][e] = c;
+            a.cn[s][e] = c;
+        }
+    }
+}
+
+struct ScatterArgs {
+    double *field[kMaxSpecies];
+    const double *x[kMaxSpecies];
+    int32_t nspecies;
+    const uint8_t *flags;
+};
+
+// Sec. 2.4: write the box solution onto the pleural mask (in-mask voxels only).
+__global__ void __launch_bounds__(kBlock) k_scatter(ScatterArgs a, BoxGeo g, const int32_t *__restrict__ tile_coord,
+                                                    int64_t NE)
+{
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < NE; e += (int64_t)gridDim.x * kBlock) {
+        if (!(a.flags[e] & F_MASK)) continue;
+        int bx, by, bz;
+        elem_box(e, g, tile_coord, bx, by, bz);
+        const int64_t L = (int64_t)(g.lo[0] + bx) + (int64_t)g.Lx * ((g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
+        for (int s = 0; s < a.nspecies; ++s) a.field[s][L] = a.x[s][e];
+    }
+}
+
+// Box-dense <-> compact conversions (tests, warm starts, the standalone operator).
+__device__ __forceinline__ int64_t dense_to_elem(int64_t d, const BoxGeo &g, const int32_t *__restrict__ tile_index)
+{
+    const int bx = (int)(d % g.n[0]);
+    const int64_t r = d / g.n[0];
+    const int by = (int)(r % g.n[1]), bz = (int)(r / g.n[1]);
+    const int32_t t = __ldg(tile_index + ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) * g.nt[0] + (bx >> g.lt[0]));
+    if (t < 0) return -1;
+    const int ix = bx & ((1 << g.lt[0]) - 1), iy = by & ((1 << g.lt[1]) - 1), iz = bz & ((1 << g.lt[2]) - 1);
+    return ((int64_t)t << (g.lt[0] + g.lt[1] + g.lt[2])) + ix + ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_export(const T *__restrict__ src, T dflt, BoxGeo g,
+                                                   const int32_t *__restrict__ tile_index, T *__restrict__ dst,
+                                                   int64_t nbox)
+{
+    for (int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x; d < nbox; d += (int64_t)gridDim.x * kBlock) {
+        const int64_t e = dense_to_elem(d, g, tile_index);
+        dst[d] = e >= 0 ? src[e] : dflt;
+    }
+}
+
+// dense -> compact; only_mask: write in-mask voxels only (import of a guess),
+// else every in-box voxel of the active tiles.
+__global__ void __launch_bounds__(kBlock) k_import(const double *__restrict__ src, BoxGeo g,
+                                                   const int32_t *__restrict__ tile_index,
+                                                   const uint8_t *__restrict__ flags, int only_mask,
+                                                   double *__restrict__ dst, int64_t nbox)
+{
+    for (int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x; d < nbox; d += (int64_t)gridDim.x * kBlock) {
+        const int64_t e = dense_to_elem(d, g, tile_index);
+        if (e < 0) continue;
+        if (only_mask && !(flags[e] & F_MASK)) continue;
+        dst[e] = src[d];
+    }
+}
+
+// compact -> dense where stored, else the per-voxel default (identity rows)
+__global__ void __launch_bounds__(kBlock) k_export_or(const double *__restrict__ src, const double *__restrict__ dflt,
+                                                      BoxGeo g, const int32_t *__restrict__ tile_index,
+                                                      double *__restrict__ dst, int64_t nbox)
+{
+    for (int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x; d < nbox; d += (int64_t)gridDim.x * kBlock) {
+        const int64_t e = dense_to_elem(d, g, tile_index);
+        dst[d] = e >= 0 ? src[e] : dflt[d];
+    }
+}
+
+static int grid_for(int64_t n, int num_sms, int per_sm = 8)
+{
+    int64_t g = (n + kBlock - 1) / kBlock;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+BoxGeo make_geo(const mpm_subgrid *sub, const int32_t dims[3])
+{
+    BoxGeo g;
+    for (int d = 0; d < 3; ++d) {
+        g.lo[d] = sub->lo[d];
+        g.n[d] = sub->n[d];
+        g.nt[d] = sub->nt[d];
+        g.lt[d] = sub->lt[d];
+    }
+    g.Lx = (uint32_t)dims[0];
+    g.Ly = (uint32_t)dims[1];
+    return g;
+}
+
+}  // namespace mpm
+
+using namespace mpm;
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
+                            const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st)
+{
+    if (!lat || !sub || !lat->cell_id || !lat->mask) return mpm_fail(ctx, MPM_ERR_ARG, "extract: null argument");
+    if (nspecies < 1 || nspecies > MPM_MAX_SPECIES) return mpm_fail(ctx, MPM_ERR_ARG, "extract: nspecies out of range");
+    for (int s = 0; s < nspecies; ++s)
+        if (!lat->field[s]) return mpm_fail(ctx, MPM_ERR_ARG, "extract: null field pointer");
+    const int64_t L = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2];
+    if (lat->dims[0] < 1 || lat->dims[1] < 1 || lat->dims[2] < 1 || L >= (int64_t)1 << 31)
+        return mpm_fail(ctx, MPM_ERR_ARG, "extract: lattice dims out of range");
+    if (margin < 0) return mpm_fail(ctx, MPM_ERR_ARG, "extract: negative margin");
+    int32_t lt[3] = {3, 3, 2};
+    if (tile) {
+        for (int d = 0; d < 3; ++d) {
+            const int32_t t = tile[d];
+            if (t < 1 || t > 64 || (t & (t - 1))) return mpm_fail(ctx, MPM_ERR_ARG, "extract: tile dims must be powers of two <= 64");
+            lt[d] = __builtin_ctz((unsigned)t);
+        }
+        const int tv = 1 << (lt[0] + lt[1] + lt[2]);
+        if (tv < 32 || tv > 1024) return mpm_fail(ctx, MPM_ERR_ARG, "extract: tile volume must be in [32, 1024]");
+    }
+
+    // ---- a1: bounding box of the tumour voxels
+    int32_t init[6] = {INT_MAX, INT_MAX, INT_MAX, -1, -1, -1};
+    MPM_CU(cudaMemcpyAsync(ctx->d_box, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    const int vec4 = ((uintptr_t)lat->cell_id % 16) == 0;
+    k_bbox<<<grid_for(L / 4 + 1, ctx->num_sms, 4), kBlock, 0, st>>>(lat->cell_id, (uint32_t)lat->dims[0],
+                                                                     (uint32_t)(lat->dims[0] * lat->dims[1]),
+                                                                     (uint32_t)L, vec4, ctx->d_box);
+    MPM_CU(cudaGetLastError());
+    int32_t *hb = (int32_t *)ctx->h_stage;
+    MPM_CU(cudaMemcpyAsync(hb, ctx->d_box, 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    if (hb[3] < 0) return mpm_fail(ctx, MPM_ERR_EMPTY, "extract: no tumour voxel (cell_id > 0)");
+    mpm_box box;
+    for (int d = 0; d < 3; ++d) {
+        box.lo[d] = hb[d] - margin < 0 ? 0 : hb[d] - margin;
+        const int64_t h = (int64_t)hb[3 + d] + margin + 1;
+        box.hi[d] = h > lat->dims[d] ? lat->dims[d] : (int32_t)h;
+    }
+
+    // ---- tiles of the box
+    mpm_subgrid tmp = *sub;   // commit only on success
+    for (int d = 0; d < 3; ++d) {
+        tmp.lo[d] = box.lo[d];
+        tmp.hi[d] = box.hi[d];
+        tmp.n[d] = box.hi[d] - box.lo[d];
+        tmp.lt[d] = lt[d];
+        tmp.nt[d] = (tmp.n[d] + (1 << lt[d]) - 1) >> lt[d];
+    }
+    const int64_t ntiles64 = (int64_t)tmp.nt[0] * tmp.nt[1] * tmp.nt[2];
+    tmp.ntiles = (int32_t)ntiles64;
+    const size_t nt = (size_t)ntiles64;
+    const size_t geo_need = align256(nt * 4) + align256(nt * 16) + align256(nt * 24) + align256(nt) + 256;
+    sub->extracted = false;   // from here on the subgrid's buffers are rewritten
+    sub->assembled = false;
+    mpm_status s0 = mpm_grow(ctx, &sub->geo, &sub->geo_bytes, geo_need, "tile tables");
+    tmp.geo = sub->geo;
+    tmp.geo_bytes = sub->geo_bytes;
+    if (s0 != MPM_OK) return s0;
+    {
+        char *p = (char *)tmp.geo;
+        tmp.tile_index = (int32_t *)p; p += align256(nt * 4);
+        tmp.tile_coord = (int32_t *)p; p += align256(nt * 16);
+        tmp.nbr = (int32_t *)p; p += align256(nt * 24);
+        tmp.active = (int8_t *)p; p += align256(nt);
+        tmp.err = (int32_t *)p;
+    }
+    MPM_CU(cudaMemsetAsync(tmp.err, 0, sizeof(int32_t), st));
+    BoxGeo g = make_geo(&tmp, lat->dims);
+    MPM_CU(cudaMemsetAsync(tmp.active, 0, nt, st));
+    MPM_CU(cudaMemsetAsync(ctx->d_count, 0, 2 * sizeof(int64_t), st));
+    const int64_t nrows = (int64_t)tmp.n[1] * tmp.n[2];
+    k_tile_active<<<grid_for(nrows * 32, ctx->num_sms, 8), kBlock, 0, st>>>(
+        lat->mask, g, tmp.active, (unsigned long long *)ctx->d_count);
+    MPM_CU(cudaGetLastError());
+    k_tile_scan<<<1, 1024, 0, st>>>(tmp.active, tmp.ntiles, g, tmp.tile_index, tmp.tile_coord,
+                                    (unsigned long long *)(ctx->d_count + 1));
+    MPM_CU(cudaGetLastError());
+    int64_t *hc = (int64_t *)ctx->h_stage;
+    MPM_CU(cudaMemcpyAsync(hc, ctx->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    tmp.mask_voxels = hc[0];
+    tmp.nact = (int32_t)hc[1];
+    const int ltv = lt[0] + lt[1] + lt[2];
+    tmp.NE = (int64_t)tmp.nact << ltv;
+    tmp.nspecies = nspecies;
+    tmp.has_dfac = lat->dfac != nullptr;
+
+    // ---- element buffers
+    const size_t NE = (size_t)tmp.NE;
+    size_t need = align256(NE) + align256(NE * 4) + (tmp.has_dfac ? align256(NE * 8) : 0);
+    need += (size_t)nspecies * (4 * align256(NE * 8) + align256(NE * 4));
+    s0 = mpm_grow(ctx, &sub->elem, &sub->elem_bytes, need > 0 ? need : 256, "element buffers");
+    tmp.elem = sub->elem;
+    tmp.elem_bytes = sub->elem_bytes;
+    if (s0 != MPM_OK) return s0;
+    {
+        char *p = (char *)tmp.elem;
+        tmp.flags = (uint8_t *)p; p += align256(NE);
+        tmp.cell = (int32_t *)p; p += align256(NE * 4);
+        tmp.dfac = nullptr;
+        if (tmp.has_dfac) { tmp.dfac = (double *)p; p += align256(NE * 8); }
+        for (int s = 0; s < MPM_MAX_SPECIES; ++s) {
+            tmp.x[s] = tmp.cn[s] = tmp.b[s] = tmp.diag[s] = nullptr;
+            tmp.diag32[s] = nullptr;
+        }
+        for (int s = 0; s < nspecies; ++s) {
+            tmp.x[s] = (double *)p; p += align256(NE * 8);
+            tmp.cn[s] = (double *)p; p += align256(NE * 8);
+            tmp.b[s] = (double *)p; p += align256(NE * 8);
+            tmp.diag[s] = (double *)p; p += align256(NE * 8);
+            tmp.diag32[s] = (float *)p; p += align256(NE * 4);
+        }
+    }
+    if (tmp.nact > 0) {
+        k_tile_nbr<<<(tmp.nact + 127) / 128, 128, 0, st>>>(tmp.tile_index, tmp.tile_coord, tmp.nact, g, tmp.nbr);
+        MPM_CU(cudaGetLastError());
+        GatherArgs ga;
+        memset(&ga, 0, sizeof(ga));
+        ga.cell_id = lat->cell_id;
+        ga.mask = lat->mask;
+        ga.dfac_lat = lat->dfac;
+        ga.nspecies = nspecies;
+        ga.flags = tmp.flags;
+        ga.cell = tmp.cell;
+        ga.dfac = tmp.dfac;
+        for (int s = 0; s < nspecies; ++s) {
+            ga.field[s] = lat->field[s];
+            ga.x[s] = tmp.x[s];
+            ga.cn[s] = tmp.cn[s];
+        }
+        k_gather<<<grid_for(tmp.NE, ctx->num_sms, 8), kBlock, 0, st>>>(ga, g, tmp.tile_coord, tmp.NE);
+        MPM_CU(cudaGetLastError());
+    }
+    tmp.extracted = true;
+    tmp.assembled = false;
+    tmp.x_fresh = true;
+    *sub = tmp;
+    if (out_box) *out_box = box;
+    return MPM_OK;
+}
+
+mpm_status mpm_scatter_impl(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st)
+{
+    if (!sub || !lat) return mpm_fail(ctx, MPM_ERR_ARG, "scatter: null argument");
+    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "scatter: subgrid not extracted");
+    for (int s = 0; s < sub->nspecies; ++s)
+        if (!lat->field[s]) return mpm_fail(ctx, MPM_ERR_ARG, "scatter: null field pointer");
+    for (int d = 0; d < 3; ++d)
+        if (sub->hi[d] > lat->dims[d]) return mpm_fail(ctx, MPM_ERR_ARG, "scatter: lattice smaller than the box");
+    if (sub->NE == 0) return MPM_OK;
+    ScatterArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nspecies = sub->nspecies;
+    a.flags = sub->flags;
+    for (int s = 0; s < sub->nspecies; ++s) { a.field[s] = lat->field[s]; a.x[s] = sub->x[s]; }
+    BoxGeo g = make_geo(sub, lat->dims);
+    k_scatter<<<grid_for(sub->NE, ctx->num_sms, 8), kBlock, 0, st>>>(a, g, sub->tile_coord, sub->NE);
+    MPM_CU(cudaGetLastError());
+    return MPM_OK;
+}
+
+mpm_status mpm_export_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst, cudaStream_t st)
+{
+    if (!sub || !dst) return mpm_fail(ctx, MPM_ERR_ARG, "export: null argument");
+    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "export: subgrid not extracted");
+    if ((what == MPM_EXPORT_X || what == MPM_EXPORT_RHS || what == MPM_EXPORT_DIAG) && (s < 0 || s >= sub->nspecies))
+        return mpm_fail(ctx, MPM_ERR_ARG, "export: species out of range");
+    if ((what == MPM_EXPORT_RHS || what == MPM_EXPORT_DIAG) && !sub->assembled)
+        return mpm_fail(ctx, MPM_ERR_ARG, "export: subgrid not assembled");
+    const int32_t dims[3] = {sub->n[0], sub->n[1], sub->n[2]};
+    BoxGeo g = make_geo(sub, dims);
+    const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
+    const int grid = grid_for(nbox, ctx->num_sms, 8);
+    switch (what) {
+    case MPM_EXPORT_X:
+        k_export<double><<<grid, kBlock, 0, st>>>(sub->x[s], 0.0, g, sub->tile_index, (double *)dst, nbox); break;
+    case MPM_EXPORT_RHS:
+        k_export<double><<<grid, kBlock, 0, st>>>(sub->b[s], 0.0, g, sub->tile_index, (double *)dst, nbox); break;
+    case MPM_EXPORT_DIAG:
+        k_export<double><<<grid, kBlock, 0, st>>>(sub->diag[s], 1.0, g, sub->tile_index, (double *)dst, nbox); break;
+    case MPM_EXPORT_FLAGS:
+        k_export<uint8_t><<<grid, kBlock, 0, st>>>(sub->flags, (uint8_t)0, g, sub->tile_index, (uint8_t *)dst, nbox); break;
+    case MPM_EXPORT_CELL:
+        k_export<int32_t><<<grid, kBlock, 0, st>>>(sub->cell, 0, g, sub->tile_index, (int32_t *)dst, nbox); break;
+    default:
+        return mpm_fail(ctx, MPM_ERR_ARG, "export: unknown field");
+    }
+    MPM_CU(cudaGetLastError());
+    return MPM_OK;
+}
+
+mpm_status mpm_import_impl(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const double *src, cudaStream_t st)
+{
+    if (!sub || !src) return mpm_fail(ctx, MPM_ERR_ARG, "import: null argument");
+    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "import: subgrid not extracted");
+    if (s < 0 || s >= sub->nspecies) return mpm_fail(ctx, MPM_ERR_ARG, "import: species out of range");
+    const int32_t dims[3] = {sub->n[0], sub->n[1], sub->n[2]};
+    BoxGeo g = make_geo(sub, dims);
+    const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
+    k_import<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(src, g, sub->tile_index, sub->flags, 1, sub->x[s], nbox);
+    MPM_CU(cudaGetLastError());
+    sub->x_fresh = false;
+    return MPM_OK;
+}
+
+// used by mpm_apply_impl (assemble.cu)
+mpm_status mpm_dense_to_elems(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, double *dst, cudaStream_t st)
+{
+    const int32_t dims[3] = {sub->n[0], sub->n[1], sub->n[2]};
+    BoxGeo g = make_geo(sub, dims);
+    const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
+    MPM_CU(cudaMemsetAsync(dst, 0, (size_t)sub->NE * sizeof(double), st));
+    k_import<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(src, g, sub->tile_index, sub->flags, 0, dst, nbox);
+    MPM_CU(cudaGetLastError());
+    return MPM_OK;
+}
+
+mpm_status mpm_elems_to_dense(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, const double *dflt_dense,
+                              double *dst, cudaStream_t st)
+{
+    const int32_t dims[3] = {sub->n[0], sub->n[1], sub->n[2]};
+    BoxGeo g = make_geo(sub, dims);
+    const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
+    k_export_or<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(src, dflt_dense, g, sub->tile_index, dst, nbox);
+    MPM_CU(cudaGetLastError());
+    return MPM_OK;
+}

@@ -1,0 +1,328 @@
+// mpm_internal.cuh -- shared declarations of the GB300 solver library.
+//
+// Data layout in HBM.  A box of dims n[3] is covered by tiles of TX x TY x TZ
+// voxels (powers of two).  Only "active" tiles (holding at least one in-mask
+// voxel) are stored, tile-major and compacted: element e of a box vector is
+// voxel (e & (TV-1)) of active tile (e >> log2 TV), x fastest inside the tile.
+// Every per-voxel array (flags, cell ids, iterate, rhs, diagonal, Krylov
+// vectors) uses that one flat index, so all streaming passes are plain,
+// perfectly coalesced 1D loops and only the 7-point stencil looks at tiles
+// (through a 6-entry neighbour table per tile).  Inactive tiles have no
+// unknowns (identity rows keeping c^n), so they are never stored or touched.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+
+namespace mpm {
+
+// flags byte of an element
+constexpr uint32_t F_MX = 1u, F_PX = 2u, F_MY = 4u, F_PY = 8u, F_MZ = 16u, F_PZ = 32u;
+constexpr uint32_t F_OPEN = 63u;   // any open face
+constexpr uint32_t F_MASK = 64u;   // voxel is in the pleural mask (an unknown)
+constexpr uint32_t F_BOX = 128u;   // voxel lies inside the box (not tile padding)
+
+constexpr int kBlock = 256;        // threads per CTA of every kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxSpecies = MPM_MAX_SPECIES;
+constexpr int kMaxM = MPM_MAX_RESTART;
+constexpr int kKStride = kMaxM + 2;           // partial slots per species
+constexpr int kKMax = kMaxSpecies * kKStride; // partial slots per block
+
+// Device view of one extracted, assembled box system.
+struct SysDev {
+    int64_t NE;                 // stored elements = nact * TV
+    int32_t ltx, lty, ltz;      // log2 tile dims
+    int32_t nspecies;
+    const int32_t *nbr;         // [nact][6] neighbour tile (-1 none): -x,+x,-y,+y,-z,+z
+    const uint8_t *flags;       // [NE]
+    const double *dfac;         // [NE] or null (uniform D)
+    double *x[kMaxSpecies];     // iterate (FP64)
+    const double *b[kMaxSpecies];
+    const double *diag[kMaxSpecies];
+    const float *diag32[kMaxSpecies];
+    void *V[kMaxSpecies];       // Krylov basis: (m+1) vectors of vstride elements
+    int64_t vstride;
+    double off[kMaxSpecies];    // dt*D_s/h^2 (uniform D: every open face)
+    double a;                   // dt/h^2 (harmonic-mean path)
+    double Dsp[kMaxSpecies];    // D_s (harmonic-mean path)
+    const int32_t *err;         // set by the assembly when a cell id lies outside the tables
+};
+
+// Per-system result written by the solver kernel.
+struct SysReport {
+    int32_t iters[kMaxSpecies];
+    int32_t cycles[kMaxSpecies];
+    int32_t status[kMaxSpecies];
+    int32_t pad_;
+    double res[kMaxSpecies];
+    double bnorm[kMaxSpecies];
+};
+
+struct TeamDesc {
+    int32_t first_block, nblocks, sys_begin, sys_end;
+};
+
+struct SolveArgs {
+    const SysDev *sys;
+    const int32_t *sys_order;   // systems of team t: sys_order[sys_begin..sys_end)
+    const TeamDesc *teams;
+    const int32_t *block_team;  // team of each block
+    double *partials;           // [2][gridDim][kKMax]
+    uint32_t *bar;              // one counter per team, 32 words apart
+    int32_t *abort_flag;        // set on a timed-out wait; every block then leaves
+    SysReport *reports;         // per system
+    double rtol, atol, inner_rtol;
+    int32_t m, maxit;
+    uint64_t timeout_ns;
+    int32_t skip_block;         // fault injection for tests: this block never arrives (-1 none)
+};
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Team-wide barrier among `nblocks` co-resident CTAs sharing counter `bar`.
+// Each arrival adds 1; the k-th barrier of a launch completes when the counter
+// reaches k*nblocks (the counter is zeroed before the launch).  The wait is
+// bounded by timeout_ns of wall time; on expiry (or when another block has
+// already given up) the global abort flag is raised and false is returned.
+__device__ __forceinline__ bool team_barrier(uint32_t *bar, uint32_t &epoch, uint32_t nblocks,
+                                             int32_t *abort_flag, uint64_t timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        epoch += 1;
+        const uint32_t target = epoch * nblocks;
+        __threadfence();
+        red_release_add_u32(bar, 1u);
+        int ok = 1;
+        const uint64_t t0 = globaltimer_ns();
+        uint32_t spins = 0;
+        for (;;) {
+            const uint32_t v = ld_acquire_u32(bar);
+            if ((int32_t)(v - target) >= 0) break;
+            if (*(volatile int32_t *)abort_flag) { ok = 0; break; }
+            if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+                atomicExch(abort_flag, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Neighbour element of e across face `dir` (0..5 = -x,+x,-y,+y,-z,+z) in the
+// compact tile-major layout.  Valid only where that face is open (the
+// neighbour then lies in an active tile by construction).
+struct TileGeo {
+    int32_t ltx, lty, ltz;
+    __device__ __forceinline__ int32_t ltv() const { return ltx + lty + ltz; }
+};
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+// Sum over open faces of u at the neighbour (uniform diffusivity), reading
+// through L2 (neighbours may belong to another CTA).
+template <typename T>
+__device__ __forceinline__ T nbr_sum(const T *__restrict__ u, const int32_t *__restrict__ nbr, int64_t e,
+                                     uint32_t f, int ltx, int lty, int ltz)
+{
+    T s = T(0);
+    if (!(f & F_OPEN)) return s;
+    const int ltv = ltx + lty + ltz;
+    const int64_t tile = e >> ltv;
+    const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
+    const uint32_t TX = 1u << ltx, TY = 1u << lty, TZ = 1u << ltz;
+    const uint32_t ix = v & (TX - 1), iy = (v >> ltx) & (TY - 1), iz = v >> (ltx + lty);
+    const int64_t base = tile << ltv;
+    if (f & F_MX) {
+        const int64_t q = ix > 0 ? e - 1 : ((int64_t)__ldg(nbr + tile * 6 + 0) << ltv) + (v + TX - 1);
+        s += ldcg(u + q);
+    }
+    if (f & F_PX) {
+        const int64_t q = ix < TX - 1 ? e + 1 : ((int64_t)__ldg(nbr + tile * 6 + 1) << ltv) + (v - (TX - 1));
+        s += ldcg(u + q);
+    }
+    if (f & F_MY) {
+        const int64_t q = iy > 0 ? e - TX : ((int64_t)__ldg(nbr + tile * 6 + 2) << ltv) + (v + (TY - 1) * TX);
+        s += ldcg(u + q);
+    }
+    if (f & F_PY) {
+        const int64_t q = iy < TY - 1 ? e + TX : ((int64_t)__ldg(nbr + tile * 6 + 3) << ltv) + (v - (TY - 1) * TX);
+        s += ldcg(u + q);
+    }
+    if (f & F_MZ) {
+        const int64_t q = iz > 0 ? e - TX * TY
+                                 : ((int64_t)__ldg(nbr + tile * 6 + 4) << ltv) + (v + (TZ - 1) * TX * TY);
+        s += ldcg(u + q);
+    }
+    if (f & F_PZ) {
+        const int64_t q = iz < TZ - 1 ? e + TX * TY
+                                      : ((int64_t)__ldg(nbr + tile * 6 + 5) << ltv) + (v - (TZ - 1) * TX * TY);
+        s += ldcg(u + q);
+    }
+    (void)base;
+    return s;
+}
+
+// Harmonic-mean variant: sum over open faces of D_f u_Q with
+// D_f = 2 D_P D_Q / (D_P + D_Q), D_P = Ds * dfac[P] (the caller multiplies by
+// dt / h^2).
+template <typename T>
+__device__ __forceinline__ T nbr_sum_var(const T *__restrict__ u, const double *__restrict__ dfac,
+                                         const int32_t *__restrict__ nbr, int64_t e, uint32_t f, int ltx,
+                                         int lty, int ltz, double Ds)
+{
+    const double dp = Ds * __ldg(dfac + e);
+    T s = T(0);
+    if (!(f & F_OPEN)) return s;
+    const int ltv = ltx + lty + ltz;
+    const int64_t tile = e >> ltv;
+    const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
+    const uint32_t TX = 1u << ltx, TY = 1u << lty, TZ = 1u << ltz;
+    const uint32_t ix = v & (TX - 1), iy = (v >> ltx) & (TY - 1), iz = v >> (ltx + lty);
+    int64_t q[6];
+    q[0] = ix > 0 ? e - 1 : ((int64_t)__ldg(nbr + tile * 6 + 0) << ltv) + (v + TX - 1);
+    q[1] = ix < TX - 1 ? e + 1 : ((int64_t)__ldg(nbr + tile * 6 + 1) << ltv) + (v - (TX - 1));
+    q[2] = iy > 0 ? e - TX : ((int64_t)__ldg(nbr + tile * 6 + 2) << ltv) + (v + (TY - 1) * TX);
+    q[3] = iy < TY - 1 ? e + TX : ((int64_t)__ldg(nbr + tile * 6 + 3) << ltv) + (v - (TY - 1) * TX);
+    q[4] = iz > 0 ? e - TX * TY : ((int64_t)__ldg(nbr + tile * 6 + 4) << ltv) + (v + (TZ - 1) * TX * TY);
+    q[5] = iz < TZ - 1 ? e + TX * TY : ((int64_t)__ldg(nbr + tile * 6 + 5) << ltv) + (v - (TZ - 1) * TX * TY);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (f & (1u << d)) {
+            const double dq = Ds * __ldg(dfac + q[d]);
+            const double hm = (dp + dq > 0.0) ? 2.0 * dp * dq / (dp + dq) : 0.0;
+            s += T(hm) * ldcg(u + q[d]);
+        }
+    }
+    return s;
+}
+
+}  // namespace mpm
+
+// ------------------------------------------------------------------ host-side objects
+struct mpm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t cap = 0;              // workspace cap (0 = none)
+    size_t allocated = 0;
+    std::string err;
+    // scratch
+    int32_t *d_box = nullptr;    // bbox result: lo[3] (min), hi[3] (max)
+    int64_t *d_count = nullptr;  // mask-voxel count, nact
+    int32_t *d_err = nullptr;    // device-side error flags
+    double *d_partials = nullptr;
+    size_t partials_cap = 0;     // doubles
+    uint32_t *d_bar = nullptr;   // barrier counters
+    int32_t bar_cap = 0;         // teams
+    int32_t *d_abort = nullptr;
+    void *d_args = nullptr;      // SysDev[], TeamDesc[], orders, block_team, reports
+    size_t args_cap = 0;
+    void *h_stage = nullptr;     // pinned staging for descriptors and reports
+    size_t stage_cap = 0;
+    double *d_tmp = nullptr;     // element scratch for apply_operator
+    size_t tmp_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // test hooks
+    uint64_t timeout_ns = 2000000000ull;
+    int32_t skip_block = -1;
+};
+
+struct mpm_subgrid {
+    bool extracted = false, assembled = false;
+    int32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+    int32_t lt[3] = {3, 3, 2};
+    int32_t nt[3] = {0, 0, 0};
+    int32_t ntiles = 0, nact = 0;
+    int64_t NE = 0, mask_voxels = 0;
+    int32_t nspecies = 0;
+    bool has_dfac = false;
+    bool x_fresh = true;         // iterate still equals c^n
+    // geometry buffers (sized by tiles)
+    void *geo = nullptr;
+    size_t geo_bytes = 0;
+    int32_t *tile_index = nullptr;   // [ntiles] compact index or -1
+    int32_t *tile_coord = nullptr;   // [nact][4] tile coords (x, y, z, pad)
+    int32_t *nbr = nullptr;          // [nact][6]
+    int8_t *active = nullptr;        // [ntiles]
+    int32_t *err = nullptr;          // assembly error flag (cell id outside the tables)
+    // element buffers
+    void *elem = nullptr;
+    size_t elem_bytes = 0;
+    uint8_t *flags = nullptr;
+    int32_t *cell = nullptr;
+    double *dfac = nullptr;
+    double *x[MPM_MAX_SPECIES] = {};
+    double *cn[MPM_MAX_SPECIES] = {};
+    double *b[MPM_MAX_SPECIES] = {};
+    double *diag[MPM_MAX_SPECIES] = {};
+    float *diag32[MPM_MAX_SPECIES] = {};
+    // Krylov basis
+    void *krylov = nullptr;
+    size_t krylov_bytes = 0;
+    // assembled scalars
+    double off[MPM_MAX_SPECIES] = {};
+    double a = 0.0;
+    double Dsp[MPM_MAX_SPECIES] = {};
+};
+
+// ------------------------------------------------------------------ host helpers (api.cu)
+mpm_status mpm_fail(mpm_ctx *ctx, mpm_status st, const std::string &msg);
+mpm_status mpm_cuda_check(mpm_ctx *ctx, cudaError_t e, const char *what);
+mpm_status mpm_grow(mpm_ctx *ctx, void **p, size_t *cap, size_t need, const char *what);
+
+#define MPM_CU(call)                                                       \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return mpm_cuda_check(ctx, e_, #call);      \
+    } while (0)
+
+// kernels' host launchers (extract.cu, assemble.cu, solver.cu)
+mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
+                            const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st);
+mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, cudaStream_t st);
+mpm_status mpm_scatter_impl(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st);
+mpm_status mpm_export_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst,
+                           cudaStream_t st);
+mpm_status mpm_import_impl(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const double *src, cudaStream_t st);
+mpm_status mpm_apply_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const double *x, double *y,
+                          cudaStream_t st);
+mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
+                          int32_t nsys, const mpm_opts *opt, mpm_report *reps, cudaStream_t st);

@@ -1,0 +1,327 @@
+"""Thin Python binding of the C ABI in include/mpm.h (argument marshalling only).
+
+Every entry point keeps its C name.  PyTorch provides device memory and
+streams; every step of the method runs in the CUDA library.  There is no
+fallback: if libmpm.so is missing or no GPU is present, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+MAX_SPECIES = 4
+MAX_RESTART = 32
+
+OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_EMPTY", "ERR_NOCONV", "ERR_BREAKDOWN", "ERR_TIMEOUT", "ERR_CUDA", "ERR_NOMEM"]
+EXPORT_X, EXPORT_RHS, EXPORT_DIAG, EXPORT_FLAGS, EXPORT_CELL = range(5)
+DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK = 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
+
+# symbols declared in include/mpm.h
+SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", "mpm_subgrid_destroy",
+           "mpm_subgrid_info", "mpm_box_extract", "mpm_assemble_coeffs", "mpm_solve_step", "mpm_solve_batch",
+           "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set"]
+
+
+class mpm_box(C.Structure):
+    _fields_ = [("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3)]
+
+    def as_tuple(self):
+        return tuple(self.lo), tuple(self.hi)
+
+
+class mpm_lattice(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("cell_id", C.c_void_p), ("mask", C.c_void_p), ("dfac", C.c_void_p),
+                ("field", C.c_void_p * MAX_SPECIES)]
+
+
+class mpm_params(C.Structure):
+    _fields_ = [("nspecies", C.c_int32), ("ncell", C.c_int32), ("dt", C.c_double), ("h", C.c_double),
+                ("D", C.c_double * MAX_SPECIES), ("mu", C.c_double * MAX_SPECIES),
+                ("c_bc", C.c_double * MAX_SPECIES), ("k_cell", C.c_void_p), ("q_cell", C.c_void_p),
+                ("bc_box", C.c_int32)]
+
+
+class mpm_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
+                ("precision", C.c_int32), ("inner_rtol", C.c_double), ("x0_given", C.c_int32),
+                ("nblocks", C.c_int32)]
+
+
+class mpm_report(C.Structure):
+    _fields_ = [("iters", C.c_int32 * MAX_SPECIES), ("cycles", C.c_int32 * MAX_SPECIES),
+                ("status", C.c_int32 * MAX_SPECIES), ("res", C.c_double * MAX_SPECIES),
+                ("bnorm", C.c_double * MAX_SPECIES), ("box_voxels", C.c_int64), ("mask_voxels", C.c_int64),
+                ("stored_voxels", C.c_int64), ("solve_ms", C.c_double)]
+
+    def as_dict(self, nspecies):
+        return {"iters": list(self.iters[:nspecies]), "cycles": list(self.cycles[:nspecies]),
+                "status": list(self.status[:nspecies]), "res": list(self.res[:nspecies]),
+                "bnorm": list(self.bnorm[:nspecies]), "box_voxels": self.box_voxels,
+                "mask_voxels": self.mask_voxels, "stored_voxels": self.stored_voxels, "solve_ms": self.solve_ms}
+
+
+class mpm_subgrid_desc(C.Structure):
+    _fields_ = [("box", mpm_box), ("n", C.c_int32 * 3), ("tile", C.c_int32 * 3), ("ntiles", C.c_int32),
+                ("nactive", C.c_int32), ("stored_voxels", C.c_int64), ("mask_voxels", C.c_int64),
+                ("nspecies", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmpm.so (built by paper_2505_03067_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "mpm_create": [C.POINTER(P), C.c_size_t],
+        "mpm_destroy": [P],
+        "mpm_last_error": [P],
+        "mpm_subgrid_create": [P, C.POINTER(P)],
+        "mpm_subgrid_destroy": [P, P],
+        "mpm_subgrid_info": [P, C.POINTER(mpm_subgrid_desc)],
+        "mpm_box_extract": [P, C.POINTER(mpm_lattice), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                            C.POINTER(mpm_box), P, P],
+        "mpm_assemble_coeffs": [P, P, C.POINTER(mpm_params), P],
+        "mpm_solve_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
+        "mpm_solve_batch": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.c_int32, C.POINTER(mpm_opts),
+                            C.POINTER(mpm_report), P],
+        "mpm_subgrid_export": [P, P, C.c_int32, C.c_int32, P, P],
+        "mpm_subgrid_import": [P, P, C.c_int32, P, P],
+        "mpm_apply_operator": [P, P, C.c_int32, P, P, P],
+        "mpm_scatter": [P, P, C.POINTER(mpm_lattice), P],
+        "mpm_debug_set": [P, C.c_int32, C.c_int64],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name == "mpm_last_error" else C.c_int
+    _lib = lib
+    return lib
+
+
+class MpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ marshalling helpers
+class DeviceLattice:
+    """A lattice held in device memory (torch tensors) and its mpm_lattice view."""
+
+    def __init__(self, lat, device="cuda"):
+        import torch
+        self.cell_id = torch.from_numpy(np.ascontiguousarray(lat.cell_id, np.int32)).to(device)
+        self.mask = torch.from_numpy(np.ascontiguousarray(lat.mask, np.uint8)).to(device)
+        self.dfac = None if lat.dfac is None else torch.from_numpy(np.ascontiguousarray(lat.dfac, np.float64)).to(device)
+        self.fields = torch.from_numpy(np.ascontiguousarray(lat.fields, np.float64)).to(device)
+        self.nspecies = int(self.fields.shape[0])
+        self.dims = (int(lat.cell_id.shape[2]), int(lat.cell_id.shape[1]), int(lat.cell_id.shape[0]))
+
+    def struct(self) -> mpm_lattice:
+        s = mpm_lattice()
+        s.dims[:] = self.dims
+        s.cell_id = self.cell_id.data_ptr()
+        s.mask = self.mask.data_ptr()
+        s.dfac = self.dfac.data_ptr() if self.dfac is not None else None
+        for k in range(self.nspecies):
+            s.field[k] = self.fields[k].data_ptr()
+        return s
+
+    def fields_numpy(self) -> np.ndarray:
+        return self.fields.cpu().numpy()
+
+
+class DeviceParams:
+    def __init__(self, params, bc_box=0, device="cuda"):
+        import torch
+        S = params.nspecies
+        self.k = torch.from_numpy(np.ascontiguousarray(params.k_cell[:S], np.float64)).to(device)
+        self.q = torch.from_numpy(np.ascontiguousarray(params.q_cell[:S], np.float64)).to(device)
+        p = mpm_params()
+        p.nspecies = S
+        p.ncell = int(params.k_cell.shape[1])
+        p.dt = float(params.dt)
+        p.h = float(params.h)
+        for s in range(S):
+            p.D[s] = float(params.D[s])
+            p.mu[s] = float(params.mu[s])
+            p.c_bc[s] = float(params.c_bc[s])
+        p.k_cell = self.k.data_ptr()
+        p.q_cell = self.q.data_ptr()
+        p.bc_box = int(bc_box)
+        self.struct = p
+
+
+def make_opts(rtol=1e-6, atol=0.0, restart=30, maxit=1000, precision=0, inner_rtol=1e-5, x0_given=0,
+              nblocks=0) -> mpm_opts:
+    o = mpm_opts()
+    o.rtol, o.atol, o.restart, o.maxit = rtol, atol, restart, maxit
+    o.precision, o.inner_rtol, o.x0_given, o.nblocks = precision, inner_rtol, x0_given, nblocks
+    return o
+
+
+class Context:
+    """Owns an mpm_ctx; the methods are the C entry points with Python arguments."""
+
+    def __init__(self, workspace_bytes: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        self.lib = load()
+        torch.cuda.init()
+        self.ptr = C.c_void_p()
+        self._check(self.lib.mpm_create(C.byref(self.ptr), workspace_bytes), "mpm_create")
+
+    def _check(self, st, what, allow=()):
+        if st != OK and st not in allow:
+            msg = self.lib.mpm_last_error(self.ptr).decode() if self.ptr else what
+            raise MpmError(st, f"{what}: {msg}")
+        return st
+
+    def close(self):
+        if self.ptr:
+            self.lib.mpm_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        return self.lib.mpm_last_error(self.ptr).decode()
+
+    def debug_set(self, key: int, value: int):
+        self._check(self.lib.mpm_debug_set(self.ptr, key, value), "mpm_debug_set")
+
+    def subgrid_create(self) -> "Subgrid":
+        h = C.c_void_p()
+        self._check(self.lib.mpm_subgrid_create(self.ptr, C.byref(h)), "mpm_subgrid_create")
+        return Subgrid(self, h)
+
+
+class Subgrid:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+        self.nspecies = 0
+
+    def destroy(self):
+        if self.h:
+            self.ctx.lib.mpm_subgrid_destroy(self.ctx.ptr, self.h)
+            self.h = C.c_void_p()
+
+    def info(self) -> dict:
+        d = mpm_subgrid_desc()
+        self.ctx._check(self.ctx.lib.mpm_subgrid_info(self.h, C.byref(d)), "mpm_subgrid_info")
+        return {"box": d.box.as_tuple(), "n": tuple(d.n), "tile": tuple(d.tile), "ntiles": d.ntiles,
+                "nactive": d.nactive, "stored_voxels": d.stored_voxels, "mask_voxels": d.mask_voxels,
+                "nspecies": d.nspecies}
+
+    def mpm_box_extract(self, lat: DeviceLattice, nspecies: int, margin: int, tile=None, stream=None):
+        box = mpm_box()
+        ls = lat.struct()
+        t = (C.c_int32 * 3)(*tile) if tile is not None else None
+        st = self.ctx.lib.mpm_box_extract(self.ctx.ptr, C.byref(ls), nspecies, margin, t, C.byref(box), self.h,
+                                          _stream_ptr(stream))
+        self.ctx._check(st, "mpm_box_extract", allow=(ERR_EMPTY,))
+        if st == ERR_EMPTY:
+            return None
+        self.nspecies = nspecies
+        return box.as_tuple()
+
+    def mpm_assemble_coeffs(self, prm: DeviceParams, stream=None):
+        self.ctx._check(self.ctx.lib.mpm_assemble_coeffs(self.ctx.ptr, self.h, C.byref(prm.struct),
+                                                         _stream_ptr(stream)), "mpm_assemble_coeffs")
+
+    def mpm_solve_step(self, opts: mpm_opts, scatter_to: DeviceLattice | None = None, stream=None,
+                       allow=(ERR_NOCONV,)):
+        rep = mpm_report()
+        ls = scatter_to.struct() if scatter_to is not None else None
+        st = self.ctx.lib.mpm_solve_step(self.ctx.ptr, self.h, C.byref(ls) if ls is not None else None,
+                                         C.byref(opts), C.byref(rep), _stream_ptr(stream))
+        self.ctx._check(st, "mpm_solve_step", allow=allow)
+        d = rep.as_dict(self.nspecies)
+        d["status_code"] = st
+        return d
+
+    def mpm_subgrid_export(self, what: int, s: int = 0, stream=None):
+        import torch
+        info = self.info()
+        nx, ny, nz = info["n"]
+        dt = {EXPORT_X: torch.float64, EXPORT_RHS: torch.float64, EXPORT_DIAG: torch.float64,
+              EXPORT_FLAGS: torch.uint8, EXPORT_CELL: torch.int32}[what]
+        out = torch.empty((nz, ny, nx), dtype=dt, device="cuda")
+        self.ctx._check(self.ctx.lib.mpm_subgrid_export(self.ctx.ptr, self.h, what, s, C.c_void_p(out.data_ptr()),
+                                                        _stream_ptr(stream)), "mpm_subgrid_export")
+        return out
+
+    def mpm_subgrid_import(self, s: int, src, stream=None):
+        self.ctx._check(self.ctx.lib.mpm_subgrid_import(self.ctx.ptr, self.h, s, C.c_void_p(src.data_ptr()),
+                                                        _stream_ptr(stream)), "mpm_subgrid_import")
+
+    def mpm_apply_operator(self, s: int, x, stream=None):
+        import torch
+        y = torch.empty_like(x)
+        self.ctx._check(self.ctx.lib.mpm_apply_operator(self.ctx.ptr, self.h, s, C.c_void_p(x.data_ptr()),
+                                                        C.c_void_p(y.data_ptr()), _stream_ptr(stream)),
+                        "mpm_apply_operator")
+        return y
+
+    def mpm_scatter(self, lat: DeviceLattice, stream=None):
+        ls = lat.struct()
+        self.ctx._check(self.ctx.lib.mpm_scatter(self.ctx.ptr, self.h, C.byref(ls), _stream_ptr(stream)),
+                        "mpm_scatter")
+
+
+def mpm_solve_batch(ctx: Context, subs, opts: mpm_opts, scatter_to=None, stream=None, allow=(ERR_NOCONV,)):
+    n = len(subs)
+    hs = (C.c_void_p * n)(*[s.h.value for s in subs])
+    lat_structs = []
+    lat_ptrs = None
+    if scatter_to is not None:
+        lat_structs = [None if l is None else l.struct() for l in scatter_to]
+        lat_ptrs = (C.POINTER(mpm_lattice) * n)(*[C.pointer(l) if l is not None else C.POINTER(mpm_lattice)()
+                                                  for l in lat_structs])
+    reps = (mpm_report * n)()
+    st = ctx.lib.mpm_solve_batch(ctx.ptr, hs, lat_ptrs, n, C.byref(opts), reps, _stream_ptr(stream))
+    ctx._check(st, "mpm_solve_batch", allow=allow)
+    return st, [reps[i].as_dict(subs[i].nspecies) for i in range(n)]
+
+
+class StepSolver:
+    """One implicit-Euler step of every species on a device lattice:
+    mpm_box_extract -> mpm_assemble_coeffs -> mpm_solve_step (with scatter)."""
+
+    def __init__(self, ctx: Context, lat: DeviceLattice, prm: DeviceParams, margin: int, tile=None):
+        self.ctx, self.lat, self.prm, self.margin, self.tile = ctx, lat, prm, margin, tile
+        self.sub = ctx.subgrid_create()
+
+    def step(self, opts: mpm_opts, stream=None, allow=(ERR_NOCONV,)):
+        box = self.sub.mpm_box_extract(self.lat, self.lat.nspecies, self.margin, self.tile, stream)
+        if box is None:
+            return {"status_code": ERR_EMPTY, "box": None}
+        self.sub.mpm_assemble_coeffs(self.prm, stream)
+        rep = self.sub.mpm_solve_step(opts, scatter_to=self.lat, stream=stream, allow=allow)
+        rep["box"] = box
+        return rep

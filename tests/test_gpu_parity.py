@@ -1,0 +1,336 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact for the box extraction (integers, bytes, copies); FP64 solves within
+1e-10 max-abs of the oracle when both are driven to ||r||_2 <= 1e-13 (the error
+of each is then below its residual, ||A^-1||_2 <= 1); the FP32-in-FP64 path
+within 1e-6 relative to the FP64 oracle solution with its own true residual
+below 1e-6 ||b||.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_03067_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(8, 8, 4), (4, 4, 4), (32, 4, 2), (8, 4, 1), (16, 16, 4)]
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_03067_gb300 import build, mpm
+    build.build()
+    return mpm
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    return M.Context()
+
+
+def _expected_flags(mask_box):
+    m = mask_box > 0
+    f = np.zeros(mask_box.shape, np.uint8)
+    f[m] |= 64
+    nz, ny, nx = m.shape
+    sh = [((slice(None), slice(None), slice(1, None)), (slice(None), slice(None), slice(0, -1)), 1),   # -x
+          ((slice(None), slice(None), slice(0, -1)), (slice(None), slice(None), slice(1, None)), 2),   # +x
+          ((slice(None), slice(1, None), slice(None)), (slice(None), slice(0, -1), slice(None)), 4),   # -y
+          ((slice(None), slice(0, -1), slice(None)), (slice(None), slice(1, None), slice(None)), 8),   # +y
+          ((slice(1, None), slice(None), slice(None)), (slice(0, -1), slice(None), slice(None)), 16),  # -z
+          ((slice(0, -1), slice(None), slice(None)), (slice(1, None), slice(None), slice(None)), 32)]  # +z
+    for me, nb, bit in sh:
+        both = m[me] & m[nb]
+        f[me] |= (both * bit).astype(np.uint8)
+    return f
+
+
+def _active_tiles(mask_box, tile):
+    tx, ty, tz = tile
+    nz, ny, nx = mask_box.shape
+    act = np.zeros(mask_box.shape, bool)
+    for k in range(0, nz, tz):
+        for j in range(0, ny, ty):
+            for i in range(0, nx, tx):
+                blk = mask_box[k:k + tz, j:j + ty, i:i + tx]
+                if blk.any():
+                    act[k:k + tz, j:j + ty, i:i + tx] = True
+    return act
+
+
+CASES = [(0, (21, 13, 11)), (1, (8, 8, 8)), (2, (33, 17, 5)), (3, (1, 1, 1)), (4, (40, 3, 9)), (5, (17, 29, 23))]
+
+
+@pytest.mark.parametrize("seed,dims", CASES)
+@pytest.mark.parametrize("tile", TILES[:3])
+def test_extract_is_bit_exact(M, ctx, seed, dims, tile):
+    wl = W.random_case(seed, dims, nspecies=3, dfac=(seed % 2 == 0))
+    if seed == 3:
+        wl.lattice.cell_id[:] = 1
+        wl.lattice.mask[:] = 1
+    lat = M.DeviceLattice(wl.lattice)
+    sub = ctx.subgrid_create()
+    box = sub.mpm_box_extract(lat, 3, wl.margin, tile)
+    assert box == oracle.bbox(wl.lattice.cell_id, wl.margin)
+    mb = oracle.box_view(wl.lattice.mask, box)
+    act = _active_tiles(mb, tile)
+    info = sub.info()
+    assert info["mask_voxels"] == int(mb.sum())
+    assert info["stored_voxels"] == info["nactive"] * tile[0] * tile[1] * tile[2]
+    flags = sub.mpm_subgrid_export(M.EXPORT_FLAGS).cpu().numpy()
+    exp = np.where(act, _expected_flags(mb) | 128, 0).astype(np.uint8)
+    assert np.array_equal(flags, exp)
+    cell = sub.mpm_subgrid_export(M.EXPORT_CELL).cpu().numpy()
+    assert np.array_equal(cell, np.where(act, oracle.box_view(wl.lattice.cell_id, box), 0))
+    for s in range(3):
+        x = sub.mpm_subgrid_export(M.EXPORT_X, s).cpu().numpy()
+        assert np.array_equal(x, np.where(act, oracle.box_view(wl.lattice.fields[s], box), 0.0))
+    sub.destroy()
+
+
+@pytest.mark.parametrize("seed,dims", CASES[:3] + CASES[4:])
+@pytest.mark.parametrize("bc_box", [0, 1])
+def test_assembly_and_operator_match_oracle_csr(M, ctx, seed, dims, bc_box):
+    import torch
+    wl = W.random_case(seed, dims, nspecies=3, dfac=(seed % 2 == 1))
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params, bc_box=bc_box)
+    sub = ctx.subgrid_create()
+    box = sub.mpm_box_extract(lat, 3, wl.margin, (8, 4, 2))
+    sub.mpm_assemble_coeffs(prm)
+    mb, cb, = (oracle.box_view(a, box) for a in (wl.lattice.mask, wl.lattice.cell_id))
+    dfb = None if wl.lattice.dfac is None else oracle.box_view(wl.lattice.dfac, box)
+    rng = np.random.default_rng(seed + 100)
+    for s in range(3):
+        A, b = oracle.assemble(mb, cb, oracle.box_view(wl.lattice.fields[s], box), wl.params, s, bc_box, dfb)
+        D = np.zeros(A.N)
+        for r in range(A.N):
+            for e in range(A.row_ptr[r], A.row_ptr[r + 1]):
+                if A.col[e] == r:
+                    D[r] = A.val[e]
+        act = _active_tiles(mb, (8, 4, 2))
+        dg = sub.mpm_subgrid_export(M.EXPORT_DIAG, s).cpu().numpy().reshape(-1)
+        rhs = sub.mpm_subgrid_export(M.EXPORT_RHS, s).cpu().numpy().reshape(-1)
+        a = act.reshape(-1)
+        assert np.max(np.abs(dg[a] - D[a]) / np.abs(D[a])) < 1e-14
+        assert np.max(np.abs(rhs[a] - b.reshape(-1)[a])) <= 1e-14 * max(1.0, np.abs(b).max())
+        x = rng.uniform(-1, 1, mb.shape)
+        y = sub.mpm_apply_operator(s, torch.from_numpy(x).cuda()).cpu().numpy().reshape(-1)
+        yref = A.matvec(x)
+        assert np.max(np.abs(y - yref)) <= 1e-13 * max(1.0, np.abs(yref).max())
+    sub.destroy()
+
+
+def _gpu_step(M, ctx, wl, opts, tile=None, lat=None, prm=None, allow=None):
+    lat = lat or M.DeviceLattice(wl.lattice)
+    prm = prm or M.DeviceParams(wl.params)
+    solver = M.StepSolver(ctx, lat, prm, wl.margin, tile)
+    rep = solver.step(opts, allow=allow if allow is not None else (M.ERR_NOCONV,))
+    return lat, rep
+
+
+@pytest.mark.parametrize("seed,dims", CASES)
+@pytest.mark.parametrize("tile", TILES)
+def test_fp64_solve_matches_oracle(M, ctx, seed, dims, tile):
+    wl = W.random_case(seed, dims, nspecies=3, dfac=(seed % 3 == 0))
+    ref = wl.lattice.copy()
+    ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=16, maxit=2000), tile)
+    assert rep["status_code"] == M.OK
+    assert all(r <= 1e-13 for r in rep["res"])
+    got = lat.fields_numpy()
+    assert np.max(np.abs(got - ref.fields)) <= 1e-10
+
+
+@pytest.mark.parametrize("restart", [2, 5, 8, 30])
+def test_restart_lengths_agree(M, ctx, restart):
+    wl = W.random_case(9, (19, 18, 17), nspecies=3)
+    ref = wl.lattice.copy()
+    oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=restart, maxit=5000))
+    assert rep["status_code"] == M.OK
+    if restart < 8:
+        assert max(rep["cycles"]) > 1
+    assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+
+
+def test_sphere32_ten_steps_fp64(M, ctx):
+    """The 32^3 single-species workload, 10 implicit-Euler steps, GMRES(30): parity
+    run with both sides at ||r||_2 <= 1e-13 per step (10 steps add at most 1e-12
+    each), max-abs within 1e-10; then the 1e-10-relative run, whose distance to the
+    parity solution is bounded by the sum of its per-step residual norms."""
+    wl = W.sphere32()
+    ref = wl.lattice.copy()
+    for _ in range(wl.steps):
+        assert oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)["status"] == oracle.OK
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    solver = M.StepSolver(ctx, lat, prm, wl.margin)
+    for _ in range(wl.steps):
+        rep = solver.step(M.make_opts(rtol=0.0, atol=1e-13, restart=30, maxit=1000))
+        assert rep["status_code"] == M.OK and rep["box"] == ((0, 0, 0), (32, 32, 32))
+    assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+    lat2 = M.DeviceLattice(wl.lattice)
+    solver2 = M.StepSolver(ctx, lat2, prm, wl.margin)
+    bound = 0.0
+    for _ in range(wl.steps):
+        rep = solver2.step(M.make_opts(rtol=wl.rtol, restart=30, maxit=1000))
+        assert rep["status_code"] == M.OK
+        assert rep["res"][0] <= 1e-10 * rep["bnorm"][0]
+        bound += rep["res"][0]
+    assert np.max(np.abs(lat2.fields_numpy() - ref.fields)) <= bound + 1e-12
+
+
+@pytest.mark.parametrize("seed,dims", CASES[:3] + [(6, (45, 37, 29))])
+def test_mixed_precision_within_1e6_of_fp64(M, ctx, seed, dims):
+    wl = W.random_case(seed, dims, nspecies=3)
+    ref = wl.lattice.copy()
+    oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=1e-6, restart=16, maxit=500, precision=1, inner_rtol=1e-5))
+    assert rep["status_code"] == M.OK
+    got = lat.fields_numpy()
+    box = rep["box"]
+    mb = oracle.box_view(wl.lattice.mask, box) > 0
+    for s in range(3):
+        assert rep["res"][s] <= 1e-6 * rep["bnorm"][s]
+        g = oracle.box_view(got[s], box)[mb]
+        r = oracle.box_view(ref.fields[s], box)[mb]
+        assert np.linalg.norm(g - r) <= 1e-6 * np.linalg.norm(r)
+        # the residual claimed by the GPU, recomputed by the oracle on the GPU's answer
+        A, b = oracle.assemble(oracle.box_view(wl.lattice.mask, box), oracle.box_view(wl.lattice.cell_id, box),
+                               oracle.box_view(wl.lattice.fields[s], box), wl.params, s)
+        xr = oracle.box_view(got[s], box).reshape(-1)
+        assert abs(np.linalg.norm(b.reshape(-1) - A.matvec(xr)) - rep["res"][s]) <= 1e-9 * rep["bnorm"][s]
+
+
+def test_deterministic(M, ctx):
+    wl = W.random_case(2, (33, 17, 25), nspecies=3)
+    outs = []
+    for _ in range(2):
+        lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=1e-8, restart=16, maxit=500))
+        outs.append(lat.fields_numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------- edge cases and failures
+def test_empty_tumour_is_reported_and_changes_nothing(M, ctx):
+    wl = W.random_case(1, (9, 9, 9))
+    wl.lattice.cell_id[:] = 0
+    lat = M.DeviceLattice(wl.lattice)
+    sub = ctx.subgrid_create()
+    assert sub.mpm_box_extract(lat, 3, 2) is None
+    assert np.array_equal(lat.fields_numpy(), wl.lattice.fields)
+
+
+def test_tumour_outside_mask_has_no_unknowns(M, ctx):
+    wl = W.random_case(4, (12, 12, 12))
+    wl.lattice.mask[:] = 0
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts())
+    assert rep["status_code"] == M.OK and rep["stored_voxels"] == 0
+    assert np.array_equal(lat.fields_numpy(), wl.lattice.fields)
+
+
+def test_single_voxel_tumour_margin_clamped(M, ctx):
+    wl = W.random_case(5, (10, 11, 12), nspecies=2)
+    wl.lattice.cell_id[:] = 0
+    wl.lattice.cell_id[0, 0, 9] = 3
+    ref = wl.lattice.copy()
+    ro = oracle.step(ref, wl.params, 3, rtol=0.0, atol=1e-13)
+    wl.margin = 3
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=8))
+    assert rep["box"] == ro["box"] == ((6, 0, 0), (10, 4, 4))
+    assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+
+
+def test_maxit_reports_noconv_and_keeps_best_iterate(M, ctx):
+    wl = W.random_case(3, (16, 16, 16), nspecies=3)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=1e-14, restart=8, maxit=1))
+    assert rep["status_code"] == M.ERR_NOCONV
+    assert all(st == M.ERR_NOCONV for st in rep["status"]) and rep["iters"] == [1, 1, 1]
+    assert not np.array_equal(lat.fields_numpy(), wl.lattice.fields)
+
+
+def test_nan_input_reports_breakdown(M, ctx):
+    wl = W.random_case(3, (16, 16, 16), nspecies=3)
+    box = oracle.bbox(wl.lattice.cell_id, wl.margin)
+    sl = oracle.box_slices(box)
+    inm = np.argwhere(wl.lattice.mask[sl] > 0)[0]
+    wl.lattice.fields[1][sl][tuple(inm)] = np.nan
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(), allow=(M.ERR_BREAKDOWN,))
+    assert rep["status_code"] == M.ERR_BREAKDOWN
+    assert rep["status"][1] == M.ERR_BREAKDOWN
+    assert rep["status"][0] == M.OK and rep["status"][2] == M.OK
+
+
+def test_cell_id_outside_tables_is_an_argument_error(M, ctx):
+    wl = W.random_case(3, (16, 16, 16), nspecies=1)
+    wl.lattice.cell_id[wl.lattice.mask > 0] = 999
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    sub = ctx.subgrid_create()
+    sub.mpm_box_extract(lat, 1, 1)
+    sub.mpm_assemble_coeffs(prm)
+    with pytest.raises(M.MpmError) as ei:
+        sub.mpm_solve_step(M.make_opts())
+    assert ei.value.status == M.ERR_ARG
+    # later solves on a clean subgrid work again
+    wl2 = W.random_case(3, (16, 16, 16), nspecies=1)
+    lat2, rep = _gpu_step(M, M.Context(), wl2, M.make_opts())
+    assert rep["status_code"] == M.OK
+
+
+def test_missing_partner_cta_times_out_and_context_survives(M):
+    """A CTA that never arrives (host-set skip flag): its partners' bounded waits
+    expire, the solve returns MPM_ERR_TIMEOUT, and the same context then solves."""
+    c = M.Context()
+    wl = W.random_case(2, (33, 17, 25), nspecies=3)
+    c.debug_set(M.DEBUG_TIMEOUT_NS, 50_000_000)
+    c.debug_set(M.DEBUG_SKIP_BLOCK, 0)
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    solver = M.StepSolver(c, lat, prm, wl.margin)
+    with pytest.raises(M.MpmError) as ei:
+        solver.step(M.make_opts(nblocks=4))
+    assert ei.value.status == M.ERR_TIMEOUT
+    assert np.array_equal(lat.fields_numpy(), wl.lattice.fields)
+    c.debug_set(M.DEBUG_SKIP_BLOCK, -1)
+    rep = solver.step(M.make_opts(nblocks=4))
+    assert rep["status_code"] == M.OK
+
+
+# ---------------------------------------------------------------- full-size workload
+@pytest.fixture(scope="module")
+def shell256():
+    return W.shell256()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_shell256_first_step_matches_oracle(M, ctx, shell256, precision):
+    """The 256^3 three-species pleural-shell workload, first step, in the launch
+    configuration the benchmark times (default grid, tile 8x8x4, GMRES(16)),
+    compared with the oracle on every in-mask voxel of the box."""
+    wl = shell256
+    ref = wl.lattice.copy()
+    ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-11)
+    assert ro["status"] == oracle.OK
+    if precision == 0:
+        opts = M.make_opts(rtol=0.0, atol=1e-11, restart=16, maxit=500)
+    else:
+        opts = M.make_opts(rtol=1e-6, restart=16, maxit=500, precision=1, inner_rtol=1e-5)
+    lat, rep = _gpu_step(M, ctx, wl, opts)
+    assert rep["status_code"] == M.OK and rep["box"] == ro["box"]
+    assert rep["mask_voxels"] == ro["mask_voxels"]
+    got = lat.fields_numpy()
+    box = ro["box"]
+    mb = oracle.box_view(wl.lattice.mask, box) > 0
+    for s in range(3):
+        g = oracle.box_view(got[s], box)[mb]
+        r = oracle.box_view(ref.fields[s], box)[mb]
+        if precision == 0:
+            assert np.max(np.abs(g - r)) <= 1e-10
+        else:
+            assert np.linalg.norm(g - r) <= 1e-6 * np.linalg.norm(r)
