@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the box-restricted implicit-Euler reaction-diffusion step.
+
+Metric: species-voxel-steps/s at 1e-6 relative residual (sum over steps and
+species of the in-mask voxels of the box, per second), plain FP64 GMRES against
+the FP32-in-FP64-refinement path, on the 256^3 three-species pleural-shell
+workload (2000 Voronoi tumour cells in a 128x128x96 region of the shell, bbox
+margin 4, D = (1, 0.5, 0.2), dt = 0.05, 20 steps).
+
+One bench step = one implicit-Euler step of the whole hot path through the C
+ABI: bounding box + gather (mpm_box_extract), assembly (mpm_assemble_coeffs),
+GMRES for the three species and the scatter onto the mask (mpm_solve_step).
+The lattice is resident in HBM; L2 is flushed (256 MB write) before every timed
+step.  `e2e` repeats the steps with the lattice in pinned host memory, copying
+it in and the fields out inside the timed region.
+
+--impl reference times the CPU oracle (single thread) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "species-voxel-steps/s at 1e-6 rel. residual: plain FP64 GMRES vs learned+mixed"
+WORKLOAD = ("shell256: 256^3 int32 CPM lattice, pleural-shell mask (ellipsoids 110/90/120 and 100/80/110), "
+            "2000 Voronoi tumour cells in a 128x128x96 shell region, bbox+4, 3 species, D=(1,0.5,0.2), "
+            "dt=0.05, per-cell rates U[0.01,0.1], 20 implicit-Euler steps, rtol 1e-6")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def solver_bytes(rep, NE, bT):
+    """Algorithmic bytes of one solver launch (per stored element, summed over
+    species): R = x, b, diag64 (8 each) + flags (1) + write u0 (bT);
+    P1_j = flags + u_j, diag, u_0..u_{j-1} + write w = 1 + (j+3) bT;
+    P2_j = read w, u_0..u_j + write w = (j+3) bT;  U = read V (k bT) + x r/w (16)."""
+    tot = 0
+    for s in range(len(rep["iters"])):
+        it, C, js = rep["iters"][s], rep["cycles"][s], rep["jsum"][s]
+        R = 25 + bT
+        P = it * (1 + 6 * bT) + 2 * bT * js
+        U = 16 * C + bT * it
+        tot += NE * (R * (C + 1) + P + U)
+    return tot
+
+
+def solver_fp64_ops(rep, NE, fp32):
+    """FP64 instructions of one solver launch per the same pass structure (an FMA,
+    an add or a convert each count one): R 10; FP64 path P1_j 8 + (j+1), P2_j
+    (j+2), U k; FP32 path U 1 per cycle (x += d)."""
+    tot = 0
+    for s in range(len(rep["iters"])):
+        it, C, js = rep["iters"][s], rep["cycles"][s], rep["jsum"][s]
+        r = 10 * (C + 1)
+        if fp32:
+            r += 2 * C
+        else:
+            r += it * 8 + (js + it) + (js + 2 * it) + it
+        tot += NE * r
+    return tot
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_record(kernel_key):
+    """Per-launch DRAM bytes of the solver kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged (hash recorded with it)."""
+    p = os.path.join(ROOT, "profiles", "k_gmres_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in ("solver.cu", "mpm_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2505_03067_gb300", "csrc", f), "rb").read())
+    rec = d.get(kernel_key)
+    if not rec or rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+def cpu_baseline(wl, nsteps):
+    import oracle
+    lat = wl.lattice.copy()
+    oracle.step(lat.copy(), wl.params, wl.margin, rtol=1e-6)       # load/build outside the timing
+    units = 0
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        rep = oracle.step(lat, wl.params, wl.margin, rtol=wl.rtol, restart=wl.restart)
+        units += rep["mask_voxels"] * wl.params.nspecies
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": "species-voxel-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {nsteps} implicit-Euler steps of shell256 (all 3 species, every in-mask voxel), "
+                      f"single-threaded C/numpy oracle, GMRES(30) to 1e-6, {dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    import numpy as np  # noqa: F401
+    if rank != 0:
+        return 0
+    from paper_2505_03067_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    wl = W.shell256()
+    lat = wl.lattice.copy()
+    for _ in range(args.warmup):
+        oracle.step(lat, wl.params, wl.margin, rtol=wl.rtol, restart=wl.restart)
+    lat = wl.lattice.copy()
+    units = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rep = oracle.step(lat, wl.params, wl.margin, rtol=wl.rtol, restart=wl.restart)
+        units += rep["mask_voxels"] * wl.params.nspecies
+    dt = time.perf_counter() - t0
+    v = units / dt
+    line = {"metric": METRIC, "value": v, "unit": "species-voxel-steps/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "path": "CPU oracle, FP64 MGS-GMRES(30)"},
+            "cpu_baseline": {"value": v, "unit": "species-voxel-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full implicit-Euler steps of shell256 (single-threaded oracle)"},
+            "e2e": {"value": v, "unit": "species-voxel-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--restart", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2505_03067_gb300 import mpm
+    from paper_2505_03067_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = W.shell256()
+    ctx = mpm.Context()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    S = wl.params.nspecies
+    paths = {"fp64": dict(precision=0), "mixed": dict(precision=1, inner_rtol=1e-6)}
+    results = {}
+    clocks = None
+    for name, extra in paths.items():
+        opts = mpm.make_opts(rtol=wl.rtol, restart=args.restart, maxit=1000, **extra)
+        lat = mpm.DeviceLattice(wl.lattice)
+        init = lat.fields.clone()
+        prm = mpm.DeviceParams(wl.params)
+        solver = mpm.StepSolver(ctx, lat, prm, wl.margin)
+        for _ in range(args.warmup):
+            solver.step(opts)
+        lat.fields.copy_(init)
+        headline = name == "mixed"
+        sampler = ClockSampler(local) if headline else None
+        barrier()
+        if sampler:
+            sampler.start()
+        l0 = ctx.launches()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        reps = []
+        for i in range(args.steps):
+            flush.fill_(i & 255)
+            evs[i][0].record(stream)
+            rep = solver.step(opts)
+            evs[i][1].record(stream)
+            reps.append(rep)
+        barrier()
+        launches = ctx.launches() - l0
+        if sampler:
+            clocks = sampler.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        units = sum(r["mask_voxels"] * S for r in reps)
+        for r in reps:
+            assert r["status_code"] == mpm.OK, r
+            assert all(res <= wl.rtol * b for res, b in zip(r["res"], r["bnorm"])), r
+        bT = 4 if extra["precision"] else 8
+        kbytes = sum(solver_bytes(r, r["stored_voxels"], bT) for r in reps)
+        kops = sum(solver_fp64_ops(r, r["stored_voxels"], bool(extra["precision"])) for r in reps)
+        kms = sum(r["solve_ms"] for r in reps)
+        results[name] = {"value": world * units / (ms_max / 1e3), "ms_per_step": ms_max / args.steps,
+                         "kernel_ms_per_step": kms / args.steps, "kernel_bytes": kbytes, "kernel_fp64_ops": kops,
+                         "kernel_ms": kms, "launches": launches,
+                         "iters_per_step": [sum(r["iters"][s] for r in reps) / len(reps) for s in range(S)],
+                         "box_voxels": reps[0]["box_voxels"], "mask_voxels": reps[0]["mask_voxels"],
+                         "stored_voxels": reps[0]["stored_voxels"]}
+        if headline:
+            results[name]["solver"] = solver
+            results[name]["opts"] = opts
+            results[name]["lat"] = lat
+            results[name]["init"] = init
+
+    # ---- end to end through the public API with host buffers
+    head = results["mixed"]
+    lat, init, solver, opts = head["lat"], head["init"], head["solver"], head["opts"]
+    lat.fields.copy_(init)
+    h_cell = lat.cell_id.cpu().pin_memory()
+    h_mask = lat.mask.cpu().pin_memory()
+    h_fields = lat.fields.cpu().pin_memory()
+    h_out = torch.empty_like(h_fields).pin_memory()
+    bi = h_cell.numel() * 4 + h_mask.numel() + h_fields.numel() * 8
+    bo = h_out.numel() * 8
+    ne = max(1, min(args.e2e_steps, args.steps))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    units = 0
+    e2e_ms = 0.0
+    for i in range(ne):
+        flush.fill_(i & 255)
+        e0.record(stream)
+        lat.cell_id.copy_(h_cell, non_blocking=True)
+        lat.mask.copy_(h_mask, non_blocking=True)
+        lat.fields.copy_(h_fields, non_blocking=True)
+        rep = solver.step(opts)
+        h_out.copy_(lat.fields, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        h_fields.copy_(h_out)
+        units += rep["mask_voxels"] * S
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * units / (float(t.item()) / 1e3), "unit": "species-voxel-steps/s",
+           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+           "note": "lattice (cell ids, mask, 3 FP64 fields) copied in from pinned host memory and the fields "
+                   "copied out every step, through the same C-ABI calls"}
+
+    # ---- roofline of the dominant kernel (the persistent GMRES solver)
+    peak, src = _peaks()
+    ach = head["kernel_bytes"] / (head["kernel_ms"] / 1e3) / 1e9
+    fp64_rate = head["kernel_fp64_ops"] / (head["kernel_ms"] / 1e3) / 1e12
+    rec = _traffic_record("shell256_mixed")
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "of fallback",
+                "kernel": "k_gmres<float,8,1,2> (persistent cooperative GMRES, FP32 Krylov + FP64 residual)",
+                "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                "algorithmic_bytes_per_launch": head["kernel_bytes"] / args.steps,
+                "fp64_tops_achieved": fp64_rate}
+    fp = results["fp64"]
+    fp_ach = fp["kernel_bytes"] / (fp["kernel_ms"] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": head["value"], "unit": "species-voxel-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "path": "mixed: FP32 GMRES(8) inside FP64 refinement, inner cycle to max(tol/4, 1e-6 ||r||)",
+                       "l2": "flushed (256 MB write) before every timed step; lattice (486 MB) > L2",
+                       "box_voxels": head["box_voxels"], "mask_voxels": head["mask_voxels"],
+                       "stored_voxels": head["stored_voxels"], "parallelism": f"replicas x{world}"},
+            "paths": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "kernel_ms_per_step", "iters_per_step")}
+                      for k, v in results.items()},
+            "fp64_path_roofline": {"achieved_gbs": fp_ach, "frac_hbm": fp_ach / peak,
+                                   "fp64_tops": fp["kernel_fp64_ops"] / (fp["kernel_ms"] / 1e3) / 1e12,
+                                   "fp64_peak_tops_nominal": 1.25},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": head["launches"], "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -80,7 +80,8 @@ typedef struct {
     int32_t restart;        /* GMRES restart length m, 1..MPM_MAX_RESTART */
     int32_t maxit;          /* total Arnoldi steps per species */
     int32_t precision;      /* 0: FP64 throughout; 1: FP32 Krylov inside FP64 refinement */
-    double inner_rtol;      /* precision 1: reduction of each FP32 inner cycle (e.g. 1e-5) */
+    double inner_rtol;      /* precision 1: an FP32 inner cycle stops at max(tol/4, inner_rtol*||r||)
+                               (e.g. 1e-6; FP32 cannot reduce much below ~1e-7) */
     int32_t x0_given;       /* 1: the subgrid's current iterate is the initial guess
                                (set by mpm_subgrid_import); 0: c^n from the extract */
     int32_t nblocks;        /* 0: automatic; else the persistent grid size (tuning) */
@@ -90,6 +91,7 @@ typedef struct {
     int32_t iters[MPM_MAX_SPECIES];     /* Arnoldi steps */
     int32_t cycles[MPM_MAX_SPECIES];    /* restarts (refinement steps for precision 1) */
     int32_t status[MPM_MAX_SPECIES];    /* mpm_status per species */
+    int32_t jsum[MPM_MAX_SPECIES];      /* sum over Arnoldi steps of their index j in the cycle */
     double res[MPM_MAX_SPECIES];        /* final true residual ||b - A x||_2 (FP64) */
     double bnorm[MPM_MAX_SPECIES];      /* ||b||_2 over in-mask rows */
     int64_t box_voxels;                 /* nx*ny*nz */
@@ -136,12 +138,13 @@ mpm_status mpm_subgrid_info(const mpm_subgrid *sub, mpm_subgrid_desc *out);
  * of all voxels with cell_id > 0, widened by `margin` and clamped,
  *     lo = max(0, min - margin),  hi = min(L, max + margin + 1),
  * split the box into tiles of dims `tile` (powers of two, product 32..1024;
- * NULL = 8x8x4), keep the tiles that hold an in-mask voxel, and copy the mask,
+ * NULL = 8x4x4), keep the tiles that hold an in-mask voxel, and copy the mask,
  * cell ids, optional dfac and the species fields c^n of those tiles into `sub`
  * (tile-major, library-owned).  `nspecies` fields are gathered.
- * Writes the box to *out_box.  Synchronises `stream` (the box size sizes the
- * buffers).  MPM_ERR_EMPTY if no voxel has cell_id > 0 (sub and out_box are
- * then unchanged).
+ * Writes the box to *out_box.  Synchronises `stream` once (the compacted
+ * size sizes the buffers).  MPM_ERR_EMPTY if no voxel has cell_id > 0:
+ * out_box is then unchanged and sub keeps its previous extraction (unless
+ * the lattice grew, which invalidates it).
  */
 mpm_status mpm_box_extract(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
                            const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, void *stream);
@@ -205,10 +208,34 @@ mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *
  *                        (default 2e9 ns); on expiry the solve returns
  *                        MPM_ERR_TIMEOUT and the context stays usable.
  *  MPM_DEBUG_SKIP_BLOCK  CTA index that leaves the solver at once, so that its
- *                        partners' waits run out (-1 = none, the default). */
+ *                        partners' waits run out (-1 = none, the default).
+ *  MPM_DEBUG_PHASE_TIMES 1: CTA 0 of every later solve records where its time
+ *                        went (read with the MPM_COUNTER_PHASE_* counters).
+ *  MPM_DEBUG_SOLVER_VARIANT  solver kernel variant 0..3 (elements in flight per
+ *                        thread and CTAs per SM; 0 = default), for tuning. */
 #define MPM_DEBUG_TIMEOUT_NS 1
 #define MPM_DEBUG_SKIP_BLOCK 2
+#define MPM_DEBUG_PHASE_TIMES 3
+#define MPM_DEBUG_SOLVER_VARIANT 4
 mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
+
+/* Counters of the context: MPM_COUNTER_LAUNCHES = kernels launched so far by
+ * this context (every entry point counts its own launches); with
+ * MPM_DEBUG_PHASE_TIMES on, the last solve's CTA-0 nanoseconds spent in the
+ * streaming passes (WORK), waiting at team barriers (WAIT), summing the team's
+ * partial sums (REDUCE) and in the FP64 least-squares/state updates (SERIAL). */
+#define MPM_COUNTER_LAUNCHES 1
+#define MPM_COUNTER_PHASE_WORK_NS 2
+#define MPM_COUNTER_PHASE_WAIT_NS 3
+#define MPM_COUNTER_PHASE_REDUCE_NS 4
+#define MPM_COUNTER_PHASE_SERIAL_NS 5
+/* WORK split by pass: residual, Arnoldi pass 1 (matvec + dots), pass 2
+ * (orthogonalisation + norm), solution update. */
+#define MPM_COUNTER_PHASE_R_NS 6
+#define MPM_COUNTER_PHASE_P1_NS 7
+#define MPM_COUNTER_PHASE_P2_NS 8
+#define MPM_COUNTER_PHASE_U_NS 9
+mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value);
 
 #ifdef __cplusplus
 }

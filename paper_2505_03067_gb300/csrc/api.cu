@@ -108,6 +108,7 @@ mpm_status mpm_destroy(mpm_ctx *ctx)
     cudaFree(ctx->d_bar);
     cudaFree(ctx->d_args);
     cudaFree(ctx->d_tmp);
+    cudaFree(ctx->d_prof);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -227,9 +228,35 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value)
     case MPM_DEBUG_SKIP_BLOCK:
         ctx->skip_block = (int32_t)value;
         return MPM_OK;
+    case MPM_DEBUG_PHASE_TIMES:
+        ctx->phase_prof = value != 0;
+        return MPM_OK;
+    case MPM_DEBUG_SOLVER_VARIANT:
+        if (value < 0 || value > 3) return mpm_fail(ctx, MPM_ERR_ARG, "debug: solver variant out of [0, 3]");
+        ctx->solver_variant = (int32_t)value;
+        return MPM_OK;
     default:
         return mpm_fail(ctx, MPM_ERR_ARG, "debug: unknown key");
     }
+}
+
+mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)
+{
+    if (!ctx || !value) return MPM_ERR_ARG;
+    if (key == MPM_COUNTER_LAUNCHES) { *value = ctx->launches; return MPM_OK; }
+    if (key == MPM_COUNTER_PHASE_WORK_NS) {
+        *value = (int64_t)(ctx->h_prof[4] + ctx->h_prof[5] + ctx->h_prof[6] + ctx->h_prof[7]);
+        return MPM_OK;
+    }
+    if (key >= MPM_COUNTER_PHASE_WAIT_NS && key <= MPM_COUNTER_PHASE_SERIAL_NS) {
+        *value = (int64_t)ctx->h_prof[key - MPM_COUNTER_PHASE_WORK_NS];
+        return MPM_OK;
+    }
+    if (key >= MPM_COUNTER_PHASE_R_NS && key <= MPM_COUNTER_PHASE_U_NS) {
+        *value = (int64_t)ctx->h_prof[4 + key - MPM_COUNTER_PHASE_R_NS];
+        return MPM_OK;
+    }
+    return MPM_ERR_ARG;
 }
 
 }  // extern "C"

@@ -161,6 +161,7 @@ mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *p
         int64_t g = (sub->NE + kBlock - 1) / kBlock;
         if (g > (int64_t)ctx->num_sms * 8) g = (int64_t)ctx->num_sms * 8;
         k_assemble<<<(int)g, kBlock, 0, st>>>(A, sub->NE);
+        ctx->launches += 1;
         MPM_CU(cudaGetLastError());
     }
     sub->assembled = true;
@@ -188,6 +189,7 @@ mpm_status mpm_apply_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const
         int64_t g = (sub->NE + kBlock - 1) / kBlock;
         if (g > (int64_t)ctx->num_sms * 8) g = (int64_t)ctx->num_sms * 8;
         k_apply<<<(int)g, kBlock, 0, st>>>(S, s, xe, ye, sub->a, sub->Dsp[s]);
+        ctx->launches += 1;
         MPM_CU(cudaGetLastError());
     }
     return mpm_elems_to_dense(ctx, sub, ye, x, y, st);

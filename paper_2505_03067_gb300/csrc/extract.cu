@@ -89,10 +89,12 @@ struct BoxGeo {
 
 // Mark tiles holding an in-mask voxel; count the in-mask voxels of the box.
 // One warp per box row (j, k).
-__global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restrict__ mask, BoxGeo g,
+__global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restrict__ mask, const BoxGeo *__restrict__ gp,
                                                         int8_t *__restrict__ active,
                                                         unsigned long long *__restrict__ count)
 {
+    const BoxGeo g = *gp;
+    if (g.n[0] <= 0) return;                  // empty lattice: no box
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarp = (int64_t)gridDim.x * kWarps;
@@ -113,14 +115,38 @@ __global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restric
     if (lane == 0 && cnt) atomicAdd(count, cnt);
 }
 
+// Box from the reduced bounds (Sec. 2.3): lo = max(0, min - margin),
+// hi = min(L, max + margin + 1); tile counts of the box.  n[0] = 0 marks an
+// empty tumour set.
+__global__ void k_box_finalize(const int32_t *__restrict__ mnmx, int32_t margin, int32_t Lx, int32_t Ly, int32_t Lz,
+                               int32_t lt0, int32_t lt1, int32_t lt2, BoxGeo *__restrict__ g)
+{
+    if (threadIdx.x != 0) return;
+    const int32_t L[3] = {Lx, Ly, Lz};
+    const int32_t lt[3] = {lt0, lt1, lt2};
+    const bool empty = mnmx[3] < 0;
+    for (int d = 0; d < 3; ++d) {
+        const int32_t lo = max(0, mnmx[d] - margin);
+        const int32_t hi = (int32_t)min((int64_t)L[d], (int64_t)mnmx[3 + d] + margin + 1);
+        g->lo[d] = empty ? 0 : lo;
+        g->n[d] = empty ? 0 : hi - lo;
+        g->lt[d] = lt[d];
+        g->nt[d] = empty ? 0 : (hi - lo + (1 << lt[d]) - 1) >> lt[d];
+    }
+    g->Lx = (uint32_t)Lx;
+    g->Ly = (uint32_t)Ly;
+}
+
 // Exclusive scan of the tile activity (one CTA): compact index per tile (-1
 // if inactive), coordinates of each active tile, and the active count.
-__global__ void __launch_bounds__(1024) k_tile_scan(const int8_t *__restrict__ active, int32_t ntiles, BoxGeo g,
+__global__ void __launch_bounds__(1024) k_tile_scan(const int8_t *__restrict__ active, const BoxGeo *__restrict__ gp,
                                                     int32_t *__restrict__ tile_index,
                                                     int32_t *__restrict__ tile_coord,
                                                     unsigned long long *__restrict__ nact_out)
 {
     __shared__ int32_t part[1024];
+    const BoxGeo g = *gp;
+    const int32_t ntiles = g.n[0] > 0 ? g.nt[0] * g.nt[1] * g.nt[2] : 0;
     const int t = threadIdx.x;
     const int32_t chunk = (ntiles + 1023) / 1024;
     const int32_t b = min(ntiles, t * chunk), e = min(ntiles, b + chunk);
@@ -339,7 +365,7 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
     if (lat->dims[0] < 1 || lat->dims[1] < 1 || lat->dims[2] < 1 || L >= (int64_t)1 << 31)
         return mpm_fail(ctx, MPM_ERR_ARG, "extract: lattice dims out of range");
     if (margin < 0) return mpm_fail(ctx, MPM_ERR_ARG, "extract: negative margin");
-    int32_t lt[3] = {3, 3, 2};
+    int32_t lt[3] = {3, 2, 2};   // 8x4x4: the least padding on thin shells among the shapes measured
     if (tile) {
         for (int d = 0; d < 3; ++d) {
             const int32_t t = tile[d];
@@ -357,31 +383,23 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
     k_bbox<<<grid_for(L / 4 + 1, ctx->num_sms, 4), kBlock, 0, st>>>(lat->cell_id, (uint32_t)lat->dims[0],
                                                                      (uint32_t)(lat->dims[0] * lat->dims[1]),
                                                                      (uint32_t)L, vec4, ctx->d_box);
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
-    int32_t *hb = (int32_t *)ctx->h_stage;
-    MPM_CU(cudaMemcpyAsync(hb, ctx->d_box, 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MPM_CU(cudaStreamSynchronize(st));
-    if (hb[3] < 0) return mpm_fail(ctx, MPM_ERR_EMPTY, "extract: no tumour voxel (cell_id > 0)");
-    mpm_box box;
-    for (int d = 0; d < 3; ++d) {
-        box.lo[d] = hb[d] - margin < 0 ? 0 : hb[d] - margin;
-        const int64_t h = (int64_t)hb[3 + d] + margin + 1;
-        box.hi[d] = h > lat->dims[d] ? lat->dims[d] : (int32_t)h;
-    }
-
-    // ---- tiles of the box
+    // box geometry on the device; tile tables sized for the whole lattice, so
+    // the only host round trip of the extract comes after the compaction
+    BoxGeo *d_geo = (BoxGeo *)(ctx->d_box + 8);
+    k_box_finalize<<<1, 32, 0, st>>>(ctx->d_box, margin, lat->dims[0], lat->dims[1], lat->dims[2], lt[0], lt[1], lt[2],
+                                     d_geo);
+    ctx->launches += 1;
+    MPM_CU(cudaGetLastError());
     mpm_subgrid tmp = *sub;   // commit only on success
-    for (int d = 0; d < 3; ++d) {
-        tmp.lo[d] = box.lo[d];
-        tmp.hi[d] = box.hi[d];
-        tmp.n[d] = box.hi[d] - box.lo[d];
-        tmp.lt[d] = lt[d];
-        tmp.nt[d] = (tmp.n[d] + (1 << lt[d]) - 1) >> lt[d];
-    }
-    const int64_t ntiles64 = (int64_t)tmp.nt[0] * tmp.nt[1] * tmp.nt[2];
-    tmp.ntiles = (int32_t)ntiles64;
-    const size_t nt = (size_t)ntiles64;
+    const int64_t ntl = (((int64_t)lat->dims[0] + (1 << lt[0]) - 1) >> lt[0]) *
+                        (((int64_t)lat->dims[1] + (1 << lt[1]) - 1) >> lt[1]) *
+                        (((int64_t)lat->dims[2] + (1 << lt[2]) - 1) >> lt[2]);
+    const size_t nt = (size_t)ntl;
     const size_t geo_need = align256(nt * 4) + align256(nt * 16) + align256(nt * 24) + align256(nt) + 256;
+    void *const old_geo = sub->geo;
+    const bool was_extracted = sub->extracted, was_assembled = sub->assembled;
     sub->extracted = false;   // from here on the subgrid's buffers are rewritten
     sub->assembled = false;
     mpm_status s0 = mpm_grow(ctx, &sub->geo, &sub->geo_bytes, geo_need, "tile tables");
@@ -396,20 +414,44 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
         tmp.active = (int8_t *)p; p += align256(nt);
         tmp.err = (int32_t *)p;
     }
-    MPM_CU(cudaMemsetAsync(tmp.err, 0, sizeof(int32_t), st));
-    BoxGeo g = make_geo(&tmp, lat->dims);
     MPM_CU(cudaMemsetAsync(tmp.active, 0, nt, st));
     MPM_CU(cudaMemsetAsync(ctx->d_count, 0, 2 * sizeof(int64_t), st));
-    const int64_t nrows = (int64_t)tmp.n[1] * tmp.n[2];
-    k_tile_active<<<grid_for(nrows * 32, ctx->num_sms, 8), kBlock, 0, st>>>(
-        lat->mask, g, tmp.active, (unsigned long long *)ctx->d_count);
+    k_tile_active<<<ctx->num_sms * 8, kBlock, 0, st>>>(lat->mask, d_geo, tmp.active, (unsigned long long *)ctx->d_count);
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
-    k_tile_scan<<<1, 1024, 0, st>>>(tmp.active, tmp.ntiles, g, tmp.tile_index, tmp.tile_coord,
+    k_tile_scan<<<1, 1024, 0, st>>>(tmp.active, d_geo, tmp.tile_index, tmp.tile_coord,
                                     (unsigned long long *)(ctx->d_count + 1));
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
-    int64_t *hc = (int64_t *)ctx->h_stage;
-    MPM_CU(cudaMemcpyAsync(hc, ctx->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    char *hs = (char *)ctx->h_stage;
+    MPM_CU(cudaMemcpyAsync(hs, ctx->d_box, 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaMemcpyAsync(hs + 64, ctx->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     MPM_CU(cudaStreamSynchronize(st));
+    const int32_t *hb = (const int32_t *)hs;
+    const int64_t *hc = (const int64_t *)(hs + 64);
+    if (hb[3] < 0) {
+        // no box: the subgrid keeps its previous extraction (its tile tables
+        // were not written) unless the tile tables had to grow
+        if (sub->geo == old_geo) {
+            sub->extracted = was_extracted;
+            sub->assembled = was_assembled;
+        }
+        return mpm_fail(ctx, MPM_ERR_EMPTY, "extract: no tumour voxel (cell_id > 0)");
+    }
+    MPM_CU(cudaMemsetAsync(tmp.err, 0, sizeof(int32_t), st));
+    mpm_box box;
+    for (int d = 0; d < 3; ++d) {
+        box.lo[d] = hb[d] - margin < 0 ? 0 : hb[d] - margin;
+        const int64_t h = (int64_t)hb[3 + d] + margin + 1;
+        box.hi[d] = h > lat->dims[d] ? lat->dims[d] : (int32_t)h;
+        tmp.lo[d] = box.lo[d];
+        tmp.hi[d] = box.hi[d];
+        tmp.n[d] = box.hi[d] - box.lo[d];
+        tmp.lt[d] = lt[d];
+        tmp.nt[d] = (tmp.n[d] + (1 << lt[d]) - 1) >> lt[d];
+    }
+    tmp.ntiles = tmp.nt[0] * tmp.nt[1] * tmp.nt[2];
+    BoxGeo g = make_geo(&tmp, lat->dims);
     tmp.mask_voxels = hc[0];
     tmp.nact = (int32_t)hc[1];
     const int ltv = lt[0] + lt[1] + lt[2];
@@ -445,6 +487,7 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
     }
     if (tmp.nact > 0) {
         k_tile_nbr<<<(tmp.nact + 127) / 128, 128, 0, st>>>(tmp.tile_index, tmp.tile_coord, tmp.nact, g, tmp.nbr);
+        ctx->launches += 1;
         MPM_CU(cudaGetLastError());
         GatherArgs ga;
         memset(&ga, 0, sizeof(ga));
@@ -461,6 +504,7 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
             ga.cn[s] = tmp.cn[s];
         }
         k_gather<<<grid_for(tmp.NE, ctx->num_sms, 8), kBlock, 0, st>>>(ga, g, tmp.tile_coord, tmp.NE);
+        ctx->launches += 1;
         MPM_CU(cudaGetLastError());
     }
     tmp.extracted = true;
@@ -487,6 +531,7 @@ mpm_status mpm_scatter_impl(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_latt
     for (int s = 0; s < sub->nspecies; ++s) { a.field[s] = lat->field[s]; a.x[s] = sub->x[s]; }
     BoxGeo g = make_geo(sub, lat->dims);
     k_scatter<<<grid_for(sub->NE, ctx->num_sms, 8), kBlock, 0, st>>>(a, g, sub->tile_coord, sub->NE);
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
     return MPM_OK;
 }
@@ -505,15 +550,20 @@ mpm_status mpm_export_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, i
     const int grid = grid_for(nbox, ctx->num_sms, 8);
     switch (what) {
     case MPM_EXPORT_X:
-        k_export<double><<<grid, kBlock, 0, st>>>(sub->x[s], 0.0, g, sub->tile_index, (double *)dst, nbox); break;
+        k_export<double><<<grid, kBlock, 0, st>>>(sub->x[s], 0.0, g, sub->tile_index, (double *)dst, nbox);
+        ctx->launches += 1; break;
     case MPM_EXPORT_RHS:
-        k_export<double><<<grid, kBlock, 0, st>>>(sub->b[s], 0.0, g, sub->tile_index, (double *)dst, nbox); break;
+        k_export<double><<<grid, kBlock, 0, st>>>(sub->b[s], 0.0, g, sub->tile_index, (double *)dst, nbox);
+        ctx->launches += 1; break;
     case MPM_EXPORT_DIAG:
-        k_export<double><<<grid, kBlock, 0, st>>>(sub->diag[s], 1.0, g, sub->tile_index, (double *)dst, nbox); break;
+        k_export<double><<<grid, kBlock, 0, st>>>(sub->diag[s], 1.0, g, sub->tile_index, (double *)dst, nbox);
+        ctx->launches += 1; break;
     case MPM_EXPORT_FLAGS:
-        k_export<uint8_t><<<grid, kBlock, 0, st>>>(sub->flags, (uint8_t)0, g, sub->tile_index, (uint8_t *)dst, nbox); break;
+        k_export<uint8_t><<<grid, kBlock, 0, st>>>(sub->flags, (uint8_t)0, g, sub->tile_index, (uint8_t *)dst, nbox);
+        ctx->launches += 1; break;
     case MPM_EXPORT_CELL:
-        k_export<int32_t><<<grid, kBlock, 0, st>>>(sub->cell, 0, g, sub->tile_index, (int32_t *)dst, nbox); break;
+        k_export<int32_t><<<grid, kBlock, 0, st>>>(sub->cell, 0, g, sub->tile_index, (int32_t *)dst, nbox);
+        ctx->launches += 1; break;
     default:
         return mpm_fail(ctx, MPM_ERR_ARG, "export: unknown field");
     }
@@ -530,6 +580,7 @@ mpm_status mpm_import_impl(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const doub
     BoxGeo g = make_geo(sub, dims);
     const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
     k_import<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(src, g, sub->tile_index, sub->flags, 1, sub->x[s], nbox);
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
     sub->x_fresh = false;
     return MPM_OK;
@@ -543,6 +594,7 @@ mpm_status mpm_dense_to_elems(mpm_ctx *ctx, const mpm_subgrid *sub, const double
     const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
     MPM_CU(cudaMemsetAsync(dst, 0, (size_t)sub->NE * sizeof(double), st));
     k_import<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(src, g, sub->tile_index, sub->flags, 0, dst, nbox);
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
     return MPM_OK;
 }
@@ -554,6 +606,7 @@ mpm_status mpm_elems_to_dense(mpm_ctx *ctx, const mpm_subgrid *sub, const double
     BoxGeo g = make_geo(sub, dims);
     const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
     k_export_or<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(src, dflt_dense, g, sub->tile_index, dst, nbox);
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
     return MPM_OK;
 }

@@ -59,7 +59,7 @@ struct SysReport {
     int32_t iters[kMaxSpecies];
     int32_t cycles[kMaxSpecies];
     int32_t status[kMaxSpecies];
-    int32_t pad_;
+    int32_t jsum[kMaxSpecies];
     double res[kMaxSpecies];
     double bnorm[kMaxSpecies];
 };
@@ -81,6 +81,7 @@ struct SolveArgs {
     int32_t m, maxit;
     uint64_t timeout_ns;
     int32_t skip_block;         // fault injection for tests: this block never arrives (-1 none)
+    unsigned long long *prof;   // nullable: CTA 0 adds ns spent in [-, wait, reduce, serial, R, P1, P2, U]
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -260,6 +261,11 @@ struct mpm_ctx {
     double *d_tmp = nullptr;     // element scratch for apply_operator
     size_t tmp_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t launches = 0;        // kernels launched by this context
+    int32_t phase_prof = 0;      // record the solver's phase times (test/tuning hook)
+    int32_t solver_variant = 0;  // solver kernel variant (tuning)
+    unsigned long long *d_prof = nullptr;
+    unsigned long long h_prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // test hooks
     uint64_t timeout_ns = 2000000000ull;
     int32_t skip_block = -1;
@@ -268,7 +274,7 @@ struct mpm_ctx {
 struct mpm_subgrid {
     bool extracted = false, assembled = false;
     int32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, n[3] = {0, 0, 0};
-    int32_t lt[3] = {3, 3, 2};
+    int32_t lt[3] = {3, 2, 2};
     int32_t nt[3] = {0, 0, 0};
     int32_t ntiles = 0, nact = 0;
     int64_t NE = 0, mask_voxels = 0;

@@ -35,41 +35,65 @@ namespace mpm {
 
 enum { ST_RUN = -1 };
 
+constexpr int kSB = 512;            // solver CTA size (16 warps)
+constexpr int kSW = kSB / 32;
+
 struct SpState {
     double beta, bnorm, tol, tol_in;
-    int32_t it, cyc, status, in_cycle, k, done, bad, pad;
+    int32_t it, cyc, status, in_cycle, k, done, bad, jsum;
 };
+
+// Species are processed in groups of NSG inside one element loop, so the face
+// flags and neighbour indices are computed once per element and the loads of
+// all species of the group are in flight together.
 
 template <int MAXM>
 struct Smem {
     double H[kMaxSpecies][(MAXM + 1) * MAXM];
     double cs[kMaxSpecies][MAXM], sn[kMaxSpecies][MAXM];
     double g[kMaxSpecies][MAXM + 1], sig[kMaxSpecies][MAXM + 1], coef[kMaxSpecies][MAXM + 1];
-    double red[kWarps][MAXM + 2];
+    float coef32[kMaxSpecies][MAXM + 1];
+    double red[kSW][kKMax];
     double tot[kKMax];
     SpState sp[kMaxSpecies];
     SysDev sys;
 };
 
-// CTA reduction of cnt per-thread values; thread i < cnt stores the CTA total
-// of value i to out[i].
-template <int N, typename AccT, int RS>
-__device__ __forceinline__ void block_reduce_store(const AccT (&acc)[N], int cnt, double (*red)[RS], double *out)
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CTA reduction of the group's values acc[g][i] (g active in gm, i < cnt): warp
+// sums in the accumulator type, cross-warp sum in FP64 in a fixed order; the
+// CTA total of species s0+g, value i lands in out[(s0+g)*kKStride + i].
+template <int NSG, int N, typename AccT>
+__device__ __forceinline__ void block_reduce_g(const AccT (&acc)[NSG][N], uint32_t gm, int cnt, int s0,
+                                               double (*red)[kKMax], double *out)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        if (i < cnt) {
-            const double v = warp_sum((double)acc[i]);
-            if (lane == 0) red[w][i] = v;
+    for (int g = 0; g < NSG; ++g) {
+        if (!((gm >> g) & 1u)) continue;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (i < cnt) {
+                const AccT v = warp_sum_t<AccT>(acc[g][i]);
+                if (lane == 0) red[w][(s0 + g) * kKStride + i] = (double)v;
+            }
         }
     }
     __syncthreads();
-    if ((int)threadIdx.x < cnt) {
+    for (int t = threadIdx.x; t < NSG * kKStride; t += kSB) {
+        const int g = t / kKStride, i = t - g * kKStride;
+        if (!((gm >> g) & 1u) || i >= cnt) continue;
+        const int slot = (s0 + g) * kKStride + i;
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += red[q][threadIdx.x];
-        out[threadIdx.x] = s;
+        for (int q = 0; q < kSW; ++q) s += red[q][slot];
+        out[slot] = s;
     }
     __syncthreads();
 }
@@ -81,18 +105,20 @@ __device__ __forceinline__ void team_reduce(const double *part, int b0, int nb, 
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nslot = kMaxSpecies * cnt;
-    for (int q = w; q < nslot; q += kWarps) {
+    for (int q = w; q < nslot; q += kSW) {
         const int s = q / cnt, i = q - s * cnt;
         if (!((smask >> s) & 1u)) continue;
         const int slot = s * kKStride + i;
-        double v0 = 0.0, v1 = 0.0;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
         int b = lane;
-        for (; b + 32 < nb; b += 64) {
+        for (; b + 96 < nb; b += 128) {
             v0 += __ldcg(part + (size_t)(b0 + b) * kKMax + slot);
             v1 += __ldcg(part + (size_t)(b0 + b + 32) * kKMax + slot);
+            v2 += __ldcg(part + (size_t)(b0 + b + 64) * kKMax + slot);
+            v3 += __ldcg(part + (size_t)(b0 + b + 96) * kKMax + slot);
         }
-        if (b < nb) v0 += __ldcg(part + (size_t)(b0 + b) * kKMax + slot);
-        const double v = warp_sum(v0 + v1);
+        for (; b < nb; b += 32) v0 += __ldcg(part + (size_t)(b0 + b) * kKMax + slot);
+        const double v = warp_sum((v0 + v1) + (v2 + v3));
         if (lane == 0) tot[slot] = v;
     }
     __syncthreads();
@@ -105,99 +131,243 @@ __device__ __forceinline__ const double *diag_of<double>(const SysDev &S, int s)
 template <>
 __device__ __forceinline__ const float *diag_of<float>(const SysDev &S, int s) { return S.diag32[s]; }
 
-// ---- R: r = b - A x in FP64; u_0 = r (stored in T); sums of r^2 and b^2 (mask rows)
-template <typename T>
-__device__ __forceinline__ void pass_residual(const SysDev &S, int s, bool first, int64_t e0, int64_t es,
-                                              double &accR, double &accB)
+// Neighbour elements of e for its open faces (closed faces get e; never read).
+__device__ __forceinline__ void nbr_elems(const int32_t *__restrict__ nbr, uint32_t e, uint32_t f, int ltx, int lty,
+                                          int ltz, uint32_t (&q)[6])
 {
-    T *u0 = (T *)S.V[s];
-    const double *__restrict__ x = S.x[s];
-    const double *__restrict__ b = S.b[s];
-    const double *__restrict__ dg = S.diag[s];
+    const int ltv = ltx + lty + ltz;
+    const uint32_t tile = e >> ltv;
+    const uint32_t v = e & ((1u << ltv) - 1u);
+    const uint32_t TX = 1u << ltx, TY = 1u << lty, TZ = 1u << ltz;
+    const uint32_t ix = v & (TX - 1), iy = (v >> ltx) & (TY - 1), iz = v >> (ltx + lty);
+    const uint32_t tb = tile << ltv;
+    q[0] = !(f & F_MX) ? e : (ix > 0 ? e - 1 : ((uint32_t)__ldg(nbr + tile * 6 + 0) << ltv) + (v + TX - 1));
+    q[1] = !(f & F_PX) ? e : (ix < TX - 1 ? e + 1 : ((uint32_t)__ldg(nbr + tile * 6 + 1) << ltv) + (v - (TX - 1)));
+    q[2] = !(f & F_MY) ? e : (iy > 0 ? e - TX : ((uint32_t)__ldg(nbr + tile * 6 + 2) << ltv) + (v + (TY - 1) * TX));
+    q[3] = !(f & F_PY) ? e : (iy < TY - 1 ? e + TX : ((uint32_t)__ldg(nbr + tile * 6 + 3) << ltv) + (v - (TY - 1) * TX));
+    q[4] = !(f & F_MZ) ? e : (iz > 0 ? e - TX * TY : ((uint32_t)__ldg(nbr + tile * 6 + 4) << ltv) + (v + (TZ - 1) * TX * TY));
+    q[5] = !(f & F_PZ) ? e : (iz < TZ - 1 ? e + TX * TY : ((uint32_t)__ldg(nbr + tile * 6 + 5) << ltv) + (v - (TZ - 1) * TX * TY));
+    (void)tb;
+}
+
+// Sum of u over the open faces with closed faces selected to zero (5 adds for
+// 6 faces; neighbours read through L2: other CTAs wrote them).
+template <typename T>
+__device__ __forceinline__ T open_sum_sel(const T *__restrict__ u, uint32_t f, const uint32_t (&q)[6])
+{
+    T v[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) v[d] = (f & (1u << d)) ? __ldcg(u + q[d]) : T(0);
+    return ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
+}
+
+// Sum of u over the open faces (neighbours read through L2: other CTAs wrote them).
+template <typename T>
+__device__ __forceinline__ T open_sum(const T *__restrict__ u, uint32_t f, const uint32_t (&q)[6])
+{
+    T s0 = T(0), s1 = T(0);
+    if (f & F_MX) s0 += __ldcg(u + q[0]);
+    if (f & F_PX) s1 += __ldcg(u + q[1]);
+    if (f & F_MY) s0 += __ldcg(u + q[2]);
+    if (f & F_PY) s1 += __ldcg(u + q[3]);
+    if (f & F_MZ) s0 += __ldcg(u + q[4]);
+    if (f & F_PZ) s1 += __ldcg(u + q[5]);
+    return s0 + s1;
+}
+
+// Harmonic-mean variant: sum of D_f u_Q, D_f = 2 D_P D_Q / (D_P + D_Q).
+template <typename T>
+__device__ __forceinline__ T open_sum_var(const T *__restrict__ u, const double *__restrict__ dfac, uint32_t e,
+                                          uint32_t f, const uint32_t (&q)[6], double Ds)
+{
+    const double dp = Ds * __ldg(dfac + e);
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (f & (1u << d)) {
+            const double dq = Ds * __ldg(dfac + q[d]);
+            const double hm = (dp + dq > 0.0) ? 2.0 * dp * dq / (dp + dq) : 0.0;
+            s += T(hm) * __ldcg(u + q[d]);
+        }
+    }
+    return s;
+}
+
+// Every pass handles U elements per thread and iteration (e, e+es, ...,
+// spaced one grid stride apart) and issues all their loads before the first
+// store: stores through the Krylov base pointer may alias later loads in the
+// compiler's eyes, so this ordering is what keeps U elements' loads in flight
+// together.  Work items hold one species (s = 0).
+
+// ---- R: r = b - A x in FP64; u_0 = r (stored in T); sums of r^2 and of b^2
+// over mask rows.
+template <typename T, int U>
+__device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint32_t e0, uint32_t es,
+                                              double &aR, double &aB)
+{
+    // FP32 path: the norms only steer the stopping test, so they accumulate in
+    // FP32 (relative accuracy ~1e-7); the residual itself is FP64.
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    const uint32_t NE = (uint32_t)S.NE;
     const bool var = S.dfac != nullptr;
-    for (int64_t e = e0; e < S.NE; e += es) {
-        const uint32_t f = S.flags[e];
-        const double xv = x[e];
-        const double ns = var ? S.a * nbr_sum_var<double>(x, S.dfac, S.nbr, e, f, S.ltx, S.lty, S.ltz, S.Dsp[s])
-                              : S.off[s] * nbr_sum<double>(x, S.nbr, e, f, S.ltx, S.lty, S.ltz);
-        const double bv = b[e];
-        const double r = bv - (dg[e] * xv - ns);
-        u0[e] = (T)r;
-        accR += r * r;
-        if (first && (f & F_MASK)) accB += bv * bv;
+    const double *x = S.x[0];
+    float fR = 0.0f, fB = 0.0f;
+    for (uint32_t e = e0; e < NE; e += U * es) {
+        uint32_t f[U], q[U][6];
+        double xv[U], ns[U], bv[U], dg[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            f[u] = eu < NE ? __ldg(S.flags + eu) : 0u;
+            if (eu < NE) nbr_elems(S.nbr, eu, f[u], S.ltx, S.lty, S.ltz, q[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            xv[u] = x[eu];
+            ns[u] = var ? S.a * open_sum_var<double>(x, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum_sel<double>(x, f[u], q[u]);
+            bv[u] = __ldg(S.b[0] + eu);
+            dg[u] = __ldg(S.diag[0] + eu);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            // r = b - diag x + off * sum_open x_Q  (two fused multiply-adds)
+            const double r = var ? bv[u] - (dg[u] * xv[u] - ns[u]) : fma(S.off[0], ns[u], fma(-dg[u], xv[u], bv[u]));
+            const T rt = (T)r;
+            ((T *)S.V[0])[eu] = rt;
+            if (kF32) {
+                fR += (float)rt * (float)rt;
+                if (first && (f[u] & F_MASK)) {
+                    const float bf = (float)bv[u];
+                    fB += bf * bf;
+                }
+            } else {
+                aR += r * r;
+                if (first && (f[u] & F_MASK)) aB += bv[u] * bv[u];
+            }
+        }
+    }
+    if (kF32) {
+        aR += (double)fR;
+        aB += (double)fB;
     }
 }
 
 // ---- P1: w = sigma_j A u_j into slot j+1; acc[i] += u_i . w for i <= j
-template <typename T, int MAXM>
-__device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int s, int j, double sigj, int64_t e0, int64_t es,
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, double sigj, uint32_t e0, uint32_t es,
                                               T (&acc)[MAXM + 1])
 {
-    T *V = (T *)S.V[s];
+    const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
-    const T *uj = V + (int64_t)j * vs;
-    T *wv = V + (int64_t)(j + 1) * vs;
-    const T *__restrict__ dg = diag_of<T>(S, s);
-    const T sj = (T)sigj;
     const bool var = S.dfac != nullptr;
-    const T offT = (T)(var ? S.a : S.off[s]);
-    for (int64_t e = e0; e < S.NE; e += es) {
-        const uint32_t f = S.flags[e];
-        const T xj = uj[e];
-        const T ns = var ? nbr_sum_var<T>(uj, S.dfac, S.nbr, e, f, S.ltx, S.lty, S.ltz, S.Dsp[s])
-                         : nbr_sum<T>(uj, S.nbr, e, f, S.ltx, S.lty, S.ltz);
-        const T w = sj * (dg[e] * xj - offT * ns);
-        wv[e] = w;
+    const T sj = (T)sigj;
+    const T offT = (T)(var ? S.a : S.off[0]);
+    const T *V = (const T *)S.V[0];
+    const T *uj = V + (int64_t)j * vs;
+    const T *dgp = diag_of<T>(S, 0);
+    for (uint32_t e = e0; e < NE; e += U * es) {
+        uint32_t f[U], q[U][6];
+        T xj[U], ns[U], dg[U], w[U];
 #pragma unroll
-        for (int i = 0; i <= MAXM; ++i) {
-            if (i < j) acc[i] += V[(int64_t)i * vs + e] * w;
-            else if (i == j) acc[i] += xj * w;
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            f[u] = eu < NE ? __ldg(S.flags + eu) : 0u;
+            if (eu < NE) nbr_elems(S.nbr, eu, f[u], S.ltx, S.lty, S.ltz, q[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            xj[u] = uj[eu];
+            ns[u] = var ? open_sum_var<T>(uj, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum<T>(uj, f[u], q[u]);
+            dg[u] = __ldg(dgp + eu);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            w[u] = sj * (dg[u] * xj[u] - offT * ns[u]);
+#pragma unroll
+            for (int i = 0; i <= MAXM; ++i) {
+                if (i < j) acc[i] += V[(int64_t)i * vs + eu] * w[u];
+                else if (i == j) acc[i] += xj[u] * w[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu < NE) ((T *)S.V[0])[(int64_t)(j + 1) * vs + eu] = w[u];
         }
     }
 }
 
 // ---- P2: w -= sum_{i<=j} c_i u_i in place (c_i = h_ij sigma_i); acc += w^2
-template <typename T, int MAXM>
-__device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int s, int j, const double *coef, int64_t e0,
-                                              int64_t es, T &acc)
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
 {
-    T *V = (T *)S.V[s];
+    const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
-    T *wv = V + (int64_t)(j + 1) * vs;
-    T c[MAXM + 1];
+    const T *V = (const T *)S.V[0];
+    for (uint32_t e = e0; e < NE; e += U * es) {
+        T w[U];
 #pragma unroll
-    for (int i = 0; i <= MAXM; ++i) c[i] = i <= j ? (T)coef[i] : T(0);
-    for (int64_t e = e0; e < S.NE; e += es) {
-        T w = wv[e];
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            T t = V[(int64_t)(j + 1) * vs + eu];
 #pragma unroll
-        for (int i = 0; i <= MAXM; ++i)
-            if (i <= j) w -= c[i] * V[(int64_t)i * vs + e];
-        wv[e] = w;
-        acc += w * w;
+            for (int i = 0; i <= MAXM; ++i)
+                if (i <= j) t -= c[i] * V[(int64_t)i * vs + eu];
+            w[u] = t;
+            acc += t * t;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu < NE) ((T *)S.V[0])[(int64_t)(j + 1) * vs + eu] = w[u];
+        }
     }
 }
 
-// ---- U: x += sum_{i<k} c_i u_i (c_i = y_i sigma_i); FP32 path: FP32 correction added in FP64
-template <typename T, int MAXM>
-__device__ __forceinline__ void pass_update(const SysDev &S, int s, int k, const double *coef, int64_t e0, int64_t es)
+// ---- U: x += sum_{i<k} c_i u_i (c_i = y_i sigma_i); the FP32 path adds its
+// FP32 correction d to the FP64 iterate.
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_update(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
 {
-    const T *V = (const T *)S.V[s];
+    const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
-    double *__restrict__ x = S.x[s];
-    T c[MAXM];
+    const T *V = (const T *)S.V[0];
+    double *x = S.x[0];
+    for (uint32_t e = e0; e < NE; e += U * es) {
+        T d[U];
+        double xv[U];
 #pragma unroll
-    for (int i = 0; i < MAXM; ++i) c[i] = i < k ? (T)coef[i] : T(0);
-    for (int64_t e = e0; e < S.NE; e += es) {
-        T d = T(0);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            T t = T(0);
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i)
-            if (i < k) d += c[i] * V[(int64_t)i * vs + e];
-        x[e] += (double)d;
+            for (int i = 0; i < MAXM; ++i)
+                if (i < k) t += c[i] * V[(int64_t)i * vs + eu];
+            d[u] = t;
+            xv[u] = x[eu];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu < NE) x[eu] = xv[u] + (double)d[u];
+        }
     }
 }
 
-template <typename T, int MAXM>
-__global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
+// U: elements in flight per thread in the streaming passes; MINB: CTAs per SM
+// the register allocation must allow (1: up to 128 registers, 2: up to 64).
+template <typename T, int MAXM, int U, int MINB>
+__global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     Smem<MAXM> &sm = *reinterpret_cast<Smem<MAXM> *>(smraw);
@@ -210,8 +380,27 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
     uint32_t epoch = 0;
     int pbuf = 0;
     const size_t pstride = (size_t)gridDim.x * kKMax;
-    const int64_t e0 = (int64_t)rank * kBlock + tid, es = (int64_t)nb * kBlock;
+    const uint32_t e0 = (uint32_t)rank * kSB + tid, es = (uint32_t)nb * kSB;
     constexpr bool kF32 = std::is_same<T, float>::value;
+    const T *coefT = kF32 ? (const T *)&sm.coef32[0][0] : (const T *)&sm.coef[0][0];
+    // optional phase timer (CTA 0, thread 0): work, barrier wait, team reduce, serial
+    const bool prof = A.prof != nullptr && blockIdx.x == 0 && tid == 0;
+    uint64_t tp = prof ? globaltimer_ns() : 0, pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int wcat = 4;   // work category of the current pass: 4 R, 5 P1, 6 P2, 7 U
+#define MPM_TICK(cat)                                   \
+    do {                                                \
+        if (prof) {                                     \
+            const uint64_t t_ = globaltimer_ns();       \
+            pacc[cat] += t_ - tp;                       \
+            tp = t_;                                    \
+        }                                               \
+    } while (0)
+#define MPM_BARRIER()                                                              \
+    do {                                                                           \
+        MPM_TICK(wcat);                                                            \
+        if (!team_barrier(bar, epoch, nb, A.abort_flag, A.timeout_ns)) return;     \
+        MPM_TICK(1);                                                               \
+    } while (0)
 
     for (int si = td.sys_begin; si < td.sys_end; ++si) {
         const int sys_id = A.sys_order[si];
@@ -223,25 +412,27 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
             const bool bad_id = S.err && __ldcg(S.err) != 0;   // cell id outside the rate tables
             SpState &p = sm.sp[tid];
             p.beta = p.bnorm = p.tol = p.tol_in = 0.0;
-            p.it = p.cyc = p.in_cycle = p.k = p.bad = 0;
+            p.it = p.cyc = p.in_cycle = p.k = p.bad = p.jsum = 0;
             p.done = bad_id ? 1 : 0;
             p.status = bad_id ? MPM_ERR_ARG : ST_RUN;
         }
         __syncthreads();
         bool first = true;
+        double *mypart = nullptr;
         for (;;) {
             // ---------------- R: true residual (FP64)
             uint32_t rmask = 0;
             for (int s = 0; s < NS; ++s) if (!sm.sp[s].done) rmask |= 1u << s;
-            for (int s = 0; s < NS; ++s) {
-                if (!((rmask >> s) & 1u)) continue;
-                double acc[2] = {0.0, 0.0};
-                pass_residual<T>(S, s, first, e0, es, acc[0], acc[1]);
-                block_reduce_store<2, double, MAXM + 2>(acc, 2, sm.red,
-                                                        A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax + s * kKStride);
+            mypart = A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax;
+            wcat = 4;
+            if (rmask & 1u) {
+                double a2[1][2] = {{0.0, 0.0}};
+                pass_residual<T, U>(S, first, e0, es, a2[0][0], a2[0][1]);
+                block_reduce_g<1, 2, double>(a2, 1u, 2, 0, sm.red, mypart);
             }
-            if (!team_barrier(bar, epoch, nb, A.abort_flag, A.timeout_ns)) return;
+            MPM_BARRIER();
             team_reduce(A.partials + pbuf * pstride, td.first_block, nb, rmask, 2, sm.tot);
+            MPM_TICK(2);
             pbuf ^= 1;
             if (tid < NS && ((rmask >> tid) & 1u)) {
                 SpState &p = sm.sp[tid];
@@ -261,11 +452,12 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
                     for (int i = 0; i <= MAXM; ++i) sm.g[tid][i] = 0.0;
                     sm.g[tid][0] = beta;
                     sm.sig[tid][0] = 1.0 / beta;
-                    p.tol_in = kF32 ? fmax(p.tol, A.inner_rtol * beta) : p.tol;
+                    p.tol_in = kF32 ? fmax(0.25 * p.tol, A.inner_rtol * beta) : p.tol;
                 }
             }
             first = false;
             __syncthreads();
+            MPM_TICK(3);
             bool any = false;
             for (int s = 0; s < NS; ++s) any |= sm.sp[s].in_cycle != 0;
             if (!any) break;
@@ -275,35 +467,39 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
                 uint32_t cm = 0;
                 for (int s = 0; s < NS; ++s) if (sm.sp[s].in_cycle) cm |= 1u << s;
                 if (!cm) break;
-                for (int s = 0; s < NS; ++s) {
-                    if (!((cm >> s) & 1u)) continue;
-                    T acc[MAXM + 1];
+                mypart = A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax;
+                wcat = 5;
+                {
+                    T acc[1][MAXM + 1];
 #pragma unroll
-                    for (int i = 0; i <= MAXM; ++i) acc[i] = T(0);
-                    pass_arnoldi1<T, MAXM>(S, s, j, sm.sig[s][j], e0, es, acc);
-                    block_reduce_store<MAXM + 1, T, MAXM + 2>(acc, j + 1, sm.red,
-                                                             A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax + s * kKStride);
+                    for (int i = 0; i <= MAXM; ++i) acc[0][i] = T(0);
+                    pass_arnoldi1<T, MAXM, U>(S, j, sm.sig[0][j], e0, es, acc[0]);
+                    block_reduce_g<1, MAXM + 1, T>(acc, 1u, j + 1, 0, sm.red, mypart);
                 }
-                if (!team_barrier(bar, epoch, nb, A.abort_flag, A.timeout_ns)) return;
+                MPM_BARRIER();
                 team_reduce(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1, sm.tot);
+                MPM_TICK(2);
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
                     for (int i = 0; i <= j; ++i) {
                         const double h = sm.sig[tid][i] * sm.tot[tid * kKStride + i];
                         sm.H[tid][i * MAXM + j] = h;
                         sm.coef[tid][i] = h * sm.sig[tid][i];
+                        sm.coef32[tid][i] = (float)sm.coef[tid][i];
                     }
                 }
                 __syncthreads();
-                for (int s = 0; s < NS; ++s) {
-                    if (!((cm >> s) & 1u)) continue;
-                    T acc[1] = {T(0)};
-                    pass_arnoldi2<T, MAXM>(S, s, j, sm.coef[s], e0, es, acc[0]);
-                    block_reduce_store<1, T, MAXM + 2>(acc, 1, sm.red,
-                                                      A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax + s * kKStride);
+                MPM_TICK(3);
+                mypart = A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax;
+                wcat = 6;
+                {
+                    T acc[1][1] = {{T(0)}};
+                    pass_arnoldi2<T, MAXM, U>(S, j, coefT, e0, es, acc[0][0]);
+                    block_reduce_g<1, 1, T>(acc, 1u, 1, 0, sm.red, mypart);
                 }
-                if (!team_barrier(bar, epoch, nb, A.abort_flag, A.timeout_ns)) return;
+                MPM_BARRIER();
                 team_reduce(A.partials + pbuf * pstride, td.first_block, nb, cm, 1, sm.tot);
+                MPM_TICK(2);
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
                     SpState &p = sm.sp[tid];
@@ -328,6 +524,7 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
                     g[j + 1] = -sn[j] * g[j];
                     g[j] = cs[j] * g[j];
                     p.it += 1;
+                    p.jsum += j;
                     p.k = j + 1;
                     if (!isfinite(g[j + 1]) || !isfinite(H[j * MAXM + j])) {
                         p.status = MPM_ERR_BREAKDOWN;
@@ -341,9 +538,10 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
                     }
                 }
                 __syncthreads();
+                MPM_TICK(3);
             }
 
-            // ---------------- least squares: R y = g (back substitution)
+            // ---------------- least squares: R y = g (back substitution), coef = y * sigma
             if (tid < NS) {
                 SpState &p = sm.sp[tid];
                 if (!p.bad && p.k > 0) {
@@ -357,21 +555,20 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
                     bool fin = true;
                     for (int i = 0; i < p.k; ++i) {
                         y[i] *= sm.sig[tid][i];
+                        sm.coef32[tid][i] = (float)y[i];
                         fin &= isfinite(y[i]) != 0;
                     }
                     if (!fin) { p.status = MPM_ERR_BREAKDOWN; p.bad = 1; p.done = 1; }
                 }
             }
             __syncthreads();
+            MPM_TICK(3);
             // ---------------- U: x += V y
-            for (int s = 0; s < NS; ++s) {
-                const SpState &p = sm.sp[s];
-                if (p.bad || p.k == 0) continue;
-                pass_update<T, MAXM>(S, s, p.k, sm.coef[s], e0, es);
-            }
+            wcat = 7;
+            if (!sm.sp[0].bad && sm.sp[0].k > 0) pass_update<T, MAXM, U>(S, sm.sp[0].k, coefT, e0, es);
             __syncthreads();
             if (tid < NS) sm.sp[tid].k = 0;
-            if (!team_barrier(bar, epoch, nb, A.abort_flag, A.timeout_ns)) return;
+            MPM_BARRIER();
         }
         if (rank == 0 && tid < NS) {
             const SpState &p = sm.sp[tid];
@@ -379,31 +576,51 @@ __global__ void __launch_bounds__(kBlock) k_gmres(SolveArgs A)
             R->iters[tid] = p.it;
             R->cycles[tid] = p.cyc;
             R->status[tid] = p.status;
+            R->jsum[tid] = p.jsum;
             R->res[tid] = p.beta;
             R->bnorm[tid] = p.bnorm;
         }
         __syncthreads();
     }
+    if (prof) {
+        MPM_TICK(wcat);
+        for (int c = 0; c < 8; ++c) A.prof[c] += pacc[c];
+    }
+#undef MPM_TICK
+#undef MPM_BARRIER
 }
 
 typedef void (*KernFn)(SolveArgs);
 
-template <typename T, int MAXM>
-struct KernInfo {
-    static KernFn fn() { return k_gmres<T, MAXM>; }
-    static size_t smem() { return sizeof(Smem<MAXM>); }
-};
+template <typename T, int MAXM, int U, int MINB>
+static KernFn kfn(size_t &smem)
+{
+    smem = sizeof(Smem<MAXM>);
+    return k_gmres<T, MAXM, U, MINB>;
+}
 
-static KernFn pick(int prec, int maxm, size_t &smem)
+// Kernel variants: variant 0 is the default of each (precision, restart
+// bucket), chosen by measurement on the 256^3 shell workload (FP32, m <= 8:
+// one element per thread at two CTAs/SM; FP64: two elements at one CTA/SM).
+// The FP32 m <= 8 bucket also has 1: one element at one CTA/SM, 2: two
+// elements at two CTAs/SM, 3: two elements at one CTA/SM.
+static KernFn pick(int prec, int maxm, int variant, size_t &smem)
 {
     if (prec == 0) {
-        if (maxm == 8) { smem = KernInfo<double, 8>::smem(); return KernInfo<double, 8>::fn(); }
-        if (maxm == 16) { smem = KernInfo<double, 16>::smem(); return KernInfo<double, 16>::fn(); }
-        smem = KernInfo<double, 32>::smem(); return KernInfo<double, 32>::fn();
+        if (maxm == 8) return variant == 1 ? kfn<double, 8, 1, 2>(smem) : kfn<double, 8, 2, 1>(smem);
+        if (maxm == 16) return kfn<double, 16, 1, 1>(smem);
+        return kfn<double, 32, 1, 1>(smem);
     }
-    if (maxm == 8) { smem = KernInfo<float, 8>::smem(); return KernInfo<float, 8>::fn(); }
-    if (maxm == 16) { smem = KernInfo<float, 16>::smem(); return KernInfo<float, 16>::fn(); }
-    smem = KernInfo<float, 32>::smem(); return KernInfo<float, 32>::fn();
+    if (maxm == 8) {
+        switch (variant) {
+        case 1: return kfn<float, 8, 1, 1>(smem);
+        case 2: return kfn<float, 8, 2, 2>(smem);
+        case 3: return kfn<float, 8, 2, 1>(smem);
+        default: return kfn<float, 8, 1, 2>(smem);
+        }
+    }
+    if (maxm == 16) return kfn<float, 16, 1, 1>(smem);
+    return kfn<float, 32, 1, 1>(smem);
 }
 
 }  // namespace mpm
@@ -435,14 +652,14 @@ SysDev mpm_make_sysdev(const mpm_subgrid *sub)
     return S;
 }
 
-int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m)
+int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 {
     const int maxm = m <= 8 ? 8 : (m <= 16 ? 16 : 32);
     size_t smem = 0;
-    KernFn fn = pick(prec, maxm, smem);
+    KernFn fn = pick(prec, maxm, variant, smem);
     if (smem > 48 * 1024) cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kSB, smem) != cudaSuccess) return 0;
     return per_sm * ctx->num_sms;
 }
 
@@ -521,9 +738,10 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
     const int maxm = m <= 8 ? 8 : (m <= 16 ? 16 : 32);
     const size_t tsz = opt->precision ? sizeof(float) : sizeof(double);
 
-    // ---- Krylov bases and initial guesses
-    std::vector<SysDev> sd(nsys);
-    std::vector<double> work(nsys);
+    // ---- Krylov bases and initial guesses; one work item per (system, species)
+    std::vector<SysDev> sd;
+    std::vector<double> work;
+    std::vector<int> item_sys, item_sp;
     for (int i = 0; i < nsys; ++i) {
         mpm_subgrid *sub = subs[i];
         const int64_t vstride = sub->NE > 0 ? ((sub->NE + 63) / 64) * 64 : 64;
@@ -535,26 +753,44 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
                 MPM_CU(cudaMemcpyAsync(sub->x[s], sub->cn[s], (size_t)sub->NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
             sub->x_fresh = true;
         }
-        sd[i] = mpm_make_sysdev(sub);
-        sd[i].vstride = vstride;
-        for (int s = 0; s < sub->nspecies; ++s) sd[i].V[s] = (char *)sub->krylov + per * s;
-        work[i] = (double)sub->NE * sub->nspecies + 1.0;
+        const SysDev full = mpm_make_sysdev(sub);
+        for (int s = 0; s < sub->nspecies; ++s) {
+            SysDev d = full;
+            d.nspecies = 1;
+            for (int t = 0; t < kMaxSpecies; ++t) {
+                d.x[t] = nullptr; d.b[t] = nullptr; d.diag[t] = nullptr; d.diag32[t] = nullptr; d.V[t] = nullptr;
+                d.off[t] = 0.0; d.Dsp[t] = 0.0;
+            }
+            d.x[0] = full.x[s];
+            d.b[0] = full.b[s];
+            d.diag[0] = full.diag[s];
+            d.diag32[0] = full.diag32[s];
+            d.off[0] = full.off[s];
+            d.Dsp[0] = full.Dsp[s];
+            d.vstride = vstride;
+            d.V[0] = (char *)sub->krylov + per * s;
+            sd.push_back(d);
+            work.push_back((double)sub->NE + 1.0);
+            item_sys.push_back(i);
+            item_sp.push_back(s);
+        }
     }
+    const int nitem = (int)sd.size();
 
     // ---- grid and teams
     size_t smem = 0;
-    KernFn fn = pick(opt->precision, maxm, smem);
-    const int gmax = mpm_solver_max_blocks(ctx, opt->precision, m);
+    KernFn fn = pick(opt->precision, maxm, ctx->solver_variant, smem);
+    const int gmax = mpm_solver_max_blocks(ctx, opt->precision, m, ctx->solver_variant);
     if (gmax < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "solve: occupancy query failed");
     int G;
     if (opt->nblocks > 0) G = std::min(opt->nblocks, gmax);
     else {
         double tot = 0.0;
         for (double w : work) tot += w;
-        // about 4 elements per thread per species at least; at most 2 CTAs per SM
-        const double want = tot / (kBlock * 4.0);
-        G = (int)std::min<double>(std::min(gmax, 2 * ctx->num_sms), std::max(1.0, want));
-        G = std::max(G, std::min(nsys, gmax));
+        // about 2 elements per thread per species at least; at most one CTA per SM
+        const double want = tot / (kSB * 2.0);
+        G = (int)std::min<double>(gmax, std::max(1.0, want));
+        G = std::max(G, std::min(nitem, gmax));
     }
     std::vector<TeamDesc> teams;
     std::vector<int32_t> order, block_team;
@@ -563,11 +799,11 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
 
     // ---- descriptors to the device (pinned staging)
     const size_t o_sys = 0;
-    const size_t o_team = a256(o_sys + sizeof(SysDev) * nsys);
+    const size_t o_team = a256(o_sys + sizeof(SysDev) * nitem);
     const size_t o_order = a256(o_team + sizeof(TeamDesc) * nteam);
-    const size_t o_bt = a256(o_order + sizeof(int32_t) * nsys);
+    const size_t o_bt = a256(o_order + sizeof(int32_t) * nitem);
     const size_t o_rep = a256(o_bt + sizeof(int32_t) * G);
-    const size_t args_need = a256(o_rep + sizeof(SysReport) * nsys);
+    const size_t args_need = a256(o_rep + sizeof(SysReport) * nitem);
     mpm_status r = mpm_grow(ctx, &ctx->d_args, &ctx->args_cap, args_need, "solver descriptors");
     if (r != MPM_OK) return r;
     if (ctx->stage_cap < args_need + 256) {
@@ -576,11 +812,11 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
         MPM_CU(cudaMallocHost(&ctx->h_stage, args_need + 4096));
         ctx->stage_cap = args_need + 4096;
     }
-    MPM_CU(cudaStreamSynchronize(st));   // the staging buffer is reused across calls
+    // the staging buffer is free: every call that uses it ends with a stream synchronisation
     char *hs = (char *)ctx->h_stage;
-    memcpy(hs + o_sys, sd.data(), sizeof(SysDev) * nsys);
+    memcpy(hs + o_sys, sd.data(), sizeof(SysDev) * nitem);
     memcpy(hs + o_team, teams.data(), sizeof(TeamDesc) * nteam);
-    memcpy(hs + o_order, order.data(), sizeof(int32_t) * nsys);
+    memcpy(hs + o_order, order.data(), sizeof(int32_t) * nitem);
     memcpy(hs + o_bt, block_team.data(), sizeof(int32_t) * G);
     MPM_CU(cudaMemcpyAsync(ctx->d_args, hs, o_rep, cudaMemcpyHostToDevice, st));
     const size_t pneed = 2 * (size_t)G * kKMax * sizeof(double);
@@ -594,7 +830,7 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
     }
     MPM_CU(cudaMemsetAsync(ctx->d_bar, 0, (size_t)nteam * 32 * sizeof(uint32_t), st));
     MPM_CU(cudaMemsetAsync(ctx->d_abort, 0, sizeof(int32_t), st));
-    MPM_CU(cudaMemsetAsync((char *)ctx->d_args + o_rep, 0, sizeof(SysReport) * nsys, st));
+    MPM_CU(cudaMemsetAsync((char *)ctx->d_args + o_rep, 0, sizeof(SysReport) * nitem, st));
 
     SolveArgs sa;
     sa.sys = (const SysDev *)((char *)ctx->d_args + o_sys);
@@ -612,16 +848,24 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
     sa.maxit = opt->maxit;
     sa.timeout_ns = ctx->timeout_ns;
     sa.skip_block = ctx->skip_block;
+    sa.prof = nullptr;
+    if (ctx->phase_prof) {
+        if (!ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+        MPM_CU(cudaMemsetAsync(ctx->d_prof, 0, 8 * sizeof(unsigned long long), st));
+        sa.prof = ctx->d_prof;
+    }
     void *kargs[] = {&sa};
     MPM_CU(cudaEventRecord(ctx->ev0, st));
-    MPM_CU(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(kBlock), kargs, smem, st));
+    MPM_CU(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(kSB), kargs, smem, st));
+    ctx->launches += 1;
     MPM_CU(cudaEventRecord(ctx->ev1, st));
 
     // ---- results
     SysReport *hrep = (SysReport *)(hs + o_rep);
-    MPM_CU(cudaMemcpyAsync(hrep, sa.reports, sizeof(SysReport) * nsys, cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaMemcpyAsync(hrep, sa.reports, sizeof(SysReport) * nitem, cudaMemcpyDeviceToHost, st));
     int32_t *hflags = (int32_t *)(hs + args_need);
     MPM_CU(cudaMemcpyAsync(hflags, ctx->d_abort, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     MPM_CU(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -639,30 +883,34 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
         default: return 5;
         }
     };
+    std::vector<mpm_report> R(nsys);
     for (int i = 0; i < nsys; ++i) {
+        memset(&R[i], 0, sizeof(mpm_report));
         mpm_subgrid *sub = subs[i];
         sub->x_fresh = false;
-        mpm_report R;
-        memset(&R, 0, sizeof(R));
-        for (int s = 0; s < sub->nspecies; ++s) {
-            R.iters[s] = hrep[i].iters[s];
-            R.cycles[s] = hrep[i].cycles[s];
-            int stt = hrep[i].status[s];
-            if (timed_out) stt = MPM_ERR_TIMEOUT;
-            else if (stt == ST_RUN) stt = MPM_ERR_NOCONV;
-            if (stt == MPM_ERR_ARG) bad_id = true;
-            R.status[s] = stt;
-            R.res[s] = hrep[i].res[s];
-            R.bnorm[s] = hrep[i].bnorm[s];
-            if (rank_of(stt) > rank_of(worst)) worst = (mpm_status)stt;
-        }
-        R.box_voxels = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
-        R.mask_voxels = sub->mask_voxels;
-        R.stored_voxels = sub->NE;
-        R.solve_ms = ms;
-        if (reps) reps[i] = R;
+        R[i].box_voxels = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
+        R[i].mask_voxels = sub->mask_voxels;
+        R[i].stored_voxels = sub->NE;
+        R[i].solve_ms = ms;
+    }
+    for (int it = 0; it < nitem; ++it) {
+        const int i = item_sys[it], s = item_sp[it];
+        R[i].iters[s] = hrep[it].iters[0];
+        R[i].jsum[s] = hrep[it].jsum[0];
+        R[i].cycles[s] = hrep[it].cycles[0];
+        int stt = hrep[it].status[0];
+        if (timed_out) stt = MPM_ERR_TIMEOUT;
+        else if (stt == ST_RUN) stt = MPM_ERR_NOCONV;
+        if (stt == MPM_ERR_ARG) bad_id = true;
+        R[i].status[s] = stt;
+        R[i].res[s] = hrep[it].res[0];
+        R[i].bnorm[s] = hrep[it].bnorm[0];
+        if (rank_of(stt) > rank_of(worst)) worst = (mpm_status)stt;
+    }
+    for (int i = 0; i < nsys; ++i) {
+        if (reps) reps[i] = R[i];
         if (!timed_out && scatter_to && scatter_to[i]) {
-            r = mpm_scatter_impl(ctx, sub, scatter_to[i], st);
+            r = mpm_scatter_impl(ctx, subs[i], scatter_to[i], st);
             if (r != MPM_OK) return r;
         }
     }

@@ -17,7 +17,7 @@ MAX_RESTART = 32
 OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(8)
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_EMPTY", "ERR_NOCONV", "ERR_BREAKDOWN", "ERR_TIMEOUT", "ERR_CUDA", "ERR_NOMEM"]
 EXPORT_X, EXPORT_RHS, EXPORT_DIAG, EXPORT_FLAGS, EXPORT_CELL = range(5)
-DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK = 1, 2
+DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK, DEBUG_PHASE_TIMES, DEBUG_SOLVER_VARIANT = 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
@@ -25,7 +25,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
 # symbols declared in include/mpm.h
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", "mpm_subgrid_destroy",
            "mpm_subgrid_info", "mpm_box_extract", "mpm_assemble_coeffs", "mpm_solve_step", "mpm_solve_batch",
-           "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set"]
+           "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
+           "mpm_counter_get"]
 
 
 class mpm_box(C.Structure):
@@ -55,13 +56,15 @@ class mpm_opts(C.Structure):
 
 class mpm_report(C.Structure):
     _fields_ = [("iters", C.c_int32 * MAX_SPECIES), ("cycles", C.c_int32 * MAX_SPECIES),
-                ("status", C.c_int32 * MAX_SPECIES), ("res", C.c_double * MAX_SPECIES),
+                ("status", C.c_int32 * MAX_SPECIES), ("jsum", C.c_int32 * MAX_SPECIES),
+                ("res", C.c_double * MAX_SPECIES),
                 ("bnorm", C.c_double * MAX_SPECIES), ("box_voxels", C.c_int64), ("mask_voxels", C.c_int64),
                 ("stored_voxels", C.c_int64), ("solve_ms", C.c_double)]
 
     def as_dict(self, nspecies):
         return {"iters": list(self.iters[:nspecies]), "cycles": list(self.cycles[:nspecies]),
-                "status": list(self.status[:nspecies]), "res": list(self.res[:nspecies]),
+                "status": list(self.status[:nspecies]), "jsum": list(self.jsum[:nspecies]),
+                "res": list(self.res[:nspecies]),
                 "bnorm": list(self.bnorm[:nspecies]), "box_voxels": self.box_voxels,
                 "mask_voxels": self.mask_voxels, "stored_voxels": self.stored_voxels, "solve_ms": self.solve_ms}
 
@@ -102,6 +105,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_apply_operator": [P, P, C.c_int32, P, P, P],
         "mpm_scatter": [P, P, C.POINTER(mpm_lattice), P],
         "mpm_debug_set": [P, C.c_int32, C.c_int64],
+        "mpm_counter_get": [P, C.c_int32, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -210,6 +214,19 @@ class Context:
 
     def error(self) -> str:
         return self.lib.mpm_last_error(self.ptr).decode()
+
+    def counter(self, key: int) -> int:
+        v = C.c_int64(0)
+        self._check(self.lib.mpm_counter_get(self.ptr, key, C.byref(v)), "mpm_counter_get")
+        return int(v.value)
+
+    def launches(self) -> int:
+        return self.counter(1)
+
+    def phase_times_us(self) -> dict:
+        """CTA-0 time split of the last solve (needs debug_set(DEBUG_PHASE_TIMES, 1))."""
+        return {k: self.counter(c) / 1e3 for k, c in (("work", 2), ("wait", 3), ("reduce", 4), ("serial", 5),
+                                                      ("R", 6), ("P1", 7), ("P2", 8), ("U", 9))}
 
     def debug_set(self, key: int, value: int):
         self._check(self.lib.mpm_debug_set(self.ptr, key, value), "mpm_debug_set")
