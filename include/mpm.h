@@ -237,6 +237,38 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
 #define MPM_COUNTER_PHASE_U_NS 9
 mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value);
 
+/*
+ * Bounding box without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory, for
+ * example code whose device memory is all owned by another allocator (a
+ * framework's caching allocator or a pool fixed at start-up), code that must
+ * not risk the device-wide synchronisation that cudaMalloc/cudaFree can
+ * cause, or a plugin whose host application controls every allocation.  It
+ * needs no context (creating one allocates) and calls no allocating routine.
+ *
+ * Computes the same box as mpm_box_extract (voxels with cell_id > 0, widened
+ * by `margin`, clamped to the lattice) and writes to out_box (device memory,
+ * 7 int32, caller-owned): lo[3], hi[3] (exclusive) and a found flag (0 when
+ * no voxel has cell_id > 0; lo and hi are then 0).  cell_id is the caller's
+ * device lattice of dims Lx*Ly*Lz < 2^31.  Kernels are queued on `stream`
+ * (cudaStream_t, NULL = legacy default); nothing synchronises.
+ *
+ * Scratch: one fixed array of MPM_NOALLOC_MAX_SLABS * 8 int32 (128 KB) per
+ * partial bound of each z-slice, compiled into the library; every GPU that
+ * loads the library holds it until the process exits.  All calls share it
+ * and each call overwrites what it reads, so calls that overlap on the GPU
+ * (on different streams or different host threads) race.  The first call on
+ * a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.
+ *
+ * Errors: MPM_ERR_ARG (null pointer, negative margin, bad dims),
+ * MPM_ERR_NOMEM (Lz > MPM_NOALLOC_MAX_SLABS: more z-slices than the fixed
+ * scratch holds), MPM_ERR_CUDA (symbol lookup or launch failed).
+ */
+#define MPM_NOALLOC_MAX_SLABS 4096
+mpm_status mpm_box_bounds_noalloc(const int32_t *cell_id, const int32_t dims[3], int32_t margin, int32_t *out_box,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

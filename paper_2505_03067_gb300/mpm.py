@@ -13,6 +13,7 @@ import numpy as np
 
 MAX_SPECIES = 4
 MAX_RESTART = 32
+NOALLOC_MAX_SLABS = 4096
 
 OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(8)
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_EMPTY", "ERR_NOCONV", "ERR_BREAKDOWN", "ERR_TIMEOUT", "ERR_CUDA", "ERR_NOMEM"]
@@ -26,7 +27,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", "mpm_subgrid_destroy",
            "mpm_subgrid_info", "mpm_box_extract", "mpm_assemble_coeffs", "mpm_solve_step", "mpm_solve_batch",
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
-           "mpm_counter_get"]
+           "mpm_counter_get", "mpm_box_bounds_noalloc"]
 
 
 class mpm_box(C.Structure):
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_scatter": [P, P, C.POINTER(mpm_lattice), P],
         "mpm_debug_set": [P, C.c_int32, C.c_int64],
         "mpm_counter_get": [P, C.c_int32, C.POINTER(C.c_int64)],
+        "mpm_box_bounds_noalloc": [P, C.POINTER(C.c_int32), C.c_int32, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -309,6 +311,17 @@ class Subgrid:
         ls = lat.struct()
         self.ctx._check(self.ctx.lib.mpm_scatter(self.ctx.ptr, self.h, C.byref(ls), _stream_ptr(stream)),
                         "mpm_scatter")
+
+
+def mpm_box_bounds_noalloc(cell_id, margin: int, out_box, stream=None) -> int:
+    """Bounding box of a device int32 lattice (torch tensor of shape (Lz, Ly, Lx))
+    into out_box (device int32 tensor of 7 entries), without any allocation by
+    the library; returns the mpm_status."""
+    lib = load()
+    lz, ly, lx = (int(v) for v in cell_id.shape)
+    dims = (C.c_int32 * 3)(lx, ly, lz)
+    return lib.mpm_box_bounds_noalloc(C.c_void_p(cell_id.data_ptr()), dims, margin,
+                                      C.c_void_p(out_box.data_ptr()), _stream_ptr(stream))
 
 
 def mpm_solve_batch(ctx: Context, subs, opts: mpm_opts, scatter_to=None, stream=None, allow=(ERR_NOCONV,)):
