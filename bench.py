@@ -28,6 +28,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -149,6 +151,99 @@ def _traffic_record(kernel_key):
     return rec
 
 
+def _timed(fn, stream, flush, i):
+    import torch
+    flush.fill_(i & 255)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = fn()
+    b.record(stream)
+    b.synchronize()
+    return out, a.elapsed_time(b)
+
+
+def bench_sphere32(mpm, W, ctx, stream, flush, warmup):
+    """32^3 single species, FP64 GMRES(30) to 1e-10 relative, 10 steps."""
+    wl = W.sphere32()
+    lat = mpm.DeviceLattice(wl.lattice)
+    init = lat.fields.clone()
+    solver = mpm.StepSolver(ctx, lat, mpm.DeviceParams(wl.params), wl.margin)
+    opts = mpm.make_opts(rtol=wl.rtol, restart=wl.restart, maxit=1000)
+    for _ in range(warmup):
+        solver.step(opts)
+    lat.fields.copy_(init)
+    ms, units, its = 0.0, 0, []
+    for i in range(wl.steps):
+        rep, t = _timed(lambda: solver.step(opts), stream, flush, i)
+        assert rep["status_code"] == mpm.OK and rep["res"][0] <= wl.rtol * rep["bnorm"][0]
+        ms += t
+        units += rep["mask_voxels"]
+        its.append(rep["iters"][0])
+    return {"value": units / (ms / 1e3), "unit": "species-voxel-steps/s", "ms_per_step": ms / wl.steps,
+            "path": "FP64 GMRES(30), rtol 1e-10", "steps": wl.steps, "iters_per_step": sum(its) / len(its)}
+
+
+def bench_patches64(mpm, W, ctx, stream, flush, warmup, steps=50):
+    """64 uneven pleural-shell patches x 3 species: one graph-replayed batched step
+    (refresh, assemble, one persistent solve of all 192 systems, scatter),
+    tiles and restart/variant from the tuner, FP32 inside FP64 refinement."""
+    ps = W.patches()
+    lats = [mpm.DeviceLattice(p.lattice) for p in ps]
+    inits = [l.fields.clone() for l in lats]
+    prms = [mpm.DeviceParams(p.params) for p in ps]
+    bs = mpm.BatchStepper(ctx, lats, prms, [p.margin for p in ps], tune_tiles=True)
+    opts = mpm.make_opts(rtol=1e-6, restart=8, maxit=1000, precision=1, inner_rtol=1e-6)
+    m, var = bs.tune(opts)
+    for _ in range(warmup):
+        bs.step(opts)
+    for l, f in zip(lats, inits):
+        l.fields.copy_(f)
+    ms, units = 0.0, 0
+    for i in range(steps):
+        (st, reps), t = _timed(lambda: bs.step(opts), stream, flush, i)
+        assert st == mpm.OK
+        ms += t
+        units += sum(r["mask_voxels"] * 3 for r in reps)
+    stored = sum(r["stored_voxels"] for r in reps)
+    return {"value": units / (ms / 1e3), "unit": "species-voxel-steps/s", "ms_per_step": ms / steps, "steps": steps,
+            "systems": 3 * len(ps), "tuned": {"restart": m, "variant": var,
+                                              "tiles": sorted(set(map(tuple, bs.tiles)))},
+            "graph": bs.graph_active(), "stored_voxels": stored,
+            "mask_voxels": sum(r["mask_voxels"] for r in reps)}
+
+
+def bench_growth512(mpm, W, ctx, stream, flush, sample=range(0, 201, 20)):
+    """512x384x384 growing tumour: at sampled steps t the Voronoi cells whose seed
+    lies in the growth box are tumour (a device-side update outside the timing),
+    then one timed step re-extracts the box and solves 3 species."""
+    import torch
+    wl, extra = W.growth512()
+    cand = torch.from_numpy(extra["cand"]).cuda()
+    labels = torch.from_numpy(extra["labels"].astype(np.int64)).cuda()
+    out = {}
+    for name, extra_o in (("fp64", dict(precision=0)), ("mixed", dict(precision=1, inner_rtol=1e-6))):
+        lat = mpm.DeviceLattice(wl.lattice)
+        solver = mpm.StepSolver(ctx, lat, mpm.DeviceParams(wl.params), wl.margin)
+        opts = mpm.make_opts(rtol=wl.rtol, restart=8, maxit=1000, **extra_o)
+        ms, units, boxes = 0.0, 0, []
+        for i, t in enumerate(sample):
+            lo, hi = W.growth_box(t, wl.steps)
+            inside = np.all((extra["seeds"] >= lo) & (extra["seeds"] < hi), axis=1)
+            ids = torch.from_numpy(np.where(inside, np.arange(1, len(inside) + 1), 0).astype(np.int32)).cuda()
+            lat.cell_id.view(-1)[cand] = ids[labels]
+            if i == 0:
+                solver.step(opts)   # warm-up at the first sampled state
+            rep, dt = _timed(lambda: solver.step(opts), stream, flush, i)
+            assert rep["status_code"] == mpm.OK, rep
+            ms += dt
+            units += rep["mask_voxels"] * 3
+            boxes.append(rep["box_voxels"])
+        out[name] = {"value": units / (ms / 1e3), "ms_per_step": ms / len(sample)}
+    return {"value": out["mixed"]["value"], "unit": "species-voxel-steps/s", "paths": out,
+            "sample": f"steps {list(sample)[0]}..{list(sample)[-1]} every {list(sample)[1] - list(sample)[0]}",
+            "box_voxels_first_last": [boxes[0], boxes[-1]]}
+
+
 def cpu_baseline(wl, nsteps):
     import oracle
     lat = wl.lattice.copy()
@@ -204,6 +299,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--restart", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the 32^3, 64-patch and 512x384x384 lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -352,6 +448,10 @@ def main():
                                    "fp64_tops": fp["kernel_fp64_ops"] / (fp["kernel_ms"] / 1e3) / 1e12,
                                    "fp64_peak_tops_nominal": 1.25},
             "roofline": roofline, "e2e": e2e, "gpu_launches": head["launches"], "clocks": clocks}
+    if not args.no_workloads:
+        line["workloads"] = {"sphere32": bench_sphere32(mpm, W, ctx, stream, flush, args.warmup),
+                             "patches64": bench_patches64(mpm, W, ctx, stream, flush, args.warmup),
+                             "growth512": bench_growth512(mpm, W, ctx, stream, flush)}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_steps)
     if rank == 0:

@@ -150,6 +150,17 @@ mpm_status mpm_box_extract(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecie
                            const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, void *stream);
 
 /*
+ * Refresh a subgrid from the lattice without recomputing its box: re-gather
+ * the face flags, cell ids, dfac and the fields c^n of the stored tiles of the
+ * last extraction (Sec. 2.3 refreshes the box only every 50 MCS; between
+ * refreshes only the fields and cell states change).  The lattice must have
+ * the dims of that extraction.  Tiles that gained an in-mask voxel since then
+ * are not picked up: call mpm_box_extract again when the mask changes.
+ * Invalidates the assembly.  Queued on `stream`, no synchronisation.
+ */
+mpm_status mpm_subgrid_refresh(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, void *stream);
+
+/*
  * Assemble the implicit-Euler FV system of every species on the extracted box
  * (Eq. 1-4 discretised as in Sec. 2.4).  For an in-mask voxel P:
  *   A_PP = 1 + dt (mu + k_cell[id]) + (dt/h^2) sum_f w_f D_f
@@ -183,6 +194,45 @@ mpm_status mpm_solve_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *sca
  */
 mpm_status mpm_solve_batch(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
                            int32_t nsys, const mpm_opts *opt, mpm_report *reps, void *stream);
+
+/*
+ * One implicit-Euler step of nsys extracted systems with fixed boxes (the
+ * batched form): for every system refresh c^n from lats[i] (as
+ * mpm_subgrid_refresh), assemble with prms[i], then solve every (system,
+ * species) pair in ONE persistent launch (as mpm_solve_batch) and scatter the
+ * solutions onto lats[i].  The first call captures the whole sequence in a
+ * CUDA graph; later calls with the same subgrids (not re-extracted), lattice
+ * and parameter structs and options replay it (one graph launch per step).
+ * Where capture is unavailable the same sequence runs eagerly.  Synchronises
+ * `stream` and fills reps (may be NULL; nsys entries).
+ */
+mpm_status mpm_batch_step(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                          const mpm_params *const *prms, int32_t nsys, const mpm_opts *opt, mpm_report *reps,
+                          void *stream);
+
+/*
+ * Autotuner, tile shape: among the candidate shapes 8x4x4, 8x8x4, 4x4x4,
+ * 8x4x2, 16x4x2, 8x8x2, 4x4x2, 16x4x4 pick the one whose active tiles store
+ * the fewest voxels for this lattice's box (ties: the larger tile), counted
+ * exactly on the device.  Writes the tile to out_tile and the stored-voxel
+ * count to *out_stored (nullable).  Synchronises `stream` once per candidate.
+ */
+mpm_status mpm_tune_tile(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, int32_t out_tile[3],
+                         int64_t *out_stored, void *stream);
+
+/*
+ * Autotuner, restart length and solver kernel variant for a batch of
+ * assembled subgrids: times a warm-up and a measured solve from c^n for every
+ * candidate (m in {4, 8, 16}; for FP32 with m <= 8 the 4 kernel variants) and
+ * keeps the fastest that converges.  Writes m into opt->restart and the
+ * variant to *out_variant, and makes that variant the context's default.
+ * cache_path (nullable) is a text file of earlier results, keyed by the GPU,
+ * precision, tolerance and every system's bucketed box shape and mask
+ * occupancy; a hit skips the timing, a miss appends a line.  The iterates are
+ * left at c^n.
+ */
+mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys, mpm_opts *opt,
+                           int32_t *out_variant, const char *cache_path, void *stream);
 
 /* Copy `what` of species s from the subgrid into dst (device, box-dense,
  * nx*ny*nz elements of the export type).  Voxels of tiles that hold no
@@ -225,6 +275,7 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
  * streaming passes (WORK), waiting at team barriers (WAIT), summing the team's
  * partial sums (REDUCE) and in the FP64 least-squares/state updates (SERIAL). */
 #define MPM_COUNTER_LAUNCHES 1
+#define MPM_COUNTER_BATCH_GRAPH 10   /* 1 if the last mpm_batch_step replays a captured graph */
 #define MPM_COUNTER_PHASE_WORK_NS 2
 #define MPM_COUNTER_PHASE_WAIT_NS 3
 #define MPM_COUNTER_PHASE_REDUCE_NS 4

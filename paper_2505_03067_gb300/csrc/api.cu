@@ -100,6 +100,8 @@ mpm_status mpm_create(mpm_ctx **out, size_t workspace_bytes)
 mpm_status mpm_destroy(mpm_ctx *ctx)
 {
     if (!ctx) return MPM_ERR_ARG;
+    mpm_batch_graph_free(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_box);
     cudaFree(ctx->d_count);
     cudaFree(ctx->d_err);
@@ -109,6 +111,7 @@ mpm_status mpm_destroy(mpm_ctx *ctx)
     cudaFree(ctx->d_args);
     cudaFree(ctx->d_tmp);
     cudaFree(ctx->d_prof);
+    cudaFree(ctx->d_tune);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -163,6 +166,13 @@ mpm_status mpm_box_extract(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecie
     return mpm_extract_impl(ctx, lat, nspecies, margin, tile, out_box, sub, (cudaStream_t)stream);
 }
 
+mpm_status mpm_subgrid_refresh(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_refresh_impl(ctx, sub, lat, (cudaStream_t)stream);
+}
+
 mpm_status mpm_assemble_coeffs(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, void *stream)
 {
     if (!ctx) return MPM_ERR_ARG;
@@ -186,6 +196,15 @@ mpm_status mpm_solve_batch(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lat
     if (!ctx) return MPM_ERR_ARG;
     ctx->err.clear();
     return mpm_solve_impl(ctx, subs, scatter_to, nsys, opt, reps, (cudaStream_t)stream);
+}
+
+mpm_status mpm_batch_step(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                          const mpm_params *const *prms, int32_t nsys, const mpm_opts *opt, mpm_report *reps,
+                          void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_batch_step_impl(ctx, subs, lats, prms, nsys, opt, reps, (cudaStream_t)stream);
 }
 
 mpm_status mpm_subgrid_export(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst, void *stream)
@@ -244,6 +263,7 @@ mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)
 {
     if (!ctx || !value) return MPM_ERR_ARG;
     if (key == MPM_COUNTER_LAUNCHES) { *value = ctx->launches; return MPM_OK; }
+    if (key == MPM_COUNTER_BATCH_GRAPH) { *value = mpm_batch_graph_active((mpm_ctx *)ctx); return MPM_OK; }
     if (key == MPM_COUNTER_PHASE_WORK_NS) {
         *value = (int64_t)(ctx->h_prof[4] + ctx->h_prof[5] + ctx->h_prof[6] + ctx->h_prof[7]);
         return MPM_OK;

@@ -507,11 +507,87 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
         ctx->launches += 1;
         MPM_CU(cudaGetLastError());
     }
+    for (int d = 0; d < 3; ++d) tmp.ldims[d] = lat->dims[d];
+    tmp.gen = sub->gen + 1;
     tmp.extracted = true;
     tmp.assembled = false;
     tmp.x_fresh = true;
     *sub = tmp;
     if (out_box) *out_box = box;
+    return MPM_OK;
+}
+
+// Active-tile count of the box for tile dims 2^lt (the tuner's bytes model):
+// the same bbox, finalize, activity and compaction kernels as the extract, on
+// the context's scratch tables.  Synchronises `st`.
+mpm_status mpm_count_active_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, const int32_t lt[3],
+                                 int64_t *nact, int64_t *mask_voxels, cudaStream_t st)
+{
+    const int64_t L = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2];
+    int32_t init[6] = {INT_MAX, INT_MAX, INT_MAX, -1, -1, -1};
+    MPM_CU(cudaMemcpyAsync(ctx->d_box, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    const int vec4 = ((uintptr_t)lat->cell_id % 16) == 0;
+    k_bbox<<<grid_for(L / 4 + 1, ctx->num_sms, 4), kBlock, 0, st>>>(lat->cell_id, (uint32_t)lat->dims[0],
+                                                                     (uint32_t)(lat->dims[0] * lat->dims[1]),
+                                                                     (uint32_t)L, vec4, ctx->d_box);
+    BoxGeo *d_geo = (BoxGeo *)(ctx->d_box + 8);
+    k_box_finalize<<<1, 32, 0, st>>>(ctx->d_box, margin, lat->dims[0], lat->dims[1], lat->dims[2], lt[0], lt[1], lt[2],
+                                     d_geo);
+    const int64_t ntl = (((int64_t)lat->dims[0] + (1 << lt[0]) - 1) >> lt[0]) *
+                        (((int64_t)lat->dims[1] + (1 << lt[1]) - 1) >> lt[1]) *
+                        (((int64_t)lat->dims[2] + (1 << lt[2]) - 1) >> lt[2]);
+    const size_t nt = (size_t)ntl;
+    const size_t need = align256(nt * 4) + align256(nt * 16) + align256(nt);
+    mpm_status r = mpm_grow(ctx, &ctx->d_tune, &ctx->tune_cap, need, "tuner tables");
+    if (r != MPM_OK) return r;
+    char *p = (char *)ctx->d_tune;
+    int32_t *tile_index = (int32_t *)p; p += align256(nt * 4);
+    int32_t *tile_coord = (int32_t *)p; p += align256(nt * 16);
+    int8_t *active = (int8_t *)p;
+    MPM_CU(cudaMemsetAsync(active, 0, nt, st));
+    MPM_CU(cudaMemsetAsync(ctx->d_count, 0, 2 * sizeof(int64_t), st));
+    k_tile_active<<<ctx->num_sms * 8, kBlock, 0, st>>>(lat->mask, d_geo, active, (unsigned long long *)ctx->d_count);
+    k_tile_scan<<<1, 1024, 0, st>>>(active, d_geo, tile_index, tile_coord, (unsigned long long *)(ctx->d_count + 1));
+    ctx->launches += 4;
+    MPM_CU(cudaGetLastError());
+    int64_t *hc = (int64_t *)ctx->h_stage;
+    MPM_CU(cudaMemcpyAsync(hc, ctx->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    *mask_voxels = hc[0];
+    *nact = hc[1];
+    return MPM_OK;
+}
+
+mpm_status mpm_refresh_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st)
+{
+    if (!sub || !lat || !lat->cell_id || !lat->mask) return mpm_fail(ctx, MPM_ERR_ARG, "refresh: null argument");
+    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "refresh: subgrid not extracted");
+    for (int d = 0; d < 3; ++d)
+        if (lat->dims[d] != sub->ldims[d]) return mpm_fail(ctx, MPM_ERR_ARG, "refresh: lattice dims differ from the extraction");
+    for (int s = 0; s < sub->nspecies; ++s)
+        if (!lat->field[s]) return mpm_fail(ctx, MPM_ERR_ARG, "refresh: null field pointer");
+    if ((lat->dfac != nullptr) != sub->has_dfac) return mpm_fail(ctx, MPM_ERR_ARG, "refresh: dfac presence differs from the extraction");
+    sub->assembled = false;
+    sub->x_fresh = true;
+    if (sub->NE == 0) return MPM_OK;
+    GatherArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.cell_id = lat->cell_id;
+    ga.mask = lat->mask;
+    ga.dfac_lat = lat->dfac;
+    ga.nspecies = sub->nspecies;
+    ga.flags = sub->flags;
+    ga.cell = sub->cell;
+    ga.dfac = sub->dfac;
+    for (int s = 0; s < sub->nspecies; ++s) {
+        ga.field[s] = lat->field[s];
+        ga.x[s] = sub->x[s];
+        ga.cn[s] = sub->cn[s];
+    }
+    BoxGeo g = make_geo(sub, lat->dims);
+    k_gather<<<grid_for(sub->NE, ctx->num_sms, 8), kBlock, 0, st>>>(ga, g, sub->tile_coord, sub->NE);
+    ctx->launches += 1;
+    MPM_CU(cudaGetLastError());
     return MPM_OK;
 }
 

@@ -264,6 +264,10 @@ struct mpm_ctx {
     int64_t launches = 0;        // kernels launched by this context
     int32_t phase_prof = 0;      // record the solver's phase times (test/tuning hook)
     int32_t solver_variant = 0;  // solver kernel variant (tuning)
+    void *batch_graph = nullptr; // captured batched step (solver.cu)
+    cudaStream_t cap_stream = nullptr;  // stream used only for graph capture
+    void *d_tune = nullptr;      // tuner scratch tables
+    size_t tune_cap = 0;
     unsigned long long *d_prof = nullptr;
     unsigned long long h_prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // test hooks
@@ -273,9 +277,11 @@ struct mpm_ctx {
 
 struct mpm_subgrid {
     bool extracted = false, assembled = false;
+    uint64_t gen = 0;                // bumped by every extraction (buffers may move)
     int32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, n[3] = {0, 0, 0};
     int32_t lt[3] = {3, 2, 2};
     int32_t nt[3] = {0, 0, 0};
+    int32_t ldims[3] = {0, 0, 0};    // lattice dims of the extraction
     int32_t ntiles = 0, nact = 0;
     int64_t NE = 0, mask_voxels = 0;
     int32_t nspecies = 0;
@@ -325,6 +331,9 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
                             const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st);
 mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, cudaStream_t st);
 mpm_status mpm_scatter_impl(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st);
+mpm_status mpm_refresh_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st);
+mpm_status mpm_count_active_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, const int32_t lt[3],
+                                 int64_t *nact, int64_t *mask_voxels, cudaStream_t st);
 mpm_status mpm_export_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst,
                            cudaStream_t st);
 mpm_status mpm_import_impl(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const double *src, cudaStream_t st);
@@ -332,3 +341,8 @@ mpm_status mpm_apply_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const
                           cudaStream_t st);
 mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
                           int32_t nsys, const mpm_opts *opt, mpm_report *reps, cudaStream_t st);
+mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                               const mpm_params *const *prms, int32_t nsys, const mpm_opts *opt, mpm_report *reps,
+                               cudaStream_t st);
+void mpm_batch_graph_free(mpm_ctx *ctx);
+int mpm_batch_graph_active(mpm_ctx *ctx);

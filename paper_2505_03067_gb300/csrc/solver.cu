@@ -720,35 +720,54 @@ static void plan_teams(const std::vector<double> &work, int G, std::vector<TeamD
     }
 }
 
-mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
-                          int32_t nsys, const mpm_opts *opt, mpm_report *reps, cudaStream_t st)
+// ------------------------------------------------------------------ solve plan / enqueue / finish
+struct SolvePlan {
+    int nsys = 0, nitem = 0, G = 0, nteam = 0;
+    size_t smem = 0;
+    KernFn fn = nullptr;
+    std::vector<SysDev> sd;
+    std::vector<int> item_sys, item_sp;
+    std::vector<TeamDesc> teams;
+    std::vector<int32_t> order, block_team;
+    size_t o_sys = 0, o_team = 0, o_order = 0, o_bt = 0, o_rep = 0, args_need = 0;
+    SolveArgs sa;
+};
+
+static mpm_status check_opts(mpm_ctx *ctx, const mpm_opts *opt)
 {
-    if (!subs || !opt || nsys < 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: null argument or nsys < 1");
+    if (!opt) return mpm_fail(ctx, MPM_ERR_ARG, "solve: null options");
     if (opt->restart < 1 || opt->restart > MPM_MAX_RESTART) return mpm_fail(ctx, MPM_ERR_ARG, "solve: restart out of [1, 32]");
     if (opt->maxit < 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: maxit < 1");
     if (opt->precision != 0 && opt->precision != 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: precision must be 0 or 1");
     if (!(opt->rtol >= 0.0) || !(opt->atol >= 0.0)) return mpm_fail(ctx, MPM_ERR_ARG, "solve: negative tolerance");
     if (opt->precision == 1 && !(opt->inner_rtol > 0.0 && opt->inner_rtol < 1.0))
         return mpm_fail(ctx, MPM_ERR_ARG, "solve: inner_rtol must be in (0, 1)");
-    for (int i = 0; i < nsys; ++i) {
-        if (!subs[i]) return mpm_fail(ctx, MPM_ERR_ARG, "solve: null subgrid");
-        if (!subs[i]->assembled) return mpm_fail(ctx, MPM_ERR_ARG, "solve: subgrid not assembled");
-    }
+    return MPM_OK;
+}
+
+// Host planning: Krylov bases (grown here, never during a capture), one work
+// item per (system, species), the grid, the team split and the descriptor
+// layout.  reset_x: restore x = c^n where a previous solve moved it (queued
+// on st).
+static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, const mpm_opts *opt, bool reset_x,
+                             cudaStream_t st, SolvePlan &P)
+{
     const int m = opt->restart;
     const int maxm = m <= 8 ? 8 : (m <= 16 ? 16 : 32);
     const size_t tsz = opt->precision ? sizeof(float) : sizeof(double);
-
-    // ---- Krylov bases and initial guesses; one work item per (system, species)
-    std::vector<SysDev> sd;
+    P.nsys = nsys;
+    for (int i = 0; i < nsys; ++i) {
+        if (!subs[i]) return mpm_fail(ctx, MPM_ERR_ARG, "solve: null subgrid");
+        if (!subs[i]->assembled && reset_x) return mpm_fail(ctx, MPM_ERR_ARG, "solve: subgrid not assembled");
+    }
     std::vector<double> work;
-    std::vector<int> item_sys, item_sp;
     for (int i = 0; i < nsys; ++i) {
         mpm_subgrid *sub = subs[i];
         const int64_t vstride = sub->NE > 0 ? ((sub->NE + 63) / 64) * 64 : 64;
         const size_t per = a256((size_t)(m + 1) * (size_t)vstride * tsz);
         mpm_status r = mpm_grow(ctx, &sub->krylov, &sub->krylov_bytes, per * sub->nspecies, "Krylov basis");
         if (r != MPM_OK) return r;
-        if (!opt->x0_given && !sub->x_fresh) {
+        if (reset_x && !opt->x0_given && !sub->x_fresh) {
             for (int s = 0; s < sub->nspecies; ++s)
                 MPM_CU(cudaMemcpyAsync(sub->x[s], sub->cn[s], (size_t)sub->NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
             sub->x_fresh = true;
@@ -769,78 +788,39 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
             d.Dsp[0] = full.Dsp[s];
             d.vstride = vstride;
             d.V[0] = (char *)sub->krylov + per * s;
-            sd.push_back(d);
+            P.sd.push_back(d);
             work.push_back((double)sub->NE + 1.0);
-            item_sys.push_back(i);
-            item_sp.push_back(s);
+            P.item_sys.push_back(i);
+            P.item_sp.push_back(s);
         }
     }
-    const int nitem = (int)sd.size();
-
-    // ---- grid and teams
-    size_t smem = 0;
-    KernFn fn = pick(opt->precision, maxm, ctx->solver_variant, smem);
+    P.nitem = (int)P.sd.size();
+    P.fn = pick(opt->precision, maxm, ctx->solver_variant, P.smem);
     const int gmax = mpm_solver_max_blocks(ctx, opt->precision, m, ctx->solver_variant);
     if (gmax < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "solve: occupancy query failed");
-    int G;
-    if (opt->nblocks > 0) G = std::min(opt->nblocks, gmax);
+    if (opt->nblocks > 0) P.G = std::min(opt->nblocks, gmax);
     else {
         double tot = 0.0;
         for (double w : work) tot += w;
-        // about 2 elements per thread per species at least; at most one CTA per SM
+        // about two elements per thread and item at least
         const double want = tot / (kSB * 2.0);
-        G = (int)std::min<double>(gmax, std::max(1.0, want));
-        G = std::max(G, std::min(nitem, gmax));
+        P.G = (int)std::min<double>(gmax, std::max(1.0, want));
+        P.G = std::max(P.G, std::min(P.nitem, gmax));
     }
-    std::vector<TeamDesc> teams;
-    std::vector<int32_t> order, block_team;
-    plan_teams(work, G, teams, order, block_team);
-    const int nteam = (int)teams.size();
-
-    // ---- descriptors to the device (pinned staging)
-    const size_t o_sys = 0;
-    const size_t o_team = a256(o_sys + sizeof(SysDev) * nitem);
-    const size_t o_order = a256(o_team + sizeof(TeamDesc) * nteam);
-    const size_t o_bt = a256(o_order + sizeof(int32_t) * nitem);
-    const size_t o_rep = a256(o_bt + sizeof(int32_t) * G);
-    const size_t args_need = a256(o_rep + sizeof(SysReport) * nitem);
-    mpm_status r = mpm_grow(ctx, &ctx->d_args, &ctx->args_cap, args_need, "solver descriptors");
+    plan_teams(work, P.G, P.teams, P.order, P.block_team);
+    P.nteam = (int)P.teams.size();
+    P.o_sys = 0;
+    P.o_team = a256(P.o_sys + sizeof(SysDev) * P.nitem);
+    P.o_order = a256(P.o_team + sizeof(TeamDesc) * P.nteam);
+    P.o_bt = a256(P.o_order + sizeof(int32_t) * P.nitem);
+    P.o_rep = a256(P.o_bt + sizeof(int32_t) * P.G);
+    P.args_need = a256(P.o_rep + sizeof(SysReport) * P.nitem);
+    const size_t pneed = 2 * (size_t)P.G * kKMax * sizeof(double);
+    mpm_status r = mpm_grow(ctx, (void **)&ctx->d_partials, &ctx->partials_cap, pneed, "reduction partials");
     if (r != MPM_OK) return r;
-    if (ctx->stage_cap < args_need + 256) {
-        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-        ctx->h_stage = nullptr;
-        MPM_CU(cudaMallocHost(&ctx->h_stage, args_need + 4096));
-        ctx->stage_cap = args_need + 4096;
-    }
-    // the staging buffer is free: every call that uses it ends with a stream synchronisation
-    char *hs = (char *)ctx->h_stage;
-    memcpy(hs + o_sys, sd.data(), sizeof(SysDev) * nitem);
-    memcpy(hs + o_team, teams.data(), sizeof(TeamDesc) * nteam);
-    memcpy(hs + o_order, order.data(), sizeof(int32_t) * nitem);
-    memcpy(hs + o_bt, block_team.data(), sizeof(int32_t) * G);
-    MPM_CU(cudaMemcpyAsync(ctx->d_args, hs, o_rep, cudaMemcpyHostToDevice, st));
-    const size_t pneed = 2 * (size_t)G * kKMax * sizeof(double);
-    r = mpm_grow(ctx, (void **)&ctx->d_partials, &ctx->partials_cap, pneed, "reduction partials");
-    if (r != MPM_OK) return r;
-    if (ctx->bar_cap < nteam) {
-        if (ctx->d_bar) cudaFree(ctx->d_bar);
-        ctx->d_bar = nullptr;
-        MPM_CU(cudaMalloc(&ctx->d_bar, (size_t)nteam * 32 * sizeof(uint32_t)));
-        ctx->bar_cap = nteam;
-    }
-    MPM_CU(cudaMemsetAsync(ctx->d_bar, 0, (size_t)nteam * 32 * sizeof(uint32_t), st));
-    MPM_CU(cudaMemsetAsync(ctx->d_abort, 0, sizeof(int32_t), st));
-    MPM_CU(cudaMemsetAsync((char *)ctx->d_args + o_rep, 0, sizeof(SysReport) * nitem, st));
-
-    SolveArgs sa;
-    sa.sys = (const SysDev *)((char *)ctx->d_args + o_sys);
-    sa.teams = (const TeamDesc *)((char *)ctx->d_args + o_team);
-    sa.sys_order = (const int32_t *)((char *)ctx->d_args + o_order);
-    sa.block_team = (const int32_t *)((char *)ctx->d_args + o_bt);
-    sa.reports = (SysReport *)((char *)ctx->d_args + o_rep);
+    SolveArgs &sa = P.sa;
+    memset(&sa, 0, sizeof(sa));
     sa.partials = ctx->d_partials;
-    sa.bar = ctx->d_bar;
-    sa.abort_flag = ctx->d_abort;
     sa.rtol = opt->rtol;
     sa.atol = opt->atol;
     sa.inner_rtol = opt->precision ? opt->inner_rtol : 0.0;
@@ -848,43 +828,63 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
     sa.maxit = opt->maxit;
     sa.timeout_ns = ctx->timeout_ns;
     sa.skip_block = ctx->skip_block;
-    sa.prof = nullptr;
-    if (ctx->phase_prof) {
-        if (!ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
-        MPM_CU(cudaMemsetAsync(ctx->d_prof, 0, 8 * sizeof(unsigned long long), st));
-        sa.prof = ctx->d_prof;
-    }
+    return MPM_OK;
+}
+
+static void fill_descriptors(const SolvePlan &P, char *h)
+{
+    memcpy(h + P.o_sys, P.sd.data(), sizeof(SysDev) * P.nitem);
+    memcpy(h + P.o_team, P.teams.data(), sizeof(TeamDesc) * P.nteam);
+    memcpy(h + P.o_order, P.order.data(), sizeof(int32_t) * P.nitem);
+    memcpy(h + P.o_bt, P.block_team.data(), sizeof(int32_t) * P.G);
+}
+
+// Queue the solve: counters and reports cleared, then the cooperative launch.
+// Only stream work (capturable); descriptors already sit at d_args.
+static mpm_status enqueue_solve(mpm_ctx *ctx, SolvePlan &P, char *d_args, uint32_t *d_bar, int32_t *d_abort,
+                                unsigned long long *d_prof, cudaStream_t st)
+{
+    SolveArgs sa = P.sa;
+    sa.sys = (const SysDev *)(d_args + P.o_sys);
+    sa.teams = (const TeamDesc *)(d_args + P.o_team);
+    sa.sys_order = (const int32_t *)(d_args + P.o_order);
+    sa.block_team = (const int32_t *)(d_args + P.o_bt);
+    sa.reports = (SysReport *)(d_args + P.o_rep);
+    sa.bar = d_bar;
+    sa.abort_flag = d_abort;
+    sa.prof = d_prof;
+    MPM_CU(cudaMemsetAsync(d_bar, 0, (size_t)P.nteam * 32 * sizeof(uint32_t), st));
+    MPM_CU(cudaMemsetAsync(d_abort, 0, sizeof(int32_t), st));
+    MPM_CU(cudaMemsetAsync(d_args + P.o_rep, 0, sizeof(SysReport) * P.nitem, st));
+    if (d_prof) MPM_CU(cudaMemsetAsync(d_prof, 0, 8 * sizeof(unsigned long long), st));
     void *kargs[] = {&sa};
-    MPM_CU(cudaEventRecord(ctx->ev0, st));
-    MPM_CU(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(kSB), kargs, smem, st));
+    MPM_CU(cudaLaunchCooperativeKernel((const void *)P.fn, dim3(P.G), dim3(kSB), kargs, P.smem, st));
     ctx->launches += 1;
-    MPM_CU(cudaEventRecord(ctx->ev1, st));
+    return MPM_OK;
+}
 
-    // ---- results
-    SysReport *hrep = (SysReport *)(hs + o_rep);
-    MPM_CU(cudaMemcpyAsync(hrep, sa.reports, sizeof(SysReport) * nitem, cudaMemcpyDeviceToHost, st));
-    int32_t *hflags = (int32_t *)(hs + args_need);
-    MPM_CU(cudaMemcpyAsync(hflags, ctx->d_abort, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    MPM_CU(cudaStreamSynchronize(st));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    const bool timed_out = hflags[0] != 0;
-    bool bad_id = false;
+static int status_rank(int s)
+{
+    switch (s) {
+    case MPM_OK: return 0;
+    case MPM_ERR_NOCONV: return 1;
+    case MPM_ERR_BREAKDOWN: return 2;
+    case MPM_ERR_ARG: return 3;
+    case MPM_ERR_TIMEOUT: return 4;
+    default: return 5;
+    }
+}
 
+// Map the per-item reports back to systems; scatter (queued) unless the solve
+// timed out or scatter already ran on the device.
+static mpm_status finish_solve(mpm_ctx *ctx, const SolvePlan &P, mpm_subgrid *const *subs, const SysReport *hrep,
+                               bool timed_out, float ms, mpm_report *reps, const mpm_lattice *const *scatter_to,
+                               cudaStream_t st)
+{
     mpm_status worst = MPM_OK;
-    auto rank_of = [](int s) {
-        switch (s) {
-        case MPM_OK: return 0;
-        case MPM_ERR_NOCONV: return 1;
-        case MPM_ERR_BREAKDOWN: return 2;
-        case MPM_ERR_ARG: return 3;
-        case MPM_ERR_TIMEOUT: return 4;
-        default: return 5;
-        }
-    };
-    std::vector<mpm_report> R(nsys);
-    for (int i = 0; i < nsys; ++i) {
+    bool bad_id = false;
+    std::vector<mpm_report> R(P.nsys);
+    for (int i = 0; i < P.nsys; ++i) {
         memset(&R[i], 0, sizeof(mpm_report));
         mpm_subgrid *sub = subs[i];
         sub->x_fresh = false;
@@ -893,8 +893,8 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
         R[i].stored_voxels = sub->NE;
         R[i].solve_ms = ms;
     }
-    for (int it = 0; it < nitem; ++it) {
-        const int i = item_sys[it], s = item_sp[it];
+    for (int it = 0; it < P.nitem; ++it) {
+        const int i = P.item_sys[it], s = P.item_sp[it];
         R[i].iters[s] = hrep[it].iters[0];
         R[i].jsum[s] = hrep[it].jsum[0];
         R[i].cycles[s] = hrep[it].cycles[0];
@@ -905,20 +905,236 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
         R[i].status[s] = stt;
         R[i].res[s] = hrep[it].res[0];
         R[i].bnorm[s] = hrep[it].bnorm[0];
-        if (rank_of(stt) > rank_of(worst)) worst = (mpm_status)stt;
+        if (status_rank(stt) > status_rank(worst)) worst = (mpm_status)stt;
     }
-    for (int i = 0; i < nsys; ++i) {
+    for (int i = 0; i < P.nsys; ++i) {
         if (reps) reps[i] = R[i];
         if (!timed_out && scatter_to && scatter_to[i]) {
-            r = mpm_scatter_impl(ctx, subs[i], scatter_to[i], st);
+            mpm_status r = mpm_scatter_impl(ctx, subs[i], scatter_to[i], st);
             if (r != MPM_OK) return r;
         }
     }
-    if (timed_out) {
-        MPM_CU(cudaMemsetAsync(ctx->d_abort, 0, sizeof(int32_t), st));
-        return mpm_fail(ctx, MPM_ERR_TIMEOUT, "solve: a bounded inter-CTA wait expired");
-    }
+    if (timed_out) return mpm_fail(ctx, MPM_ERR_TIMEOUT, "solve: a bounded inter-CTA wait expired");
     if (bad_id) return mpm_fail(ctx, MPM_ERR_ARG, "solve: a cell id lies outside the rate tables");
     if (worst != MPM_OK) mpm_fail(ctx, worst, "solve: not every species converged");
     return worst;
+}
+
+static mpm_status ensure_stage(mpm_ctx *ctx, size_t need)
+{
+    if (ctx->stage_cap >= need) return MPM_OK;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->stage_cap = 0;
+    MPM_CU(cudaMallocHost(&ctx->h_stage, need));
+    ctx->stage_cap = need;
+    return MPM_OK;
+}
+
+mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
+                          int32_t nsys, const mpm_opts *opt, mpm_report *reps, cudaStream_t st)
+{
+    if (!subs || nsys < 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: null argument or nsys < 1");
+    mpm_status r = check_opts(ctx, opt);
+    if (r != MPM_OK) return r;
+    SolvePlan P;
+    r = plan_solve(ctx, subs, nsys, opt, true, st, P);
+    if (r != MPM_OK) return r;
+    r = mpm_grow(ctx, &ctx->d_args, &ctx->args_cap, P.args_need, "solver descriptors");
+    if (r != MPM_OK) return r;
+    r = ensure_stage(ctx, P.args_need + 4096);
+    if (r != MPM_OK) return r;
+    if (ctx->bar_cap < P.nteam) {
+        if (ctx->d_bar) cudaFree(ctx->d_bar);
+        ctx->d_bar = nullptr;
+        ctx->bar_cap = 0;
+        MPM_CU(cudaMalloc(&ctx->d_bar, (size_t)P.nteam * 32 * sizeof(uint32_t)));
+        ctx->bar_cap = P.nteam;
+    }
+    if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+    // the staging buffer is free: every call that uses it ends with a stream synchronisation
+    char *hs = (char *)ctx->h_stage;
+    fill_descriptors(P, hs);
+    MPM_CU(cudaMemcpyAsync(ctx->d_args, hs, P.o_rep, cudaMemcpyHostToDevice, st));
+    MPM_CU(cudaEventRecord(ctx->ev0, st));
+    r = enqueue_solve(ctx, P, (char *)ctx->d_args, ctx->d_bar, ctx->d_abort, ctx->phase_prof ? ctx->d_prof : nullptr, st);
+    if (r != MPM_OK) return r;
+    MPM_CU(cudaEventRecord(ctx->ev1, st));
+    SysReport *hrep = (SysReport *)(hs + P.o_rep);
+    MPM_CU(cudaMemcpyAsync(hrep, (char *)ctx->d_args + P.o_rep, sizeof(SysReport) * P.nitem, cudaMemcpyDeviceToHost, st));
+    int32_t *hflags = (int32_t *)(hs + P.args_need);
+    MPM_CU(cudaMemcpyAsync(hflags, ctx->d_abort, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    const bool timed_out = hflags[0] != 0;
+    r = finish_solve(ctx, P, subs, hrep, timed_out, ms, reps, scatter_to, st);
+    if (timed_out) cudaMemsetAsync(ctx->d_abort, 0, sizeof(int32_t), st);
+    return r;
+}
+
+// ------------------------------------------------------------------ batched step in a CUDA graph
+struct BatchGraph {
+    bool valid = false;
+    bool graph_failed = false;
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    char *d_args = nullptr;
+    size_t args_cap = 0;
+    uint32_t *d_bar = nullptr;
+    int32_t *d_abort = nullptr;
+    int64_t graph_launches = 0;    // kernels in the captured graph
+    SolvePlan plan;
+};
+
+static void batch_key(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                      const mpm_params *const *prms, int nsys, const mpm_opts *opt, std::vector<unsigned char> &k)
+{
+    auto put = [&](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        k.insert(k.end(), c, c + n);
+    };
+    put(&nsys, sizeof(nsys));
+    put(opt, sizeof(*opt));
+    put(&ctx->solver_variant, sizeof(int32_t));
+    put(&ctx->timeout_ns, sizeof(uint64_t));
+    put(&ctx->skip_block, sizeof(int32_t));
+    for (int i = 0; i < nsys; ++i) {
+        put(&subs[i], sizeof(void *));
+        put(&subs[i]->gen, sizeof(subs[i]->gen));
+        put(&subs[i]->krylov, sizeof(void *));
+        put(lats[i], sizeof(mpm_lattice));
+        put(prms[i], sizeof(mpm_params));
+    }
+}
+
+void mpm_batch_graph_free(mpm_ctx *ctx)
+{
+    BatchGraph *B = (BatchGraph *)ctx->batch_graph;
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    cudaFree(B->d_args);
+    cudaFree(B->d_bar);
+    cudaFree(B->d_abort);
+    delete B;
+    ctx->batch_graph = nullptr;
+}
+
+mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                               const mpm_params *const *prms, int32_t nsys, const mpm_opts *opt, mpm_report *reps,
+                               cudaStream_t st)
+{
+    if (!subs || !lats || !prms || nsys < 1) return mpm_fail(ctx, MPM_ERR_ARG, "batch_step: null argument or nsys < 1");
+    mpm_status r = check_opts(ctx, opt);
+    if (r != MPM_OK) return r;
+    for (int i = 0; i < nsys; ++i)
+        if (!subs[i] || !lats[i] || !prms[i] || !subs[i]->extracted)
+            return mpm_fail(ctx, MPM_ERR_ARG, "batch_step: null or unextracted system");
+    if (!ctx->batch_graph) ctx->batch_graph = new BatchGraph();
+    BatchGraph *B = (BatchGraph *)ctx->batch_graph;
+    std::vector<unsigned char> key;
+    batch_key(ctx, subs, lats, prms, nsys, opt, key);
+    const bool use_graph = !ctx->phase_prof;
+    if (!(B->valid && B->key == key) || !use_graph) {
+        // (re)build: eager planning first (allocations), then capture
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+        B->valid = false;
+        for (int i = 0; i < nsys; ++i) {
+            r = mpm_refresh_impl(ctx, subs[i], lats[i], st);
+            if (r != MPM_OK) return r;
+            r = mpm_assemble_impl(ctx, subs[i], prms[i], st);
+            if (r != MPM_OK) return r;
+        }
+        B->plan = SolvePlan();
+        r = plan_solve(ctx, subs, nsys, opt, false, st, B->plan);
+        if (r != MPM_OK) return r;
+        r = mpm_grow(ctx, (void **)&B->d_args, &B->args_cap, B->plan.args_need, "batch descriptors");
+        if (r != MPM_OK) return r;
+        if (!B->d_bar) {
+            MPM_CU(cudaMalloc(&B->d_bar, (size_t)ctx->num_sms * 4 * 32 * sizeof(uint32_t)));
+            MPM_CU(cudaMalloc(&B->d_abort, 256));
+        }
+        if (B->plan.nteam > ctx->num_sms * 4) return mpm_fail(ctx, MPM_ERR_ARG, "batch_step: too many teams");
+        r = ensure_stage(ctx, B->plan.args_need + 4096);
+        if (r != MPM_OK) return r;
+        fill_descriptors(B->plan, (char *)ctx->h_stage);
+        MPM_CU(cudaMemcpyAsync(B->d_args, ctx->h_stage, B->plan.o_rep, cudaMemcpyHostToDevice, st));
+        MPM_CU(cudaStreamSynchronize(st));   // descriptors in place before any capture
+        if (use_graph && !B->graph_failed) {
+            // capture on a stream of the context (the caller's may be the legacy
+            // default stream, which cannot be captured); the graph is then
+            // launched on the caller's stream
+            if (!ctx->cap_stream) MPM_CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cudaStream_t cs = ctx->cap_stream;
+            cudaGraph_t g = nullptr;
+            const int64_t launches0 = ctx->launches;
+            bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                for (int i = 0; i < nsys && ok; ++i) {
+                    ok = mpm_refresh_impl(ctx, subs[i], lats[i], cs) == MPM_OK &&
+                         mpm_assemble_impl(ctx, subs[i], prms[i], cs) == MPM_OK;
+                }
+                ok = ok && enqueue_solve(ctx, B->plan, B->d_args, B->d_bar, B->d_abort, nullptr, cs) == MPM_OK;
+                for (int i = 0; i < nsys && ok; ++i) ok = mpm_scatter_impl(ctx, subs[i], lats[i], cs) == MPM_OK;
+                const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+                ok = ok && ec == cudaSuccess && g != nullptr;
+            }
+            B->graph_launches = ctx->launches - launches0;
+            ctx->launches = launches0;   // captured, not launched
+            if (ok) ok = cudaGraphInstantiate(&B->exec, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (ok) {
+                B->valid = true;
+                B->key = key;
+            } else {
+                B->exec = nullptr;
+                B->graph_failed = true;   // this device or driver cannot capture it: stay eager
+            }
+        }
+    }
+    SolvePlan &P = B->plan;
+    r = ensure_stage(ctx, P.args_need + 4096);
+    if (r != MPM_OK) return r;
+    char *hs = (char *)ctx->h_stage;
+    MPM_CU(cudaEventRecord(ctx->ev0, st));
+    if (B->valid) {
+        MPM_CU(cudaGraphLaunch(B->exec, st));
+        ctx->launches += B->graph_launches;
+    } else {
+        // eager form of the same sequence (graph unavailable or phase timing on)
+        for (int i = 0; i < nsys; ++i) {
+            r = mpm_refresh_impl(ctx, subs[i], lats[i], st);
+            if (r != MPM_OK) return r;
+            r = mpm_assemble_impl(ctx, subs[i], prms[i], st);
+            if (r != MPM_OK) return r;
+        }
+        if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+        r = enqueue_solve(ctx, P, B->d_args, B->d_bar, B->d_abort, ctx->phase_prof ? ctx->d_prof : nullptr, st);
+        if (r != MPM_OK) return r;
+        for (int i = 0; i < nsys; ++i) {
+            r = mpm_scatter_impl(ctx, subs[i], lats[i], st);
+            if (r != MPM_OK) return r;
+        }
+    }
+    MPM_CU(cudaEventRecord(ctx->ev1, st));
+    SysReport *hrep = (SysReport *)(hs + P.o_rep);
+    MPM_CU(cudaMemcpyAsync(hrep, B->d_args + P.o_rep, sizeof(SysReport) * P.nitem, cudaMemcpyDeviceToHost, st));
+    int32_t *hflags = (int32_t *)(hs + P.args_need);
+    MPM_CU(cudaMemcpyAsync(hflags, B->d_abort, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    const bool timed_out = hflags[0] != 0;
+    for (int i = 0; i < nsys; ++i) subs[i]->assembled = true;
+    return finish_solve(ctx, P, subs, hrep, timed_out, ms, reps, nullptr, st);
+}
+
+int mpm_batch_graph_active(mpm_ctx *ctx)
+{
+    BatchGraph *B = (BatchGraph *)ctx->batch_graph;
+    return B && B->valid ? 1 : 0;
 }

@@ -27,7 +27,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", "mpm_subgrid_destroy",
            "mpm_subgrid_info", "mpm_box_extract", "mpm_assemble_coeffs", "mpm_solve_step", "mpm_solve_batch",
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
-           "mpm_counter_get", "mpm_box_bounds_noalloc"]
+           "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
+           "mpm_tune_tile", "mpm_tune_solver"]
 
 
 class mpm_box(C.Structure):
@@ -98,6 +99,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_box_extract": [P, C.POINTER(mpm_lattice), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
                             C.POINTER(mpm_box), P, P],
         "mpm_assemble_coeffs": [P, P, C.POINTER(mpm_params), P],
+        "mpm_subgrid_refresh": [P, P, C.POINTER(mpm_lattice), P],
+        "mpm_tune_tile": [P, C.POINTER(mpm_lattice), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), P],
+        "mpm_tune_solver": [P, C.POINTER(P), C.c_int32, C.POINTER(mpm_opts), C.POINTER(C.c_int32), C.c_char_p, P],
+        "mpm_batch_step": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.POINTER(C.POINTER(mpm_params)),
+                           C.c_int32, C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
         "mpm_solve_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
         "mpm_solve_batch": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.c_int32, C.POINTER(mpm_opts),
                             C.POINTER(mpm_report), P],
@@ -233,6 +239,23 @@ class Context:
     def debug_set(self, key: int, value: int):
         self._check(self.lib.mpm_debug_set(self.ptr, key, value), "mpm_debug_set")
 
+    def mpm_tune_tile(self, lat: "DeviceLattice", margin: int, stream=None):
+        t = (C.c_int32 * 3)()
+        n = C.c_int64(0)
+        ls = lat.struct()
+        self._check(self.lib.mpm_tune_tile(self.ptr, C.byref(ls), margin, t, C.byref(n), _stream_ptr(stream)),
+                    "mpm_tune_tile")
+        return tuple(t), int(n.value)
+
+    def mpm_tune_solver(self, subs, opts: "mpm_opts", cache_path=None, stream=None):
+        n = len(subs)
+        hs = (C.c_void_p * n)(*[s.h.value for s in subs])
+        v = C.c_int32(0)
+        cp = cache_path.encode() if cache_path else None
+        self._check(self.lib.mpm_tune_solver(self.ptr, hs, n, C.byref(opts), C.byref(v), cp, _stream_ptr(stream)),
+                    "mpm_tune_solver")
+        return int(opts.restart), int(v.value)
+
     def subgrid_create(self) -> "Subgrid":
         h = C.c_void_p()
         self._check(self.lib.mpm_subgrid_create(self.ptr, C.byref(h)), "mpm_subgrid_create")
@@ -268,6 +291,11 @@ class Subgrid:
             return None
         self.nspecies = nspecies
         return box.as_tuple()
+
+    def mpm_subgrid_refresh(self, lat: DeviceLattice, stream=None):
+        ls = lat.struct()
+        self.ctx._check(self.ctx.lib.mpm_subgrid_refresh(self.ctx.ptr, self.h, C.byref(ls), _stream_ptr(stream)),
+                        "mpm_subgrid_refresh")
 
     def mpm_assemble_coeffs(self, prm: DeviceParams, stream=None):
         self.ctx._check(self.ctx.lib.mpm_assemble_coeffs(self.ctx.ptr, self.h, C.byref(prm.struct),
@@ -337,6 +365,49 @@ def mpm_solve_batch(ctx: Context, subs, opts: mpm_opts, scatter_to=None, stream=
     st = ctx.lib.mpm_solve_batch(ctx.ptr, hs, lat_ptrs, n, C.byref(opts), reps, _stream_ptr(stream))
     ctx._check(st, "mpm_solve_batch", allow=allow)
     return st, [reps[i].as_dict(subs[i].nspecies) for i in range(n)]
+
+
+class BatchStepper:
+    """Fixed-box batched steps of many systems (mpm_batch_step): every system is
+    extracted once, then each step refreshes, assembles, solves all (system,
+    species) pairs in one persistent launch and scatters, replayed from a CUDA
+    graph after the first call."""
+
+    def __init__(self, ctx: Context, lats, prms, margins, tile=None, tune_tiles=False):
+        self.ctx = ctx
+        self.lats, self.prms = list(lats), list(prms)
+        self.subs = []
+        self.tiles = []
+        for lat, m in zip(self.lats, margins):
+            sub = ctx.subgrid_create()
+            t = ctx.mpm_tune_tile(lat, m)[0] if tune_tiles else tile
+            self.tiles.append(t)
+            box = sub.mpm_box_extract(lat, lat.nspecies, m, t)
+            if box is None:
+                raise MpmError(ERR_EMPTY, "batch system without tumour")
+            self.subs.append(sub)
+        n = len(self.subs)
+        self._hs = (C.c_void_p * n)(*[s.h.value for s in self.subs])
+        self._ls = [l.struct() for l in self.lats]
+        self._lp = (C.POINTER(mpm_lattice) * n)(*[C.pointer(l) for l in self._ls])
+        self._pp = (C.POINTER(mpm_params) * n)(*[C.pointer(p.struct) for p in self.prms])
+        self._reps = (mpm_report * n)()
+        for sub, prm in zip(self.subs, self.prms):
+            sub.mpm_assemble_coeffs(prm)
+
+    def tune(self, opts: mpm_opts, cache_path=None):
+        """Restart length and kernel variant for this batch (mpm_tune_solver)."""
+        return self.ctx.mpm_tune_solver(self.subs, opts, cache_path)
+
+    def step(self, opts: mpm_opts, stream=None, allow=(ERR_NOCONV,)):
+        n = len(self.subs)
+        st = self.ctx.lib.mpm_batch_step(self.ctx.ptr, self._hs, self._lp, self._pp, n, C.byref(opts), self._reps,
+                                         _stream_ptr(stream))
+        self.ctx._check(st, "mpm_batch_step", allow=allow)
+        return st, [self._reps[i].as_dict(self.subs[i].nspecies) for i in range(n)]
+
+    def graph_active(self) -> bool:
+        return self.ctx.counter(10) == 1
 
 
 class StepSolver:

@@ -1,0 +1,96 @@
+"""Batched solves: many uneven pleural-shell patches x 3 species in one
+persistent launch (mpm_solve_batch) and the graph-captured fixed-box step
+(mpm_batch_step), against single-system solves and the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_03067_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_03067_gb300 import build, mpm
+    build.build()
+    return mpm
+
+
+@pytest.fixture(scope="module")
+def patches():
+    ps = W.patches()
+    # a spread of sizes: the 6 smallest, 2 middle and the largest patch
+    order = sorted(range(len(ps)), key=lambda i: ps[i].lattice.cell_id.size)
+    pick = order[:6] + order[31:33] + order[-1:]
+    return [ps[i] for i in pick]
+
+
+def _oracle_steps(wl, nsteps):
+    ref = wl.lattice.copy()
+    for _ in range(nsteps):
+        rep = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-12)
+        assert rep["status"] == oracle.OK
+    return ref
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_step_graph_matches_oracle(M, patches, precision):
+    ctx = M.Context()
+    lats = [M.DeviceLattice(p.lattice) for p in patches]
+    prms = [M.DeviceParams(p.params) for p in patches]
+    bs = M.BatchStepper(ctx, lats, prms, [p.margin for p in patches])
+    if precision == 0:
+        opts = M.make_opts(rtol=0.0, atol=1e-12, restart=8, maxit=500)
+    else:
+        opts = M.make_opts(rtol=1e-9, restart=8, maxit=500, precision=1, inner_rtol=1e-6)
+    for step in range(3):
+        st, reps = bs.step(opts)
+        assert st == M.OK
+        if step >= 1:
+            assert bs.graph_active()
+    for p, lat, rep in zip(patches, lats, reps):
+        ref = _oracle_steps(p, 3)
+        got = lat.fields_numpy()
+        m = p.lattice.mask > 0
+        for s in range(3):
+            if precision == 0:
+                assert np.max(np.abs(got[s] - ref.fields[s])) <= 1e-10
+            else:
+                assert np.linalg.norm(got[s][m] - ref.fields[s][m]) <= 3e-9 * np.linalg.norm(ref.fields[s][m])
+
+
+def test_solve_batch_matches_single_solves(M, patches):
+    ctx = M.Context()
+    opts = M.make_opts(rtol=0.0, atol=1e-12, restart=8, maxit=500)
+    lats_b = [M.DeviceLattice(p.lattice) for p in patches]
+    subs = []
+    for p, lat in zip(patches, lats_b):
+        sub = ctx.subgrid_create()
+        sub.mpm_box_extract(lat, 3, p.margin)
+        sub.mpm_assemble_coeffs(M.DeviceParams(p.params))
+        subs.append(sub)
+    st, reps = M.mpm_solve_batch(ctx, subs, opts, scatter_to=lats_b)
+    assert st == M.OK
+    for p, lat in zip(patches, lats_b):
+        lat1 = M.DeviceLattice(p.lattice)
+        M.StepSolver(ctx, lat1, M.DeviceParams(p.params), p.margin).step(opts)
+        assert np.max(np.abs(lat.fields_numpy() - lat1.fields_numpy())) <= 1e-10
+
+
+def test_refresh_equals_re_extract(M):
+    wl = W.random_case(31, (24, 20, 18), nspecies=3)
+    ctx = M.Context()
+    lat = M.DeviceLattice(wl.lattice)
+    sub = ctx.subgrid_create()
+    sub.mpm_box_extract(lat, 3, wl.margin)
+    lat.fields.mul_(0.5)
+    sub.mpm_subgrid_refresh(lat)
+    x_ref = [sub.mpm_subgrid_export(M.EXPORT_X, s).cpu().numpy() for s in range(3)]
+    sub2 = ctx.subgrid_create()
+    sub2.mpm_box_extract(lat, 3, wl.margin)
+    for s in range(3):
+        assert np.array_equal(x_ref[s], sub2.mpm_subgrid_export(M.EXPORT_X, s).cpu().numpy())
