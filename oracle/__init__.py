@@ -204,3 +204,124 @@ def step(lat, params, margin: int, bc_box: int = 0, rtol: float = 1e-12, atol: f
         if info["status"] != OK:
             rep["status"] = info["status"]
     return rep
+
+
+# ---------------------------------------------------------------- CNN reference (cnn_oracle.c)
+CNN_CHANNELS = (9, 24, 24, 24, 24, 24, 3)
+
+
+def _cnn_lib():
+    L = lib()
+    if not getattr(L, "_cnn_ready", False):
+        L.orc_bf16.restype = C.c_double
+        L.orc_bf16.argtypes = [C.c_double]
+        L.orc_gelu.restype = C.c_double
+        L.orc_gelu.argtypes = [C.c_double]
+        L.orc_gelu_grad.restype = C.c_double
+        L.orc_gelu_grad.argtypes = [C.c_double]
+        L.orc_cnn_nparams.restype = C.c_int64
+        L.orc_cnn_loss.restype = C.c_double
+        L._cnn_ready = True
+    return L
+
+
+def bf16(a):
+    """Round to bfloat16 (nearest even), returned as float64."""
+    a = np.array(a, np.float64, copy=True)
+    _cnn_lib().orc_bf16_array(C.c_int64(a.size), _p(a))
+    return a
+
+
+def gelu(z):
+    return _cnn_lib().orc_gelu(float(z))
+
+
+def gelu_grad(z):
+    return _cnn_lib().orc_gelu_grad(float(z))
+
+
+def cnn_nparams() -> int:
+    return int(_cnn_lib().orc_cnn_nparams())
+
+
+def conv3(x, W, b=None):
+    """x: (nz, ny, nx, Ci); W: (27, Ci, Co); zero padding; returns (nz, ny, nx, Co)."""
+    x = np.ascontiguousarray(x, np.float64)
+    nz, ny, nx, Ci = x.shape
+    W = np.ascontiguousarray(W, np.float64)
+    Co = W.shape[2]
+    out = np.empty((nz, ny, nx, Co))
+    bb = None if b is None else np.ascontiguousarray(b, np.float64)
+    _cnn_lib().orc_conv3(nx, ny, nz, Ci, Co, _p(x), _p(W), _p(bb), _p(out))
+    return out
+
+
+def conv3_dgrad(gout, W, Ci):
+    gout = np.ascontiguousarray(gout, np.float64)
+    nz, ny, nx, Co = gout.shape
+    gin = np.empty((nz, ny, nx, Ci))
+    _cnn_lib().orc_conv3_dgrad(nx, ny, nz, Ci, Co, _p(gout), _p(np.ascontiguousarray(W, np.float64)), _p(gin))
+    return gin
+
+
+def conv3_wgrad(x, gout):
+    x = np.ascontiguousarray(x, np.float64)
+    gout = np.ascontiguousarray(gout, np.float64)
+    nz, ny, nx, Ci = x.shape
+    Co = gout.shape[3]
+    gW = np.empty((27, Ci, Co))
+    gb = np.empty(Co)
+    _cnn_lib().orc_conv3_wgrad(nx, ny, nz, Ci, Co, _p(x), _p(gout), _p(gW), _p(gb))
+    return gW, gb
+
+
+def cnn_forward(x, fields, params, s_out, round_act=True):
+    """x: (nz, ny, nx, 9); fields: (nz, ny, nx, 3); params: flat [W1, b1, ..., W6, b6].
+    Returns pred (nz, ny, nx, 3) and the (z, a) buffers for cnn_backward."""
+    x = np.ascontiguousarray(x, np.float64)
+    nz, ny, nx, _ = x.shape
+    V = nx * ny * nz
+    f = np.ascontiguousarray(fields, np.float64)
+    P = np.ascontiguousarray(params, np.float64)
+    z = np.zeros(6 * V * 24)
+    a = np.zeros(5 * V * 24)
+    pred = np.empty((nz, ny, nx, 3))
+    _cnn_lib().orc_cnn_forward(nx, ny, nz, _p(x), _p(f), _p(P), C.c_double(s_out), int(round_act), _p(z), _p(a),
+                               _p(pred))
+    return pred, (z, a)
+
+
+def cnn_loss(pred, target, mask):
+    pred = np.ascontiguousarray(pred, np.float64)
+    target = np.ascontiguousarray(target, np.float64)
+    m = np.ascontiguousarray(mask, np.uint8)
+    g = np.empty_like(pred)
+    L = _cnn_lib().orc_cnn_loss(C.c_int64(m.size), _p(pred), _p(target), _p(m), _p(g))
+    return float(L), g
+
+
+def cnn_backward(x, params, s_out, cache, gpred):
+    x = np.ascontiguousarray(x, np.float64)
+    nz, ny, nx, _ = x.shape
+    z, a = cache
+    P = np.ascontiguousarray(params, np.float64)
+    g = np.empty_like(P)
+    _cnn_lib().orc_cnn_backward(nx, ny, nz, _p(x), _p(P), C.c_double(s_out), _p(z), _p(a),
+                                _p(np.ascontiguousarray(gpred, np.float64)), _p(g))
+    return g
+
+
+def adam(p, g, m, v, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on p, m, v (float64 arrays)."""
+    _cnn_lib().orc_adam(C.c_int64(p.size), _p(p), _p(np.ascontiguousarray(g, np.float64)), _p(m), _p(v),
+                        C.c_double(lr), C.c_double(b1), C.c_double(b2), C.c_double(eps), int(t))
+
+
+def cnn_param_slices():
+    """(W, b) slices of each layer in the flat parameter vector."""
+    out, o = [], 0
+    for l in range(6):
+        ci, co = CNN_CHANNELS[l], CNN_CHANNELS[l + 1]
+        out.append((slice(o, o + 27 * ci * co), slice(o + 27 * ci * co, o + 27 * ci * co + co), ci, co))
+        o += 27 * ci * co + co
+    return out
