@@ -234,6 +234,44 @@ mpm_status mpm_tune_tile(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, i
 mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys, mpm_opts *opt,
                            int32_t *out_variant, const char *cache_path, void *stream);
 
+/*
+ * Learned warm start (a small 3D CNN; the paper has no network).  Six 3x3x3
+ * convolutions with zero padding and biases, channels 9 -> 24 -> 24 -> 24 ->
+ * 24 -> 24 -> 3, erf-GELU after layers 1-5, output pred = c^n + s_out * z6
+ * (the next-step fields of 3 species).  bf16 weights and activations, FP32
+ * accumulation on the tensor cores; the FP32 master parameters are flat,
+ * per layer W[27][Ci][Co] (tap (dx+1) + 3(dy+1) + 9(dz+1)) followed by b[Co].
+ * Features (9 channels, stored as 16 bf16 per voxel, x fastest): c^n of the 3
+ * species (scaled 1, 1, 20), one-hot medium/tumour, per-cell rates (uptake of
+ * species 0 and 1, source of species 2; scaled 10), mask.
+ */
+typedef struct mpm_cnn mpm_cnn;
+/* max_voxels: largest batch * box volume the network will see. */
+mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **cnn, int64_t max_voxels);
+mpm_status mpm_cnn_destroy(mpm_ctx *ctx, mpm_cnn *cnn);
+/* Host FP32 parameters (n must equal the network's count); resets Adam. */
+mpm_status mpm_cnn_set_params(mpm_ctx *ctx, mpm_cnn *cnn, const float *host_params, int64_t n, float s_out,
+                              void *stream);
+/* which 0: parameters, 1: the gradient of the last mpm_cnn_train_step; to host. */
+mpm_status mpm_cnn_get_params(mpm_ctx *ctx, const mpm_cnn *cnn, int32_t which, float *host_out, int64_t n,
+                              void *stream);
+/* Features of a box of the lattice (device): x [V][16] bf16, fields [V][3] FP32 (c^n). */
+mpm_status mpm_cnn_features(mpm_ctx *ctx, const mpm_lattice *lat, const mpm_params *prm, const mpm_box *box,
+                            void *x_bf16, float *fields, void *stream);
+/* pred [batch*V][3] FP32 = network(x) for batch crops of dims (device pointers). */
+mpm_status mpm_cnn_forward(mpm_ctx *ctx, mpm_cnn *cnn, const void *x_bf16, const float *fields, const int32_t dims[3],
+                           int32_t batch, float *pred, void *stream);
+/* Forward, masked mean-squared error against target [batch*V][3] (mask = feature 8), backward; with
+ * apply = 1 one Adam step (lr; beta 0.9, 0.999; eps 1e-8).  *loss_out (nullable) gets the loss
+ * (synchronises `stream`). */
+mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *cnn, const void *x_bf16, const float *fields,
+                              const float *target, const int32_t dims[3], int32_t batch, float lr, int32_t apply,
+                              double *loss_out, void *stream);
+/* Initial guess for a solve: features of sub's box from lat, the network, and the prediction
+ * written into the iterate of every species on the in-mask voxels (then solve with x0_given = 1). */
+mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
+                         const mpm_params *prm, void *stream);
+
 /* Copy `what` of species s from the subgrid into dst (device, box-dense,
  * nx*ny*nz elements of the export type).  Voxels of tiles that hold no
  * in-mask voxel are not stored: they receive 0 (1 for DIAG).  Queued on

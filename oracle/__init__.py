@@ -300,14 +300,14 @@ def cnn_loss(pred, target, mask):
     return float(L), g
 
 
-def cnn_backward(x, params, s_out, cache, gpred):
+def cnn_backward(x, params, s_out, cache, gpred, round_grad=False):
     x = np.ascontiguousarray(x, np.float64)
     nz, ny, nx, _ = x.shape
     z, a = cache
     P = np.ascontiguousarray(params, np.float64)
     g = np.empty_like(P)
     _cnn_lib().orc_cnn_backward(nx, ny, nz, _p(x), _p(P), C.c_double(s_out), _p(z), _p(a),
-                                _p(np.ascontiguousarray(gpred, np.float64)), _p(g))
+                                _p(np.ascontiguousarray(gpred, np.float64)), int(round_grad), _p(g))
     return g
 
 

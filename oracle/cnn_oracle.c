@@ -190,17 +190,21 @@ double orc_cnn_loss(int64_t V, const double *pred, const double *target, const u
 /*
  * Backward pass from gpred = dLoss/dpred through the stored z and a (the
  * bf16 rounding of the activations is treated as the identity, a
- * straight-through derivative, as on the GPU).  Writes grads (flat, like the
- * parameters).
+ * straight-through derivative, as on the GPU).  round_grad: round each
+ * layer's dLoss/dz to bf16 where the GPU stores it (off for the
+ * finite-difference pins).  Writes grads (flat, like the parameters).
  */
 void orc_cnn_backward(int nx, int ny, int nz, const double *x, const double *params, double s_out,
-                      const double *z, const double *a, const double *gpred, double *grads)
+                      const double *z, const double *a, const double *gpred, int round_grad, double *grads)
 {
     const int64_t V = (int64_t)nx * ny * nz;
     double *g = (double *)malloc(sizeof(double) * (size_t)(V * 24));
     double *gp = (double *)malloc(sizeof(double) * (size_t)(V * 24));
     for (int64_t v = 0; v < V; ++v)
-        for (int s = 0; s < 3; ++s) g[v * 3 + s] = s_out * gpred[v * 3 + s];     /* dL/dz6 */
+        for (int s = 0; s < 3; ++s) {
+            const double gz = s_out * gpred[v * 3 + s];                           /* dL/dz6 */
+            g[v * 3 + s] = round_grad ? orc_bf16(gz) : gz;
+        }
     for (int l = NL - 1; l >= 0; --l) {
         const int Ci = kCh[l], Co = kCh[l + 1];
         const double *W = params + woff(l);
@@ -210,7 +214,10 @@ void orc_cnn_backward(int nx, int ny, int nz, const double *x, const double *par
         if (l == 0) break;
         orc_conv3_dgrad(nx, ny, nz, Ci, Co, g, W, gp);                             /* dL/da_{l} */
         const double *zp = z + (int64_t)(l - 1) * V * 24;
-        for (int64_t i = 0; i < V * Ci; ++i) g[i] = gp[i] * orc_gelu_grad(zp[i]); /* dL/dz_{l} */
+        for (int64_t i = 0; i < V * Ci; ++i) {                                     /* dL/dz_{l} */
+            const double gz = gp[i] * orc_gelu_grad(zp[i]);
+            g[i] = round_grad ? orc_bf16(gz) : gz;
+        }
     }
     free(g);
     free(gp);

@@ -662,6 +662,34 @@ mpm_status mpm_import_impl(mpm_ctx *ctx, mpm_subgrid *sub, int32_t s, const doub
     return MPM_OK;
 }
 
+// prediction [V][3] (float, box-dense) -> iterate of every species on in-mask voxels
+__global__ void __launch_bounds__(kBlock) k_import_pred(const float *__restrict__ pred, BoxGeo g,
+                                                        const int32_t *__restrict__ tile_index,
+                                                        const uint8_t *__restrict__ flags, int nspecies,
+                                                        double *x0, double *x1, double *x2, int64_t nbox)
+{
+    for (int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x; d < nbox; d += (int64_t)gridDim.x * kBlock) {
+        const int64_t e = dense_to_elem(d, g, tile_index);
+        if (e < 0 || !(flags[e] & F_MASK)) continue;
+        x0[e] = (double)pred[d * 3 + 0];
+        if (nspecies > 1) x1[e] = (double)pred[d * 3 + 1];
+        if (nspecies > 2) x2[e] = (double)pred[d * 3 + 2];
+    }
+}
+
+mpm_status mpm_import_pred_impl(mpm_ctx *ctx, mpm_subgrid *sub, const float *pred, cudaStream_t st)
+{
+    const int32_t dims[3] = {sub->n[0], sub->n[1], sub->n[2]};
+    BoxGeo g = make_geo(sub, dims);
+    const int64_t nbox = (int64_t)sub->n[0] * sub->n[1] * sub->n[2];
+    k_import_pred<<<grid_for(nbox, ctx->num_sms, 8), kBlock, 0, st>>>(pred, g, sub->tile_index, sub->flags,
+                                                                      sub->nspecies, sub->x[0], sub->x[1], sub->x[2], nbox);
+    ctx->launches += 1;
+    MPM_CU(cudaGetLastError());
+    sub->x_fresh = false;
+    return MPM_OK;
+}
+
 // used by mpm_apply_impl (assemble.cu)
 mpm_status mpm_dense_to_elems(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, double *dst, cudaStream_t st)
 {

@@ -28,7 +28,8 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_subgrid_info", "mpm_box_extract", "mpm_assemble_coeffs", "mpm_solve_step", "mpm_solve_batch",
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
-           "mpm_tune_tile", "mpm_tune_solver"]
+           "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
+           "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess"]
 
 
 class mpm_box(C.Structure):
@@ -100,6 +101,15 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                             C.POINTER(mpm_box), P, P],
         "mpm_assemble_coeffs": [P, P, C.POINTER(mpm_params), P],
         "mpm_subgrid_refresh": [P, P, C.POINTER(mpm_lattice), P],
+        "mpm_cnn_create": [P, C.POINTER(P), C.c_int64],
+        "mpm_cnn_destroy": [P, P],
+        "mpm_cnn_set_params": [P, P, P, C.c_int64, C.c_float, P],
+        "mpm_cnn_get_params": [P, P, C.c_int32, P, C.c_int64, P],
+        "mpm_cnn_features": [P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_box), P, P, P],
+        "mpm_cnn_forward": [P, P, P, P, C.POINTER(C.c_int32), C.c_int32, P, P],
+        "mpm_cnn_train_step": [P, P, P, P, P, C.POINTER(C.c_int32), C.c_int32, C.c_float, C.c_int32,
+                               C.POINTER(C.c_double), P],
+        "mpm_cnn_guess": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), P],
         "mpm_tune_tile": [P, C.POINTER(mpm_lattice), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), P],
         "mpm_tune_solver": [P, C.POINTER(P), C.c_int32, C.POINTER(mpm_opts), C.POINTER(C.c_int32), C.c_char_p, P],
         "mpm_batch_step": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.POINTER(C.POINTER(mpm_params)),
@@ -426,3 +436,86 @@ class StepSolver:
         rep = self.sub.mpm_solve_step(opts, scatter_to=self.lat, stream=stream, allow=allow)
         rep["box"] = box
         return rep
+
+
+CNN_CHANNELS = (9, 24, 24, 24, 24, 24, 3)
+CNN_NPARAMS = sum(27 * a * b + b for a, b in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]))
+
+
+def cnn_init_params(seed: int = 0, last_scale: float = 0.1):
+    """He-style random initial parameters (float32, flat layout of include/mpm.h)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for l, (ci, co) in enumerate(zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:])):
+        w = rng.normal(size=27 * ci * co) * np.sqrt(2.0 / (27 * ci))
+        if l == 5:
+            w *= last_scale
+        out += [w, np.zeros(co)]
+    return np.concatenate(out).astype(np.float32)
+
+
+class CNN:
+    """The learned warm start's network (mpm_cnn_*); tensors are torch CUDA tensors."""
+
+    def __init__(self, ctx: Context, max_voxels: int, params=None, s_out: float = 0.01):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        ctx._check(ctx.lib.mpm_cnn_create(ctx.ptr, C.byref(self.h), int(max_voxels)), "mpm_cnn_create")
+        self.set_params(cnn_init_params() if params is None else params, s_out)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.mpm_cnn_destroy(self.ctx.ptr, self.h)
+            self.h = C.c_void_p()
+
+    def set_params(self, params, s_out: float = 0.01, stream=None):
+        p = np.ascontiguousarray(params, np.float32)
+        self.s_out = s_out
+        self.ctx._check(self.ctx.lib.mpm_cnn_set_params(self.ctx.ptr, self.h, C.c_void_p(p.ctypes.data), p.size,
+                                                        C.c_float(s_out), _stream_ptr(stream)), "mpm_cnn_set_params")
+
+    def get(self, which: int = 0, stream=None) -> np.ndarray:
+        out = np.empty(CNN_NPARAMS, np.float32)
+        self.ctx._check(self.ctx.lib.mpm_cnn_get_params(self.ctx.ptr, self.h, which, C.c_void_p(out.ctypes.data),
+                                                        out.size, _stream_ptr(stream)), "mpm_cnn_get_params")
+        return out
+
+    def features(self, lat: DeviceLattice, prm: DeviceParams, box, stream=None):
+        import torch
+        (lo, hi) = box
+        n = [h - l for l, h in zip(lo, hi)]
+        V = n[0] * n[1] * n[2]
+        x = torch.empty((V, 16), dtype=torch.bfloat16, device="cuda")
+        f = torch.empty((V, 3), dtype=torch.float32, device="cuda")
+        b = mpm_box()
+        b.lo[:] = lo
+        b.hi[:] = hi
+        ls = lat.struct()
+        self.ctx._check(self.ctx.lib.mpm_cnn_features(self.ctx.ptr, C.byref(ls), C.byref(prm.struct), C.byref(b),
+                                                      C.c_void_p(x.data_ptr()), C.c_void_p(f.data_ptr()),
+                                                      _stream_ptr(stream)), "mpm_cnn_features")
+        return x, f
+
+    def forward(self, x, fields, dims, batch: int = 1, stream=None):
+        import torch
+        pred = torch.empty((x.shape[0], 3), dtype=torch.float32, device="cuda")
+        d = (C.c_int32 * 3)(*dims)
+        self.ctx._check(self.ctx.lib.mpm_cnn_forward(self.ctx.ptr, self.h, C.c_void_p(x.data_ptr()),
+                                                     C.c_void_p(fields.data_ptr()), d, batch,
+                                                     C.c_void_p(pred.data_ptr()), _stream_ptr(stream)),
+                        "mpm_cnn_forward")
+        return pred
+
+    def train_step(self, x, fields, target, dims, batch: int, lr: float, apply: bool = True, stream=None) -> float:
+        d = (C.c_int32 * 3)(*dims)
+        loss = C.c_double(0)
+        self.ctx._check(self.ctx.lib.mpm_cnn_train_step(self.ctx.ptr, self.h, C.c_void_p(x.data_ptr()),
+                                                        C.c_void_p(fields.data_ptr()), C.c_void_p(target.data_ptr()),
+                                                        d, batch, C.c_float(lr), int(apply), C.byref(loss),
+                                                        _stream_ptr(stream)), "mpm_cnn_train_step")
+        return float(loss.value)
+
+    def guess(self, sub: Subgrid, lat: DeviceLattice, prm: DeviceParams, stream=None):
+        ls = lat.struct()
+        self.ctx._check(self.ctx.lib.mpm_cnn_guess(self.ctx.ptr, self.h, sub.h, C.byref(ls), C.byref(prm.struct),
+                                                   _stream_ptr(stream)), "mpm_cnn_guess")
