@@ -244,6 +244,25 @@ def bench_growth512(mpm, W, ctx, stream, flush, sample=range(0, 201, 20)):
             "box_voxels_first_last": [boxes[0], boxes[-1]]}
 
 
+def bench_learned(mpm, ctx, samples=20000):
+    """The learned warm start: train the network on `samples` pairs generated by the
+    FP64 solver on the GPU (32^3 sphere-like lattices), then time the 32^3 sphere
+    workload to 1e-6 with x0 = c^n and with x0 = the network's prediction, FP64
+    and FP32-in-FP64 (device time includes features + forward)."""
+    from paper_2505_03067_gb300 import learned
+    cnn, hist = learned.train(ctx, samples=samples)
+    out = {"train_seconds": hist["seconds"], "samples": hist["samples"],
+           "loss_first_last": [float(np.mean(hist["loss"][:5])), float(np.mean(hist["loss"][-20:]))]}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        ev = learned.evaluate_sphere32(ctx, cnn, rtol=1e-6, precision=prec)
+        for k in ("plain", "learned"):
+            e = ev[k]
+            out[f"{name}_{k}"] = {"value": 32 ** 3 / (e["ms_per_step"] / 1e3), "ms_per_step": e["ms_per_step"],
+                                  "iters_per_step": e["iters_per_step"], "max_rel_res": e["max_rel_res"]}
+    cnn.close()
+    return out
+
+
 def cpu_baseline(wl, nsteps):
     import oracle
     lat = wl.lattice.copy()
@@ -300,6 +319,7 @@ def main():
     ap.add_argument("--restart", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="skip the 32^3, 64-patch and 512x384x384 lines")
+    ap.add_argument("--train-samples", type=int, default=20000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -451,7 +471,8 @@ def main():
     if not args.no_workloads:
         line["workloads"] = {"sphere32": bench_sphere32(mpm, W, ctx, stream, flush, args.warmup),
                              "patches64": bench_patches64(mpm, W, ctx, stream, flush, args.warmup),
-                             "growth512": bench_growth512(mpm, W, ctx, stream, flush)}
+                             "growth512": bench_growth512(mpm, W, ctx, stream, flush),
+                             "learned_sphere32": bench_learned(mpm, ctx, args.train_samples)}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_steps)
     if rank == 0:

@@ -1,0 +1,95 @@
+"""Training and use of the learned warm start (marshalling only: every step runs
+in the library's kernels through the C ABI).
+
+Training data come from the library's own FP64 solver, generated on the GPU
+while training: B trajectories of 32^3 lattices (workloads.sphere_training_case)
+are advanced one implicit-Euler step at a time; each step gives a pair
+(features of c^n, c^{n+1}) per trajectory, and the batch of B pairs makes one
+Adam step (mpm_cnn_train_step).  A trajectory restarts from a new random
+lattice after `traj_len` steps.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import mpm
+from . import workloads as W
+
+
+class _Traj:
+    def __init__(self, ctx, rng, n):
+        self.wl = W.sphere_training_case(rng, n)
+        self.lat = mpm.DeviceLattice(self.wl.lattice)
+        self.prm = mpm.DeviceParams(self.wl.params)
+        self.solver = mpm.StepSolver(ctx, self.lat, self.prm, self.wl.margin)
+        self.age = 0
+
+
+def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, lr: float = 2e-3,
+          traj_len: int = 12, seed: int = 4, params=None, log_every: int = 0):
+    """Train a fresh network (or `params`) on `samples` pairs; returns (CNN, history)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    V = n ** 3
+    cnn = mpm.CNN(ctx, batch * V, mpm.cnn_init_params(seed) if params is None else params, s_out=0.01)
+    x = torch.empty((batch * V, 16), dtype=torch.bfloat16, device="cuda")
+    f = torch.empty((batch * V, 3), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((batch * V, 3), dtype=torch.float32, device="cuda")
+    trajs = [_Traj(ctx, rng, n) for _ in range(batch)]
+    opts = mpm.make_opts(rtol=1e-10, restart=16, maxit=500)
+    box = ((0, 0, 0), (n, n, n))
+    hist = []
+    t0 = time.time()
+    nsteps = max(1, samples // batch)
+    for it in range(nsteps):
+        for b, tr in enumerate(trajs):
+            if tr.age >= traj_len:
+                trajs[b] = tr = _Traj(ctx, rng, n)
+            xb, fb = cnn.features(tr.lat, tr.prm, box)
+            x[b * V:(b + 1) * V] = xb
+            f[b * V:(b + 1) * V] = fb
+            tr.solver.step(opts)
+            _, fa = cnn.features(tr.lat, tr.prm, box)
+            tgt[b * V:(b + 1) * V] = fa
+            tr.age += 1
+        # cosine decay of the learning rate
+        lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * it / nsteps))
+        loss = cnn.train_step(x, f, tgt, (n, n, n), batch, lr_t)
+        hist.append(loss)
+        if log_every and it % log_every == 0:
+            print(f"step {it}/{nsteps} loss {loss:.3e} ({time.time() - t0:.1f} s)", flush=True)
+    return cnn, {"loss": hist, "seconds": time.time() - t0, "samples": nsteps * batch}
+
+
+def evaluate_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, precision: int = 0, steps: int = 10):
+    """The 32^3 sphere workload advanced `steps` steps twice from the same state:
+    with x0 = c^n and with x0 = the network's prediction.  Returns Arnoldi steps
+    and device time (solve, plus the network's forward for the learned form)."""
+    import torch
+    wl = W.sphere32()
+    out = {}
+    for learned in (False, True):
+        lat = mpm.DeviceLattice(wl.lattice)
+        prm = mpm.DeviceParams(wl.params)
+        sub = ctx.subgrid_create()
+        its, ms, res = [], 0.0, []
+        stream = torch.cuda.current_stream()
+        for _ in range(steps):
+            sub.mpm_box_extract(lat, 1, wl.margin)
+            sub.mpm_assemble_coeffs(prm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if learned:
+                cnn.guess(sub, lat, prm)
+            rep = sub.mpm_solve_step(mpm.make_opts(rtol=rtol, restart=30, maxit=500, precision=precision,
+                                                   inner_rtol=1e-6, x0_given=int(learned)), scatter_to=lat)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            its.append(rep["iters"][0])
+            res.append(rep["res"][0] / rep["bnorm"][0])
+        out["learned" if learned else "plain"] = {"iters_per_step": float(np.mean(its)), "ms_per_step": ms / steps,
+                                                 "max_rel_res": float(max(res)), "final": lat.fields_numpy()}
+    return out

@@ -327,3 +327,42 @@ def random_case(seed: int, dims, nspecies: int = 3, p_mask: float = 0.8, p_tumou
     df = rng.uniform(0.2, 3.0, size=shape) if dfac else None
     return Workload(f"random{seed}", Lattice(cell_id, mask, fields, df), params, margin=1,
                     steps=2, rtol=1e-12, restart=30)
+
+
+# --------------------------------------------------------------------------- learned warm start
+def sphere_training_case(rng, n: int = 32, three_species=None) -> Workload:
+    """A 32^3 training lattice around the 32^3 sphere workload: every voxel in the
+    domain, a solid tumour sphere of radius U[4, 12] at a random centre split into
+    ~50 Voronoi cells; species 0 as in the sphere workload (D = 1, dt = 0.1,
+    c0 = c_b = 1) with per-cell uptake U[0.01, 0.1].  Species 1-2 either carry the
+    shell workload's nutrient and cytokine (D 0.5 / 0.2, per-cell uptake /
+    secretion U[0.01, 0.1], cytokine decay 0.01, c_b 1 / 0) or are absent (all
+    zero), as in the single-species workload."""
+    dims = (n, n, n)
+    x, y, z = _grid(dims)
+    r = rng.uniform(4.0, 12.0)
+    c = rng.uniform(r * 0.5, n - 1 - r * 0.5, size=3)
+    tumour = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= r * r
+    if not tumour.any():
+        tumour[int(c[2]), int(c[1]), int(c[0])] = True
+    pts = np.stack([x[tumour], y[tumour], z[tumour]], axis=1)
+    ncells = max(1, min(50, len(pts)))
+    seeds = pts[rng.choice(len(pts), ncells, replace=False)] + rng.uniform(-0.5, 0.5, (ncells, 3))
+    cell_id = np.zeros(x.shape, np.int32)
+    cell_id[tumour] = _voronoi_labels(pts, seeds) + 1
+    three = bool(rng.random() < 0.5) if three_species is None else three_species
+    k = np.zeros((3, ncells + 1))
+    q = np.zeros((3, ncells + 1))
+    k[0, 1:] = rng.uniform(0.01, 0.1, ncells)
+    fields = np.zeros((3,) + x.shape)
+    fields[0] = 1.0
+    if three:
+        k[1, 1:] = rng.uniform(0.01, 0.1, ncells)
+        q[2, 1:] = rng.uniform(0.01, 0.1, ncells)
+        fields[1] = 1.0
+        params = Params(3, 0.1, 1.0, np.array([1.0, 0.5, 0.2]), np.array([0.0, 0.0, 0.01]),
+                        np.array([1.0, 1.0, 0.0]), k, q)
+    else:
+        params = Params(3, 0.1, 1.0, np.array([1.0, 1.0, 1.0]), np.zeros(3), np.array([1.0, 0.0, 0.0]), k, q)
+    return Workload("sphere_train", Lattice(cell_id, np.ones(x.shape, np.uint8), fields), params, margin=n,
+                    steps=10, rtol=1e-10, restart=30)

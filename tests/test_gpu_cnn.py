@@ -147,3 +147,32 @@ def test_guess_seeds_the_solver(M):
     ref = wl.lattice.copy()
     oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-12)
     assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+
+
+def test_trained_network_gain_on_sphere32(M):
+    """Train on GPU-generated pairs (the FP64 solver's own steps), then measure on
+    the 32^3 sphere workload what the network's guess gains over x0 = c^n: the
+    initial relative residual of the first step (a solve with rtol = 1 stops at
+    its first residual and reports it) and the Arnoldi steps to 1e-6 over 10
+    steps.  Both answers meet the tolerance and agree within its bound."""
+    from paper_2505_03067_gb300 import learned
+    ctx = M.Context()
+    cnn, hist = learned.train(ctx, samples=4000)
+    assert np.mean(hist["loss"][-20:]) < 0.2 * np.mean(hist["loss"][:5])
+    wl = W.sphere32()
+    r0 = {}
+    for use in (False, True):
+        lat = M.DeviceLattice(wl.lattice)
+        prm = M.DeviceParams(wl.params)
+        sub = ctx.subgrid_create()
+        sub.mpm_box_extract(lat, 1, wl.margin)
+        sub.mpm_assemble_coeffs(prm)
+        if use:
+            cnn.guess(sub, lat, prm)
+        rep = sub.mpm_solve_step(M.make_opts(rtol=1.0, restart=8, maxit=10, x0_given=int(use)))
+        r0[use] = rep["res"][0] / rep["bnorm"][0]
+    assert r0[True] < 0.5 * r0[False], r0
+    ev = learned.evaluate_sphere32(ctx, cnn, rtol=1e-6)
+    assert ev["learned"]["max_rel_res"] <= 1e-6 and ev["plain"]["max_rel_res"] <= 1e-6
+    assert ev["learned"]["iters_per_step"] <= ev["plain"]["iters_per_step"]
+    assert np.max(np.abs(ev["learned"]["final"] - ev["plain"]["final"])) <= 10 * 2e-6 * np.sqrt(32 ** 3)
