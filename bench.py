@@ -48,22 +48,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def solver_bytes(rep, NE, bT):
-    """Algorithmic bytes of one solver launch (per stored element, summed over
-    species): R = x, b, diag64 (8 each) + flags (1) + write u0 (bT);
-    P1_j = flags + u_j, diag, u_0..u_{j-1} + write w = 1 + (j+3) bT;
-    P2_j = read w, u_0..u_j + write w = (j+3) bT;  U = read V (k bT) + x r/w (16)."""
+def solver_bytes(rep, NM, NE, bT):
+    """Algorithmic bytes of one solver launch: per in-mask voxel (the unknowns,
+    NM) and species, R = x, b, diag64 (8 each) + write u0 (bT);
+    P1_j = u_j, diag, u_0..u_{j-1} + write w = (j+3) bT; P2_j = read w,
+    u_0..u_j + write w = (j+3) bT; U = read V (k bT) + x r/w (16); plus the
+    flag byte of every stored element (NE) in every pass."""
     tot = 0
     for s in range(len(rep["iters"])):
         it, C, js = rep["iters"][s], rep["cycles"][s], rep["jsum"][s]
-        R = 25 + bT
-        P = it * (1 + 6 * bT) + 2 * bT * js
+        R = 24 + bT
+        P = it * 6 * bT + 2 * bT * js
         U = 16 * C + bT * it
-        tot += NE * (R * (C + 1) + P + U)
+        passes = (C + 1) + 2 * it + C
+        tot += NM * (R * (C + 1) + P + U) + NE * passes
     return tot
 
 
-def solver_fp64_ops(rep, NE, fp32):
+def solver_fp64_ops(rep, NM, fp32):
     """FP64 instructions of one solver launch per the same pass structure (an FMA,
     an add or a convert each count one): R 10; FP64 path P1_j 8 + (j+1), P2_j
     (j+2), U k; FP32 path U 1 per cycle (x += d)."""
@@ -75,7 +77,7 @@ def solver_fp64_ops(rep, NE, fp32):
             r += 2 * C
         else:
             r += it * 8 + (js + it) + (js + 2 * it) + it
-        tot += NE * r
+        tot += NM * r
     return tot
 
 
@@ -151,6 +153,20 @@ def _traffic_record(kernel_key):
     return rec
 
 
+def replica_value(units: float, ms_local: float, world: int, device=None):
+    """Whole-job throughput of N independent replicas: every rank processed
+    `units` in `ms_local` ms; the job time is the maximum over ranks (one
+    all-reduce, measurement only) and value = world * units / t_max."""
+    t = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units / (t / 1e3), t
+
+
 def _timed(fn, stream, flush, i):
     import torch
     flush.fill_(i & 255)
@@ -198,17 +214,20 @@ def bench_patches64(mpm, W, ctx, stream, flush, warmup, steps=50):
         bs.step(opts)
     for l, f in zip(lats, inits):
         l.fields.copy_(f)
-    ms, units = 0.0, 0
+    ms, units, imb = 0.0, 0, []
     for i in range(steps):
         (st, reps), t = _timed(lambda: bs.step(opts), stream, flush, i)
         assert st == mpm.OK
         ms += t
         units += sum(r["mask_voxels"] * 3 for r in reps)
+        imb.append(ctx.imbalance())
     stored = sum(r["stored_voxels"] for r in reps)
     return {"value": units / (ms / 1e3), "unit": "species-voxel-steps/s", "ms_per_step": ms / steps, "steps": steps,
             "systems": 3 * len(ps), "tuned": {"restart": m, "variant": var,
                                               "tiles": sorted(set(map(tuple, bs.tiles)))},
             "graph": bs.graph_active(), "stored_voxels": stored,
+            "imbalance_f": {"mean": float(np.mean(imb)), "max": float(np.max(imb)),
+                            "definition": "t_max/<t> - 1 over the CTA teams of the persistent launch"},
             "mask_voxels": sum(r["mask_voxels"] for r in reps)}
 
 
@@ -380,19 +399,16 @@ def main():
         if sampler:
             clocks = sampler.stop()
         ms = sum(a.elapsed_time(b) for a, b in evs)
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
         units = sum(r["mask_voxels"] * S for r in reps)
+        _, ms_max = replica_value(units, ms, world, "cuda")
         for r in reps:
             assert r["status_code"] == mpm.OK, r
             assert all(res <= wl.rtol * b for res, b in zip(r["res"], r["bnorm"])), r
         bT = 4 if extra["precision"] else 8
-        kbytes = sum(solver_bytes(r, r["stored_voxels"], bT) for r in reps)
-        kops = sum(solver_fp64_ops(r, r["stored_voxels"], bool(extra["precision"])) for r in reps)
+        kbytes = sum(solver_bytes(r, r["mask_voxels"], r["stored_voxels"], bT) for r in reps)
+        kops = sum(solver_fp64_ops(r, r["mask_voxels"], bool(extra["precision"])) for r in reps)
         kms = sum(r["solve_ms"] for r in reps)
-        results[name] = {"value": world * units / (ms_max / 1e3), "ms_per_step": ms_max / args.steps,
+        results[name] = {"value": replica_value(units, ms_max, 1)[0] * world, "ms_per_step": ms_max / args.steps,
                          "kernel_ms_per_step": kms / args.steps, "kernel_bytes": kbytes, "kernel_fp64_ops": kops,
                          "kernel_ms": kms, "launches": launches,
                          "iters_per_step": [sum(r["iters"][s] for r in reps) / len(reps) for s in range(S)],
@@ -433,10 +449,8 @@ def main():
         e2e_ms += e0.elapsed_time(e1)
         h_fields.copy_(h_out)
         units += rep["mask_voxels"] * S
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * units / (float(t.item()) / 1e3), "unit": "species-voxel-steps/s",
+    e2e_value, _ = replica_value(units, e2e_ms, world, "cuda")
+    e2e = {"value": e2e_value, "unit": "species-voxel-steps/s",
            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
            "note": "lattice (cell ids, mask, 3 FP64 fields) copied in from pinned host memory and the fields "
                    "copied out every step, through the same C-ABI calls"}

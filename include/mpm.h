@@ -97,7 +97,10 @@ typedef struct {
     int64_t box_voxels;                 /* nx*ny*nz */
     int64_t mask_voxels;                /* in-mask voxels of the box (the unknowns) */
     int64_t stored_voxels;              /* voxels of the active tiles held in HBM */
-    double solve_ms;                    /* device time of the solve kernel (CUDA events) */
+    double solve_ms;                    /* device time of the solve kernel (CUDA events; for
+                                           mpm_batch_step: of the whole step) */
+    double item_ms[MPM_MAX_SPECIES];    /* device time of each species' work item inside the
+                                           persistent launch */
 } mpm_report;
 
 /* Shape of an extracted subgrid (host struct filled by mpm_subgrid_info). */
@@ -138,7 +141,7 @@ mpm_status mpm_subgrid_info(const mpm_subgrid *sub, mpm_subgrid_desc *out);
  * of all voxels with cell_id > 0, widened by `margin` and clamped,
  *     lo = max(0, min - margin),  hi = min(L, max + margin + 1),
  * split the box into tiles of dims `tile` (powers of two, product 32..1024;
- * NULL = 8x4x4), keep the tiles that hold an in-mask voxel, and copy the mask,
+ * NULL = 4x4x4), keep the tiles that hold an in-mask voxel, and copy the mask,
  * cell ids, optional dfac and the species fields c^n of those tiles into `sub`
  * (tile-major, library-owned).  `nspecies` fields are gathered.
  * Writes the box to *out_box.  Synchronises `stream` once (the compacted
@@ -314,6 +317,10 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
  * partial sums (REDUCE) and in the FP64 least-squares/state updates (SERIAL). */
 #define MPM_COUNTER_LAUNCHES 1
 #define MPM_COUNTER_BATCH_GRAPH 10   /* 1 if the last mpm_batch_step replays a captured graph */
+/* Load imbalance of the last solve, the paper's f = t_max / <t> - 1 (Sec. 2.5)
+ * with the CTA teams of the persistent launch in place of the cores, in parts
+ * per million. */
+#define MPM_COUNTER_IMBALANCE_PPM 11
 #define MPM_COUNTER_PHASE_WORK_NS 2
 #define MPM_COUNTER_PHASE_WAIT_NS 3
 #define MPM_COUNTER_PHASE_REDUCE_NS 4

@@ -264,6 +264,7 @@ mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)
     if (!ctx || !value) return MPM_ERR_ARG;
     if (key == MPM_COUNTER_LAUNCHES) { *value = ctx->launches; return MPM_OK; }
     if (key == MPM_COUNTER_BATCH_GRAPH) { *value = mpm_batch_graph_active((mpm_ctx *)ctx); return MPM_OK; }
+    if (key == MPM_COUNTER_IMBALANCE_PPM) { *value = (int64_t)(ctx->last_imbalance * 1e6 + 0.5); return MPM_OK; }
     if (key == MPM_COUNTER_PHASE_WORK_NS) {
         *value = (int64_t)(ctx->h_prof[4] + ctx->h_prof[5] + ctx->h_prof[6] + ctx->h_prof[7]);
         return MPM_OK;

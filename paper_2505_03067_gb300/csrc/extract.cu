@@ -365,7 +365,7 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
     if (lat->dims[0] < 1 || lat->dims[1] < 1 || lat->dims[2] < 1 || L >= (int64_t)1 << 31)
         return mpm_fail(ctx, MPM_ERR_ARG, "extract: lattice dims out of range");
     if (margin < 0) return mpm_fail(ctx, MPM_ERR_ARG, "extract: negative margin");
-    int32_t lt[3] = {3, 2, 2};   // 8x4x4: the least padding on thin shells among the shapes measured
+    int32_t lt[3] = {2, 2, 2};   // 4x4x4: the fastest solve on thin shells among the shapes measured
     if (tile) {
         for (int d = 0; d < 3; ++d) {
             const int32_t t = tile[d];

@@ -62,6 +62,7 @@ struct SysReport {
     int32_t jsum[kMaxSpecies];
     double res[kMaxSpecies];
     double bnorm[kMaxSpecies];
+    unsigned long long t_ns;    // device time of the item (its team's CTA 0)
 };
 
 struct TeamDesc {
@@ -270,6 +271,7 @@ struct mpm_ctx {
     size_t tune_cap = 0;
     unsigned long long *d_prof = nullptr;
     unsigned long long h_prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double last_imbalance = 0.0; // t_max / <t> - 1 over the teams of the last solve
     // test hooks
     uint64_t timeout_ns = 2000000000ull;
     int32_t skip_block = -1;
@@ -279,7 +281,7 @@ struct mpm_subgrid {
     bool extracted = false, assembled = false;
     uint64_t gen = 0;                // bumped by every extraction (buffers may move)
     int32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, n[3] = {0, 0, 0};
-    int32_t lt[3] = {3, 2, 2};
+    int32_t lt[3] = {2, 2, 2};
     int32_t nt[3] = {0, 0, 0};
     int32_t ldims[3] = {0, 0, 0};    // lattice dims of the extraction
     int32_t ntiles = 0, nact = 0;

@@ -212,13 +212,23 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
     const bool var = S.dfac != nullptr;
     const double *x = S.x[0];
     float fR = 0.0f, fB = 0.0f;
+    // the flag bytes are read-only during the solve: fetch the next iteration's
+    // one iteration ahead, so the neighbour loads never wait for them
+    uint32_t fn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? __ldg(S.flags + e0 + u * es) : 0u;
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
         double xv[U], ns[U], bv[U], dg[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            f[u] = fn[u];
+            const uint32_t en = e + (U + u) * es;
+            fn[u] = en < NE ? __ldg(S.flags + en) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
-            f[u] = eu < NE ? __ldg(S.flags + eu) : 0u;
             if (eu < NE) nbr_elems(S.nbr, eu, f[u], S.ltx, S.lty, S.ltz, q[u]);
         }
 #pragma unroll
@@ -269,13 +279,21 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, double sig
     const T *V = (const T *)S.V[0];
     const T *uj = V + (int64_t)j * vs;
     const T *dgp = diag_of<T>(S, 0);
+    uint32_t fn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? __ldg(S.flags + e0 + u * es) : 0u;
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
         T xj[U], ns[U], dg[U], w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            f[u] = fn[u];
+            const uint32_t en = e + (U + u) * es;
+            fn[u] = en < NE ? __ldg(S.flags + en) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
-            f[u] = eu < NE ? __ldg(S.flags + eu) : 0u;
             if (eu < NE) nbr_elems(S.nbr, eu, f[u], S.ltx, S.lty, S.ltz, q[u]);
         }
 #pragma unroll
@@ -404,6 +422,7 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
 
     for (int si = td.sys_begin; si < td.sys_end; ++si) {
         const int sys_id = A.sys_order[si];
+        const uint64_t t_item0 = globaltimer_ns();
         if (tid == 0) sm.sys = A.sys[sys_id];
         __syncthreads();
         const SysDev &S = sm.sys;
@@ -579,6 +598,7 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
             R->jsum[tid] = p.jsum;
             R->res[tid] = p.beta;
             R->bnorm[tid] = p.bnorm;
+            R->t_ns = globaltimer_ns() - t_item0;
         }
         __syncthreads();
     }
@@ -893,8 +913,19 @@ static mpm_status finish_solve(mpm_ctx *ctx, const SolvePlan &P, mpm_subgrid *co
         R[i].stored_voxels = sub->NE;
         R[i].solve_ms = ms;
     }
+    // the paper's load imbalance f = t_max / <t> - 1 (Sec. 2.5), over CTA teams
+    {
+        std::vector<double> tt(P.nteam, 0.0);
+        for (int t = 0; t < P.nteam; ++t)
+            for (int k = P.teams[t].sys_begin; k < P.teams[t].sys_end; ++k) tt[t] += (double)hrep[P.order[k]].t_ns;
+        double mx = 0.0, mean = 0.0;
+        for (double v : tt) { mx = std::max(mx, v); mean += v; }
+        mean /= std::max(1, P.nteam);
+        ctx->last_imbalance = mean > 0.0 ? mx / mean - 1.0 : 0.0;
+    }
     for (int it = 0; it < P.nitem; ++it) {
         const int i = P.item_sys[it], s = P.item_sp[it];
+        R[i].item_ms[s] = (double)hrep[it].t_ns * 1e-6;
         R[i].iters[s] = hrep[it].iters[0];
         R[i].jsum[s] = hrep[it].jsum[0];
         R[i].cycles[s] = hrep[it].cycles[0];

@@ -23,7 +23,7 @@ int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant);
 
 namespace {
 
-const int32_t kTiles[][3] = {{8, 4, 4}, {8, 8, 4}, {4, 4, 4}, {8, 4, 2}, {16, 4, 2}, {8, 8, 2}, {4, 4, 2}, {16, 4, 4}};
+const int32_t kTiles[][3] = {{4, 4, 4}, {8, 4, 4}, {8, 8, 4}, {8, 4, 2}, {16, 4, 2}, {8, 8, 2}, {4, 4, 2}, {16, 4, 4}};
 const int32_t kRestarts[] = {4, 8, 16};
 
 int ilog2(int v)

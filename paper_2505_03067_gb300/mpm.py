@@ -62,14 +62,15 @@ class mpm_report(C.Structure):
                 ("status", C.c_int32 * MAX_SPECIES), ("jsum", C.c_int32 * MAX_SPECIES),
                 ("res", C.c_double * MAX_SPECIES),
                 ("bnorm", C.c_double * MAX_SPECIES), ("box_voxels", C.c_int64), ("mask_voxels", C.c_int64),
-                ("stored_voxels", C.c_int64), ("solve_ms", C.c_double)]
+                ("stored_voxels", C.c_int64), ("solve_ms", C.c_double), ("item_ms", C.c_double * MAX_SPECIES)]
 
     def as_dict(self, nspecies):
         return {"iters": list(self.iters[:nspecies]), "cycles": list(self.cycles[:nspecies]),
                 "status": list(self.status[:nspecies]), "jsum": list(self.jsum[:nspecies]),
                 "res": list(self.res[:nspecies]),
                 "bnorm": list(self.bnorm[:nspecies]), "box_voxels": self.box_voxels,
-                "mask_voxels": self.mask_voxels, "stored_voxels": self.stored_voxels, "solve_ms": self.solve_ms}
+                "mask_voxels": self.mask_voxels, "stored_voxels": self.stored_voxels, "solve_ms": self.solve_ms,
+                "item_ms": list(self.item_ms[:nspecies])}
 
 
 class mpm_subgrid_desc(C.Structure):
@@ -240,6 +241,10 @@ class Context:
 
     def launches(self) -> int:
         return self.counter(1)
+
+    def imbalance(self) -> float:
+        """The paper's load imbalance f = t_max / <t> - 1 over the CTA teams of the last solve."""
+        return self.counter(11) / 1e6
 
     def phase_times_us(self) -> dict:
         """CTA-0 time split of the last solve (needs debug_set(DEBUG_PHASE_TIMES, 1))."""

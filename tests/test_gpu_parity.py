@@ -334,3 +334,13 @@ def test_shell256_first_step_matches_oracle(M, ctx, shell256, precision):
             assert np.max(np.abs(g - r)) <= 1e-10
         else:
             assert np.linalg.norm(g - r) <= 1e-6 * np.linalg.norm(r)
+
+
+def test_four_species_il8(M, ctx):
+    """Eq. 1-4 with all four species (O2, nutrient, IL6, IL8): the same kernels with S = 4."""
+    wl = W.random_case(40, (23, 19, 17), nspecies=4)
+    ref = wl.lattice.copy()
+    oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=2000))
+    assert rep["status_code"] == M.OK and len(rep["iters"]) == 4
+    assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
