@@ -191,8 +191,11 @@ mpm_status mpm_solve_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *sca
 
 /*
  * Solve nsys independent subgrids (every species of each) in ONE persistent
- * launch: the grid is split into teams of CTAs, each team takes a list of
- * systems chosen by a longest-first partition of their sizes.  scatter_to may
+ * launch: the grid is split into teams of CTAs; a team takes either one large
+ * (system, species) pair on several CTAs or several small ones in turn on one
+ * CTA, planned to minimise the longest team's estimated time (per pass a fixed
+ * synchronisation cost plus the stored elements over the team's CTAs; the
+ * paper's load-imbalance concern, Sec. 2.5).  scatter_to may
  * be NULL or hold nsys entries (each nullable).  reps may be NULL or hold nsys.
  */
 mpm_status mpm_solve_batch(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *scatter_to,
@@ -201,9 +204,11 @@ mpm_status mpm_solve_batch(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lat
 /*
  * One implicit-Euler step of nsys extracted systems with fixed boxes (the
  * batched form): for every system refresh c^n from lats[i] (as
- * mpm_subgrid_refresh), assemble with prms[i], then solve every (system,
- * species) pair in ONE persistent launch (as mpm_solve_batch) and scatter the
- * solutions onto lats[i].  The first call captures the whole sequence in a
+ * mpm_subgrid_refresh) and assemble with prms[i], all systems in one launch;
+ * then solve every (system, species) pair in ONE persistent launch (as
+ * mpm_solve_batch) and scatter the solutions onto lats[i], again one launch.
+ * Systems that share a lattice must have disjoint boxes: the scatters of all
+ * systems run concurrently.  The first call captures the whole sequence in a
  * CUDA graph; later calls with the same subgrids (not re-extracted), lattice
  * and parameter structs and options replay it (one graph launch per step).
  * Where capture is unavailable the same sequence runs eagerly.  Synchronises

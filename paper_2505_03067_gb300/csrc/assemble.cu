@@ -9,11 +9,8 @@
 namespace mpm {
 
 struct AsmArgs {
-    int32_t nspecies, ncell, bc_box;
+    AsmCoef C;
     int32_t n[3], lt[3];
-    double dt, a;                       // a = dt / h^2
-    double D[kMaxSpecies], mu[kMaxSpecies], cbc[kMaxSpecies];
-    const double *k_cell, *q_cell;      // [nspecies][ncell]
     const uint8_t *flags;
     const int32_t *cell;
     const double *dfac;
@@ -26,17 +23,16 @@ struct AsmArgs {
     int32_t *err;
 };
 
-// For an in-mask voxel P of species s:
-//   A_PP = 1 + dt (mu_s + k_cell[s][id]) + a (sum_open D_f + 2 D_P n_dir)
-//   b_P  = c^n_P + dt q_cell[s][id] + a 2 D_P c_bc n_dir
-// n_dir = number of faces of P on the box boundary (0 with bc_box = 1).
+// Rows of the stored elements: in-mask voxels by assemble_row, every other
+// element an identity row keeping c^n (tile padding: 0).  The neighbours'
+// diffusivity factors come from the compact copy through the tile table.
 __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs A, int64_t NE)
 {
     const int ltv = A.lt[0] + A.lt[1] + A.lt[2];
     for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < NE; e += (int64_t)gridDim.x * kBlock) {
         const uint32_t f = A.flags[e];
         if (!(f & F_MASK)) {                       // padding or masked voxel: identity row
-            for (int s = 0; s < A.nspecies; ++s) {
+            for (int s = 0; s < A.C.nspecies; ++s) {
                 A.diag[s][e] = 1.0;
                 A.diag32[s][e] = 1.0f;
                 A.b[s][e] = (f & F_BOX) ? A.cn[s][e] : 0.0;
@@ -44,59 +40,41 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs A, int64_t NE)
             continue;
         }
         int32_t id = A.cell[e];
-        if (id < 0 || id >= A.ncell) {
+        if (id < 0 || id >= A.C.ncell) {
             atomicOr(A.err, 1);
             id = 0;
         }
+        const int64_t tile = e >> ltv;
+        const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
+        const uint32_t TX = 1u << A.lt[0], TY = 1u << A.lt[1], TZ = 1u << A.lt[2];
+        const uint32_t ix = v & (TX - 1), iy = (v >> A.lt[0]) & (TY - 1), iz = v >> (A.lt[0] + A.lt[1]);
         int ndir = 0;
-        if (A.bc_box == 0) {
-            const int64_t tile = e >> ltv;
-            const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
+        if (A.C.bc_box == 0) {
             const int4 tc = __ldg(reinterpret_cast<const int4 *>(A.tile_coord) + tile);
-            const int bx = (tc.x << A.lt[0]) + (int)(v & ((1u << A.lt[0]) - 1));
-            const int by = (tc.y << A.lt[1]) + (int)((v >> A.lt[0]) & ((1u << A.lt[1]) - 1));
-            const int bz = (tc.z << A.lt[2]) + (int)(v >> (A.lt[0] + A.lt[1]));
+            const int bx = (tc.x << A.lt[0]) + (int)ix;
+            const int by = (tc.y << A.lt[1]) + (int)iy;
+            const int bz = (tc.z << A.lt[2]) + (int)iz;
             ndir = (bx == 0) + (bx == A.n[0] - 1) + (by == 0) + (by == A.n[1] - 1) + (bz == 0) + (bz == A.n[2] - 1);
         }
         const double fp = A.dfac ? A.dfac[e] : 1.0;
-        // harmonic-mean face diffusivities with the neighbours' factors
-        if (A.dfac) {
-            const int64_t tile = e >> ltv;
-            const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
-            const uint32_t TX = 1u << A.lt[0], TY = 1u << A.lt[1], TZ = 1u << A.lt[2];
-            const uint32_t ix = v & (TX - 1), iy = (v >> A.lt[0]) & (TY - 1), iz = v >> (A.lt[0] + A.lt[1]);
-            int64_t q[6];
-            q[0] = ix > 0 ? e - 1 : ((int64_t)A.nbr[tile * 6 + 0] << ltv) + (v + TX - 1);
-            q[1] = ix < TX - 1 ? e + 1 : ((int64_t)A.nbr[tile * 6 + 1] << ltv) + (v - (TX - 1));
-            q[2] = iy > 0 ? e - TX : ((int64_t)A.nbr[tile * 6 + 2] << ltv) + (v + (TY - 1) * TX);
-            q[3] = iy < TY - 1 ? e + TX : ((int64_t)A.nbr[tile * 6 + 3] << ltv) + (v - (TY - 1) * TX);
-            q[4] = iz > 0 ? e - TX * TY : ((int64_t)A.nbr[tile * 6 + 4] << ltv) + (v + (TZ - 1) * TX * TY);
-            q[5] = iz < TZ - 1 ? e + TX * TY : ((int64_t)A.nbr[tile * 6 + 5] << ltv) + (v - (TZ - 1) * TX * TY);
-            for (int s = 0; s < A.nspecies; ++s) {
-                const double dp = A.D[s] * fp;
-                double acc = 0.0;
-                for (int d = 0; d < 6; ++d) {
-                    if (f & (1u << d)) {
-                        const double dq = A.D[s] * A.dfac[q[d]];
-                        acc += (dp + dq > 0.0) ? 2.0 * dp * dq / (dp + dq) : 0.0;
-                    }
-                }
-                const double kv = A.mu[s] + A.k_cell[(int64_t)s * A.ncell + id];
-                const double dg = 1.0 + A.dt * kv + A.a * (acc + 2.0 * dp * ndir);
-                A.diag[s][e] = dg;
-                A.diag32[s][e] = (float)dg;
-                A.b[s][e] = A.cn[s][e] + A.dt * A.q_cell[(int64_t)s * A.ncell + id] + A.a * 2.0 * dp * A.cbc[s] * ndir;
+        auto dq = [&](int d) -> double {
+            int64_t q;
+            switch (d) {
+            case 0: q = ix > 0 ? e - 1 : ((int64_t)A.nbr[tile * 6 + 0] << ltv) + (v + TX - 1); break;
+            case 1: q = ix < TX - 1 ? e + 1 : ((int64_t)A.nbr[tile * 6 + 1] << ltv) + (v - (TX - 1)); break;
+            case 2: q = iy > 0 ? e - TX : ((int64_t)A.nbr[tile * 6 + 2] << ltv) + (v + (TY - 1) * TX); break;
+            case 3: q = iy < TY - 1 ? e + TX : ((int64_t)A.nbr[tile * 6 + 3] << ltv) + (v - (TY - 1) * TX); break;
+            case 4: q = iz > 0 ? e - TX * TY : ((int64_t)A.nbr[tile * 6 + 4] << ltv) + (v + (TZ - 1) * TX * TY); break;
+            default: q = iz < TZ - 1 ? e + TX * TY : ((int64_t)A.nbr[tile * 6 + 5] << ltv) + (v - (TZ - 1) * TX * TY);
             }
-            continue;
-        }
-        const int nopen = __popc(f & F_OPEN);
-        for (int s = 0; s < A.nspecies; ++s) {
-            const double Ds = A.D[s];
-            const double kv = A.mu[s] + A.k_cell[(int64_t)s * A.ncell + id];
-            const double dg = 1.0 + A.dt * kv + A.a * Ds * (double)(nopen + 2 * ndir);
+            return A.dfac[q];
+        };
+        for (int s = 0; s < A.C.nspecies; ++s) {
+            double dg, b;
+            assemble_row(A.C, s, f, id, ndir, A.dfac != nullptr, fp, dq, A.cn[s][e], dg, b);
             A.diag[s][e] = dg;
             A.diag32[s][e] = (float)dg;
-            A.b[s][e] = A.cn[s][e] + A.dt * A.q_cell[(int64_t)s * A.ncell + id] + A.a * 2.0 * Ds * A.cbc[s] * ndir;
+            A.b[s][e] = b;
         }
     }
 }
@@ -118,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(SysDev S, int s, const double 
 
 using namespace mpm;
 
-mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *p, cudaStream_t st)
+mpm_status mpm_assemble_check(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_params *p)
 {
     if (!sub || !p) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: null argument");
     if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: subgrid not extracted");
@@ -128,34 +106,58 @@ mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *p
     if (p->bc_box != 0 && p->bc_box != 1) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: bc_box must be 0 or 1");
     for (int s = 0; s < p->nspecies; ++s)
         if (!(p->D[s] >= 0.0) || !(p->mu[s] >= 0.0)) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: D and mu must be >= 0");
+    return MPM_OK;
+}
+
+void mpm_asm_coef(const mpm_params *p, AsmCoef *C)
+{
+    memset(C, 0, sizeof(*C));
+    C->nspecies = p->nspecies;
+    C->ncell = p->ncell;
+    C->bc_box = p->bc_box;
+    C->dt = p->dt;
+    C->a = p->dt / (p->h * p->h);
+    for (int s = 0; s < p->nspecies; ++s) {
+        C->D[s] = p->D[s];
+        C->mu[s] = p->mu[s];
+        C->cbc[s] = p->c_bc[s];
+    }
+    C->k_cell = p->k_cell;
+    C->q_cell = p->q_cell;
+}
+
+// The scalars the solver reads from the subgrid: the uniform-D off-diagonal
+// dt D_s / h^2, and a = dt / h^2 with D_s for the harmonic-mean path.
+void mpm_set_assembled_scalars(mpm_subgrid *sub, const mpm_params *p)
+{
+    sub->a = p->dt / (p->h * p->h);
+    for (int s = 0; s < MPM_MAX_SPECIES; ++s) {
+        sub->off[s] = s < p->nspecies ? sub->a * p->D[s] : 0.0;
+        sub->Dsp[s] = s < p->nspecies ? p->D[s] : 0.0;
+    }
+}
+
+mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *p, cudaStream_t st)
+{
+    mpm_status r = mpm_assemble_check(ctx, sub, p);
+    if (r != MPM_OK) return r;
     AsmArgs A;
     memset(&A, 0, sizeof(A));
-    A.nspecies = p->nspecies;
-    A.ncell = p->ncell;
-    A.bc_box = p->bc_box;
+    mpm_asm_coef(p, &A.C);
     for (int d = 0; d < 3; ++d) { A.n[d] = sub->n[d]; A.lt[d] = sub->lt[d]; }
-    A.dt = p->dt;
-    A.a = p->dt / (p->h * p->h);
     for (int s = 0; s < p->nspecies; ++s) {
-        A.D[s] = p->D[s];
-        A.mu[s] = p->mu[s];
-        A.cbc[s] = p->c_bc[s];
         A.cn[s] = sub->cn[s];
         A.b[s] = sub->b[s];
         A.diag[s] = sub->diag[s];
         A.diag32[s] = sub->diag32[s];
-        sub->off[s] = A.a * p->D[s];
     }
-    A.k_cell = p->k_cell;
-    A.q_cell = p->q_cell;
     A.flags = sub->flags;
     A.cell = sub->cell;
     A.dfac = sub->dfac;
     A.tile_coord = sub->tile_coord;
     A.nbr = sub->nbr;
     A.err = sub->err;
-    sub->a = A.a;
-    for (int s = 0; s < MPM_MAX_SPECIES; ++s) sub->Dsp[s] = s < p->nspecies ? p->D[s] : 0.0;
+    mpm_set_assembled_scalars(sub, p);
     MPM_CU(cudaMemsetAsync(sub->err, 0, sizeof(int32_t), st));
     if (sub->NE > 0) {
         int64_t g = (sub->NE + kBlock - 1) / kBlock;

@@ -81,12 +81,6 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const int32_t *__restrict__ cel
 }
 
 // ---------------------------------------------------------------- tiles
-struct BoxGeo {
-    int32_t lo[3], n[3], nt[3];
-    int32_t lt[3];
-    uint32_t Lx, Ly;
-};
-
 // Mark tiles holding an in-mask voxel; count the in-mask voxels of the box.
 // One warp per box row (j, k).
 __global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restrict__ mask, const BoxGeo *__restrict__ gp,
@@ -192,20 +186,6 @@ __global__ void k_tile_nbr(const int32_t *__restrict__ tile_index, const int32_t
             r = tile_index[(q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]];
         nbr[6 * a + d] = r;
     }
-}
-
-// Box coordinates of element e; returns false for tile padding outside the box.
-__device__ __forceinline__ bool elem_box(int64_t e, const BoxGeo &g, const int32_t *__restrict__ tile_coord,
-                                         int &bx, int &by, int &bz)
-{
-    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
-    const int64_t tile = e >> ltv;
-    const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
-    const int4 tc = __ldg(reinterpret_cast<const int4 *>(tile_coord) + tile);
-    bx = (tc.x << g.lt[0]) + (int)(v & ((1u << g.lt[0]) - 1));
-    by = (tc.y << g.lt[1]) + (int)((v >> g.lt[0]) & ((1u << g.lt[1]) - 1));
-    bz = (tc.z << g.lt[2]) + (int)(v >> (g.lt[0] + g.lt[1]));
-    return bx < g.n[0] && by < g.n[1] && bz < g.n[2];
 }
 
 struct GatherArgs {

@@ -34,6 +34,68 @@ constexpr int kMaxM = MPM_MAX_RESTART;
 constexpr int kKStride = kMaxM + 2;           // partial slots per species
 constexpr int kKMax = kMaxSpecies * kKStride; // partial slots per block
 
+// Box geometry of an extraction: box origin and dims in the lattice, tile
+// counts and log2 tile dims, lattice row and plane strides.
+struct BoxGeo {
+    int32_t lo[3], n[3], nt[3];
+    int32_t lt[3];
+    uint32_t Lx, Ly;
+};
+
+// Box coordinates of element e; returns false for tile padding outside the box.
+__device__ __forceinline__ bool elem_box(int64_t e, const BoxGeo &g, const int32_t *__restrict__ tile_coord,
+                                         int &bx, int &by, int &bz)
+{
+    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
+    const int64_t tile = e >> ltv;
+    const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
+    const int4 tc = __ldg(reinterpret_cast<const int4 *>(tile_coord) + tile);
+    bx = (tc.x << g.lt[0]) + (int)(v & ((1u << g.lt[0]) - 1));
+    by = (tc.y << g.lt[1]) + (int)((v >> g.lt[0]) & ((1u << g.lt[1]) - 1));
+    bz = (tc.z << g.lt[2]) + (int)(v >> (g.lt[0] + g.lt[1]));
+    return bx < g.n[0] && by < g.n[1] && bz < g.n[2];
+}
+
+BoxGeo make_geo(const ::mpm_subgrid *sub, const int32_t dims[3]);   // extract.cu
+
+// Coefficients of the implicit-Euler system (Eq. 1-4) shared by every row.
+struct AsmCoef {
+    int32_t nspecies, ncell, bc_box;
+    double dt, a;                       // a = dt / h^2
+    double D[kMaxSpecies], mu[kMaxSpecies], cbc[kMaxSpecies];
+    const double *k_cell, *q_cell;      // [nspecies][ncell]
+};
+
+// Diagonal and right-hand side of the row of an in-mask voxel P, species s:
+//   A_PP = 1 + dt (mu_s + k_cell[s][id]) + a (sum_open D_f + 2 D_P n_dir)
+//   b_P  = c^n_P + dt q_cell[s][id] + a 2 D_P c_bc n_dir
+// with D_f the harmonic mean of D_s fp and D_s dq(d) over the open faces d when
+// the diffusivity varies (has_dfac), else D_s on every open face.  n_dir counts
+// the faces of P on the box boundary (Dirichlet c_bc there).  dq(d) returns the
+// diffusivity factor of the neighbour across face d.
+template <typename DQ>
+__device__ __forceinline__ void assemble_row(const AsmCoef &C, int s, uint32_t f, int id, int ndir, bool has_dfac,
+                                             double fp, DQ dq, double cn, double &dg, double &b)
+{
+    const double kv = C.mu[s] + C.k_cell[(int64_t)s * C.ncell + id];
+    if (has_dfac) {
+        const double dp = C.D[s] * fp;
+        double acc = 0.0;
+        for (int d = 0; d < 6; ++d) {
+            if (f & (1u << d)) {
+                const double dn = C.D[s] * dq(d);
+                acc += (dp + dn > 0.0) ? 2.0 * dp * dn / (dp + dn) : 0.0;
+            }
+        }
+        dg = 1.0 + C.dt * kv + C.a * (acc + 2.0 * dp * ndir);
+        b = cn + C.dt * C.q_cell[(int64_t)s * C.ncell + id] + C.a * 2.0 * dp * C.cbc[s] * ndir;
+    } else {
+        const double Ds = C.D[s];
+        dg = 1.0 + C.dt * kv + C.a * Ds * (double)(__popc(f & F_OPEN) + 2 * ndir);
+        b = cn + C.dt * C.q_cell[(int64_t)s * C.ncell + id] + C.a * 2.0 * Ds * C.cbc[s] * ndir;
+    }
+}
+
 // Device view of one extracted, assembled box system.
 struct SysDev {
     int64_t NE;                 // stored elements = nact * TV
@@ -332,8 +394,20 @@ mpm_status mpm_grow(mpm_ctx *ctx, void **p, size_t *cap, size_t need, const char
 mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
                             const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st);
 mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, cudaStream_t st);
+mpm_status mpm_assemble_check(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_params *p);
+void mpm_asm_coef(const mpm_params *p, mpm::AsmCoef *C);
+void mpm_set_assembled_scalars(mpm_subgrid *sub, const mpm_params *p);
 mpm_status mpm_scatter_impl(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st);
 mpm_status mpm_refresh_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st);
+// batched forms of refresh + assemble and of scatter (batch.cu): one launch for
+// all systems; the descriptors live in device memory the caller owns
+size_t mpm_batch_desc_bytes(int32_t nsys);
+mpm_status mpm_batch_prep_check(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                                const mpm_params *const *prms, int32_t nsys);
+mpm_status mpm_batch_desc_fill(mpm_subgrid *const *subs, const mpm_lattice *const *lats,
+                               const mpm_params *const *prms, int32_t nsys, void *host, int64_t *nblocks);
+mpm_status mpm_batch_prep_launch(mpm_ctx *ctx, const void *d_desc, int32_t nsys, int64_t nblocks, cudaStream_t st);
+mpm_status mpm_batch_scatter_launch(mpm_ctx *ctx, const void *d_desc, int32_t nsys, int64_t nblocks, cudaStream_t st);
 mpm_status mpm_count_active_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, const int32_t lt[3],
                                  int64_t *nact, int64_t *mask_voxels, cudaStream_t st);
 mpm_status mpm_export_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst,

@@ -24,6 +24,7 @@
 // the Arnoldi passes run in FP32; R stays FP64 and U adds the FP32 correction
 // to the FP64 iterate, so each restart is one step of iterative refinement
 // whose inner cycle stops at max(tol, inner_rtol * ||r||).
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -685,8 +686,52 @@ int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Longest-first partition of systems onto teams (the batched form).  Each team
-// gets a share of the grid proportional to its work, at least one CTA.
+// Team plan of the batched form, with the paper's load-imbalance concern
+// (Sec. 2.5) in mind.  A pass of item i on a team of c CTAs costs about
+// kPassFixed + work_i / c element-equivalents: the fixed part is the per-pass
+// synchronisation (team barrier, reduction, least squares; the constant was
+// set by timing the 64-patch batch), the rest the streaming work.  For a
+// candidate makespan T, items whose cost on one CTA fits in T are packed
+// first-fit-decreasing onto single-CTA teams of capacity T; larger items get
+// ceil(work / (T - fixed)) CTAs of their own.  The smallest T that fits in G
+// CTAs is kept (binary search), and the spare CTAs go to the largest teams.
+static constexpr double kPassFixed = 3000.0;
+
+static bool try_plan(const std::vector<double> &work, const std::vector<int> &idx, int G, double T,
+                     std::vector<std::vector<int>> &members, std::vector<int> &nbk)
+{
+    members.clear();
+    nbk.clear();
+    std::vector<double> load;
+    int used = 0;
+    for (int i : idx) {
+        const double one = kPassFixed + work[i];
+        if (one > T) {
+            if (T <= kPassFixed * 1.05) return false;
+            const int c = (int)std::ceil(work[i] / (T - kPassFixed));
+            members.push_back({i});
+            nbk.push_back(c);
+            load.push_back(-1.0);
+            used += c;
+        } else {
+            int t = -1;
+            for (size_t k = 0; k < load.size(); ++k)
+                if (load[k] >= 0.0 && load[k] + one <= T) { t = (int)k; break; }
+            if (t < 0) {
+                members.push_back({});
+                nbk.push_back(1);
+                load.push_back(0.0);
+                t = (int)load.size() - 1;
+                used += 1;
+            }
+            members[t].push_back(i);
+            load[t] += one;
+        }
+        if (used > G) return false;
+    }
+    return used <= G;
+}
+
 static void plan_teams(const std::vector<double> &work, int G, std::vector<TeamDesc> &teams,
                        std::vector<int32_t> &order, std::vector<int32_t> &block_team)
 {
@@ -694,40 +739,46 @@ static void plan_teams(const std::vector<double> &work, int G, std::vector<TeamD
     std::vector<int> idx(nsys);
     for (int i = 0; i < nsys; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
-    double total = 0.0;
-    for (double w : work) total += w;
-    const int nteam = std::max(1, std::min(nsys, G));
-    std::vector<std::vector<int>> members(nteam);
-    std::vector<double> load(nteam, 0.0);
-    for (int i : idx) {           // LPT: next-largest system onto the least-loaded team
-        int best = 0;
-        for (int t = 1; t < nteam; ++t) if (load[t] < load[best]) best = t;
-        members[best].push_back(i);
-        load[best] += work[i];
-    }
-    // CTAs proportional to load (largest remainder), at least one each
-    std::vector<int> nbk(nteam, 1);
-    int left = G - nteam;
-    if (left > 0 && total > 0) {
-        std::vector<std::pair<double, int>> rem;
-        int given = 0;
-        for (int t = 0; t < nteam; ++t) {
-            const double ideal = load[t] / total * left;
-            const int fl = (int)ideal;
-            nbk[t] += fl;
-            given += fl;
-            rem.push_back({ideal - fl, t});
+    std::vector<std::vector<int>> members;
+    std::vector<int> nbk;
+    if (nsys == 1) {
+        members = {{0}};
+        nbk = {G};
+    } else {
+        double hi = 1.0;   // everything on one CTA
+        for (int i = 0; i < nsys; ++i) hi += kPassFixed + work[i];
+        double lo = kPassFixed * 1.05;
+        for (int it = 0; it < 60; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            std::vector<std::vector<int>> m2;
+            std::vector<int> n2;
+            if (try_plan(work, idx, G, mid, m2, n2)) hi = mid;
+            else lo = mid;
         }
-        std::stable_sort(rem.begin(), rem.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
-            return a.first > b.first;
-        });
-        for (int r = 0; r < left - given && r < (int)rem.size(); ++r) nbk[rem[r].second] += 1;
+        if (!try_plan(work, idx, G, hi, members, nbk)) {   // cannot happen for G >= 1; keep a valid plan
+            members = {idx};
+            nbk = {G};
+        }
+        int used = 0;
+        for (int c : nbk) used += c;
+        // spare CTAs to the teams with the most work per CTA
+        while (used < G) {
+            int best = 0;
+            double bw = -1.0;
+            for (size_t t = 0; t < members.size(); ++t) {
+                double w = 0.0;
+                for (int i : members[t]) w += work[i];
+                if (w / nbk[t] > bw) { bw = w / nbk[t]; best = (int)t; }
+            }
+            nbk[best] += 1;
+            ++used;
+        }
     }
     teams.clear();
     order.clear();
     block_team.clear();
     int fb = 0;
-    for (int t = 0; t < nteam; ++t) {
+    for (size_t t = 0; t < members.size(); ++t) {
         TeamDesc d;
         d.first_block = fb;
         d.nblocks = nbk[t];
@@ -735,7 +786,7 @@ static void plan_teams(const std::vector<double> &work, int G, std::vector<TeamD
         for (int i : members[t]) order.push_back(i);
         d.sys_end = (int32_t)order.size();
         teams.push_back(d);
-        for (int b = 0; b < nbk[t]; ++b) block_team.push_back(t);
+        for (int b = 0; b < nbk[t]; ++b) block_team.push_back((int32_t)t);
         fb += nbk[t];
     }
 }
@@ -1017,6 +1068,10 @@ struct BatchGraph {
     int32_t *d_abort = nullptr;
     int64_t graph_launches = 0;    // kernels in the captured graph
     SolvePlan plan;
+    std::vector<char> h_desc;      // batched preparation / scatter descriptors
+    char *d_desc = nullptr;
+    size_t desc_cap = 0;
+    int64_t prep_blocks = 0;
 };
 
 static void batch_key(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
@@ -1048,6 +1103,7 @@ void mpm_batch_graph_free(mpm_ctx *ctx)
     cudaFree(B->d_args);
     cudaFree(B->d_bar);
     cudaFree(B->d_abort);
+    cudaFree(B->d_desc);
     delete B;
     ctx->batch_graph = nullptr;
 }
@@ -1062,6 +1118,8 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
     for (int i = 0; i < nsys; ++i)
         if (!subs[i] || !lats[i] || !prms[i] || !subs[i]->extracted)
             return mpm_fail(ctx, MPM_ERR_ARG, "batch_step: null or unextracted system");
+    r = mpm_batch_prep_check(ctx, subs, lats, prms, nsys);
+    if (r != MPM_OK) return r;
     if (!ctx->batch_graph) ctx->batch_graph = new BatchGraph();
     BatchGraph *B = (BatchGraph *)ctx->batch_graph;
     std::vector<unsigned char> key;
@@ -1072,12 +1130,15 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
         if (B->exec) cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
         B->valid = false;
-        for (int i = 0; i < nsys; ++i) {
-            r = mpm_refresh_impl(ctx, subs[i], lats[i], st);
-            if (r != MPM_OK) return r;
-            r = mpm_assemble_impl(ctx, subs[i], prms[i], st);
-            if (r != MPM_OK) return r;
-        }
+        const size_t dbytes = mpm_batch_desc_bytes(nsys);
+        B->h_desc.assign(dbytes, 0);
+        mpm_batch_desc_fill(subs, lats, prms, nsys, B->h_desc.data(), &B->prep_blocks);
+        r = mpm_grow(ctx, (void **)&B->d_desc, &B->desc_cap, dbytes, "batch preparation descriptors");
+        if (r != MPM_OK) return r;
+        MPM_CU(cudaMemcpyAsync(B->d_desc, B->h_desc.data(), dbytes, cudaMemcpyHostToDevice, st));
+        r = mpm_batch_prep_launch(ctx, B->d_desc, nsys, B->prep_blocks, st);
+        if (r != MPM_OK) return r;
+        for (int i = 0; i < nsys; ++i) { subs[i]->assembled = true; subs[i]->x_fresh = true; }
         B->plan = SolvePlan();
         r = plan_solve(ctx, subs, nsys, opt, false, st, B->plan);
         if (r != MPM_OK) return r;
@@ -1103,12 +1164,9 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
             const int64_t launches0 = ctx->launches;
             bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                for (int i = 0; i < nsys && ok; ++i) {
-                    ok = mpm_refresh_impl(ctx, subs[i], lats[i], cs) == MPM_OK &&
-                         mpm_assemble_impl(ctx, subs[i], prms[i], cs) == MPM_OK;
-                }
+                ok = mpm_batch_prep_launch(ctx, B->d_desc, nsys, B->prep_blocks, cs) == MPM_OK;
                 ok = ok && enqueue_solve(ctx, B->plan, B->d_args, B->d_bar, B->d_abort, nullptr, cs) == MPM_OK;
-                for (int i = 0; i < nsys && ok; ++i) ok = mpm_scatter_impl(ctx, subs[i], lats[i], cs) == MPM_OK;
+                ok = ok && mpm_batch_scatter_launch(ctx, B->d_desc, nsys, B->prep_blocks, cs) == MPM_OK;
                 const cudaError_t ec = cudaStreamEndCapture(cs, &g);
                 ok = ok && ec == cudaSuccess && g != nullptr;
             }
@@ -1136,19 +1194,13 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
         ctx->launches += B->graph_launches;
     } else {
         // eager form of the same sequence (graph unavailable or phase timing on)
-        for (int i = 0; i < nsys; ++i) {
-            r = mpm_refresh_impl(ctx, subs[i], lats[i], st);
-            if (r != MPM_OK) return r;
-            r = mpm_assemble_impl(ctx, subs[i], prms[i], st);
-            if (r != MPM_OK) return r;
-        }
+        r = mpm_batch_prep_launch(ctx, B->d_desc, nsys, B->prep_blocks, st);
+        if (r != MPM_OK) return r;
         if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
         r = enqueue_solve(ctx, P, B->d_args, B->d_bar, B->d_abort, ctx->phase_prof ? ctx->d_prof : nullptr, st);
         if (r != MPM_OK) return r;
-        for (int i = 0; i < nsys; ++i) {
-            r = mpm_scatter_impl(ctx, subs[i], lats[i], st);
-            if (r != MPM_OK) return r;
-        }
+        r = mpm_batch_scatter_launch(ctx, B->d_desc, nsys, B->prep_blocks, st);
+        if (r != MPM_OK) return r;
     }
     MPM_CU(cudaEventRecord(ctx->ev1, st));
     SysReport *hrep = (SysReport *)(hs + P.o_rep);

@@ -94,3 +94,45 @@ def test_refresh_equals_re_extract(M):
     sub2.mpm_box_extract(lat, 3, wl.margin)
     for s in range(3):
         assert np.array_equal(x_ref[s], sub2.mpm_subgrid_export(M.EXPORT_X, s).cpu().numpy())
+
+
+@pytest.mark.parametrize("dfac,bc_box", [(False, 0), (True, 0), (True, 1)])
+def test_batched_preparation_equals_per_system_assembly(M, dfac, bc_box):
+    """The one-launch refresh + assembly of every system of a batched step gives,
+    element for element, the rows, c^n and flags of the per-system refresh and
+    assembly (uniform and harmonic-mean diffusivity, both box conditions)."""
+    shapes = [((9, 7, 5), 3), ((21, 13, 11), 2), ((33, 17, 25), 3), ((5, 5, 5), 1), ((40, 9, 12), 4)]
+    wls = [W.random_case(40 + i, dims, nspecies=ns, dfac=dfac) for i, (dims, ns) in enumerate(shapes)]
+    ctx = M.Context()
+    lats = [M.DeviceLattice(w.lattice) for w in wls]
+    prms = [M.DeviceParams(w.params, bc_box=bc_box) for w in wls]
+    bs = M.BatchStepper(ctx, lats, prms, [w.margin for w in wls], tile=(4, 4, 2))
+    st, reps = bs.step(M.make_opts(rtol=1e-10, restart=8, maxit=500))
+    assert st == M.OK
+    for w, sub_b in zip(wls, bs.subs):
+        lat1 = M.DeviceLattice(w.lattice)
+        sub = ctx.subgrid_create()
+        sub.mpm_box_extract(lat1, w.params.nspecies, w.margin, (4, 4, 2))
+        sub.mpm_assemble_coeffs(M.DeviceParams(w.params, bc_box=bc_box))
+        for what in (M.EXPORT_FLAGS, M.EXPORT_CELL):
+            assert np.array_equal(sub_b.mpm_subgrid_export(what, 0).cpu().numpy(),
+                                  sub.mpm_subgrid_export(what, 0).cpu().numpy())
+        for s in range(w.params.nspecies):
+            for what in (M.EXPORT_RHS, M.EXPORT_DIAG):
+                assert np.array_equal(sub_b.mpm_subgrid_export(what, s).cpu().numpy(),
+                                      sub.mpm_subgrid_export(what, s).cpu().numpy())
+
+
+def test_batch_step_flags_only_the_system_with_a_bad_cell_id(M):
+    ctx = M.Context()
+    ps = [W.random_case(50 + i, (16, 12, 10), nspecies=2) for i in range(3)]
+    bad = ps[1].lattice.cell_id.copy()
+    idx = np.flatnonzero((ps[1].lattice.mask > 0).ravel() & (bad.ravel() > 0))[0]
+    bad.reshape(-1)[idx] = ps[1].params.ncell + 3
+    ps[1].lattice.cell_id = bad
+    lats = [M.DeviceLattice(p.lattice) for p in ps]
+    prms = [M.DeviceParams(p.params) for p in ps]
+    bs = M.BatchStepper(ctx, lats, prms, [p.margin for p in ps])
+    st, reps = bs.step(M.make_opts(rtol=1e-10, restart=8, maxit=500), allow=(M.ERR_NOCONV, M.ERR_ARG))
+    assert st == M.ERR_ARG
+    assert [set(r["status"]) for r in reps] == [{M.OK}, {M.ERR_ARG}, {M.OK}]
