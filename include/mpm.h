@@ -219,6 +219,36 @@ mpm_status mpm_batch_step(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
                           void *stream);
 
 /*
+ * One implicit-Euler step of every species on a lattice, device-resident:
+ * the whole path of Sec. 2.3-2.4 with Eq. 1-4 solved by restarted GMRES --
+ * bounding box of the tumour voxels grown by `margin`, tile compaction, the
+ * gather of c^n, mask and cell ids with the assembly, the persistent solve
+ * and the scatter onto the pleural mask -- with no host round trip between
+ * the stages.  The subgrid's buffers are sized for the whole lattice (every
+ * box fits), so the box and the element count pass from kernel to kernel in
+ * device memory; the host learns them, with the report, once the step is
+ * done.  The first call, and any call whose lattice or parameter struct,
+ * options, margin or tile differ, captures the stages in a CUDA graph;
+ * later calls replay it (one graph launch and one synchronisation of
+ * `stream` per step).  The solver grid follows the previous step's element
+ * count (re-planned when it moves by more than 25%).
+ *   sub     : a subgrid of ctx; after the call it holds this step's extraction
+ *             (exports, mpm_apply_operator and mpm_solve_step work on it).
+ *   tile    : as in mpm_box_extract (NULL: 4x4x4).
+ *   opt     : as in mpm_solve_step; x0_given must be 0 (the step starts at c^n).
+ *   rep     : nullable; filled as by mpm_solve_step.
+ *   out_box : nullable; the box of this step.
+ * Returns MPM_ERR_EMPTY (lattice unchanged, no extraction held) when no voxel
+ * has cell_id > 0, MPM_ERR_TIMEOUT (lattice unchanged) when a bounded
+ * inter-CTA wait expired, otherwise the status of mpm_solve_step.
+ * Device memory per subgrid: about (5 + 36 S) bytes per lattice voxel for the
+ * element buffers plus (m + 1) S 4 (FP32 Krylov) or 8 (FP64) bytes per voxel
+ * for the Krylov bases (S species, m the restart length), padded to tiles.
+ */
+mpm_status mpm_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
+                    const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, void *stream);
+
+/*
  * Autotuner, tile shape: among the candidate shapes 8x4x4, 8x8x4, 4x4x4,
  * 8x4x2, 16x4x2, 8x8x2, 4x4x2, 16x4x4 pick the one whose active tiles store
  * the fewest voxels for this lattice's box (ties: the larger tile), counted

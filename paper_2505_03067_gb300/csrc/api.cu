@@ -52,6 +52,7 @@ mpm_status mpm_grow(mpm_ctx *ctx, void **p, size_t *cap, size_t need, const char
 
 static void free_sub_buffers(mpm_ctx *ctx, mpm_subgrid *sub)
 {
+    mpm_step_free(ctx, sub);
     void **bufs[3] = {&sub->geo, &sub->elem, &sub->krylov};
     size_t *caps[3] = {&sub->geo_bytes, &sub->elem_bytes, &sub->krylov_bytes};
     for (int i = 0; i < 3; ++i) {
@@ -205,6 +206,14 @@ mpm_status mpm_batch_step(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
     if (!ctx) return MPM_ERR_ARG;
     ctx->err.clear();
     return mpm_batch_step_impl(ctx, subs, lats, prms, nsys, opt, reps, (cudaStream_t)stream);
+}
+
+mpm_status mpm_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
+                    const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_step_impl(ctx, sub, lat, prm, margin, tile, opt, rep, out_box, (cudaStream_t)stream);
 }
 
 mpm_status mpm_subgrid_export(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst, void *stream)

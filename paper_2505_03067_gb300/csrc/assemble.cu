@@ -101,6 +101,13 @@ mpm_status mpm_assemble_check(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_pa
     if (!sub || !p) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: null argument");
     if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: subgrid not extracted");
     if (p->nspecies != sub->nspecies) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: nspecies differs from the extract");
+    return mpm_params_check(ctx, p);
+}
+
+mpm_status mpm_params_check(mpm_ctx *ctx, const mpm_params *p)
+{
+    if (!p) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: null parameters");
+    if (p->nspecies < 1 || p->nspecies > MPM_MAX_SPECIES) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: nspecies out of range");
     if (p->ncell < 1 || !p->k_cell || !p->q_cell) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: empty rate tables");
     if (!(p->dt > 0.0) || !(p->h > 0.0)) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: dt and h must be > 0");
     if (p->bc_box != 0 && p->bc_box != 1) return mpm_fail(ctx, MPM_ERR_ARG, "assemble: bc_box must be 0 or 1");

@@ -13,17 +13,6 @@ namespace mpm {
 // int32 lattice (4 B/voxel): 16-byte loads, four in flight per thread; the
 // coordinate arithmetic only runs for tumour voxels.  Per-CTA reduction, then
 // six atomics per CTA that found any tumour voxel.
-__device__ __forceinline__ void bbox_upd(uint32_t e, uint32_t Lx, uint32_t Lxy, int (&mn)[3], int (&mx)[3])
-{
-    const uint32_t k = e / Lxy;
-    const uint32_t r = e - k * Lxy;
-    const uint32_t j = r / Lx;
-    const uint32_t i = r - j * Lx;
-    mn[0] = min(mn[0], (int)i); mx[0] = max(mx[0], (int)i);
-    mn[1] = min(mn[1], (int)j); mx[1] = max(mx[1], (int)j);
-    mn[2] = min(mn[2], (int)k); mx[2] = max(mx[2], (int)k);
-}
-
 __global__ void __launch_bounds__(kBlock) k_bbox(const int32_t *__restrict__ cell, uint32_t Lx, uint32_t Lxy,
                                                  uint32_t ntot, int vec4, int32_t *__restrict__ out)
 {
@@ -83,12 +72,10 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const int32_t *__restrict__ cel
 // ---------------------------------------------------------------- tiles
 // Mark tiles holding an in-mask voxel; count the in-mask voxels of the box.
 // One warp per box row (j, k).
-__global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restrict__ mask, const BoxGeo *__restrict__ gp,
-                                                        int8_t *__restrict__ active,
-                                                        unsigned long long *__restrict__ count)
+__device__ __forceinline__ void tile_active_rows(const uint8_t *__restrict__ mask, const BoxGeo &g,
+                                                 int8_t *__restrict__ active, unsigned long long *__restrict__ count)
 {
-    const BoxGeo g = *gp;
-    if (g.n[0] <= 0) return;                  // empty lattice: no box
+    if (g.n[0] <= 0) return;                  // empty tumour set: no box
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarp = (int64_t)gridDim.x * kWarps;
@@ -109,82 +96,122 @@ __global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restric
     if (lane == 0 && cnt) atomicAdd(count, cnt);
 }
 
-// Box from the reduced bounds (Sec. 2.3): lo = max(0, min - margin),
-// hi = min(L, max + margin + 1); tile counts of the box.  n[0] = 0 marks an
-// empty tumour set.
+__global__ void __launch_bounds__(kBlock) k_tile_active(const uint8_t *__restrict__ mask, const BoxGeo *__restrict__ gp,
+                                                        int8_t *__restrict__ active,
+                                                        unsigned long long *__restrict__ count)
+{
+    const BoxGeo g = *gp;
+    tile_active_rows(mask, g, active, count);
+}
+
 __global__ void k_box_finalize(const int32_t *__restrict__ mnmx, int32_t margin, int32_t Lx, int32_t Ly, int32_t Lz,
                                int32_t lt0, int32_t lt1, int32_t lt2, BoxGeo *__restrict__ g)
 {
     if (threadIdx.x != 0) return;
-    const int32_t L[3] = {Lx, Ly, Lz};
-    const int32_t lt[3] = {lt0, lt1, lt2};
-    const bool empty = mnmx[3] < 0;
-    for (int d = 0; d < 3; ++d) {
-        const int32_t lo = max(0, mnmx[d] - margin);
-        const int32_t hi = (int32_t)min((int64_t)L[d], (int64_t)mnmx[3 + d] + margin + 1);
-        g->lo[d] = empty ? 0 : lo;
-        g->n[d] = empty ? 0 : hi - lo;
-        g->lt[d] = lt[d];
-        g->nt[d] = empty ? 0 : (hi - lo + (1 << lt[d]) - 1) >> lt[d];
-    }
-    g->Lx = (uint32_t)Lx;
-    g->Ly = (uint32_t)Ly;
+    *g = box_geo(mnmx, margin, Lx, Ly, Lz, lt0, lt1, lt2);
 }
 
-// Exclusive scan of the tile activity (one CTA): compact index per tile (-1
-// if inactive), coordinates of each active tile, and the active count.
-__global__ void __launch_bounds__(1024) k_tile_scan(const int8_t *__restrict__ active, const BoxGeo *__restrict__ gp,
+// Exclusive scan of the tile activity by one CTA of 1024 threads, 8192 tiles
+// per round: every lane reads the activity bytes of 8 tiles as one 8-byte
+// word (bytes are 0 or 1; the next round's word is loaded before this one is
+// used), warps scan their lanes' counts with shuffles, warp 0 scans the warp
+// totals.  Writes the compact index of each tile (-1 if inactive) and the
+// coordinates of each active tile in box-tile order; clear: zero the
+// activity bytes after use.  Returns the active count (every thread).
+__device__ __forceinline__ int32_t tile_scan_body(int8_t *__restrict__ active, const BoxGeo &g,
+                                                  int32_t *__restrict__ tile_index, int32_t *__restrict__ tile_coord,
+                                                  bool clear)
+{
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    const int32_t ntiles = g.n[0] > 0 ? g.nt[0] * g.nt[1] * g.nt[2] : 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    unsigned long long *aw = reinterpret_cast<unsigned long long *>(active);
+    const int32_t nxy = g.nt[0] * g.nt[1];
+    unsigned long long wn = 8 * tid < ntiles ? aw[tid] : 0ull;
+    for (int32_t base = 0; base < ntiles; base += 8192) {
+        const int32_t i0 = base + 8 * tid;
+        unsigned long long w = wn;
+        const int32_t in = i0 + 8192;
+        wn = in < ntiles ? aw[in >> 3] : 0ull;
+        if (i0 + 8 > ntiles) w &= i0 >= ntiles ? 0ull : (~0ull >> (8 * (i0 + 8 - ntiles)));
+        const int32_t c = __popcll(w & 0x0101010101010101ull);
+        int32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t t = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t v = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += v;
+            }
+            wsum[lane] = t;   // inclusive
+        }
+        __syncthreads();
+        int32_t idx = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - c;
+        if (i0 < ntiles) {
+            int32_t tx = i0 % g.nt[0], ty = (i0 / g.nt[0]) % g.nt[1], tz = i0 / nxy;
+            for (int k = 0; k < 8; ++k) {
+                const int32_t i = i0 + k;
+                if (i >= ntiles) break;
+                if ((w >> (8 * k)) & 1ull) {
+                    tile_index[i] = idx;
+                    reinterpret_cast<int4 *>(tile_coord)[idx] = make_int4(tx, ty, tz, 0);
+                    ++idx;
+                } else {
+                    tile_index[i] = -1;
+                }
+                if (++tx == g.nt[0]) {
+                    tx = 0;
+                    if (++ty == g.nt[1]) { ty = 0; ++tz; }
+                }
+            }
+            if (clear) aw[i0 >> 3] = 0ull;
+        }
+        __syncthreads();
+        if (tid == 0) carry += wsum[31];
+        __syncthreads();
+    }
+    return carry;
+}
+
+__global__ void __launch_bounds__(1024) k_tile_scan(int8_t *__restrict__ active, const BoxGeo *__restrict__ gp,
                                                     int32_t *__restrict__ tile_index,
                                                     int32_t *__restrict__ tile_coord,
                                                     unsigned long long *__restrict__ nact_out)
 {
-    __shared__ int32_t part[1024];
     const BoxGeo g = *gp;
-    const int32_t ntiles = g.n[0] > 0 ? g.nt[0] * g.nt[1] * g.nt[2] : 0;
-    const int t = threadIdx.x;
-    const int32_t chunk = (ntiles + 1023) / 1024;
-    const int32_t b = min(ntiles, t * chunk), e = min(ntiles, b + chunk);
-    int32_t c = 0;
-    for (int32_t i = b; i < e; ++i) c += active[i] ? 1 : 0;
-    part[t] = c;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {      // Hillis-Steele inclusive scan
-        const int32_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int32_t idx = part[t] - c;
-    for (int32_t i = b; i < e; ++i) {
-        if (active[i]) {
-            tile_index[i] = idx;
-            const int32_t tx = i % g.nt[0], ty = (i / g.nt[0]) % g.nt[1], tz = i / (g.nt[0] * g.nt[1]);
-            tile_coord[4 * idx + 0] = tx;
-            tile_coord[4 * idx + 1] = ty;
-            tile_coord[4 * idx + 2] = tz;
-            tile_coord[4 * idx + 3] = 0;
-            ++idx;
-        } else {
-            tile_index[i] = -1;
-        }
-    }
-    if (t == 1023) *nact_out = (unsigned long long)part[1023];
+    const int32_t n = tile_scan_body(active, g, tile_index, tile_coord, false);
+    if (threadIdx.x == 0) *nact_out = (unsigned long long)n;
 }
 
+// Neighbour table of the active tiles; the box and the active count come from
+// the device (grid-stride, so any grid covers them).
 __global__ void k_tile_nbr(const int32_t *__restrict__ tile_index, const int32_t *__restrict__ tile_coord,
-                           int32_t nact, BoxGeo g, int32_t *__restrict__ nbr)
+                           const unsigned long long *__restrict__ nactp, const BoxGeo *__restrict__ gp,
+                           int32_t *__restrict__ nbr)
 {
-    const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nact) return;
-    const int32_t c[3] = {tile_coord[4 * a], tile_coord[4 * a + 1], tile_coord[4 * a + 2]};
+    const BoxGeo g = *gp;
+    const int64_t nact = g.n[0] > 0 ? (int64_t)*nactp : 0;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nact; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c[3] = {tile_coord[4 * a], tile_coord[4 * a + 1], tile_coord[4 * a + 2]};
 #pragma unroll
-    for (int d = 0; d < 6; ++d) {
-        int32_t q[3] = {c[0], c[1], c[2]};
-        q[d >> 1] += (d & 1) ? 1 : -1;
-        int32_t r = -1;
-        if (q[0] >= 0 && q[0] < g.nt[0] && q[1] >= 0 && q[1] < g.nt[1] && q[2] >= 0 && q[2] < g.nt[2])
-            r = tile_index[(q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]];
-        nbr[6 * a + d] = r;
+        for (int d = 0; d < 6; ++d) {
+            int32_t q[3] = {c[0], c[1], c[2]};
+            q[d >> 1] += (d & 1) ? 1 : -1;
+            int32_t r = -1;
+            if (q[0] >= 0 && q[0] < g.nt[0] && q[1] >= 0 && q[1] < g.nt[1] && q[2] >= 0 && q[2] < g.nt[2])
+                r = tile_index[(q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]];
+            nbr[6 * a + d] = r;
+        }
     }
 }
 
@@ -334,27 +361,46 @@ using namespace mpm;
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
-                            const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st)
+// Lattice arguments of an extraction: pointers, species fields, dims.
+mpm_status mpm_lattice_check(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies)
 {
-    if (!lat || !sub || !lat->cell_id || !lat->mask) return mpm_fail(ctx, MPM_ERR_ARG, "extract: null argument");
+    if (!lat || !lat->cell_id || !lat->mask) return mpm_fail(ctx, MPM_ERR_ARG, "extract: null argument");
     if (nspecies < 1 || nspecies > MPM_MAX_SPECIES) return mpm_fail(ctx, MPM_ERR_ARG, "extract: nspecies out of range");
     for (int s = 0; s < nspecies; ++s)
         if (!lat->field[s]) return mpm_fail(ctx, MPM_ERR_ARG, "extract: null field pointer");
     const int64_t L = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2];
     if (lat->dims[0] < 1 || lat->dims[1] < 1 || lat->dims[2] < 1 || L >= (int64_t)1 << 31)
         return mpm_fail(ctx, MPM_ERR_ARG, "extract: lattice dims out of range");
-    if (margin < 0) return mpm_fail(ctx, MPM_ERR_ARG, "extract: negative margin");
-    int32_t lt[3] = {2, 2, 2};   // 4x4x4: the fastest solve on thin shells among the shapes measured
-    if (tile) {
-        for (int d = 0; d < 3; ++d) {
-            const int32_t t = tile[d];
-            if (t < 1 || t > 64 || (t & (t - 1))) return mpm_fail(ctx, MPM_ERR_ARG, "extract: tile dims must be powers of two <= 64");
-            lt[d] = __builtin_ctz((unsigned)t);
-        }
-        const int tv = 1 << (lt[0] + lt[1] + lt[2]);
-        if (tv < 32 || tv > 1024) return mpm_fail(ctx, MPM_ERR_ARG, "extract: tile volume must be in [32, 1024]");
+    return MPM_OK;
+}
+
+// log2 tile dims from tile (null: 4x4x4, the fastest solve on thin shells
+// among the shapes measured); powers of two <= 64, volume in [32, 1024].
+mpm_status mpm_tile_lt(mpm_ctx *ctx, const int32_t tile[3], int32_t lt[3])
+{
+    lt[0] = lt[1] = lt[2] = 2;
+    if (!tile) return MPM_OK;
+    for (int d = 0; d < 3; ++d) {
+        const int32_t t = tile[d];
+        if (t < 1 || t > 64 || (t & (t - 1))) return mpm_fail(ctx, MPM_ERR_ARG, "extract: tile dims must be powers of two <= 64");
+        lt[d] = __builtin_ctz((unsigned)t);
     }
+    const int tv = 1 << (lt[0] + lt[1] + lt[2]);
+    if (tv < 32 || tv > 1024) return mpm_fail(ctx, MPM_ERR_ARG, "extract: tile volume must be in [32, 1024]");
+    return MPM_OK;
+}
+
+mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies, int32_t margin,
+                            const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st)
+{
+    if (!sub) return mpm_fail(ctx, MPM_ERR_ARG, "extract: null argument");
+    mpm_status rc = mpm_lattice_check(ctx, lat, nspecies);
+    if (rc != MPM_OK) return rc;
+    const int64_t L = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2];
+    if (margin < 0) return mpm_fail(ctx, MPM_ERR_ARG, "extract: negative margin");
+    int32_t lt[3];
+    rc = mpm_tile_lt(ctx, tile, lt);
+    if (rc != MPM_OK) return rc;
 
     // ---- a1: bounding box of the tumour voxels
     int32_t init[6] = {INT_MAX, INT_MAX, INT_MAX, -1, -1, -1};
@@ -380,6 +426,7 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
     const size_t geo_need = align256(nt * 4) + align256(nt * 16) + align256(nt * 24) + align256(nt) + 256;
     void *const old_geo = sub->geo;
     const bool was_extracted = sub->extracted, was_assembled = sub->assembled;
+    mpm_step_invalidate(sub);   // the tile tables are shared with the device-resident step
     sub->extracted = false;   // from here on the subgrid's buffers are rewritten
     sub->assembled = false;
     mpm_status s0 = mpm_grow(ctx, &sub->geo, &sub->geo_bytes, geo_need, "tile tables");
@@ -466,7 +513,8 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
         }
     }
     if (tmp.nact > 0) {
-        k_tile_nbr<<<(tmp.nact + 127) / 128, 128, 0, st>>>(tmp.tile_index, tmp.tile_coord, tmp.nact, g, tmp.nbr);
+        k_tile_nbr<<<(tmp.nact + 127) / 128, 128, 0, st>>>(tmp.tile_index, tmp.tile_coord,
+                                                           (const unsigned long long *)(ctx->d_count + 1), d_geo, tmp.nbr);
         ctx->launches += 1;
         MPM_CU(cudaGetLastError());
         GatherArgs ga;
@@ -694,3 +742,58 @@ mpm_status mpm_elems_to_dense(mpm_ctx *ctx, const mpm_subgrid *sub, const double
     MPM_CU(cudaGetLastError());
     return MPM_OK;
 }
+
+// ---------------------------------------------------------------- device-resident step
+// Buffers of a subgrid sized for the whole lattice: every box of this lattice
+// fits, so the step never has to learn the box size on the host before it
+// launches the next stage.  Element buffers hold ceil(L/T) tiles of T voxels
+// per axis; pointers move only when a buffer grows.
+mpm_status mpm_step_buffers(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, int32_t nspecies, const int32_t lt[3])
+{
+    const int64_t ntl = (((int64_t)lat->dims[0] + (1 << lt[0]) - 1) >> lt[0]) *
+                        (((int64_t)lat->dims[1] + (1 << lt[1]) - 1) >> lt[1]) *
+                        (((int64_t)lat->dims[2] + (1 << lt[2]) - 1) >> lt[2]);
+    const size_t nt = (size_t)ntl;
+    const size_t NE = nt << (lt[0] + lt[1] + lt[2]);
+    const bool has_dfac = lat->dfac != nullptr;
+    const size_t geo_need = align256(nt * 4) + align256(nt * 16) + align256(nt * 24) + align256(nt) + 256;
+    size_t need = align256(NE) + align256(NE * 4) + (has_dfac ? align256(NE * 8) : 0);
+    need += (size_t)nspecies * (4 * align256(NE * 8) + align256(NE * 4));
+    sub->extracted = false;
+    sub->assembled = false;
+    mpm_status r = mpm_grow(ctx, &sub->geo, &sub->geo_bytes, geo_need, "tile tables");
+    if (r != MPM_OK) return r;
+    r = mpm_grow(ctx, &sub->elem, &sub->elem_bytes, need, "element buffers");
+    if (r != MPM_OK) return r;
+    char *p = (char *)sub->geo;
+    sub->tile_index = (int32_t *)p; p += align256(nt * 4);
+    sub->tile_coord = (int32_t *)p; p += align256(nt * 16);
+    sub->nbr = (int32_t *)p; p += align256(nt * 24);
+    sub->active = (int8_t *)p; p += align256(nt);
+    sub->err = (int32_t *)p;
+    p = (char *)sub->elem;
+    sub->flags = (uint8_t *)p; p += align256(NE);
+    sub->cell = (int32_t *)p; p += align256(NE * 4);
+    sub->dfac = nullptr;
+    if (has_dfac) { sub->dfac = (double *)p; p += align256(NE * 8); }
+    for (int s = 0; s < MPM_MAX_SPECIES; ++s) {
+        sub->x[s] = sub->cn[s] = sub->b[s] = sub->diag[s] = nullptr;
+        sub->diag32[s] = nullptr;
+    }
+    for (int s = 0; s < nspecies; ++s) {
+        sub->x[s] = (double *)p; p += align256(NE * 8);
+        sub->cn[s] = (double *)p; p += align256(NE * 8);
+        sub->b[s] = (double *)p; p += align256(NE * 8);
+        sub->diag[s] = (double *)p; p += align256(NE * 8);
+        sub->diag32[s] = (float *)p; p += align256(NE * 4);
+    }
+    for (int d = 0; d < 3; ++d) {
+        sub->lt[d] = lt[d];
+        sub->ldims[d] = lat->dims[d];
+    }
+    sub->nspecies = nspecies;
+    sub->has_dfac = has_dfac;
+    sub->NE_cap = (int64_t)NE;
+    return MPM_OK;
+}
+

@@ -43,13 +43,17 @@ struct BoxGeo {
 };
 
 // Box coordinates of element e; returns false for tile padding outside the box.
+// kCoherent: the tile coordinates were written earlier in the same kernel
+// (read through L2, not the read-only path).
+template <bool kCoherent = false>
 __device__ __forceinline__ bool elem_box(int64_t e, const BoxGeo &g, const int32_t *__restrict__ tile_coord,
                                          int &bx, int &by, int &bz)
 {
     const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
     const int64_t tile = e >> ltv;
     const uint32_t v = (uint32_t)(e & ((1 << ltv) - 1));
-    const int4 tc = __ldg(reinterpret_cast<const int4 *>(tile_coord) + tile);
+    const int4 *tcp = reinterpret_cast<const int4 *>(tile_coord) + tile;
+    const int4 tc = kCoherent ? __ldcg(tcp) : __ldg(tcp);
     bx = (tc.x << g.lt[0]) + (int)(v & ((1u << g.lt[0]) - 1));
     by = (tc.y << g.lt[1]) + (int)((v >> g.lt[0]) & ((1u << g.lt[1]) - 1));
     bz = (tc.z << g.lt[2]) + (int)(v >> (g.lt[0] + g.lt[1]));
@@ -57,6 +61,50 @@ __device__ __forceinline__ bool elem_box(int64_t e, const BoxGeo &g, const int32
 }
 
 BoxGeo make_geo(const ::mpm_subgrid *sub, const int32_t dims[3]);   // extract.cu
+
+// Running min / max of the (x, y, z) of lattice index e (bounding box, Sec. 2.3).
+__device__ __forceinline__ void bbox_upd(uint32_t e, uint32_t Lx, uint32_t Lxy, int (&mn)[3], int (&mx)[3])
+{
+    const uint32_t k = e / Lxy;
+    const uint32_t r = e - k * Lxy;
+    const uint32_t j = r / Lx;
+    const uint32_t i = r - j * Lx;
+    mn[0] = min(mn[0], (int)i); mx[0] = max(mx[0], (int)i);
+    mn[1] = min(mn[1], (int)j); mx[1] = max(mx[1], (int)j);
+    mn[2] = min(mn[2], (int)k); mx[2] = max(mx[2], (int)k);
+}
+
+
+// Box from the reduced bounds (Sec. 2.3): lo = max(0, min - margin),
+// hi = min(L, max + margin + 1); tile counts of the box.  n[0] = 0 marks an
+// empty tumour set.
+__device__ __forceinline__ BoxGeo box_geo(const int32_t *__restrict__ mnmx, int32_t margin, int32_t Lx, int32_t Ly,
+                                          int32_t Lz, int32_t lt0, int32_t lt1, int32_t lt2)
+{
+    BoxGeo g;
+    const int32_t L[3] = {Lx, Ly, Lz};
+    const int32_t lt[3] = {lt0, lt1, lt2};
+    const bool empty = mnmx[3] < 0;
+    for (int d = 0; d < 3; ++d) {
+        const int32_t lo = max(0, mnmx[d] - margin);
+        const int32_t hi = (int32_t)min((int64_t)L[d], (int64_t)mnmx[3 + d] + margin + 1);
+        g.lo[d] = empty ? 0 : lo;
+        g.n[d] = empty ? 0 : hi - lo;
+        g.lt[d] = lt[d];
+        g.nt[d] = empty ? 0 : (hi - lo + (1 << lt[d]) - 1) >> lt[d];
+    }
+    g.Lx = (uint32_t)Lx;
+    g.Ly = (uint32_t)Ly;
+    return g;
+}
+
+
+// Box and element count of a device-resident step, written by the tile scan
+// and read by the later stages (the host does not know them yet).
+struct StepDyn {
+    int64_t NE;
+    BoxGeo g;
+};
 
 // Coefficients of the implicit-Euler system (Eq. 1-4) shared by every row.
 struct AsmCoef {
@@ -99,6 +147,7 @@ __device__ __forceinline__ void assemble_row(const AsmCoef &C, int s, uint32_t f
 // Device view of one extracted, assembled box system.
 struct SysDev {
     int64_t NE;                 // stored elements = nact * TV
+    const int64_t *NEp;         // if set, the element count is read here on the device
     int32_t ltx, lty, ltz;      // log2 tile dims
     int32_t nspecies;
     const int32_t *nbr;         // [nact][6] neighbour tile (-1 none): -x,+x,-y,+y,-z,+z
@@ -348,6 +397,8 @@ struct mpm_subgrid {
     int32_t ldims[3] = {0, 0, 0};    // lattice dims of the extraction
     int32_t ntiles = 0, nact = 0;
     int64_t NE = 0, mask_voxels = 0;
+    int64_t NE_cap = 0;              // element capacity of the buffers (device-resident step)
+    void *step = nullptr;            // device-resident step state (solver.cu)
     int32_t nspecies = 0;
     bool has_dfac = false;
     bool x_fresh = true;         // iterate still equals c^n
@@ -395,6 +446,9 @@ mpm_status mpm_extract_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspeci
                             const int32_t tile[3], mpm_box *out_box, mpm_subgrid *sub, cudaStream_t st);
 mpm_status mpm_assemble_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_params *prm, cudaStream_t st);
 mpm_status mpm_assemble_check(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_params *p);
+mpm_status mpm_params_check(mpm_ctx *ctx, const mpm_params *p);
+mpm_status mpm_lattice_check(mpm_ctx *ctx, const mpm_lattice *lat, int32_t nspecies);
+mpm_status mpm_tile_lt(mpm_ctx *ctx, const int32_t tile[3], int32_t lt[3]);
 void mpm_asm_coef(const mpm_params *p, mpm::AsmCoef *C);
 void mpm_set_assembled_scalars(mpm_subgrid *sub, const mpm_params *p);
 mpm_status mpm_scatter_impl(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *lat, cudaStream_t st);
@@ -408,6 +462,20 @@ mpm_status mpm_batch_desc_fill(mpm_subgrid *const *subs, const mpm_lattice *cons
                                const mpm_params *const *prms, int32_t nsys, void *host, int64_t *nblocks);
 mpm_status mpm_batch_prep_launch(mpm_ctx *ctx, const void *d_desc, int32_t nsys, int64_t nblocks, cudaStream_t st);
 mpm_status mpm_batch_scatter_launch(mpm_ctx *ctx, const void *d_desc, int32_t nsys, int64_t nblocks, cudaStream_t st);
+// single system with the box and element count known only on the device (batch.cu)
+size_t mpm_step_xscr_bytes(int nb);
+int mpm_step_extract_grid(mpm_ctx *ctx);
+mpm_status mpm_step_extract_launch(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                                   int32_t margin, int nb, char *d_xscr, int32_t *d_box, int64_t *d_count,
+                                   void *d_dyn, uint32_t *d_sbar, int32_t nsbar, int32_t *d_sabort, void *d_reports,
+                                   size_t report_bytes, double *d_rates, cudaStream_t st);
+mpm_status mpm_step_scatter_launch(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                                   const void *d_dyn, const int32_t *d_box, const int64_t *d_count,
+                                   const int32_t *d_abort, int nb, char *d_xscr, const void *d_reports,
+                                   size_t report_bytes, void *h_mapped, cudaStream_t st);
+// extraction with buffers sized for the whole lattice and no host round trip (extract.cu)
+mpm_status mpm_step_buffers(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, int32_t nspecies, const int32_t lt[3]);
+
 mpm_status mpm_count_active_impl(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, const int32_t lt[3],
                                  int64_t *nact, int64_t *mask_voxels, cudaStream_t st);
 mpm_status mpm_export_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst,
@@ -421,4 +489,8 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
                                const mpm_params *const *prms, int32_t nsys, const mpm_opts *opt, mpm_report *reps,
                                cudaStream_t st);
 void mpm_batch_graph_free(mpm_ctx *ctx);
+mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
+                         const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, cudaStream_t st);
+void mpm_step_free(mpm_ctx *ctx, mpm_subgrid *sub);
+void mpm_step_invalidate(mpm_subgrid *sub);
 int mpm_batch_graph_active(mpm_ctx *ctx);

@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
     for (int si = td.sys_begin; si < td.sys_end; ++si) {
         const int sys_id = A.sys_order[si];
         const uint64_t t_item0 = globaltimer_ns();
-        if (tid == 0) sm.sys = A.sys[sys_id];
+        if (tid == 0) {
+            sm.sys = A.sys[sys_id];
+            if (sm.sys.NEp) sm.sys.NE = *sm.sys.NEp;   // sized on the device (device-resident step)
+        }
         __syncthreads();
         const SysDev &S = sm.sys;
         const int NS = S.nspecies;
@@ -820,8 +823,18 @@ static mpm_status check_opts(mpm_ctx *ctx, const mpm_opts *opt)
 // item per (system, species), the grid, the team split and the descriptor
 // layout.  reset_x: restore x = c^n where a previous solve moved it (queued
 // on st).
+// Overrides of the device-resident step (one system): the Krylov stride is
+// set by the buffers' element capacity, the work estimate by the previous
+// step's element count, the grid by the caller, and the kernel reads the
+// element count from the device.
+struct PlanOverride {
+    int64_t NE_cap, NE_est;
+    const int64_t *NEp;
+    int G;
+};
+
 static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, const mpm_opts *opt, bool reset_x,
-                             cudaStream_t st, SolvePlan &P)
+                             cudaStream_t st, SolvePlan &P, const PlanOverride *ov = nullptr)
 {
     const int m = opt->restart;
     const int maxm = m <= 8 ? 8 : (m <= 16 ? 16 : 32);
@@ -834,7 +847,8 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
     std::vector<double> work;
     for (int i = 0; i < nsys; ++i) {
         mpm_subgrid *sub = subs[i];
-        const int64_t vstride = sub->NE > 0 ? ((sub->NE + 63) / 64) * 64 : 64;
+        const int64_t ne_v = ov ? ov->NE_cap : sub->NE;
+        const int64_t vstride = ne_v > 0 ? ((ne_v + 63) / 64) * 64 : 64;
         const size_t per = a256((size_t)(m + 1) * (size_t)vstride * tsz);
         mpm_status r = mpm_grow(ctx, &sub->krylov, &sub->krylov_bytes, per * sub->nspecies, "Krylov basis");
         if (r != MPM_OK) return r;
@@ -843,7 +857,11 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
                 MPM_CU(cudaMemcpyAsync(sub->x[s], sub->cn[s], (size_t)sub->NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
             sub->x_fresh = true;
         }
-        const SysDev full = mpm_make_sysdev(sub);
+        SysDev full = mpm_make_sysdev(sub);
+        if (ov) {
+            full.NE = 0;
+            full.NEp = ov->NEp;
+        }
         for (int s = 0; s < sub->nspecies; ++s) {
             SysDev d = full;
             d.nspecies = 1;
@@ -860,7 +878,7 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
             d.vstride = vstride;
             d.V[0] = (char *)sub->krylov + per * s;
             P.sd.push_back(d);
-            work.push_back((double)sub->NE + 1.0);
+            work.push_back((double)(ov ? ov->NE_est : sub->NE) + 1.0);
             P.item_sys.push_back(i);
             P.item_sp.push_back(s);
         }
@@ -869,7 +887,8 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
     P.fn = pick(opt->precision, maxm, ctx->solver_variant, P.smem);
     const int gmax = mpm_solver_max_blocks(ctx, opt->precision, m, ctx->solver_variant);
     if (gmax < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "solve: occupancy query failed");
-    if (opt->nblocks > 0) P.G = std::min(opt->nblocks, gmax);
+    if (ov && ov->G > 0) P.G = std::min(ov->G, gmax);
+    else if (opt->nblocks > 0) P.G = std::min(opt->nblocks, gmax);
     else {
         double tot = 0.0;
         for (double w : work) tot += w;
@@ -913,7 +932,7 @@ static void fill_descriptors(const SolvePlan &P, char *h)
 // Queue the solve: counters and reports cleared, then the cooperative launch.
 // Only stream work (capturable); descriptors already sit at d_args.
 static mpm_status enqueue_solve(mpm_ctx *ctx, SolvePlan &P, char *d_args, uint32_t *d_bar, int32_t *d_abort,
-                                unsigned long long *d_prof, cudaStream_t st)
+                                unsigned long long *d_prof, cudaStream_t st, bool zeroed = false)
 {
     SolveArgs sa = P.sa;
     sa.sys = (const SysDev *)(d_args + P.o_sys);
@@ -924,9 +943,11 @@ static mpm_status enqueue_solve(mpm_ctx *ctx, SolvePlan &P, char *d_args, uint32
     sa.bar = d_bar;
     sa.abort_flag = d_abort;
     sa.prof = d_prof;
-    MPM_CU(cudaMemsetAsync(d_bar, 0, (size_t)P.nteam * 32 * sizeof(uint32_t), st));
-    MPM_CU(cudaMemsetAsync(d_abort, 0, sizeof(int32_t), st));
-    MPM_CU(cudaMemsetAsync(d_args + P.o_rep, 0, sizeof(SysReport) * P.nitem, st));
+    if (!zeroed) {   // else a preceding kernel of the same stream zeroed them
+        MPM_CU(cudaMemsetAsync(d_bar, 0, (size_t)P.nteam * 32 * sizeof(uint32_t), st));
+        MPM_CU(cudaMemsetAsync(d_abort, 0, sizeof(int32_t), st));
+        MPM_CU(cudaMemsetAsync(d_args + P.o_rep, 0, sizeof(SysReport) * P.nitem, st));
+    }
     if (d_prof) MPM_CU(cudaMemsetAsync(d_prof, 0, 8 * sizeof(unsigned long long), st));
     void *kargs[] = {&sa};
     MPM_CU(cudaLaunchCooperativeKernel((const void *)P.fn, dim3(P.G), dim3(kSB), kargs, P.smem, st));
@@ -1072,6 +1093,8 @@ struct BatchGraph {
     char *d_desc = nullptr;
     size_t desc_cap = 0;
     int64_t prep_blocks = 0;
+    double *d_partials = nullptr;  // the graph's own reduction buffer (the context's may move)
+    size_t partials_cap = 0;
 };
 
 static void batch_key(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice *const *lats,
@@ -1104,6 +1127,7 @@ void mpm_batch_graph_free(mpm_ctx *ctx)
     cudaFree(B->d_bar);
     cudaFree(B->d_abort);
     cudaFree(B->d_desc);
+    cudaFree(B->d_partials);
     delete B;
     ctx->batch_graph = nullptr;
 }
@@ -1144,6 +1168,10 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
         if (r != MPM_OK) return r;
         r = mpm_grow(ctx, (void **)&B->d_args, &B->args_cap, B->plan.args_need, "batch descriptors");
         if (r != MPM_OK) return r;
+        r = mpm_grow(ctx, (void **)&B->d_partials, &B->partials_cap, 2 * (size_t)B->plan.G * kKMax * sizeof(double),
+                     "batch reduction partials");
+        if (r != MPM_OK) return r;
+        B->plan.sa.partials = B->d_partials;
         if (!B->d_bar) {
             MPM_CU(cudaMalloc(&B->d_bar, (size_t)ctx->num_sms * 4 * 32 * sizeof(uint32_t)));
             MPM_CU(cudaMalloc(&B->d_abort, 256));
@@ -1220,4 +1248,289 @@ int mpm_batch_graph_active(mpm_ctx *ctx)
 {
     BatchGraph *B = (BatchGraph *)ctx->batch_graph;
     return B && B->valid ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ device-resident step in a CUDA graph
+// One step of one lattice with no host round trip between its stages: the
+// extraction, preparation, solve, scatter and the copies of the results all
+// run from one graph, with buffers sized for the whole lattice and the box
+// and element count passed from kernel to kernel in device memory.
+struct StepGraph {
+    bool valid = false;
+    bool graph_failed = false;
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_launches = 0;
+    SolvePlan plan;
+    int G = 0;                      // grid of the current plan
+    int64_t last_NE = -1;           // element count of the previous step (-1: none)
+    char *d_scr = nullptr;          // box (256 B), counts (256 B), abort flag (256 B), StepDyn (256 B)
+    char *d_args = nullptr;         // solver descriptors and reports
+    size_t args_cap = 0;
+    uint32_t *d_bar = nullptr;
+    double *d_partials = nullptr;
+    size_t partials_cap = 0;
+    double *d_rates = nullptr;      // rate tables of the preparation
+    size_t rates_cap = 0;
+    char *d_xscr = nullptr;         // scratch of the cooperative extraction
+    int xnb = 0;                    // its grid
+    char *h_out = nullptr;          // host-mapped: box, counts, abort flag, reports (written by the scatter)
+    char *h_out_dev = nullptr;      // its device address
+    size_t hout_cap = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+static constexpr size_t kOutBox = 0, kOutCount = 64, kOutAbort = 128, kOutRep = 256;
+static constexpr size_t kScrBox = 0, kScrCount = 256, kScrAbort = 512, kScrDyn = 768;
+
+void mpm_step_free(mpm_ctx *ctx, mpm_subgrid *sub)
+{
+    StepGraph *T = (StepGraph *)sub->step;
+    if (!T) return;
+    if (ctx) ctx->allocated -= T->args_cap + T->partials_cap + T->rates_cap;
+    if (T->exec) cudaGraphExecDestroy(T->exec);
+    cudaFree(T->d_scr);
+    cudaFree(T->d_args);
+    cudaFree(T->d_bar);
+    cudaFree(T->d_partials);
+    cudaFree(T->d_rates);
+    cudaFree(T->d_xscr);
+    if (T->h_out) cudaFreeHost(T->h_out);
+    if (T->e0) cudaEventDestroy(T->e0);
+    if (T->e1) cudaEventDestroy(T->e1);
+    delete T;
+    sub->step = nullptr;
+}
+
+// Another extraction rewrote the subgrid's tables: the step's between-step
+// state (activity bytes) must be set up again.
+void mpm_step_invalidate(mpm_subgrid *sub)
+{
+    StepGraph *T = (StepGraph *)sub->step;
+    if (T) T->valid = false;
+}
+
+// The stages of one step on stream cs (captured or eager): the cooperative
+// extraction + preparation, the solve, the scatter with the result copy.
+static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, const mpm_lattice *lat,
+                               const mpm_params *prm, int32_t margin, bool capturing, cudaStream_t cs)
+{
+    int32_t *d_box = (int32_t *)(T->d_scr + kScrBox);
+    int64_t *d_count = (int64_t *)(T->d_scr + kScrCount);
+    int32_t *d_abort = (int32_t *)(T->d_scr + kScrAbort);
+    void *d_dyn = T->d_scr + kScrDyn;
+    char *d_rep = T->d_args + T->plan.o_rep;
+    const size_t rep_bytes = sizeof(SysReport) * T->plan.nitem;
+    mpm_status r = mpm_step_extract_launch(ctx, sub, lat, prm, margin, T->xnb, T->d_xscr, d_box, d_count, d_dyn,
+                                           T->d_bar, T->plan.nteam * 32, d_abort, d_rep, rep_bytes, T->d_rates, cs);
+    if (r != MPM_OK) return r;
+    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    MPM_CU(cudaEventRecordWithFlags(T->e0, cs, evf));
+    r = enqueue_solve(ctx, T->plan, T->d_args, T->d_bar, d_abort, ctx->phase_prof ? ctx->d_prof : nullptr, cs, true);
+    if (r != MPM_OK) return r;
+    MPM_CU(cudaEventRecordWithFlags(T->e1, cs, evf));
+    r = mpm_step_scatter_launch(ctx, sub, lat, prm, d_dyn, d_box, d_count, d_abort, T->xnb, T->d_xscr, d_rep,
+                                rep_bytes, T->h_out_dev, cs);
+    if (r != MPM_OK) return r;
+    if (ctx->phase_prof)
+        MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
+    return MPM_OK;
+}
+
+// Grid of the persistent solve for S items of NE elements (the sizing of
+// plan_solve: about two elements per thread and item, at least one CTA per
+// item, at most the co-resident maximum).
+static int step_grid(int64_t NE, int S, int gmax)
+{
+    const double want = (double)S * (double)(NE + 1) / (kSB * 2.0);
+    int G = (int)std::min<double>(gmax, std::max(1.0, want));
+    return std::max(G, std::min(S, gmax));
+}
+
+mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
+                         const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, cudaStream_t st)
+{
+    if (!sub || !prm) return mpm_fail(ctx, MPM_ERR_ARG, "step: null argument");
+    mpm_status r = mpm_params_check(ctx, prm);
+    if (r != MPM_OK) return r;
+    r = mpm_lattice_check(ctx, lat, prm->nspecies);
+    if (r != MPM_OK) return r;
+    if (margin < 0) return mpm_fail(ctx, MPM_ERR_ARG, "step: negative margin");
+    r = check_opts(ctx, opt);
+    if (r != MPM_OK) return r;
+    if (opt->x0_given) return mpm_fail(ctx, MPM_ERR_ARG, "step: x0_given is not supported (the step starts from c^n)");
+    int32_t lt[3];
+    r = mpm_tile_lt(ctx, tile, lt);
+    if (r != MPM_OK) return r;
+    if (!sub->step) sub->step = new StepGraph();
+    StepGraph *T = (StepGraph *)sub->step;
+    const int S = prm->nspecies;
+    // buffers for the whole lattice (pointers move only when they grow)
+    const void *old_geo = sub->geo, *old_elem = sub->elem;
+    r = mpm_step_buffers(ctx, sub, lat, S, lt);
+    if (r != MPM_OK) return r;
+    if (sub->geo != old_geo || sub->elem != old_elem) T->valid = false;
+    // grid: from the previous step's element count, kept while within 25%
+    const int gmax = mpm_solver_max_blocks(ctx, opt->precision, opt->restart, ctx->solver_variant);
+    if (gmax < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "step: occupancy query failed");
+    const int64_t NE_est = T->last_NE >= 0 ? T->last_NE : sub->NE_cap;
+    int G = opt->nblocks > 0 ? std::min(opt->nblocks, gmax) : step_grid(NE_est, S, gmax);
+    if (opt->nblocks <= 0 && T->G > 0 && T->G <= gmax && G >= T->G * 4 / 5 && G <= T->G * 5 / 4) G = T->G;
+    if (!T->d_scr) {
+        MPM_CU(cudaMalloc(&T->d_scr, 1024));
+        MPM_CU(cudaMemset(T->d_scr, 0, 1024));
+        T->xnb = mpm_step_extract_grid(ctx);
+        if (T->xnb < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "step: extraction occupancy query failed");
+        MPM_CU(cudaMalloc(&T->d_xscr, mpm_step_xscr_bytes(T->xnb)));
+        T->valid = false;
+        MPM_CU(cudaMalloc(&T->d_bar, (size_t)ctx->num_sms * 4 * 32 * sizeof(uint32_t)));
+        MPM_CU(cudaEventCreate(&T->e0));
+        MPM_CU(cudaEventCreate(&T->e1));
+    }
+    auto make_key = [&](std::vector<unsigned char> &key) {
+        key.clear();
+        auto put = [&](const void *p, size_t n) {
+            const unsigned char *c = (const unsigned char *)p;
+            key.insert(key.end(), c, c + n);
+        };
+        put(lat, sizeof(mpm_lattice));
+        put(prm, sizeof(mpm_params));
+        put(opt, sizeof(mpm_opts));
+        put(&margin, sizeof(margin));
+        put(lt, 3 * sizeof(int32_t));
+        put(&G, sizeof(G));
+        put(&ctx->solver_variant, sizeof(int32_t));
+        put(&ctx->timeout_ns, sizeof(uint64_t));
+        put(&ctx->skip_block, sizeof(int32_t));
+        put(&sub->geo, sizeof(void *));
+        put(&sub->elem, sizeof(void *));
+        put(&sub->krylov, sizeof(void *));
+    };
+    std::vector<unsigned char> key;
+    make_key(key);
+    const bool use_graph = !ctx->phase_prof;
+    if (!(T->valid && T->key == key) || !use_graph) {
+        if (T->exec) cudaGraphExecDestroy(T->exec);
+        T->exec = nullptr;
+        T->valid = false;
+        // solver plan: stride from the capacity, grid G, element count from the device
+        PlanOverride ov;
+        ov.NE_cap = sub->NE_cap;
+        ov.NE_est = NE_est;
+        ov.NEp = &((const StepDyn *)(T->d_scr + kScrDyn))->NE;
+        ov.G = G;
+        mpm_set_assembled_scalars(sub, prm);   // read into the solver's descriptors
+        T->plan = SolvePlan();
+        r = plan_solve(ctx, &sub, 1, opt, false, st, T->plan, &ov);
+        if (r != MPM_OK) return r;
+        make_key(key);   // the Krylov basis may have grown
+        r = mpm_grow(ctx, (void **)&T->d_args, &T->args_cap, T->plan.args_need, "step solver descriptors");
+        if (r != MPM_OK) return r;
+        r = mpm_grow(ctx, (void **)&T->d_partials, &T->partials_cap, 2 * (size_t)T->plan.G * kKMax * sizeof(double),
+                     "step reduction partials");
+        if (r != MPM_OK) return r;
+        T->plan.sa.partials = T->d_partials;
+        r = mpm_grow(ctx, (void **)&T->d_rates, &T->rates_cap, 2 * (size_t)prm->nspecies * prm->ncell * sizeof(double),
+                     "step rate tables");
+        if (r != MPM_OK) return r;
+        if (T->plan.nteam > ctx->num_sms * 4) return mpm_fail(ctx, MPM_ERR_ARG, "step: too many teams");
+        const size_t hneed = kOutRep + sizeof(SysReport) * T->plan.nitem;
+        if (T->hout_cap < hneed) {
+            if (T->h_out) cudaFreeHost(T->h_out);
+            T->h_out = T->h_out_dev = nullptr;
+            T->hout_cap = 0;
+            MPM_CU(cudaHostAlloc((void **)&T->h_out, hneed, cudaHostAllocMapped));
+            T->hout_cap = hneed;
+            MPM_CU(cudaHostGetDevicePointer((void **)&T->h_out_dev, T->h_out, 0));
+        }
+        if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+        r = ensure_stage(ctx, T->plan.args_need + 4096);
+        if (r != MPM_OK) return r;
+        fill_descriptors(T->plan, (char *)ctx->h_stage);
+        MPM_CU(cudaMemcpyAsync(T->d_args, ctx->h_stage, T->plan.o_rep, cudaMemcpyHostToDevice, st));
+        // between-step state: activity bytes, the extraction's barrier counter and abort flag at zero
+        {
+            const int64_t ntl = (((int64_t)lat->dims[0] + (1 << lt[0]) - 1) >> lt[0]) *
+                                (((int64_t)lat->dims[1] + (1 << lt[1]) - 1) >> lt[1]) *
+                                (((int64_t)lat->dims[2] + (1 << lt[2]) - 1) >> lt[2]);
+            MPM_CU(cudaMemsetAsync(sub->active, 0, (size_t)ntl, st));
+            MPM_CU(cudaMemsetAsync(T->d_xscr, 0, mpm_step_xscr_bytes(T->xnb), st));
+        }
+        MPM_CU(cudaStreamSynchronize(st));   // descriptors and slots in place before any capture
+        T->G = G;
+        if (use_graph && !T->graph_failed) {
+            if (!ctx->cap_stream) MPM_CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cudaStream_t cs = ctx->cap_stream;
+            cudaGraph_t g = nullptr;
+            const int64_t launches0 = ctx->launches;
+            bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                ok = enqueue_step(ctx, T, sub, lat, prm, margin, true, cs) == MPM_OK;
+                const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+                ok = ok && ec == cudaSuccess && g != nullptr;
+            }
+            T->graph_launches = ctx->launches - launches0;
+            ctx->launches = launches0;
+            if (ok) ok = cudaGraphInstantiate(&T->exec, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (ok) {
+                T->valid = true;
+                T->key = key;
+            } else {
+                T->exec = nullptr;
+                T->graph_failed = true;   // stay eager on this device or driver
+            }
+        }
+    }
+    if (T->valid) {
+        MPM_CU(cudaGraphLaunch(T->exec, st));
+        ctx->launches += T->graph_launches;
+    } else {
+        r = enqueue_step(ctx, T, sub, lat, prm, margin, false, st);
+        if (r != MPM_OK) return r;
+    }
+    MPM_CU(cudaStreamSynchronize(st));
+    const volatile int32_t *hb = (const volatile int32_t *)(T->h_out + kOutBox);
+    const volatile int64_t *hc = (const volatile int64_t *)(T->h_out + kOutCount);
+    const bool x_timed_out = *(const volatile int32_t *)(T->h_out + kOutAbort + 4) != 0;
+    const bool timed_out = x_timed_out || *(const volatile int32_t *)(T->h_out + kOutAbort) != 0;
+    if (x_timed_out) {   // nothing was solved or written; set the between-step state up again
+        T->valid = false;
+        sub->extracted = false;
+        sub->assembled = false;
+        return mpm_fail(ctx, MPM_ERR_TIMEOUT, "step: a bounded grid barrier of the extraction expired");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, T->e0, T->e1);
+    cudaGetLastError();
+    sub->gen += 1;
+    if (hb[3] < 0) {   // no tumour voxel: nothing was solved or written
+        sub->extracted = false;
+        sub->assembled = false;
+        sub->NE = 0;
+        T->last_NE = 0;
+        return mpm_fail(ctx, MPM_ERR_EMPTY, "step: no tumour voxel (cell_id > 0)");
+    }
+    mpm_box box;
+    for (int d = 0; d < 3; ++d) {
+        box.lo[d] = hb[d] - margin < 0 ? 0 : hb[d] - margin;
+        const int64_t h = (int64_t)hb[3 + d] + margin + 1;
+        box.hi[d] = h > lat->dims[d] ? lat->dims[d] : (int32_t)h;
+        sub->lo[d] = box.lo[d];
+        sub->hi[d] = box.hi[d];
+        sub->n[d] = box.hi[d] - box.lo[d];
+        sub->nt[d] = (sub->n[d] + (1 << lt[d]) - 1) >> lt[d];
+    }
+    sub->ntiles = sub->nt[0] * sub->nt[1] * sub->nt[2];
+    sub->mask_voxels = hc[0];
+    sub->nact = (int32_t)hc[1];
+    sub->NE = (int64_t)sub->nact << (lt[0] + lt[1] + lt[2]);
+    sub->extracted = true;
+    sub->assembled = true;
+    T->last_NE = sub->NE;
+    if (out_box) *out_box = box;
+    r = finish_solve(ctx, T->plan, &sub, (const SysReport *)(T->h_out + kOutRep), timed_out, ms, rep, nullptr, st);
+    sub->x_fresh = false;
+    return r;
 }

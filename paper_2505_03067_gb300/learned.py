@@ -46,6 +46,7 @@ def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, l
     for it in range(nsteps):
         for b, tr in enumerate(trajs):
             if tr.age >= traj_len:
+                tr.solver.sub.destroy()
                 trajs[b] = tr = _Traj(ctx, rng, n)
             xb, fb = cnn.features(tr.lat, tr.prm, box)
             x[b * V:(b + 1) * V] = xb

@@ -29,7 +29,8 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
-           "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess"]
+           "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
+           "mpm_step"]
 
 
 class mpm_box(C.Structure):
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_batch_step": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.POINTER(C.POINTER(mpm_params)),
                            C.c_int32, C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
         "mpm_solve_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
+        "mpm_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, C.POINTER(C.c_int32),
+                     C.POINTER(mpm_opts), C.POINTER(mpm_report), C.POINTER(mpm_box), P],
         "mpm_solve_batch": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.c_int32, C.POINTER(mpm_opts),
                             C.POINTER(mpm_report), P],
         "mpm_subgrid_export": [P, P, C.c_int32, C.c_int32, P, P],
@@ -327,6 +330,26 @@ class Subgrid:
         d["status_code"] = st
         return d
 
+    def mpm_step(self, lat: DeviceLattice, prm: "DeviceParams", margin: int, opts: mpm_opts, tile=None,
+                 stream=None, allow=(ERR_NOCONV,)):
+        """One device-resident step (mpm_step): box, compaction, assembly, solve
+        and scatter from one CUDA graph; the report gains "box" (None if no
+        tumour voxel) and "status_code"."""
+        rep = mpm_report()
+        box = mpm_box()
+        ls = lat.struct()
+        t = (C.c_int32 * 3)(*tile) if tile is not None else None
+        st = self.ctx.lib.mpm_step(self.ctx.ptr, self.h, C.byref(ls), C.byref(prm.struct), margin, t,
+                                   C.byref(opts), C.byref(rep), C.byref(box), _stream_ptr(stream))
+        self.ctx._check(st, "mpm_step", allow=tuple(allow) + (ERR_EMPTY,))
+        if st == ERR_EMPTY:
+            return {"status_code": ERR_EMPTY, "box": None}
+        self.nspecies = int(prm.struct.nspecies)
+        d = rep.as_dict(self.nspecies)
+        d["status_code"] = st
+        d["box"] = box.as_tuple()
+        return d
+
     def mpm_subgrid_export(self, what: int, s: int = 0, stream=None):
         import torch
         info = self.info()
@@ -426,14 +449,19 @@ class BatchStepper:
 
 
 class StepSolver:
-    """One implicit-Euler step of every species on a device lattice:
-    mpm_box_extract -> mpm_assemble_coeffs -> mpm_solve_step (with scatter)."""
+    """One implicit-Euler step of every species on a device lattice.  By
+    default the device-resident mpm_step (one CUDA graph per step); with
+    fused=False the composition mpm_box_extract -> mpm_assemble_coeffs ->
+    mpm_solve_step (with scatter)."""
 
-    def __init__(self, ctx: Context, lat: DeviceLattice, prm: DeviceParams, margin: int, tile=None):
+    def __init__(self, ctx: Context, lat: DeviceLattice, prm: DeviceParams, margin: int, tile=None, fused=True):
         self.ctx, self.lat, self.prm, self.margin, self.tile = ctx, lat, prm, margin, tile
+        self.fused = fused
         self.sub = ctx.subgrid_create()
 
     def step(self, opts: mpm_opts, stream=None, allow=(ERR_NOCONV,)):
+        if self.fused:
+            return self.sub.mpm_step(self.lat, self.prm, self.margin, opts, self.tile, stream, allow)
         box = self.sub.mpm_box_extract(self.lat, self.lat.nspecies, self.margin, self.tile, stream)
         if box is None:
             return {"status_code": ERR_EMPTY, "box": None}

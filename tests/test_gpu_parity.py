@@ -125,21 +125,23 @@ def test_assembly_and_operator_match_oracle_csr(M, ctx, seed, dims, bc_box):
     sub.destroy()
 
 
-def _gpu_step(M, ctx, wl, opts, tile=None, lat=None, prm=None, allow=None):
+def _gpu_step(M, ctx, wl, opts, tile=None, lat=None, prm=None, allow=None, fused=True):
     lat = lat or M.DeviceLattice(wl.lattice)
     prm = prm or M.DeviceParams(wl.params)
-    solver = M.StepSolver(ctx, lat, prm, wl.margin, tile)
+    solver = M.StepSolver(ctx, lat, prm, wl.margin, tile, fused=fused)
     rep = solver.step(opts, allow=allow if allow is not None else (M.ERR_NOCONV,))
     return lat, rep
 
 
 @pytest.mark.parametrize("seed,dims", CASES)
 @pytest.mark.parametrize("tile", TILES)
-def test_fp64_solve_matches_oracle(M, ctx, seed, dims, tile):
+@pytest.mark.parametrize("fused", [True, False])
+def test_fp64_solve_matches_oracle(M, ctx, seed, dims, tile, fused):
     wl = W.random_case(seed, dims, nspecies=3, dfac=(seed % 3 == 0))
     ref = wl.lattice.copy()
     ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
-    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=16, maxit=2000), tile)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=16, maxit=2000), tile, fused=fused)
+    assert rep["box"] == ro["box"] and rep["mask_voxels"] == ro["mask_voxels"]
     assert rep["status_code"] == M.OK
     assert all(r <= 1e-13 for r in rep["res"])
     got = lat.fields_numpy()
@@ -310,9 +312,9 @@ def shell256():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_shell256_first_step_matches_oracle(M, ctx, shell256, precision):
-    """The 256^3 three-species pleural-shell workload, first step, in the launch
-    configuration the benchmark times (default grid, tile 8x8x4, GMRES(16)),
-    compared with the oracle on every in-mask voxel of the box."""
+    """The 256^3 three-species pleural-shell workload, first step, through the
+    device-resident step the benchmark times (default grid and tile), compared
+    with the oracle on every in-mask voxel of the box."""
     wl = shell256
     ref = wl.lattice.copy()
     ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-11)
@@ -344,3 +346,100 @@ def test_four_species_il8(M, ctx):
     lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=2000))
     assert rep["status_code"] == M.OK and len(rep["iters"]) == 4
     assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+
+
+# ---------------------------------------------------------------- device-resident step
+def _grow_cells(wl, r, centre):
+    """Tumour = mask voxels within radius r of centre, ids by octant (1..8)."""
+    lz, ly, lx = wl.lattice.cell_id.shape
+    z, y, x = np.meshgrid(np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    d = np.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2)
+    ids = 1 + (x > centre[0]) + 2 * (y > centre[1]) + 4 * (z > centre[2])
+    return np.where((d <= r) & (wl.lattice.mask > 0), ids, 0).astype(np.int32)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_device_resident_step_follows_a_moving_growing_tumour(M, ctx, precision):
+    """Eight steps of one graph-replayed step while the tumour grows and moves:
+    the box (and so the element count and the solver's re-planned grid) changes
+    between replays; every step matches the oracle's step on the same lattice."""
+    import torch
+    wl = W.random_case(21, (48, 40, 36), nspecies=3, ncell=9)
+    ref = wl.lattice.copy()
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    solver = M.StepSolver(ctx, lat, prm, wl.margin, (4, 4, 2))
+    if precision == 0:
+        opts = M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=2000)
+    else:
+        opts = M.make_opts(rtol=1e-9, restart=8, maxit=2000, precision=1, inner_rtol=1e-6)
+    boxes = []
+    for k, (r, c) in enumerate([(1.5, (8, 9, 10)), (3, (9, 10, 10)), (6, (12, 12, 12)), (10, (16, 14, 14)),
+                                (4, (30, 20, 20)), (14, (24, 20, 18)), (20, (24, 20, 18)), (2, (40, 30, 28))]):
+        cid = _grow_cells(wl, r, c)
+        if not (cid > 0).any():
+            continue
+        ref.cell_id = cid
+        lat.cell_id.copy_(torch.from_numpy(cid))
+        ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+        rep = solver.step(opts)
+        assert rep["status_code"] == M.OK and rep["box"] == ro["box"], (k, rep["box"], ro["box"])
+        assert rep["mask_voxels"] == ro["mask_voxels"]
+        boxes.append(rep["box"])
+        got = lat.fields_numpy()
+        if precision == 0:
+            assert np.max(np.abs(got - ref.fields)) <= 1e-10, k
+        else:
+            for s in range(3):
+                assert np.linalg.norm(got[s] - ref.fields[s]) <= 3e-8 * np.linalg.norm(ref.fields[s]), (k, s)
+            lat.fields.copy_(torch.from_numpy(ref.fields))   # keep both sides on the same c^n
+    assert len(set(boxes)) >= 6
+
+
+def test_device_resident_step_empty_then_tumour(M, ctx):
+    """No tumour voxel: MPM_ERR_EMPTY and the lattice unchanged; once a tumour
+    appears the same subgrid steps it."""
+    import torch
+    wl = W.random_case(22, (20, 18, 16), nspecies=2)
+    cid = wl.lattice.cell_id.copy()
+    wl.lattice.cell_id[:] = 0
+    lat = M.DeviceLattice(wl.lattice)
+    solver = M.StepSolver(ctx, lat, M.DeviceParams(wl.params), wl.margin)
+    opts = M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=500)
+    rep = solver.step(opts)
+    assert rep["status_code"] == M.ERR_EMPTY and rep["box"] is None
+    assert np.array_equal(lat.fields_numpy(), wl.lattice.fields)
+    lat.cell_id.copy_(torch.from_numpy(cid))
+    ref = wl.lattice.copy()
+    ref.cell_id = cid
+    ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    rep = solver.step(opts)
+    assert rep["status_code"] == M.OK and rep["box"] == ro["box"]
+    assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+    # and back to empty: nothing is written
+    before = lat.fields_numpy()
+    lat.cell_id.zero_()
+    assert solver.step(opts)["status_code"] == M.ERR_EMPTY
+    assert np.array_equal(lat.fields_numpy(), before)
+
+
+def test_device_resident_step_replays_one_graph(M):
+    """After the first call the step is one graph launch of three kernels (the
+    cooperative extraction + preparation, the solve, the scatter), and the
+    exports see the step's extraction."""
+    c = M.Context()
+    wl = W.random_case(23, (26, 22, 20), nspecies=3)
+    lat = M.DeviceLattice(wl.lattice)
+    solver = M.StepSolver(c, lat, M.DeviceParams(wl.params), wl.margin)
+    opts = M.make_opts(rtol=1e-10, restart=8, maxit=500)
+    solver.step(opts)
+    l0 = c.launches()
+    for _ in range(3):
+        assert solver.step(opts)["status_code"] == M.OK
+    assert c.launches() - l0 == 3 * 3
+    info = solver.sub.info()
+    box = oracle.bbox(wl.lattice.cell_id, wl.margin)
+    assert info["box"] == box
+    flags = solver.sub.mpm_subgrid_export(M.EXPORT_FLAGS).cpu().numpy()
+    mb = oracle.box_view(wl.lattice.mask, box)
+    assert int(((flags & 64) > 0).sum()) == int(mb.sum())
