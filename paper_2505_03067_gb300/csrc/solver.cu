@@ -48,11 +48,17 @@ struct SpState {
 // flags and neighbour indices are computed once per element and the loads of
 // all species of the group are in flight together.
 
-template <int MAXM>
+// G: the type of the small serial least-squares problem (Hessenberg matrix,
+// Givens rotations, residual vector, basis scales) -- the Krylov type: FP32
+// on the FP32-Krylov path, whose inner solve only has to reach about 1e-6
+// relative (the FP64 residual pass decides convergence), FP64 otherwise.  On
+// GB300 every FP64 instruction of this one-thread section costs tens of cycles.
+template <int MAXM, typename G>
 struct Smem {
-    double H[kMaxSpecies][(MAXM + 1) * MAXM];
-    double cs[kMaxSpecies][MAXM], sn[kMaxSpecies][MAXM];
-    double g[kMaxSpecies][MAXM + 1], sig[kMaxSpecies][MAXM + 1], coef[kMaxSpecies][MAXM + 1];
+    G H[kMaxSpecies][(MAXM + 1) * MAXM];
+    G cs[kMaxSpecies][MAXM], sn[kMaxSpecies][MAXM];
+    G g[kMaxSpecies][MAXM + 1], sig[kMaxSpecies][MAXM + 1];
+    double coef[kMaxSpecies][MAXM + 1];
     float coef32[kMaxSpecies][MAXM + 1];
     double red[kSW][kKMax];
     double tot[kKMax];
@@ -269,13 +275,12 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
 
 // ---- P1: w = sigma_j A u_j into slot j+1; acc[i] += u_i . w for i <= j
 template <typename T, int MAXM, int U>
-__device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, double sigj, uint32_t e0, uint32_t es,
+__device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
                                               T (&acc)[MAXM + 1])
 {
     const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
     const bool var = S.dfac != nullptr;
-    const T sj = (T)sigj;
     const T offT = (T)(var ? S.a : S.off[0]);
     const T *V = (const T *)S.V[0];
     const T *uj = V + (int64_t)j * vs;
@@ -389,7 +394,7 @@ template <typename T, int MAXM, int U, int MINB>
 __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    Smem<MAXM> &sm = *reinterpret_cast<Smem<MAXM> *>(smraw);
+    Smem<MAXM, T> &sm = *reinterpret_cast<Smem<MAXM, T> *>(smraw);
     if ((int)blockIdx.x == A.skip_block) return;    // fault injection: this CTA never arrives
     const int tid = threadIdx.x;
     const int team = A.block_team[blockIdx.x];
@@ -472,9 +477,9 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
                     p.in_cycle = 1;
                     p.cyc += 1;
                     p.k = 0;
-                    for (int i = 0; i <= MAXM; ++i) sm.g[tid][i] = 0.0;
-                    sm.g[tid][0] = beta;
-                    sm.sig[tid][0] = 1.0 / beta;
+                    for (int i = 0; i <= MAXM; ++i) sm.g[tid][i] = T(0);
+                    sm.g[tid][0] = (T)beta;
+                    sm.sig[tid][0] = (T)(1.0 / beta);
                     p.tol_in = kF32 ? fmax(0.25 * p.tol, A.inner_rtol * beta) : p.tol;
                 }
             }
@@ -505,10 +510,11 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
                     for (int i = 0; i <= j; ++i) {
-                        const double h = sm.sig[tid][i] * sm.tot[tid * kKStride + i];
+                        const T h = sm.sig[tid][i] * (T)sm.tot[tid * kKStride + i];
                         sm.H[tid][i * MAXM + j] = h;
-                        sm.coef[tid][i] = h * sm.sig[tid][i];
-                        sm.coef32[tid][i] = (float)sm.coef[tid][i];
+                        const T c = h * sm.sig[tid][i];
+                        if (kF32) sm.coef32[tid][i] = (float)c;
+                        else sm.coef[tid][i] = (double)c;
                     }
                 }
                 __syncthreads();
@@ -526,24 +532,24 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
                     SpState &p = sm.sp[tid];
-                    double *H = sm.H[tid];
-                    double *cs = sm.cs[tid], *sn = sm.sn[tid], *g = sm.g[tid];
-                    const double hn = sqrt(sm.tot[tid * kKStride]);
+                    T *H = sm.H[tid];
+                    T *cs = sm.cs[tid], *sn = sm.sn[tid], *g = sm.g[tid];
+                    const T hn = sqrt((T)sm.tot[tid * kKStride]);
                     H[(j + 1) * MAXM + j] = hn;
                     for (int i = 0; i < j; ++i) {
-                        const double t0 = H[i * MAXM + j], t1 = H[(i + 1) * MAXM + j];
+                        const T t0 = H[i * MAXM + j], t1 = H[(i + 1) * MAXM + j];
                         H[i * MAXM + j] = cs[i] * t0 + sn[i] * t1;
                         H[(i + 1) * MAXM + j] = -sn[i] * t0 + cs[i] * t1;
                     }
-                    const double aa = H[j * MAXM + j], bb = hn;
-                    if (bb == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+                    const T aa = H[j * MAXM + j], bb = hn;
+                    if (bb == T(0)) { cs[j] = T(1); sn[j] = T(0); }
                     else {
-                        const double r = hypot(aa, bb);
+                        const T r = hypot(aa, bb);
                         cs[j] = aa / r;
                         sn[j] = bb / r;
                     }
                     H[j * MAXM + j] = cs[j] * aa + sn[j] * bb;
-                    H[(j + 1) * MAXM + j] = 0.0;
+                    H[(j + 1) * MAXM + j] = T(0);
                     g[j + 1] = -sn[j] * g[j];
                     g[j] = cs[j] * g[j];
                     p.it += 1;
@@ -554,10 +560,11 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
                         p.bad = 1;
                         p.done = 1;
                         p.in_cycle = 0;
-                    } else if (fabs(g[j + 1]) <= p.tol_in || p.it >= A.maxit || hn <= 1e-300 || j + 1 == A.m) {
+                    } else if (fabs(g[j + 1]) <= (T)p.tol_in || p.it >= A.maxit || hn <= T(kF32 ? 1e-30 : 1e-300) ||
+                               j + 1 == A.m) {
                         p.in_cycle = 0;
                     } else {
-                        sm.sig[tid][j + 1] = 1.0 / hn;
+                        sm.sig[tid][j + 1] = T(1) / hn;
                     }
                 }
                 __syncthreads();
@@ -568,17 +575,16 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
             if (tid < NS) {
                 SpState &p = sm.sp[tid];
                 if (!p.bad && p.k > 0) {
-                    const double *H = sm.H[tid];
-                    double *y = sm.coef[tid];
+                    const T *H = sm.H[tid];
+                    T *y = kF32 ? (T *)sm.coef32[tid] : (T *)sm.coef[tid];
                     for (int i = p.k - 1; i >= 0; --i) {
-                        double acc = sm.g[tid][i];
+                        T acc = sm.g[tid][i];
                         for (int l = i + 1; l < p.k; ++l) acc -= H[i * MAXM + l] * y[l];
                         y[i] = acc / H[i * MAXM + i];
                     }
                     bool fin = true;
                     for (int i = 0; i < p.k; ++i) {
                         y[i] *= sm.sig[tid][i];
-                        sm.coef32[tid][i] = (float)y[i];
                         fin &= isfinite(y[i]) != 0;
                     }
                     if (!fin) { p.status = MPM_ERR_BREAKDOWN; p.bad = 1; p.done = 1; }
@@ -619,7 +625,7 @@ typedef void (*KernFn)(SolveArgs);
 template <typename T, int MAXM, int U, int MINB>
 static KernFn kfn(size_t &smem)
 {
-    smem = sizeof(Smem<MAXM>);
+    smem = sizeof(Smem<MAXM, T>);
     return k_gmres<T, MAXM, U, MINB>;
 }
 
