@@ -473,6 +473,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "path": "mixed: FP32 GMRES(8) inside FP64 refinement, inner cycle to max(tol/4, 1e-6 ||r||)",
+                       "step": "mpm_step: one CUDA graph per step (cooperative extraction + assembly, persistent GMRES, scatter)",
                        "l2": "flushed (256 MB write) before every timed step; lattice (486 MB) > L2",
                        "box_voxels": head["box_voxels"], "mask_voxels": head["mask_voxels"],
                        "stored_voxels": head["stored_voxels"], "parallelism": f"replicas x{world}"},
