@@ -249,6 +249,22 @@ mpm_status mpm_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, cons
                     const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, void *stream);
 
 /*
+ * mpm_step in two halves, so that a caller can queue steps back to back and
+ * keep the host's own work off the device's timeline.  mpm_step_enqueue
+ * queues one step on `stream` and returns (the first call, or one whose
+ * arguments changed, also builds the graph and synchronises `stream` while
+ * doing so); it does not wait for the step.  mpm_step_wait synchronises
+ * `stream` and reports the LAST step enqueued on `sub` (rep, out_box and the
+ * status as mpm_step returns them; MPM_ERR_ARG if none is pending).  The
+ * solver grid is re-planned only from results that were waited for.  The
+ * caller must not change the lattice between a step's enqueue and its
+ * completion except by stream-ordered work on `stream`.
+ */
+mpm_status mpm_step_enqueue(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                            int32_t margin, const int32_t tile[3], const mpm_opts *opt, void *stream);
+mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, void *stream);
+
+/*
  * Autotuner, tile shape: among the candidate shapes 8x4x4, 8x8x4, 4x4x4,
  * 8x4x2, 16x4x2, 8x8x2, 4x4x2, 16x4x4 pick the one whose active tiles store
  * the fewest voxels for this lattice's box (ties: the larger tile), counted
@@ -337,8 +353,10 @@ mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *
  *                        partners' waits run out (-1 = none, the default).
  *  MPM_DEBUG_PHASE_TIMES 1: CTA 0 of every later solve records where its time
  *                        went (read with the MPM_COUNTER_PHASE_* counters).
- *  MPM_DEBUG_SOLVER_VARIANT  solver kernel variant 0..3 (elements in flight per
- *                        thread and CTAs per SM; 0 = default), for tuning. */
+ *  MPM_DEBUG_SOLVER_VARIANT  solver kernel variant 0..4 (elements in flight per
+ *                        thread, CTAs per SM, threads per CTA; 0 = default;
+ *                        a bucket without the variant uses its default), for
+ *                        tuning. */
 #define MPM_DEBUG_TIMEOUT_NS 1
 #define MPM_DEBUG_SKIP_BLOCK 2
 #define MPM_DEBUG_PHASE_TIMES 3
@@ -366,6 +384,10 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
 #define MPM_COUNTER_PHASE_P1_NS 7
 #define MPM_COUNTER_PHASE_P2_NS 8
 #define MPM_COUNTER_PHASE_U_NS 9
+/* mpm_step only: time of the extraction (up to the grid barrier that ends it)
+ * and of the wait for the last team plus the scatter, on CTA 0. */
+#define MPM_COUNTER_PHASE_EXTRACT_NS 12
+#define MPM_COUNTER_PHASE_SCATTER_NS 13
 mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value);
 
 /*

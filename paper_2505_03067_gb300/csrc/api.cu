@@ -216,6 +216,21 @@ mpm_status mpm_step(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, cons
     return mpm_step_impl(ctx, sub, lat, prm, margin, tile, opt, rep, out_box, (cudaStream_t)stream);
 }
 
+mpm_status mpm_step_enqueue(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                            int32_t margin, const int32_t tile[3], const mpm_opts *opt, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_step_enqueue_impl(ctx, sub, lat, prm, margin, tile, opt, (cudaStream_t)stream);
+}
+
+mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_step_wait_impl(ctx, sub, rep, out_box, (cudaStream_t)stream);
+}
+
 mpm_status mpm_subgrid_export(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst, void *stream)
 {
     if (!ctx) return MPM_ERR_ARG;
@@ -260,7 +275,7 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value)
         ctx->phase_prof = value != 0;
         return MPM_OK;
     case MPM_DEBUG_SOLVER_VARIANT:
-        if (value < 0 || value > 3) return mpm_fail(ctx, MPM_ERR_ARG, "debug: solver variant out of [0, 3]");
+        if (value < 0 || value > 4) return mpm_fail(ctx, MPM_ERR_ARG, "debug: solver variant out of [0, 4]");
         ctx->solver_variant = (int32_t)value;
         return MPM_OK;
     default:
@@ -280,6 +295,10 @@ mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)
     }
     if (key >= MPM_COUNTER_PHASE_WAIT_NS && key <= MPM_COUNTER_PHASE_SERIAL_NS) {
         *value = (int64_t)ctx->h_prof[key - MPM_COUNTER_PHASE_WORK_NS];
+        return MPM_OK;
+    }
+    if (key == MPM_COUNTER_PHASE_EXTRACT_NS || key == MPM_COUNTER_PHASE_SCATTER_NS) {
+        *value = (int64_t)ctx->h_prof[key == MPM_COUNTER_PHASE_EXTRACT_NS ? 8 : 9];
         return MPM_OK;
     }
     if (key >= MPM_COUNTER_PHASE_R_NS && key <= MPM_COUNTER_PHASE_U_NS) {

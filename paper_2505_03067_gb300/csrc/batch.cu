@@ -17,38 +17,11 @@
 #include <cstring>
 
 #include "mpm_internal.cuh"
+#include "step_kernels.cuh"
 
 namespace mpm {
 
 constexpr int kEPT = 4;   // elements per thread
-
-struct BatchSys {
-    BoxGeo g;
-    int64_t NE;
-    const int32_t *tile_coord;
-    const int32_t *cell_id;     // lattice
-    const uint8_t *mask;        // lattice
-    const double *dfac_lat;     // lattice, or null
-    double *field[kMaxSpecies]; // lattice fields (read by the preparation, written by the scatter)
-    uint8_t *flags;
-    int32_t *cell;
-    double *dfac;
-    double *x[kMaxSpecies], *cn[kMaxSpecies], *b[kMaxSpecies], *diag[kMaxSpecies];
-    float *diag32[kMaxSpecies];
-    int32_t *err;
-    const int32_t *tile_index;  // device-resident step: the neighbour table is built here
-    int32_t *nbr;
-    const double *dk, *dq;      // device-resident step: per (species, cell) 1 + dt (mu + k), dt q
-    AsmCoef C;
-};
-
-// Per-CTA tables of the device-resident preparation (uniform D): a D_s n for
-// n open faces plus box faces counted twice (0..12), and 2 a D_s c_bc,s n
-// for n box faces (0..6).
-struct RowTab {
-    double aDn[kMaxSpecies][13];
-    double wbn[kMaxSpecies][7];
-};
 
 // Descriptor buffer: int64 first_block[nsys + 1], then BatchSys[nsys].
 __host__ __device__ __forceinline__ size_t desc_off(int32_t nsys)
@@ -71,97 +44,6 @@ __global__ void k_batch_reset_err(const char *__restrict__ buf, int nsys)
 {
     const BatchSys *D = reinterpret_cast<const BatchSys *>(buf + desc_off(nsys));
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x) *D[i].err = 0;
-}
-
-// One element of the fused preparation: flags, cell id, diffusivity factor
-// and c^n gathered from the lattice, then the row of every species.
-// kTab: the device-resident form (rows from the rate tables; tile coordinates
-// and tables written earlier in the same kernel, so read through L2).
-template <bool kTab>
-__device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, int64_t e, const RowTab *tab = nullptr)
-{
-    const int ns = S.C.nspecies;
-    int bx, by, bz;
-    if (!elem_box<kTab>(e, g, S.tile_coord, bx, by, bz)) {   // tile padding
-        S.flags[e] = 0;
-        S.cell[e] = 0;
-        if (S.dfac) S.dfac[e] = 1.0;
-        for (int s = 0; s < ns; ++s) {
-            S.x[s][e] = 0.0;
-            S.cn[s][e] = 0.0;
-            S.diag[s][e] = 1.0;
-            S.diag32[s][e] = 1.0f;
-            S.b[s][e] = 0.0;
-        }
-        return;
-    }
-    const int64_t sy = g.Lx, sz = (int64_t)g.Lx * g.Ly;
-    const int64_t L = (int64_t)(g.lo[0] + bx) + sy * (g.lo[1] + by) + sz * (g.lo[2] + bz);
-    uint32_t f = F_BOX;
-    if (__ldg(S.mask + L)) {
-        f |= F_MASK;
-        if (bx > 0 && __ldg(S.mask + L - 1)) f |= F_MX;
-        if (bx < g.n[0] - 1 && __ldg(S.mask + L + 1)) f |= F_PX;
-        if (by > 0 && __ldg(S.mask + L - sy)) f |= F_MY;
-        if (by < g.n[1] - 1 && __ldg(S.mask + L + sy)) f |= F_PY;
-        if (bz > 0 && __ldg(S.mask + L - sz)) f |= F_MZ;
-        if (bz < g.n[2] - 1 && __ldg(S.mask + L + sz)) f |= F_PZ;
-    }
-    S.flags[e] = (uint8_t)f;
-    int32_t id = __ldg(S.cell_id + L);
-    S.cell[e] = id;
-    const double fp = S.dfac_lat ? __ldg(S.dfac_lat + L) : 1.0;
-    if (S.dfac) S.dfac[e] = fp;
-    if (!(f & F_MASK)) {                        // identity row keeping c^n
-        for (int s = 0; s < ns; ++s) {
-            const double c = __ldg(S.field[s] + L);
-            S.x[s][e] = c;
-            S.cn[s][e] = c;
-            S.diag[s][e] = 1.0;
-            S.diag32[s][e] = 1.0f;
-            S.b[s][e] = c;
-        }
-        return;
-    }
-    if (id < 0 || id >= S.C.ncell) {
-        atomicOr(S.err, 1);
-        id = 0;
-    }
-    const int ndir = S.C.bc_box == 0 ? (bx == 0) + (bx == g.n[0] - 1) + (by == 0) + (by == g.n[1] - 1) +
-                                           (bz == 0) + (bz == g.n[2] - 1)
-                                     : 0;
-    auto dq = [&](int d) -> double {
-        const int64_t o = d == 0 ? -1 : d == 1 ? 1 : d == 2 ? -sy : d == 3 ? sy : d == 4 ? -sz : sz;
-        return __ldg(S.dfac_lat + L + o);
-    };
-    for (int s = 0; s < ns; ++s) {
-        const double c = __ldg(S.field[s] + L);
-        double dg, bb;
-        if (kTab && !S.dfac) {
-            // the rows of assemble_row with the per-cell and per-count products
-            // taken from tables: three FP64 additions per species
-            const int64_t k = (int64_t)s * S.C.ncell + id;
-            dg = __ldcg(S.dk + k) + tab->aDn[s][__popc(f & F_OPEN) + 2 * ndir];
-            bb = (c + __ldcg(S.dq + k)) + tab->wbn[s][ndir];
-        } else {
-            assemble_row(S.C, s, f, id, ndir, S.dfac != nullptr, fp, dq, c, dg, bb);
-        }
-        S.x[s][e] = c;
-        S.cn[s][e] = c;
-        S.diag[s][e] = dg;
-        S.diag32[s][e] = (float)dg;
-        S.b[s][e] = bb;
-    }
-}
-
-// Sec. 2.4: the box solution onto the pleural mask (in-mask voxels only).
-__device__ __forceinline__ void scatter_elem(const BatchSys &S, const BoxGeo &g, int64_t e)
-{
-    if (!(S.flags[e] & F_MASK)) return;
-    int bx, by, bz;
-    elem_box(e, g, S.tile_coord, bx, by, bz);
-    const int64_t L = (int64_t)(g.lo[0] + bx) + (int64_t)g.Lx * ((g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
-    for (int s = 0; s < S.C.nspecies; ++s) S.field[s][L] = S.x[s][e];
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_prep(const char *__restrict__ buf, int nsys)
@@ -194,344 +76,6 @@ __global__ void __launch_bounds__(kBlock) k_batch_scatter(const char *__restrict
 // first element of each tile), and the scatter's CTA 0 copies the step's
 // results to host-mapped memory and resets the box and count slots for the
 // next step (so the graph has no memset or copy nodes).
-// Per-(species, cell) rate terms of the rows (Eq. 1-4) for the device-resident
-// preparation: dk = 1 + dt (mu_s + k_cell[s][id]), dq = dt q_cell[s][id].
-struct RateArgs {
-    int32_t nspecies, ncell;
-    double dt;
-    double mu[kMaxSpecies];
-    const double *k_cell, *q_cell;
-    double *dk, *dq;
-};
-
-struct ExtractArgs {
-    const int32_t *cell_id;
-    const uint8_t *mask;
-    int32_t L[3], lt[3], margin, vec4;
-    int32_t *part_box;                 // [grid][8]: per-CTA min[3], max[3]
-    unsigned long long *part_cnt;      // [grid][2]: per-CTA mask voxels, active tiles
-    uint32_t *bar;                     // grid barrier counter (zero at launch)
-    int32_t *xabort;                   // set when a grid barrier gave up
-    uint64_t timeout_ns;
-    int32_t *box_out;                  // raw min[3], max[3] (for the host)
-    BoxGeo *geo_out;
-    unsigned long long *count_out;     // mask voxels, active tiles (for the host)
-    StepDyn *dyn;
-    int8_t *active;
-    int32_t *tile_index, *tile_coord, *err;
-    uint32_t *sbar;                    // the solver's barrier counters, abort flag and reports: zeroed here
-    int32_t nsbar;
-    int32_t *sabort;
-    uint32_t *srep;
-    int32_t nrep_words;
-    RateArgs ra;
-};
-
-constexpr int kXB = 1024;   // threads per CTA of the cooperative extraction
-
-// Block-wide sum of 1024 threads (every thread gets the total).
-__device__ __forceinline__ unsigned long long xblock_sum(unsigned long long v, unsigned long long *sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-    for (int i = 0; i < kXB / 32; ++i) t += sh[i];
-    return t;
-}
-
-// The extraction and preparation of the device-resident step as one
-// cooperative kernel: phases separated by bounded grid barriers, partial
-// results per CTA (no atomics, so every count is deterministic).
-//   A  bounding box of cell_id > 0 (Sec. 2.3): per-CTA min / max
-//   B  box from all partials (every CTA); tile activity of the box rows and
-//      the in-mask count; rate tables
-//   C  active tiles per CTA chunk of the box tiles
-//   D  compaction: chunk offsets from the partial counts, compact index and
-//      coordinates of every tile, activity bytes cleared for the next step;
-//      the solver's counters zeroed
-//   E  the gather and rows of every stored element (Eq. 1-4) and the tile
-//      neighbour table; the element count is published for the solver last,
-//      so a barrier that gave up leaves it at zero (nothing is solved).
-__global__ void __launch_bounds__(kXB, 1) k_extract_step(const __grid_constant__ ExtractArgs A,
-                                                         const __grid_constant__ BatchSys S)
-{
-    __shared__ int32_t smm[6][kXB / 32];
-    __shared__ unsigned long long ssum[kXB / 32];
-    __shared__ BoxGeo g;
-    __shared__ RowTab tab;
-    __shared__ int32_t wtot[kXB / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nb = gridDim.x, b = blockIdx.x;
-    uint32_t epoch = 0;
-    if (b == 0 && tid == 0) { A.dyn->NE = 0; A.dyn->g.n[0] = 0; }
-    // ---- A: bounding box, per CTA
-    {
-        const int64_t Ltot = (int64_t)A.L[0] * A.L[1] * A.L[2];
-        const uint32_t Lx = (uint32_t)A.L[0], Lxy = (uint32_t)(A.L[0] * A.L[1]);
-        int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {-1, -1, -1};
-        const uint32_t t0 = b * kXB + tid, nth = nb * kXB;
-        uint32_t done = 0;
-        if (A.vec4) {
-            const int4 *c4 = reinterpret_cast<const int4 *>(A.cell_id);
-            const uint32_t n4 = (uint32_t)(Ltot / 4);
-            uint32_t q = t0;
-            for (; q + 3 * nth < n4; q += 4 * nth) {
-                int4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = __ldcs(c4 + q + u * nth);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if ((v[u].x > 0) | (v[u].y > 0) | (v[u].z > 0) | (v[u].w > 0)) {
-                        const uint32_t e = 4 * (q + u * nth);
-                        if (v[u].x > 0) bbox_upd(e + 0, Lx, Lxy, mn, mx);
-                        if (v[u].y > 0) bbox_upd(e + 1, Lx, Lxy, mn, mx);
-                        if (v[u].z > 0) bbox_upd(e + 2, Lx, Lxy, mn, mx);
-                        if (v[u].w > 0) bbox_upd(e + 3, Lx, Lxy, mn, mx);
-                    }
-                }
-            }
-            for (; q < n4; q += nth) {
-                const int4 v = __ldcs(c4 + q);
-                const uint32_t e = 4 * q;
-                if (v.x > 0) bbox_upd(e + 0, Lx, Lxy, mn, mx);
-                if (v.y > 0) bbox_upd(e + 1, Lx, Lxy, mn, mx);
-                if (v.z > 0) bbox_upd(e + 2, Lx, Lxy, mn, mx);
-                if (v.w > 0) bbox_upd(e + 3, Lx, Lxy, mn, mx);
-            }
-            done = n4 * 4;
-        }
-        for (uint32_t e = done + t0; e < (uint32_t)Ltot; e += nth)
-            if (__ldcs(A.cell_id + e) > 0) bbox_upd(e, Lx, Lxy, mn, mx);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int lo = __reduce_min_sync(0xffffffffu, mn[d]);
-            const int hi = __reduce_max_sync(0xffffffffu, mx[d]);
-            if (lane == 0) { smm[d][warp] = lo; smm[3 + d][warp] = hi; }
-        }
-        __syncthreads();
-        if (tid < 6) {
-            int v = tid < 3 ? INT_MAX : -1;
-            for (int i = 0; i < kXB / 32; ++i) v = tid < 3 ? min(v, smm[tid][i]) : max(v, smm[tid][i]);
-            A.part_box[8 * b + tid] = v;
-        }
-    }
-    if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return;
-    // ---- B: the box (every CTA), tile activity, in-mask count, rate tables
-    {
-        int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {-1, -1, -1};
-        for (int i = tid; i < nb; i += kXB) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                mn[d] = min(mn[d], __ldcg(A.part_box + 8 * i + d));
-                mx[d] = max(mx[d], __ldcg(A.part_box + 8 * i + 3 + d));
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int lo = __reduce_min_sync(0xffffffffu, mn[d]);
-            const int hi = __reduce_max_sync(0xffffffffu, mx[d]);
-            if (lane == 0) { smm[d][warp] = lo; smm[3 + d][warp] = hi; }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int32_t mm[6];
-            for (int d = 0; d < 6; ++d) {
-                int v = d < 3 ? INT_MAX : -1;
-                for (int i = 0; i < kXB / 32; ++i) v = d < 3 ? min(v, smm[d][i]) : max(v, smm[d][i]);
-                mm[d] = v;
-            }
-            g = box_geo(mm, A.margin, A.L[0], A.L[1], A.L[2], A.lt[0], A.lt[1], A.lt[2]);
-            if (b == 0) {
-                for (int d = 0; d < 6; ++d) A.box_out[d] = mm[d];
-                *A.geo_out = g;
-            }
-        }
-        for (int i = tid; i < S.C.nspecies * 20; i += kXB) {   // per-CTA row tables (phase E)
-            const int s = i / 20, n = i % 20;
-            if (n < 13) tab.aDn[s][n] = S.C.a * S.C.D[s] * (double)n;
-            else tab.wbn[s][n - 13] = S.C.a * 2.0 * S.C.D[s] * S.C.cbc[s] * (double)(n - 13);
-        }
-        const int64_t nr = (int64_t)A.ra.nspecies * A.ra.ncell;
-        for (int64_t i = (int64_t)b * kXB + tid; i < nr; i += (int64_t)nb * kXB) {
-            const int s = (int)(i / A.ra.ncell);
-            A.ra.dk[i] = 1.0 + A.ra.dt * (A.ra.mu[s] + A.ra.k_cell[i]);
-            A.ra.dq[i] = A.ra.dt * A.ra.q_cell[i];
-        }
-        __syncthreads();
-        unsigned long long cnt = 0;
-        if (g.n[0] > 0) {
-            const int64_t gw = (int64_t)b * (kXB / 32) + warp, nw = (int64_t)nb * (kXB / 32);
-            const int64_t nrows = (int64_t)g.n[1] * g.n[2];
-            for (int64_t row = gw; row < nrows; row += nw) {
-                const int by = (int)(row % g.n[1]), bz = (int)(row / g.n[1]);
-                const int64_t L0 = (int64_t)g.lo[0] + (int64_t)g.Lx * ((int64_t)(g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
-                const int64_t trow = ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) * g.nt[0];
-                for (int bx = lane; bx < g.n[0]; bx += 32) {
-                    if (__ldg(A.mask + L0 + bx)) {
-                        ++cnt;
-                        A.active[trow + (bx >> g.lt[0])] = 1;
-                    }
-                }
-            }
-        }
-        cnt = xblock_sum(cnt, ssum);
-        if (tid == 0) A.part_cnt[2 * b + 0] = cnt;
-    }
-    if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return;
-    // ---- C: active tiles of this CTA's chunk (8-tile words)
-    const int32_t ntiles = g.n[0] > 0 ? g.nt[0] * g.nt[1] * g.nt[2] : 0;
-    const int32_t nwords = (ntiles + 7) >> 3;
-    const int32_t wchunk = (nwords + nb - 1) / nb;
-    const int32_t w0 = min(nwords, b * wchunk), w1 = min(nwords, w0 + wchunk);
-    unsigned long long *aw = reinterpret_cast<unsigned long long *>(A.active);
-    auto word = [&](int32_t wi) -> unsigned long long {
-        unsigned long long w = __ldcg(aw + wi);
-        const int32_t i0 = 8 * wi;
-        if (i0 + 8 > ntiles) w &= ~0ull >> (8 * (i0 + 8 - ntiles));
-        return w;
-    };
-    {
-        unsigned long long c = 0;
-        for (int32_t wi = w0 + tid; wi < w1; wi += kXB) c += __popcll(word(wi) & 0x0101010101010101ull);
-        c = xblock_sum(c, ssum);
-        if (tid == 0) A.part_cnt[2 * b + 1] = c;
-    }
-    if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return;
-    // ---- D: compaction
-    int64_t nact = 0;
-    {
-        unsigned long long before = 0, tot = 0, mtot = 0;
-        for (int i = tid; i < nb; i += kXB) {
-            const unsigned long long c = __ldcg(A.part_cnt + 2 * i + 1);
-            tot += c;
-            if (i < b) before += c;
-            mtot += __ldcg(A.part_cnt + 2 * i + 0);
-        }
-        before = xblock_sum(before, ssum);
-        tot = xblock_sum(tot, ssum);
-        mtot = xblock_sum(mtot, ssum);
-        nact = (int64_t)tot;
-        if (b == 0 && tid == 0) {
-            A.count_out[0] = mtot;
-            A.count_out[1] = tot;
-            *A.err = 0;
-            *A.sabort = 0;
-        }
-        if (b == 0) {
-            for (int i = tid; i < A.nsbar; i += kXB) A.sbar[i] = 0u;
-            for (int i = tid; i < A.nrep_words; i += kXB) A.srep[i] = 0u;
-        }
-        const int32_t nxy = g.nt[0] * g.nt[1];
-        int32_t carry = (int32_t)before;
-        for (int32_t base = w0; base < w1; base += kXB) {
-            const int32_t wi = base + tid;
-            const unsigned long long w = wi < w1 ? word(wi) : 0ull;
-            const int32_t c = __popcll(w & 0x0101010101010101ull);
-            int32_t incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            __syncthreads();
-            if (lane == 31) wtot[warp] = incl;
-            __syncthreads();
-            int32_t woff = 0, rtot = 0;
-            for (int i = 0; i < kXB / 32; ++i) {
-                const int32_t t = wtot[i];
-                if (i < warp) woff += t;
-                rtot += t;
-            }
-            int32_t idx = carry + woff + incl - c;
-            if (wi < w1) {
-                const int32_t i0 = 8 * wi;
-                int32_t tx = i0 % g.nt[0], ty = (i0 / g.nt[0]) % g.nt[1], tz = i0 / nxy;
-                for (int k = 0; k < 8; ++k) {
-                    const int32_t i = i0 + k;
-                    if (i >= ntiles) break;
-                    if ((w >> (8 * k)) & 1ull) {
-                        A.tile_index[i] = idx;
-                        reinterpret_cast<int4 *>(A.tile_coord)[idx] = make_int4(tx, ty, tz, 0);
-                        ++idx;
-                    } else {
-                        A.tile_index[i] = -1;
-                    }
-                    if (++tx == g.nt[0]) {
-                        tx = 0;
-                        if (++ty == g.nt[1]) { ty = 0; ++tz; }
-                    }
-                }
-                aw[wi] = 0ull;   // activity cleared for the next step
-            }
-            carry += rtot;
-        }
-    }
-    if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return;
-    // ---- E: gather + rows of every stored element, neighbour table
-    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
-    const int64_t NE = g.n[0] > 0 ? nact << ltv : 0;
-    for (int64_t e = (int64_t)b * kXB + tid; e < NE; e += (int64_t)nb * kXB) {
-        prep_elem<true>(S, g, e, &tab);
-        if ((e & ((1 << ltv) - 1)) == 0) {          // neighbour tiles of this tile
-            const int64_t a = e >> ltv;
-            const int4 c = __ldcg(reinterpret_cast<const int4 *>(S.tile_coord) + a);
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                int32_t q[3] = {c.x, c.y, c.z};
-                q[d >> 1] += (d & 1) ? 1 : -1;
-                int32_t r = -1;
-                if (q[0] >= 0 && q[0] < g.nt[0] && q[1] >= 0 && q[1] < g.nt[1] && q[2] >= 0 && q[2] < g.nt[2])
-                    r = __ldcg(S.tile_index + (q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]);
-                S.nbr[6 * a + d] = r;
-            }
-        }
-    }
-    if (b == 0 && tid == 0) {
-        A.dyn->g = g;
-        A.dyn->NE = NE;
-    }
-}
-
-struct StepOut {
-    const int32_t *box;            // raw min[3], max[3]
-    const unsigned long long *count;   // mask voxels, active tiles
-    const int32_t *abort_flag;
-    const int32_t *xabort;         // the extraction's grid barrier gave up
-    uint32_t *xbar;                // the extraction's barrier counter: zeroed for the next step
-    const uint32_t *reports;
-    int32_t nrep_words;
-    char *host;                    // host-mapped: box at 0, counts at 64, abort at 128, reports at 256
-};
-
-__global__ void __launch_bounds__(kBlock) k_step_scatter(const __grid_constant__ BatchSys S,
-                                                         const StepDyn *__restrict__ D, StepOut o)
-{
-    // a timed-out solve or extraction leaves the lattice as it was
-    const bool aborted = *o.abort_flag != 0 || *o.xabort != 0;
-    if (blockIdx.x == 0) {
-        int32_t *hb = reinterpret_cast<int32_t *>(o.host);
-        unsigned long long *hc = reinterpret_cast<unsigned long long *>(o.host + 64);
-        uint32_t *hr = reinterpret_cast<uint32_t *>(o.host + 256);
-        if (threadIdx.x < 6) hb[threadIdx.x] = o.box[threadIdx.x];
-        if (threadIdx.x < 2) hc[threadIdx.x] = o.count[threadIdx.x];
-        if (threadIdx.x == 0) {
-            *reinterpret_cast<int32_t *>(o.host + 128) = *o.abort_flag;
-            *reinterpret_cast<int32_t *>(o.host + 132) = *o.xabort;
-            *o.xbar = 0u;
-        }
-        for (int i = threadIdx.x; i < o.nrep_words; i += blockDim.x) hr[i] = o.reports[i];
-    }
-    if (aborted) return;
-    const int64_t NE = D->NE;
-    const BoxGeo g = D->g;
-    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < NE; e += (int64_t)gridDim.x * kBlock)
-        scatter_elem(S, g, e);
-}
-
 }  // namespace mpm
 
 using namespace mpm;
@@ -624,111 +168,3 @@ mpm_status mpm_batch_scatter_launch(mpm_ctx *ctx, const void *d_desc, int32_t ns
     return MPM_OK;
 }
 
-// Static descriptor of a device-resident step (host image, passed by value).
-static BatchSys step_sys(mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, const double *d_rates)
-{
-    BatchSys S;
-    memset(&S, 0, sizeof(S));
-    S.tile_coord = sub->tile_coord;
-    S.cell_id = lat->cell_id;
-    S.mask = lat->mask;
-    S.dfac_lat = lat->dfac;
-    S.flags = sub->flags;
-    S.cell = sub->cell;
-    S.dfac = sub->dfac;
-    for (int s = 0; s < sub->nspecies; ++s) {
-        S.field[s] = lat->field[s];
-        S.x[s] = sub->x[s];
-        S.cn[s] = sub->cn[s];
-        S.b[s] = sub->b[s];
-        S.diag[s] = sub->diag[s];
-        S.diag32[s] = sub->diag32[s];
-    }
-    S.err = sub->err;
-    S.tile_index = sub->tile_index;
-    S.nbr = sub->nbr;
-    S.dk = d_rates;
-    S.dq = d_rates ? d_rates + (size_t)prm->nspecies * prm->ncell : nullptr;
-    mpm_asm_coef(prm, &S.C);
-    return S;
-}
-
-// Scratch of the cooperative extraction for a grid of nb CTAs: per-CTA box
-// partials (32 B), count partials (16 B), then the barrier counter and the
-// abort flag (256 B each).
-size_t mpm_step_xscr_bytes(int nb) { return (size_t)nb * 48 + 512 + 256; }
-
-int mpm_step_extract_grid(mpm_ctx *ctx)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_extract_step, kXB, 0) != cudaSuccess ||
-        per_sm < 1)
-        return 0;
-    return ctx->num_sms;   // one CTA per SM
-}
-
-mpm_status mpm_step_extract_launch(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
-                                   int32_t margin, int nb, char *d_xscr, int32_t *d_box, int64_t *d_count,
-                                   void *d_dyn, uint32_t *d_sbar, int32_t nsbar, int32_t *d_sabort, void *d_reports,
-                                   size_t report_bytes, double *d_rates, cudaStream_t st)
-{
-    const BatchSys S = step_sys(sub, lat, prm, d_rates);
-    ExtractArgs A;
-    memset(&A, 0, sizeof(A));
-    A.cell_id = lat->cell_id;
-    A.mask = lat->mask;
-    for (int d = 0; d < 3; ++d) { A.L[d] = lat->dims[d]; A.lt[d] = sub->lt[d]; }
-    A.margin = margin;
-    A.vec4 = ((uintptr_t)lat->cell_id % 16) == 0;
-    A.part_box = (int32_t *)d_xscr;
-    A.part_cnt = (unsigned long long *)(d_xscr + (size_t)nb * 32);
-    A.bar = (uint32_t *)(d_xscr + (size_t)nb * 48 + 256);
-    A.xabort = (int32_t *)(d_xscr + (size_t)nb * 48 + 512);
-    A.timeout_ns = ctx->timeout_ns;
-    A.box_out = d_box;
-    A.geo_out = (BoxGeo *)(d_box + 8);
-    A.count_out = (unsigned long long *)d_count;
-    A.dyn = (StepDyn *)d_dyn;
-    A.active = sub->active;
-    A.tile_index = sub->tile_index;
-    A.tile_coord = sub->tile_coord;
-    A.err = sub->err;
-    A.sbar = d_sbar;
-    A.nsbar = nsbar;
-    A.sabort = d_sabort;
-    A.srep = (uint32_t *)d_reports;
-    A.nrep_words = (int32_t)(report_bytes / 4);
-    A.ra.nspecies = prm->nspecies;
-    A.ra.ncell = prm->ncell;
-    A.ra.dt = prm->dt;
-    for (int s = 0; s < prm->nspecies; ++s) A.ra.mu[s] = prm->mu[s];
-    A.ra.k_cell = prm->k_cell;
-    A.ra.q_cell = prm->q_cell;
-    A.ra.dk = d_rates;
-    A.ra.dq = d_rates + (size_t)prm->nspecies * prm->ncell;
-    void *kargs[] = {(void *)&A, (void *)&S};
-    MPM_CU(cudaLaunchCooperativeKernel((const void *)k_extract_step, dim3(nb), dim3(kXB), kargs, 0, st));
-    ctx->launches += 1;
-    return MPM_OK;
-}
-
-mpm_status mpm_step_scatter_launch(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
-                                   const void *d_dyn, const int32_t *d_box, const int64_t *d_count,
-                                   const int32_t *d_abort, int nb, char *d_xscr, const void *d_reports,
-                                   size_t report_bytes, void *h_mapped, cudaStream_t st)
-{
-    const BatchSys S = step_sys(sub, lat, prm, nullptr);
-    StepOut o;
-    o.box = d_box;
-    o.count = (const unsigned long long *)d_count;
-    o.abort_flag = d_abort;
-    o.xbar = (uint32_t *)(d_xscr + (size_t)nb * 48 + 256);
-    o.xabort = (const int32_t *)(d_xscr + (size_t)nb * 48 + 512);
-    o.reports = (const uint32_t *)d_reports;
-    o.nrep_words = (int32_t)(report_bytes / 4);
-    o.host = (char *)h_mapped;
-    k_step_scatter<<<ctx->num_sms * 8, kBlock, 0, st>>>(S, (const StepDyn *)d_dyn, o);
-    ctx->launches += 1;
-    MPM_CU(cudaGetLastError());
-    return MPM_OK;
-}

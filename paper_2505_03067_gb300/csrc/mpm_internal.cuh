@@ -29,6 +29,7 @@ constexpr uint32_t F_BOX = 128u;   // voxel lies inside the box (not tile paddin
 
 constexpr int kBlock = 256;        // threads per CTA of every kernel
 constexpr int kWarps = kBlock / 32;
+constexpr int kProfSlots = 10;      // phase timer: [-, wait, reduce, serial, R, P1, P2, U, extract, scatter]
 constexpr int kMaxSpecies = MPM_MAX_SPECIES;
 constexpr int kMaxM = MPM_MAX_RESTART;
 constexpr int kKStride = kMaxM + 2;           // partial slots per species
@@ -381,7 +382,7 @@ struct mpm_ctx {
     void *d_tune = nullptr;      // tuner scratch tables
     size_t tune_cap = 0;
     unsigned long long *d_prof = nullptr;
-    unsigned long long h_prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long h_prof[16] = {};   // phase timer slots (kProfSlots used)
     double last_imbalance = 0.0; // t_max / <t> - 1 over the teams of the last solve
     // test hooks
     uint64_t timeout_ns = 2000000000ull;
@@ -462,17 +463,6 @@ mpm_status mpm_batch_desc_fill(mpm_subgrid *const *subs, const mpm_lattice *cons
                                const mpm_params *const *prms, int32_t nsys, void *host, int64_t *nblocks);
 mpm_status mpm_batch_prep_launch(mpm_ctx *ctx, const void *d_desc, int32_t nsys, int64_t nblocks, cudaStream_t st);
 mpm_status mpm_batch_scatter_launch(mpm_ctx *ctx, const void *d_desc, int32_t nsys, int64_t nblocks, cudaStream_t st);
-// single system with the box and element count known only on the device (batch.cu)
-size_t mpm_step_xscr_bytes(int nb);
-int mpm_step_extract_grid(mpm_ctx *ctx);
-mpm_status mpm_step_extract_launch(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
-                                   int32_t margin, int nb, char *d_xscr, int32_t *d_box, int64_t *d_count,
-                                   void *d_dyn, uint32_t *d_sbar, int32_t nsbar, int32_t *d_sabort, void *d_reports,
-                                   size_t report_bytes, double *d_rates, cudaStream_t st);
-mpm_status mpm_step_scatter_launch(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
-                                   const void *d_dyn, const int32_t *d_box, const int64_t *d_count,
-                                   const int32_t *d_abort, int nb, char *d_xscr, const void *d_reports,
-                                   size_t report_bytes, void *h_mapped, cudaStream_t st);
 // extraction with buffers sized for the whole lattice and no host round trip (extract.cu)
 mpm_status mpm_step_buffers(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, int32_t nspecies, const int32_t lt[3]);
 
@@ -491,6 +481,9 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
 void mpm_batch_graph_free(mpm_ctx *ctx);
 mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
                          const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, cudaStream_t st);
+mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                                 int32_t margin, const int32_t tile[3], const mpm_opts *opt, cudaStream_t st);
+mpm_status mpm_step_wait_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, cudaStream_t st);
 void mpm_step_free(mpm_ctx *ctx, mpm_subgrid *sub);
 void mpm_step_invalidate(mpm_subgrid *sub);
 int mpm_batch_graph_active(mpm_ctx *ctx);

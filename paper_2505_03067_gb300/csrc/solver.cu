@@ -31,13 +31,13 @@
 #include <algorithm>
 
 #include "mpm_internal.cuh"
+#include "step_kernels.cuh"
 
 namespace mpm {
 
 enum { ST_RUN = -1 };
 
-constexpr int kSB = 512;            // solver CTA size (16 warps)
-constexpr int kSW = kSB / 32;
+constexpr int kSB = 512;            // default solver CTA size (16 warps); variants also use 1024
 
 struct SpState {
     double beta, bnorm, tol, tol_in;
@@ -53,14 +53,14 @@ struct SpState {
 // on the FP32-Krylov path, whose inner solve only has to reach about 1e-6
 // relative (the FP64 residual pass decides convergence), FP64 otherwise.  On
 // GB300 every FP64 instruction of this one-thread section costs tens of cycles.
-template <int MAXM, typename G>
+template <int MAXM, typename G, int NT>
 struct Smem {
     G H[kMaxSpecies][(MAXM + 1) * MAXM];
     G cs[kMaxSpecies][MAXM], sn[kMaxSpecies][MAXM];
     G g[kMaxSpecies][MAXM + 1], sig[kMaxSpecies][MAXM + 1];
     double coef[kMaxSpecies][MAXM + 1];
     float coef32[kMaxSpecies][MAXM + 1];
-    double red[kSW][kKMax];
+    double red[NT / 32][kKMax];
     double tot[kKMax];
     SpState sp[kMaxSpecies];
     SysDev sys;
@@ -76,7 +76,7 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
 // CTA reduction of the group's values acc[g][i] (g active in gm, i < cnt): warp
 // sums in the accumulator type, cross-warp sum in FP64 in a fixed order; the
 // CTA total of species s0+g, value i lands in out[(s0+g)*kKStride + i].
-template <int NSG, int N, typename AccT>
+template <int NSG, int N, typename AccT, int NT>
 __device__ __forceinline__ void block_reduce_g(const AccT (&acc)[NSG][N], uint32_t gm, int cnt, int s0,
                                                double (*red)[kKMax], double *out)
 {
@@ -93,13 +93,13 @@ __device__ __forceinline__ void block_reduce_g(const AccT (&acc)[NSG][N], uint32
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < NSG * kKStride; t += kSB) {
+    for (int t = threadIdx.x; t < NSG * kKStride; t += NT) {
         const int g = t / kKStride, i = t - g * kKStride;
         if (!((gm >> g) & 1u) || i >= cnt) continue;
         const int slot = (s0 + g) * kKStride + i;
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < kSW; ++q) s += red[q][slot];
+        for (int q = 0; q < NT / 32; ++q) s += red[q][slot];
         out[slot] = s;
     }
     __syncthreads();
@@ -107,12 +107,13 @@ __device__ __forceinline__ void block_reduce_g(const AccT (&acc)[NSG][N], uint32
 
 // Team sum of the slots s*kKStride + i (i < cnt) of the species in smask, in a
 // fixed order (lane l adds blocks l, l+32, ...; then a fixed shuffle tree).
+template <int NT>
 __device__ __forceinline__ void team_reduce(const double *part, int b0, int nb, uint32_t smask, int cnt,
                                             double *tot)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nslot = kMaxSpecies * cnt;
-    for (int q = w; q < nslot; q += kSW) {
+    for (int q = w; q < nslot; q += NT / 32) {
         const int s = q / cnt, i = q - s * cnt;
         if (!((smask >> s) & 1u)) continue;
         const int slot = s * kKStride + i;
@@ -138,6 +139,12 @@ __device__ __forceinline__ const double *diag_of<double>(const SysDev &S, int s)
 template <>
 __device__ __forceinline__ const float *diag_of<float>(const SysDev &S, int s) { return S.diag32[s]; }
 
+// Loads of data written before the solve (face flags, rows, neighbour table,
+// diffusivity factors): plain cached loads, not the read-only path -- in the
+// device-resident step the same kernel wrote them before a grid barrier.
+template <typename T>
+__device__ __forceinline__ T ldro(const T *p) { return *p; }
+
 // Neighbour elements of e for its open faces (closed faces get e; never read).
 __device__ __forceinline__ void nbr_elems(const int32_t *__restrict__ nbr, uint32_t e, uint32_t f, int ltx, int lty,
                                           int ltz, uint32_t (&q)[6])
@@ -148,12 +155,12 @@ __device__ __forceinline__ void nbr_elems(const int32_t *__restrict__ nbr, uint3
     const uint32_t TX = 1u << ltx, TY = 1u << lty, TZ = 1u << ltz;
     const uint32_t ix = v & (TX - 1), iy = (v >> ltx) & (TY - 1), iz = v >> (ltx + lty);
     const uint32_t tb = tile << ltv;
-    q[0] = !(f & F_MX) ? e : (ix > 0 ? e - 1 : ((uint32_t)__ldg(nbr + tile * 6 + 0) << ltv) + (v + TX - 1));
-    q[1] = !(f & F_PX) ? e : (ix < TX - 1 ? e + 1 : ((uint32_t)__ldg(nbr + tile * 6 + 1) << ltv) + (v - (TX - 1)));
-    q[2] = !(f & F_MY) ? e : (iy > 0 ? e - TX : ((uint32_t)__ldg(nbr + tile * 6 + 2) << ltv) + (v + (TY - 1) * TX));
-    q[3] = !(f & F_PY) ? e : (iy < TY - 1 ? e + TX : ((uint32_t)__ldg(nbr + tile * 6 + 3) << ltv) + (v - (TY - 1) * TX));
-    q[4] = !(f & F_MZ) ? e : (iz > 0 ? e - TX * TY : ((uint32_t)__ldg(nbr + tile * 6 + 4) << ltv) + (v + (TZ - 1) * TX * TY));
-    q[5] = !(f & F_PZ) ? e : (iz < TZ - 1 ? e + TX * TY : ((uint32_t)__ldg(nbr + tile * 6 + 5) << ltv) + (v - (TZ - 1) * TX * TY));
+    q[0] = !(f & F_MX) ? e : (ix > 0 ? e - 1 : ((uint32_t)ldro(nbr + tile * 6 + 0) << ltv) + (v + TX - 1));
+    q[1] = !(f & F_PX) ? e : (ix < TX - 1 ? e + 1 : ((uint32_t)ldro(nbr + tile * 6 + 1) << ltv) + (v - (TX - 1)));
+    q[2] = !(f & F_MY) ? e : (iy > 0 ? e - TX : ((uint32_t)ldro(nbr + tile * 6 + 2) << ltv) + (v + (TY - 1) * TX));
+    q[3] = !(f & F_PY) ? e : (iy < TY - 1 ? e + TX : ((uint32_t)ldro(nbr + tile * 6 + 3) << ltv) + (v - (TY - 1) * TX));
+    q[4] = !(f & F_MZ) ? e : (iz > 0 ? e - TX * TY : ((uint32_t)ldro(nbr + tile * 6 + 4) << ltv) + (v + (TZ - 1) * TX * TY));
+    q[5] = !(f & F_PZ) ? e : (iz < TZ - 1 ? e + TX * TY : ((uint32_t)ldro(nbr + tile * 6 + 5) << ltv) + (v - (TZ - 1) * TX * TY));
     (void)tb;
 }
 
@@ -187,12 +194,12 @@ template <typename T>
 __device__ __forceinline__ T open_sum_var(const T *__restrict__ u, const double *__restrict__ dfac, uint32_t e,
                                           uint32_t f, const uint32_t (&q)[6], double Ds)
 {
-    const double dp = Ds * __ldg(dfac + e);
+    const double dp = Ds * ldro(dfac + e);
     T s = T(0);
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
         if (f & (1u << d)) {
-            const double dq = Ds * __ldg(dfac + q[d]);
+            const double dq = Ds * ldro(dfac + q[d]);
             const double hm = (dp + dq > 0.0) ? 2.0 * dp * dq / (dp + dq) : 0.0;
             s += T(hm) * __ldcg(u + q[d]);
         }
@@ -223,7 +230,7 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
     // one iteration ahead, so the neighbour loads never wait for them
     uint32_t fn[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? __ldg(S.flags + e0 + u * es) : 0u;
+    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? ldro(S.flags + e0 + u * es) : 0u;
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
         double xv[U], ns[U], bv[U], dg[U];
@@ -231,7 +238,7 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
         for (int u = 0; u < U; ++u) {
             f[u] = fn[u];
             const uint32_t en = e + (U + u) * es;
-            fn[u] = en < NE ? __ldg(S.flags + en) : 0u;
+            fn[u] = en < NE ? ldro(S.flags + en) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -244,8 +251,8 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
             if (eu >= NE) continue;
             xv[u] = x[eu];
             ns[u] = var ? S.a * open_sum_var<double>(x, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum_sel<double>(x, f[u], q[u]);
-            bv[u] = __ldg(S.b[0] + eu);
-            dg[u] = __ldg(S.diag[0] + eu);
+            bv[u] = ldro(S.b[0] + eu);
+            dg[u] = ldro(S.diag[0] + eu);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -287,7 +294,7 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
     const T *dgp = diag_of<T>(S, 0);
     uint32_t fn[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? __ldg(S.flags + e0 + u * es) : 0u;
+    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? ldro(S.flags + e0 + u * es) : 0u;
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
         T xj[U], ns[U], dg[U], w[U];
@@ -295,7 +302,7 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
         for (int u = 0; u < U; ++u) {
             f[u] = fn[u];
             const uint32_t en = e + (U + u) * es;
-            fn[u] = en < NE ? __ldg(S.flags + en) : 0u;
+            fn[u] = en < NE ? ldro(S.flags + en) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -308,7 +315,7 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
             if (eu >= NE) continue;
             xj[u] = uj[eu];
             ns[u] = var ? open_sum_var<T>(uj, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum<T>(uj, f[u], q[u]);
-            dg[u] = __ldg(dgp + eu);
+            dg[u] = ldro(dgp + eu);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -388,14 +395,11 @@ __device__ __forceinline__ void pass_update(const SysDev &S, int k, const T *c, 
     }
 }
 
-// U: elements in flight per thread in the streaming passes; MINB: CTAs per SM
-// the register allocation must allow (1: up to 128 registers, 2: up to 64).
-template <typename T, int MAXM, int U, int MINB>
-__global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
+// The persistent GMRES of one CTA of a team (every item of its team in turn).
+// Returns early when a team barrier gave up (the abort flag is then set).
+template <typename T, int MAXM, int U, int NT>
+__device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT> &sm)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Smem<MAXM, T> &sm = *reinterpret_cast<Smem<MAXM, T> *>(smraw);
-    if ((int)blockIdx.x == A.skip_block) return;    // fault injection: this CTA never arrives
     const int tid = threadIdx.x;
     const int team = A.block_team[blockIdx.x];
     const TeamDesc td = A.teams[team];
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
     uint32_t epoch = 0;
     int pbuf = 0;
     const size_t pstride = (size_t)gridDim.x * kKMax;
-    const uint32_t e0 = (uint32_t)rank * kSB + tid, es = (uint32_t)nb * kSB;
+    const uint32_t e0 = (uint32_t)rank * NT + tid, es = (uint32_t)nb * NT;
     constexpr bool kF32 = std::is_same<T, float>::value;
     const T *coefT = kF32 ? (const T *)&sm.coef32[0][0] : (const T *)&sm.coef[0][0];
     // optional phase timer (CTA 0, thread 0): work, barrier wait, team reduce, serial
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
         const uint64_t t_item0 = globaltimer_ns();
         if (tid == 0) {
             sm.sys = A.sys[sys_id];
-            if (sm.sys.NEp) sm.sys.NE = *sm.sys.NEp;   // sized on the device (device-resident step)
+            if (sm.sys.NEp) sm.sys.NE = __ldcg(sm.sys.NEp);   // sized on the device (device-resident step)
         }
         __syncthreads();
         const SysDev &S = sm.sys;
@@ -456,10 +460,10 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
             if (rmask & 1u) {
                 double a2[1][2] = {{0.0, 0.0}};
                 pass_residual<T, U>(S, first, e0, es, a2[0][0], a2[0][1]);
-                block_reduce_g<1, 2, double>(a2, 1u, 2, 0, sm.red, mypart);
+                block_reduce_g<1, 2, double, NT>(a2, 1u, 2, 0, sm.red, mypart);
             }
             MPM_BARRIER();
-            team_reduce(A.partials + pbuf * pstride, td.first_block, nb, rmask, 2, sm.tot);
+            team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, rmask, 2, sm.tot);
             MPM_TICK(2);
             pbuf ^= 1;
             if (tid < NS && ((rmask >> tid) & 1u)) {
@@ -502,10 +506,10 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
 #pragma unroll
                     for (int i = 0; i <= MAXM; ++i) acc[0][i] = T(0);
                     pass_arnoldi1<T, MAXM, U>(S, j, sm.sig[0][j], e0, es, acc[0]);
-                    block_reduce_g<1, MAXM + 1, T>(acc, 1u, j + 1, 0, sm.red, mypart);
+                    block_reduce_g<1, MAXM + 1, T, NT>(acc, 1u, j + 1, 0, sm.red, mypart);
                 }
                 MPM_BARRIER();
-                team_reduce(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1, sm.tot);
+                team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1, sm.tot);
                 MPM_TICK(2);
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
@@ -524,10 +528,10 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
                 {
                     T acc[1][1] = {{T(0)}};
                     pass_arnoldi2<T, MAXM, U>(S, j, coefT, e0, es, acc[0][0]);
-                    block_reduce_g<1, 1, T>(acc, 1u, 1, 0, sm.red, mypart);
+                    block_reduce_g<1, 1, T, NT>(acc, 1u, 1, 0, sm.red, mypart);
                 }
                 MPM_BARRIER();
-                team_reduce(A.partials + pbuf * pstride, td.first_block, nb, cm, 1, sm.tot);
+                team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, 1, sm.tot);
                 MPM_TICK(2);
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
@@ -620,37 +624,143 @@ __global__ void __launch_bounds__(kSB, MINB) k_gmres(SolveArgs A)
 #undef MPM_BARRIER
 }
 
+// U: elements in flight per thread in the streaming passes; MINB: CTAs per SM
+// the register allocation must allow (1: up to 128 registers, 2: up to 64).
+template <typename T, int MAXM, int U, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) k_gmres(SolveArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem<MAXM, T, NT> &sm = *reinterpret_cast<Smem<MAXM, T, NT> *>(smraw);
+    if ((int)blockIdx.x == A.skip_block) return;    // fault injection: this CTA never arrives
+    gmres_body<T, MAXM, U, NT>(A, sm);
+}
+
+// ------------------------------------------------------------------ the whole step in one kernel
+// Results of the device-resident step for the host (host-mapped memory):
+// raw box min[3], max[3] at 0, counts (mask voxels, active tiles) at 64, the
+// abort flag at 128, the reports at 256.
+struct StepOut {
+    const int32_t *box;
+    const unsigned long long *count;
+    const uint32_t *reports;
+    int32_t nrep_words;
+    char *host;
+    uint32_t *exit_count;          // CTAs that left; the last one copies and resets
+};
+
+struct StepArgs {
+    SolveArgs sa;
+    ExtractArgs xa;                // xa.bar: the grid barrier; xa.xabort == sa.abort_flag
+    BatchSys S;
+    StepOut o;
+};
+
+// One implicit-Euler step of one lattice: the extraction phases A-E (bbox,
+// activity, compaction, gather + rows), a grid barrier, the team solves, a
+// grid barrier, the scatter onto the pleural mask (skipped if any wait gave
+// up).  The last CTA to leave copies the results to host-mapped memory and
+// resets the grid barrier and exit counters for the next step.
+template <typename T, int MAXM, int U, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepArgs P)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem<MAXM, T, NT> &sm = *reinterpret_cast<Smem<MAXM, T, NT> *>(smraw);
+    const int tid = threadIdx.x, nb = gridDim.x, b = blockIdx.x;
+    // optional phase timer (CTA 0): extraction up to the grid barrier after
+    // it, and the wait for the last team plus the scatter
+    const bool prof = P.sa.prof != nullptr && b == 0 && tid == 0;
+    uint64_t t0 = prof ? globaltimer_ns() : 0;
+    if (b != P.sa.skip_block) {                     // fault injection: this CTA never arrives
+        uint32_t epoch = 0;
+        bool ok = extract_phases<NT>(P.xa, P.S, b, nb, epoch);
+        ok = ok && team_barrier(P.xa.bar, epoch, nb, P.xa.xabort, P.xa.timeout_ns);
+        if (prof) {
+            const uint64_t t = globaltimer_ns();
+            P.sa.prof[8] += t - t0;
+        }
+        if (ok) gmres_body<T, MAXM, U, NT>(P.sa, sm);
+        if (prof) t0 = globaltimer_ns();
+        ok = ok && team_barrier(P.xa.bar, epoch, nb, P.xa.xabort, P.xa.timeout_ns);
+        if (ok && *(volatile int32_t *)P.xa.xabort == 0) {
+            const int64_t NE = __ldcg(&P.xa.dyn->NE);
+            const BoxGeo g = P.xa.dyn->g;
+            for (int64_t e = (int64_t)b * NT + tid; e < NE; e += (int64_t)nb * NT) scatter_elem<true>(P.S, g, e);
+        }
+        if (prof) P.sa.prof[9] += globaltimer_ns() - t0;
+    }
+    __syncthreads();
+    __shared__ int s_last;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(P.o.exit_count, 1u) == (unsigned)nb - 1u;
+        __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) return;
+    int32_t *hb = reinterpret_cast<int32_t *>(P.o.host);
+    unsigned long long *hc = reinterpret_cast<unsigned long long *>(P.o.host + 64);
+    uint32_t *hr = reinterpret_cast<uint32_t *>(P.o.host + 256);
+    if (tid < 6) hb[tid] = __ldcg(P.o.box + tid);
+    if (tid < 2) hc[tid] = __ldcg(P.o.count + tid);
+    if (tid == 0) *reinterpret_cast<int32_t *>(P.o.host + 128) = *(volatile int32_t *)P.xa.xabort;
+    for (int i = tid; i < P.o.nrep_words; i += NT) hr[i] = __ldcg(P.o.reports + i);
+    if (tid == 0) {
+        *P.xa.bar = 0u;
+        *P.o.exit_count = 0u;
+    }
+}
+
 typedef void (*KernFn)(SolveArgs);
 
-template <typename T, int MAXM, int U, int MINB>
-static KernFn kfn(size_t &smem)
+typedef void (*StepFn)(StepArgs);
+
+// A kernel variant: the solve kernel, the whole-step kernel of the same
+// instantiation, its dynamic shared memory and CTA size.
+struct Variant {
+    KernFn fn;
+    StepFn stepfn;
+    size_t smem;
+    int nt;
+};
+
+template <typename T, int MAXM, int U, int MINB, int NT>
+static Variant var_of()
 {
-    smem = sizeof(Smem<MAXM, T>);
-    return k_gmres<T, MAXM, U, MINB>;
+    return Variant{k_gmres<T, MAXM, U, MINB, NT>, k_step<T, MAXM, U, MINB, NT>, sizeof(Smem<MAXM, T, NT>), NT};
 }
 
 // Kernel variants: variant 0 is the default of each (precision, restart
 // bucket), chosen by measurement on the 256^3 shell workload (FP32, m <= 8:
-// one element per thread at two CTAs/SM; FP64: two elements at one CTA/SM).
-// The FP32 m <= 8 bucket also has 1: one element at one CTA/SM, 2: two
-// elements at two CTAs/SM, 3: two elements at one CTA/SM.
-static KernFn pick(int prec, int maxm, int variant, size_t &smem)
+// one element per thread at two CTAs/SM of 512 threads; FP64: two elements
+// at one CTA/SM).  The FP32 m <= 8 bucket also has 1: one element at one
+// CTA/SM, 2: two elements at two CTAs/SM, 3: two elements at one CTA/SM,
+// 4: one element at one CTA/SM of 1024 threads (half the CTAs per team: fewer
+// barrier arrivals and partial sums).  The FP64 m <= 8 bucket has 1: one
+// element at two CTAs/SM, 2: one element at one CTA/SM of 1024 threads.
+static Variant pick(int prec, int maxm, int variant)
 {
     if (prec == 0) {
-        if (maxm == 8) return variant == 1 ? kfn<double, 8, 1, 2>(smem) : kfn<double, 8, 2, 1>(smem);
-        if (maxm == 16) return kfn<double, 16, 1, 1>(smem);
-        return kfn<double, 32, 1, 1>(smem);
+        if (maxm == 8) {
+            switch (variant) {
+            case 1: return var_of<double, 8, 1, 2, 512>();
+            case 2: return var_of<double, 8, 1, 1, 1024>();
+            default: return var_of<double, 8, 2, 1, 512>();
+            }
+        }
+        if (maxm == 16) return var_of<double, 16, 1, 1, 512>();
+        return var_of<double, 32, 1, 1, 512>();
     }
     if (maxm == 8) {
         switch (variant) {
-        case 1: return kfn<float, 8, 1, 1>(smem);
-        case 2: return kfn<float, 8, 2, 2>(smem);
-        case 3: return kfn<float, 8, 2, 1>(smem);
-        default: return kfn<float, 8, 1, 2>(smem);
+        case 1: return var_of<float, 8, 1, 1, 512>();
+        case 2: return var_of<float, 8, 2, 2, 512>();
+        case 3: return var_of<float, 8, 2, 1, 512>();
+        case 4: return var_of<float, 8, 1, 1, 1024>();
+        default: return var_of<float, 8, 1, 2, 512>();
         }
     }
-    if (maxm == 16) return kfn<float, 16, 1, 1>(smem);
-    return kfn<float, 32, 1, 1>(smem);
+    if (maxm == 16) return var_of<float, 16, 1, 1, 512>();
+    return var_of<float, 32, 1, 1, 512>();
 }
 
 }  // namespace mpm
@@ -682,15 +792,27 @@ SysDev mpm_make_sysdev(const mpm_subgrid *sub)
     return S;
 }
 
+// Co-resident CTAs of a variant's kernel (the solve, or the whole step).
+static int variant_max_blocks(mpm_ctx *ctx, const Variant &v, bool step)
+{
+    const void *f = step ? (const void *)v.stepfn : (const void *)v.fn;
+    if (v.smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, v.nt, v.smem) != cudaSuccess) return 0;
+    return per_sm * ctx->num_sms;
+}
+
 int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 {
     const int maxm = m <= 8 ? 8 : (m <= 16 ? 16 : 32);
-    size_t smem = 0;
-    KernFn fn = pick(prec, maxm, variant, smem);
-    if (smem > 48 * 1024) cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kSB, smem) != cudaSuccess) return 0;
-    return per_sm * ctx->num_sms;
+    return variant_max_blocks(ctx, pick(prec, maxm, variant), false);
+}
+
+// Number of kernel variants of a (precision, restart) bucket (for the tuner).
+int mpm_solver_variants(int prec, int m)
+{
+    if (m > 8) return 1;
+    return prec == 1 ? 5 : 3;
 }
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -804,7 +926,9 @@ static void plan_teams(const std::vector<double> &work, int G, std::vector<TeamD
 struct SolvePlan {
     int nsys = 0, nitem = 0, G = 0, nteam = 0;
     size_t smem = 0;
+    int nt = kSB;                   // threads per CTA
     KernFn fn = nullptr;
+    StepFn stepfn = nullptr;        // the whole-step kernel of the same variant
     std::vector<SysDev> sd;
     std::vector<int> item_sys, item_sp;
     std::vector<TeamDesc> teams;
@@ -890,7 +1014,13 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
         }
     }
     P.nitem = (int)P.sd.size();
-    P.fn = pick(opt->precision, maxm, ctx->solver_variant, P.smem);
+    {
+        const Variant v = pick(opt->precision, maxm, ctx->solver_variant);
+        P.fn = v.fn;
+        P.stepfn = v.stepfn;
+        P.smem = v.smem;
+        P.nt = v.nt;
+    }
     const int gmax = mpm_solver_max_blocks(ctx, opt->precision, m, ctx->solver_variant);
     if (gmax < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "solve: occupancy query failed");
     if (ov && ov->G > 0) P.G = std::min(ov->G, gmax);
@@ -899,7 +1029,7 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
         double tot = 0.0;
         for (double w : work) tot += w;
         // about two elements per thread and item at least
-        const double want = tot / (kSB * 2.0);
+        const double want = tot / (P.nt * 2.0);
         P.G = (int)std::min<double>(gmax, std::max(1.0, want));
         P.G = std::max(P.G, std::min(P.nitem, gmax));
     }
@@ -954,9 +1084,9 @@ static mpm_status enqueue_solve(mpm_ctx *ctx, SolvePlan &P, char *d_args, uint32
         MPM_CU(cudaMemsetAsync(d_abort, 0, sizeof(int32_t), st));
         MPM_CU(cudaMemsetAsync(d_args + P.o_rep, 0, sizeof(SysReport) * P.nitem, st));
     }
-    if (d_prof) MPM_CU(cudaMemsetAsync(d_prof, 0, 8 * sizeof(unsigned long long), st));
+    if (d_prof) MPM_CU(cudaMemsetAsync(d_prof, 0, kProfSlots * sizeof(unsigned long long), st));
     void *kargs[] = {&sa};
-    MPM_CU(cudaLaunchCooperativeKernel((const void *)P.fn, dim3(P.G), dim3(kSB), kargs, P.smem, st));
+    MPM_CU(cudaLaunchCooperativeKernel((const void *)P.fn, dim3(P.G), dim3(P.nt), kargs, P.smem, st));
     ctx->launches += 1;
     return MPM_OK;
 }
@@ -1060,7 +1190,7 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
         MPM_CU(cudaMalloc(&ctx->d_bar, (size_t)P.nteam * 32 * sizeof(uint32_t)));
         ctx->bar_cap = P.nteam;
     }
-    if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+    if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, kProfSlots * sizeof(unsigned long long)));
     // the staging buffer is free: every call that uses it ends with a stream synchronisation
     char *hs = (char *)ctx->h_stage;
     fill_descriptors(P, hs);
@@ -1073,7 +1203,7 @@ mpm_status mpm_solve_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
     MPM_CU(cudaMemcpyAsync(hrep, (char *)ctx->d_args + P.o_rep, sizeof(SysReport) * P.nitem, cudaMemcpyDeviceToHost, st));
     int32_t *hflags = (int32_t *)(hs + P.args_need);
     MPM_CU(cudaMemcpyAsync(hflags, ctx->d_abort, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, kProfSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     MPM_CU(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -1230,7 +1360,7 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
         // eager form of the same sequence (graph unavailable or phase timing on)
         r = mpm_batch_prep_launch(ctx, B->d_desc, nsys, B->prep_blocks, st);
         if (r != MPM_OK) return r;
-        if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+        if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, kProfSlots * sizeof(unsigned long long)));
         r = enqueue_solve(ctx, P, B->d_args, B->d_bar, B->d_abort, ctx->phase_prof ? ctx->d_prof : nullptr, st);
         if (r != MPM_OK) return r;
         r = mpm_batch_scatter_launch(ctx, B->d_desc, nsys, B->prep_blocks, st);
@@ -1241,7 +1371,7 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
     MPM_CU(cudaMemcpyAsync(hrep, B->d_args + P.o_rep, sizeof(SysReport) * P.nitem, cudaMemcpyDeviceToHost, st));
     int32_t *hflags = (int32_t *)(hs + P.args_need);
     MPM_CU(cudaMemcpyAsync(hflags, B->d_abort, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (ctx->phase_prof) MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, kProfSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     MPM_CU(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -1273,27 +1403,35 @@ struct StepGraph {
     char *d_scr = nullptr;          // box (256 B), counts (256 B), abort flag (256 B), StepDyn (256 B)
     char *d_args = nullptr;         // solver descriptors and reports
     size_t args_cap = 0;
-    uint32_t *d_bar = nullptr;
+    uint32_t *d_bar = nullptr;      // team barrier counters
     double *d_partials = nullptr;
     size_t partials_cap = 0;
     double *d_rates = nullptr;      // rate tables of the preparation
     size_t rates_cap = 0;
-    char *d_xscr = nullptr;         // scratch of the cooperative extraction
-    int xnb = 0;                    // its grid
-    char *h_out = nullptr;          // host-mapped: box, counts, abort flag, reports (written by the scatter)
+    char *d_xscr = nullptr;         // per-CTA extraction partials, grid barrier, exit counter
+    size_t xscr_cap = 0;
+    char *h_out = nullptr;          // host-mapped: box, counts, abort flag, reports (written by the kernel)
     char *h_out_dev = nullptr;      // its device address
     size_t hout_cap = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // what mpm_step_wait needs from the last enqueued step
+    bool pending = false;
+    int32_t margin = 0, lt[3] = {2, 2, 2}, ldims[3] = {0, 0, 0};
+    int gmax_key[3] = {-1, -1, -1};  // (precision, restart bucket, variant) of the cached grid limit
+    int gmax = 0;
 };
 
 static constexpr size_t kOutBox = 0, kOutCount = 64, kOutAbort = 128, kOutRep = 256;
 static constexpr size_t kScrBox = 0, kScrCount = 256, kScrAbort = 512, kScrDyn = 768;
 
+// Extraction scratch for a grid of nb CTAs: box partials (32 B per CTA), count
+// partials (16 B per CTA), then the grid barrier counter and the exit counter.
+static size_t xscr_bytes(int nb) { return (size_t)nb * 48 + 512; }
+
 void mpm_step_free(mpm_ctx *ctx, mpm_subgrid *sub)
 {
     StepGraph *T = (StepGraph *)sub->step;
     if (!T) return;
-    if (ctx) ctx->allocated -= T->args_cap + T->partials_cap + T->rates_cap;
+    if (ctx) ctx->allocated -= T->args_cap + T->partials_cap + T->rates_cap + T->xscr_cap;
     if (T->exec) cudaGraphExecDestroy(T->exec);
     cudaFree(T->d_scr);
     cudaFree(T->d_args);
@@ -1302,8 +1440,6 @@ void mpm_step_free(mpm_ctx *ctx, mpm_subgrid *sub)
     cudaFree(T->d_rates);
     cudaFree(T->d_xscr);
     if (T->h_out) cudaFreeHost(T->h_out);
-    if (T->e0) cudaEventDestroy(T->e0);
-    if (T->e1) cudaEventDestroy(T->e1);
     delete T;
     sub->step = nullptr;
 }
@@ -1316,45 +1452,117 @@ void mpm_step_invalidate(mpm_subgrid *sub)
     if (T) T->valid = false;
 }
 
-// The stages of one step on stream cs (captured or eager): the cooperative
-// extraction + preparation, the solve, the scatter with the result copy.
-static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, const mpm_lattice *lat,
-                               const mpm_params *prm, int32_t margin, bool capturing, cudaStream_t cs)
+// Static descriptor of a device-resident step (host image, passed by value).
+static BatchSys step_sys(mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, const double *d_rates)
 {
+    BatchSys S;
+    memset(&S, 0, sizeof(S));
+    S.tile_coord = sub->tile_coord;
+    S.cell_id = lat->cell_id;
+    S.mask = lat->mask;
+    S.dfac_lat = lat->dfac;
+    S.flags = sub->flags;
+    S.cell = sub->cell;
+    S.dfac = sub->dfac;
+    for (int s = 0; s < sub->nspecies; ++s) {
+        S.field[s] = lat->field[s];
+        S.x[s] = sub->x[s];
+        S.cn[s] = sub->cn[s];
+        S.b[s] = sub->b[s];
+        S.diag[s] = sub->diag[s];
+        S.diag32[s] = sub->diag32[s];
+    }
+    S.err = sub->err;
+    S.tile_index = sub->tile_index;
+    S.nbr = sub->nbr;
+    S.dk = d_rates;
+    S.dq = d_rates + (size_t)prm->nspecies * prm->ncell;
+    mpm_asm_coef(prm, &S.C);
+    return S;
+}
+
+// One step on stream cs (captured or eager): the whole-step kernel.
+static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, const mpm_lattice *lat,
+                               const mpm_params *prm, int32_t margin, cudaStream_t cs)
+{
+    SolvePlan &P = T->plan;
+    const int nb = P.G;
     int32_t *d_box = (int32_t *)(T->d_scr + kScrBox);
     int64_t *d_count = (int64_t *)(T->d_scr + kScrCount);
     int32_t *d_abort = (int32_t *)(T->d_scr + kScrAbort);
-    void *d_dyn = T->d_scr + kScrDyn;
-    char *d_rep = T->d_args + T->plan.o_rep;
-    const size_t rep_bytes = sizeof(SysReport) * T->plan.nitem;
-    mpm_status r = mpm_step_extract_launch(ctx, sub, lat, prm, margin, T->xnb, T->d_xscr, d_box, d_count, d_dyn,
-                                           T->d_bar, T->plan.nteam * 32, d_abort, d_rep, rep_bytes, T->d_rates, cs);
-    if (r != MPM_OK) return r;
-    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    MPM_CU(cudaEventRecordWithFlags(T->e0, cs, evf));
-    r = enqueue_solve(ctx, T->plan, T->d_args, T->d_bar, d_abort, ctx->phase_prof ? ctx->d_prof : nullptr, cs, true);
-    if (r != MPM_OK) return r;
-    MPM_CU(cudaEventRecordWithFlags(T->e1, cs, evf));
-    r = mpm_step_scatter_launch(ctx, sub, lat, prm, d_dyn, d_box, d_count, d_abort, T->xnb, T->d_xscr, d_rep,
-                                rep_bytes, T->h_out_dev, cs);
-    if (r != MPM_OK) return r;
+    StepDyn *d_dyn = (StepDyn *)(T->d_scr + kScrDyn);
+    char *d_rep = T->d_args + P.o_rep;
+    const size_t rep_bytes = sizeof(SysReport) * P.nitem;
+    StepArgs A;
+    memset(&A, 0, sizeof(A));
+    A.sa = P.sa;
+    A.sa.sys = (const SysDev *)(T->d_args + P.o_sys);
+    A.sa.teams = (const TeamDesc *)(T->d_args + P.o_team);
+    A.sa.sys_order = (const int32_t *)(T->d_args + P.o_order);
+    A.sa.block_team = (const int32_t *)(T->d_args + P.o_bt);
+    A.sa.reports = (SysReport *)d_rep;
+    A.sa.bar = T->d_bar;
+    A.sa.abort_flag = d_abort;
+    A.sa.prof = ctx->phase_prof ? ctx->d_prof : nullptr;
+    ExtractArgs &X = A.xa;
+    X.cell_id = lat->cell_id;
+    X.mask = lat->mask;
+    for (int d = 0; d < 3; ++d) { X.L[d] = lat->dims[d]; X.lt[d] = sub->lt[d]; }
+    X.margin = margin;
+    X.vec4 = ((uintptr_t)lat->cell_id % 16) == 0;
+    X.part_box = (int32_t *)T->d_xscr;
+    X.part_cnt = (unsigned long long *)(T->d_xscr + (size_t)nb * 32);
+    X.bar = (uint32_t *)(T->d_xscr + (size_t)nb * 48);
+    X.xabort = d_abort;
+    X.timeout_ns = ctx->timeout_ns;
+    X.box_out = d_box;
+    X.geo_out = (BoxGeo *)(d_box + 8);
+    X.count_out = (unsigned long long *)d_count;
+    X.dyn = d_dyn;
+    X.active = sub->active;
+    X.tile_index = sub->tile_index;
+    X.tile_coord = sub->tile_coord;
+    X.err = sub->err;
+    X.sbar = T->d_bar;
+    X.nsbar = P.nteam * 32;
+    X.srep = (uint32_t *)d_rep;
+    X.nrep_words = (int32_t)(rep_bytes / 4);
+    X.ra.nspecies = prm->nspecies;
+    X.ra.ncell = prm->ncell;
+    X.ra.dt = prm->dt;
+    for (int s = 0; s < prm->nspecies; ++s) X.ra.mu[s] = prm->mu[s];
+    X.ra.k_cell = prm->k_cell;
+    X.ra.q_cell = prm->q_cell;
+    X.ra.dk = T->d_rates;
+    X.ra.dq = T->d_rates + (size_t)prm->nspecies * prm->ncell;
+    A.S = step_sys(sub, lat, prm, T->d_rates);
+    A.o.box = d_box;
+    A.o.count = (const unsigned long long *)d_count;
+    A.o.reports = (const uint32_t *)d_rep;
+    A.o.nrep_words = (int32_t)(rep_bytes / 4);
+    A.o.host = T->h_out_dev;
+    A.o.exit_count = (uint32_t *)(T->d_xscr + (size_t)nb * 48 + 256);
+    if (ctx->phase_prof) MPM_CU(cudaMemsetAsync(ctx->d_prof, 0, kProfSlots * sizeof(unsigned long long), cs));
+    void *kargs[] = {&A};
+    MPM_CU(cudaLaunchCooperativeKernel((const void *)P.stepfn, dim3(nb), dim3(P.nt), kargs, P.smem, cs));
+    ctx->launches += 1;
     if (ctx->phase_prof)
-        MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
+        MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, kProfSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
     return MPM_OK;
 }
 
 // Grid of the persistent solve for S items of NE elements (the sizing of
 // plan_solve: about two elements per thread and item, at least one CTA per
 // item, at most the co-resident maximum).
-static int step_grid(int64_t NE, int S, int gmax)
+static int step_grid(int64_t NE, int S, int gmax, int nt)
 {
-    const double want = (double)S * (double)(NE + 1) / (kSB * 2.0);
+    const double want = (double)S * (double)(NE + 1) / (nt * 2.0);
     int G = (int)std::min<double>(gmax, std::max(1.0, want));
     return std::max(G, std::min(S, gmax));
 }
 
-mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
-                         const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, cudaStream_t st)
+mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                                 int32_t margin, const int32_t tile[3], const mpm_opts *opt, cudaStream_t st)
 {
     if (!sub || !prm) return mpm_fail(ctx, MPM_ERR_ARG, "step: null argument");
     mpm_status r = mpm_params_check(ctx, prm);
@@ -1376,22 +1584,26 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
     r = mpm_step_buffers(ctx, sub, lat, S, lt);
     if (r != MPM_OK) return r;
     if (sub->geo != old_geo || sub->elem != old_elem) T->valid = false;
-    // grid: from the previous step's element count, kept while within 25%
-    const int gmax = mpm_solver_max_blocks(ctx, opt->precision, opt->restart, ctx->solver_variant);
+    // grid: from the previous step's element count, kept while within 25%;
+    // at most the co-resident CTAs of the whole-step kernel
+    const int maxm = opt->restart <= 8 ? 8 : (opt->restart <= 16 ? 16 : 32);
+    const Variant var = pick(opt->precision, maxm, ctx->solver_variant);
+    if (T->gmax_key[0] != opt->precision || T->gmax_key[1] != maxm || T->gmax_key[2] != ctx->solver_variant) {
+        T->gmax = variant_max_blocks(ctx, var, true);   // occupancy query: once per variant
+        T->gmax_key[0] = opt->precision;
+        T->gmax_key[1] = maxm;
+        T->gmax_key[2] = ctx->solver_variant;
+    }
+    const int gmax = T->gmax;
     if (gmax < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "step: occupancy query failed");
     const int64_t NE_est = T->last_NE >= 0 ? T->last_NE : sub->NE_cap;
-    int G = opt->nblocks > 0 ? std::min(opt->nblocks, gmax) : step_grid(NE_est, S, gmax);
+    int G = opt->nblocks > 0 ? std::min(opt->nblocks, gmax) : step_grid(NE_est, S, gmax, var.nt);
     if (opt->nblocks <= 0 && T->G > 0 && T->G <= gmax && G >= T->G * 4 / 5 && G <= T->G * 5 / 4) G = T->G;
     if (!T->d_scr) {
         MPM_CU(cudaMalloc(&T->d_scr, 1024));
         MPM_CU(cudaMemset(T->d_scr, 0, 1024));
-        T->xnb = mpm_step_extract_grid(ctx);
-        if (T->xnb < 1) return mpm_fail(ctx, MPM_ERR_CUDA, "step: extraction occupancy query failed");
-        MPM_CU(cudaMalloc(&T->d_xscr, mpm_step_xscr_bytes(T->xnb)));
-        T->valid = false;
         MPM_CU(cudaMalloc(&T->d_bar, (size_t)ctx->num_sms * 4 * 32 * sizeof(uint32_t)));
-        MPM_CU(cudaEventCreate(&T->e0));
-        MPM_CU(cudaEventCreate(&T->e1));
+        T->valid = false;
     }
     auto make_key = [&](std::vector<unsigned char> &key) {
         key.clear();
@@ -1439,6 +1651,8 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
         r = mpm_grow(ctx, (void **)&T->d_rates, &T->rates_cap, 2 * (size_t)prm->nspecies * prm->ncell * sizeof(double),
                      "step rate tables");
         if (r != MPM_OK) return r;
+        r = mpm_grow(ctx, (void **)&T->d_xscr, &T->xscr_cap, xscr_bytes(T->plan.G), "step extraction scratch");
+        if (r != MPM_OK) return r;
         if (T->plan.nteam > ctx->num_sms * 4) return mpm_fail(ctx, MPM_ERR_ARG, "step: too many teams");
         const size_t hneed = kOutRep + sizeof(SysReport) * T->plan.nitem;
         if (T->hout_cap < hneed) {
@@ -1449,18 +1663,21 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
             T->hout_cap = hneed;
             MPM_CU(cudaHostGetDevicePointer((void **)&T->h_out_dev, T->h_out, 0));
         }
-        if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+        if (ctx->phase_prof && !ctx->d_prof) MPM_CU(cudaMalloc(&ctx->d_prof, kProfSlots * sizeof(unsigned long long)));
         r = ensure_stage(ctx, T->plan.args_need + 4096);
         if (r != MPM_OK) return r;
         fill_descriptors(T->plan, (char *)ctx->h_stage);
         MPM_CU(cudaMemcpyAsync(T->d_args, ctx->h_stage, T->plan.o_rep, cudaMemcpyHostToDevice, st));
-        // between-step state: activity bytes, the extraction's barrier counter and abort flag at zero
+        // between-step state at its initial values: activity bytes, grid barrier
+        // and exit counters, team barrier counters and the abort flag at zero
         {
             const int64_t ntl = (((int64_t)lat->dims[0] + (1 << lt[0]) - 1) >> lt[0]) *
                                 (((int64_t)lat->dims[1] + (1 << lt[1]) - 1) >> lt[1]) *
                                 (((int64_t)lat->dims[2] + (1 << lt[2]) - 1) >> lt[2]);
             MPM_CU(cudaMemsetAsync(sub->active, 0, (size_t)ntl, st));
-            MPM_CU(cudaMemsetAsync(T->d_xscr, 0, mpm_step_xscr_bytes(T->xnb), st));
+            MPM_CU(cudaMemsetAsync(T->d_xscr, 0, xscr_bytes(T->plan.G), st));
+            MPM_CU(cudaMemsetAsync(T->d_scr, 0, 1024, st));
+            MPM_CU(cudaMemsetAsync(T->d_bar, 0, (size_t)ctx->num_sms * 4 * 32 * sizeof(uint32_t), st));
         }
         MPM_CU(cudaStreamSynchronize(st));   // descriptors and slots in place before any capture
         T->G = G;
@@ -1471,7 +1688,7 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
             const int64_t launches0 = ctx->launches;
             bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                ok = enqueue_step(ctx, T, sub, lat, prm, margin, true, cs) == MPM_OK;
+                ok = enqueue_step(ctx, T, sub, lat, prm, margin, cs) == MPM_OK;
                 const cudaError_t ec = cudaStreamEndCapture(cs, &g);
                 ok = ok && ec == cudaSuccess && g != nullptr;
             }
@@ -1493,23 +1710,43 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
         MPM_CU(cudaGraphLaunch(T->exec, st));
         ctx->launches += T->graph_launches;
     } else {
-        r = enqueue_step(ctx, T, sub, lat, prm, margin, false, st);
+        r = enqueue_step(ctx, T, sub, lat, prm, margin, st);
         if (r != MPM_OK) return r;
     }
+    T->pending = true;
+    T->margin = margin;
+    for (int d = 0; d < 3; ++d) {
+        T->lt[d] = lt[d];
+        T->ldims[d] = lat->dims[d];
+    }
+    return MPM_OK;
+}
+
+// Waits for the subgrid's enqueued steps and reports the last one.
+mpm_status mpm_step_wait_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, cudaStream_t st)
+{
+    if (!sub) return mpm_fail(ctx, MPM_ERR_ARG, "step_wait: null subgrid");
+    StepGraph *T = (StepGraph *)sub->step;
+    if (!T || !T->pending) return mpm_fail(ctx, MPM_ERR_ARG, "step_wait: no step was enqueued on this subgrid");
     MPM_CU(cudaStreamSynchronize(st));
+    T->pending = false;
+    const int32_t margin = T->margin;
+    const int32_t *lt = T->lt;
+    mpm_status r;
     const volatile int32_t *hb = (const volatile int32_t *)(T->h_out + kOutBox);
     const volatile int64_t *hc = (const volatile int64_t *)(T->h_out + kOutCount);
-    const bool x_timed_out = *(const volatile int32_t *)(T->h_out + kOutAbort + 4) != 0;
-    const bool timed_out = x_timed_out || *(const volatile int32_t *)(T->h_out + kOutAbort) != 0;
-    if (x_timed_out) {   // nothing was solved or written; set the between-step state up again
+    if (*(const volatile int32_t *)(T->h_out + kOutAbort) != 0) {
+        // a bounded wait expired: nothing was scattered; set the between-step state up again
         T->valid = false;
         sub->extracted = false;
         sub->assembled = false;
-        return mpm_fail(ctx, MPM_ERR_TIMEOUT, "step: a bounded grid barrier of the extraction expired");
+        return mpm_fail(ctx, MPM_ERR_TIMEOUT, "step: a bounded inter-CTA wait expired");
     }
+    const bool timed_out = false;
+    // the solve's own time: the longest work item (the kernel is one launch per step)
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, T->e0, T->e1);
-    cudaGetLastError();
+    for (int it = 0; it < T->plan.nitem; ++it)
+        ms = std::max(ms, (float)(((const SysReport *)(T->h_out + kOutRep))[it].t_ns * 1e-6));
     sub->gen += 1;
     if (hb[3] < 0) {   // no tumour voxel: nothing was solved or written
         sub->extracted = false;
@@ -1522,7 +1759,7 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
     for (int d = 0; d < 3; ++d) {
         box.lo[d] = hb[d] - margin < 0 ? 0 : hb[d] - margin;
         const int64_t h = (int64_t)hb[3 + d] + margin + 1;
-        box.hi[d] = h > lat->dims[d] ? lat->dims[d] : (int32_t)h;
+        box.hi[d] = h > T->ldims[d] ? T->ldims[d] : (int32_t)h;
         sub->lo[d] = box.lo[d];
         sub->hi[d] = box.hi[d];
         sub->n[d] = box.hi[d] - box.lo[d];
@@ -1539,4 +1776,12 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
     r = finish_solve(ctx, T->plan, &sub, (const SysReport *)(T->h_out + kOutRep), timed_out, ms, rep, nullptr, st);
     sub->x_fresh = false;
     return r;
+}
+
+mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
+                         const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, cudaStream_t st)
+{
+    mpm_status r = mpm_step_enqueue_impl(ctx, sub, lat, prm, margin, tile, opt, st);
+    if (r != MPM_OK) return r;
+    return mpm_step_wait_impl(ctx, sub, rep, out_box, st);
 }

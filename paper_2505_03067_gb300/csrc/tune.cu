@@ -20,6 +20,7 @@
 #include "mpm_internal.cuh"
 
 int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant);
+int mpm_solver_variants(int prec, int m);
 
 namespace {
 
@@ -142,7 +143,7 @@ extern "C" mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, in
     double best_ms = 1e300;
     int best_m = opt->restart, best_v = 0;
     for (int32_t mm : kRestarts) {
-        const int nvar = (opt->precision == 1 && mm <= 8) ? 4 : 1;
+        const int nvar = mpm_solver_variants(opt->precision, mm);
         for (int v = 0; v < nvar; ++v) {
             mpm_opts o = *opt;
             o.restart = mm;

@@ -30,7 +30,7 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
            "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
-           "mpm_step"]
+           "mpm_step", "mpm_step_enqueue", "mpm_step_wait"]
 
 
 class mpm_box(C.Structure):
@@ -119,6 +119,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_solve_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
         "mpm_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, C.POINTER(C.c_int32),
                      C.POINTER(mpm_opts), C.POINTER(mpm_report), C.POINTER(mpm_box), P],
+        "mpm_step_enqueue": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, C.POINTER(C.c_int32),
+                             C.POINTER(mpm_opts), P],
+        "mpm_step_wait": [P, P, C.POINTER(mpm_report), C.POINTER(mpm_box), P],
         "mpm_solve_batch": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.c_int32, C.POINTER(mpm_opts),
                             C.POINTER(mpm_report), P],
         "mpm_subgrid_export": [P, P, C.c_int32, C.c_int32, P, P],
@@ -252,7 +255,8 @@ class Context:
     def phase_times_us(self) -> dict:
         """CTA-0 time split of the last solve (needs debug_set(DEBUG_PHASE_TIMES, 1))."""
         return {k: self.counter(c) / 1e3 for k, c in (("work", 2), ("wait", 3), ("reduce", 4), ("serial", 5),
-                                                      ("R", 6), ("P1", 7), ("P2", 8), ("U", 9))}
+                                                      ("R", 6), ("P1", 7), ("P2", 8), ("U", 9),
+                                                      ("extract", 12), ("scatter", 13))}
 
     def debug_set(self, key: int, value: int):
         self._check(self.lib.mpm_debug_set(self.ptr, key, value), "mpm_debug_set")
@@ -345,6 +349,28 @@ class Subgrid:
         if st == ERR_EMPTY:
             return {"status_code": ERR_EMPTY, "box": None}
         self.nspecies = int(prm.struct.nspecies)
+        d = rep.as_dict(self.nspecies)
+        d["status_code"] = st
+        d["box"] = box.as_tuple()
+        return d
+
+    def mpm_step_enqueue(self, lat: DeviceLattice, prm: "DeviceParams", margin: int, opts: mpm_opts, tile=None,
+                         stream=None):
+        """Queue one device-resident step (mpm_step_enqueue); no wait."""
+        ls = lat.struct()
+        t = (C.c_int32 * 3)(*tile) if tile is not None else None
+        self.ctx._check(self.ctx.lib.mpm_step_enqueue(self.ctx.ptr, self.h, C.byref(ls), C.byref(prm.struct), margin,
+                                                      t, C.byref(opts), _stream_ptr(stream)), "mpm_step_enqueue")
+        self.nspecies = int(prm.struct.nspecies)
+
+    def mpm_step_wait(self, stream=None, allow=(ERR_NOCONV,)):
+        """Wait for the queued steps and report the last one (as mpm_step)."""
+        rep = mpm_report()
+        box = mpm_box()
+        st = self.ctx.lib.mpm_step_wait(self.ctx.ptr, self.h, C.byref(rep), C.byref(box), _stream_ptr(stream))
+        self.ctx._check(st, "mpm_step_wait", allow=tuple(allow) + (ERR_EMPTY,))
+        if st == ERR_EMPTY:
+            return {"status_code": ERR_EMPTY, "box": None}
         d = rep.as_dict(self.nspecies)
         d["status_code"] = st
         d["box"] = box.as_tuple()
@@ -458,6 +484,13 @@ class StepSolver:
         self.ctx, self.lat, self.prm, self.margin, self.tile = ctx, lat, prm, margin, tile
         self.fused = fused
         self.sub = ctx.subgrid_create()
+
+    def step_async(self, opts: mpm_opts, stream=None):
+        """Queue one device-resident step (read the result with wait())."""
+        self.sub.mpm_step_enqueue(self.lat, self.prm, self.margin, opts, self.tile, stream)
+
+    def wait(self, stream=None, allow=(ERR_NOCONV,)):
+        return self.sub.mpm_step_wait(stream, allow)
 
     def step(self, opts: mpm_opts, stream=None, allow=(ERR_NOCONV,)):
         if self.fused:

@@ -424,9 +424,9 @@ def test_device_resident_step_empty_then_tumour(M, ctx):
 
 
 def test_device_resident_step_replays_one_graph(M):
-    """After the first call the step is one graph launch of three kernels (the
-    cooperative extraction + preparation, the solve, the scatter), and the
-    exports see the step's extraction."""
+    """After the first call the step is one graph launch of one cooperative
+    kernel (extraction, assembly, solve, scatter), and the exports see the
+    step's extraction."""
     c = M.Context()
     wl = W.random_case(23, (26, 22, 20), nspecies=3)
     lat = M.DeviceLattice(wl.lattice)
@@ -436,10 +436,33 @@ def test_device_resident_step_replays_one_graph(M):
     l0 = c.launches()
     for _ in range(3):
         assert solver.step(opts)["status_code"] == M.OK
-    assert c.launches() - l0 == 3 * 3
+    assert c.launches() - l0 == 3
     info = solver.sub.info()
     box = oracle.bbox(wl.lattice.cell_id, wl.margin)
     assert info["box"] == box
     flags = solver.sub.mpm_subgrid_export(M.EXPORT_FLAGS).cpu().numpy()
     mb = oracle.box_view(wl.lattice.mask, box)
     assert int(((flags & 64) > 0).sum()) == int(mb.sum())
+
+
+def test_queued_steps_equal_waited_steps(M, ctx):
+    """Steps queued back to back (mpm_step_enqueue, one mpm_step_wait at the end)
+    give the lattice of the same steps waited for one by one, bit for bit (a
+    fixed grid, so both use one plan); a wait with nothing queued is an
+    argument error."""
+    wl = W.random_case(24, (30, 26, 22), nspecies=3)
+    opts = M.make_opts(rtol=1e-10, restart=8, maxit=500, nblocks=8)
+    lat1, lat2 = M.DeviceLattice(wl.lattice), M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    s1 = M.StepSolver(ctx, lat1, prm, wl.margin)
+    s2 = M.StepSolver(ctx, lat2, prm, wl.margin)
+    reps = [s1.step(opts) for _ in range(4)]
+    for _ in range(4):
+        s2.step_async(opts)
+    last = s2.wait()
+    assert last["status_code"] == M.OK and last["box"] == reps[-1]["box"]
+    assert last["iters"] == reps[-1]["iters"]
+    assert np.array_equal(lat1.fields_numpy(), lat2.fields_numpy())
+    with pytest.raises(M.MpmError) as ei:
+        s2.wait()
+    assert ei.value.status == M.ERR_ARG
