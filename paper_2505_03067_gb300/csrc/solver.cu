@@ -730,13 +730,14 @@ static Variant var_of()
 }
 
 // Kernel variants: variant 0 is the default of each (precision, restart
-// bucket), chosen by measurement on the 256^3 shell workload (FP32, m <= 8:
-// one element per thread at two CTAs/SM of 512 threads; FP64: two elements
-// at one CTA/SM).  The FP32 m <= 8 bucket also has 1: one element at one
-// CTA/SM, 2: two elements at two CTAs/SM, 3: two elements at one CTA/SM,
-// 4: one element at one CTA/SM of 1024 threads (half the CTAs per team: fewer
-// barrier arrivals and partial sums).  The FP64 m <= 8 bucket has 1: one
-// element at two CTAs/SM, 2: one element at one CTA/SM of 1024 threads.
+// bucket), chosen by measurement on the 256^3 shell workload.  FP32, m <= 8:
+// 0: one element per thread at one CTA/SM of 768 threads (up to 80
+// registers; fewer CTAs per team than two 512-thread CTAs/SM, so less barrier
+// and reduction time), 1: one element at one CTA/SM of 512, 2: two elements
+// at two CTAs/SM of 512, 3: two elements at one CTA/SM of 512, 4: one element
+// at one CTA/SM of 1024, 5: one element at two CTAs/SM of 512 (64
+// registers).  FP64, m <= 8: 0: two elements at one CTA/SM of 512, 1: one
+// element at two CTAs/SM, 2: one element at one CTA/SM of 1024.
 static Variant pick(int prec, int maxm, int variant)
 {
     if (prec == 0) {
@@ -756,7 +757,8 @@ static Variant pick(int prec, int maxm, int variant)
         case 2: return var_of<float, 8, 2, 2, 512>();
         case 3: return var_of<float, 8, 2, 1, 512>();
         case 4: return var_of<float, 8, 1, 1, 1024>();
-        default: return var_of<float, 8, 1, 2, 512>();
+        case 5: return var_of<float, 8, 1, 2, 512>();
+        default: return var_of<float, 8, 1, 1, 768>();
         }
     }
     if (maxm == 16) return var_of<float, 16, 1, 1, 512>();
@@ -812,7 +814,7 @@ int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 int mpm_solver_variants(int prec, int m)
 {
     if (m > 8) return 1;
-    return prec == 1 ? 5 : 3;
+    return prec == 1 ? 6 : 3;
 }
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
