@@ -388,6 +388,14 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
  * and of the wait for the last team plus the scatter, on CTA 0. */
 #define MPM_COUNTER_PHASE_EXTRACT_NS 12
 #define MPM_COUNTER_PHASE_SCATTER_NS 13
+/* mpm_step only, the extraction's phases each up to its grid barrier: the
+ * bounding box, the tile activity, the active-tile counts, the compaction and
+ * the gather + rows (the last without a barrier). */
+#define MPM_COUNTER_PHASE_BBOX_NS 14
+#define MPM_COUNTER_PHASE_ACTIVITY_NS 15
+#define MPM_COUNTER_PHASE_COUNT_NS 16
+#define MPM_COUNTER_PHASE_COMPACT_NS 17
+#define MPM_COUNTER_PHASE_GATHER_NS 18
 mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value);
 
 /*

@@ -297,6 +297,10 @@ mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)
         *value = (int64_t)ctx->h_prof[key - MPM_COUNTER_PHASE_WORK_NS];
         return MPM_OK;
     }
+    if (key >= MPM_COUNTER_PHASE_BBOX_NS && key <= MPM_COUNTER_PHASE_GATHER_NS) {
+        *value = (int64_t)ctx->h_prof[10 + key - MPM_COUNTER_PHASE_BBOX_NS];
+        return MPM_OK;
+    }
     if (key == MPM_COUNTER_PHASE_EXTRACT_NS || key == MPM_COUNTER_PHASE_SCATTER_NS) {
         *value = (int64_t)ctx->h_prof[key == MPM_COUNTER_PHASE_EXTRACT_NS ? 8 : 9];
         return MPM_OK;

@@ -29,7 +29,8 @@ constexpr uint32_t F_BOX = 128u;   // voxel lies inside the box (not tile paddin
 
 constexpr int kBlock = 256;        // threads per CTA of every kernel
 constexpr int kWarps = kBlock / 32;
-constexpr int kProfSlots = 10;      // phase timer: [-, wait, reduce, serial, R, P1, P2, U, extract, scatter]
+constexpr int kProfSlots = 15;      // phase timer: [-, wait, reduce, serial, R, P1, P2, U, extract, scatter,
+                                    //  extraction phases A..E]
 constexpr int kMaxSpecies = MPM_MAX_SPECIES;
 constexpr int kMaxM = MPM_MAX_RESTART;
 constexpr int kKStride = kMaxM + 2;           // partial slots per species

@@ -1537,6 +1537,7 @@ static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, con
     X.ra.q_cell = prm->q_cell;
     X.ra.dk = T->d_rates;
     X.ra.dq = T->d_rates + (size_t)prm->nspecies * prm->ncell;
+    X.prof = ctx->phase_prof ? ctx->d_prof : nullptr;
     A.S = step_sys(sub, lat, prm, T->d_rates);
     A.o.box = d_box;
     A.o.count = (const unsigned long long *)d_count;

@@ -161,6 +161,7 @@ struct ExtractArgs {
     uint32_t *srep;
     int32_t nrep_words;
     RateArgs ra;
+    unsigned long long *prof;          // nullable: CTA 0 adds ns per phase A..E (each up to its barrier)
 };
 
 // Block-wide sum over NT threads (every thread gets the total).
@@ -202,6 +203,15 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
     __shared__ RowTab tab;
     __shared__ int32_t wtot[NT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool prof = A.prof != nullptr && b == 0 && tid == 0;
+    uint64_t tp = prof ? globaltimer_ns() : 0;
+    auto tick = [&](int slot) {
+        if (prof) {
+            const uint64_t t = globaltimer_ns();
+            A.prof[slot] += t - tp;
+            tp = t;
+        }
+    };
     if (b == 0 && tid == 0) { A.dyn->NE = 0; A.dyn->g.n[0] = 0; }
     // ---- A: bounding box, per CTA
     {
@@ -255,6 +265,7 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         }
     }
     if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
+    tick(10);
     // ---- B: the box (every CTA), tile activity, in-mask count, rate tables
     {
         int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {-1, -1, -1};
@@ -317,6 +328,7 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         if (tid == 0) A.part_cnt[2 * b + 0] = cnt;
     }
     if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
+    tick(11);
     // ---- C: active tiles of this CTA's chunk (8-tile words)
     const int32_t ntiles = g.n[0] > 0 ? g.nt[0] * g.nt[1] * g.nt[2] : 0;
     const int32_t nwords = (ntiles + 7) >> 3;
@@ -336,6 +348,7 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         if (tid == 0) A.part_cnt[2 * b + 1] = c;
     }
     if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
+    tick(12);
     // ---- D: compaction
     int64_t nact = 0;
     {
@@ -405,6 +418,7 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         }
     }
     if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
+    tick(13);
     // ---- E: gather + rows of every stored element, neighbour table
     const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
     const int64_t NE = g.n[0] > 0 ? nact << ltv : 0;
@@ -428,6 +442,7 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         A.dyn->g = g;
         A.dyn->NE = NE;
     }
+    tick(14);
     return true;
 }
 

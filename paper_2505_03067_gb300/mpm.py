@@ -256,7 +256,9 @@ class Context:
         """CTA-0 time split of the last solve (needs debug_set(DEBUG_PHASE_TIMES, 1))."""
         return {k: self.counter(c) / 1e3 for k, c in (("work", 2), ("wait", 3), ("reduce", 4), ("serial", 5),
                                                       ("R", 6), ("P1", 7), ("P2", 8), ("U", 9),
-                                                      ("extract", 12), ("scatter", 13))}
+                                                      ("extract", 12), ("scatter", 13), ("x_bbox", 14),
+                                                      ("x_activity", 15), ("x_count", 16), ("x_compact", 17),
+                                                      ("x_gather", 18))}
 
     def debug_set(self, key: int, value: int):
         self._check(self.lib.mpm_debug_set(self.ptr, key, value), "mpm_debug_set")
