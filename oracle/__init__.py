@@ -325,3 +325,106 @@ def cnn_param_slices():
         out.append((slice(o, o + 27 * ci * co), slice(o + 27 * ci * co, o + 27 * ci * co + co), ci, co))
         o += 27 * ci * co + co
     return out
+
+
+# ---------------------------------------------------------------- flexible GMRES with the network (row a13)
+def fgmres(A: CSR, b, x0, M, restart: int = 30, tol_abs: float = 1e-12, maxit: int = 10000):
+    """Right-preconditioned flexible GMRES(m): the Arnoldi process runs on
+    A z_j with z_j = M(v_j) for a preconditioner M that may change from one
+    application to the next, modified Gram-Schmidt, Givens rotations for the
+    least-squares problem, and the update x += Z y from the preconditioned
+    directions; a cycle restarts from the true residual.  Plain NumPy."""
+    b = np.asarray(b, np.float64).reshape(-1)
+    x = np.array(x0, np.float64).reshape(-1).copy()
+    it = cyc = 0
+    status = ERR_NOCONV
+    while True:
+        r = b - A.matvec(x)
+        beta = float(np.sqrt(r @ r))
+        if not np.isfinite(beta):
+            status = ERR_BREAKDOWN
+            break
+        if beta <= tol_abs:
+            status = OK
+            break
+        if it >= maxit:
+            break
+        cyc += 1
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        k = 0
+        for j in range(restart):
+            z = np.asarray(M(V[j]), np.float64).reshape(-1)
+            Z.append(z)
+            w = A.matvec(z)
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            hn = float(np.sqrt(w @ w))
+            H[j + 1, j] = hn
+            for i in range(j):
+                t0, t1 = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * t0 + sn[i] * t1
+                H[i + 1, j] = -sn[i] * t0 + cs[i] * t1
+            den = float(np.hypot(H[j, j], hn))
+            cs[j], sn[j] = (1.0, 0.0) if den == 0.0 else (H[j, j] / den, hn / den)
+            H[j, j] = cs[j] * H[j, j] + sn[j] * hn
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            k = j + 1
+            if hn > 0.0:
+                V.append(w / hn)
+            if abs(g[j + 1]) <= tol_abs or it >= maxit or hn == 0.0:
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        for i in range(k):
+            x = x + y[i] * Z[i]
+    r = b - A.matvec(x)
+    return x, {"status": status, "iters": it, "cycles": cyc, "res": float(np.sqrt(r @ r))}
+
+
+def cnn_precond_inputs(v_box, s, cell_box, mask_box, params):
+    """Inputs of the network used as a preconditioner for species s: the
+    network's nine channels with the field of species s set to v (scaled as
+    the features scale it: 1, 1, 20 for species 0, 1, 2), the other fields and
+    the source map at zero (homogeneous problem), the medium / tumour one-hot,
+    the uptake maps 10 k_0, 10 k_1 and the mask; BF16-rounded like the device
+    features.  Returns x (nz, ny, nx, 9) and fields (nz, ny, nx, 3)."""
+    nz, ny, nx = mask_box.shape
+    x = np.zeros((nz, ny, nx, 9))
+    f = np.zeros((nz, ny, nx, 3))
+    fscale = (1.0, 1.0, 20.0)
+    vf = np.asarray(v_box, np.float64).astype(np.float32).astype(np.float64)
+    f[..., s] = vf
+    x[..., s] = bf16((vf * np.float32(fscale[s])).astype(np.float32))
+    cid = np.where((cell_box >= 0) & (cell_box < params.ncell), cell_box, 0)
+    x[..., 3] = (cid == 0)
+    x[..., 4] = (cid > 0)
+    if params.nspecies > 0:
+        x[..., 5] = bf16((np.float32(10.0) * params.k_cell[0][cid].astype(np.float32)).astype(np.float32))
+    if params.nspecies > 1:
+        x[..., 6] = bf16((np.float32(10.0) * params.k_cell[1][cid].astype(np.float32)).astype(np.float32))
+    x[..., 8] = (mask_box > 0)
+    return x, f
+
+
+def cnn_precond(v_box, s, cell_box, mask_box, params, net_params, s_out):
+    """The network as a (nonlinear) right preconditioner for species s: with
+    m = max |v|, z = m * net(v / m)[s] on the in-mask voxels, 0 elsewhere
+    (m scales v into the range the network was trained on)."""
+    v = np.asarray(v_box, np.float64)
+    m = float(np.max(np.abs(v)))
+    if m == 0.0:
+        return np.zeros_like(v)
+    x, f = cnn_precond_inputs(v / m, s, cell_box, mask_box, params)
+    pred, _ = cnn_forward(x, f, bf16(np.asarray(net_params, np.float64)), s_out)
+    return np.where(mask_box > 0, m * pred[..., s], 0.0)
