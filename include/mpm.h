@@ -326,6 +326,31 @@ mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *cnn, const void *x_bf16, co
 mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
                          const mpm_params *prm, void *stream);
 
+/*
+ * Solve every species of an assembled subgrid by right-preconditioned
+ * flexible GMRES(opt->restart) with the network as the preconditioner: for a
+ * Krylov vector v of species s, z = m * net(v / m)[s] on the in-mask voxels
+ * (m = max |v|), the network's inputs being v in the field channel of s, the
+ * other fields and the source map at zero, and the lattice's cell ids, uptake
+ * maps and mask over the box (the homogeneous problem, whose solution operator
+ * is A^-1).  Modified Gram-Schmidt, Givens rotations, the update from the
+ * preconditioned directions, restarts from the true FP64 residual; stopping
+ * rule and statuses as mpm_solve_step, in FP64 (opt->precision is ignored).
+ * x0 is c^n, or the iterate as it stands with opt->x0_given = 1 (for
+ * instance after mpm_cnn_guess).  scatter_to (nullable) receives the result
+ * as in mpm_solve_step.  The box must fit the network (mpm_cnn_create's
+ * max_voxels); species 0..2 only.  Synchronises `stream` once per Arnoldi
+ * step: this is the learned solver's reference path, not the fast one.
+ */
+/* The preconditioner of mpm_solve_fgmres_cnn applied to one box-dense FP64
+ * vector v of species s (device, nx*ny*nz): z (device, box-dense) = the
+ * network's z on the stored in-mask voxels, 0 elsewhere.  Queued on `stream`. */
+mpm_status mpm_cnn_precond(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
+                           const mpm_params *prm, int32_t s, const double *v, double *z, void *stream);
+mpm_status mpm_solve_fgmres_cnn(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
+                                const mpm_params *prm, const mpm_lattice *scatter_to, const mpm_opts *opt,
+                                mpm_report *rep, void *stream);
+
 /* Copy `what` of species s from the subgrid into dst (device, box-dense,
  * nx*ny*nz elements of the export type).  Voxels of tiles that hold no
  * in-mask voxel are not stored: they receive 0 (1 for DIAG).  Queued on

@@ -111,6 +111,7 @@ mpm_status mpm_destroy(mpm_ctx *ctx)
     cudaFree(ctx->d_bar);
     cudaFree(ctx->d_args);
     cudaFree(ctx->d_tmp);
+    cudaFree(ctx->d_fg);
     cudaFree(ctx->d_prof);
     cudaFree(ctx->d_tune);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -229,6 +230,15 @@ mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_bo
     if (!ctx) return MPM_ERR_ARG;
     ctx->err.clear();
     return mpm_step_wait_impl(ctx, sub, rep, out_box, (cudaStream_t)stream);
+}
+
+mpm_status mpm_solve_fgmres_cnn(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
+                                const mpm_params *prm, const mpm_lattice *scatter_to, const mpm_opts *opt,
+                                mpm_report *rep, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_solve_fgmres_impl(ctx, cnn, sub, lat, prm, scatter_to, opt, rep, (cudaStream_t)stream);
 }
 
 mpm_status mpm_subgrid_export(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t what, int32_t s, void *dst, void *stream)

@@ -203,3 +203,18 @@ mpm_status mpm_apply_impl(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const
     }
     return mpm_elems_to_dense(ctx, sub, ye, x, y, st);
 }
+
+// y = A x on compact element vectors of species s (no box-dense conversion).
+mpm_status mpm_apply_compact(mpm_ctx *ctx, const mpm_subgrid *sub, int32_t s, const double *x, double *y,
+                             cudaStream_t st)
+{
+    if (!sub->assembled) return mpm_fail(ctx, MPM_ERR_ARG, "apply: subgrid not assembled");
+    if (sub->NE == 0) return MPM_OK;
+    const SysDev S = mpm_make_sysdev(sub);
+    int64_t g = (sub->NE + kBlock - 1) / kBlock;
+    if (g > (int64_t)ctx->num_sms * 8) g = (int64_t)ctx->num_sms * 8;
+    k_apply<<<(int)g, kBlock, 0, st>>>(S, s, x, y, sub->a, sub->Dsp[s]);
+    ctx->launches += 1;
+    MPM_CU(cudaGetLastError());
+    return MPM_OK;
+}

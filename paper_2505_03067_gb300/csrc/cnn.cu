@@ -684,3 +684,168 @@ extern "C" mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *c, const void *x
     return MPM_OK;
 }
 
+
+// ---------------------------------------------------------------- the network as a preconditioner
+// Row a13: flexible GMRES applies z = m * net(v / m) to a vector v of one
+// species (m = max |v|, which puts v in the range the network was trained
+// on), with the other fields and the source map at zero (the homogeneous
+// problem), and keeps z on the in-mask voxels only.
+namespace mpm {
+
+struct PcArgs {
+    BoxGeo g;                      // the subgrid's box
+    const int32_t *tile_index;     // box tile -> compact tile (-1: not stored)
+    const int32_t *tile_coord;
+    const uint8_t *flags;          // compact
+    const int32_t *cell;           // lattice
+    const uint8_t *mask;           // lattice
+    const double *k_cell;
+    int nspecies, ncell, s;
+    const double *v;               // compact input
+    double *z;                     // compact output
+    const double *scale;           // device scalar m
+    __nv_bfloat16 *x;              // [V][16]
+    float *fields;                 // [V][3]
+    const float *pred;             // [V][3]
+    int64_t NE;
+};
+
+__global__ void k_pc_amax(const double *__restrict__ v, int64_t n, double *__restrict__ out)
+{
+    __shared__ double sh[32];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, sh[i]);
+        *out = t;
+    }
+}
+
+__global__ void k_pc_features(PcArgs P)
+{
+    const BoxGeo &g = P.g;
+    const long long V = (long long)g.n[0] * g.n[1] * g.n[2];
+    const double m = *P.scale;
+    const float fscale[3] = {1.0f, 1.0f, 20.0f};
+    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < V; d += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(d % g.n[0]);
+        const long long r = d / g.n[0];
+        const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+        const int32_t t = P.tile_index[((long long)(k >> g.lt[2]) * g.nt[1] + (j >> g.lt[1])) * g.nt[0] + (i >> g.lt[0])];
+        double val = 0.0;
+        if (t >= 0 && m > 0.0) {
+            const int ix = i & ((1 << g.lt[0]) - 1), iy = j & ((1 << g.lt[1]) - 1), iz = k & ((1 << g.lt[2]) - 1);
+            const int64_t e = ((int64_t)t << ltv) + ix + ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
+            val = P.v[e] / m;
+        }
+        const long long L = (long long)(g.lo[0] + i) + (long long)g.Lx * ((g.lo[1] + j) + (long long)g.Ly * (g.lo[2] + k));
+        int id = P.cell[L];
+        if (id < 0 || id >= P.ncell) id = 0;
+        float f[kInStride];
+#pragma unroll
+        for (int c = 0; c < kInStride; ++c) f[c] = 0.0f;
+        const float vf = (float)val;
+        for (int c = 0; c < 3; ++c) P.fields[d * 3 + c] = c == P.s ? vf : 0.0f;
+        f[P.s] = vf * fscale[P.s];
+        f[3] = id == 0 ? 1.0f : 0.0f;
+        f[4] = id > 0 ? 1.0f : 0.0f;
+        f[5] = P.nspecies > 0 ? (float)P.k_cell[id] * 10.0f : 0.0f;
+        f[6] = P.nspecies > 1 ? (float)P.k_cell[P.ncell + id] * 10.0f : 0.0f;
+        f[8] = P.mask[L] ? 1.0f : 0.0f;
+#pragma unroll
+        for (int c = 0; c < kInStride; c += 2)
+            *reinterpret_cast<__nv_bfloat162 *>(P.x + d * kInStride + c) = __floats2bfloat162_rn(f[c], f[c + 1]);
+    }
+}
+
+__global__ void k_pc_out(PcArgs P)
+{
+    const BoxGeo &g = P.g;
+    const double m = *P.scale;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.NE; e += (int64_t)gridDim.x * blockDim.x) {
+        double zv = 0.0;
+        if ((P.flags[e] & F_MASK) && m > 0.0) {
+            int bx, by, bz;
+            elem_box(e, g, P.tile_coord, bx, by, bz);
+            const int64_t d = bx + (int64_t)g.n[0] * (by + (int64_t)g.n[1] * bz);
+            zv = m * (double)P.pred[d * 3 + P.s];
+        }
+        P.z[e] = zv;
+    }
+}
+
+}  // namespace mpm
+
+// z = the network's preconditioner applied to v (compact FP64 vectors of
+// species s of sub); d_scale: one device double of scratch.  Stream work only.
+mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                                const mpm_params *prm, int s, const double *v, double *z, double *d_scale,
+                                cudaStream_t st)
+{
+    const long long V = (long long)sub->n[0] * sub->n[1] * sub->n[2];
+    if (V > c->maxV) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: box larger than the network was created for");
+    if (s < 0 || s > 2) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: the network covers species 0..2");
+    PcArgs P;
+    memset(&P, 0, sizeof(P));
+    P.g = make_geo(sub, lat->dims);
+    P.tile_index = sub->tile_index;
+    P.tile_coord = sub->tile_coord;
+    P.flags = sub->flags;
+    P.cell = lat->cell_id;
+    P.mask = lat->mask;
+    P.k_cell = prm->k_cell;
+    P.nspecies = prm->nspecies;
+    P.ncell = prm->ncell;
+    P.s = s;
+    P.v = v;
+    P.z = z;
+    P.scale = d_scale;
+    P.x = c->gx;
+    P.fields = c->gfields;
+    P.pred = c->pred;
+    P.NE = sub->NE;
+    k_pc_amax<<<1, 1024, 0, st>>>(v, sub->NE, d_scale);
+    k_pc_features<<<ctx->num_sms * 4, 256, 0, st>>>(P);
+    ctx->launches += 2;
+    MPM_CU(cudaGetLastError());
+    mpm_status r = forward(ctx, c, c->gx, c->gfields, sub->n, 1, c->pred, st);
+    if (r != MPM_OK) return r;
+    k_pc_out<<<ctx->num_sms * 4, 256, 0, st>>>(P);
+    ctx->launches += 1;
+    MPM_CU(cudaGetLastError());
+    return MPM_OK;
+}
+
+mpm_status mpm_dense_to_elems(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, double *dst, cudaStream_t st);
+mpm_status mpm_elems_to_dense(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, const double *dflt_dense,
+                              double *dst, cudaStream_t st);
+
+extern "C" mpm_status mpm_cnn_precond(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                                      const mpm_params *prm, int32_t s, const double *v, double *z, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !sub || !lat || !prm || !v || !z) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: null argument");
+    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: subgrid not extracted");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vec = (size_t)(sub->NE > 0 ? sub->NE : 1);
+    mpm_status r = mpm_grow(ctx, (void **)&ctx->d_fg, &ctx->fg_cap, (2 * vec + 8) * sizeof(double), "precond scratch");
+    if (r != MPM_OK) return r;
+    double *ve = ctx->d_fg, *ze = ve + vec, *scal = ze + vec;
+    if (sub->NE > 0) {
+        r = mpm_dense_to_elems(ctx, sub, v, ve, st);
+        if (r != MPM_OK) return r;
+        r = mpm_cnn_precond_impl(ctx, c, sub, lat, prm, s, ve, ze, scal, st);
+        if (r != MPM_OK) return r;
+    }
+    const long long V = (long long)sub->n[0] * sub->n[1] * sub->n[2];
+    MPM_CU(cudaMemsetAsync(z, 0, (size_t)V * sizeof(double), st));
+    if (sub->NE == 0) return MPM_OK;
+    return mpm_elems_to_dense(ctx, sub, ze, z, z, st);
+}

@@ -373,6 +373,8 @@ struct mpm_ctx {
     void *h_stage = nullptr;     // pinned staging for descriptors and reports
     size_t stage_cap = 0;
     double *d_tmp = nullptr;     // element scratch for apply_operator
+    double *d_fg = nullptr;      // flexible GMRES workspace
+    size_t fg_cap = 0;
     size_t tmp_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t launches = 0;        // kernels launched by this context
@@ -485,6 +487,9 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
 mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
                                  int32_t margin, const int32_t tile[3], const mpm_opts *opt, cudaStream_t st);
 mpm_status mpm_step_wait_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, cudaStream_t st);
+mpm_status mpm_solve_fgmres_impl(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
+                                 const mpm_params *prm, const mpm_lattice *scatter_to, const mpm_opts *opt,
+                                 mpm_report *rep, cudaStream_t st);
 void mpm_step_free(mpm_ctx *ctx, mpm_subgrid *sub);
 void mpm_step_invalidate(mpm_subgrid *sub);
 int mpm_batch_graph_active(mpm_ctx *ctx);

@@ -30,7 +30,7 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
            "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
-           "mpm_step", "mpm_step_enqueue", "mpm_step_wait"]
+           "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond"]
 
 
 class mpm_box(C.Structure):
@@ -112,6 +112,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_cnn_train_step": [P, P, P, P, P, C.POINTER(C.c_int32), C.c_int32, C.c_float, C.c_int32,
                                C.POINTER(C.c_double), P],
         "mpm_cnn_guess": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), P],
+        "mpm_solve_fgmres_cnn": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_lattice),
+                                 C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
+        "mpm_cnn_precond": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, P, P, P],
         "mpm_tune_tile": [P, C.POINTER(mpm_lattice), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), P],
         "mpm_tune_solver": [P, C.POINTER(P), C.c_int32, C.POINTER(mpm_opts), C.POINTER(C.c_int32), C.c_char_p, P],
         "mpm_batch_step": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.POINTER(C.POINTER(mpm_params)),
@@ -587,3 +590,28 @@ class CNN:
         ls = lat.struct()
         self.ctx._check(self.ctx.lib.mpm_cnn_guess(self.ctx.ptr, self.h, sub.h, C.byref(ls), C.byref(prm.struct),
                                                    _stream_ptr(stream)), "mpm_cnn_guess")
+
+    def precond(self, sub: Subgrid, lat: DeviceLattice, prm: DeviceParams, s: int, v, stream=None):
+        """The FGMRES preconditioner on a box-dense FP64 tensor v (mpm_cnn_precond)."""
+        import torch
+        z = torch.empty_like(v)
+        ls = lat.struct()
+        self.ctx._check(self.ctx.lib.mpm_cnn_precond(self.ctx.ptr, self.h, sub.h, C.byref(ls), C.byref(prm.struct),
+                                                     int(s), v.data_ptr(), z.data_ptr(), _stream_ptr(stream)),
+                        "mpm_cnn_precond")
+        return z
+
+    def solve_fgmres(self, sub: Subgrid, lat: DeviceLattice, prm: DeviceParams, opts: mpm_opts,
+                     scatter_to: DeviceLattice | None = None, stream=None, allow=(ERR_NOCONV,)):
+        """Flexible GMRES with this network as the right preconditioner
+        (mpm_solve_fgmres_cnn) on an assembled subgrid."""
+        rep = mpm_report()
+        ls = lat.struct()
+        ss = scatter_to.struct() if scatter_to is not None else None
+        st = self.ctx.lib.mpm_solve_fgmres_cnn(self.ctx.ptr, self.h, sub.h, C.byref(ls), C.byref(prm.struct),
+                                               C.byref(ss) if ss is not None else None, C.byref(opts),
+                                               C.byref(rep), _stream_ptr(stream))
+        self.ctx._check(st, "mpm_solve_fgmres_cnn", allow=allow)
+        d = rep.as_dict(sub.nspecies)
+        d["status_code"] = st
+        return d
