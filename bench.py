@@ -296,10 +296,12 @@ def bench_growth512(mpm, W, ctx, stream, flush, sample=range(0, 201, 20)):
 
 
 def bench_learned(mpm, ctx, samples=20000):
-    """The learned warm start: train the network on `samples` pairs generated by the
-    FP64 solver on the GPU (32^3 sphere-like lattices), then time the 32^3 sphere
-    workload to 1e-6 with x0 = c^n and with x0 = the network's prediction, FP64
-    and FP32-in-FP64 (device time includes features + forward)."""
+    """The learned solver: train the network on `samples` pairs generated by the
+    FP64 solver on the GPU (32^3 sphere-like lattices, a quarter of them
+    homogeneous problems), then time the 32^3 sphere workload to 1e-6 with
+    x0 = c^n and with x0 = the network's prediction, FP64 and FP32-in-FP64
+    (device time includes features + forward), and with flexible GMRES using
+    the network as the right preconditioner (from c^n and from the guess)."""
     from paper_2505_03067_gb300 import learned
     cnn, hist = learned.train(ctx, samples=samples)
     out = {"train_seconds": hist["seconds"], "samples": hist["samples"],
@@ -310,6 +312,12 @@ def bench_learned(mpm, ctx, samples=20000):
             e = ev[k]
             out[f"{name}_{k}"] = {"value": 32 ** 3 / (e["ms_per_step"] / 1e3), "ms_per_step": e["ms_per_step"],
                                   "iters_per_step": e["iters_per_step"], "max_rel_res": e["max_rel_res"]}
+    # row a13: flexible GMRES with the network as the right preconditioner (FP64)
+    ev = learned.evaluate_fgmres_sphere32(ctx, cnn, rtol=1e-6)
+    for k in ("fgmres", "guess_fgmres"):
+        e = ev[k]
+        out[f"fp64_{k}"] = {"value": 32 ** 3 / (e["ms_per_step"] / 1e3), "ms_per_step": e["ms_per_step"],
+                            "iters_per_step": e["iters_per_step"], "max_rel_res": e["max_rel_res"]}
     cnn.close()
     return out
 

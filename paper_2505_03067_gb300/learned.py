@@ -19,8 +19,8 @@ from . import workloads as W
 
 
 class _Traj:
-    def __init__(self, ctx, rng, n):
-        self.wl = W.sphere_training_case(rng, n)
+    def __init__(self, ctx, rng, n, homogeneous_frac=0.0):
+        self.wl = W.sphere_training_case(rng, n, homogeneous=bool(rng.random() < homogeneous_frac))
         self.lat = mpm.DeviceLattice(self.wl.lattice)
         self.prm = mpm.DeviceParams(self.wl.params)
         self.solver = mpm.StepSolver(ctx, self.lat, self.prm, self.wl.margin)
@@ -28,8 +28,11 @@ class _Traj:
 
 
 def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, lr: float = 2e-3,
-          traj_len: int = 12, seed: int = 4, params=None, log_every: int = 0):
-    """Train a fresh network (or `params`) on `samples` pairs; returns (CNN, history)."""
+          traj_len: int = 12, seed: int = 4, params=None, log_every: int = 0, homogeneous_frac: float = 0.25):
+    """Train a fresh network (or `params`) on `samples` pairs; returns (CNN, history).
+    A fraction homogeneous_frac of the trajectories are homogeneous problems
+    (zero sources and boundary values), whose pairs (v, A^-1 v) teach the
+    network the map it applies as the FGMRES preconditioner."""
     import torch
     rng = np.random.default_rng(seed)
     V = n ** 3
@@ -37,7 +40,7 @@ def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, l
     x = torch.empty((batch * V, 16), dtype=torch.bfloat16, device="cuda")
     f = torch.empty((batch * V, 3), dtype=torch.float32, device="cuda")
     tgt = torch.empty((batch * V, 3), dtype=torch.float32, device="cuda")
-    trajs = [_Traj(ctx, rng, n) for _ in range(batch)]
+    trajs = [_Traj(ctx, rng, n, homogeneous_frac) for _ in range(batch)]
     opts = mpm.make_opts(rtol=1e-10, restart=16, maxit=500)
     box = ((0, 0, 0), (n, n, n))
     hist = []
@@ -47,7 +50,7 @@ def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, l
         for b, tr in enumerate(trajs):
             if tr.age >= traj_len:
                 tr.solver.sub.destroy()
-                trajs[b] = tr = _Traj(ctx, rng, n)
+                trajs[b] = tr = _Traj(ctx, rng, n, homogeneous_frac)
             xb, fb = cnn.features(tr.lat, tr.prm, box)
             x[b * V:(b + 1) * V] = xb
             f[b * V:(b + 1) * V] = fb
@@ -93,4 +96,38 @@ def evaluate_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, precision: int 
             res.append(rep["res"][0] / rep["bnorm"][0])
         out["learned" if learned else "plain"] = {"iters_per_step": float(np.mean(its)), "ms_per_step": ms / steps,
                                                  "max_rel_res": float(max(res)), "final": lat.fields_numpy()}
+    return out
+
+
+def evaluate_fgmres_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, steps: int = 10, restart: int = 8):
+    """The 32^3 sphere workload advanced `steps` steps by flexible GMRES with the
+    network as the right preconditioner (mpm_solve_fgmres_cnn, FP64), from
+    x0 = c^n and from the learned guess.  Returns Arnoldi steps and device time
+    per step (extraction and assembly excluded, as in evaluate_sphere32)."""
+    import torch
+    wl = W.sphere32()
+    out = {}
+    for guess in (False, True):
+        lat = mpm.DeviceLattice(wl.lattice)
+        prm = mpm.DeviceParams(wl.params)
+        sub = ctx.subgrid_create()
+        its, ms, res = [], 0.0, []
+        stream = torch.cuda.current_stream()
+        for _ in range(steps):
+            sub.mpm_box_extract(lat, 1, wl.margin)
+            sub.mpm_assemble_coeffs(prm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if guess:
+                cnn.guess(sub, lat, prm)
+            rep = cnn.solve_fgmres(sub, lat, prm, mpm.make_opts(rtol=rtol, restart=restart, maxit=500,
+                                                                x0_given=int(guess)), scatter_to=lat)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            its.append(rep["iters"][0])
+            res.append(rep["res"][0] / rep["bnorm"][0])
+        out["guess_fgmres" if guess else "fgmres"] = {"iters_per_step": float(np.mean(its)),
+                                                       "ms_per_step": ms / steps, "max_rel_res": float(max(res)),
+                                                       "final": lat.fields_numpy()}
     return out

@@ -330,14 +330,19 @@ def random_case(seed: int, dims, nspecies: int = 3, p_mask: float = 0.8, p_tumou
 
 
 # --------------------------------------------------------------------------- learned warm start
-def sphere_training_case(rng, n: int = 32, three_species=None) -> Workload:
+def sphere_training_case(rng, n: int = 32, three_species=None, homogeneous: bool = False) -> Workload:
     """A 32^3 training lattice around the 32^3 sphere workload: every voxel in the
     domain, a solid tumour sphere of radius U[4, 12] at a random centre split into
     ~50 Voronoi cells; species 0 as in the sphere workload (D = 1, dt = 0.1,
     c0 = c_b = 1) with per-cell uptake U[0.01, 0.1].  Species 1-2 either carry the
     shell workload's nutrient and cytokine (D 0.5 / 0.2, per-cell uptake /
     secretion U[0.01, 0.1], cytokine decay 0.01, c_b 1 / 0) or are absent (all
-    zero), as in the single-species workload."""
+    zero), as in the single-species workload.  homogeneous: the same operators
+    with every boundary value and source at zero and one species, drawn at
+    random, carrying three Gaussian bumps (centres uniform, widths U[2, 8],
+    amplitudes U[-1, 1]) while the others are zero -- the next step is then
+    A^-1 applied to that field, the map the network approximates as a
+    preconditioner."""
     dims = (n, n, n)
     x, y, z = _grid(dims)
     r = rng.uniform(4.0, 12.0)
@@ -364,5 +369,14 @@ def sphere_training_case(rng, n: int = 32, three_species=None) -> Workload:
                         np.array([1.0, 1.0, 0.0]), k, q)
     else:
         params = Params(3, 0.1, 1.0, np.array([1.0, 1.0, 1.0]), np.zeros(3), np.array([1.0, 0.0, 0.0]), k, q)
+    if homogeneous:
+        sp = int(rng.integers(0, 3 if three else 1))
+        fields = np.zeros((3,) + x.shape)
+        for _ in range(3):
+            cc = rng.uniform(0, n - 1, size=3)
+            w = rng.uniform(2.0, 8.0)
+            fields[sp] += rng.uniform(-1.0, 1.0) * np.exp(-((x - cc[0]) ** 2 + (y - cc[1]) ** 2 + (z - cc[2]) ** 2)
+                                                         / (2 * w * w))
+        params = Params(3, params.dt, params.h, params.D, params.mu, np.zeros(3), params.k_cell, np.zeros_like(q))
     return Workload("sphere_train", Lattice(cell_id, np.ones(x.shape, np.uint8), fields), params, margin=n,
                     steps=10, rtol=1e-10, restart=30)

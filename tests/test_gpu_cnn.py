@@ -176,3 +176,8 @@ def test_trained_network_gain_on_sphere32(M):
     assert ev["learned"]["max_rel_res"] <= 1e-6 and ev["plain"]["max_rel_res"] <= 1e-6
     assert ev["learned"]["iters_per_step"] <= ev["plain"]["iters_per_step"]
     assert np.max(np.abs(ev["learned"]["final"] - ev["plain"]["final"])) <= 10 * 2e-6 * np.sqrt(32 ** 3)
+    # row a13: the same network as the right preconditioner of flexible GMRES
+    fg = learned.evaluate_fgmres_sphere32(ctx, cnn, rtol=1e-6)
+    for k in ("fgmres", "guess_fgmres"):
+        assert fg[k]["max_rel_res"] <= 1e-6, k
+        assert np.max(np.abs(fg[k]["final"] - ev["plain"]["final"])) <= 10 * 2e-6 * np.sqrt(32 ** 3), k
