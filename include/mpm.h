@@ -85,6 +85,10 @@ typedef struct {
     int32_t x0_given;       /* 1: the subgrid's current iterate is the initial guess
                                (set by mpm_subgrid_import); 0: c^n from the extract */
     int32_t nblocks;        /* 0: automatic; else the persistent grid size (tuning) */
+    int32_t reorth;         /* 1: a second classical Gram-Schmidt pass for an Arnoldi step whose
+                               ||w|| fell below 0.7 of its norm before orthogonalisation
+                               (the Daniel-Gragg-Kaufman-Stewart test; 0 or 1, else MPM_ERR_ARG; the modified
+                               Gram-Schmidt of mpm_solve_fgmres_cnn ignores it) */
 } mpm_opts;
 
 typedef struct {
@@ -101,6 +105,7 @@ typedef struct {
                                            mpm_batch_step: of the whole step) */
     double item_ms[MPM_MAX_SPECIES];    /* device time of each species' work item inside the
                                            persistent launch */
+    int32_t reorth[MPM_MAX_SPECIES];    /* Arnoldi steps that took the second Gram-Schmidt pass */
 } mpm_report;
 
 /* Shape of an extracted subgrid (host struct filled by mpm_subgrid_info). */

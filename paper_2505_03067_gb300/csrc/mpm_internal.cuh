@@ -175,6 +175,7 @@ struct SysReport {
     int32_t jsum[kMaxSpecies];
     double res[kMaxSpecies];
     double bnorm[kMaxSpecies];
+    int32_t reorth[kMaxSpecies];
     unsigned long long t_ns;    // device time of the item (its team's CTA 0)
 };
 
@@ -195,6 +196,7 @@ struct SolveArgs {
     int32_t m, maxit;
     uint64_t timeout_ns;
     int32_t skip_block;         // fault injection for tests: this block never arrives (-1 none)
+    int32_t reorth;             // second Gram-Schmidt pass when ||w|| < 0.7 ||w_before||
     unsigned long long *prof;   // nullable: CTA 0 adds ns spent in [-, wait, reduce, serial, R, P1, P2, U]
 };
 

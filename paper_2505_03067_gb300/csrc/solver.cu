@@ -41,7 +41,9 @@ constexpr int kSB = 512;            // default solver CTA size (16 warps); varia
 
 struct SpState {
     double beta, bnorm, tol, tol_in;
+    double wwb;                       // ||w||^2 before the orthogonalisation (reorthogonalisation test)
     int32_t it, cyc, status, in_cycle, k, done, bad, jsum;
+    int32_t reo, nreo;                // second Gram-Schmidt pass due / passes so far
 };
 
 // Species are processed in groups of NSG inside one element loop, so the face
@@ -283,7 +285,7 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
 // ---- P1: w = sigma_j A u_j into slot j+1; acc[i] += u_i . w for i <= j
 template <typename T, int MAXM, int U>
 __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
-                                              T (&acc)[MAXM + 1])
+                                              T (&acc)[MAXM + 1], bool want_ww)
 {
     const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
@@ -326,6 +328,7 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
             for (int i = 0; i <= MAXM; ++i) {
                 if (i < j) acc[i] += V[(int64_t)i * vs + eu] * w[u];
                 else if (i == j) acc[i] += xj[u] * w[u];
+                else if (i == j + 1 && want_ww) acc[i] += w[u] * w[u];
             }
         }
 #pragma unroll
@@ -360,6 +363,26 @@ __device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c
         for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
             if (eu < NE) ((T *)S.V[0])[(int64_t)(j + 1) * vs + eu] = w[u];
+        }
+    }
+}
+
+// ---- P1b (reorthogonalisation): acc[i] += u_i . w for i <= j, w in slot j+1
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_dots(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
+{
+    const uint32_t NE = (uint32_t)S.NE;
+    const int64_t vs = S.vstride;
+    const T *V = (const T *)S.V[0];
+    for (uint32_t e = e0; e < NE; e += U * es) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu >= NE) continue;
+            const T w = V[(int64_t)(j + 1) * vs + eu];
+#pragma unroll
+            for (int i = 0; i <= MAXM; ++i)
+                if (i <= j) acc[i] += V[(int64_t)i * vs + eu] * w;
         }
     }
 }
@@ -445,6 +468,8 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
             SpState &p = sm.sp[tid];
             p.beta = p.bnorm = p.tol = p.tol_in = 0.0;
             p.it = p.cyc = p.in_cycle = p.k = p.bad = p.jsum = 0;
+            p.wwb = 0.0;
+            p.reo = p.nreo = 0;
             p.done = bad_id ? 1 : 0;
             p.status = bad_id ? MPM_ERR_ARG : ST_RUN;
         }
@@ -505,11 +530,11 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
                     T acc[1][MAXM + 1];
 #pragma unroll
                     for (int i = 0; i <= MAXM; ++i) acc[0][i] = T(0);
-                    pass_arnoldi1<T, MAXM, U>(S, j, sm.sig[0][j], e0, es, acc[0]);
-                    block_reduce_g<1, MAXM + 1, T, NT>(acc, 1u, j + 1, 0, sm.red, mypart);
+                    pass_arnoldi1<T, MAXM, U>(S, j, sm.sig[0][j], e0, es, acc[0], A.reorth != 0);
+                    block_reduce_g<1, MAXM + 1, T, NT>(acc, 1u, j + 1 + (A.reorth != 0), 0, sm.red, mypart);
                 }
                 MPM_BARRIER();
-                team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1, sm.tot);
+                team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1 + (A.reorth != 0), sm.tot);
                 MPM_TICK(2);
                 pbuf ^= 1;
                 if (tid < NS && ((cm >> tid) & 1u)) {
@@ -520,6 +545,7 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
                         if (kF32) sm.coef32[tid][i] = (float)c;
                         else sm.coef[tid][i] = (double)c;
                     }
+                    if (A.reorth) sm.sp[tid].wwb = sm.tot[tid * kKStride + j + 1];
                 }
                 __syncthreads();
                 MPM_TICK(3);
@@ -534,6 +560,51 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
                 team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, 1, sm.tot);
                 MPM_TICK(2);
                 pbuf ^= 1;
+                // optional second classical Gram-Schmidt pass (opt->reorth) when the
+                // orthogonalisation removed most of w: ||w|| < 0.7 ||w_before||
+                if (tid < NS && ((cm >> tid) & 1u))
+                    sm.sp[tid].reo = A.reorth && sm.tot[tid * kKStride] < 0.49 * sm.sp[tid].wwb ? 1 : 0;
+                __syncthreads();
+                bool reo = false;   // uniform over the team: every CTA reads the same totals
+                for (int s = 0; s < NS; ++s) reo |= ((cm >> s) & 1u) && sm.sp[s].reo;
+                if (reo) {
+                    mypart = A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax;
+                    wcat = 5;
+                    {
+                        T acc[1][MAXM + 1];
+#pragma unroll
+                        for (int i = 0; i <= MAXM; ++i) acc[0][i] = T(0);
+                        pass_dots<T, MAXM, U>(S, j, e0, es, acc[0]);
+                        block_reduce_g<1, MAXM + 1, T, NT>(acc, 1u, j + 1, 0, sm.red, mypart);
+                    }
+                    MPM_BARRIER();
+                    team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1, sm.tot);
+                    MPM_TICK(2);
+                    pbuf ^= 1;
+                    if (tid < NS && ((cm >> tid) & 1u)) {
+                        for (int i = 0; i <= j; ++i) {   // h_ij += sigma_i (u_i . w); subtract sigma_i^2 (u_i . w) u_i
+                            const T d = (T)sm.tot[tid * kKStride + i];
+                            sm.H[tid][i * MAXM + j] += sm.sig[tid][i] * d;
+                            const T c = sm.sig[tid][i] * sm.sig[tid][i] * d;
+                            if (kF32) sm.coef32[tid][i] = (float)c;
+                            else sm.coef[tid][i] = (double)c;
+                        }
+                        sm.sp[tid].nreo += 1;
+                    }
+                    __syncthreads();
+                    MPM_TICK(3);
+                    mypart = A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax;
+                    wcat = 6;
+                    {
+                        T acc[1][1] = {{T(0)}};
+                        pass_arnoldi2<T, MAXM, U>(S, j, coefT, e0, es, acc[0][0]);
+                        block_reduce_g<1, 1, T, NT>(acc, 1u, 1, 0, sm.red, mypart);
+                    }
+                    MPM_BARRIER();
+                    team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, 1, sm.tot);
+                    MPM_TICK(2);
+                    pbuf ^= 1;
+                }
                 if (tid < NS && ((cm >> tid) & 1u)) {
                     SpState &p = sm.sp[tid];
                     T *H = sm.H[tid];
@@ -612,6 +683,7 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
             R->jsum[tid] = p.jsum;
             R->res[tid] = p.beta;
             R->bnorm[tid] = p.bnorm;
+            R->reorth[tid] = p.nreo;
             R->t_ns = globaltimer_ns() - t_item0;
         }
         __syncthreads();
@@ -737,7 +809,8 @@ static Variant var_of()
 // at two CTAs/SM of 512, 3: two elements at one CTA/SM of 512, 4: one element
 // at one CTA/SM of 1024, 5: one element at two CTAs/SM of 512 (64
 // registers).  FP64, m <= 8: 0: two elements at one CTA/SM of 512, 1: one
-// element at two CTAs/SM, 2: one element at one CTA/SM of 1024.
+// element at two CTAs/SM, 2: one element at one CTA/SM of 1024, 3: one
+// element at one CTA/SM of 768, 4: two elements at one CTA/SM of 768.
 static Variant pick(int prec, int maxm, int variant)
 {
     if (prec == 0) {
@@ -745,6 +818,8 @@ static Variant pick(int prec, int maxm, int variant)
             switch (variant) {
             case 1: return var_of<double, 8, 1, 2, 512>();
             case 2: return var_of<double, 8, 1, 1, 1024>();
+            case 3: return var_of<double, 8, 1, 1, 768>();
+            case 4: return var_of<double, 8, 2, 1, 768>();
             default: return var_of<double, 8, 2, 1, 512>();
             }
         }
@@ -814,7 +889,7 @@ int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 int mpm_solver_variants(int prec, int m)
 {
     if (m > 8) return 1;
-    return prec == 1 ? 6 : 3;
+    return prec == 1 ? 6 : 5;
 }
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -945,6 +1020,7 @@ static mpm_status check_opts(mpm_ctx *ctx, const mpm_opts *opt)
     if (opt->restart < 1 || opt->restart > MPM_MAX_RESTART) return mpm_fail(ctx, MPM_ERR_ARG, "solve: restart out of [1, 32]");
     if (opt->maxit < 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: maxit < 1");
     if (opt->precision != 0 && opt->precision != 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: precision must be 0 or 1");
+    if (opt->reorth != 0 && opt->reorth != 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: reorth must be 0 or 1");
     if (!(opt->rtol >= 0.0) || !(opt->atol >= 0.0)) return mpm_fail(ctx, MPM_ERR_ARG, "solve: negative tolerance");
     if (opt->precision == 1 && !(opt->inner_rtol > 0.0 && opt->inner_rtol < 1.0))
         return mpm_fail(ctx, MPM_ERR_ARG, "solve: inner_rtol must be in (0, 1)");
@@ -1052,6 +1128,7 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
     sa.rtol = opt->rtol;
     sa.atol = opt->atol;
     sa.inner_rtol = opt->precision ? opt->inner_rtol : 0.0;
+    sa.reorth = opt->reorth;
     sa.m = m;
     sa.maxit = opt->maxit;
     sa.timeout_ns = ctx->timeout_ns;
@@ -1146,6 +1223,7 @@ static mpm_status finish_solve(mpm_ctx *ctx, const SolvePlan &P, mpm_subgrid *co
         R[i].status[s] = stt;
         R[i].res[s] = hrep[it].res[0];
         R[i].bnorm[s] = hrep[it].bnorm[0];
+        R[i].reorth[s] = hrep[it].reorth[0];
         if (status_rank(stt) > status_rank(worst)) worst = (mpm_status)stt;
     }
     for (int i = 0; i < P.nsys; ++i) {

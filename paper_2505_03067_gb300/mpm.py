@@ -55,7 +55,7 @@ class mpm_params(C.Structure):
 class mpm_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
                 ("precision", C.c_int32), ("inner_rtol", C.c_double), ("x0_given", C.c_int32),
-                ("nblocks", C.c_int32)]
+                ("nblocks", C.c_int32), ("reorth", C.c_int32)]
 
 
 class mpm_report(C.Structure):
@@ -63,7 +63,8 @@ class mpm_report(C.Structure):
                 ("status", C.c_int32 * MAX_SPECIES), ("jsum", C.c_int32 * MAX_SPECIES),
                 ("res", C.c_double * MAX_SPECIES),
                 ("bnorm", C.c_double * MAX_SPECIES), ("box_voxels", C.c_int64), ("mask_voxels", C.c_int64),
-                ("stored_voxels", C.c_int64), ("solve_ms", C.c_double), ("item_ms", C.c_double * MAX_SPECIES)]
+                ("stored_voxels", C.c_int64), ("solve_ms", C.c_double), ("item_ms", C.c_double * MAX_SPECIES),
+                ("reorth", C.c_int32 * MAX_SPECIES)]
 
     def as_dict(self, nspecies):
         return {"iters": list(self.iters[:nspecies]), "cycles": list(self.cycles[:nspecies]),
@@ -71,7 +72,7 @@ class mpm_report(C.Structure):
                 "res": list(self.res[:nspecies]),
                 "bnorm": list(self.bnorm[:nspecies]), "box_voxels": self.box_voxels,
                 "mask_voxels": self.mask_voxels, "stored_voxels": self.stored_voxels, "solve_ms": self.solve_ms,
-                "item_ms": list(self.item_ms[:nspecies])}
+                "item_ms": list(self.item_ms[:nspecies]), "reorth": list(self.reorth[:nspecies])}
 
 
 class mpm_subgrid_desc(C.Structure):
@@ -204,10 +205,11 @@ class DeviceParams:
 
 
 def make_opts(rtol=1e-6, atol=0.0, restart=30, maxit=1000, precision=0, inner_rtol=1e-5, x0_given=0,
-              nblocks=0) -> mpm_opts:
+              nblocks=0, reorth=0) -> mpm_opts:
     o = mpm_opts()
     o.rtol, o.atol, o.restart, o.maxit = rtol, atol, restart, maxit
     o.precision, o.inner_rtol, o.x0_given, o.nblocks = precision, inner_rtol, x0_given, nblocks
+    o.reorth = reorth
     return o
 
 

@@ -466,3 +466,52 @@ def test_queued_steps_equal_waited_steps(M, ctx):
     with pytest.raises(M.MpmError) as ei:
         s2.wait()
     assert ei.value.status == M.ERR_ARG
+
+
+# ---------------------------------------------------------------- optional reorthogonalisation
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("seed,dims", [(7, (23, 19, 15)), (2, (33, 17, 5))])
+def test_reorthogonalised_fp64_solve_matches_oracle(M, ctx, seed, dims, fused):
+    """opt.reorth = 1 adds a second Gram-Schmidt pass to every Arnoldi step
+    whose ||w|| dropped below 0.7 of its norm before orthogonalisation; the
+    solution is the same linear system's, so it meets the oracle at the same
+    bound, and the pass count is reported.  With A near a multiple of the
+    identity most of A u_j lies along u_j, so the test fires on most steps."""
+    wl = W.random_case(seed, dims, nspecies=3, dfac=True)
+    ref = wl.lattice.copy()
+    oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    got = {}
+    for ro in (0, 1):
+        lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=0.0, atol=1e-13, restart=16, maxit=3000, reorth=ro),
+                             fused=fused)
+        assert rep["status_code"] == M.OK
+        assert all(r <= 1e-13 for r in rep["res"])
+        assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10
+        got[ro] = rep
+    assert got[0]["reorth"] == [0, 0, 0]
+    assert all(0 < n <= it for n, it in zip(got[1]["reorth"], got[1]["iters"]))
+    # a second pass can only tighten the basis: no species needs many more steps
+    assert all(b <= a + 2 for a, b in zip(got[0]["iters"], got[1]["iters"]))
+
+
+def test_reorthogonalised_mixed_precision(M, ctx):
+    wl = W.random_case(6, (45, 37, 29), nspecies=3)
+    ref = wl.lattice.copy()
+    oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=1e-6, restart=16, maxit=500, precision=1, inner_rtol=1e-5,
+                                                  reorth=1))
+    assert rep["status_code"] == M.OK and min(rep["reorth"]) > 0
+    box = rep["box"]
+    mb = oracle.box_view(wl.lattice.mask, box) > 0
+    for s in range(3):
+        assert rep["res"][s] <= 1e-6 * rep["bnorm"][s]
+        g = oracle.box_view(lat.fields_numpy()[s], box)[mb]
+        r = oracle.box_view(ref.fields[s], box)[mb]
+        assert np.linalg.norm(g - r) <= 1e-6 * np.linalg.norm(r)
+
+
+def test_reorth_flag_out_of_range_is_an_argument_error(M, ctx):
+    wl = W.random_case(3, (16, 16, 16), nspecies=1)
+    with pytest.raises(M.MpmError) as ei:
+        _gpu_step(M, ctx, wl, M.make_opts(reorth=2))
+    assert ei.value.status == M.ERR_ARG
