@@ -8,11 +8,12 @@ workload (2000 Voronoi tumour cells in a 128x128x96 region of the shell, bbox
 margin 4, D = (1, 0.5, 0.2), dt = 0.05, 20 steps).
 
 One bench step = one implicit-Euler step of the whole hot path through the C
-ABI: bounding box + gather (mpm_box_extract), assembly (mpm_assemble_coeffs),
-GMRES for the three species and the scatter onto the mask (mpm_solve_step).
-The lattice is resident in HBM; L2 is flushed (256 MB write) before every timed
-step.  `e2e` repeats the steps with the lattice in pinned host memory, copying
-it in and the fields out inside the timed region.
+ABI (mpm_step / mpm_step_enqueue: one kernel per step): bounding box, tile
+compaction, gather + assembly, GMRES for the three species and the scatter
+onto the mask.  The lattice is resident in HBM; L2 is flushed (256 MB write)
+before every timed step.  `e2e` repeats the steps through mpm_step_host with
+the lattice in pinned host memory: the cell ids copied in and the step's box
+of the fields copied out inside the timed region.
 
 --impl reference times the CPU oracle (single thread) on the same workload.
 """
@@ -464,39 +465,41 @@ def main():
             results[name]["lat"] = lat
             results[name]["init"] = init
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (mpm_step_host)
     head = results["mixed"]
     lat, init, solver, opts = head["lat"], head["init"], head["solver"], head["opts"]
-    lat.fields.copy_(init)
     h_cell = lat.cell_id.cpu().pin_memory()
     h_mask = lat.mask.cpu().pin_memory()
-    h_buf = [lat.fields.cpu().pin_memory(), torch.empty_like(lat.fields, device="cpu").pin_memory()]
-    bi = h_cell.numel() * 4 + h_mask.numel() + h_buf[0].numel() * 8
-    bo = h_buf[0].numel() * 8
+    h_fields = init.cpu().pin_memory()
     ne = max(1, min(args.e2e_steps, args.steps))
+    # the first call brings the whole state in (mask and fields); every timed
+    # step then moves the step's input, the cell-id lattice, in and the step's
+    # box of the three fields out
+    solver.step_host(h_cell, h_fields, opts, mask=h_mask, fields_in=True)
     barrier()
     eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne)]
-    # every step copies its inputs in from pinned host memory and its fields
-    # out (the next step's input), all queued on the stream
+    bo = 0
     for i in range(ne):
         flush.fill_(i & 255)
         eev[i][0].record(stream)
-        lat.cell_id.copy_(h_cell, non_blocking=True)
-        lat.mask.copy_(h_mask, non_blocking=True)
-        lat.fields.copy_(h_buf[i % 2], non_blocking=True)
-        solver.step_async(opts)
-        h_buf[(i + 1) % 2].copy_(lat.fields, non_blocking=True)
+        erep = solver.step_host(h_cell, h_fields, opts)
         eev[i][1].record(stream)
-    erep = solver.wait()
+        (x0, y0, z0), (x1, y1, z1) = erep["box"]
+        bo += S * 8 * (x1 - x0) * (y1 - y0) * (z1 - z0)
+    torch.cuda.synchronize()
     barrier()
     assert erep["status_code"] == mpm.OK, erep
+    assert all(res <= wl.rtol * b for res, b in zip(erep["res"], erep["bnorm"])), erep
     e2e_ms = sum(a.elapsed_time(b) for a, b in eev)
     units = erep["mask_voxels"] * S * ne
     e2e_value, _ = replica_value(units, e2e_ms, world, "cuda")
+    bi = h_cell.numel() * 4
     e2e = {"value": e2e_value, "unit": "species-voxel-steps/s",
-           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-           "note": "lattice (cell ids, mask, 3 FP64 fields) copied in from pinned host memory and the fields "
-                   "copied out every step, queued with the step through the same C-ABI calls"}
+           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo // ne,
+           "note": "mpm_step_host per step (one synchronous C-ABI call): the 256^3 int32 cell-id lattice copied in "
+                   "from pinned host memory, the step, and the step's box of the 3 FP64 fields copied back to the "
+                   "pinned host fields (a step changes no voxel outside its box); the mask and the initial fields "
+                   "went in once before the timed steps"}
 
     # ---- roofline of the dominant kernel (the persistent GMRES solver)
     peak, src = _peaks()

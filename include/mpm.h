@@ -269,6 +269,39 @@ mpm_status mpm_step_enqueue(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *l
                             int32_t margin, const int32_t tile[3], const mpm_opts *opt, void *stream);
 mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, void *stream);
 
+/* The inputs of a step in host memory, for mpm_step_host (page-locked memory
+ * lets the copies run at the link's full speed; pageable memory also works). */
+typedef struct {
+    const int32_t *cell_id;             /* nullable: the device lattice's cell ids are current */
+    const uint8_t *mask;                /* nullable: the device mask is current */
+    double *field[MPM_MAX_SPECIES];     /* nullable per species: read with MPM_HOST_FIELDS_IN;
+                                           receives the step's box of the device field */
+} mpm_host_lattice;
+
+#define MPM_HOST_FIELDS_IN 1            /* mpm_step_host: copy the host fields in before the step */
+
+/*
+ * mpm_step with the step's inputs and results in host memory.  On `stream`:
+ * copies host->cell_id and host->mask (when not NULL) and, with
+ * MPM_HOST_FIELDS_IN, every non-NULL host field into the device lattice `dev`
+ * (whose buffers the call overwrites), runs mpm_step on `dev`, waits for it,
+ * and copies the step's box of every device field into the host field of the
+ * same species (one 3-D copy per species, box rows only).  A step changes no
+ * voxel outside its box, so a host field that equalled the device field
+ * before the step equals it afterwards: a caller that keeps the fields in
+ * step (MPM_HOST_FIELDS_IN on the first call and after changing them on the
+ * host) moves the cell ids in and the box out per step.  The fields are
+ * copied back for every status that lets the step write them (MPM_OK,
+ * MPM_ERR_NOCONV, MPM_ERR_BREAKDOWN) and left alone otherwise.
+ *   dev   : device lattice (as for mpm_step), dims give the size of every copy.
+ *   flags : 0 or MPM_HOST_FIELDS_IN; other bits: MPM_ERR_ARG.
+ * Other arguments, the return value and the report are those of mpm_step.
+ * Synchronous: `stream` is idle when the call returns.
+ */
+mpm_status mpm_step_host(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_host_lattice *host, const mpm_lattice *dev,
+                         const mpm_params *prm, int32_t margin, const int32_t tile[3], const mpm_opts *opt,
+                         int32_t flags, mpm_report *rep, mpm_box *out_box, void *stream);
+
 /*
  * Autotuner, tile shape: among the candidate shapes 8x4x4, 8x8x4, 4x4x4,
  * 8x4x2, 16x4x2, 8x8x2, 4x4x2, 16x4x4 pick the one whose active tiles store

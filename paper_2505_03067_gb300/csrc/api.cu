@@ -232,6 +232,56 @@ mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_bo
     return mpm_step_wait_impl(ctx, sub, rep, out_box, (cudaStream_t)stream);
 }
 
+mpm_status mpm_step_host(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_host_lattice *host, const mpm_lattice *dev,
+                         const mpm_params *prm, int32_t margin, const int32_t tile[3], const mpm_opts *opt,
+                         int32_t flags, mpm_report *rep, mpm_box *out_box, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!host || !dev || !prm) return mpm_fail(ctx, MPM_ERR_ARG, "step_host: null argument");
+    if (flags & ~MPM_HOST_FIELDS_IN) return mpm_fail(ctx, MPM_ERR_ARG, "step_host: unknown flag");
+    if (prm->nspecies < 1 || prm->nspecies > MPM_MAX_SPECIES)
+        return mpm_fail(ctx, MPM_ERR_ARG, "step_host: nspecies out of range");
+    for (int d = 0; d < 3; ++d)
+        if (dev->dims[d] < 1) return mpm_fail(ctx, MPM_ERR_ARG, "step_host: lattice dims must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nx = (size_t)dev->dims[0], ny = (size_t)dev->dims[1], nz = (size_t)dev->dims[2];
+    const size_t nvox = nx * ny * nz;
+    // the device lattice's buffers are the caller's; this call overwrites them
+    if (host->cell_id) {
+        if (!dev->cell_id) return mpm_fail(ctx, MPM_ERR_ARG, "step_host: null device cell ids");
+        MPM_CU(cudaMemcpyAsync((void *)dev->cell_id, host->cell_id, nvox * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    if (host->mask) {
+        if (!dev->mask) return mpm_fail(ctx, MPM_ERR_ARG, "step_host: null device mask");
+        MPM_CU(cudaMemcpyAsync((void *)dev->mask, host->mask, nvox, cudaMemcpyHostToDevice, st));
+    }
+    if (flags & MPM_HOST_FIELDS_IN)
+        for (int s = 0; s < prm->nspecies; ++s)
+            if (host->field[s] && dev->field[s])
+                MPM_CU(cudaMemcpyAsync(dev->field[s], host->field[s], nvox * sizeof(double), cudaMemcpyHostToDevice, st));
+    mpm_box box = {{0, 0, 0}, {0, 0, 0}};
+    const mpm_status r = mpm_step_impl(ctx, sub, dev, prm, margin, tile, opt, rep, &box, st);
+    if (out_box && (r == MPM_OK || r == MPM_ERR_NOCONV || r == MPM_ERR_BREAKDOWN)) *out_box = box;
+    if (r != MPM_OK && r != MPM_ERR_NOCONV && r != MPM_ERR_BREAKDOWN) return r;
+    // the box of every field back to the host: rows of nx doubles, pitch nx
+    for (int s = 0; s < prm->nspecies; ++s) {
+        if (!host->field[s] || !dev->field[s]) continue;
+        if (box.hi[0] <= box.lo[0] || box.hi[1] <= box.lo[1] || box.hi[2] <= box.lo[2]) break;
+        cudaMemcpy3DParms p = {};
+        p.srcPtr = make_cudaPitchedPtr(dev->field[s], nx * sizeof(double), nx, ny);
+        p.dstPtr = make_cudaPitchedPtr(host->field[s], nx * sizeof(double), nx, ny);
+        p.srcPos = make_cudaPos((size_t)box.lo[0] * sizeof(double), (size_t)box.lo[1], (size_t)box.lo[2]);
+        p.dstPos = p.srcPos;
+        p.extent = make_cudaExtent((size_t)(box.hi[0] - box.lo[0]) * sizeof(double), (size_t)(box.hi[1] - box.lo[1]),
+                                   (size_t)(box.hi[2] - box.lo[2]));
+        p.kind = cudaMemcpyDeviceToHost;
+        MPM_CU(cudaMemcpy3DAsync(&p, st));
+    }
+    MPM_CU(cudaStreamSynchronize(st));
+    return r;
+}
+
 mpm_status mpm_solve_fgmres_cnn(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
                                 const mpm_params *prm, const mpm_lattice *scatter_to, const mpm_opts *opt,
                                 mpm_report *rep, void *stream)

@@ -147,23 +147,36 @@ __device__ __forceinline__ const float *diag_of<float>(const SysDev &S, int s) {
 template <typename T>
 __device__ __forceinline__ T ldro(const T *p) { return *p; }
 
-// Neighbour elements of e for its open faces (closed faces get e; never read).
-__device__ __forceinline__ void nbr_elems(const int32_t *__restrict__ nbr, uint32_t e, uint32_t f, int ltx, int lty,
-                                          int ltz, uint32_t (&q)[6])
+// The six neighbour-tile entries of e's tile (-x,+x,-y,+y,-z,+z; 24 bytes,
+// 8-byte aligned).  The passes fetch them one iteration ahead together with
+// the flag byte, so an element's neighbour indices never wait on a table load.
+__device__ __forceinline__ void tile_nbrs(const int32_t *__restrict__ nbr, uint32_t e, int ltv, int32_t (&t)[6])
+{
+    const int2 *p = reinterpret_cast<const int2 *>(nbr + (size_t)(e >> ltv) * 6);
+    const int2 a = ldro(p), b = ldro(p + 1), c = ldro(p + 2);
+    t[0] = a.x;
+    t[1] = a.y;
+    t[2] = b.x;
+    t[3] = b.y;
+    t[4] = c.x;
+    t[5] = c.y;
+}
+
+// Neighbour elements of e for its open faces from its tile's entries t
+// (closed faces get e; never read).
+__device__ __forceinline__ void nbr_elems_t(const int32_t (&t)[6], uint32_t e, uint32_t f, int ltx, int lty, int ltz,
+                                            uint32_t (&q)[6])
 {
     const int ltv = ltx + lty + ltz;
-    const uint32_t tile = e >> ltv;
     const uint32_t v = e & ((1u << ltv) - 1u);
     const uint32_t TX = 1u << ltx, TY = 1u << lty, TZ = 1u << ltz;
     const uint32_t ix = v & (TX - 1), iy = (v >> ltx) & (TY - 1), iz = v >> (ltx + lty);
-    const uint32_t tb = tile << ltv;
-    q[0] = !(f & F_MX) ? e : (ix > 0 ? e - 1 : ((uint32_t)ldro(nbr + tile * 6 + 0) << ltv) + (v + TX - 1));
-    q[1] = !(f & F_PX) ? e : (ix < TX - 1 ? e + 1 : ((uint32_t)ldro(nbr + tile * 6 + 1) << ltv) + (v - (TX - 1)));
-    q[2] = !(f & F_MY) ? e : (iy > 0 ? e - TX : ((uint32_t)ldro(nbr + tile * 6 + 2) << ltv) + (v + (TY - 1) * TX));
-    q[3] = !(f & F_PY) ? e : (iy < TY - 1 ? e + TX : ((uint32_t)ldro(nbr + tile * 6 + 3) << ltv) + (v - (TY - 1) * TX));
-    q[4] = !(f & F_MZ) ? e : (iz > 0 ? e - TX * TY : ((uint32_t)ldro(nbr + tile * 6 + 4) << ltv) + (v + (TZ - 1) * TX * TY));
-    q[5] = !(f & F_PZ) ? e : (iz < TZ - 1 ? e + TX * TY : ((uint32_t)ldro(nbr + tile * 6 + 5) << ltv) + (v - (TZ - 1) * TX * TY));
-    (void)tb;
+    q[0] = !(f & F_MX) ? e : (ix > 0 ? e - 1 : ((uint32_t)t[0] << ltv) + (v + TX - 1));
+    q[1] = !(f & F_PX) ? e : (ix < TX - 1 ? e + 1 : ((uint32_t)t[1] << ltv) + (v - (TX - 1)));
+    q[2] = !(f & F_MY) ? e : (iy > 0 ? e - TX : ((uint32_t)t[2] << ltv) + (v + (TY - 1) * TX));
+    q[3] = !(f & F_PY) ? e : (iy < TY - 1 ? e + TX : ((uint32_t)t[3] << ltv) + (v - (TY - 1) * TX));
+    q[4] = !(f & F_MZ) ? e : (iz > 0 ? e - TX * TY : ((uint32_t)t[4] << ltv) + (v + (TZ - 1) * TX * TY));
+    q[5] = !(f & F_PZ) ? e : (iz < TZ - 1 ? e + TX * TY : ((uint32_t)t[5] << ltv) + (v - (TZ - 1) * TX * TY));
 }
 
 // Sum of u over the open faces with closed faces selected to zero (5 adds for
@@ -177,18 +190,18 @@ __device__ __forceinline__ T open_sum_sel(const T *__restrict__ u, uint32_t f, c
     return ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
 }
 
-// Sum of u over the open faces (neighbours read through L2: other CTAs wrote them).
+// Sum of u over the open faces (neighbours read through L2: other CTAs wrote
+// them).  A closed face's index is e itself, so all six loads are issued
+// unconditionally, back to back, and the closed ones are selected away.
 template <typename T>
 __device__ __forceinline__ T open_sum(const T *__restrict__ u, uint32_t f, const uint32_t (&q)[6])
 {
-    T s0 = T(0), s1 = T(0);
-    if (f & F_MX) s0 += __ldcg(u + q[0]);
-    if (f & F_PX) s1 += __ldcg(u + q[1]);
-    if (f & F_MY) s0 += __ldcg(u + q[2]);
-    if (f & F_PY) s1 += __ldcg(u + q[3]);
-    if (f & F_MZ) s0 += __ldcg(u + q[4]);
-    if (f & F_PZ) s1 += __ldcg(u + q[5]);
-    return s0 + s1;
+    T v[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) v[d] = __ldcg(u + q[d]);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) v[d] = (f & (1u << d)) ? v[d] : T(0);
+    return ((v[0] + v[2]) + v[4]) + ((v[1] + v[3]) + v[5]);
 }
 
 // Harmonic-mean variant: sum of D_f u_Q, D_f = 2 D_P D_Q / (D_P + D_Q).
@@ -228,24 +241,29 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
     const bool var = S.dfac != nullptr;
     const double *x = S.x[0];
     float fR = 0.0f, fB = 0.0f;
-    // the flag bytes are read-only during the solve: fetch the next iteration's
-    // one iteration ahead, so the neighbour loads never wait for them
+    // the flag bytes and the tile's neighbour entries are read-only during the
+    // solve: fetch the next iteration's one iteration ahead, so the neighbour
+    // loads never wait for them
+    const int ltv = S.ltx + S.lty + S.ltz;
     uint32_t fn[U];
+    int32_t tn[U][6];
 #pragma unroll
-    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? ldro(S.flags + e0 + u * es) : 0u;
+    for (int u = 0; u < U; ++u) {
+        const uint32_t en = e0 + u * es;
+        fn[u] = en < NE ? ldro(S.flags + en) : 0u;
+        if (en < NE) tile_nbrs(S.nbr, en, ltv, tn[u]);
+    }
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
         double xv[U], ns[U], bv[U], dg[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            const uint32_t eu = e + u * es;
+            if (eu < NE) nbr_elems_t(tn[u], eu, fn[u], S.ltx, S.lty, S.ltz, q[u]);
             f[u] = fn[u];
             const uint32_t en = e + (U + u) * es;
             fn[u] = en < NE ? ldro(S.flags + en) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t eu = e + u * es;
-            if (eu < NE) nbr_elems(S.nbr, eu, f[u], S.ltx, S.lty, S.ltz, q[u]);
+            if (en < NE) tile_nbrs(S.nbr, en, ltv, tn[u]);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -294,23 +312,29 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
     const T *V = (const T *)S.V[0];
     const T *uj = V + (int64_t)j * vs;
     const T *dgp = diag_of<T>(S, 0);
+    const int ltv = S.ltx + S.lty + S.ltz;
     uint32_t fn[U];
+    int32_t tn[U][6];
 #pragma unroll
-    for (int u = 0; u < U; ++u) fn[u] = e0 + u * es < NE ? ldro(S.flags + e0 + u * es) : 0u;
+    for (int u = 0; u < U; ++u) {
+        const uint32_t en = e0 + u * es;
+        fn[u] = en < NE ? ldro(S.flags + en) : 0u;
+        if (en < NE) tile_nbrs(S.nbr, en, ltv, tn[u]);
+    }
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
-        T xj[U], ns[U], dg[U], w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            f[u] = fn[u];
-            const uint32_t en = e + (U + u) * es;
-            fn[u] = en < NE ? ldro(S.flags + en) : 0u;
-        }
+        T xj[U], ns[U], dg[U], w[U], vi[U][MAXM];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
-            if (eu < NE) nbr_elems(S.nbr, eu, f[u], S.ltx, S.lty, S.ltz, q[u]);
+            if (eu < NE) nbr_elems_t(tn[u], eu, fn[u], S.ltx, S.lty, S.ltz, q[u]);
+            f[u] = fn[u];
+            const uint32_t en = e + (U + u) * es;
+            fn[u] = en < NE ? ldro(S.flags + en) : 0u;
+            if (en < NE) tile_nbrs(S.nbr, en, ltv, tn[u]);
         }
+        // every load of the iteration before the first product: the stencil
+        // values and the basis entries u_i(e), i < j, travel together
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
@@ -318,6 +342,8 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
             xj[u] = uj[eu];
             ns[u] = var ? open_sum_var<T>(uj, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum<T>(uj, f[u], q[u]);
             dg[u] = ldro(dgp + eu);
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) vi[u][i] = i < j ? V[(int64_t)i * vs + eu] : T(0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -326,7 +352,7 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
             w[u] = sj * (dg[u] * xj[u] - offT * ns[u]);
 #pragma unroll
             for (int i = 0; i <= MAXM; ++i) {
-                if (i < j) acc[i] += V[(int64_t)i * vs + eu] * w[u];
+                if (i < j) acc[i] += vi[u][i] * w[u];
                 else if (i == j) acc[i] += xj[u] * w[u];
                 else if (i == j + 1 && want_ww) acc[i] += w[u] * w[u];
             }

@@ -30,7 +30,8 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
            "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
-           "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond"]
+           "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond",
+           "mpm_step_host"]
 
 
 class mpm_box(C.Structure):
@@ -43,6 +44,13 @@ class mpm_box(C.Structure):
 class mpm_lattice(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("cell_id", C.c_void_p), ("mask", C.c_void_p), ("dfac", C.c_void_p),
                 ("field", C.c_void_p * MAX_SPECIES)]
+
+
+class mpm_host_lattice(C.Structure):
+    _fields_ = [("cell_id", C.c_void_p), ("mask", C.c_void_p), ("field", C.c_void_p * MAX_SPECIES)]
+
+
+HOST_FIELDS_IN = 1
 
 
 class mpm_params(C.Structure):
@@ -126,6 +134,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_step_enqueue": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, C.POINTER(C.c_int32),
                              C.POINTER(mpm_opts), P],
         "mpm_step_wait": [P, P, C.POINTER(mpm_report), C.POINTER(mpm_box), P],
+        "mpm_step_host": [P, P, C.POINTER(mpm_host_lattice), C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32,
+                          C.POINTER(C.c_int32), C.POINTER(mpm_opts), C.c_int32, C.POINTER(mpm_report),
+                          C.POINTER(mpm_box), P],
         "mpm_solve_batch": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.c_int32, C.POINTER(mpm_opts),
                             C.POINTER(mpm_report), P],
         "mpm_subgrid_export": [P, P, C.c_int32, C.c_int32, P, P],
@@ -361,6 +372,38 @@ class Subgrid:
         d["box"] = box.as_tuple()
         return d
 
+    def mpm_step_host(self, cell_id, mask, fields, lat: DeviceLattice, prm: "DeviceParams", margin: int,
+                      opts: mpm_opts, fields_in=False, tile=None, stream=None, allow=(ERR_NOCONV,)):
+        """mpm_step with the inputs in host memory: `cell_id` (int32), `mask`
+        (uint8) and `fields` ([S, Lz, Ly, Lx] float64) are contiguous CPU
+        tensors (None: the device copy is current); `fields` receives the
+        step's box of every field."""
+        h = mpm_host_lattice()
+        for name, t in (("cell_id", cell_id), ("mask", mask)):
+            if t is not None:
+                assert t.device.type == "cpu" and t.is_contiguous() and t.numel() == lat.cell_id.numel()
+                setattr(h, name, t.data_ptr())
+        if fields is not None:
+            assert fields.device.type == "cpu" and fields.is_contiguous() and fields.dtype == lat.fields.dtype
+            assert fields.shape == lat.fields.shape
+            for s_ in range(fields.shape[0]):
+                h.field[s_] = fields[s_].data_ptr()
+        rep = mpm_report()
+        box = mpm_box()
+        ls = lat.struct()
+        t = (C.c_int32 * 3)(*tile) if tile is not None else None
+        st = self.ctx.lib.mpm_step_host(self.ctx.ptr, self.h, C.byref(h), C.byref(ls), C.byref(prm.struct), margin, t,
+                                        C.byref(opts), HOST_FIELDS_IN if fields_in else 0, C.byref(rep),
+                                        C.byref(box), _stream_ptr(stream))
+        self.ctx._check(st, "mpm_step_host", allow=tuple(allow) + (ERR_EMPTY,))
+        if st == ERR_EMPTY:
+            return {"status_code": ERR_EMPTY, "box": None}
+        self.nspecies = int(prm.struct.nspecies)
+        d = rep.as_dict(self.nspecies)
+        d["status_code"] = st
+        d["box"] = box.as_tuple()
+        return d
+
     def mpm_step_enqueue(self, lat: DeviceLattice, prm: "DeviceParams", margin: int, opts: mpm_opts, tile=None,
                          stream=None):
         """Queue one device-resident step (mpm_step_enqueue); no wait."""
@@ -498,6 +541,13 @@ class StepSolver:
 
     def wait(self, stream=None, allow=(ERR_NOCONV,)):
         return self.sub.mpm_step_wait(stream, allow)
+
+    def step_host(self, cell_id, fields, opts: mpm_opts, mask=None, fields_in=False, stream=None,
+                  allow=(ERR_NOCONV,)):
+        """One step from host buffers (mpm_step_host): the cell ids (and the
+        mask, and with fields_in the fields) in, the step's box of the fields out."""
+        return self.sub.mpm_step_host(cell_id, mask, fields, self.lat, self.prm, self.margin, opts, fields_in,
+                                      self.tile, stream, allow)
 
     def step(self, opts: mpm_opts, stream=None, allow=(ERR_NOCONV,)):
         if self.fused:

@@ -515,3 +515,50 @@ def test_reorth_flag_out_of_range_is_an_argument_error(M, ctx):
     with pytest.raises(M.MpmError) as ei:
         _gpu_step(M, ctx, wl, M.make_opts(reorth=2))
     assert ei.value.status == M.ERR_ARG
+
+
+# ---------------------------------------------------------------- host buffers (mpm_step_host)
+def test_step_from_host_buffers_follows_a_moving_tumour(M, ctx):
+    """mpm_step_host: the host's cell ids (and on the first call its mask and
+    fields) go in, the step's box of every field comes back; the device
+    lattice starts out wrong (zero cell ids, mask and fields), so the answer
+    can only come from the copies.  Each step meets the oracle's step, and
+    after each the host fields equal the device fields bit for bit."""
+    import torch
+    wl = W.random_case(23, (40, 36, 30), nspecies=3, ncell=9)
+    ref = wl.lattice.copy()
+    zero = wl.lattice.copy()
+    zero.cell_id = np.zeros_like(zero.cell_id)
+    zero.mask = np.zeros_like(zero.mask)
+    zero.fields = np.zeros_like(zero.fields)
+    lat = M.DeviceLattice(zero)
+    prm = M.DeviceParams(wl.params)
+    solver = M.StepSolver(ctx, lat, prm, wl.margin, (4, 4, 4))
+    h_mask = torch.from_numpy(np.ascontiguousarray(wl.lattice.mask, np.uint8)).pin_memory()
+    h_fields = torch.from_numpy(np.ascontiguousarray(wl.lattice.fields)).pin_memory()
+    opts = M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=2000)
+    for k, (r, c) in enumerate([(3, (8, 9, 10)), (6, (12, 12, 12)), (4, (25, 20, 16)), (9, (20, 18, 15))]):
+        cid = _grow_cells(wl, r, c)
+        ref.cell_id = cid
+        h_cell = torch.from_numpy(np.ascontiguousarray(cid, np.int32)).pin_memory()
+        ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13)
+        first = k == 0
+        rep = solver.step_host(h_cell, h_fields, opts, mask=h_mask if first else None, fields_in=first)
+        assert rep["status_code"] == M.OK and rep["box"] == ro["box"], (k, rep["box"], ro["box"])
+        assert np.max(np.abs(h_fields.numpy() - ref.fields)) <= 1e-10, k
+        assert np.array_equal(h_fields.numpy(), lat.fields_numpy()), k
+        assert np.array_equal(lat.cell_id.cpu().numpy(), cid)
+
+
+def test_step_from_host_buffers_rejects_unknown_flags(M, ctx):
+    import ctypes as C
+    wl = W.random_case(3, (16, 16, 16), nspecies=1)
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    sub = ctx.subgrid_create()
+    h = M.mpm_host_lattice()
+    rep, box = M.mpm_report(), M.mpm_box()
+    st = ctx.lib.mpm_step_host(ctx.ptr, sub.h, C.byref(h), C.byref(lat.struct()), C.byref(prm.struct), wl.margin,
+                               None, C.byref(M.make_opts()), 2, C.byref(rep), C.byref(box), None)
+    assert st == M.ERR_ARG
+    sub.destroy()
