@@ -235,12 +235,15 @@ __device__ __forceinline__ double warp_sum(double v)
 __device__ __forceinline__ bool team_barrier(uint32_t *bar, uint32_t &epoch, uint32_t nblocks,
                                              int32_t *abort_flag, uint64_t timeout_ns)
 {
+    // The CTA barrier orders every thread's earlier writes (the partials)
+    // before thread 0's release; the acquire load orders the other CTAs'
+    // writes before the barrier that releases this CTA's threads.  The abort
+    // flag and the clock are checked every 16 polls.
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1;
         const uint32_t target = epoch * nblocks;
-        __threadfence();
         red_release_add_u32(bar, 1u);
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();
@@ -248,15 +251,16 @@ __device__ __forceinline__ bool team_barrier(uint32_t *bar, uint32_t &epoch, uin
         for (;;) {
             const uint32_t v = ld_acquire_u32(bar);
             if ((int32_t)(v - target) >= 0) break;
-            if (*(volatile int32_t *)abort_flag) { ok = 0; break; }
-            if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
-                atomicExch(abort_flag, 1);
-                ok = 0;
-                break;
+            if ((++spins & 15u) == 0) {
+                if (*(volatile int32_t *)abort_flag) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicExch(abort_flag, 1);
+                    ok = 0;
+                    break;
+                }
             }
             __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

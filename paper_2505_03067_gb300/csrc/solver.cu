@@ -186,7 +186,9 @@ __device__ __forceinline__ T open_sum_sel(const T *__restrict__ u, uint32_t f, c
 {
     T v[6];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) v[d] = (f & (1u << d)) ? __ldcg(u + q[d]) : T(0);
+    for (int d = 0; d < 6; ++d) v[d] = __ldcg(u + q[d]);   // a closed face reads e itself
+#pragma unroll
+    for (int d = 0; d < 6; ++d) v[d] = (f & (1u << d)) ? v[d] : T(0);
     return ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
 }
 
@@ -230,15 +232,15 @@ __device__ __forceinline__ T open_sum_var(const T *__restrict__ u, const double 
 
 // ---- R: r = b - A x in FP64; u_0 = r (stored in T); sums of r^2 and of b^2
 // over mask rows.
-template <typename T, int U>
-__device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint32_t e0, uint32_t es,
-                                              double &aR, double &aB)
+template <typename T, int U, bool VAR>
+__device__ __forceinline__ void pass_residual_t(const SysDev &S, bool first, uint32_t e0, uint32_t es,
+                                                double &aR, double &aB)
 {
     // FP32 path: the norms only steer the stopping test, so they accumulate in
     // FP32 (relative accuracy ~1e-7); the residual itself is FP64.
     constexpr bool kF32 = std::is_same<T, float>::value;
     const uint32_t NE = (uint32_t)S.NE;
-    const bool var = S.dfac != nullptr;
+    constexpr bool var = VAR;
     const double *x = S.x[0];
     float fR = 0.0f, fB = 0.0f;
     // the flag bytes and the tile's neighbour entries are read-only during the
@@ -300,14 +302,23 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
     }
 }
 
+// the harmonic-mean (per-voxel D) and the uniform-D form as separate loops
+template <typename T, int U>
+__device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint32_t e0, uint32_t es,
+                                              double &aR, double &aB)
+{
+    if (S.dfac) pass_residual_t<T, U, true>(S, first, e0, es, aR, aB);
+    else pass_residual_t<T, U, false>(S, first, e0, es, aR, aB);
+}
+
 // ---- P1: w = sigma_j A u_j into slot j+1; acc[i] += u_i . w for i <= j
-template <typename T, int MAXM, int U>
-__device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
-                                              T (&acc)[MAXM + 1], bool want_ww)
+template <typename T, int MAXM, int U, bool VAR>
+__device__ __forceinline__ void pass_arnoldi1_t(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
+                                                T (&acc)[MAXM + 1], bool want_ww)
 {
     const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
-    const bool var = S.dfac != nullptr;
+    constexpr bool var = VAR;
     const T offT = (T)(var ? S.a : S.off[0]);
     const T *V = (const T *)S.V[0];
     const T *uj = V + (int64_t)j * vs;
@@ -363,6 +374,14 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
             if (eu < NE) ((T *)S.V[0])[(int64_t)(j + 1) * vs + eu] = w[u];
         }
     }
+}
+
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
+                                              T (&acc)[MAXM + 1], bool want_ww)
+{
+    if (S.dfac) pass_arnoldi1_t<T, MAXM, U, true>(S, j, sj, e0, es, acc, want_ww);
+    else pass_arnoldi1_t<T, MAXM, U, false>(S, j, sj, e0, es, acc, want_ww);
 }
 
 // ---- P2: w -= sum_{i<=j} c_i u_i in place (c_i = h_ij sigma_i); acc += w^2
