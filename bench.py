@@ -508,7 +508,7 @@ def main():
     rec = _traffic_record("shell256_mixed_step")
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "of fallback",
-                "kernel": "k_step<float,8,1,1,768> (the whole step in one cooperative kernel: extraction, "
+                "kernel": "k_step<float,8,1,1,512> (the whole step in one cooperative kernel: extraction, "
                           "assembly, persistent GMRES with FP32 Krylov + FP64 residual, scatter)",
                 "duration": "CUDA events around each step's graph launch (one kernel per graph)",
                 "traffic": rec["dram_bytes_per_launch"] if rec else None,

@@ -416,7 +416,7 @@ mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *
  *                        partners' waits run out (-1 = none, the default).
  *  MPM_DEBUG_PHASE_TIMES 1: CTA 0 of every later solve records where its time
  *                        went (read with the MPM_COUNTER_PHASE_* counters).
- *  MPM_DEBUG_SOLVER_VARIANT  solver kernel variant 0..5 (elements in flight per
+ *  MPM_DEBUG_SOLVER_VARIANT  solver kernel variant 0..6 (elements in flight per
  *                        thread, CTAs per SM, threads per CTA; 0 = default;
  *                        a bucket without the variant uses its default), for
  *                        tuning. */

@@ -271,7 +271,7 @@ __device__ __forceinline__ void pass_residual_t(const SysDev &S, bool first, uin
         for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
             if (eu >= NE) continue;
-            xv[u] = x[eu];
+            xv[u] = __ldcg(x + eu);   // the update may have written it from another CTA
             ns[u] = var ? S.a * open_sum_var<double>(x, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum_sel<double>(x, f[u], q[u]);
             bv[u] = ldro(S.b[0] + eu);
             dg[u] = ldro(S.diag[0] + eu);
@@ -376,17 +376,130 @@ __device__ __forceinline__ void pass_arnoldi1_t(const SysDev &S, int j, T sj, ui
     }
 }
 
+// Four consecutive elements of a vector: one 16-byte load (FP32) or two (FP64).
+template <typename T>
+struct Q4 {
+    T v[4];
+};
+__device__ __forceinline__ Q4<float> ld4cg(const float *p)
+{
+    const float4 a = __ldcg(reinterpret_cast<const float4 *>(p));
+    return Q4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Q4<double> ld4cg(const double *p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return Q4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ Q4<float> ld4ro(const float *p)
+{
+    const float4 a = ldro(reinterpret_cast<const float4 *>(p));
+    return Q4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Q4<double> ld4ro(const double *p)
+{
+    const double2 a = ldro(reinterpret_cast<const double2 *>(p)), b = ldro(reinterpret_cast<const double2 *>(p) + 1);
+    return Q4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float *p, const float (&w)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&w)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(w[0], w[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(w[2], w[3]);
+}
+
+// The FP32 basis on tiles at least four wide in x: P1 (uniform D), P2, the
+// update and the reorthogonalisation's dots run on 4-element chunks of tile
+// rows (FP64 passes are bound by the FP64 rate and keep one element per
+// thread).  A pass reads what another pass wrote through L2, whichever thread
+// wrote it.
+template <typename T>
+__device__ __forceinline__ bool use_rows(const SysDev &S)
+{
+    return std::is_same<T, float>::value && S.ltx >= 2;
+}
+
+// ---- P1 for uniform D on tiles at least four wide in x: one 4-element chunk
+// of a tile row per thread and iteration.  Its u_j, the chunks at -y, +y, -z,
+// +z (same offsets within the tile, or in the neighbour tile), diag and the
+// basis rows travel as 16-byte vectors; the two x ends are single loads.  Per
+// element the operands and the order of the sum are those of the scalar pass,
+// so w is the same bit for bit; the dot products add four elements per thread
+// and iteration.  Vectors written during the solve are read through L2.
+template <typename T, int MAXM>
+__device__ __forceinline__ void pass_arnoldi1_rows(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
+                                                   T (&acc)[MAXM + 1], bool want_ww)
+{
+    const uint32_t NR = (uint32_t)S.NE >> 2;
+    const int64_t vs = S.vstride;
+    const T offT = (T)S.off[0];
+    T *V = (T *)S.V[0];
+    const T *uj = V + (int64_t)j * vs;
+    const T *dgp = diag_of<T>(S, 0);
+    const int ltx = S.ltx, lty = S.lty, ltv = S.ltx + S.lty + S.ltz;
+    const uint32_t TX = 1u << ltx, TY = 1u << lty, TZ = 1u << S.ltz, TXY = TX * TY;
+    for (uint32_t r = e0; r < NR; r += es) {
+        const uint32_t e = r << 2;
+        const uint32_t v0 = e & ((1u << ltv) - 1u);
+        const uint32_t ix0 = v0 & (TX - 1), iy = (v0 >> ltx) & (TY - 1), iz = v0 >> (ltx + lty);
+        int32_t tn[6];
+        tile_nbrs(S.nbr, e, ltv, tn);
+        const uchar4 fl = ldro(reinterpret_cast<const uchar4 *>(S.flags) + r);
+        // element of the neighbour tile across face d at offset o, or e when
+        // there is none (every face that way is then closed)
+        auto other = [&](int d, uint32_t o) -> uint32_t { return tn[d] >= 0 ? ((uint32_t)tn[d] << ltv) + o : e; };
+        const uint32_t qym = iy > 0 ? e - TX : other(2, v0 + (TY - 1) * TX);
+        const uint32_t qyp = iy < TY - 1 ? e + TX : other(3, v0 - (TY - 1) * TX);
+        const uint32_t qzm = iz > 0 ? e - TXY : other(4, v0 + (TZ - 1) * TXY);
+        const uint32_t qzp = iz < TZ - 1 ? e + TXY : other(5, v0 - (TZ - 1) * TXY);
+        const uint32_t qxm = ix0 > 0 ? e - 1 : other(0, v0 + TX - 1);
+        const uint32_t qxp = ix0 + 4 < TX ? e + 4 : other(1, v0 - ix0);
+        const Q4<T> u = ld4cg(uj + e);
+        const Q4<T> ym = ld4cg(uj + qym), yp = ld4cg(uj + qyp), zm = ld4cg(uj + qzm), zp = ld4cg(uj + qzp);
+        const T xm = __ldcg(uj + qxm), xp = __ldcg(uj + qxp);
+        const Q4<T> dg = ld4ro(dgp + e);
+        const uint32_t ff[4] = {fl.x, fl.y, fl.z, fl.w};
+        T w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t f = ff[k];
+            T v[6] = {k > 0 ? u.v[k - 1] : xm, k < 3 ? u.v[k + 1] : xp, ym.v[k], yp.v[k], zm.v[k], zp.v[k]};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) v[d] = (f & (1u << d)) ? v[d] : T(0);
+            const T ns = ((v[0] + v[2]) + v[4]) + ((v[1] + v[3]) + v[5]);
+            w[k] = sj * (dg.v[k] * u.v[k] - offT * ns);
+        }
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) {
+            if (i < j) {
+                const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
+                acc[i] += ((b.v[0] * w[0] + b.v[1] * w[1]) + (b.v[2] * w[2] + b.v[3] * w[3]));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i <= MAXM; ++i) {
+            if (i == j) acc[i] += ((u.v[0] * w[0] + u.v[1] * w[1]) + (u.v[2] * w[2] + u.v[3] * w[3]));
+            else if (i == j + 1 && want_ww) acc[i] += ((w[0] * w[0] + w[1] * w[1]) + (w[2] * w[2] + w[3] * w[3]));
+        }
+        st4(V + (int64_t)(j + 1) * vs + e, w);
+    }
+}
+
 template <typename T, int MAXM, int U>
 __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
                                               T (&acc)[MAXM + 1], bool want_ww)
 {
     if (S.dfac) pass_arnoldi1_t<T, MAXM, U, true>(S, j, sj, e0, es, acc, want_ww);
+    else if (use_rows<T>(S)) pass_arnoldi1_rows<T, MAXM>(S, j, sj, e0, es, acc, want_ww);
     else pass_arnoldi1_t<T, MAXM, U, false>(S, j, sj, e0, es, acc, want_ww);
 }
 
 // ---- P2: w -= sum_{i<=j} c_i u_i in place (c_i = h_ij sigma_i); acc += w^2
 template <typename T, int MAXM, int U>
-__device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
+__device__ __forceinline__ void pass_arnoldi2_e(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
 {
     const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
@@ -397,7 +510,7 @@ __device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c
         for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
             if (eu >= NE) continue;
-            T t = V[(int64_t)(j + 1) * vs + eu];
+            T t = __ldcg(V + (int64_t)(j + 1) * vs + eu);   // P1 may have written it from another CTA
 #pragma unroll
             for (int i = 0; i <= MAXM; ++i)
                 if (i <= j) t -= c[i] * V[(int64_t)i * vs + eu];
@@ -412,9 +525,39 @@ __device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c
     }
 }
 
+template <typename T, int MAXM>
+__device__ __forceinline__ void pass_arnoldi2_rows(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
+{
+    const uint32_t NR = (uint32_t)S.NE >> 2;
+    const int64_t vs = S.vstride;
+    T *V = (T *)S.V[0];
+    for (uint32_t r = e0; r < NR; r += es) {
+        const uint32_t e = r << 2;
+        Q4<T> t = ld4cg(V + (int64_t)(j + 1) * vs + e);
+#pragma unroll
+        for (int i = 0; i <= MAXM; ++i) {
+            if (i <= j) {
+                const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
+                const T ci = c[i];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) t.v[k] -= ci * b.v[k];
+            }
+        }
+        acc += (t.v[0] * t.v[0] + t.v[1] * t.v[1]) + (t.v[2] * t.v[2] + t.v[3] * t.v[3]);
+        st4(V + (int64_t)(j + 1) * vs + e, t.v);
+    }
+}
+
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
+{
+    if (use_rows<T>(S)) pass_arnoldi2_rows<T, MAXM>(S, j, c, e0, es, acc);
+    else pass_arnoldi2_e<T, MAXM, U>(S, j, c, e0, es, acc);
+}
+
 // ---- P1b (reorthogonalisation): acc[i] += u_i . w for i <= j, w in slot j+1
 template <typename T, int MAXM, int U>
-__device__ __forceinline__ void pass_dots(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
+__device__ __forceinline__ void pass_dots_e(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
 {
     const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
@@ -432,10 +575,36 @@ __device__ __forceinline__ void pass_dots(const SysDev &S, int j, uint32_t e0, u
     }
 }
 
+template <typename T, int MAXM>
+__device__ __forceinline__ void pass_dots_rows(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
+{
+    const uint32_t NR = (uint32_t)S.NE >> 2;
+    const int64_t vs = S.vstride;
+    const T *V = (const T *)S.V[0];
+    for (uint32_t r = e0; r < NR; r += es) {
+        const uint32_t e = r << 2;
+        const Q4<T> w = ld4cg(V + (int64_t)(j + 1) * vs + e);
+#pragma unroll
+        for (int i = 0; i <= MAXM; ++i) {
+            if (i <= j) {
+                const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
+                acc[i] += (b.v[0] * w.v[0] + b.v[1] * w.v[1]) + (b.v[2] * w.v[2] + b.v[3] * w.v[3]);
+            }
+        }
+    }
+}
+
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_dots(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
+{
+    if (use_rows<T>(S)) pass_dots_rows<T, MAXM>(S, j, e0, es, acc);
+    else pass_dots_e<T, MAXM, U>(S, j, e0, es, acc);
+}
+
 // ---- U: x += sum_{i<k} c_i u_i (c_i = y_i sigma_i); the FP32 path adds its
 // FP32 correction d to the FP64 iterate.
 template <typename T, int MAXM, int U>
-__device__ __forceinline__ void pass_update(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
+__device__ __forceinline__ void pass_update_e(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
 {
     const uint32_t NE = (uint32_t)S.NE;
     const int64_t vs = S.vstride;
@@ -461,6 +630,40 @@ __device__ __forceinline__ void pass_update(const SysDev &S, int k, const T *c, 
             if (eu < NE) x[eu] = xv[u] + (double)d[u];
         }
     }
+}
+
+template <typename T, int MAXM>
+__device__ __forceinline__ void pass_update_rows(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
+{
+    const uint32_t NR = (uint32_t)S.NE >> 2;
+    const int64_t vs = S.vstride;
+    const T *V = (const T *)S.V[0];
+    double *x = S.x[0];
+    for (uint32_t r = e0; r < NR; r += es) {
+        const uint32_t e = r << 2;
+        const Q4<double> xv = ld4cg(x + e);
+        T d[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) {
+            if (i < k) {
+                const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
+                const T ci = c[i];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d[q] += ci * b.v[q];
+            }
+        }
+        double xo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xo[q] = xv.v[q] + (double)d[q];
+        st4(x + e, xo);
+    }
+}
+
+template <typename T, int MAXM, int U>
+__device__ __forceinline__ void pass_update(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
+{
+    if (use_rows<T>(S)) pass_update_rows<T, MAXM>(S, k, c, e0, es);
+    else pass_update_e<T, MAXM, U>(S, k, c, e0, es);
 }
 
 // The persistent GMRES of one CTA of a team (every item of its team in turn).
@@ -873,12 +1076,13 @@ static Variant pick(int prec, int maxm, int variant)
     }
     if (maxm == 8) {
         switch (variant) {
-        case 1: return var_of<float, 8, 1, 1, 512>();
+        case 1: return var_of<float, 8, 1, 1, 768>();
         case 2: return var_of<float, 8, 2, 2, 512>();
         case 3: return var_of<float, 8, 2, 1, 512>();
         case 4: return var_of<float, 8, 1, 1, 1024>();
         case 5: return var_of<float, 8, 1, 2, 512>();
-        default: return var_of<float, 8, 1, 1, 768>();
+        case 6: return var_of<float, 8, 1, 1, 640>();
+        default: return var_of<float, 8, 1, 1, 512>();
         }
     }
     if (maxm == 16) return var_of<float, 16, 1, 1, 512>();
@@ -934,7 +1138,7 @@ int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 int mpm_solver_variants(int prec, int m)
 {
     if (m > 8) return 1;
-    return prec == 1 ? 6 : 5;
+    return prec == 1 ? 7 : 5;
 }
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }

@@ -92,7 +92,7 @@ def test_patches64_tuned_graph_batch(M):
     bs = M.BatchStepper(ctx, lats, prms, [p.margin for p in ps], tune_tiles=True)
     opts = M.make_opts(rtol=1e-6, restart=8, maxit=500, precision=1, inner_rtol=1e-6)
     m, var = bs.tune(opts)
-    assert m in (4, 8, 16) and 0 <= var <= 5
+    assert m in (4, 8, 16) and 0 <= var <= 6
     befores = [p.lattice.copy() for p in ps]
     st, reps = bs.step(opts)
     assert st == M.OK
