@@ -1068,6 +1068,7 @@ static Variant pick(int prec, int maxm, int variant)
             case 2: return var_of<double, 8, 1, 1, 1024>();
             case 3: return var_of<double, 8, 1, 1, 768>();
             case 4: return var_of<double, 8, 2, 1, 768>();
+            case 5: return var_of<double, 8, 1, 1, 512>();
             default: return var_of<double, 8, 2, 1, 512>();
             }
         }
@@ -1138,7 +1139,7 @@ int mpm_solver_max_blocks(mpm_ctx *ctx, int prec, int m, int variant)
 int mpm_solver_variants(int prec, int m)
 {
     if (m > 8) return 1;
-    return prec == 1 ? 7 : 5;
+    return prec == 1 ? 7 : 6;
 }
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }

@@ -62,24 +62,52 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
     }
     const int64_t sy = g.Lx, sz = (int64_t)g.Lx * g.Ly;
     const int64_t L = (int64_t)(g.lo[0] + bx) + sy * (g.lo[1] + by) + sz * (g.lo[2] + bz);
+    // every lattice load of the element before its first store (a store may
+    // alias a later load in the compiler's eyes): the mask at the voxel and
+    // its in-box neighbours, the cell id, the diffusivity factor, c^n of
+    // every species
+    const bool hx0 = bx > 0, hx1 = bx < g.n[0] - 1, hy0 = by > 0, hy1 = by < g.n[1] - 1, hz0 = bz > 0,
+               hz1 = bz < g.n[2] - 1;
+    const uint32_t m0 = __ldg(S.mask + L);
+    const uint32_t m1 = hx0 ? __ldg(S.mask + L - 1) : 0u, m2 = hx1 ? __ldg(S.mask + L + 1) : 0u;
+    const uint32_t m3 = hy0 ? __ldg(S.mask + L - sy) : 0u, m4 = hy1 ? __ldg(S.mask + L + sy) : 0u;
+    const uint32_t m5 = hz0 ? __ldg(S.mask + L - sz) : 0u, m6 = hz1 ? __ldg(S.mask + L + sz) : 0u;
+    const int32_t id0 = __ldg(S.cell_id + L);
+    const double fp = S.dfac_lat ? __ldg(S.dfac_lat + L) : 1.0;
+    double cs[kMaxSpecies];
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) cs[s] = s < ns ? __ldg(S.field[s] + L) : 0.0;
     uint32_t f = F_BOX;
-    if (__ldg(S.mask + L)) {
+    if (m0) {
         f |= F_MASK;
-        if (bx > 0 && __ldg(S.mask + L - 1)) f |= F_MX;
-        if (bx < g.n[0] - 1 && __ldg(S.mask + L + 1)) f |= F_PX;
-        if (by > 0 && __ldg(S.mask + L - sy)) f |= F_MY;
-        if (by < g.n[1] - 1 && __ldg(S.mask + L + sy)) f |= F_PY;
-        if (bz > 0 && __ldg(S.mask + L - sz)) f |= F_MZ;
-        if (bz < g.n[2] - 1 && __ldg(S.mask + L + sz)) f |= F_PZ;
+        if (m1) f |= F_MX;
+        if (m2) f |= F_PX;
+        if (m3) f |= F_MY;
+        if (m4) f |= F_PY;
+        if (m5) f |= F_MZ;
+        if (m6) f |= F_PZ;
+    }
+    const bool inm = (f & F_MASK) != 0;
+    const bool bad = inm && (id0 < 0 || id0 >= S.C.ncell);
+    const int32_t id = bad ? 0 : id0;
+    // the rate-table entries of the cell id, every species together
+    double dkv[kMaxSpecies], dqv[kMaxSpecies];
+    const bool tabrow = kTab && !S.dfac && inm;
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        const int64_t k = (int64_t)s * S.C.ncell + id;
+        dkv[s] = tabrow && s < ns ? __ldcg(S.dk + k) : 0.0;
+        dqv[s] = tabrow && s < ns ? __ldcg(S.dq + k) : 0.0;
     }
     S.flags[e] = (uint8_t)f;
-    int32_t id = __ldg(S.cell_id + L);
-    S.cell[e] = id;
-    const double fp = S.dfac_lat ? __ldg(S.dfac_lat + L) : 1.0;
+    S.cell[e] = id0;
     if (S.dfac) S.dfac[e] = fp;
-    if (!(f & F_MASK)) {                        // identity row keeping c^n
-        for (int s = 0; s < ns; ++s) {
-            const double c = __ldg(S.field[s] + L);
+    if (bad) atomicOr(S.err, 1);
+    if (!inm) {                                 // identity row keeping c^n
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) {
+            if (s >= ns) break;
+            const double c = cs[s];
             S.x[s][e] = c;
             S.cn[s][e] = c;
             S.diag[s][e] = 1.0;
@@ -88,10 +116,6 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
         }
         return;
     }
-    if (id < 0 || id >= S.C.ncell) {
-        atomicOr(S.err, 1);
-        id = 0;
-    }
     const int ndir = S.C.bc_box == 0 ? (bx == 0) + (bx == g.n[0] - 1) + (by == 0) + (by == g.n[1] - 1) +
                                            (bz == 0) + (bz == g.n[2] - 1)
                                      : 0;
@@ -99,15 +123,16 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
         const int64_t o = d == 0 ? -1 : d == 1 ? 1 : d == 2 ? -sy : d == 3 ? sy : d == 4 ? -sz : sz;
         return __ldg(S.dfac_lat + L + o);
     };
-    for (int s = 0; s < ns; ++s) {
-        const double c = __ldg(S.field[s] + L);
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        if (s >= ns) break;
+        const double c = cs[s];
         double dg, bb;
-        if (kTab && !S.dfac) {
+        if (tabrow) {
             // the rows of assemble_row with the per-cell and per-count products
             // taken from tables: three FP64 additions per species
-            const int64_t k = (int64_t)s * S.C.ncell + id;
-            dg = __ldcg(S.dk + k) + tab->aDn[s][__popc(f & F_OPEN) + 2 * ndir];
-            bb = (c + __ldcg(S.dq + k)) + tab->wbn[s][ndir];
+            dg = dkv[s] + tab->aDn[s][__popc(f & F_OPEN) + 2 * ndir];
+            bb = (c + dqv[s]) + tab->wbn[s][ndir];
         } else {
             assemble_row(S.C, s, f, id, ndir, S.dfac != nullptr, fp, dq, c, dg, bb);
         }
@@ -223,19 +248,28 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         if (A.vec4) {
             const int4 *c4 = reinterpret_cast<const int4 *>(A.cell_id);
             const uint32_t n4 = (uint32_t)(Ltot / 4);
+            // 16-byte streaming loads, kD per thread in flight (about 64 KB per
+            // SM): the scan is bound by the bytes the SMs keep in flight
+            constexpr int kD = NT <= 512 ? 8 : 4;
+            const bool rows4 = (Lx & 3u) == 0;   // the four voxels of a load share a row
             uint32_t q = t0;
-            for (; q + 3 * nth < n4; q += 4 * nth) {
-                int4 v[4];
+            for (; q + (kD - 1) * nth < n4; q += kD * nth) {
+                int4 v[kD];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = __ldcs(c4 + q + u * nth);
+                for (int u = 0; u < kD; ++u) v[u] = __ldcs(c4 + q + u * nth);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if ((v[u].x > 0) | (v[u].y > 0) | (v[u].z > 0) | (v[u].w > 0)) {
-                        const uint32_t e = 4 * (q + u * nth);
-                        if (v[u].x > 0) bbox_upd(e + 0, Lx, Lxy, mn, mx);
-                        if (v[u].y > 0) bbox_upd(e + 1, Lx, Lxy, mn, mx);
-                        if (v[u].z > 0) bbox_upd(e + 2, Lx, Lxy, mn, mx);
-                        if (v[u].w > 0) bbox_upd(e + 3, Lx, Lxy, mn, mx);
+                for (int u = 0; u < kD; ++u) {
+                    const uint32_t pm = (v[u].x > 0) | ((v[u].y > 0) << 1) | ((v[u].z > 0) << 2) | ((v[u].w > 0) << 3);
+                    if (!pm) continue;
+                    const uint32_t e = 4 * (q + u * nth);
+                    if (rows4) {   // the first and the last tumour voxel bound the other two
+                        bbox_upd(e + (__ffs(pm) - 1), Lx, Lxy, mn, mx);
+                        bbox_upd(e + (31 - __clz(pm)), Lx, Lxy, mn, mx);
+                    } else {
+                        if (pm & 1u) bbox_upd(e + 0, Lx, Lxy, mn, mx);
+                        if (pm & 2u) bbox_upd(e + 1, Lx, Lxy, mn, mx);
+                        if (pm & 4u) bbox_upd(e + 2, Lx, Lxy, mn, mx);
+                        if (pm & 8u) bbox_upd(e + 3, Lx, Lxy, mn, mx);
                     }
                 }
             }
