@@ -344,13 +344,28 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         __syncthreads();
         unsigned long long cnt = 0;
         if (g.n[0] > 0) {
+            // one row per warp and iteration; the first four 32-voxel chunks of
+            // the row have their mask bytes in flight together
             const int64_t gw = (int64_t)b * (NT / 32) + warp, nw = (int64_t)nb * (NT / 32);
             const int64_t nrows = (int64_t)g.n[1] * g.n[2];
             for (int64_t row = gw; row < nrows; row += nw) {
                 const int by = (int)(row % g.n[1]), bz = (int)(row / g.n[1]);
                 const int64_t L0 = (int64_t)g.lo[0] + (int64_t)g.Lx * ((int64_t)(g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
                 const int64_t trow = ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) * g.nt[0];
-                for (int bx = lane; bx < g.n[0]; bx += 32) {
+                uint32_t m[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int bx = c * 32 + lane;
+                    m[c] = bx < g.n[0] ? __ldg(A.mask + L0 + bx) : 0u;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (m[c]) {
+                        ++cnt;
+                        A.active[trow + ((c * 32 + lane) >> g.lt[0])] = 1;
+                    }
+                }
+                for (int bx = 128 + lane; bx < g.n[0]; bx += 32) {
                     if (__ldg(A.mask + L0 + bx)) {
                         ++cnt;
                         A.active[trow + (bx >> g.lt[0])] = 1;
