@@ -1048,7 +1048,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
         if (ok && *(volatile int32_t *)P.xa.xabort == 0) {
             const int64_t NE = __ldcg(&P.xa.dyn->NE);
             const BoxGeo g = P.xa.dyn->g;
-            for (int64_t e = (int64_t)b * NT + tid; e < NE; e += (int64_t)nb * NT) scatter_elem<true>(P.S, g, e);
+            if (g.lt[0] >= 2) {   // 4-element chunks of tile rows
+                for (int64_t r = (int64_t)b * NT + tid; r < (NE >> 2); r += (int64_t)nb * NT)
+                    scatter_chunk(P.S, g, (uint32_t)r);
+            } else {
+                for (int64_t e = (int64_t)b * NT + tid; e < NE; e += (int64_t)nb * NT) scatter_elem<true>(P.S, g, e);
+            }
         }
         if (prof) P.sa.prof[9] += globaltimer_ns() - t0;
     }

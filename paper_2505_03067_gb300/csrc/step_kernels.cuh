@@ -144,6 +144,146 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
     }
 }
 
+// The device-resident preparation for uniform D on tiles at least four wide
+// in x: one 4-element chunk of a tile row (four x-consecutive voxels of the
+// lattice) per call.  One tile-coordinate load serves the four elements, the
+// lattice loads of all four are in flight together, and the element arrays
+// are written with 4- to 16-byte stores.  Per element the rows are those of
+// prep_elem<true> (same operands, same order).
+__device__ __forceinline__ void prep_chunk(const BatchSys &S, const BoxGeo &g, uint32_t r, const RowTab *tab)
+{
+    const int ns = S.C.nspecies;
+    const uint32_t e = r << 2;
+    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
+    const int4 tc = __ldcg(reinterpret_cast<const int4 *>(S.tile_coord) + (e >> ltv));
+    const uint32_t v0 = e & ((1u << ltv) - 1u);
+    const int ix0 = (int)(v0 & ((1u << g.lt[0]) - 1u));
+    const int iy = (int)((v0 >> g.lt[0]) & ((1u << g.lt[1]) - 1u)), iz = (int)(v0 >> (g.lt[0] + g.lt[1]));
+    const int bx0 = (tc.x << g.lt[0]) + ix0, by = (tc.y << g.lt[1]) + iy, bz = (tc.z << g.lt[2]) + iz;
+    const int nv = (by < g.n[1] && bz < g.n[2]) ? max(0, min(4, g.n[0] - bx0)) : 0;   // elements in the box
+    const int64_t sy = g.Lx, sz = (int64_t)g.Lx * g.Ly;
+    const int64_t L0 = (int64_t)(g.lo[0] + bx0) + sy * (g.lo[1] + by) + sz * (g.lo[2] + bz);
+    const bool hy0 = by > 0, hy1 = by < g.n[1] - 1, hz0 = bz > 0, hz1 = bz < g.n[2] - 1;
+    uint32_t mo[4], my0[4], my1[4], mz0[4], mz1[4];
+    int32_t id0[4];
+    double cs[kMaxSpecies][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool in = k < nv;
+        const int64_t L = L0 + k;
+        mo[k] = in ? __ldg(S.mask + L) : 0u;
+        my0[k] = in && hy0 ? __ldg(S.mask + L - sy) : 0u;
+        my1[k] = in && hy1 ? __ldg(S.mask + L + sy) : 0u;
+        mz0[k] = in && hz0 ? __ldg(S.mask + L - sz) : 0u;
+        mz1[k] = in && hz1 ? __ldg(S.mask + L + sz) : 0u;
+        id0[k] = in ? __ldg(S.cell_id + L) : 0;
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) cs[s][k] = in && s < ns ? __ldg(S.field[s] + L) : 0.0;
+    }
+    const uint32_t mxm = nv > 0 && bx0 > 0 ? __ldg(S.mask + L0 - 1) : 0u;
+    const uint32_t mxp = nv == 4 && bx0 + 4 < g.n[0] ? __ldg(S.mask + L0 + 4) : 0u;
+    uint32_t f[4];
+    int32_t id[4];
+    int nd[4];
+    bool anybad = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int bx = bx0 + k;
+        uint32_t fk = k < nv ? F_BOX : 0u;
+        if (mo[k]) {
+            fk |= F_MASK;
+            if (k > 0 ? mo[k - 1] != 0u : mxm != 0u) fk |= F_MX;
+            if (k < 3 ? (k + 1 < nv && mo[k + 1] != 0u) : mxp != 0u) fk |= F_PX;
+            if (my0[k]) fk |= F_MY;
+            if (my1[k]) fk |= F_PY;
+            if (mz0[k]) fk |= F_MZ;
+            if (mz1[k]) fk |= F_PZ;
+        }
+        f[k] = fk;
+        const bool bad = (fk & F_MASK) && (id0[k] < 0 || id0[k] >= S.C.ncell);
+        anybad |= bad;
+        id[k] = bad ? 0 : id0[k];
+        nd[k] = S.C.bc_box == 0 ? (bx == 0) + (bx == g.n[0] - 1) + (by == 0) + (by == g.n[1] - 1) + (bz == 0) +
+                                      (bz == g.n[2] - 1)
+                                : 0;
+    }
+    *reinterpret_cast<uchar4 *>(S.flags + e) = make_uchar4((uint8_t)f[0], (uint8_t)f[1], (uint8_t)f[2], (uint8_t)f[3]);
+    *reinterpret_cast<int4 *>(S.cell + e) = make_int4(id0[0], id0[1], id0[2], id0[3]);
+    if (anybad) atomicOr(S.err, 1);
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        if (s >= ns) break;
+        double dkv[4], dqv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t t = (int64_t)s * S.C.ncell + id[k];
+            const bool row = (f[k] & F_MASK) != 0;
+            // plain cached loads: the tables were written before a grid barrier
+            // and never read before it, and neighbouring voxels mostly share a cell
+            dkv[k] = row ? S.dk[t] : 0.0;
+            dqv[k] = row ? S.dq[t] : 0.0;
+        }
+        double xo[4], dg[4], bb[4];
+        float d32[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double c = cs[s][k];
+            if (!(f[k] & F_BOX)) {            // tile padding
+                xo[k] = 0.0;
+                dg[k] = 1.0;
+                bb[k] = 0.0;
+            } else if (!(f[k] & F_MASK)) {    // identity row keeping c^n
+                xo[k] = c;
+                dg[k] = 1.0;
+                bb[k] = c;
+            } else {
+                xo[k] = c;
+                dg[k] = dkv[k] + tab->aDn[s][__popc(f[k] & F_OPEN) + 2 * nd[k]];
+                bb[k] = (c + dqv[k]) + tab->wbn[s][nd[k]];
+            }
+            d32[k] = (float)dg[k];
+        }
+        double2 *x2 = reinterpret_cast<double2 *>(S.x[s] + e), *c2 = reinterpret_cast<double2 *>(S.cn[s] + e);
+        double2 *b2 = reinterpret_cast<double2 *>(S.b[s] + e), *g2 = reinterpret_cast<double2 *>(S.diag[s] + e);
+        x2[0] = make_double2(xo[0], xo[1]);
+        x2[1] = make_double2(xo[2], xo[3]);
+        c2[0] = make_double2(xo[0], xo[1]);
+        c2[1] = make_double2(xo[2], xo[3]);
+        b2[0] = make_double2(bb[0], bb[1]);
+        b2[1] = make_double2(bb[2], bb[3]);
+        g2[0] = make_double2(dg[0], dg[1]);
+        g2[1] = make_double2(dg[2], dg[3]);
+        *reinterpret_cast<float4 *>(S.diag32[s] + e) = make_float4(d32[0], d32[1], d32[2], d32[3]);
+    }
+}
+
+// The scatter on a 4-element chunk of a tile row (one tile-coordinate load
+// and one flags word for four elements).  The tile coordinates were written
+// earlier in the same kernel.
+__device__ __forceinline__ void scatter_chunk(const BatchSys &S, const BoxGeo &g, uint32_t r)
+{
+    const uint32_t e = r << 2;
+    const uchar4 fl = *reinterpret_cast<const uchar4 *>(S.flags + e);
+    const uint32_t f[4] = {fl.x, fl.y, fl.z, fl.w};
+    if (!((f[0] | f[1] | f[2] | f[3]) & F_MASK)) return;
+    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
+    const int4 tc = __ldcg(reinterpret_cast<const int4 *>(S.tile_coord) + (e >> ltv));
+    const uint32_t v0 = e & ((1u << ltv) - 1u);
+    const int bx0 = (tc.x << g.lt[0]) + (int)(v0 & ((1u << g.lt[0]) - 1u));
+    const int by = (tc.y << g.lt[1]) + (int)((v0 >> g.lt[0]) & ((1u << g.lt[1]) - 1u));
+    const int bz = (tc.z << g.lt[2]) + (int)(v0 >> (g.lt[0] + g.lt[1]));
+    const int64_t L0 =
+        (int64_t)(g.lo[0] + bx0) + (int64_t)g.Lx * ((g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
+    for (int s = 0; s < S.C.nspecies; ++s) {
+        const double2 a = reinterpret_cast<const double2 *>(S.x[s] + e)[0];
+        const double2 c = reinterpret_cast<const double2 *>(S.x[s] + e)[1];
+        const double xv[4] = {a.x, a.y, c.x, c.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (f[k] & F_MASK) S.field[s][L0 + k] = xv[k];
+    }
+}
+
 // Sec. 2.4: the box solution onto the pleural mask (in-mask voxels only).
 // kCoherent: the tile coordinates were written earlier in the same kernel.
 template <bool kCoherent = false>
@@ -471,8 +611,12 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
     // ---- E: gather + rows of every stored element, neighbour table
     const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
     const int64_t NE = g.n[0] > 0 ? nact << ltv : 0;
-    for (int64_t e = (int64_t)b * NT + tid; e < NE; e += (int64_t)nb * NT) {
-        prep_elem<true>(S, g, e, &tab);
+    const bool chunks = g.lt[0] >= 2 && !S.dfac;
+    const int64_t nunit = chunks ? NE >> 2 : NE;   // 4-element chunks or elements
+    for (int64_t u = (int64_t)b * NT + tid; u < nunit; u += (int64_t)nb * NT) {
+        const int64_t e = chunks ? u << 2 : u;
+        if (chunks) prep_chunk(S, g, (uint32_t)u, &tab);
+        else prep_elem<true>(S, g, e, &tab);
         if ((e & ((1 << ltv) - 1)) == 0) {          // neighbour tiles of this tile
             const int64_t a = e >> ltv;
             const int4 c = __ldcg(reinterpret_cast<const int4 *>(S.tile_coord) + a);
