@@ -562,3 +562,39 @@ def test_step_from_host_buffers_rejects_unknown_flags(M, ctx):
                                None, C.byref(M.make_opts()), 2, C.byref(rep), C.byref(box), None)
     assert st == M.ERR_ARG
     sub.destroy()
+
+
+@pytest.mark.parametrize("tile", [(4, 4, 4), (8, 4, 1), (16, 4, 2), (2, 4, 4), (4, 2, 8)])
+@pytest.mark.parametrize("dfac", [False, True])
+def test_device_resident_step_rows_equal_composition(M, ctx, tile, dfac):
+    """The device-resident step's gather + rows (4-element chunks of tile rows
+    when tiles are at least four wide and D is uniform, one element per thread
+    otherwise) against mpm_box_extract + mpm_assemble_coeffs, on a box whose x
+    extent leaves partial chunks: flags and cell ids bit for bit; the rows bit
+    for bit where both evaluate the same expression (per-voxel D), and within
+    an ulp where the step sums per-cell table entries (uniform D: the tables
+    round dt*q and a*D*n before the sums the assembly fuses into FMAs)."""
+    wl = W.random_case(31, (37, 23, 19), nspecies=3, dfac=dfac)
+    lat1 = M.DeviceLattice(wl.lattice)
+    lat2 = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    solver = M.StepSolver(ctx, lat1, prm, wl.margin, tile)
+    rep = solver.step(M.make_opts(rtol=1e-8, restart=8, maxit=500))
+    assert rep["status_code"] == M.OK
+    sub2 = ctx.subgrid_create()
+    box = sub2.mpm_box_extract(lat2, 3, wl.margin, tile)
+    sub2.mpm_assemble_coeffs(prm)
+    assert box == rep["box"]
+    for what in (M.EXPORT_FLAGS, M.EXPORT_CELL):
+        a = solver.sub.mpm_subgrid_export(what).cpu().numpy()
+        b = sub2.mpm_subgrid_export(what).cpu().numpy()
+        assert np.array_equal(a, b), what
+    for s in range(3):
+        for what in (M.EXPORT_RHS, M.EXPORT_DIAG):
+            a = solver.sub.mpm_subgrid_export(what, s).cpu().numpy()
+            b = sub2.mpm_subgrid_export(what, s).cpu().numpy()
+            if dfac:
+                assert np.array_equal(a, b), (what, s)
+            else:
+                assert np.all(np.abs(a - b) <= 2.3e-16 * np.abs(b)), (what, s, np.max(np.abs(a - b)))
+    sub2.destroy()
