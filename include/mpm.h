@@ -452,8 +452,10 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
 #define MPM_COUNTER_PHASE_EXTRACT_NS 12
 #define MPM_COUNTER_PHASE_SCATTER_NS 13
 /* mpm_step only, the extraction's phases each up to its grid barrier: the
- * bounding box, the tile activity, the active-tile counts, the compaction and
- * the gather + rows (the last without a barrier). */
+ * bounding box, the tile activity, the active-tile counts (a phase of its own
+ * only for boxes of more than 64 Ki tiles; otherwise counted within the
+ * compaction and near 0 here), the compaction and the gather + rows (the last
+ * without a barrier). */
 #define MPM_COUNTER_PHASE_BBOX_NS 14
 #define MPM_COUNTER_PHASE_ACTIVITY_NS 15
 #define MPM_COUNTER_PHASE_COUNT_NS 16

@@ -530,23 +530,35 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         if (i0 + 8 > ntiles) w &= ~0ull >> (8 * (i0 + 8 - ntiles));
         return w;
     };
-    {
+    // up to 8192 words (64 Ki tiles) every CTA counts the active tiles before
+    // its chunk itself, which spares this phase and its grid barrier
+    const bool onepass = nwords <= 8192;
+    if (!onepass) {
         unsigned long long c = 0;
         for (int32_t wi = w0 + tid; wi < w1; wi += NT) c += __popcll(word(wi) & 0x0101010101010101ull);
         c = xblock_sum<NT>(c, ssum);
         if (tid == 0) A.part_cnt[2 * b + 1] = c;
+        if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
     }
-    if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
     tick(12);
     // ---- D: compaction
     int64_t nact = 0;
     {
         unsigned long long before = 0, tot = 0, mtot = 0;
         for (int i = tid; i < nb; i += NT) {
-            const unsigned long long c = __ldcg(A.part_cnt + 2 * i + 1);
-            tot += c;
-            if (i < b) before += c;
+            if (!onepass) {
+                const unsigned long long c = __ldcg(A.part_cnt + 2 * i + 1);
+                tot += c;
+                if (i < b) before += c;
+            }
             mtot += __ldcg(A.part_cnt + 2 * i + 0);
+        }
+        if (onepass) {
+            for (int32_t wi = tid; wi < nwords; wi += NT) {
+                const unsigned long long c = __popcll(word(wi) & 0x0101010101010101ull);
+                tot += c;
+                if (wi < w0) before += c;
+            }
         }
         before = xblock_sum<NT>(before, ssum);
         tot = xblock_sum<NT>(tot, ssum);
@@ -601,7 +613,6 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
                         if (++ty == g.nt[1]) { ty = 0; ++tz; }
                     }
                 }
-                aw[wi] = 0ull;   // activity cleared for the next step
             }
             carry += rtot;
         }
@@ -609,6 +620,9 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
     if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
     tick(13);
     // ---- E: gather + rows of every stored element, neighbour table
+    // (the activity words of this CTA's chunk are cleared for the next step
+    // here, after every CTA has counted them)
+    for (int32_t wi = w0 + tid; wi < w1; wi += NT) aw[wi] = 0ull;
     const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
     const int64_t NE = g.n[0] > 0 ? nact << ltv : 0;
     const bool chunks = g.lt[0] >= 2 && !S.dfac;

@@ -598,3 +598,41 @@ def test_device_resident_step_rows_equal_composition(M, ctx, tile, dfac):
             else:
                 assert np.all(np.abs(a - b) <= 2.3e-16 * np.abs(b)), (what, s, np.max(np.abs(a - b)))
     sub2.destroy()
+
+
+def test_device_resident_step_many_tiles_equals_composition(M, ctx):
+    """A box of more than 64 Ki tiles (4x4x2 tiles on a ~130^3 box), where the
+    device-resident step counts the active tiles in a phase of its own before
+    the compaction: the same flags, cell ids and tile order as the composition
+    path, rows within an ulp (rate tables), and the same solution within the
+    residual bound."""
+    wl = W.random_case(41, (144, 140, 136), nspecies=2, ncell=9)
+    cid = _grow_cells(wl, 64, (72, 70, 68))
+    wl.lattice.cell_id = cid
+    lat1 = M.DeviceLattice(wl.lattice)
+    lat2 = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    tile = (4, 4, 2)
+    opts = M.make_opts(rtol=1e-12, restart=8, maxit=2000)
+    solver = M.StepSolver(ctx, lat1, prm, wl.margin, tile)
+    rep = solver.step(opts)
+    assert rep["status_code"] == M.OK
+    info = solver.sub.info()
+    assert info["ntiles"] > 65536
+    sub2 = ctx.subgrid_create()
+    box = sub2.mpm_box_extract(lat2, 2, wl.margin, tile)
+    assert box == rep["box"]
+    for what in (M.EXPORT_FLAGS, M.EXPORT_CELL):
+        assert np.array_equal(solver.sub.mpm_subgrid_export(what).cpu().numpy(),
+                              sub2.mpm_subgrid_export(what).cpu().numpy()), what
+    sub2.mpm_assemble_coeffs(prm)
+    for s in range(2):
+        a = solver.sub.mpm_subgrid_export(M.EXPORT_RHS, s).cpu().numpy()
+        b = sub2.mpm_subgrid_export(M.EXPORT_RHS, s).cpu().numpy()
+        assert np.all(np.abs(a - b) <= 2.3e-16 * np.abs(b)), s
+    r2 = sub2.mpm_solve_step(opts, scatter_to=lat2)
+    assert r2["status_code"] == M.OK
+    # both solutions are within ||r||_2 <= 1e-12 ||b||_2 of the exact one (||A^-1||_2 <= 1)
+    bound = 1e-12 * sum(max(a, b) for a, b in zip(rep["bnorm"], r2["bnorm"]))
+    assert np.max(np.abs(lat1.fields_numpy() - lat2.fields_numpy())) <= bound
+    sub2.destroy()
