@@ -317,7 +317,7 @@ __device__ __forceinline__ void pass_residual(const SysDev &S, bool first, uint3
 }
 
 // ---- P1: w = sigma_j A u_j into slot j+1; acc[i] += u_i . w for i <= j
-template <typename T, int MAXM, int U, bool VAR, int JJ = -1>
+template <typename T, int MAXM, int U, bool VAR, int JJ = -1, int LIM = MAXM>
 __device__ __forceinline__ void pass_arnoldi1_t(const SysDev &S, int jr, T sj, uint32_t e0, uint32_t es,
                                                 T (&acc)[MAXM + 1], bool want_ww)
 {
@@ -340,7 +340,7 @@ __device__ __forceinline__ void pass_arnoldi1_t(const SysDev &S, int jr, T sj, u
     }
     for (uint32_t e = e0; e < NE; e += U * es) {
         uint32_t f[U], q[U][6];
-        T xj[U], ns[U], dg[U], w[U], vi[U][MAXM];
+        T xj[U], ns[U], dg[U], w[U], vi[U][LIM];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t eu = e + u * es;
@@ -360,7 +360,7 @@ __device__ __forceinline__ void pass_arnoldi1_t(const SysDev &S, int jr, T sj, u
             ns[u] = var ? open_sum_var<T>(uj, S.dfac, eu, f[u], q[u], S.Dsp[0]) : open_sum<T>(uj, f[u], q[u]);
             dg[u] = ldro(dgp + eu);
 #pragma unroll
-            for (int i = 0; i < MAXM; ++i) vi[u][i] = i < j ? __ldcg(V + (int64_t)i * vs + eu) : T(0);
+            for (int i = 0; i < LIM; ++i) vi[u][i] = i < j ? __ldcg(V + (int64_t)i * vs + eu) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -368,7 +368,7 @@ __device__ __forceinline__ void pass_arnoldi1_t(const SysDev &S, int jr, T sj, u
             if (eu >= NE) continue;
             w[u] = sj * (dg[u] * xj[u] - offT * ns[u]);
 #pragma unroll
-            for (int i = 0; i <= MAXM; ++i) {
+            for (int i = 0; i <= LIM; ++i) {
                 if (i < j) acc[i] += vi[u][i] * w[u];
                 else if (i == j) acc[i] += xj[u] * w[u];
                 else if (i == j + 1 && want_ww) acc[i] += w[u] * w[u];
@@ -405,6 +405,18 @@ template <typename T, int MAXM>
 __device__ __forceinline__ constexpr bool exact_j()
 {
     return std::is_same<T, double>::value && MAXM == 8;
+}
+
+// The restart buckets above 8: the basis loops of a pass run to the smallest
+// multiple of 8 above j (j < MAXM) instead of MAXM, so a loop carries at most
+// seven predicated-off iterations.  f receives std::integral_constant<int, LIM>.
+template <int MAXM, typename F>
+__device__ __forceinline__ void with_limit(int j, F &&f)
+{
+    if (MAXM <= 8 || j < 8) f(std::integral_constant<int, (MAXM < 8 ? MAXM : 8)>{});
+    else if (MAXM <= 16 || j < 16) f(std::integral_constant<int, (MAXM < 16 ? MAXM : 16)>{});
+    else if (MAXM <= 24 || j < 24) f(std::integral_constant<int, (MAXM < 24 ? MAXM : 24)>{});
+    else f(std::integral_constant<int, MAXM>{});
 }
 
 // Four consecutive elements of a vector: one 16-byte load (FP32) or two (FP64).
@@ -462,7 +474,7 @@ __device__ __forceinline__ bool use_rows(const SysDev &S)
 // element the operands and the order of the sum are those of the scalar pass,
 // so w is the same bit for bit; the dot products add four elements per thread
 // and iteration.  Vectors written during the solve are read through L2.
-template <typename T, int MAXM>
+template <typename T, int MAXM, int LIM = MAXM>
 __device__ __forceinline__ void pass_arnoldi1_rows(const SysDev &S, int j, T sj, uint32_t e0, uint32_t es,
                                                    T (&acc)[MAXM + 1], bool want_ww)
 {
@@ -506,14 +518,14 @@ __device__ __forceinline__ void pass_arnoldi1_rows(const SysDev &S, int j, T sj,
             w[k] = sj * (dg.v[k] * u.v[k] - offT * ns);
         }
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i) {
+        for (int i = 0; i < LIM; ++i) {
             if (i < j) {
                 const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
                 acc[i] += ((b.v[0] * w[0] + b.v[1] * w[1]) + (b.v[2] * w[2] + b.v[3] * w[3]));
             }
         }
 #pragma unroll
-        for (int i = 0; i <= MAXM; ++i) {
+        for (int i = 0; i <= LIM; ++i) {
             if (i == j) acc[i] += ((u.v[0] * w[0] + u.v[1] * w[1]) + (u.v[2] * w[2] + u.v[3] * w[3]));
             else if (i == j + 1 && want_ww) acc[i] += ((w[0] * w[0] + w[1] * w[1]) + (w[2] * w[2] + w[3] * w[3]));
         }
@@ -530,13 +542,18 @@ __device__ __forceinline__ void pass_arnoldi1(const SysDev &S, int j, T sj, uint
             with_exact(j, [&](auto J) { pass_arnoldi1_t<T, MAXM, U, true, decltype(J)::value>(S, j, sj, e0, es, acc, want_ww); });
         else
             with_exact(j, [&](auto J) { pass_arnoldi1_t<T, MAXM, U, false, decltype(J)::value>(S, j, sj, e0, es, acc, want_ww); });
-    } else if (S.dfac) pass_arnoldi1_t<T, MAXM, U, true>(S, j, sj, e0, es, acc, want_ww);
-    else if (use_rows<T>(S)) pass_arnoldi1_rows<T, MAXM>(S, j, sj, e0, es, acc, want_ww);
-    else pass_arnoldi1_t<T, MAXM, U, false>(S, j, sj, e0, es, acc, want_ww);
+    } else {
+        with_limit<MAXM>(j, [&](auto L) {
+            constexpr int LIM = decltype(L)::value;
+            if (S.dfac) pass_arnoldi1_t<T, MAXM, U, true, -1, LIM>(S, j, sj, e0, es, acc, want_ww);
+            else if (use_rows<T>(S)) pass_arnoldi1_rows<T, MAXM, LIM>(S, j, sj, e0, es, acc, want_ww);
+            else pass_arnoldi1_t<T, MAXM, U, false, -1, LIM>(S, j, sj, e0, es, acc, want_ww);
+        });
+    }
 }
 
 // ---- P2: w -= sum_{i<=j} c_i u_i in place (c_i = h_ij sigma_i); acc += w^2
-template <typename T, int MAXM, int U, int JJ = -1>
+template <typename T, int MAXM, int U, int JJ = -1, int LIM = MAXM>
 __device__ __forceinline__ void pass_arnoldi2_e(const SysDev &S, int jr, const T *c, uint32_t e0, uint32_t es, T &acc)
 {
     const int j = JJ >= 0 ? JJ : jr;
@@ -551,7 +568,7 @@ __device__ __forceinline__ void pass_arnoldi2_e(const SysDev &S, int jr, const T
             if (eu >= NE) continue;
             T t = __ldcg(V + (int64_t)(j + 1) * vs + eu);   // P1 may have written it from another CTA
 #pragma unroll
-            for (int i = 0; i <= MAXM; ++i)
+            for (int i = 0; i <= LIM; ++i)
                 if (i <= j) t -= c[i] * V[(int64_t)i * vs + eu];
             w[u] = t;
             acc += t * t;
@@ -564,7 +581,7 @@ __device__ __forceinline__ void pass_arnoldi2_e(const SysDev &S, int jr, const T
     }
 }
 
-template <typename T, int MAXM>
+template <typename T, int MAXM, int LIM = MAXM>
 __device__ __forceinline__ void pass_arnoldi2_rows(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
 {
     const uint32_t NR = (uint32_t)S.NE >> 2;
@@ -574,7 +591,7 @@ __device__ __forceinline__ void pass_arnoldi2_rows(const SysDev &S, int j, const
         const uint32_t e = r << 2;
         Q4<T> t = ld4cg(V + (int64_t)(j + 1) * vs + e);
 #pragma unroll
-        for (int i = 0; i <= MAXM; ++i) {
+        for (int i = 0; i <= LIM; ++i) {
             if (i <= j) {
                 const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
                 const T ci = c[i];
@@ -590,14 +607,18 @@ __device__ __forceinline__ void pass_arnoldi2_rows(const SysDev &S, int j, const
 template <typename T, int MAXM, int U>
 __device__ __forceinline__ void pass_arnoldi2(const SysDev &S, int j, const T *c, uint32_t e0, uint32_t es, T &acc)
 {
-    if (use_rows<T>(S)) pass_arnoldi2_rows<T, MAXM>(S, j, c, e0, es, acc);
-    else if (exact_j<T, MAXM>())
+    if (exact_j<T, MAXM>() && !use_rows<T>(S))
         with_exact(j, [&](auto J) { pass_arnoldi2_e<T, MAXM, U, decltype(J)::value>(S, j, c, e0, es, acc); });
-    else pass_arnoldi2_e<T, MAXM, U>(S, j, c, e0, es, acc);
+    else
+        with_limit<MAXM>(j, [&](auto L) {
+            constexpr int LIM = decltype(L)::value;
+            if (use_rows<T>(S)) pass_arnoldi2_rows<T, MAXM, LIM>(S, j, c, e0, es, acc);
+            else pass_arnoldi2_e<T, MAXM, U, -1, LIM>(S, j, c, e0, es, acc);
+        });
 }
 
 // ---- P1b (reorthogonalisation): acc[i] += u_i . w for i <= j, w in slot j+1
-template <typename T, int MAXM, int U>
+template <typename T, int MAXM, int U, int LIM = MAXM>
 __device__ __forceinline__ void pass_dots_e(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
 {
     const uint32_t NE = (uint32_t)S.NE;
@@ -610,13 +631,13 @@ __device__ __forceinline__ void pass_dots_e(const SysDev &S, int j, uint32_t e0,
             if (eu >= NE) continue;
             const T w = V[(int64_t)(j + 1) * vs + eu];
 #pragma unroll
-            for (int i = 0; i <= MAXM; ++i)
+            for (int i = 0; i <= LIM; ++i)
                 if (i <= j) acc[i] += V[(int64_t)i * vs + eu] * w;
         }
     }
 }
 
-template <typename T, int MAXM>
+template <typename T, int MAXM, int LIM = MAXM>
 __device__ __forceinline__ void pass_dots_rows(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
 {
     const uint32_t NR = (uint32_t)S.NE >> 2;
@@ -626,7 +647,7 @@ __device__ __forceinline__ void pass_dots_rows(const SysDev &S, int j, uint32_t 
         const uint32_t e = r << 2;
         const Q4<T> w = ld4cg(V + (int64_t)(j + 1) * vs + e);
 #pragma unroll
-        for (int i = 0; i <= MAXM; ++i) {
+        for (int i = 0; i <= LIM; ++i) {
             if (i <= j) {
                 const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
                 acc[i] += (b.v[0] * w.v[0] + b.v[1] * w.v[1]) + (b.v[2] * w.v[2] + b.v[3] * w.v[3]);
@@ -638,13 +659,16 @@ __device__ __forceinline__ void pass_dots_rows(const SysDev &S, int j, uint32_t 
 template <typename T, int MAXM, int U>
 __device__ __forceinline__ void pass_dots(const SysDev &S, int j, uint32_t e0, uint32_t es, T (&acc)[MAXM + 1])
 {
-    if (use_rows<T>(S)) pass_dots_rows<T, MAXM>(S, j, e0, es, acc);
-    else pass_dots_e<T, MAXM, U>(S, j, e0, es, acc);
+    with_limit<MAXM>(j, [&](auto L) {
+        constexpr int LIM = decltype(L)::value;
+        if (use_rows<T>(S)) pass_dots_rows<T, MAXM, LIM>(S, j, e0, es, acc);
+        else pass_dots_e<T, MAXM, U, LIM>(S, j, e0, es, acc);
+    });
 }
 
 // ---- U: x += sum_{i<k} c_i u_i (c_i = y_i sigma_i); the FP32 path adds its
 // FP32 correction d to the FP64 iterate.
-template <typename T, int MAXM, int U, int KK = -1>
+template <typename T, int MAXM, int U, int KK = -1, int LIM = MAXM>
 __device__ __forceinline__ void pass_update_e(const SysDev &S, int kr, const T *c, uint32_t e0, uint32_t es)
 {
     const int k = KK >= 0 ? KK : kr;   // KK >= 0: the vector count known at compile time
@@ -661,7 +685,7 @@ __device__ __forceinline__ void pass_update_e(const SysDev &S, int kr, const T *
             if (eu >= NE) continue;
             T t = T(0);
 #pragma unroll
-            for (int i = 0; i < MAXM; ++i)
+            for (int i = 0; i < LIM; ++i)
                 if (i < k) t += c[i] * V[(int64_t)i * vs + eu];
             d[u] = t;
             xv[u] = x[eu];
@@ -674,7 +698,7 @@ __device__ __forceinline__ void pass_update_e(const SysDev &S, int kr, const T *
     }
 }
 
-template <typename T, int MAXM>
+template <typename T, int MAXM, int LIM = MAXM>
 __device__ __forceinline__ void pass_update_rows(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
 {
     const uint32_t NR = (uint32_t)S.NE >> 2;
@@ -686,7 +710,7 @@ __device__ __forceinline__ void pass_update_rows(const SysDev &S, int k, const T
         const Q4<double> xv = ld4cg(x + e);
         T d[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i) {
+        for (int i = 0; i < LIM; ++i) {
             if (i < k) {
                 const Q4<T> b = ld4cg(V + (int64_t)i * vs + e);
                 const T ci = c[i];
@@ -704,10 +728,14 @@ __device__ __forceinline__ void pass_update_rows(const SysDev &S, int k, const T
 template <typename T, int MAXM, int U>
 __device__ __forceinline__ void pass_update(const SysDev &S, int k, const T *c, uint32_t e0, uint32_t es)
 {
-    if (use_rows<T>(S)) pass_update_rows<T, MAXM>(S, k, c, e0, es);
-    else if (exact_j<T, MAXM>())   // k = 1..8 vectors
+    if (exact_j<T, MAXM>() && !use_rows<T>(S))   // k = 1..8 vectors
         with_exact(k - 1, [&](auto J) { pass_update_e<T, MAXM, U, decltype(J)::value + 1>(S, k, c, e0, es); });
-    else pass_update_e<T, MAXM, U>(S, k, c, e0, es);
+    else
+        with_limit<MAXM>(k - 1, [&](auto L) {   // i < k <= LIM
+            constexpr int LIM = decltype(L)::value;
+            if (use_rows<T>(S)) pass_update_rows<T, MAXM, LIM>(S, k, c, e0, es);
+            else pass_update_e<T, MAXM, U, -1, LIM>(S, k, c, e0, es);
+        });
 }
 
 // The persistent GMRES of one CTA of a team (every item of its team in turn).
