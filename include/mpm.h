@@ -89,6 +89,14 @@ typedef struct {
                                ||w|| fell below 0.7 of its norm before orthogonalisation
                                (the Daniel-Gragg-Kaufman-Stewart test; 0 or 1, else MPM_ERR_ARG; the modified
                                Gram-Schmidt of mpm_solve_fgmres_cnn ignores it) */
+    int32_t box_every;      /* mpm_step only (Sec. 2.3's box cadence): 0 or 1, a new bounding box,
+                               tile set and neighbour table every step; K > 1, a full extraction
+                               on the first step and then every K steps, the steps in between
+                               keeping the box and tiles and re-gathering c^n, cell ids and rows.
+                               The mask must not change between full extractions. */
+    int32_t box_guard;      /* mpm_step with box_every > 1: a tumour voxel (cell id > 0) within
+                               box_guard voxels of a box face that is not a lattice face makes
+                               the next step a full extraction (0: off).  Negative: MPM_ERR_ARG */
 } mpm_opts;
 
 typedef struct {
@@ -461,6 +469,10 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
 #define MPM_COUNTER_PHASE_COUNT_NS 16
 #define MPM_COUNTER_PHASE_COMPACT_NS 17
 #define MPM_COUNTER_PHASE_GATHER_NS 18
+/* mpm_step: full extractions (new box, tile set and neighbour table) since the
+ * step's graph was last set up, as of the last step waited for (with
+ * mpm_opts.box_every > 1 the other steps keep the box). */
+#define MPM_COUNTER_STEP_FULL_EXTRACTIONS 19
 mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value);
 
 /*

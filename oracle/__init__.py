@@ -168,11 +168,15 @@ def dense_solve(A: CSR, b):
 
 # ---------------------------------------------------------------- one step of the method
 def step(lat, params, margin: int, bc_box: int = 0, rtol: float = 1e-12, atol: float = 0.0,
-         restart: int = 30, maxit: int = 10000, solver: str = "gmres", x0=None):
+         restart: int = 30, maxit: int = 10000, solver: str = "gmres", x0=None, box=None):
     """Advance every species of `lat` (a workloads.Lattice, modified in place) by one
     implicit-Euler step inside the bounding box; returns a report dict.  `x0`
-    optionally gives per-species initial guesses on the box (default c^n)."""
-    box = bbox(lat.cell_id, margin)
+    optionally gives per-species initial guesses on the box (default c^n).
+    `box` (lo, hi) solves on a box kept from an earlier step instead of this
+    step's bounding box: Sec. 2.3 refreshes the box only every 50 MCS and the
+    steps in between keep it."""
+    if box is None:
+        box = bbox(lat.cell_id, margin)
     if box is None:
         return {"status": ERR_EMPTY, "box": None}
     sl = box_slices(box)

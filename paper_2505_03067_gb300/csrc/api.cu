@@ -369,6 +369,7 @@ mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)
         *value = (int64_t)ctx->h_prof[4 + key - MPM_COUNTER_PHASE_R_NS];
         return MPM_OK;
     }
+    if (key == MPM_COUNTER_STEP_FULL_EXTRACTIONS) { *value = ctx->step_nfull; return MPM_OK; }
     return MPM_ERR_ARG;
 }
 

@@ -393,6 +393,7 @@ struct mpm_ctx {
     unsigned long long *d_prof = nullptr;
     unsigned long long h_prof[16] = {};   // phase timer slots (kProfSlots used)
     double last_imbalance = 0.0; // t_max / <t> - 1 over the teams of the last solve
+    int64_t step_nfull = 0;      // mpm_step: full extractions so far (MPM_COUNTER_STEP_FULL_EXTRACTIONS)
     // test hooks
     uint64_t timeout_ns = 2000000000ull;
     int32_t skip_block = -1;

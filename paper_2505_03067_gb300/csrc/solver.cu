@@ -207,6 +207,8 @@ static mpm_status check_opts(mpm_ctx *ctx, const mpm_opts *opt)
     if (opt->maxit < 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: maxit < 1");
     if (opt->precision != 0 && opt->precision != 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: precision must be 0 or 1");
     if (opt->reorth != 0 && opt->reorth != 1) return mpm_fail(ctx, MPM_ERR_ARG, "solve: reorth must be 0 or 1");
+    if (opt->box_every < 0 || opt->box_guard < 0)
+        return mpm_fail(ctx, MPM_ERR_ARG, "solve: box_every and box_guard must not be negative");
     if (!(opt->rtol >= 0.0) || !(opt->atol >= 0.0)) return mpm_fail(ctx, MPM_ERR_ARG, "solve: negative tolerance");
     if (opt->precision == 1 && !(opt->inner_rtol > 0.0 && opt->inner_rtol < 1.0))
         return mpm_fail(ctx, MPM_ERR_ARG, "solve: inner_rtol must be in (0, 1)");
@@ -687,7 +689,8 @@ struct StepGraph {
 };
 
 static constexpr size_t kOutBox = 0, kOutCount = 64, kOutAbort = 128, kOutRep = 256;
-static constexpr size_t kScrBox = 0, kScrCount = 256, kScrAbort = 512, kScrDyn = 768;
+static constexpr size_t kScrBox = 0, kScrCount = 256, kScrAbort = 512, kScrDyn = 768, kScrCad = 896;
+static constexpr size_t kOutNFull = 160;   // full extractions so far (StepCad::nfull)
 
 // Extraction scratch for a grid of nb CTAs: box partials (32 B per CTA), count
 // partials (16 B per CTA), then the grid barrier counter and the exit counter.
@@ -749,7 +752,7 @@ static BatchSys step_sys(mpm_subgrid *sub, const mpm_lattice *lat, const mpm_par
 
 // One step on stream cs (captured or eager): the whole-step kernel.
 static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, const mpm_lattice *lat,
-                               const mpm_params *prm, int32_t margin, cudaStream_t cs)
+                               const mpm_params *prm, int32_t margin, const mpm_opts *opt, cudaStream_t cs)
 {
     SolvePlan &P = T->plan;
     const int nb = P.G;
@@ -802,6 +805,9 @@ static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, con
     X.ra.dk = T->d_rates;
     X.ra.dq = T->d_rates + (size_t)prm->nspecies * prm->ncell;
     X.prof = ctx->phase_prof ? ctx->d_prof : nullptr;
+    X.cad = (StepCad *)(T->d_scr + kScrCad);
+    X.box_every = opt->box_every;
+    X.box_guard = opt->box_guard;
     A.S = step_sys(sub, lat, prm, T->d_rates);
     A.o.box = d_box;
     A.o.count = (const unsigned long long *)d_count;
@@ -955,7 +961,7 @@ mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_latti
             const int64_t launches0 = ctx->launches;
             bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                ok = enqueue_step(ctx, T, sub, lat, prm, margin, cs) == MPM_OK;
+                ok = enqueue_step(ctx, T, sub, lat, prm, margin, opt, cs) == MPM_OK;
                 const cudaError_t ec = cudaStreamEndCapture(cs, &g);
                 ok = ok && ec == cudaSuccess && g != nullptr;
             }
@@ -977,7 +983,7 @@ mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_latti
         MPM_CU(cudaGraphLaunch(T->exec, st));
         ctx->launches += T->graph_launches;
     } else {
-        r = enqueue_step(ctx, T, sub, lat, prm, margin, st);
+        r = enqueue_step(ctx, T, sub, lat, prm, margin, opt, st);
         if (r != MPM_OK) return r;
     }
     T->pending = true;
@@ -1002,6 +1008,7 @@ mpm_status mpm_step_wait_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, m
     mpm_status r;
     const volatile int32_t *hb = (const volatile int32_t *)(T->h_out + kOutBox);
     const volatile int64_t *hc = (const volatile int64_t *)(T->h_out + kOutCount);
+    ctx->step_nfull = *(const volatile uint32_t *)(T->h_out + kOutNFull);
     if (*(const volatile int32_t *)(T->h_out + kOutAbort) != 0) {
         // a bounded wait expired: nothing was scattered; set the between-step state up again
         T->valid = false;

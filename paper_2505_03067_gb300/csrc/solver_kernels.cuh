@@ -1062,9 +1062,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     // it, and the wait for the last team plus the scatter
     const bool prof = P.sa.prof != nullptr && b == 0 && tid == 0;
     uint64_t t0 = prof ? globaltimer_ns() : 0;
+    // the box cadence: a full extraction unless the previous step let this one
+    // keep the box (its last CTA decided; see the end of this kernel)
+    const bool full = P.xa.box_every <= 1 || *(const volatile uint32_t *)&P.xa.cad->refresh_ok == 0u;
     if (b != P.sa.skip_block) {                     // fault injection: this CTA never arrives
         uint32_t epoch = 0;
-        bool ok = extract_phases<NT>(P.xa, P.S, b, nb, epoch);
+        bool ok = full ? extract_phases<NT>(P.xa, P.S, b, nb, epoch) : refresh_phases<NT>(P.xa, P.S, b, nb, epoch);
         ok = ok && team_barrier(P.xa.bar, epoch, nb, P.xa.xabort, P.xa.timeout_ns);
         if (prof) {
             const uint64_t t = globaltimer_ns();
@@ -1102,6 +1105,18 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     if (tid == 0) *reinterpret_cast<int32_t *>(P.o.host + 128) = *(volatile int32_t *)P.xa.xabort;
     for (int i = tid; i < P.o.nrep_words; i += NT) hr[i] = __ldcg(P.o.reports + i);
     if (tid == 0) {
+        // the cadence for the next step: keep the box while fewer than
+        // box_every steps used it, no tumour voxel reached its guard band, the
+        // box is not empty and no wait gave up
+        StepCad *c = P.xa.cad;
+        const uint32_t cnt = full ? 1u : c->count + 1u;
+        c->count = cnt;
+        if (full) c->nfull += 1u;
+        const bool keep = P.xa.box_every > 1 && cnt < (uint32_t)P.xa.box_every &&
+                          *(volatile uint32_t *)&c->guard_hit == 0u && __ldcg(&P.xa.dyn->NE) > 0 &&
+                          *(volatile int32_t *)P.xa.xabort == 0;
+        c->refresh_ok = keep ? 1u : 0u;
+        *reinterpret_cast<uint32_t *>(P.o.host + 160) = c->nfull;
         *P.xa.bar = 0u;
         *P.o.exit_count = 0u;
     }

@@ -38,12 +38,38 @@ struct RowTab {
     double wbn[kMaxSpecies][7];
 };
 
+// Box cadence of the device-resident step (Sec. 2.3 refreshes the box every
+// 50 MCS and keeps it in between).  Device memory, zero when the step is set
+// up: refresh_ok = 1 lets the next step keep the box, count = steps since the
+// last full extraction, guard_hit = a tumour voxel was gathered in the guard
+// band, nfull = full extractions so far.
+struct StepCad {
+    uint32_t refresh_ok, count, guard_hit, nfull;
+};
+
+// The guard band of a box: the voxels within h of a box face that lies
+// inside the lattice (a face on the lattice boundary cannot be crossed).
+struct GuardBand {
+    int h;
+    int lo_in[3], hi_in[3];
+    __device__ __forceinline__ bool in(int bx, int by, int bz, const BoxGeo &g) const
+    {
+        const int c[3] = {bx, by, bz};
+        bool r = false;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r |= (lo_in[d] && c[d] < h) || (hi_in[d] && c[d] >= g.n[d] - h);
+        return r;
+    }
+};
+
 // One element of the fused preparation: flags, cell id, diffusivity factor
 // and c^n gathered from the lattice, then the row of every species.
 // kTab: the device-resident form (rows from the rate tables; tile coordinates
 // and tables written earlier in the same kernel, so read through L2).
+// gb (device-resident step): a tumour voxel in the guard band sets *hit.
 template <bool kTab>
-__device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, int64_t e, const RowTab *tab = nullptr)
+__device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, int64_t e, const RowTab *tab = nullptr,
+                                          const GuardBand *gb = nullptr, bool *hit = nullptr)
 {
     const int ns = S.C.nspecies;
     int bx, by, bz;
@@ -73,6 +99,7 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
     const uint32_t m3 = hy0 ? __ldg(S.mask + L - sy) : 0u, m4 = hy1 ? __ldg(S.mask + L + sy) : 0u;
     const uint32_t m5 = hz0 ? __ldg(S.mask + L - sz) : 0u, m6 = hz1 ? __ldg(S.mask + L + sz) : 0u;
     const int32_t id0 = __ldg(S.cell_id + L);
+    if (gb && id0 > 0 && gb->in(bx, by, bz, g)) *hit = true;
     const double fp = S.dfac_lat ? __ldg(S.dfac_lat + L) : 1.0;
     double cs[kMaxSpecies];
 #pragma unroll
@@ -150,7 +177,8 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
 // lattice loads of all four are in flight together, and the element arrays
 // are written with 4- to 16-byte stores.  Per element the rows are those of
 // prep_elem<true> (same operands, same order).
-__device__ __forceinline__ void prep_chunk(const BatchSys &S, const BoxGeo &g, uint32_t r, const RowTab *tab)
+__device__ __forceinline__ void prep_chunk(const BatchSys &S, const BoxGeo &g, uint32_t r, const RowTab *tab,
+                                           const GuardBand *gb, bool *hit)
 {
     const int ns = S.C.nspecies;
     const uint32_t e = r << 2;
@@ -179,6 +207,11 @@ __device__ __forceinline__ void prep_chunk(const BatchSys &S, const BoxGeo &g, u
         id0[k] = in ? __ldg(S.cell_id + L) : 0;
 #pragma unroll
         for (int s = 0; s < kMaxSpecies; ++s) cs[s][k] = in && s < ns ? __ldg(S.field[s] + L) : 0.0;
+    }
+    if (gb) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < nv && id0[k] > 0 && gb->in(bx0 + k, by, bz, g)) *hit = true;
     }
     const uint32_t mxm = nv > 0 && bx0 > 0 ? __ldg(S.mask + L0 - 1) : 0u;
     const uint32_t mxp = nv == 4 && bx0 + 4 < g.n[0] ? __ldg(S.mask + L0 + 4) : 0u;
@@ -326,8 +359,78 @@ struct ExtractArgs {
     uint32_t *srep;
     int32_t nrep_words;
     RateArgs ra;
+    StepCad *cad;                      // box cadence state
+    int32_t box_every, box_guard;      // mpm_opts' cadence: full extraction every box_every steps
     unsigned long long *prof;          // nullable: CTA 0 adds ns per phase A..E (each up to its barrier)
 };
+
+// Per-CTA row tables and, grid-strided, the per-(species, cell) rate tables.
+template <int NT>
+__device__ __forceinline__ void row_tables(const ExtractArgs &A, const BatchSys &S, int b, int nb, RowTab &tab)
+{
+    const int tid = threadIdx.x;
+    for (int i = tid; i < S.C.nspecies * 20; i += NT) {
+        const int s = i / 20, n = i % 20;
+        if (n < 13) tab.aDn[s][n] = S.C.a * S.C.D[s] * (double)n;
+        else tab.wbn[s][n - 13] = S.C.a * 2.0 * S.C.D[s] * S.C.cbc[s] * (double)(n - 13);
+    }
+    const int64_t nr = (int64_t)A.ra.nspecies * A.ra.ncell;
+    for (int64_t i = (int64_t)b * NT + tid; i < nr; i += (int64_t)nb * NT) {
+        const int s = (int)(i / A.ra.ncell);
+        A.ra.dk[i] = 1.0 + A.ra.dt * (A.ra.mu[s] + A.ra.k_cell[i]);
+        A.ra.dq[i] = A.ra.dt * A.ra.q_cell[i];
+    }
+}
+
+// The guard band of box g (empty unless the cadence keeps boxes).
+__device__ __forceinline__ GuardBand guard_band(const ExtractArgs &A, const BoxGeo &g)
+{
+    GuardBand gb;
+    gb.h = A.box_every > 1 ? A.box_guard : 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        gb.lo_in[d] = g.lo[d] > 0;
+        gb.hi_in[d] = g.lo[d] + g.n[d] < A.L[d];
+    }
+    return gb;
+}
+
+// Phase E: gather + rows of every stored element (4-element chunks where the
+// tiles are at least four wide and D is uniform), the neighbour table when
+// nbr, and the guard vote (one atomic per CTA).
+template <int NT>
+__device__ __forceinline__ void gather_phase(const ExtractArgs &A, const BatchSys &S, const BoxGeo &g, int64_t NE,
+                                             int b, int nb, const RowTab &tab, bool nbr)
+{
+    const int tid = threadIdx.x;
+    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
+    const GuardBand gbv = guard_band(A, g);
+    const GuardBand *gb = gbv.h > 0 ? &gbv : nullptr;
+    bool hit = false;
+    const bool chunks = g.lt[0] >= 2 && !S.dfac;
+    const int64_t nunit = chunks ? NE >> 2 : NE;   // 4-element chunks or elements
+    for (int64_t u = (int64_t)b * NT + tid; u < nunit; u += (int64_t)nb * NT) {
+        const int64_t e = chunks ? u << 2 : u;
+        if (chunks) prep_chunk(S, g, (uint32_t)u, &tab, gb, &hit);
+        else prep_elem<true>(S, g, e, &tab, gb, &hit);
+        if (nbr && (e & ((1 << ltv) - 1)) == 0) {   // neighbour tiles of this tile
+            const int64_t a = e >> ltv;
+            const int4 c = __ldcg(reinterpret_cast<const int4 *>(S.tile_coord) + a);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                int32_t q[3] = {c.x, c.y, c.z};
+                q[d >> 1] += (d & 1) ? 1 : -1;
+                int32_t r = -1;
+                if (q[0] >= 0 && q[0] < g.nt[0] && q[1] >= 0 && q[1] < g.nt[1] && q[2] >= 0 && q[2] < g.nt[2])
+                    r = __ldcg(S.tile_index + (q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]);
+                S.nbr[6 * a + d] = r;
+            }
+        }
+    }
+    if (gb) {   // uniform over the CTA
+        if (__syncthreads_or(hit) && tid == 0) atomicOr(&A.cad->guard_hit, 1u);
+    }
+}
 
 // Block-wide sum over NT threads (every thread gets the total).
 template <int NT>
@@ -377,7 +480,11 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
             tp = t;
         }
     };
-    if (b == 0 && tid == 0) { A.dyn->NE = 0; A.dyn->g.n[0] = 0; }
+    if (b == 0 && tid == 0) {
+        A.dyn->NE = 0;
+        A.dyn->g.n[0] = 0;
+        A.cad->guard_hit = 0u;
+    }
     // ---- A: bounding box, per CTA
     {
         const int64_t Ltot = (int64_t)A.L[0] * A.L[1] * A.L[2];
@@ -470,17 +577,7 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
                 *A.geo_out = g;
             }
         }
-        for (int i = tid; i < S.C.nspecies * 20; i += NT) {   // per-CTA row tables (phase E)
-            const int s = i / 20, n = i % 20;
-            if (n < 13) tab.aDn[s][n] = S.C.a * S.C.D[s] * (double)n;
-            else tab.wbn[s][n - 13] = S.C.a * 2.0 * S.C.D[s] * S.C.cbc[s] * (double)(n - 13);
-        }
-        const int64_t nr = (int64_t)A.ra.nspecies * A.ra.ncell;
-        for (int64_t i = (int64_t)b * NT + tid; i < nr; i += (int64_t)nb * NT) {
-            const int s = (int)(i / A.ra.ncell);
-            A.ra.dk[i] = 1.0 + A.ra.dt * (A.ra.mu[s] + A.ra.k_cell[i]);
-            A.ra.dq[i] = A.ra.dt * A.ra.q_cell[i];
-        }
+        row_tables<NT>(A, S, b, nb, tab);   // per-CTA row tables (phase E), rate tables
         __syncthreads();
         unsigned long long cnt = 0;
         if (g.n[0] > 0) {
@@ -625,31 +722,40 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
     for (int32_t wi = w0 + tid; wi < w1; wi += NT) aw[wi] = 0ull;
     const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
     const int64_t NE = g.n[0] > 0 ? nact << ltv : 0;
-    const bool chunks = g.lt[0] >= 2 && !S.dfac;
-    const int64_t nunit = chunks ? NE >> 2 : NE;   // 4-element chunks or elements
-    for (int64_t u = (int64_t)b * NT + tid; u < nunit; u += (int64_t)nb * NT) {
-        const int64_t e = chunks ? u << 2 : u;
-        if (chunks) prep_chunk(S, g, (uint32_t)u, &tab);
-        else prep_elem<true>(S, g, e, &tab);
-        if ((e & ((1 << ltv) - 1)) == 0) {          // neighbour tiles of this tile
-            const int64_t a = e >> ltv;
-            const int4 c = __ldcg(reinterpret_cast<const int4 *>(S.tile_coord) + a);
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                int32_t q[3] = {c.x, c.y, c.z};
-                q[d >> 1] += (d & 1) ? 1 : -1;
-                int32_t r = -1;
-                if (q[0] >= 0 && q[0] < g.nt[0] && q[1] >= 0 && q[1] < g.nt[1] && q[2] >= 0 && q[2] < g.nt[2])
-                    r = __ldcg(S.tile_index + (q[2] * g.nt[1] + q[1]) * g.nt[0] + q[0]);
-                S.nbr[6 * a + d] = r;
-            }
-        }
-    }
+    gather_phase<NT>(A, S, g, NE, b, nb, tab, true);
     if (b == 0 && tid == 0) {
         A.dyn->g = g;
         A.dyn->NE = NE;
     }
     tick(14);
+    return true;
+}
+
+// A step that keeps the box, tiles and neighbour table of the last full
+// extraction (box_every > 1): the resets the compaction does, the row and rate
+// tables, one grid barrier, then the gather + rows of every stored element.
+template <int NT>
+__device__ __forceinline__ bool refresh_phases(const ExtractArgs &A, const BatchSys &S, int b, int nb, uint32_t &epoch)
+{
+    __shared__ RowTab tab;
+    const int tid = threadIdx.x;
+    const bool prof = A.prof != nullptr && b == 0 && tid == 0;
+    uint64_t tp = prof ? globaltimer_ns() : 0;
+    if (b == 0) {
+        if (tid == 0) {
+            *A.err = 0;
+            A.cad->guard_hit = 0u;
+        }
+        for (int i = tid; i < A.nsbar; i += NT) A.sbar[i] = 0u;
+        for (int i = tid; i < A.nrep_words; i += NT) A.srep[i] = 0u;
+    }
+    row_tables<NT>(A, S, b, nb, tab);
+    __syncthreads();
+    if (!team_barrier(A.bar, epoch, nb, A.xabort, A.timeout_ns)) return false;
+    const BoxGeo g = A.dyn->g;
+    const int64_t NE = A.dyn->NE;
+    gather_phase<NT>(A, S, g, NE, b, nb, tab, false);
+    if (prof) A.prof[14] += globaltimer_ns() - tp;
     return true;
 }
 

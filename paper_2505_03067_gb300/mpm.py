@@ -19,6 +19,7 @@ OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_CUDA, ERR_NO
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_EMPTY", "ERR_NOCONV", "ERR_BREAKDOWN", "ERR_TIMEOUT", "ERR_CUDA", "ERR_NOMEM"]
 EXPORT_X, EXPORT_RHS, EXPORT_DIAG, EXPORT_FLAGS, EXPORT_CELL = range(5)
 DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK, DEBUG_PHASE_TIMES, DEBUG_SOLVER_VARIANT = 1, 2, 3, 4
+COUNTER_STEP_FULL_EXTRACTIONS = 19
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
@@ -63,7 +64,7 @@ class mpm_params(C.Structure):
 class mpm_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
                 ("precision", C.c_int32), ("inner_rtol", C.c_double), ("x0_given", C.c_int32),
-                ("nblocks", C.c_int32), ("reorth", C.c_int32)]
+                ("nblocks", C.c_int32), ("reorth", C.c_int32), ("box_every", C.c_int32), ("box_guard", C.c_int32)]
 
 
 class mpm_report(C.Structure):
@@ -216,11 +217,11 @@ class DeviceParams:
 
 
 def make_opts(rtol=1e-6, atol=0.0, restart=30, maxit=1000, precision=0, inner_rtol=1e-5, x0_given=0,
-              nblocks=0, reorth=0) -> mpm_opts:
+              nblocks=0, reorth=0, box_every=1, box_guard=0) -> mpm_opts:
     o = mpm_opts()
     o.rtol, o.atol, o.restart, o.maxit = rtol, atol, restart, maxit
     o.precision, o.inner_rtol, o.x0_given, o.nblocks = precision, inner_rtol, x0_given, nblocks
-    o.reorth = reorth
+    o.reorth, o.box_every, o.box_guard = reorth, box_every, box_guard
     return o
 
 

@@ -636,3 +636,75 @@ def test_device_resident_step_many_tiles_equals_composition(M, ctx):
     bound = 1e-12 * sum(max(a, b) for a, b in zip(rep["bnorm"], r2["bnorm"]))
     assert np.max(np.abs(lat1.fields_numpy() - lat2.fields_numpy())) <= bound
     sub2.destroy()
+
+
+# ---------------------------------------------------------------- box cadence (Sec. 2.3: a box every 50 MCS)
+def test_box_cadence_static_tumour_is_bit_identical(M):
+    """box_every = 4 on a tumour that does not move: the steps in between keep
+    the box, tiles and neighbour table and re-gather c^n and the rows, which
+    gives the every-step extraction's results bit for bit; 10 steps take 3 full
+    extractions (steps 0, 4, 8)."""
+    c = M.Context()
+    wl = W.random_case(19, (30, 26, 22), nspecies=3)
+    outs = []
+    for every in (1, 4):
+        lat = M.DeviceLattice(wl.lattice)
+        solver = M.StepSolver(c, lat, M.DeviceParams(wl.params), wl.margin)
+        opts = M.make_opts(rtol=1e-10, restart=8, maxit=500, box_every=every)
+        for _ in range(10):
+            rep = solver.step(opts)
+            assert rep["status_code"] == M.OK
+        outs.append(lat.fields_numpy())
+        assert c.counter(M.COUNTER_STEP_FULL_EXTRACTIONS) == (10 if every == 1 else 3)
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_box_cadence_keeps_the_box_and_the_guard_refreshes_it(M, ctx):
+    """A growing tumour with box_every = 50 and a guard band of 2 voxels (the
+    margin is 4): while the tumour stays clear of the band the box is kept (the
+    oracle, solving on the same kept box, agrees at 1e-10); once a tumour voxel
+    enters the band, the next step extracts a new box, the bounding box of
+    that step's tumour."""
+    wl = W.random_case(21, (48, 40, 36), nspecies=3, ncell=9)
+    wl.margin = 4
+    ref = wl.lattice.copy()
+    lat = M.DeviceLattice(wl.lattice)
+    solver = M.StepSolver(ctx, lat, M.DeviceParams(wl.params), wl.margin, (4, 4, 2))
+    opts = M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=2000, box_every=50, box_guard=2)
+    kept, refreshed = 0, 0
+    box = None
+    pending_refresh = True
+    for k, r in enumerate([3.0, 3.0, 3.6, 4.2, 5.0, 5.0, 6.0, 7.5, 7.5, 9.0]):
+        cid = _grow_cells(wl, r, (20, 18, 16))
+        ref.cell_id = cid
+        lat.cell_id.copy_(__import__("torch").from_numpy(cid))
+        rep = solver.step(opts)
+        assert rep["status_code"] == M.OK
+        fresh = oracle.bbox(cid, wl.margin)
+        if pending_refresh:
+            assert rep["box"] == fresh, k          # a full extraction
+            refreshed += 1
+        else:
+            assert rep["box"] == box, k            # the kept box
+            kept += 1
+        box = rep["box"]
+        ro = oracle.step(ref, wl.params, wl.margin, rtol=0.0, atol=1e-13, box=box)
+        assert np.max(np.abs(lat.fields_numpy() - ref.fields)) <= 1e-10, k
+        # the guard: a tumour voxel within 2 of a box face inside the lattice
+        (lx, ly, lz), (hx, hy, hz) = box
+        zz, yy, xx = np.nonzero(cid > 0)
+        L = (cid.shape[2], cid.shape[1], cid.shape[0])
+        near = False
+        for c_, lo, hi, n in ((xx, lx, hx, L[0]), (yy, ly, hy, L[1]), (zz, lz, hz, L[2])):
+            inb = (c_ >= lo) & (c_ < hi)
+            near |= bool(np.any(inb & (c_ < lo + 2) & (lo > 0))) or bool(np.any(inb & (c_ >= hi - 2) & (hi < n)))
+        pending_refresh = near
+    assert kept >= 3 and refreshed >= 2
+
+
+def test_box_cadence_rejects_negative_values(M, ctx):
+    wl = W.random_case(3, (16, 16, 16), nspecies=1)
+    for kw in ({"box_every": -1}, {"box_guard": -2}):
+        with pytest.raises(M.MpmError) as ei:
+            _gpu_step(M, ctx, wl, M.make_opts(**kw))
+        assert ei.value.status == M.ERR_ARG

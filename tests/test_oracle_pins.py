@@ -316,3 +316,23 @@ def test_empty_tumour_reports_empty():
     wl = W.random_case(1, (5, 5, 5))
     wl.lattice.cell_id[:] = 0
     assert oracle.step(wl.lattice, wl.params, 2)["status"] == oracle.ERR_EMPTY
+
+
+def test_step_on_a_kept_box():
+    """oracle.step(box=...) solves on a box kept from an earlier step: given the
+    step's own bounding box it is the plain step bit for bit, and with a smaller
+    kept box the voxels outside it keep c^n."""
+    wl = W.random_case(5, (14, 12, 10), nspecies=2)
+    a, b = wl.lattice.copy(), wl.lattice.copy()
+    box = oracle.bbox(wl.lattice.cell_id, wl.margin)
+    oracle.step(a, wl.params, wl.margin, rtol=0.0, atol=1e-12)
+    oracle.step(b, wl.params, wl.margin, rtol=0.0, atol=1e-12, box=box)
+    assert np.array_equal(a.fields, b.fields)
+    (lx, ly, lz), (hx, hy, hz) = box
+    small = ((lx + 1, ly + 1, lz + 1), (hx - 1, hy - 1, hz - 1))
+    c = wl.lattice.copy()
+    oracle.step(c, wl.params, wl.margin, rtol=0.0, atol=1e-12, box=small)
+    out = np.ones(c.fields.shape[1:], bool)
+    out[oracle.box_slices(small)] = False
+    assert np.array_equal(c.fields[:, out], wl.lattice.fields[:, out])
+    assert not np.array_equal(c.fields, wl.lattice.fields)
