@@ -857,16 +857,17 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
                 team_reduce<NT>(A.partials + pbuf * pstride, td.first_block, nb, cm, j + 1 + (A.reorth != 0), sm.tot);
                 MPM_TICK(2);
                 pbuf ^= 1;
-                if (tid < NS && ((cm >> tid) & 1u)) {
-                    for (int i = 0; i <= j; ++i) {
-                        const T h = sm.sig[tid][i] * (T)sm.tot[tid * kKStride + i];
-                        sm.H[tid][i * MAXM + j] = h;
-                        const T c = h * sm.sig[tid][i];
-                        if (kF32) sm.coef32[tid][i] = (float)c;
-                        else sm.coef[tid][i] = (double)c;
-                    }
-                    if (A.reorth) sm.sp[tid].wwb = sm.tot[tid * kKStride + j + 1];
+                // the new Hessenberg column and the projection coefficients, one
+                // thread per basis vector (a work item holds one species)
+                if (tid <= j && (cm & 1u)) {
+                    const int i = tid;
+                    const T h = sm.sig[0][i] * (T)sm.tot[i];
+                    sm.H[0][i * MAXM + j] = h;
+                    const T c = h * sm.sig[0][i];
+                    if (kF32) sm.coef32[0][i] = (float)c;
+                    else sm.coef[0][i] = (double)c;
                 }
+                if (tid == 0 && (cm & 1u) && A.reorth) sm.sp[0].wwb = sm.tot[j + 1];
                 __syncthreads();
                 MPM_TICK(3);
                 mypart = A.partials + pbuf * pstride + (size_t)blockIdx.x * kKMax;
@@ -939,9 +940,9 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
                     const T aa = H[j * MAXM + j], bb = hn;
                     if (bb == T(0)) { cs[j] = T(1); sn[j] = T(0); }
                     else {
-                        const T r = hypot(aa, bb);
-                        cs[j] = aa / r;
-                        sn[j] = bb / r;
+                        const T ri = T(1) / hypot(aa, bb);   // one division (FP64 divisions are long here)
+                        cs[j] = aa * ri;
+                        sn[j] = bb * ri;
                     }
                     H[j * MAXM + j] = cs[j] * aa + sn[j] * bb;
                     H[(j + 1) * MAXM + j] = T(0);
@@ -966,16 +967,24 @@ __device__ __forceinline__ void gmres_body(const SolveArgs &A, Smem<MAXM, T, NT>
                 MPM_TICK(3);
             }
 
-            // ---------------- least squares: R y = g (back substitution), coef = y * sigma
+            // ---------------- least squares: R y = g (back substitution), coef = y * sigma;
+            // the reciprocals of the diagonal first, one thread each, so the
+            // sequential substitution has no division
+            {
+                const SpState &p = sm.sp[0];
+                if (!p.bad && tid < p.k) sm.cs[0][tid] = T(1) / sm.H[0][tid * MAXM + tid];   // cs no longer needed
+            }
+            __syncthreads();
             if (tid < NS) {
                 SpState &p = sm.sp[tid];
                 if (!p.bad && p.k > 0) {
                     const T *H = sm.H[tid];
+                    const T *rd = sm.cs[tid];
                     T *y = kF32 ? (T *)sm.coef32[tid] : (T *)sm.coef[tid];
                     for (int i = p.k - 1; i >= 0; --i) {
                         T acc = sm.g[tid][i];
                         for (int l = i + 1; l < p.k; ++l) acc -= H[i * MAXM + l] * y[l];
-                        y[i] = acc / H[i * MAXM + i];
+                        y[i] = acc * rd[i];
                     }
                     bool fin = true;
                     for (int i = 0; i < p.k; ++i) {

@@ -397,15 +397,15 @@ __device__ __forceinline__ GuardBand guard_band(const ExtractArgs &A, const BoxG
 
 // Phase E: gather + rows of every stored element (4-element chunks where the
 // tiles are at least four wide and D is uniform), the neighbour table when
-// nbr, and the guard vote (one atomic per CTA).
-template <int NT>
-__device__ __forceinline__ void gather_phase(const ExtractArgs &A, const BatchSys &S, const BoxGeo &g, int64_t NE,
-                                             int b, int nb, const RowTab &tab, bool nbr)
+// nbr, and with kGuard the guard vote (one atomic per CTA).
+template <int NT, bool kGuard>
+__device__ __forceinline__ void gather_phase_t(const ExtractArgs &A, const BatchSys &S, const BoxGeo &g, int64_t NE,
+                                               int b, int nb, const RowTab &tab, bool nbr)
 {
     const int tid = threadIdx.x;
     const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
     const GuardBand gbv = guard_band(A, g);
-    const GuardBand *gb = gbv.h > 0 ? &gbv : nullptr;
+    const GuardBand *gb = kGuard ? &gbv : nullptr;
     bool hit = false;
     const bool chunks = g.lt[0] >= 2 && !S.dfac;
     const int64_t nunit = chunks ? NE >> 2 : NE;   // 4-element chunks or elements
@@ -427,9 +427,15 @@ __device__ __forceinline__ void gather_phase(const ExtractArgs &A, const BatchSy
             }
         }
     }
-    if (gb) {   // uniform over the CTA
-        if (__syncthreads_or(hit) && tid == 0) atomicOr(&A.cad->guard_hit, 1u);
-    }
+    if (kGuard && __syncthreads_or(hit) && tid == 0) atomicOr(&A.cad->guard_hit, 1u);
+}
+
+template <int NT>
+__device__ __forceinline__ void gather_phase(const ExtractArgs &A, const BatchSys &S, const BoxGeo &g, int64_t NE,
+                                             int b, int nb, const RowTab &tab, bool nbr)
+{
+    if (A.box_every > 1 && A.box_guard > 0) gather_phase_t<NT, true>(A, S, g, NE, b, nb, tab, nbr);
+    else gather_phase_t<NT, false>(A, S, g, NE, b, nb, tab, nbr);
 }
 
 // Block-wide sum over NT threads (every thread gets the total).
