@@ -5,18 +5,20 @@
 // parallel).
 //
 // Structure of a launch.  The grid is split into teams of co-resident CTAs;
-// each team solves a list of systems, every species of a system in lock step.
+// each team solves a list of work items, one (system, species) pair each.
 // A cycle is
 //   R   r = b - A x (FP64), ||r||, ||b||                       -> barrier
 //   for j = 0..m-1 (classical Gram-Schmidt in two passes):
 //     P1  w = A v_j (7-point stencil) and h_ij = <v_i, w>, i<=j -> barrier
 //     P2  w -= sum_i h_ij v_i, ||w||                           -> barrier
-//         Givens rotation of the new Hessenberg column (FP64, one thread per
-//         species, redundantly in every CTA)
+//         Givens rotation of the new Hessenberg column (in the Krylov type,
+//         redundantly in every CTA)
 //   U   x += V y (y from the triangular solve)                 -> barrier
 // and the next R pass doubles as the true-residual convergence test.  Krylov
 // vectors are stored unnormalised with a scale sigma_i = 1/||v_i||, so no
-// pass is spent on normalisation.
+// pass is spent on normalisation.  With the FP32 basis on tiles at least four
+// wide, P1, P2 and U give each thread 4-element chunks of tile rows (16-byte
+// vector loads); R and the FP64 basis keep one or two elements per thread.
 //
 // Reductions are deterministic: every CTA writes its partial sums to a
 // double-buffered slot, and after the team barrier every CTA sums the team's
