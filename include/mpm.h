@@ -249,6 +249,9 @@ mpm_status mpm_batch_step(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_latt
  *             (exports, mpm_apply_operator and mpm_solve_step work on it).
  *   tile    : as in mpm_box_extract (NULL: 4x4x4).
  *   opt     : as in mpm_solve_step; x0_given must be 0 (the step starts at c^n).
+ *             box_every / box_guard set the box cadence (default: a new box every
+ *             step); the kernel itself decides, step by step, whether to extract
+ *             or keep the box, so queued steps follow the cadence too.
  *   rep     : nullable; filled as by mpm_solve_step.
  *   out_box : nullable; the box of this step.
  * Returns MPM_ERR_EMPTY (lattice unchanged, no extraction held) when no voxel
