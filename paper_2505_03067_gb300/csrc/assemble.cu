@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs A, int64_t NE)
             double dg, b;
             assemble_row(A.C, s, f, id, ndir, A.dfac != nullptr, fp, dq, A.cn[s][e], dg, b);
             A.diag[s][e] = dg;
-            A.diag32[s][e] = (float)dg;
+            A.diag32[s][e] = f32_rz(dg);
             A.b[s][e] = b;
         }
     }

@@ -77,6 +77,36 @@ __device__ __forceinline__ void bbox_upd(uint32_t e, uint32_t Lx, uint32_t Lxy, 
 }
 
 
+// The FP32 value of x rounded toward zero, formed from its IEEE-754 bits with
+// integer operations: the FP64-to-FP32 conversion instruction shares GB300's
+// narrow FP64 pipe with the residual's arithmetic.  Magnitudes below the FP32
+// normal range give a signed zero, above it infinity; NaN stays NaN.
+__device__ __forceinline__ float f32_rz(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t sgn = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const int e = (int)ex - 896;   // FP32 biased exponent
+    uint32_t bits;
+    if (e <= 0) bits = sgn;
+    else if (e >= 255) bits = sgn | 0x7f800000u | ((ex == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+    else bits = sgn | ((uint32_t)e << 23) | m;
+    return __uint_as_float(bits);
+}
+
+// The FP64 value of an FP32 x (exact), formed from its IEEE-754 bits with
+// integer operations, for the same reason; subnormal inputs give a signed zero.
+__device__ __forceinline__ double f64_of(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t sgn = b & 0x80000000u, ex = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    uint32_t hi, lo;
+    if (ex == 0) { hi = sgn; lo = 0u; }
+    else if (ex == 0xffu) { hi = sgn | 0x7ff00000u | (m >> 3); lo = m << 29; }
+    else { hi = sgn | ((ex + 896u) << 20) | (m >> 3); lo = m << 29; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // Box from the reduced bounds (Sec. 2.3): lo = max(0, min - margin),
 // hi = min(L, max + margin + 1); tile counts of the box.  n[0] = 0 marks an
 // empty tumour set.

@@ -237,6 +237,13 @@ __device__ __forceinline__ T open_sum_var(const T *__restrict__ u, const double 
 // compiler's eyes, so this ordering is what keeps U elements' loads in flight
 // together.  Work items hold one species (s = 0).
 
+template <typename T>
+__device__ __forceinline__ T to_basis(double x);
+template <>
+__device__ __forceinline__ float to_basis<float>(double x) { return f32_rz(x); }
+template <>
+__device__ __forceinline__ double to_basis<double>(double x) { return x; }
+
 // ---- R: r = b - A x in FP64; u_0 = r (stored in T); sums of r^2 and of b^2
 // over mask rows.
 template <typename T, int U, bool VAR>
@@ -289,12 +296,12 @@ __device__ __forceinline__ void pass_residual_t(const SysDev &S, bool first, uin
             if (eu >= NE) continue;
             // r = b - diag x + off * sum_open x_Q  (two fused multiply-adds)
             const double r = var ? bv[u] - (dg[u] * xv[u] - ns[u]) : fma(S.off[0], ns[u], fma(-dg[u], xv[u], bv[u]));
-            const T rt = (T)r;
+            const T rt = to_basis<T>(r);
             ((T *)S.V[0])[eu] = rt;
             if (kF32) {
                 fR += (float)rt * (float)rt;
                 if (first && (f[u] & F_MASK)) {
-                    const float bf = (float)bv[u];
+                    const float bf = f32_rz(bv[u]);
                     fB += bf * bf;
                 }
             } else {
@@ -722,7 +729,7 @@ __device__ __forceinline__ void pass_update_rows(const SysDev &S, int k, const T
         }
         double xo[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xo[q] = xv.v[q] + (double)d[q];
+        for (int q = 0; q < 4; ++q) xo[q] = xv.v[q] + f64_of(d[q]);
         st4(x + e, xo);
     }
 }

@@ -166,7 +166,7 @@ __device__ __forceinline__ void prep_elem(const BatchSys &S, const BoxGeo &g, in
         S.x[s][e] = c;
         S.cn[s][e] = c;
         S.diag[s][e] = dg;
-        S.diag32[s][e] = (float)dg;
+        S.diag32[s][e] = f32_rz(dg);
         S.b[s][e] = bb;
     }
 }
@@ -274,7 +274,7 @@ __device__ __forceinline__ void prep_chunk(const BatchSys &S, const BoxGeo &g, u
                 dg[k] = dkv[k] + tab->aDn[s][__popc(f[k] & F_OPEN) + 2 * nd[k]];
                 bb[k] = (c + dqv[k]) + tab->wbn[s][nd[k]];
             }
-            d32[k] = (float)dg[k];
+            d32[k] = f32_rz(dg[k]);
         }
         double2 *x2 = reinterpret_cast<double2 *>(S.x[s] + e), *c2 = reinterpret_cast<double2 *>(S.cn[s] + e);
         double2 *b2 = reinterpret_cast<double2 *>(S.b[s] + e), *g2 = reinterpret_cast<double2 *>(S.diag[s] + e);
