@@ -437,6 +437,19 @@ mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *
 #define MPM_DEBUG_SOLVER_VARIANT 4
 mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
 
+/* Test hook: the FP32 Krylov path's bit-level conversions applied to n
+ * device values, with CUDA's own conversions beside them as the reference:
+ * out32[i] = in64[i] rounded toward zero to FP32 by integer operations
+ * (magnitudes below FP32's normal range, 2^-126, give a signed zero where
+ * CUDA gives a subnormal; magnitudes of 2^128 and above give infinity where
+ * CUDA's round-toward-zero gives the largest finite FP32; NaN stays NaN),
+ * ref32[i] = __double2float_rz(in64[i]); out64[i] = in32[i] widened by
+ * integer operations (FP32 subnormals give a signed zero), ref64[i] =
+ * (double)in32[i].  All device arrays of n entries; queued on `stream`.
+ * MPM_ERR_ARG for n < 0 or a null pointer. */
+mpm_status mpm_debug_convert(const double *in64, float *out32, float *ref32, const float *in32, double *out64,
+                             double *ref64, int64_t n, void *stream);
+
 /* Counters of the context: MPM_COUNTER_LAUNCHES = kernels launched so far by
  * this context (every entry point counts its own launches); with
  * MPM_DEBUG_PHASE_TIMES on, the last solve's CTA-0 nanoseconds spent in the
@@ -499,8 +512,10 @@ mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value);
  * loads the library holds it until the process exits.  All calls share it
  * and each call overwrites what it reads, so calls that overlap on the GPU
  * (on different streams or different host threads) race.  The first call on
- * a device looks up the array's device address with that device current;
- * make that first call before any stream capture.
+ * a device looks up the array's device address with that device current
+ * and keeps it; make that first call before any stream capture.  The address
+ * is not looked up again: after cudaDeviceReset on a device, do not call
+ * this entry point on that device in the same process.
  *
  * Errors: MPM_ERR_ARG (null pointer, negative margin, bad dims),
  * MPM_ERR_NOMEM (Lz > MPM_NOALLOC_MAX_SLABS: more z-slices than the fixed

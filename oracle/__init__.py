@@ -34,17 +34,22 @@ _SOURCES = ["oracle.c", "cnn_oracle.c"]
 _lib = None
 
 OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN = 0, 1, 2, 3, 4
+# -ffp-contract=off: no fused multiply-add contraction on any target
+BUILD_FLAGS = ["-O3", "-ffp-contract=off"]
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into oracle/lib/liboracle.so (plain -O2, no -march)."""
+    """Compile the C oracle into oracle/lib/liboracle.so with BUILD_FLAGS.  No
+    -march=native: the oracle must give the same results on every host it is
+    built on (an x86 build machine and the Arm host of the GPU), and a
+    target-specific build may contract a*b+c into fused multiply-adds."""
     os.makedirs(_LIBDIR, exist_ok=True)
     so = os.path.join(_LIBDIR, "liboracle.so")
     srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
     if not force and os.path.exists(so) and all(os.path.getmtime(so) >= os.path.getmtime(s) for s in srcs):
         return so
     tmp = so + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
+    subprocess.check_call(["gcc"] + BUILD_FLAGS + ["-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
     os.replace(tmp, so)
     return so
 

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/mpm.h: context and subgrid lifetime, memory
 // accounting, error plumbing.  No exception crosses the ABI; every entry
 // point returns an mpm_status and records a message on the context.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -64,6 +65,24 @@ static void free_sub_buffers(mpm_ctx *ctx, mpm_subgrid *sub)
         *caps[i] = 0;
     }
 }
+
+namespace mpm {
+// The bit-level conversions of the FP32 Krylov path, applied elementwise
+// (test hook: mpm_debug_convert).
+// CUDA's own conversions (round toward zero, and the exact widening) are
+// written beside them as the reference.
+__global__ void k_debug_convert(const double *__restrict__ in64, float *__restrict__ out32,
+                                float *__restrict__ ref32, const float *__restrict__ in32,
+                                double *__restrict__ out64, double *__restrict__ ref64, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        out32[i] = f32_rz(in64[i]);
+        ref32[i] = __double2float_rz(in64[i]);
+        out64[i] = f64_of(in32[i]);
+        ref64[i] = (double)in32[i];
+    }
+}
+}  // namespace mpm
 
 extern "C" {
 
@@ -341,6 +360,16 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value)
     default:
         return mpm_fail(ctx, MPM_ERR_ARG, "debug: unknown key");
     }
+}
+
+mpm_status mpm_debug_convert(const double *in64, float *out32, float *ref32, const float *in32, double *out64,
+                             double *ref64, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!in64 || !out32 || !ref32 || !in32 || !out64 || !ref64))) return MPM_ERR_ARG;
+    if (n == 0) return MPM_OK;
+    const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mpm::k_debug_convert<<<nb, 256, 0, (cudaStream_t)stream>>>(in64, out32, ref32, in32, out64, ref64, n);
+    return cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ERR_CUDA;
 }
 
 mpm_status mpm_counter_get(const mpm_ctx *ctx, int32_t key, int64_t *value)

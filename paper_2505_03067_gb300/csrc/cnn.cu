@@ -1,5 +1,5 @@
 // cnn.cu -- the learned warm start: a small 3D CNN trained on the GPU by the
-// library's own kernels (SURVEY-level design; the paper has no network).
+// library's own kernels (the paper has no network; this is one of the faster forms built around its solve).
 //
 // Network: six 3x3x3 convolutions with zero padding and a bias, channels
 // 9 -> 24 -> 24 -> 24 -> 24 -> 24 -> 3, erf-GELU after layers 1-5, and a

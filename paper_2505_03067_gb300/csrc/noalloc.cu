@@ -99,8 +99,12 @@ __global__ void __launch_bounds__(1024) k_slab_reduce(const int32_t *__restrict_
     }
 }
 
+// Device address of g_slab_bounds per device ordinal, looked up once.  A
+// cudaDeviceReset unloads the module that holds the array, so an address
+// cached before a reset is stale afterwards: a process that resets a device
+// must not call this entry point on that device again.
 std::mutex g_mu;
-int32_t *g_ptr[64] = {};   // device address of g_slab_bounds, per device ordinal
+int32_t *g_ptr[64] = {};
 
 }  // namespace
 
@@ -125,9 +129,19 @@ extern "C" mpm_status mpm_box_bounds_noalloc(const int32_t *cell_id, const int32
         }
         scratch = g_ptr[dev];
     }
+    // launched through cudaLaunchKernel so that each launch's own return code
+    // is checked: an error left pending by unrelated earlier work is neither
+    // consumed nor reported as this call's failure
     cudaStream_t st = (cudaStream_t)stream;
-    k_slab_bounds<<<dims[2], 256, 0, st>>>(cell_id, (uint32_t)dims[0], (uint32_t)dims[1], scratch);
-    k_slab_reduce<<<1, 1024, 0, st>>>(scratch, dims[0], dims[1], dims[2], margin, out_box);
-    if (cudaGetLastError() != cudaSuccess) return MPM_ERR_CUDA;
+    const uint32_t lx = (uint32_t)dims[0], ly = (uint32_t)dims[1];
+    const int32_t *cell = cell_id;
+    void *a1[] = {(void *)&cell, (void *)&lx, (void *)&ly, (void *)&scratch};
+    if (cudaLaunchKernel((const void *)k_slab_bounds, dim3((unsigned)dims[2]), dim3(256), a1, 0, st) != cudaSuccess)
+        return MPM_ERR_CUDA;
+    int32_t Lx = dims[0], Ly = dims[1], Lz = dims[2], mg = margin;
+    int32_t *ob = out_box;
+    void *a2[] = {(void *)&scratch, (void *)&Lx, (void *)&Ly, (void *)&Lz, (void *)&mg, (void *)&ob};
+    if (cudaLaunchKernel((const void *)k_slab_reduce, dim3(1), dim3(1024), a2, 0, st) != cudaSuccess)
+        return MPM_ERR_CUDA;
     return MPM_OK;
 }

@@ -250,13 +250,12 @@ template <typename T, int U, bool VAR>
 __device__ __forceinline__ void pass_residual_t(const SysDev &S, bool first, uint32_t e0, uint32_t es,
                                                 double &aR, double &aB)
 {
-    // FP32 path: the norms only steer the stopping test, so they accumulate in
-    // FP32 (relative accuracy ~1e-7); the residual itself is FP64.
-    constexpr bool kF32 = std::is_same<T, float>::value;
+    // The residual and both norms are FP64 on either path: squares of FP32
+    // values would underflow for fields below ~1e-19 and end the solve on a
+    // zero norm.
     const uint32_t NE = (uint32_t)S.NE;
     constexpr bool var = VAR;
     const double *x = S.x[0];
-    float fR = 0.0f, fB = 0.0f;
     // the flag bytes and the tile's neighbour entries are read-only during the
     // solve: fetch the next iteration's one iteration ahead, so the neighbour
     // loads never wait for them
@@ -296,23 +295,10 @@ __device__ __forceinline__ void pass_residual_t(const SysDev &S, bool first, uin
             if (eu >= NE) continue;
             // r = b - diag x + off * sum_open x_Q  (two fused multiply-adds)
             const double r = var ? bv[u] - (dg[u] * xv[u] - ns[u]) : fma(S.off[0], ns[u], fma(-dg[u], xv[u], bv[u]));
-            const T rt = to_basis<T>(r);
-            ((T *)S.V[0])[eu] = rt;
-            if (kF32) {
-                fR += (float)rt * (float)rt;
-                if (first && (f[u] & F_MASK)) {
-                    const float bf = f32_rz(bv[u]);
-                    fB += bf * bf;
-                }
-            } else {
-                aR += r * r;
-                if (first && (f[u] & F_MASK)) aB += bv[u] * bv[u];
-            }
+            ((T *)S.V[0])[eu] = to_basis<T>(r);
+            aR = fma(r, r, aR);
+            if (first && (f[u] & F_MASK)) aB = fma(bv[u], bv[u], aB);
         }
-    }
-    if (kF32) {
-        aR += (double)fR;
-        aB += (double)fB;
     }
 }
 

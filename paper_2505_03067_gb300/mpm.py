@@ -32,7 +32,7 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
            "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
            "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond",
-           "mpm_step_host"]
+           "mpm_step_host", "mpm_debug_convert"]
 
 
 class mpm_box(C.Structure):
@@ -147,6 +147,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_debug_set": [P, C.c_int32, C.c_int64],
         "mpm_counter_get": [P, C.c_int32, C.POINTER(C.c_int64)],
         "mpm_box_bounds_noalloc": [P, C.POINTER(C.c_int32), C.c_int32, P, P],
+        "mpm_debug_convert": [P, P, P, P, P, P, C.c_int64, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -460,11 +461,39 @@ def mpm_box_bounds_noalloc(cell_id, margin: int, out_box, stream=None) -> int:
     """Bounding box of a device int32 lattice (torch tensor of shape (Lz, Ly, Lx))
     into out_box (device int32 tensor of 7 entries), without any allocation by
     the library; returns the mpm_status."""
+    import torch
+    if not (isinstance(cell_id, torch.Tensor) and cell_id.is_cuda and cell_id.dtype == torch.int32
+            and cell_id.is_contiguous() and cell_id.dim() == 3):
+        raise ValueError("mpm_box_bounds_noalloc: cell_id must be a contiguous 3-D int32 CUDA tensor (Lz, Ly, Lx)")
+    if not (isinstance(out_box, torch.Tensor) and out_box.is_cuda and out_box.dtype == torch.int32
+            and out_box.is_contiguous() and out_box.numel() >= 7):
+        raise ValueError("mpm_box_bounds_noalloc: out_box must be a contiguous int32 CUDA tensor of >= 7 entries")
+    if cell_id.device != out_box.device:
+        raise ValueError("mpm_box_bounds_noalloc: cell_id and out_box must be on the same device")
     lib = load()
     lz, ly, lx = (int(v) for v in cell_id.shape)
     dims = (C.c_int32 * 3)(lx, ly, lz)
     return lib.mpm_box_bounds_noalloc(C.c_void_p(cell_id.data_ptr()), dims, margin,
                                       C.c_void_p(out_box.data_ptr()), _stream_ptr(stream))
+
+
+def mpm_debug_convert(in64, in32, stream=None):
+    """The FP32 Krylov path's bit-level conversions on device tensors (test
+    hook): returns (f32_rz(in64), __double2float_rz(in64), f64_of(in32),
+    (double) in32)."""
+    import torch
+    if not (in64.is_cuda and in64.dtype == torch.float64 and in64.is_contiguous() and in32.is_cuda
+            and in32.dtype == torch.float32 and in32.is_contiguous() and in32.numel() == in64.numel()):
+        raise ValueError("mpm_debug_convert: contiguous CUDA float64 and float32 tensors of equal size")
+    n = in64.numel()
+    out32, ref32 = (torch.empty(n, dtype=torch.float32, device=in64.device) for _ in range(2))
+    out64, ref64 = (torch.empty(n, dtype=torch.float64, device=in64.device) for _ in range(2))
+    ptr = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    st = load().mpm_debug_convert(ptr(in64), ptr(out32), ptr(ref32), ptr(in32), ptr(out64), ptr(ref64), n,
+                                  _stream_ptr(stream))
+    if st != OK:
+        raise MpmError(st, "mpm_debug_convert failed")
+    return out32, ref32, out64, ref64
 
 
 def mpm_solve_batch(ctx: Context, subs, opts: mpm_opts, scatter_to=None, stream=None, allow=(ERR_NOCONV,)):

@@ -209,6 +209,32 @@ def test_mixed_precision_within_1e6_of_fp64(M, ctx, seed, dims):
         assert abs(np.linalg.norm(b.reshape(-1) - A.matvec(xr)) - rep["res"][s]) <= 1e-9 * rep["bnorm"][s]
 
 
+@pytest.mark.parametrize("scale", [1e-20, 1e-30])
+@pytest.mark.parametrize("fused", [True, False])
+def test_mixed_precision_tiny_fields(M, ctx, scale, fused):
+    # every concentration, boundary value and source scaled by 1e-20 / 1e-30:
+    # the solution scales exactly (the system is linear), and the FP32 path
+    # must neither stop on an underflowed norm nor break down
+    wl = W.random_case(31, (23, 17, 13), nspecies=3)
+    wl.lattice.fields *= scale
+    wl.params.c_bc *= scale
+    wl.params.q_cell *= scale
+    ref = wl.lattice.copy()
+    oracle.step(ref, wl.params, wl.margin, rtol=1e-12)
+    lat, rep = _gpu_step(M, ctx, wl, M.make_opts(rtol=1e-6, restart=16, maxit=500, precision=1, inner_rtol=1e-5),
+                         fused=fused)
+    assert rep["status_code"] == M.OK
+    got = lat.fields_numpy()
+    box = rep["box"]
+    mb = oracle.box_view(wl.lattice.mask, box) > 0
+    for s in range(3):
+        assert 0.0 < rep["bnorm"][s] and rep["res"][s] <= 1e-6 * rep["bnorm"][s]
+        assert rep["iters"][s] > 0
+        g = oracle.box_view(got[s], box)[mb]
+        r = oracle.box_view(ref.fields[s], box)[mb]
+        assert np.linalg.norm(g - r) <= 1e-6 * np.linalg.norm(r)
+
+
 def test_deterministic(M, ctx):
     wl = W.random_case(2, (33, 17, 25), nspecies=3)
     outs = []
