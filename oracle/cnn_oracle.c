@@ -8,6 +8,13 @@
  * pred = fields + s_out * z6.  Loss: mean squared error over the in-mask
  * voxels and the 3 species.  Optimiser: Adam (Kingma & Ba 2015).
  *
+ * Activity mask: the network sees the pleural space only.  A voxel is active
+ * when its mask feature (input channel 8) is set; the input of layer 1 and
+ * the activations a_1..a_5 are zero at inactive voxels, so an inactive voxel
+ * contributes nothing to any output, as a masked (zero-flux) voxel
+ * contributes nothing to the finite-volume operator of Sec. 2.4.  With every
+ * voxel active this is the plain network.
+ *
  * Precision model of the GPU path, reproduced here: inputs, weights and the
  * activations a_1..a_5 are rounded to bfloat16 (round to nearest even) where
  * the GPU stores them; all arithmetic is FP64 (the GPU accumulates in FP32).
@@ -149,11 +156,23 @@ static int64_t woff(int l)
  * [5][V][24] activations (bf16-rounded when round_act, as on the GPU; the
  * finite-difference pins switch it off); pred: [V][3].
  */
+/* The input of layer 1: x at active voxels (mask feature set), 0 elsewhere. */
+static double *masked_input(int64_t V, const double *x)
+{
+    double *xm = (double *)malloc(sizeof(double) * (size_t)(V * 9));
+    for (int64_t v = 0; v < V; ++v) {
+        const int act = x[v * 9 + 8] > 0.5;
+        for (int c = 0; c < 9; ++c) xm[v * 9 + c] = act ? x[v * 9 + c] : 0.0;
+    }
+    return xm;
+}
+
 void orc_cnn_forward(int nx, int ny, int nz, const double *x, const double *fields, const double *params,
                      double s_out, int round_act, double *z, double *a, double *pred)
 {
     const int64_t V = (int64_t)nx * ny * nz;
-    const double *in = x;
+    double *xm = masked_input(V, x);
+    const double *in = xm;
     for (int l = 0; l < NL; ++l) {
         const int Ci = kCh[l], Co = kCh[l + 1];
         const double *W = params + woff(l);
@@ -162,10 +181,17 @@ void orc_cnn_forward(int nx, int ny, int nz, const double *x, const double *fiel
         orc_conv3(nx, ny, nz, Ci, Co, in, W, b, zl);
         if (l < NL - 1) {
             double *al = a + (int64_t)l * V * 24;
-            for (int64_t i = 0; i < V * Co; ++i) al[i] = round_act ? orc_bf16(orc_gelu(zl[i])) : orc_gelu(zl[i]);
+            for (int64_t v = 0; v < V; ++v) {
+                const int act = x[v * 9 + 8] > 0.5;
+                for (int c = 0; c < Co; ++c) {
+                    const double g = orc_gelu(zl[v * Co + c]);
+                    al[v * Co + c] = !act ? 0.0 : (round_act ? orc_bf16(g) : g);
+                }
+            }
             in = al;
         }
     }
+    free(xm);
     const double *z6 = z + (int64_t)(NL - 1) * V * 24;
     for (int64_t v = 0; v < V; ++v)
         for (int s = 0; s < 3; ++s) pred[v * 3 + s] = fields[v * 3 + s] + s_out * z6[v * 3 + s];
@@ -190,14 +216,16 @@ double orc_cnn_loss(int64_t V, const double *pred, const double *target, const u
 /*
  * Backward pass from gpred = dLoss/dpred through the stored z and a (the
  * bf16 rounding of the activations is treated as the identity, a
- * straight-through derivative, as on the GPU).  round_grad: round each
- * layer's dLoss/dz to bf16 where the GPU stores it (off for the
+ * straight-through derivative, as on the GPU).  The activity mask enters as
+ * in the forward pass: dLoss/dz_l is zero at inactive voxels.  round_grad:
+ * round each layer's dLoss/dz to bf16 where the GPU stores it (off for the
  * finite-difference pins).  Writes grads (flat, like the parameters).
  */
 void orc_cnn_backward(int nx, int ny, int nz, const double *x, const double *params, double s_out,
                       const double *z, const double *a, const double *gpred, int round_grad, double *grads)
 {
     const int64_t V = (int64_t)nx * ny * nz;
+    double *xm = masked_input(V, x);
     double *g = (double *)malloc(sizeof(double) * (size_t)(V * 24));
     double *gp = (double *)malloc(sizeof(double) * (size_t)(V * 24));
     for (int64_t v = 0; v < V; ++v)
@@ -209,16 +237,21 @@ void orc_cnn_backward(int nx, int ny, int nz, const double *x, const double *par
         const int Ci = kCh[l], Co = kCh[l + 1];
         const double *W = params + woff(l);
         double *gW = grads + woff(l);
-        const double *in = l == 0 ? x : a + (int64_t)(l - 1) * V * 24;
+        const double *in = l == 0 ? xm : a + (int64_t)(l - 1) * V * 24;
         orc_conv3_wgrad(nx, ny, nz, Ci, Co, in, g, gW, gW + 27LL * Ci * Co);
         if (l == 0) break;
         orc_conv3_dgrad(nx, ny, nz, Ci, Co, g, W, gp);                             /* dL/da_{l} */
         const double *zp = z + (int64_t)(l - 1) * V * 24;
-        for (int64_t i = 0; i < V * Ci; ++i) {                                     /* dL/dz_{l} */
-            const double gz = gp[i] * orc_gelu_grad(zp[i]);
-            g[i] = round_grad ? orc_bf16(gz) : gz;
+        for (int64_t v = 0; v < V; ++v) {                                          /* dL/dz_{l} */
+            const int act = x[v * 9 + 8] > 0.5;
+            for (int c = 0; c < Ci; ++c) {
+                const int64_t i = v * Ci + c;
+                const double gz = act ? gp[i] * orc_gelu_grad(zp[i]) : 0.0;
+                g[i] = round_grad ? orc_bf16(gz) : gz;
+            }
         }
     }
+    free(xm);
     free(g);
     free(gp);
 }

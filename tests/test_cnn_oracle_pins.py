@@ -1,8 +1,10 @@
 """Pins of the CNN reference (no GPU): convolution special cases with closed
 forms, the adjoint identities that define its input and weight gradients, the
-full backward pass against central finite differences, GELU against the erf
-formula, Adam's first step in closed form, and bfloat16 rounding against
-PyTorch's conversion."""
+full backward pass against central finite differences, the activity mask
+(inactive voxels influence nothing; all-active is the plain network), the
+bf16-stored-gradient backward against the chain rule written out, GELU
+against the erf formula, Adam's first step in closed form, and bfloat16
+rounding against PyTorch's conversion."""
 import math
 
 import numpy as np
@@ -125,3 +127,92 @@ def test_bf16_rounding():
     x = np.random.default_rng(5).normal(size=1000) * 10 ** np.random.default_rng(6).uniform(-5, 5, 1000)
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).double().numpy()
     assert np.array_equal(oracle.bf16(x), ref)
+
+
+def _masked_case(rng, shape, p_act=0.6):
+    x = rng.normal(size=shape + (9,))
+    act = rng.random(shape) < p_act
+    x[..., 8] = act
+    return x, act
+
+
+def _plain_forward(x, f, P, s_out, act):
+    """The network written out from oracle.conv3, GELU and bf16 rounding, with
+    the activity mask applied to the layer-1 input and to a_1..a_5."""
+    gelu = np.vectorize(oracle.gelu)
+    a = np.where(act[..., None], x, 0.0)
+    for l, (sw, sb, ci, co) in enumerate(oracle.cnn_param_slices()):
+        z = oracle.conv3(a, P[sw].reshape(27, ci, co), P[sb])
+        if l < 5:
+            a = np.where(act[..., None], oracle.bf16(gelu(z)), 0.0)
+    return f + s_out * z
+
+
+def test_all_active_and_masked_network_written_out():
+    rng = np.random.default_rng(7)
+    shape = (4, 3, 5)
+    P = oracle.bf16(_rand_params(rng))
+    f = rng.normal(size=shape + (3,))
+    for p_act in (1.0, 0.5):
+        x, act = _masked_case(rng, shape, p_act)
+        pred, _ = oracle.cnn_forward(x, f, P, 0.3)
+        assert np.array_equal(pred, _plain_forward(x, f, P, 0.3, act))
+
+
+def test_inactive_voxels_do_not_influence_active_outputs():
+    rng = np.random.default_rng(8)
+    shape = (5, 4, 6)
+    P = oracle.bf16(_rand_params(rng, 3.0))
+    f = rng.normal(size=shape + (3,))
+    x, act = _masked_case(rng, shape, 0.5)
+    pred, (z, a) = oracle.cnn_forward(x, f, P, 0.3)
+    x2 = x.copy()
+    x2[~act, :8] = rng.normal(size=(int((~act).sum()), 8)) * 100.0
+    f2 = f.copy()
+    f2[~act] = 7.0
+    pred2, (_, a2) = oracle.cnn_forward(x2, f2, P, 0.3)
+    assert np.array_equal(pred[act], pred2[act])
+    V = act.size
+    for l in range(5):
+        al = a[l * V * 24:(l + 1) * V * 24].reshape(shape + (24,))
+        assert np.all(al[~act] == 0.0) and np.array_equal(al, a2[l * V * 24:(l + 1) * V * 24].reshape(al.shape))
+
+
+def test_bf16_stored_gradient_backward_is_the_chain_rule():
+    """The backward pass that stores each dLoss/dz in bf16 (as the GPU does)
+    equals the chain rule written out layer by layer from the pinned pieces
+    (conv3_wgrad, conv3_dgrad, gelu_grad, bf16) with bf16 applied to every
+    stored dLoss/dz and the activity mask applied to each."""
+    rng = np.random.default_rng(9)
+    shape = (3, 4, 5)
+    V = int(np.prod(shape))
+    P = oracle.bf16(_rand_params(rng, 3.0))
+    f = rng.normal(size=shape + (3,))
+    t = rng.normal(size=shape + (3,))
+    x, act = _masked_case(rng, shape, 0.7)
+    s_out = 0.4
+    pred, (z, a) = oracle.cnn_forward(x, f, P, s_out)
+    _, gp = oracle.cnn_loss(pred, t, act.astype(np.uint8))
+    got = oracle.cnn_backward(x, P, s_out, (z, a), gp, round_grad=True)
+
+    gelu_grad = np.vectorize(oracle.gelu_grad)
+    slices = oracle.cnn_param_slices()
+    zs = [z[l * V * 24:l * V * 24 + V * slices[l][3]].reshape(shape + (slices[l][3],)) for l in range(6)]
+    acts = [a[l * V * 24:(l + 1) * V * 24].reshape(shape + (24,)) for l in range(5)]
+    want = np.zeros_like(P)
+    g = oracle.bf16(s_out * gp)                                   # dLoss/dz_6, stored in bf16
+    for l in range(5, -1, -1):
+        sw, sb, ci, co = slices[l]
+        inp = np.where(act[..., None], x, 0.0) if l == 0 else acts[l - 1]
+        gW, gb = oracle.conv3_wgrad(inp, g)
+        want[sw] = gW.reshape(-1)
+        want[sb] = gb
+        if l == 0:
+            break
+        gin = oracle.conv3_dgrad(g, P[sw].reshape(27, ci, co), ci)      # dLoss/da_l
+        g = oracle.bf16(np.where(act[..., None], gin * gelu_grad(zs[l - 1]), 0.0))
+    assert np.array_equal(got, want)
+    # and it differs from the unrounded backward by bf16-sized amounts only
+    ref = oracle.cnn_backward(x, P, s_out, (z, a), gp)
+    assert not np.array_equal(got, ref)
+    assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
