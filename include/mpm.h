@@ -341,37 +341,64 @@ mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys,
  * Learned warm start (a small 3D CNN; the paper has no network).  Six 3x3x3
  * convolutions with zero padding and biases, channels 9 -> 24 -> 24 -> 24 ->
  * 24 -> 24 -> 3, erf-GELU after layers 1-5, output pred = c^n + s_out * z6
- * (the next-step fields of 3 species).  bf16 weights and activations, FP32
- * accumulation on the tensor cores; the FP32 master parameters are flat,
- * per layer W[27][Ci][Co] (tap (dx+1) + 3(dy+1) + 9(dz+1)) followed by b[Co].
- * Features (9 channels, stored as 16 bf16 per voxel, x fastest): c^n of the 3
- * species (scaled 1, 1, 20), one-hot medium/tumour, per-cell rates (uptake of
- * species 0 and 1, source of species 2; scaled 10), mask.
+ * (the next-step fields of 3 species), with an activity mask: the network
+ * sees the pleural space of its box only (the layer-1 input and activations
+ * 1-5 are zero outside the mask or the box, as masked voxels carry no flux,
+ * Sec. 2.4).  bf16 weights and activations, FP32 accumulation on the
+ * tensor cores (tcgen05); the FP32 master parameters are flat, per layer
+ * W[27][Ci][Co] (tap (dx+1) + 3(dy+1) + 9(dz+1)) followed by b[Co].
+ * Features (9 channels): c^n of the 3 species (scaled 1, 1, 20), one-hot
+ * medium/tumour, per-cell rates (uptake of species 0 and 1, source of
+ * species 2; scaled 10), mask.
+ *
+ * A network works on up to max_images IMAGES of dims image_dims -- lattices
+ * of those dims -- each restricted to a box.  Its buffers are indexed like
+ * the lattice, so a network whose image dims are a lattice's dims applies to
+ * that lattice in place (mpm_cnn_guess, the learned mpm_step).  Device
+ * memory: about 82 bytes per image voxel for inference, 500 for training.
  */
 typedef struct mpm_cnn mpm_cnn;
-/* max_voxels: largest batch * box volume the network will see. */
-mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **cnn, int64_t max_voxels);
+#define MPM_CNN_INPUT 0     /* mpm_cnn_load_image: features of the lattice's fields (c^n) */
+#define MPM_CNN_TARGET 1    /* mpm_cnn_load_image: the lattice's fields as the training target */
+/* train: 0 inference only, 1 also training (keeps activations, gradients, Adam state).
+ * Errors: MPM_ERR_ARG (bad dims, max_images outside 1..16, more than 2^31 voxels), MPM_ERR_NOMEM. */
+mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **cnn, const int32_t image_dims[3], int32_t max_images,
+                          int32_t train);
 mpm_status mpm_cnn_destroy(mpm_ctx *ctx, mpm_cnn *cnn);
-/* Host FP32 parameters (n must equal the network's count); resets Adam. */
+/* Host FP32 parameters (n must equal the network's count); resets Adam; synchronises `stream`. */
 mpm_status mpm_cnn_set_params(mpm_ctx *ctx, mpm_cnn *cnn, const float *host_params, int64_t n, float s_out,
                               void *stream);
-/* which 0: parameters, 1: the gradient of the last mpm_cnn_train_step; to host. */
+/* which 0: parameters, 1: the gradient of the last mpm_cnn_train_step (training networks); to host. */
 mpm_status mpm_cnn_get_params(mpm_ctx *ctx, const mpm_cnn *cnn, int32_t which, float *host_out, int64_t n,
                               void *stream);
-/* Features of a box of the lattice (device): x [V][16] bf16, fields [V][3] FP32 (c^n). */
-mpm_status mpm_cnn_features(mpm_ctx *ctx, const mpm_lattice *lat, const mpm_params *prm, const mpm_box *box,
-                            void *x_bf16, float *fields, void *stream);
-/* pred [batch*V][3] FP32 = network(x) for batch crops of dims (device pointers). */
-mpm_status mpm_cnn_forward(mpm_ctx *ctx, mpm_cnn *cnn, const void *x_bf16, const float *fields, const int32_t dims[3],
-                           int32_t batch, float *pred, void *stream);
-/* Forward, masked mean-squared error against target [batch*V][3] (mask = feature 8), backward; with
- * apply = 1 one Adam step (lr; beta 0.9, 0.999; eps 1e-8).  *loss_out (nullable) gets the loss
- * (synchronises `stream`). */
-mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *cnn, const void *x_bf16, const float *fields,
-                              const float *target, const int32_t dims[3], int32_t batch, float lr, int32_t apply,
-                              double *loss_out, void *stream);
-/* Initial guess for a solve: features of sub's box from lat, the network, and the prediction
- * written into the iterate of every species on the in-mask voxels (then solve with x0_given = 1). */
+/* Image b (0 <= b < max_images) from a device lattice of the image dims on `box`:
+ * MPM_CNN_INPUT sets the image's box and loads mask, features and c^n;
+ * MPM_CNN_TARGET loads the lattice's fields as the target (training networks).
+ * Queued on `stream`. */
+mpm_status mpm_cnn_load_image(mpm_ctx *ctx, mpm_cnn *cnn, int32_t b, const mpm_lattice *lat, const mpm_params *prm,
+                              const mpm_box *box, int32_t what, void *stream);
+/* Copy of the loaded features of images 0..nimg-1 (x_bf16: [nimg][voxels][16] bf16, channels as
+ * above, 9..14 zero, 15 = 1; zero at voxels outside the mask) and their masks (device, caller-owned;
+ * only the voxels of each image's box are defined).  Queued on `stream`. */
+mpm_status mpm_cnn_export_features(mpm_ctx *ctx, const mpm_cnn *cnn, int32_t nimg, void *x_bf16, uint8_t *mask,
+                                   void *stream);
+/* Test hook (training networks): the FP32 pre-activations z of layer `layer` (1..5) of images
+ * 0..nimg-1 as the last mpm_cnn_train_step computed them, [nimg][voxels][24] into dst (device);
+ * defined at the active voxels. */
+mpm_status mpm_cnn_export_preact(mpm_ctx *ctx, const mpm_cnn *cnn, int32_t layer, int32_t nimg, float *dst,
+                                 void *stream);
+/* The network on images 0..nimg-1: pred (device, nullable) [nimg][voxels of an image][3] FP32 receives
+ * the prediction at the active voxels (others untouched).  Queued on `stream`. */
+mpm_status mpm_cnn_forward(mpm_ctx *ctx, mpm_cnn *cnn, int32_t nimg, float *pred, void *stream);
+/* Forward on images 0..nimg-1, mean squared error against their targets over the active voxels and
+ * the 3 species, backward; with apply = 1 one Adam step (lr; beta 0.9, 0.999; eps 1e-8).  *loss_out
+ * (nullable) gets the loss (synchronises `stream`).  MPM_ERR_TIMEOUT: a bounded wait in a kernel
+ * gave up (the context stays usable). */
+mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *cnn, int32_t nimg, float lr, int32_t apply, double *loss_out,
+                              void *stream);
+/* Initial guess for a solve: features of sub's box from lat (dims = the network's image dims), the
+ * network, and the prediction written into the iterate of every species on the in-mask voxels (then
+ * solve with x0_given = 1).  A non-finite prediction leaves c^n.  Queued on `stream`. */
 mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
                          const mpm_params *prm, void *stream);
 

@@ -1,317 +1,129 @@
-// cnn.cu -- the learned warm start: a small 3D CNN trained on the GPU by the
-// library's own kernels (the paper has no network; this is one of the faster forms built around its solve).
+// cnn.cu -- the learned warm start: a small 3D CNN evaluated and trained on
+// the GPU by the library's own tensor-core kernels (cnn_tc.cuh).  The paper
+// has no network; this is one of the faster forms built around its solve.
 //
 // Network: six 3x3x3 convolutions with zero padding and a bias, channels
-// 9 -> 24 -> 24 -> 24 -> 24 -> 24 -> 3, erf-GELU after layers 1-5, and a
-// residual output pred = c^n + s_out * z6 (the next-step fields).
+// 9 -> 24 -> 24 -> 24 -> 24 -> 24 -> 3, erf-GELU after layers 1-5, a residual
+// output pred = c^n + s_out * z6 (the next-step fields), and an activity
+// mask: the network sees the pleural space of its box only -- the layer-1
+// input and the activations a_1..a_5 are zero at voxels outside the mask or
+// the box, as a masked voxel contributes nothing to the finite-volume
+// operator (zero flux, Sec. 2.4).
 //
-// Storage: activations are bfloat16, channel-last ([voxel][C], x fastest,
-// crops of a batch one after the other) with C = 16 for the 9 input features
-// and C = 24 for hidden layers; pre-activations z are kept in FP32 for the
-// backward pass.  Weights live as an FP32 master vector (the layout of the
-// oracle: per layer W[27][Ci][Co] then b[Co]) plus two bf16 copies per layer:
-// the forward layout [27][Co_pad][Ci_pad] and the input-gradient layout (taps
-// flipped, channels swapped).
-//
-// Convolutions (forward and input gradient) are implicit GEMMs on the tensor
-// cores with mma.sync m16n8k16 / m16n8k8 (bf16 in, fp32 accumulate): a warp
-// owns 16 consecutive voxels of an x-row and all output channels; K runs over
-// the 27 taps times the input channels.  The weight gradient is a reduction
-// over voxels done in FP32 SIMT with per-CTA partials summed in fixed order.
+// Storage.  bf16 channel-last [voxel][C] buffers indexed like the lattice
+// (images of dims L stacked along z): C = 16 for the 9 features (channel 15
+// holds a constant 1 at active voxels: its row of the weight gradient is the
+// bias gradient; its weights are zero), 24 for hidden activations and
+// gradients, 8 for the output gradient; FP32 pre-activations for the backward
+// pass.  Parameters: an FP32 master vector in the flat layout
+// [W_1, b_1, ..., W_6, b_6], W_l[27][Ci][Co] with tap (dx+1) + 3(dy+1) +
+// 9(dz+1), and per layer a bf16 weight image for the forward convolution and
+// one for the input gradient (taps flipped, channels swapped), laid out as
+// the tensor cores read them from shared memory.
 #include <cuda_bf16.h>
 
 #include <cmath>
 #include <cstring>
 #include <vector>
 
-#include "mpm_internal.cuh"
+#include "cnn_tc.cuh"
 
 namespace mpm {
 
+using tc::CnnDom;
+using tc::Unit;
+
 constexpr int kLayers = 6;
 __host__ __device__ constexpr int chan(int l) { return l == 0 ? 9 : (l == kLayers ? 3 : 24); }
-constexpr int kInStride = 16;    // channels stored for the 9 input features
-constexpr int kHidStride = 24;   // channels stored for hidden activations
-constexpr int kOutPad = 8;       // output channels of layer 6 padded to one n-tile
+constexpr int kXC = 16;   // feature channels stored per voxel
+constexpr int kHC = 24;   // hidden channels stored per voxel
+constexpr int kGC6 = 8;   // output-gradient channels stored per voxel
 
-__host__ __device__ constexpr int in_stride(int l) { return l == 0 ? kInStride : kHidStride; }
-__host__ __device__ constexpr int out_pad(int l) { return l == kLayers - 1 ? kOutPad : kHidStride; }
+// Stored input channels and MMA N of each layer's forward convolution, and of
+// the input-gradient convolution through layer l (l >= 1).
+__host__ __device__ constexpr int fwd_ci(int l) { return l == 0 ? kXC : kHC; }
+__host__ __device__ constexpr int fwd_no(int l) { return l == kLayers - 1 ? 16 : 32; }
+__host__ __device__ constexpr int dg_ci(int l) { return l == kLayers - 1 ? kGC6 : kHC; }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z)
+__host__ __device__ constexpr int wimg_bytes(int ci, int no)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    return 9 * (3 * (ci / 8) + ((3 * (ci / 8)) & 1)) * (no / 8) * 128;
 }
 
-__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void mma1688(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0)
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(b0));
-}
-
-enum { EPI_GELU = 0, EPI_OUT = 1, EPI_DGRAD = 2 };
-
-struct ConvArgs {
-    const __nv_bfloat16 *in;    // [V][CIN]
-    int nx, ny, nz, B;
-    const __nv_bfloat16 *W;     // [27][NT*8][CIN]
-    const float *bias;          // [NT*8] or null
-    float *z_out;               // EPI_GELU: [V][NT*8]
-    __nv_bfloat16 *a_out;       // EPI_GELU: [V][NT*8]
-    const float *fields;        // EPI_OUT: [V][3]
-    float *pred;                // EPI_OUT: [V][3]
-    float s_out;
-    const float *zprev;         // EPI_DGRAD: [V][NT*8]
-    __nv_bfloat16 *g_out;       // EPI_DGRAD: [V][NT*8]
-};
-
-__device__ __forceinline__ uint32_t ld_bf2(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-// Implicit-GEMM 3x3x3 convolution, zero padding per crop.  8 warps per CTA,
-// each warp one 16-voxel x-segment; weights staged in shared memory.
-template <int CIN, int NT, int EPI>
-__global__ void __launch_bounds__(256) k_conv3(ConvArgs A)
-{
-    constexpr int CO = NT * 8;
-    extern __shared__ __align__(16) unsigned char cnn_smem[];
-    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(cnn_smem);
-    for (int i = threadIdx.x; i < 27 * CO * CIN / 2; i += blockDim.x)
-        reinterpret_cast<uint32_t *>(Ws)[i] = reinterpret_cast<const uint32_t *>(A.W)[i];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int nsx = (A.nx + 15) >> 4;
-    const long long nseg = (long long)nsx * A.ny * A.nz * A.B;
-    const long long seg = (long long)blockIdx.x * 8 + warp;
-    if (seg >= nseg) return;
-    const int sx = (int)(seg % nsx);
-    long long r = seg / nsx;
-    const int y = (int)(r % A.ny); r /= A.ny;
-    const int z = (int)(r % A.nz);
-    const int b = (int)(r / A.nz);
-    const int x0 = sx << 4;
-    float acc[NT][4];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
-    const long long crop = (long long)b * A.nz * A.ny * A.nx;
-#pragma unroll 1
-    for (int t = 0; t < 27; ++t) {
-        const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-        const int yy = y + dy, zz = z + dz;
-        const bool rowok = yy >= 0 && yy < A.ny && zz >= 0 && zz < A.nz;
-        const int xa = x0 + gid + dx, xb = x0 + gid + 8 + dx;
-        const bool va = rowok && xa >= 0 && xa < A.nx, vb = rowok && xb >= 0 && xb < A.nx;
-        const long long rowbase = crop + ((long long)zz * A.ny + yy) * A.nx;
-        const __nv_bfloat16 *pa = A.in + (rowbase + xa) * CIN;
-        const __nv_bfloat16 *pb = A.in + (rowbase + xb) * CIN;
-        const __nv_bfloat16 *wt = Ws + (size_t)t * CO * CIN;
-#pragma unroll
-        for (int c0 = 0; c0 + 16 <= CIN; c0 += 16) {
-            const uint32_t a0 = va ? ld_bf2(pa + c0 + tig * 2) : 0u;
-            const uint32_t a1 = vb ? ld_bf2(pb + c0 + tig * 2) : 0u;
-            const uint32_t a2 = va ? ld_bf2(pa + c0 + 8 + tig * 2) : 0u;
-            const uint32_t a3 = vb ? ld_bf2(pb + c0 + 8 + tig * 2) : 0u;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const __nv_bfloat16 *wr = wt + (n * 8 + gid) * CIN + c0 + tig * 2;
-                mma16816(acc[n], a0, a1, a2, a3, ld_bf2(wr), ld_bf2(wr + 8));
-            }
-        }
-        if (CIN % 16 == 8) {
-            constexpr int c0 = CIN - 8;
-            const uint32_t a0 = va ? ld_bf2(pa + c0 + tig * 2) : 0u;
-            const uint32_t a1 = vb ? ld_bf2(pb + c0 + tig * 2) : 0u;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) mma1688(acc[n], a0, a1, ld_bf2(wt + (n * 8 + gid) * CIN + c0 + tig * 2));
-        }
-    }
-    // epilogue: thread holds voxels x0+gid (acc[.][0..1]) and x0+gid+8 (acc[.][2..3]),
-    // output channels n*8 + tig*2 + {0, 1}
-    const long long obase = crop + ((long long)z * A.ny + y) * A.nx;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int xv = x0 + gid + 8 * h;
-        if (xv >= A.nx) continue;
-        const long long v = obase + xv;
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            const int co = n * 8 + tig * 2;
-            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
-            if (EPI != EPI_DGRAD && A.bias) { v0 += A.bias[co]; v1 += A.bias[co + 1]; }
-            if (EPI == EPI_GELU) {
-                *reinterpret_cast<float2 *>(A.z_out + v * CO + co) = make_float2(v0, v1);
-                *reinterpret_cast<__nv_bfloat162 *>(A.a_out + v * CO + co) = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
-            } else if (EPI == EPI_OUT) {
-                if (co < 3) A.pred[v * 3 + co] = A.fields[v * 3 + co] + A.s_out * v0;
-                if (co + 1 < 3) A.pred[v * 3 + co + 1] = A.fields[v * 3 + co + 1] + A.s_out * v1;
-            } else {
-                const float2 zp = *reinterpret_cast<const float2 *>(A.zprev + v * CO + co);
-                *reinterpret_cast<__nv_bfloat162 *>(A.g_out + v * CO + co) =
-                    __floats2bfloat162_rn(v0 * gelu_grad_f(zp.x), v1 * gelu_grad_f(zp.y));
-            }
-        }
-    }
-}
-
-// Weight and bias gradient of one layer: dW[t][ci][co] = sum_v in[v+off(t)][ci] g[v][co],
-// db[co] = sum_v g[v][co].  Row r < 27*CI is (t, ci); row 27*CI is the bias.
-// Each CTA sums its voxel chunks into partials[blockIdx][row][co].
-template <int CI, int CIS, int CO, int GS>
-__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__ in,
-                                               const __nv_bfloat16 *__restrict__ g, int nx, int ny, int nz, int B,
-                                               float *__restrict__ partials)
-{
-    constexpr int CH = 64;
-    constexpr int ROWS = 27 * CI + 1;
-    __shared__ float gs[CH][CO];
-    __shared__ int cx[CH], cy[CH], cz[CH];
-    __shared__ long long cb[CH];
-    const long long V = (long long)nx * ny * nz * B;
-    const long long nchunk = (V + CH - 1) / CH;
-    float acc[(ROWS + 255) / 256][CO];
-#pragma unroll
-    for (int k = 0; k < (ROWS + 255) / 256; ++k)
-#pragma unroll
-        for (int c = 0; c < CO; ++c) acc[k][c] = 0.0f;
-    for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < CH * CO; i += blockDim.x) {
-            const int vv = i / CO, c = i - vv * CO;
-            const long long v = ch * CH + vv;
-            gs[vv][c] = v < V ? __bfloat162float(g[v * GS + c]) : 0.0f;
-        }
-        for (int i = threadIdx.x; i < CH; i += blockDim.x) {
-            long long v = ch * CH + i;
-            if (v >= V) v = V - 1;
-            cx[i] = (int)(v % nx);
-            long long r2 = v / nx;
-            cy[i] = (int)(r2 % ny);
-            r2 /= ny;
-            cz[i] = (int)(r2 % nz);
-            cb[i] = (r2 / nz) * (long long)nx * ny * nz;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < (ROWS + 255) / 256; ++k) {
-            const int row = threadIdx.x + 256 * k;
-            if (row >= ROWS) continue;
-            if (row == 27 * CI) {
-                for (int vv = 0; vv < CH; ++vv)
-#pragma unroll
-                    for (int c = 0; c < CO; ++c) acc[k][c] += gs[vv][c];
-                continue;
-            }
-            const int t = row / CI, ci = row - t * CI;
-            const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-            for (int vv = 0; vv < CH; ++vv) {
-                const int xx = cx[vv] + dx, yy = cy[vv] + dy, zz = cz[vv] + dz;
-                if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
-                const float a = __bfloat162float(in[(cb[vv] + ((long long)zz * ny + yy) * nx + xx) * CIS + ci]);
-#pragma unroll
-                for (int c = 0; c < CO; ++c) acc[k][c] += a * gs[vv][c];
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < (ROWS + 255) / 256; ++k) {
-        const int row = threadIdx.x + 256 * k;
-        if (row >= ROWS) continue;
-        float *o = partials + ((size_t)blockIdx.x * ROWS + row) * CO;
-#pragma unroll
-        for (int c = 0; c < CO; ++c) o[c] = acc[k][c];
-    }
-}
-
-// grads[off + i] = sum over CTAs (fixed order) of partials[b][i], i < n
-__global__ void k_wgrad_reduce(const float *__restrict__ partials, int nblk, int n, float *__restrict__ grads)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * n + i];
-    grads[i] = s;
-}
-
-// bf16 forward and input-gradient weight layouts of every layer from the FP32 master.
+// ---------------------------------------------------------------- weights
 struct PrepArgs {
     const float *master;
-    __nv_bfloat16 *wf[kLayers];
-    __nv_bfloat16 *wd[kLayers];
-    float *bias[kLayers];
     long long off[kLayers];
+    unsigned char *wf[kLayers];    // forward weight images
+    unsigned char *wd[kLayers];    // input-gradient weight images (l >= 1)
+    float *bias[kLayers];          // [fwd_no(l)]
 };
+
+// Entry e (a bf16 element) of a weight image with input channels CI and N =
+// NO: core matrix cm = e / 64 at ((p * QP + q) * NG + ng), row r, column j.
+// Forward: value W[t][ci][co]; input gradient: W[26 - t][co][ci] (the tap
+// mirrored, input and output channels exchanged).
+__device__ float wimg_value(const float *W, int Ci, int Co, int CI, int NO, int e, bool dgrad)
+{
+    const int KC = CI / 8, QC = 3 * KC, QP = QC + (QC & 1), NG = NO / 8;
+    const int cm = e >> 6, w = e & 63, r = w >> 3, j = w & 7;
+    const int ng = cm % NG, rest = cm / NG;
+    const int q = rest % QP, p = rest / QP;
+    if (q >= QC) return 0.0f;
+    const int c = q / KC, kc = q % KC;
+    const int dx = c - 1, dy = p % 3 - 1, dz = p / 3 - 1;
+    const int t = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+    const int n = ng * 8 + r, k = kc * 8 + j;   // output, input channel of this convolution
+    if (!dgrad) return (k < Ci && n < Co) ? W[((long long)t * Ci + k) * Co + n] : 0.0f;
+    // input-gradient convolution of layer (Ci -> Co): its inputs are the Co channels
+    return (k < Co && n < Ci) ? W[((long long)(26 - t) * Ci + n) * Co + k] : 0.0f;
+}
 
 __global__ void k_prep_weights(PrepArgs P)
 {
     const int l = blockIdx.y;
     const int Ci = chan(l), Co = chan(l + 1);
-    const int CIS = in_stride(l), COP = out_pad(l);
     const float *W = P.master + P.off[l];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 27 * COP * CIS; i += gridDim.x * blockDim.x) {
-        const int t = i / (COP * CIS), rem = i - t * COP * CIS;
-        const int co = rem / CIS, ci = rem - co * CIS;
-        const float w = (ci < Ci && co < Co) ? W[((long long)t * Ci + ci) * Co + co] : 0.0f;
-        P.wf[l][i] = __float2bfloat16_rn(w);
-    }
-    if (l > 0) {   // input gradient: in = g_l (COP channels), out = grad of a_{l-1} (CIS channels)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 27 * CIS * COP; i += gridDim.x * blockDim.x) {
-            const int t = i / (CIS * COP), rem = i - t * CIS * COP;
-            const int o = rem / COP, c = rem - o * COP;   // o: input channel of layer l, c: its output channel
-            const int tf = 26 - t;
-            const float w = (o < Ci && c < Co) ? W[((long long)tf * Ci + o) * Co + c] : 0.0f;
-            P.wd[l][i] = __float2bfloat16_rn(w);
-        }
+    const int nf = wimg_bytes(fwd_ci(l), fwd_no(l)) / 2;
+    __nv_bfloat16 *wf = reinterpret_cast<__nv_bfloat16 *>(P.wf[l]);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x)
+        wf[e] = __float2bfloat16_rn(wimg_value(W, Ci, Co, fwd_ci(l), fwd_no(l), e, false));
+    if (l > 0) {
+        const int nd = wimg_bytes(dg_ci(l), 32) / 2;
+        __nv_bfloat16 *wd = reinterpret_cast<__nv_bfloat16 *>(P.wd[l]);
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nd; e += gridDim.x * blockDim.x)
+            wd[e] = __float2bfloat16_rn(wimg_value(W, Ci, Co, dg_ci(l), 32, e, true));
     }
     if (blockIdx.x == 0)
-        for (int c = threadIdx.x; c < COP; c += blockDim.x) P.bias[l][c] = c < Co ? W[27LL * Ci * Co + c] : 0.0f;
+        for (int c = threadIdx.x; c < fwd_no(l); c += blockDim.x) P.bias[l][c] = c < Co ? W[27LL * Ci * Co + c] : 0.0f;
 }
 
-// Masked MSE over 3 species: loss partials and g6 = s_out * dLoss/dpred
-// (bf16, 8 channels, 3..7 zero).  The mask is input feature 8.
-__global__ void k_loss(const float *__restrict__ pred, const float *__restrict__ target,
-                       const __nv_bfloat16 *__restrict__ x, long long V, float s_out,
-                       const unsigned long long *__restrict__ nmask, __nv_bfloat16 *__restrict__ g6,
-                       double *__restrict__ loss)
+// The gradient of layer l's weights and bias from the weight-gradient
+// kernel's per-CTA partial sums (summed in CTA order): row m of tap pair p
+// holds (dx copy c, channel ci) = ((c * KC + kc) * 8 + j); the bias row is
+// the ones column (CI = 24: the pad K-column; CI = 16: feature channel 15).
+__global__ void k_wgrad_reduce(const float *__restrict__ partials, int nblk, int CI, int NO, int Ci, int Co,
+                               float *__restrict__ grads)
 {
-    const double inv = *nmask > 0 ? 1.0 / (3.0 * (double)*nmask) : 0.0;
-    double part = 0.0;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-        const float m = __bfloat162float(x[v * kInStride + 8]) > 0.5f ? 1.0f : 0.0f;
-        __nv_bfloat16 out[kOutPad];
-#pragma unroll
-        for (int c = 0; c < kOutPad; ++c) out[c] = __float2bfloat16_rn(0.0f);
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const float d = m * (pred[v * 3 + s] - target[v * 3 + s]);
-            part += (double)d * d * inv;
-            out[s] = __float2bfloat16_rn((float)(s_out * 2.0 * d * inv));
+    const int KC = CI / 8;
+    const int n = 27 * Ci * Co + Co;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int p, m, co;
+        if (i < 27 * Ci * Co) {
+            const int t = i / (Ci * Co), ci = (i / Co) % Ci;
+            co = i % Co;
+            const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+            p = (dy + 1) + 3 * (dz + 1);
+            m = ((dx + 1) * KC + ci / 8) * 8 + (ci % 8);
+        } else {
+            co = i - 27 * Ci * Co;
+            p = 4;
+            m = CI == kHC ? 3 * KC * 8 : (KC + 1) * 8 + 7;
         }
-        uint4 u;
-        memcpy(&u, out, 16);
-        *reinterpret_cast<uint4 *>(g6 + v * kOutPad) = u;
+        float s = 0.0f;
+        for (int b = 0; b < nblk; ++b) s += partials[(((size_t)b * 9 + p) * 128 + m) * NO + co];
+        grads[i] = s;
     }
-    part = warp_sum(part);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
-}
-
-__global__ void k_count_mask(const __nv_bfloat16 *__restrict__ x, long long V, unsigned long long *__restrict__ n)
-{
-    unsigned c = 0;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
-        c += __bfloat162float(x[v * kInStride + 8]) > 0.5f ? 1u : 0u;
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(n, (unsigned long long)c);
 }
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
@@ -327,389 +139,339 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     }
 }
 
-// Input features of a box crop of the lattice: c^n of the species (scaled by
-// fscale), one-hot medium / tumour, the per-cell rates of the cell (uptake of
-// species 0 and 1, source of species 2; scaled by rscale) and the mask.
-struct FeatArgs {
+// ---------------------------------------------------------------- plans
+// Candidate unit ci of image mode -> unit record; false if it lies outside its image's box.
+__device__ __forceinline__ bool unit_of(const CnnDom &D, int64_t ci, Unit &u)
+{
+    const int nsx = (D.L[0] + tc::kSlabX - 1) / tc::kSlabX, nsy = (D.L[1] + tc::kSlabY - 1) / tc::kSlabY;
+    const int nzs = (D.L[2] + tc::kZSeg - 1) / tc::kZSeg;
+    const int i = (int)(ci % nsx);
+    int64_t r = ci / nsx;
+    const int j = (int)(r % nsy);
+    r /= nsy;
+    const int kz = (int)(r % nzs);
+    const int b = (int)(r / nzs);
+    u.b = b;
+    u.ox = D.lo[b][0] + i * tc::kSlabX;
+    u.oy = D.lo[b][1] + j * tc::kSlabY;
+    u.z0 = D.lo[b][2] + kz * tc::kZSeg;
+    u.nz = min(tc::kZSeg, D.n[b][2] - kz * tc::kZSeg);
+    u.pad0 = u.pad1 = u.pad2 = 0;
+    return i * tc::kSlabX < D.n[b][0] && j * tc::kSlabY < D.n[b][1] && u.nz > 0;
+}
+
+// Image mode, one warp per candidate unit: any active voxel (in the box, mask set)?
+__global__ void k_plan_flags(const __grid_constant__ CnnDom D, const uint8_t *__restrict__ mask, int64_t ncand,
+                             uint8_t *__restrict__ flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (int64_t c = w0; c < ncand; c += nw) {
+        Unit u;
+        bool any = false;
+        if (unit_of(D, c, u)) {
+            for (int i = lane; i < tc::kSlabX * tc::kSlabY * u.nz && !any; i += 32) {
+                const int x = u.ox + (i & 7), y = u.oy + ((i >> 3) & 15), z = u.z0 + (i >> 7);
+                any = tc::in_box(D, u.b, x, y, z) && mask[tc::vox_index(D, u.b, x, y, z)] != 0;
+            }
+        }
+        any = __any_sync(0xffffffffu, any);
+        if (lane == 0) flags[c] = any ? 1 : 0;
+    }
+}
+
+// Image mode, one CTA: the flagged units in candidate order (a fixed order:
+// the weight gradient's per-CTA sums depend on it); writes the domain too.
+__global__ void __launch_bounds__(1024) k_plan_compact(const __grid_constant__ CnnDom D,
+                                                       const uint8_t *__restrict__ flags, int64_t ncand,
+                                                       Unit *__restrict__ units, int32_t *__restrict__ counters,
+                                                       CnnDom *__restrict__ dom_out)
+{
+    __shared__ int s_w[32];
+    __shared__ int s_base;
+    if (threadIdx.x == 0) {
+        s_base = 0;
+        *dom_out = D;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t c0 = 0; c0 < ncand; c0 += 1024) {
+        const int64_t c = c0 + threadIdx.x;
+        const bool f = c < ncand && flags[c];
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_w[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int i = 0; i < 32; ++i) {
+            if (i < wid) off += s_w[i];
+            tot += s_w[i];
+        }
+        if (f) {
+            Unit u;
+            unit_of(D, c, u);
+            units[s_base + off + __popc(bal & ((1u << lane) - 1u))] = u;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counters[0] = s_base;
+}
+
+// Solver mode: the box of a subgrid (from device memory) on a lattice of dims
+// L; a unit is listed when a tile of the subgrid overlapping it is active (a
+// superset of the units holding an in-mask voxel, which is all the plan
+// needs).  counters[0] must be zero; the listing order does not matter (every
+// output voxel belongs to one unit).
+__global__ void k_plan_box(const BoxGeo *__restrict__ geo, const int32_t *__restrict__ tile_index, int32_t L0,
+                           int32_t L1, int32_t L2, Unit *__restrict__ units, int32_t *__restrict__ counters,
+                           CnnDom *__restrict__ dom_out)
+{
+    const BoxGeo g = *geo;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        CnnDom D;
+        memset(&D, 0, sizeof(D));
+        D.L[0] = L0;
+        D.L[1] = L1;
+        D.L[2] = L2;
+        D.B = 1;
+        for (int d = 0; d < 3; ++d) {
+            D.lo[0][d] = g.lo[d];
+            D.n[0][d] = g.n[d];
+        }
+        *dom_out = D;
+    }
+    if (g.n[0] <= 0) return;
+    const int nsx = (g.n[0] + tc::kSlabX - 1) / tc::kSlabX, nsy = (g.n[1] + tc::kSlabY - 1) / tc::kSlabY;
+    const int nzs = (g.n[2] + tc::kZSeg - 1) / tc::kZSeg;
+    const int64_t ncand = (int64_t)nsx * nsy * nzs;
+    const int lane = threadIdx.x & 31;
+    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < ncand; c0 += gridDim.x * (int64_t)blockDim.x) {
+        const int64_t c = c0 + threadIdx.x;
+        bool f = false;
+        Unit u;
+        if (c < ncand) {
+            const int i = (int)(c % nsx), j = (int)((c / nsx) % nsy), kz = (int)(c / ((int64_t)nsx * nsy));
+            const int bx0 = i * tc::kSlabX, by0 = j * tc::kSlabY, bz0 = kz * tc::kZSeg;
+            const int bx1 = min(bx0 + tc::kSlabX, g.n[0]) - 1, by1 = min(by0 + tc::kSlabY, g.n[1]) - 1,
+                      bz1 = min(bz0 + tc::kZSeg, g.n[2]) - 1;
+            for (int tz = bz0 >> g.lt[2]; tz <= (bz1 >> g.lt[2]) && !f; ++tz)
+                for (int ty = by0 >> g.lt[1]; ty <= (by1 >> g.lt[1]) && !f; ++ty)
+                    for (int tx = bx0 >> g.lt[0]; tx <= (bx1 >> g.lt[0]) && !f; ++tx)
+                        f = __ldg(tile_index + ((int64_t)tz * g.nt[1] + ty) * g.nt[0] + tx) >= 0;
+            u.b = 0;
+            u.ox = g.lo[0] + bx0;
+            u.oy = g.lo[1] + by0;
+            u.z0 = g.lo[2] + bz0;
+            u.nz = bz1 - bz0 + 1;
+            u.pad0 = u.pad1 = u.pad2 = 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(counters, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (f) units[base + __popc(bal & ((1u << lane) - 1u))] = u;
+    }
+}
+
+// ---------------------------------------------------------------- features
+// Feature channels of a voxel: c^n of the 3 species scaled (1, 1, 20), one-hot
+// medium / tumour, the cell's rates scaled 10 (uptake of species 0 and 1,
+// source of species 2), the mask, and channel 15 = 1.
+struct FeatSrc {
     const int32_t *cell;
-    const uint8_t *mask;
     const double *field[kMaxSpecies];
     int nspecies, ncell;
     const double *k_cell, *q_cell;
-    int lo[3], n[3];
-    int Lx, Ly;
-    float fscale[3], rscale;
-    __nv_bfloat16 *x;    // [V][16]
-    float *fields;       // [V][3]
 };
 
-__global__ void k_features(FeatArgs F)
+__device__ __forceinline__ void feat_store(__nv_bfloat16 *xo, const float (&f)[kXC])
 {
-    const long long V = (long long)F.n[0] * F.n[1] * F.n[2];
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(v % F.n[0]);
-        const long long r = v / F.n[0];
-        const int j = (int)(r % F.n[1]), k = (int)(r / F.n[1]);
-        const long long L = (long long)(F.lo[0] + i) + (long long)F.Lx * ((F.lo[1] + j) + (long long)F.Ly * (F.lo[2] + k));
-        int id = F.cell[L];
-        if (id < 0 || id >= F.ncell) id = 0;
-        float f[kInStride];
+    uint32_t w[8];
 #pragma unroll
-        for (int c = 0; c < kInStride; ++c) f[c] = 0.0f;
+    for (int c = 0; c < 8; ++c) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+        w[c] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    reinterpret_cast<uint4 *>(xo)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4 *>(xo)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// fld[s]: the value of species s's field channel before scaling
+__device__ __forceinline__ void features_of(const FeatSrc &F, int64_t L, const float (&fld)[3], bool with_source,
+                                            float (&f)[kXC])
+{
+    int id = F.cell[L];
+    if (id < 0 || id >= F.ncell) id = 0;
+#pragma unroll
+    for (int c = 0; c < kXC; ++c) f[c] = 0.0f;
+    f[0] = fld[0] * 1.0f;
+    f[1] = fld[1] * 1.0f;
+    f[2] = fld[2] * 20.0f;
+    f[3] = id == 0 ? 1.0f : 0.0f;
+    f[4] = id > 0 ? 1.0f : 0.0f;
+    f[5] = F.nspecies > 0 ? (float)F.k_cell[id] * 10.0f : 0.0f;
+    f[6] = F.nspecies > 1 ? (float)F.k_cell[F.ncell + id] * 10.0f : 0.0f;
+    f[7] = (with_source && F.nspecies > 2) ? (float)F.q_cell[2 * (long long)F.ncell + id] * 10.0f : 0.0f;
+    f[8] = 1.0f;
+    f[15] = 1.0f;
+}
+
+// Image mode: the box voxels of lattice F (dims = the image dims) into image b:
+// mask, features and c^n (FP32).
+__global__ void k_feat_image(FeatSrc F, const uint8_t *__restrict__ lmask, int32_t L0, int32_t L1, int32_t L2, int b,
+                             int32_t lo0, int32_t lo1, int32_t lo2, int32_t n0, int32_t n1, int32_t n2,
+                             uint8_t *__restrict__ mask, __nv_bfloat16 *__restrict__ x, float *__restrict__ f32)
+{
+    const int64_t nb = (int64_t)n0 * n1 * n2;
+    const int64_t img = (int64_t)b * L0 * L1 * L2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += gridDim.x * (int64_t)blockDim.x) {
+        const int xx = lo0 + (int)(i % n0);
+        const int64_t r = i / n0;
+        const int yy = lo1 + (int)(r % n1), zz = lo2 + (int)(r / n1);
+        const int64_t L = xx + (int64_t)L0 * (yy + (int64_t)L1 * zz);
+        const int64_t v = img + L;
+        const uint8_t m = lmask[L] != 0;
+        mask[v] = m;
+        float fld[3];
+        for (int s = 0; s < 3; ++s) fld[s] = s < F.nspecies ? (float)F.field[s][L] : 0.0f;
+        for (int s = 0; s < 3; ++s) f32[v * 3 + s] = fld[s];
+        float f[kXC];
+        features_of(F, L, fld, true, f);
+        if (!m) {
+#pragma unroll
+            for (int c = 0; c < kXC; ++c) f[c] = 0.0f;
+        }
+        feat_store(x + v * kXC, f);
+    }
+}
+
+// Image mode: the target of image b = the lattice's fields on the box (FP32).
+__global__ void k_target_image(FeatSrc F, int32_t L0, int32_t L1, int32_t L2, int b, int32_t lo0, int32_t lo1,
+                               int32_t lo2, int32_t n0, int32_t n1, int32_t n2, float *__restrict__ tgt)
+{
+    const int64_t nb = (int64_t)n0 * n1 * n2;
+    const int64_t img = (int64_t)b * L0 * L1 * L2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += gridDim.x * (int64_t)blockDim.x) {
+        const int xx = lo0 + (int)(i % n0);
+        const int64_t r = i / n0;
+        const int yy = lo1 + (int)(r % n1), zz = lo2 + (int)(r / n1);
+        const int64_t L = xx + (int64_t)L0 * (yy + (int64_t)L1 * zz);
+        for (int s = 0; s < 3; ++s) tgt[(img + L) * 3 + s] = s < F.nspecies ? (float)F.field[s][L] : 0.0f;
+    }
+}
+
+// Box coordinates (x, y, z) of a lattice voxel -> its element in the subgrid
+// (-1 when its tile is not stored).
+__device__ __forceinline__ int64_t elem_of(const BoxGeo &g, const int32_t *__restrict__ tile_index, int x, int y, int z)
+{
+    const int bx = x - g.lo[0], by = y - g.lo[1], bz = z - g.lo[2];
+    const int32_t t = __ldg(tile_index + ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) * g.nt[0] + (bx >> g.lt[0]));
+    if (t < 0) return -1;
+    const int ix = bx & ((1 << g.lt[0]) - 1), iy = by & ((1 << g.lt[1]) - 1), iz = bz & ((1 << g.lt[2]) - 1);
+    return ((int64_t)t << (g.lt[0] + g.lt[1] + g.lt[2])) + ix + ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
+}
+
+// Solver mode: features of the active voxels of every listed unit (B = 1, the
+// lattice itself).  vin == null: c^n from the lattice (the guess); otherwise
+// the field channel of species s carries vin / m (compact vector of the
+// subgrid, m = *vscale), the other fields and the source map are zero (the
+// preconditioner's homogeneous problem), and f32 receives the field channels.
+struct FeatUnits {
+    FeatSrc F;
+    const uint8_t *lmask;
+    const CnnDom *dom;
+    const Unit *units;
+    const int32_t *nunits;
+    __nv_bfloat16 *x;
+    float *f32;
+    const double *vin;
+    const double *vscale;
+    int s;
+    const BoxGeo *geo;
+    const int32_t *tile_index;
+};
+
+__global__ void k_feat_units(const __grid_constant__ FeatUnits A)
+{
+    const CnnDom &D = *A.dom;
+    const int nu = *A.nunits;
+    const double m = A.vin ? *A.vscale : 1.0;
+    for (int ui = blockIdx.x; ui < nu; ui += gridDim.x) {
+        const Unit u = A.units[ui];
+        for (int i = threadIdx.x; i < tc::kSlabX * tc::kSlabY * u.nz; i += blockDim.x) {
+            const int x = u.ox + (i & 7), y = u.oy + ((i >> 3) & 15), z = u.z0 + (i >> 7);
+            if (!tc::in_box(D, 0, x, y, z)) continue;
+            const int64_t L = tc::vox_index(D, 0, x, y, z);
+            if (!A.lmask[L]) continue;
+            float fld[3] = {0.0f, 0.0f, 0.0f};
+            if (!A.vin) {
+                for (int s = 0; s < 3; ++s) fld[s] = s < A.F.nspecies ? (float)A.F.field[s][L] : 0.0f;
+            } else {
+                if (m > 0.0) {
+                    const int64_t e = elem_of(*A.geo, A.tile_index, x, y, z);
+                    if (e >= 0) fld[A.s] = (float)(A.vin[e] / m);
+                }
+                for (int s = 0; s < 3; ++s) A.f32[L * 3 + s] = fld[s];
+            }
+            float f[kXC];
+            features_of(A.F, L, fld, A.vin == nullptr, f);
+            feat_store(A.x + L * kXC, f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- loss
+__device__ __forceinline__ bool active_image_voxel(const CnnDom &D, const uint8_t *__restrict__ mask, int64_t v,
+                                                   int64_t V)
+{
+    const int b = (int)(v / V);
+    const int64_t r = v - (int64_t)b * V;
+    const int x = (int)(r % D.L[0]), y = (int)((r / D.L[0]) % D.L[1]), z = (int)(r / ((int64_t)D.L[0] * D.L[1]));
+    return tc::in_box(D, b, x, y, z) && mask[v];
+}
+
+__global__ void k_count_active(const __grid_constant__ CnnDom D, const uint8_t *__restrict__ mask,
+                               unsigned long long *__restrict__ n)
+{
+    const int64_t V = (int64_t)D.L[0] * D.L[1] * D.L[2];
+    unsigned c = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V * D.B; v += gridDim.x * (int64_t)blockDim.x)
+        c += active_image_voxel(D, mask, v, V) ? 1u : 0u;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(n, (unsigned long long)c);
+}
+
+// Masked MSE over the active voxels and 3 species: loss and
+// g6 = s_out * dLoss/dpred (bf16, 8 channels, 3..7 zero).
+__global__ void k_loss(const __grid_constant__ CnnDom D, const uint8_t *__restrict__ mask, const float *__restrict__ pred,
+                       const float *__restrict__ target, float s_out, const unsigned long long *__restrict__ nact,
+                       __nv_bfloat16 *__restrict__ g6, double *__restrict__ loss)
+{
+    const double inv = *nact > 0 ? 1.0 / (3.0 * (double)*nact) : 0.0;
+    const int64_t V = (int64_t)D.L[0] * D.L[1] * D.L[2];
+    double part = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V * D.B; v += gridDim.x * (int64_t)blockDim.x) {
+        if (!active_image_voxel(D, mask, v, V)) continue;
+        __nv_bfloat16 out[kGC6];
+#pragma unroll
+        for (int c = 0; c < kGC6; ++c) out[c] = __float2bfloat16_rn(0.0f);
+#pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const float c = s < F.nspecies ? (float)F.field[s][L] : 0.0f;
-            F.fields[v * 3 + s] = c;
-            f[s] = c * F.fscale[s];
+            const float d = pred[v * 3 + s] - target[v * 3 + s];
+            part += (double)d * d * inv;
+            out[s] = __float2bfloat16_rn((float)(s_out * 2.0 * d * inv));
         }
-        f[3] = id == 0 ? 1.0f : 0.0f;
-        f[4] = id > 0 ? 1.0f : 0.0f;
-        f[5] = F.nspecies > 0 ? (float)F.k_cell[id] * F.rscale : 0.0f;
-        f[6] = F.nspecies > 1 ? (float)F.k_cell[F.ncell + id] * F.rscale : 0.0f;
-        f[7] = F.nspecies > 2 ? (float)F.q_cell[2 * (long long)F.ncell + id] * F.rscale : 0.0f;
-        f[8] = F.mask[L] ? 1.0f : 0.0f;
-#pragma unroll
-        for (int c = 0; c < kInStride; c += 2)
-            *reinterpret_cast<__nv_bfloat162 *>(F.x + v * kInStride + c) = __floats2bfloat162_rn(f[c], f[c + 1]);
+        uint4 u;
+        memcpy(&u, out, 16);
+        *reinterpret_cast<uint4 *>(g6 + v * kGC6) = u;
     }
+    part = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
 }
 
-}  // namespace mpm
-
-using namespace mpm;
-
-struct mpm_cnn {
-    long long maxV = 0;
-    long long nparams = 0;
-    long long off[kLayers] = {};
-    float *master = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    __nv_bfloat16 *wf[kLayers] = {}, *wd[kLayers] = {};
-    float *bias[kLayers] = {};
-    float *z[kLayers] = {};           // pre-activations [V][out_pad]
-    __nv_bfloat16 *a[kLayers] = {};   // activations (a[5] unused)
-    __nv_bfloat16 *g = nullptr, *g2 = nullptr;   // gradient ping-pong [V][24]
-    float *pred = nullptr;
-    float *partials = nullptr;
-    int nblk_w = 0;
-    unsigned long long *d_nmask = nullptr;
-    double *d_loss = nullptr;
-    __nv_bfloat16 *gx = nullptr;      // features of one box (mpm_cnn_guess)
-    float *gfields = nullptr;
-    int step = 0;
-    float s_out = 0.01f;
-    std::vector<void *> allocs;
-};
-
-static mpm_status cnn_alloc(mpm_ctx *ctx, mpm_cnn *c, void **p, size_t bytes)
-{
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return mpm_fail(ctx, MPM_ERR_NOMEM, "cnn: device allocation failed");
-    }
-    c->allocs.push_back(*p);
-    return MPM_OK;
-}
-
-template <int CIN, int NT, int EPI>
-static cudaError_t launch_conv(const ConvArgs &A, long long V, cudaStream_t st)
-{
-    const size_t smem = (size_t)27 * NT * 8 * CIN * sizeof(__nv_bfloat16);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_conv3<CIN, NT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    const long long nseg = (long long)((A.nx + 15) / 16) * A.ny * A.nz * A.B;
-    (void)V;
-    k_conv3<CIN, NT, EPI><<<(unsigned)((nseg + 7) / 8), 256, smem, st>>>(A);
-    return cudaGetLastError();
-}
-
-mpm_status mpm_import_pred_impl(mpm_ctx *ctx, mpm_subgrid *sub, const float *pred, cudaStream_t st);
-
-extern "C" mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **out, int64_t max_voxels)
-{
-    if (!ctx || !out || max_voxels < 1) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_create: bad argument");
-    mpm_cnn *c = new mpm_cnn();
-    c->maxV = max_voxels;
-    long long n = 0;
-    for (int l = 0; l < kLayers; ++l) {
-        c->off[l] = n;
-        n += 27LL * chan(l) * chan(l + 1) + chan(l + 1);
-    }
-    c->nparams = n;
-    mpm_status r = MPM_OK;
-    auto A = [&](void **p, size_t b) { if (r == MPM_OK) r = cnn_alloc(ctx, c, p, b); };
-    A((void **)&c->master, n * 4);
-    A((void **)&c->grads, n * 4);
-    A((void **)&c->m, n * 4);
-    A((void **)&c->v, n * 4);
-    for (int l = 0; l < kLayers; ++l) {
-        A((void **)&c->wf[l], 27 * out_pad(l) * in_stride(l) * 2);
-        A((void **)&c->wd[l], 27 * out_pad(l) * in_stride(l) * 2);
-        A((void **)&c->bias[l], out_pad(l) * 4);
-        A((void **)&c->z[l], (size_t)max_voxels * out_pad(l) * 4);
-        if (l < kLayers - 1) A((void **)&c->a[l], (size_t)max_voxels * kHidStride * 2);
-    }
-    A((void **)&c->g, (size_t)max_voxels * kHidStride * 2);
-    A((void **)&c->g2, (size_t)max_voxels * kHidStride * 2);
-    A((void **)&c->pred, (size_t)max_voxels * 3 * 4);
-    c->nblk_w = 2 * ctx->num_sms;
-    A((void **)&c->partials, (size_t)c->nblk_w * (27 * 24 + 1) * 24 * 4);
-    A((void **)&c->d_nmask, 256);
-    A((void **)&c->d_loss, 256);
-    A((void **)&c->gx, (size_t)max_voxels * kInStride * 2);
-    A((void **)&c->gfields, (size_t)max_voxels * 3 * 4);
-    if (r != MPM_OK) {
-        mpm_cnn_destroy(ctx, c);
-        return r;
-    }
-    cudaMemset(c->m, 0, n * 4);
-    cudaMemset(c->v, 0, n * 4);
-    *out = c;
-    return MPM_OK;
-}
-
-extern "C" mpm_status mpm_cnn_destroy(mpm_ctx *ctx, mpm_cnn *c)
-{
-    (void)ctx;
-    if (!c) return MPM_ERR_ARG;
-    for (void *p : c->allocs) cudaFree(p);
-    delete c;
-    return MPM_OK;
-}
-
-static mpm_status prep(mpm_ctx *ctx, mpm_cnn *c, cudaStream_t st)
-{
-    PrepArgs P;
-    P.master = c->master;
-    for (int l = 0; l < kLayers; ++l) {
-        P.wf[l] = c->wf[l];
-        P.wd[l] = c->wd[l];
-        P.bias[l] = c->bias[l];
-        P.off[l] = c->off[l];
-    }
-    k_prep_weights<<<dim3(16, kLayers), 256, 0, st>>>(P);
-    ctx->launches += 1;
-    MPM_CU(cudaGetLastError());
-    return MPM_OK;
-}
-
-extern "C" mpm_status mpm_cnn_set_params(mpm_ctx *ctx, mpm_cnn *c, const float *host_params, int64_t n, float s_out, void *stream)
-{
-    if (!ctx || !c || !host_params || n != c->nparams) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_set_params: bad argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    MPM_CU(cudaMemcpyAsync(c->master, host_params, n * 4, cudaMemcpyHostToDevice, st));
-    MPM_CU(cudaMemsetAsync(c->m, 0, n * 4, st));
-    MPM_CU(cudaMemsetAsync(c->v, 0, n * 4, st));
-    MPM_CU(cudaStreamSynchronize(st));
-    c->step = 0;
-    c->s_out = s_out;
-    return prep(ctx, c, st);
-}
-
-extern "C" mpm_status mpm_cnn_get_params(mpm_ctx *ctx, const mpm_cnn *c, int32_t which, float *host_out, int64_t n, void *stream)
-{
-    if (!ctx || !c || !host_out || n != c->nparams) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_get_params: bad argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    MPM_CU(cudaMemcpyAsync(host_out, which == 1 ? c->grads : c->master, n * 4, cudaMemcpyDeviceToHost, st));
-    MPM_CU(cudaStreamSynchronize(st));
-    return MPM_OK;
-}
-
-extern "C" mpm_status mpm_cnn_features(mpm_ctx *ctx, const mpm_lattice *lat, const mpm_params *prm, const mpm_box *box,
-                            void *x_bf16, float *fields, void *stream)
-{
-    if (!ctx || !lat || !prm || !box || !x_bf16 || !fields) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_features: null argument");
-    FeatArgs F;
-    memset(&F, 0, sizeof(F));
-    F.cell = lat->cell_id;
-    F.mask = lat->mask;
-    F.nspecies = prm->nspecies;
-    for (int s = 0; s < prm->nspecies && s < kMaxSpecies; ++s) F.field[s] = lat->field[s];
-    F.ncell = prm->ncell;
-    F.k_cell = prm->k_cell;
-    F.q_cell = prm->q_cell;
-    for (int d = 0; d < 3; ++d) {
-        F.lo[d] = box->lo[d];
-        F.n[d] = box->hi[d] - box->lo[d];
-        if (F.n[d] < 1 || box->lo[d] < 0 || box->hi[d] > lat->dims[d]) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_features: bad box");
-    }
-    F.Lx = lat->dims[0];
-    F.Ly = lat->dims[1];
-    F.fscale[0] = 1.0f;
-    F.fscale[1] = 1.0f;
-    F.fscale[2] = 20.0f;
-    F.rscale = 10.0f;
-    F.x = (__nv_bfloat16 *)x_bf16;
-    F.fields = fields;
-    k_features<<<ctx->num_sms * 4, 256, 0, (cudaStream_t)stream>>>(F);
-    ctx->launches += 1;
-    MPM_CU(cudaGetLastError());
-    return MPM_OK;
-}
-
-static mpm_status forward(mpm_ctx *ctx, mpm_cnn *c, const void *x, const float *fields, const int32_t dims[3], int B,
-                          float *pred, cudaStream_t st)
-{
-    const long long V = (long long)dims[0] * dims[1] * dims[2] * B;
-    if (V > c->maxV) return mpm_fail(ctx, MPM_ERR_ARG, "cnn: more voxels than the network was created for");
-    ConvArgs A;
-    memset(&A, 0, sizeof(A));
-    A.nx = dims[0]; A.ny = dims[1]; A.nz = dims[2]; A.B = B;
-    for (int l = 0; l < kLayers; ++l) {
-        A.in = l == 0 ? (const __nv_bfloat16 *)x : c->a[l - 1];
-        A.W = c->wf[l];
-        A.bias = c->bias[l];
-        cudaError_t e;
-        if (l < kLayers - 1) {
-            A.z_out = c->z[l];
-            A.a_out = c->a[l];
-            e = l == 0 ? launch_conv<16, 3, EPI_GELU>(A, V, st) : launch_conv<24, 3, EPI_GELU>(A, V, st);
-        } else {
-            A.fields = fields;
-            A.pred = pred;
-            A.s_out = c->s_out;
-            e = launch_conv<24, 1, EPI_OUT>(A, V, st);
-        }
-        ctx->launches += 1;
-        if (e != cudaSuccess) return mpm_cuda_check(ctx, e, "cnn forward conv");
-    }
-    return MPM_OK;
-}
-
-extern "C" mpm_status mpm_cnn_forward(mpm_ctx *ctx, mpm_cnn *c, const void *x_bf16, const float *fields, const int32_t dims[3],
-                           int32_t batch, float *pred, void *stream)
-{
-    if (!ctx || !c || !x_bf16 || !fields || !dims || !pred || batch < 1) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_forward: bad argument");
-    return forward(ctx, c, x_bf16, fields, dims, batch, pred, (cudaStream_t)stream);
-}
-
-template <int CI, int CIS, int CO, int GS>
-static mpm_status wgrad_layer(mpm_ctx *ctx, mpm_cnn *c, const __nv_bfloat16 *in, const __nv_bfloat16 *g,
-                              const int32_t dims[3], int B, float *grads_out, cudaStream_t st)
-{
-    k_wgrad<CI, CIS, CO, GS><<<c->nblk_w, 256, 0, st>>>(in, g, dims[0], dims[1], dims[2], B, c->partials);
-    const int n = (27 * CI + 1) * CO;
-    k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(c->partials, c->nblk_w, n, grads_out);
-    ctx->launches += 2;
-    MPM_CU(cudaGetLastError());
-    return MPM_OK;
-}
-
-// Forward, loss and the gradient of every parameter into c->grads.
-static mpm_status backward(mpm_ctx *ctx, mpm_cnn *c, const void *x, const float *fields, const float *target,
-                           const int32_t dims[3], int B, cudaStream_t st)
-{
-    mpm_status r = forward(ctx, c, x, fields, dims, B, c->pred, st);
-    if (r != MPM_OK) return r;
-    const long long V = (long long)dims[0] * dims[1] * dims[2] * B;
-    MPM_CU(cudaMemsetAsync(c->d_nmask, 0, 8, st));
-    MPM_CU(cudaMemsetAsync(c->d_loss, 0, 8, st));
-    k_count_mask<<<ctx->num_sms * 4, 256, 0, st>>>((const __nv_bfloat16 *)x, V, c->d_nmask);
-    k_loss<<<ctx->num_sms * 4, 256, 0, st>>>(c->pred, target, (const __nv_bfloat16 *)x, V, c->s_out, c->d_nmask,
-                                             c->g, c->d_loss);
-    ctx->launches += 2;
-    MPM_CU(cudaGetLastError());
-    // layer 6: g holds dL/dz6 (8 channels)
-    __nv_bfloat16 *g = c->g, *gn = c->g2;
-    for (int l = kLayers - 1; l >= 0; --l) {
-        float *gW = c->grads + c->off[l];
-        const __nv_bfloat16 *in = l == 0 ? (const __nv_bfloat16 *)x : c->a[l - 1];
-        if (l == kLayers - 1) r = wgrad_layer<24, 24, 3, 8>(ctx, c, in, g, dims, B, gW, st);
-        else if (l == 0) r = wgrad_layer<9, 16, 24, 24>(ctx, c, in, g, dims, B, gW, st);
-        else r = wgrad_layer<24, 24, 24, 24>(ctx, c, in, g, dims, B, gW, st);
-        if (r != MPM_OK) return r;
-        if (l == 0) break;
-        // dL/dz_{l-1} = conv^T(g; W_l) * gelu'(z_{l-1})
-        ConvArgs A;
-        memset(&A, 0, sizeof(A));
-        A.nx = dims[0]; A.ny = dims[1]; A.nz = dims[2]; A.B = B;
-        A.in = g;
-        A.W = c->wd[l];
-        A.zprev = c->z[l - 1];
-        A.g_out = gn;
-        cudaError_t e = l == kLayers - 1 ? launch_conv<8, 3, EPI_DGRAD>(A, V, st) : launch_conv<24, 3, EPI_DGRAD>(A, V, st);
-        ctx->launches += 1;
-        if (e != cudaSuccess) return mpm_cuda_check(ctx, e, "cnn input-gradient conv");
-        __nv_bfloat16 *t = g;
-        g = gn;
-        gn = t;
-    }
-    return MPM_OK;
-}
-
-extern "C" mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
-                         void *stream)
-{
-    if (!ctx || !c || !sub || !lat || !prm) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_guess: null argument");
-    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_guess: subgrid not extracted");
-    if (sub->nspecies > 3) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_guess: the network predicts 3 species");
-    const long long V = (long long)sub->n[0] * sub->n[1] * sub->n[2];
-    if (V > c->maxV) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_guess: box larger than the network was created for");
-    cudaStream_t st = (cudaStream_t)stream;
-    mpm_box box;
-    for (int d = 0; d < 3; ++d) { box.lo[d] = sub->lo[d]; box.hi[d] = sub->hi[d]; }
-    mpm_status r = mpm_cnn_features(ctx, lat, prm, &box, c->gx, c->gfields, stream);
-    if (r != MPM_OK) return r;
-    r = forward(ctx, c, c->gx, c->gfields, sub->n, 1, c->pred, st);
-    if (r != MPM_OK) return r;
-    return mpm_import_pred_impl(ctx, sub, c->pred, st);
-}
-
-extern "C" mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *c, const void *x_bf16, const float *fields, const float *target,
-                              const int32_t dims[3], int32_t batch, float lr, int32_t apply, double *loss_out,
-                              void *stream)
-{
-    if (!ctx || !c || !x_bf16 || !fields || !target || !dims || batch < 1)
-        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_train_step: bad argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    mpm_status r = backward(ctx, c, x_bf16, fields, target, dims, batch, st);
-    if (r != MPM_OK) return r;
-    if (apply) {
-        c->step += 1;
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float c1 = 1.0f - powf(b1, (float)c->step), c2 = 1.0f - powf(b2, (float)c->step);
-        k_adam<<<ctx->num_sms, 256, 0, st>>>(c->master, c->grads, c->m, c->v, c->nparams, lr, b1, b2, 1e-8f, c1, c2);
-        ctx->launches += 1;
-        MPM_CU(cudaGetLastError());
-        r = prep(ctx, c, st);
-        if (r != MPM_OK) return r;
-    }
-    if (loss_out) {
-        MPM_CU(cudaMemcpyAsync(ctx->h_stage, c->d_loss, 8, cudaMemcpyDeviceToHost, st));
-        MPM_CU(cudaStreamSynchronize(st));
-        *loss_out = *(double *)ctx->h_stage;
-    }
-    return MPM_OK;
-}
-
-
-// ---------------------------------------------------------------- the network as a preconditioner
-// Row a13: flexible GMRES applies z = m * net(v / m) to a vector v of one
-// species (m = max |v|, which puts v in the range the network was trained
-// on), with the other fields and the source map at zero (the homogeneous
-// problem), and keeps z on the in-mask voxels only.
-namespace mpm {
-
-struct PcArgs {
-    BoxGeo g;                      // the subgrid's box
-    const int32_t *tile_index;     // box tile -> compact tile (-1: not stored)
-    const int32_t *tile_coord;
-    const uint8_t *flags;          // compact
-    const int32_t *cell;           // lattice
-    const uint8_t *mask;           // lattice
-    const double *k_cell;
-    int nspecies, ncell, s;
-    const double *v;               // compact input
-    double *z;                     // compact output
-    const double *scale;           // device scalar m
-    __nv_bfloat16 *x;              // [V][16]
-    float *fields;                 // [V][3]
-    const float *pred;             // [V][3]
-    int64_t NE;
-};
-
+// ---------------------------------------------------------------- preconditioner helpers
 __global__ void k_pc_amax(const double *__restrict__ v, int64_t n, double *__restrict__ out)
 {
     __shared__ double sh[32];
@@ -726,100 +488,638 @@ __global__ void k_pc_amax(const double *__restrict__ v, int64_t n, double *__res
     }
 }
 
-__global__ void k_pc_features(PcArgs P)
-{
-    const BoxGeo &g = P.g;
-    const long long V = (long long)g.n[0] * g.n[1] * g.n[2];
-    const double m = *P.scale;
-    const float fscale[3] = {1.0f, 1.0f, 20.0f};
-    const int ltv = g.lt[0] + g.lt[1] + g.lt[2];
-    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < V; d += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(d % g.n[0]);
-        const long long r = d / g.n[0];
-        const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
-        const int32_t t = P.tile_index[((long long)(k >> g.lt[2]) * g.nt[1] + (j >> g.lt[1])) * g.nt[0] + (i >> g.lt[0])];
-        double val = 0.0;
-        if (t >= 0 && m > 0.0) {
-            const int ix = i & ((1 << g.lt[0]) - 1), iy = j & ((1 << g.lt[1]) - 1), iz = k & ((1 << g.lt[2]) - 1);
-            const int64_t e = ((int64_t)t << ltv) + ix + ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
-            val = P.v[e] / m;
-        }
-        const long long L = (long long)(g.lo[0] + i) + (long long)g.Lx * ((g.lo[1] + j) + (long long)g.Ly * (g.lo[2] + k));
-        int id = P.cell[L];
-        if (id < 0 || id >= P.ncell) id = 0;
-        float f[kInStride];
-#pragma unroll
-        for (int c = 0; c < kInStride; ++c) f[c] = 0.0f;
-        const float vf = (float)val;
-        for (int c = 0; c < 3; ++c) P.fields[d * 3 + c] = c == P.s ? vf : 0.0f;
-        f[P.s] = vf * fscale[P.s];
-        f[3] = id == 0 ? 1.0f : 0.0f;
-        f[4] = id > 0 ? 1.0f : 0.0f;
-        f[5] = P.nspecies > 0 ? (float)P.k_cell[id] * 10.0f : 0.0f;
-        f[6] = P.nspecies > 1 ? (float)P.k_cell[P.ncell + id] * 10.0f : 0.0f;
-        f[8] = P.mask[L] ? 1.0f : 0.0f;
-#pragma unroll
-        for (int c = 0; c < kInStride; c += 2)
-            *reinterpret_cast<__nv_bfloat162 *>(P.x + d * kInStride + c) = __floats2bfloat162_rn(f[c], f[c + 1]);
-    }
-}
+// z[e] = m * pred[s] on the in-mask stored elements of the listed units
+// (pred = v / m + s_out z6 from the network's image-mode output).
+struct PcOut {
+    const CnnDom *dom;
+    const Unit *units;
+    const int32_t *nunits;
+    const uint8_t *lmask;
+    const float *pred;            // [V][3] lattice-indexed
+    const BoxGeo *geo;
+    const int32_t *tile_index;
+    const double *vscale;
+    int s;
+    double *z;
+};
 
-__global__ void k_pc_out(PcArgs P)
+__global__ void k_pc_scatter(const __grid_constant__ PcOut P)
 {
-    const BoxGeo &g = P.g;
-    const double m = *P.scale;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.NE; e += (int64_t)gridDim.x * blockDim.x) {
-        double zv = 0.0;
-        if ((P.flags[e] & F_MASK) && m > 0.0) {
-            int bx, by, bz;
-            elem_box(e, g, P.tile_coord, bx, by, bz);
-            const int64_t d = bx + (int64_t)g.n[0] * (by + (int64_t)g.n[1] * bz);
-            zv = m * (double)P.pred[d * 3 + P.s];
+    const CnnDom &D = *P.dom;
+    const int nu = *P.nunits;
+    const double m = *P.vscale;
+    if (!(m > 0.0)) return;
+    for (int ui = blockIdx.x; ui < nu; ui += gridDim.x) {
+        const Unit u = P.units[ui];
+        for (int i = threadIdx.x; i < tc::kSlabX * tc::kSlabY * u.nz; i += blockDim.x) {
+            const int x = u.ox + (i & 7), y = u.oy + ((i >> 3) & 15), z = u.z0 + (i >> 7);
+            if (!tc::in_box(D, 0, x, y, z)) continue;
+            const int64_t L = tc::vox_index(D, 0, x, y, z);
+            if (!P.lmask[L]) continue;
+            const int64_t e = elem_of(*P.geo, P.tile_index, x, y, z);
+            if (e >= 0) P.z[e] = m * (double)P.pred[L * 3 + P.s];
         }
-        P.z[e] = zv;
     }
 }
 
 }  // namespace mpm
 
-// z = the network's preconditioner applied to v (compact FP64 vectors of
-// species s of sub); d_scale: one device double of scratch.  Stream work only.
+using namespace mpm;
+
+struct mpm_cnn {
+    int32_t L[3] = {0, 0, 0};
+    int32_t maxB = 0;
+    long long V = 0;                 // voxels per image
+    bool train = false;
+    long long nparams = 0;
+    long long off[kLayers] = {};
+    float *master = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    unsigned char *wf[kLayers] = {}, *wd[kLayers] = {};
+    float *bias[kLayers] = {};
+    __nv_bfloat16 *x = nullptr;      // [B V][16]
+    uint8_t *mask = nullptr;         // [B V] (image mode)
+    float *f32 = nullptr;            // [B V][3] c^n (image mode) / field channels (preconditioner)
+    float *target = nullptr;         // [B V][3]
+    float *pred = nullptr;           // [B V][3]
+    __nv_bfloat16 *a[kLayers - 1] = {};   // activations (inference: a[0], a[1] ping-pong)
+    float *z[kLayers - 1] = {};      // pre-activations (training)
+    __nv_bfloat16 *g = nullptr, *g2 = nullptr, *g6 = nullptr;
+    float *partials = nullptr;
+    CnnDom *dom = nullptr;
+    Unit *units = nullptr;
+    long long max_units = 0;
+    uint8_t *flags = nullptr;
+    int32_t *counters = nullptr;     // [0] listed units, [1..15] work counters
+    BoxGeo *geo = nullptr;           // host-known box (guess, preconditioner)
+    unsigned long long *nact = nullptr;
+    double *loss = nullptr;
+    int32_t *h_err = nullptr, *d_err = nullptr;   // host-mapped: a bounded wait gave up
+    CnnDom hdom;                     // image boxes as loaded
+    int step = 0;
+    float s_out = 0.01f;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+mpm_status cnn_alloc(mpm_ctx *ctx, mpm_cnn *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return mpm_fail(ctx, MPM_ERR_NOMEM, "cnn: device allocation failed");
+    }
+    c->allocs.push_back(*p);
+    return MPM_OK;
+}
+
+// One forward / input-gradient convolution over the listed units; `slot` is
+// its work counter.
+template <int CI, int NO, int EPI>
+mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t st)
+{
+    static bool attr = false;
+    constexpr int smem = tc::ConvSmem<CI, NO>::BYTES;
+    if (!attr) {
+        cudaFuncSetAttribute(tc::k_conv_tc<CI, NO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    A.dom = c->dom;
+    A.units = c->units;
+    A.nunits = c->counters;
+    A.work = c->counters + slot;
+    A.err = c->d_err;
+    A.timeout_ns = ctx->timeout_ns;
+    tc::k_conv_tc<CI, NO, EPI><<<ctx->num_sms, tc::kThreads, smem, st>>>(A);
+    ctx->launches += 1;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn convolution");
+}
+
+template <int CI, int NO>
+mpm_status wgrad(mpm_ctx *ctx, mpm_cnn *c, const __nv_bfloat16 *in, const __nv_bfloat16 *g, int gc, int l,
+                 cudaStream_t st)
+{
+    static bool attr = false;
+    constexpr int smem = tc::WgSmem<CI, NO>::BYTES;
+    if (!attr) {
+        cudaFuncSetAttribute(tc::k_wgrad_tc<CI, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    tc::WgradArgs A;
+    memset(&A, 0, sizeof(A));
+    A.in = in;
+    A.g = g;
+    A.gc = gc;
+    A.mask = c->mask;
+    A.dom = c->dom;
+    A.units = c->units;
+    A.nunits = c->counters;
+    A.partials = c->partials;
+    A.err = c->d_err;
+    A.timeout_ns = ctx->timeout_ns;
+    tc::k_wgrad_tc<CI, NO><<<ctx->num_sms, tc::kThreads, smem, st>>>(A);
+    k_wgrad_reduce<<<64, 256, 0, st>>>(c->partials, ctx->num_sms, CI, NO, chan(l), chan(l + 1), c->grads + c->off[l]);
+    ctx->launches += 2;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn weight gradient");
+}
+
+mpm_status prep(mpm_ctx *ctx, mpm_cnn *c, cudaStream_t st)
+{
+    PrepArgs P;
+    memset(&P, 0, sizeof(P));
+    P.master = c->master;
+    for (int l = 0; l < kLayers; ++l) {
+        P.off[l] = c->off[l];
+        P.wf[l] = c->wf[l];
+        P.wd[l] = c->wd[l];
+        P.bias[l] = c->bias[l];
+    }
+    k_prep_weights<<<dim3(32, kLayers), 256, 0, st>>>(P);
+    ctx->launches += 1;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn weight preparation");
+}
+
+mpm_status check_err(mpm_ctx *ctx, mpm_cnn *c)
+{
+    if (*(volatile int32_t *)c->h_err) {
+        *(volatile int32_t *)c->h_err = 0;
+        return mpm_fail(ctx, MPM_ERR_TIMEOUT, "cnn: a bounded wait in a convolution kernel gave up");
+    }
+    return MPM_OK;
+}
+
+// Image mode plan over images 0..nimg-1 (their boxes as loaded).
+mpm_status plan_images(mpm_ctx *ctx, mpm_cnn *c, int nimg, cudaStream_t st)
+{
+    CnnDom D = c->hdom;
+    D.B = nimg;
+    const long long ncand = (long long)nimg * ((c->L[0] + 7) / 8) * ((c->L[1] + 15) / 16) * ((c->L[2] + 7) / 8);
+    MPM_CU(cudaMemsetAsync(c->counters, 0, 16 * sizeof(int32_t), st));
+    k_plan_flags<<<ctx->num_sms * 4, 256, 0, st>>>(D, c->mask, ncand, c->flags);
+    k_plan_compact<<<1, 1024, 0, st>>>(D, c->flags, ncand, c->units, c->counters, c->dom);
+    ctx->launches += 2;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn plan");
+}
+
+// The six layers.  Inference (train = false): activations ping-pong in a[0],
+// a[1]; training: a[l] and z[l] kept for the backward pass.  The last layer's
+// output is described by out_args (image mode: pred / f32; solver mode: the
+// iterate).
+mpm_status forward_layers(mpm_ctx *ctx, mpm_cnn *c, const uint8_t *mask, bool train, const tc::ConvArgs &out_args,
+                          cudaStream_t st)
+{
+    for (int l = 0; l < kLayers; ++l) {
+        tc::ConvArgs A;
+        memset(&A, 0, sizeof(A));
+        A.mask = mask;
+        A.in = l == 0 ? c->x : (train ? c->a[l - 1] : c->a[(l - 1) & 1]);
+        A.wimg = c->wf[l];
+        A.bias = c->bias[l];
+        mpm_status r;
+        if (l < kLayers - 1) {
+            A.a_out = train ? c->a[l] : c->a[l & 1];
+            A.z_out = train ? c->z[l] : nullptr;
+            r = l == 0 ? conv<kXC, 32, tc::EPI_GELU>(ctx, c, A, 1 + l, st)
+                       : conv<kHC, 32, tc::EPI_GELU>(ctx, c, A, 1 + l, st);
+        } else {
+            tc::ConvArgs O = out_args;
+            O.mask = mask;
+            O.in = A.in;
+            O.wimg = A.wimg;
+            O.bias = A.bias;
+            O.s_out = c->s_out;
+            r = conv<kHC, 16, tc::EPI_OUT>(ctx, c, O, 1 + l, st);
+        }
+        if (r != MPM_OK) return r;
+    }
+    return MPM_OK;
+}
+
+FeatSrc feat_src(const mpm_lattice *lat, const mpm_params *prm)
+{
+    FeatSrc F;
+    memset(&F, 0, sizeof(F));
+    F.cell = lat->cell_id;
+    F.nspecies = prm->nspecies;
+    for (int s = 0; s < prm->nspecies && s < kMaxSpecies; ++s) F.field[s] = lat->field[s];
+    F.ncell = prm->ncell;
+    F.k_cell = prm->k_cell;
+    F.q_cell = prm->q_cell;
+    return F;
+}
+
+mpm_status solver_mode_check(mpm_ctx *ctx, mpm_cnn *c, const mpm_subgrid *sub, const mpm_lattice *lat,
+                             const mpm_params *prm, const char *who)
+{
+    if (!c || !sub || !lat || !prm) return mpm_fail(ctx, MPM_ERR_ARG, std::string(who) + ": null argument");
+    if (!sub->extracted) return mpm_fail(ctx, MPM_ERR_ARG, std::string(who) + ": subgrid not extracted");
+    for (int d = 0; d < 3; ++d)
+        if (lat->dims[d] != c->L[d])
+            return mpm_fail(ctx, MPM_ERR_ARG, std::string(who) + ": lattice dims differ from the network's image dims");
+    if (sub->nspecies > 3) return mpm_fail(ctx, MPM_ERR_ARG, std::string(who) + ": the network predicts 3 species");
+    return MPM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **out, const int32_t image_dims[3], int32_t max_images,
+                                     int32_t train)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!out || !image_dims || max_images < 1 || max_images > tc::kMaxImages || (train != 0 && train != 1))
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_create: bad argument");
+    for (int d = 0; d < 3; ++d)
+        if (image_dims[d] < 1) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_create: bad image dims");
+    const long long V = (long long)image_dims[0] * image_dims[1] * image_dims[2];
+    if (V * max_images >= (1LL << 31)) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_create: more than 2^31 voxels");
+    mpm_cnn *c = new mpm_cnn();
+    for (int d = 0; d < 3; ++d) c->L[d] = image_dims[d];
+    c->maxB = max_images;
+    c->V = V;
+    c->train = train != 0;
+    memset(&c->hdom, 0, sizeof(c->hdom));
+    for (int d = 0; d < 3; ++d) c->hdom.L[d] = image_dims[d];
+    long long n = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        c->off[l] = n;
+        n += 27LL * chan(l) * chan(l + 1) + chan(l + 1);
+    }
+    c->nparams = n;
+    const size_t VT = (size_t)V * max_images;
+    c->max_units = (long long)max_images * ((image_dims[0] + 7) / 8) * ((image_dims[1] + 15) / 16) *
+                   ((image_dims[2] + 7) / 8);
+    mpm_status r = MPM_OK;
+    auto A = [&](void **p, size_t b) {
+        if (r == MPM_OK) r = cnn_alloc(ctx, c, p, b);
+    };
+    A((void **)&c->master, n * 4);
+    A((void **)&c->grads, n * 4);
+    A((void **)&c->m, n * 4);
+    A((void **)&c->v, n * 4);
+    for (int l = 0; l < kLayers; ++l) {
+        A((void **)&c->wf[l], wimg_bytes(fwd_ci(l), fwd_no(l)));
+        if (l > 0) A((void **)&c->wd[l], wimg_bytes(dg_ci(l), 32));
+        A((void **)&c->bias[l], 32 * 4);
+    }
+    A((void **)&c->x, VT * kXC * 2);
+    A((void **)&c->mask, VT);
+    A((void **)&c->f32, VT * 3 * 4);
+    A((void **)&c->pred, VT * 3 * 4);
+    for (int l = 0; l < (c->train ? kLayers - 1 : 2); ++l) A((void **)&c->a[l], VT * kHC * 2);
+    if (c->train) {
+        for (int l = 0; l < kLayers - 1; ++l) A((void **)&c->z[l], VT * kHC * 4);
+        A((void **)&c->target, VT * 3 * 4);
+        A((void **)&c->g, VT * kHC * 2);
+        A((void **)&c->g2, VT * kHC * 2);
+        A((void **)&c->g6, VT * kGC6 * 2);
+        A((void **)&c->partials, (size_t)ctx->num_sms * 9 * 128 * 32 * 4);
+    }
+    A((void **)&c->dom, sizeof(CnnDom));
+    A((void **)&c->units, (size_t)c->max_units * sizeof(Unit));
+    A((void **)&c->flags, (size_t)c->max_units);
+    A((void **)&c->counters, 64 * sizeof(int32_t));
+    A((void **)&c->geo, 256);
+    A((void **)&c->nact, 256);
+    A((void **)&c->loss, 256);
+    if (r == MPM_OK) {
+        if (cudaHostAlloc((void **)&c->h_err, 64, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&c->d_err, c->h_err, 0) != cudaSuccess) {
+            cudaGetLastError();
+            r = mpm_fail(ctx, MPM_ERR_NOMEM, "cnn: host-mapped allocation failed");
+        } else {
+            *c->h_err = 0;
+        }
+    }
+    if (r == MPM_OK) {
+        cudaMemset(c->m, 0, n * 4);
+        cudaMemset(c->v, 0, n * 4);
+        cudaMemset(c->mask, 0, VT);
+        cudaMemset(c->counters, 0, 64 * sizeof(int32_t));
+        if (cudaDeviceSynchronize() != cudaSuccess) r = mpm_cuda_check(ctx, cudaGetLastError(), "cnn_create");
+    }
+    if (r != MPM_OK) {
+        mpm_cnn_destroy(ctx, c);
+        return r;
+    }
+    *out = c;
+    return MPM_OK;
+}
+
+extern "C" mpm_status mpm_cnn_destroy(mpm_ctx *ctx, mpm_cnn *c)
+{
+    (void)ctx;
+    if (!c) return MPM_ERR_ARG;
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    delete c;
+    return MPM_OK;
+}
+
+extern "C" mpm_status mpm_cnn_set_params(mpm_ctx *ctx, mpm_cnn *c, const float *host_params, int64_t n, float s_out,
+                                         void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !host_params || n != c->nparams) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_set_params: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    MPM_CU(cudaMemcpyAsync(c->master, host_params, n * 4, cudaMemcpyHostToDevice, st));
+    MPM_CU(cudaMemsetAsync(c->m, 0, n * 4, st));
+    MPM_CU(cudaMemsetAsync(c->v, 0, n * 4, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    c->step = 0;
+    c->s_out = s_out;
+    return prep(ctx, c, st);
+}
+
+extern "C" mpm_status mpm_cnn_get_params(mpm_ctx *ctx, const mpm_cnn *c, int32_t which, float *host_out, int64_t n,
+                                         void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !host_out || n != c->nparams || which < 0 || which > 1 || (which == 1 && !c->train))
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_get_params: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    MPM_CU(cudaMemcpyAsync(host_out, which == 1 ? c->grads : c->master, n * 4, cudaMemcpyDeviceToHost, st));
+    MPM_CU(cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+extern "C" mpm_status mpm_cnn_load_image(mpm_ctx *ctx, mpm_cnn *c, int32_t b, const mpm_lattice *lat,
+                                         const mpm_params *prm, const mpm_box *box, int32_t what, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !lat || !prm || !box || b < 0 || b >= c->maxB)
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: bad argument");
+    if (what != MPM_CNN_INPUT && what != MPM_CNN_TARGET) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: bad `what`");
+    if (what == MPM_CNN_TARGET && !c->train) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: not a training network");
+    for (int d = 0; d < 3; ++d) {
+        if (lat->dims[d] != c->L[d])
+            return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: lattice dims differ from the image dims");
+        if (box->lo[d] < 0 || box->hi[d] > lat->dims[d] || box->hi[d] <= box->lo[d])
+            return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: bad box");
+    }
+    if (!lat->cell_id || !lat->mask || prm->nspecies < 1 || prm->ncell < 1 || !prm->k_cell || !prm->q_cell)
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: null lattice array or rate table");
+    for (int s = 0; s < prm->nspecies && s < 3; ++s)
+        if (!lat->field[s]) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_load_image: null field");
+    cudaStream_t st = (cudaStream_t)stream;
+    const FeatSrc F = feat_src(lat, prm);
+    const int n0 = box->hi[0] - box->lo[0], n1 = box->hi[1] - box->lo[1], n2 = box->hi[2] - box->lo[2];
+    if (what == MPM_CNN_INPUT) {
+        for (int d = 0; d < 3; ++d) {
+            c->hdom.lo[b][d] = box->lo[d];
+            c->hdom.n[b][d] = box->hi[d] - box->lo[d];
+        }
+        k_feat_image<<<ctx->num_sms * 4, 256, 0, st>>>(F, lat->mask, c->L[0], c->L[1], c->L[2], b, box->lo[0],
+                                                        box->lo[1], box->lo[2], n0, n1, n2, c->mask, c->x, c->f32);
+    } else {
+        k_target_image<<<ctx->num_sms * 4, 256, 0, st>>>(F, c->L[0], c->L[1], c->L[2], b, box->lo[0], box->lo[1],
+                                                          box->lo[2], n0, n1, n2, c->target);
+    }
+    ctx->launches += 1;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn_load_image");
+}
+
+extern "C" mpm_status mpm_cnn_export_features(mpm_ctx *ctx, const mpm_cnn *c, int32_t nimg, void *x_bf16,
+                                              uint8_t *mask, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || nimg < 1 || nimg > c->maxB || !x_bf16 || !mask)
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_export_features: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->V * nimg;
+    MPM_CU(cudaMemcpyAsync(x_bf16, c->x, n * kXC * 2, cudaMemcpyDeviceToDevice, st));
+    MPM_CU(cudaMemcpyAsync(mask, c->mask, n, cudaMemcpyDeviceToDevice, st));
+    return MPM_OK;
+}
+
+extern "C" mpm_status mpm_cnn_export_preact(mpm_ctx *ctx, const mpm_cnn *c, int32_t layer, int32_t nimg, float *dst,
+                                            void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !c->train || layer < 1 || layer > kLayers - 1 || nimg < 1 || nimg > c->maxB || !dst)
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_export_preact: bad argument");
+    MPM_CU(cudaMemcpyAsync(dst, c->z[layer - 1], (size_t)c->V * nimg * kHC * 4, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+    return MPM_OK;
+}
+
+extern "C" mpm_status mpm_cnn_forward(mpm_ctx *ctx, mpm_cnn *c, int32_t nimg, float *pred, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || nimg < 1 || nimg > c->maxB) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_forward: bad argument");
+    mpm_status r = check_err(ctx, c);
+    if (r != MPM_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    r = plan_images(ctx, c, nimg, st);
+    if (r != MPM_OK) return r;
+    tc::ConvArgs O;
+    memset(&O, 0, sizeof(O));
+    O.f32 = c->f32;
+    O.pred = pred ? pred : c->pred;
+    return forward_layers(ctx, c, c->mask, false, O, st);
+}
+
+extern "C" mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *c, int32_t nimg, float lr, int32_t apply,
+                                         double *loss_out, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !c->train || nimg < 1 || nimg > c->maxB || (apply != 0 && apply != 1))
+        return mpm_fail(ctx, MPM_ERR_ARG, "cnn_train_step: bad argument");
+    mpm_status r = check_err(ctx, c);
+    if (r != MPM_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    r = plan_images(ctx, c, nimg, st);
+    if (r != MPM_OK) return r;
+    tc::ConvArgs O;
+    memset(&O, 0, sizeof(O));
+    O.f32 = c->f32;
+    O.pred = c->pred;
+    r = forward_layers(ctx, c, c->mask, true, O, st);
+    if (r != MPM_OK) return r;
+    CnnDom D = c->hdom;
+    D.B = nimg;
+    MPM_CU(cudaMemsetAsync(c->nact, 0, 8, st));
+    MPM_CU(cudaMemsetAsync(c->loss, 0, 8, st));
+    k_count_active<<<ctx->num_sms * 4, 256, 0, st>>>(D, c->mask, c->nact);
+    k_loss<<<ctx->num_sms * 4, 256, 0, st>>>(D, c->mask, c->pred, c->target, c->s_out, c->nact, c->g6, c->loss);
+    ctx->launches += 2;
+    MPM_CU(cudaGetLastError());
+    // backward: each layer's weight gradient from its input and dLoss/dz of
+    // its output, then dLoss/dz of the layer below through the input gradient
+    __nv_bfloat16 *g = c->g, *gn = c->g2;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const __nv_bfloat16 *in = l == 0 ? c->x : c->a[l - 1];
+        const __nv_bfloat16 *gl = l == kLayers - 1 ? c->g6 : g;
+        if (l == kLayers - 1) r = wgrad<kHC, 16>(ctx, c, in, gl, kGC6, l, st);
+        else if (l == 0) r = wgrad<kXC, 32>(ctx, c, in, gl, kHC, l, st);
+        else r = wgrad<kHC, 32>(ctx, c, in, gl, kHC, l, st);
+        if (r != MPM_OK) return r;
+        if (l == 0) break;
+        tc::ConvArgs A;
+        memset(&A, 0, sizeof(A));
+        A.mask = c->mask;
+        A.in = gl;
+        A.wimg = c->wd[l];
+        A.zprev = c->z[l - 1];
+        __nv_bfloat16 *dst = l == kLayers - 1 ? g : gn;
+        A.g_out = dst;
+        const int slot = 7 + (kLayers - 1 - l);
+        r = l == kLayers - 1 ? conv<kGC6, 32, tc::EPI_DGRAD>(ctx, c, A, slot, st)
+                             : conv<kHC, 32, tc::EPI_DGRAD>(ctx, c, A, slot, st);
+        if (r != MPM_OK) return r;
+        if (l != kLayers - 1) {
+            __nv_bfloat16 *t = g;
+            g = gn;
+            gn = t;
+        }
+    }
+    if (apply) {
+        c->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.0f - powf(b1, (float)c->step), c2 = 1.0f - powf(b2, (float)c->step);
+        k_adam<<<ctx->num_sms, 256, 0, st>>>(c->master, c->grads, c->m, c->v, c->nparams, lr, b1, b2, 1e-8f, c1, c2);
+        ctx->launches += 1;
+        MPM_CU(cudaGetLastError());
+        r = prep(ctx, c, st);
+        if (r != MPM_OK) return r;
+    }
+    if (loss_out) {
+        MPM_CU(cudaMemcpyAsync(ctx->h_stage, c->loss, 8, cudaMemcpyDeviceToHost, st));
+        MPM_CU(cudaStreamSynchronize(st));
+        *loss_out = *(double *)ctx->h_stage;
+        return check_err(ctx, c);
+    }
+    return MPM_OK;
+}
+
+// The guess of a subgrid's solve with its box in device memory (d_geo): plan
+// from the subgrid's tile activity, features from the lattice's c^n, the
+// network, and the prediction into the iterate of every species on the
+// in-mask stored elements.  Stream work only (graph-capturable).
+mpm_status mpm_cnn_enqueue_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                                 const mpm_params *prm, const BoxGeo *d_geo, cudaStream_t st)
+{
+    MPM_CU(cudaMemsetAsync(c->counters, 0, 16 * sizeof(int32_t), st));
+    k_plan_box<<<ctx->num_sms, 256, 0, st>>>(d_geo, sub->tile_index, lat->dims[0], lat->dims[1], lat->dims[2], c->units,
+                                             c->counters, c->dom);
+    FeatUnits FU;
+    memset(&FU, 0, sizeof(FU));
+    FU.F = feat_src(lat, prm);
+    FU.lmask = lat->mask;
+    FU.dom = c->dom;
+    FU.units = c->units;
+    FU.nunits = c->counters;
+    FU.x = c->x;
+    k_feat_units<<<ctx->num_sms * 2, 256, 0, st>>>(FU);
+    ctx->launches += 2;
+    MPM_CU(cudaGetLastError());
+    tc::ConvArgs O;
+    memset(&O, 0, sizeof(O));
+    for (int s = 0; s < 3 && s < prm->nspecies; ++s) {
+        O.field[s] = lat->field[s];
+        O.xs[s] = sub->x[s];
+    }
+    O.nspecies = prm->nspecies < 3 ? prm->nspecies : 3;
+    O.tile_index = sub->tile_index;
+    O.geo = d_geo;
+    return forward_layers(ctx, c, lat->mask, false, O, st);
+}
+
+mpm_status mpm_cnn_check(mpm_ctx *ctx, mpm_cnn *c, const mpm_subgrid *sub, const mpm_lattice *lat,
+                         const mpm_params *prm)
+{
+    mpm_status r = solver_mode_check(ctx, c, sub, lat, prm, "learned step");
+    if (r != MPM_OK) return r;
+    return check_err(ctx, c);
+}
+
+extern "C" mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                                    const mpm_params *prm, void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    mpm_status r = solver_mode_check(ctx, c, sub, lat, prm, "cnn_guess");
+    if (r != MPM_OK) return r;
+    r = check_err(ctx, c);
+    if (r != MPM_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const BoxGeo g = make_geo(sub, lat->dims);
+    MPM_CU(cudaMemcpyAsync(c->geo, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+    r = mpm_cnn_enqueue_guess(ctx, c, sub, lat, prm, c->geo, st);
+    if (r != MPM_OK) return r;
+    sub->x_fresh = false;
+    return MPM_OK;
+}
+
+// ---------------------------------------------------------------- the network as a preconditioner
+// Row a13: flexible GMRES applies z = m * net(v / m) to a vector v of one
+// species (m = max |v|, which puts v in the range the network was trained
+// on), with the other fields and the source map at zero (the homogeneous
+// problem), and keeps z on the in-mask voxels only.  z = d_scale-scaled
+// network output on compact FP64 vectors of species s of sub; d_scale: one
+// device double of scratch.  Stream work only.
 mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
                                 const mpm_params *prm, int s, const double *v, double *z, double *d_scale,
                                 cudaStream_t st)
 {
-    const long long V = (long long)sub->n[0] * sub->n[1] * sub->n[2];
-    if (V > c->maxV) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: box larger than the network was created for");
-    if (s < 0 || s > 2) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: the network covers species 0..2");
-    PcArgs P;
-    memset(&P, 0, sizeof(P));
-    P.g = make_geo(sub, lat->dims);
-    P.tile_index = sub->tile_index;
-    P.tile_coord = sub->tile_coord;
-    P.flags = sub->flags;
-    P.cell = lat->cell_id;
-    P.mask = lat->mask;
-    P.k_cell = prm->k_cell;
-    P.nspecies = prm->nspecies;
-    P.ncell = prm->ncell;
-    P.s = s;
-    P.v = v;
-    P.z = z;
-    P.scale = d_scale;
-    P.x = c->gx;
-    P.fields = c->gfields;
-    P.pred = c->pred;
-    P.NE = sub->NE;
-    k_pc_amax<<<1, 1024, 0, st>>>(v, sub->NE, d_scale);
-    k_pc_features<<<ctx->num_sms * 4, 256, 0, st>>>(P);
-    ctx->launches += 2;
-    MPM_CU(cudaGetLastError());
-    mpm_status r = forward(ctx, c, c->gx, c->gfields, sub->n, 1, c->pred, st);
+    mpm_status r = solver_mode_check(ctx, c, sub, lat, prm, "cnn_precond");
     if (r != MPM_OK) return r;
-    k_pc_out<<<ctx->num_sms * 4, 256, 0, st>>>(P);
-    ctx->launches += 1;
+    if (s < 0 || s > 2) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: the network covers species 0..2");
+    const BoxGeo g = make_geo(sub, lat->dims);
+    MPM_CU(cudaMemcpyAsync(c->geo, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+    MPM_CU(cudaMemsetAsync(z, 0, (size_t)(sub->NE > 0 ? sub->NE : 1) * sizeof(double), st));
+    if (sub->NE == 0) return MPM_OK;
+    k_pc_amax<<<1, 1024, 0, st>>>(v, sub->NE, d_scale);
+    MPM_CU(cudaMemsetAsync(c->counters, 0, 16 * sizeof(int32_t), st));
+    k_plan_box<<<ctx->num_sms, 256, 0, st>>>(c->geo, sub->tile_index, lat->dims[0], lat->dims[1], lat->dims[2],
+                                             c->units, c->counters, c->dom);
+    FeatUnits FU;
+    memset(&FU, 0, sizeof(FU));
+    FU.F = feat_src(lat, prm);
+    FU.lmask = lat->mask;
+    FU.dom = c->dom;
+    FU.units = c->units;
+    FU.nunits = c->counters;
+    FU.x = c->x;
+    FU.f32 = c->f32;
+    FU.vin = v;
+    FU.vscale = d_scale;
+    FU.s = s;
+    FU.geo = c->geo;
+    FU.tile_index = sub->tile_index;
+    k_feat_units<<<ctx->num_sms * 2, 256, 0, st>>>(FU);
+    ctx->launches += 3;
     MPM_CU(cudaGetLastError());
-    return MPM_OK;
+    // image-mode output (pred = field channels + s_out z6) on the lattice-indexed buffer
+    tc::ConvArgs O;
+    memset(&O, 0, sizeof(O));
+    O.pred = c->pred;
+    O.f32 = c->f32;
+    r = forward_layers(ctx, c, lat->mask, false, O, st);
+    if (r != MPM_OK) return r;
+    PcOut P;
+    P.dom = c->dom;
+    P.units = c->units;
+    P.nunits = c->counters;
+    P.lmask = lat->mask;
+    P.pred = c->pred;
+    P.geo = c->geo;
+    P.tile_index = sub->tile_index;
+    P.vscale = d_scale;
+    P.s = s;
+    P.z = z;
+    k_pc_scatter<<<ctx->num_sms * 2, 256, 0, st>>>(P);
+    ctx->launches += 1;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn preconditioner output");
 }
 
 mpm_status mpm_dense_to_elems(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, double *dst, cudaStream_t st);

@@ -33,13 +33,9 @@ def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, l
     A fraction homogeneous_frac of the trajectories are homogeneous problems
     (zero sources and boundary values), whose pairs (v, A^-1 v) teach the
     network the map it applies as the FGMRES preconditioner."""
-    import torch
     rng = np.random.default_rng(seed)
-    V = n ** 3
-    cnn = mpm.CNN(ctx, batch * V, mpm.cnn_init_params(seed) if params is None else params, s_out=0.01)
-    x = torch.empty((batch * V, 16), dtype=torch.bfloat16, device="cuda")
-    f = torch.empty((batch * V, 3), dtype=torch.float32, device="cuda")
-    tgt = torch.empty((batch * V, 3), dtype=torch.float32, device="cuda")
+    cnn = mpm.CNN(ctx, (n, n, n), batch, mpm.cnn_init_params(seed) if params is None else params, s_out=0.01,
+                  train=True)
     trajs = [_Traj(ctx, rng, n, homogeneous_frac) for _ in range(batch)]
     opts = mpm.make_opts(rtol=1e-10, restart=16, maxit=500)
     box = ((0, 0, 0), (n, n, n))
@@ -51,16 +47,13 @@ def train(ctx: mpm.Context, samples: int = 20000, batch: int = 8, n: int = 32, l
             if tr.age >= traj_len:
                 tr.solver.sub.destroy()
                 trajs[b] = tr = _Traj(ctx, rng, n, homogeneous_frac)
-            xb, fb = cnn.features(tr.lat, tr.prm, box)
-            x[b * V:(b + 1) * V] = xb
-            f[b * V:(b + 1) * V] = fb
+            cnn.load_image(b, tr.lat, tr.prm, box, mpm.CNN_INPUT)
             tr.solver.step(opts)
-            _, fa = cnn.features(tr.lat, tr.prm, box)
-            tgt[b * V:(b + 1) * V] = fa
+            cnn.load_image(b, tr.lat, tr.prm, box, mpm.CNN_TARGET)
             tr.age += 1
         # cosine decay of the learning rate
         lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * it / nsteps))
-        loss = cnn.train_step(x, f, tgt, (n, n, n), batch, lr_t)
+        loss = cnn.train_step(batch, lr_t)
         hist.append(loss)
         if log_every and it % log_every == 0:
             print(f"step {it}/{nsteps} loss {loss:.3e} ({time.time() - t0:.1f} s)", flush=True)

@@ -20,6 +20,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_EMPTY", "ERR_NOCONV", "ERR_BREAKDOWN", "ER
 EXPORT_X, EXPORT_RHS, EXPORT_DIAG, EXPORT_FLAGS, EXPORT_CELL = range(5)
 DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK, DEBUG_PHASE_TIMES, DEBUG_SOLVER_VARIANT = 1, 2, 3, 4
 COUNTER_STEP_FULL_EXTRACTIONS = 19
+CNN_INPUT, CNN_TARGET = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmpm.so")
@@ -30,7 +31,7 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
-           "mpm_cnn_get_params", "mpm_cnn_features", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
+           "mpm_cnn_get_params", "mpm_cnn_load_image", "mpm_cnn_export_features", "mpm_cnn_export_preact", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
            "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond",
            "mpm_step_host", "mpm_debug_convert"]
 
@@ -113,14 +114,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                             C.POINTER(mpm_box), P, P],
         "mpm_assemble_coeffs": [P, P, C.POINTER(mpm_params), P],
         "mpm_subgrid_refresh": [P, P, C.POINTER(mpm_lattice), P],
-        "mpm_cnn_create": [P, C.POINTER(P), C.c_int64],
+        "mpm_cnn_create": [P, C.POINTER(P), C.POINTER(C.c_int32), C.c_int32, C.c_int32],
         "mpm_cnn_destroy": [P, P],
         "mpm_cnn_set_params": [P, P, P, C.c_int64, C.c_float, P],
         "mpm_cnn_get_params": [P, P, C.c_int32, P, C.c_int64, P],
-        "mpm_cnn_features": [P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_box), P, P, P],
-        "mpm_cnn_forward": [P, P, P, P, C.POINTER(C.c_int32), C.c_int32, P, P],
-        "mpm_cnn_train_step": [P, P, P, P, P, C.POINTER(C.c_int32), C.c_int32, C.c_float, C.c_int32,
-                               C.POINTER(C.c_double), P],
+        "mpm_cnn_load_image": [P, P, C.c_int32, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_box),
+                               C.c_int32, P],
+        "mpm_cnn_forward": [P, P, C.c_int32, P, P],
+        "mpm_cnn_export_features": [P, P, C.c_int32, P, P, P],
+        "mpm_cnn_export_preact": [P, P, C.c_int32, C.c_int32, P, P],
+        "mpm_cnn_train_step": [P, P, C.c_int32, C.c_float, C.c_int32, C.POINTER(C.c_double), P],
         "mpm_cnn_guess": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), P],
         "mpm_solve_fgmres_cnn": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_lattice),
                                  C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
@@ -608,12 +611,20 @@ def cnn_init_params(seed: int = 0, last_scale: float = 0.1):
 
 
 class CNN:
-    """The learned warm start's network (mpm_cnn_*); tensors are torch CUDA tensors."""
+    """The learned warm start's network (mpm_cnn_*) on up to max_images images
+    of dims image_dims = (Lx, Ly, Lz); tensors are torch CUDA tensors."""
 
-    def __init__(self, ctx: Context, max_voxels: int, params=None, s_out: float = 0.01):
+    def __init__(self, ctx: Context, image_dims, max_images: int = 1, params=None, s_out: float = 0.01,
+                 train: bool = False):
         self.ctx = ctx
         self.h = C.c_void_p()
-        ctx._check(ctx.lib.mpm_cnn_create(ctx.ptr, C.byref(self.h), int(max_voxels)), "mpm_cnn_create")
+        self.dims = tuple(int(v) for v in image_dims)
+        self.V = self.dims[0] * self.dims[1] * self.dims[2]
+        self.max_images = int(max_images)
+        self.train = bool(train)
+        d = (C.c_int32 * 3)(*self.dims)
+        ctx._check(ctx.lib.mpm_cnn_create(ctx.ptr, C.byref(self.h), d, self.max_images, int(bool(train))),
+                   "mpm_cnn_create")
         self.set_params(cnn_init_params() if params is None else params, s_out)
 
     def close(self):
@@ -633,39 +644,50 @@ class CNN:
                                                         out.size, _stream_ptr(stream)), "mpm_cnn_get_params")
         return out
 
-    def features(self, lat: DeviceLattice, prm: DeviceParams, box, stream=None):
-        import torch
+    def load_image(self, b: int, lat: DeviceLattice, prm: DeviceParams, box, what: int = 0, stream=None):
+        """Image b from lattice `lat` on box ((lo), (hi)): what = CNN_INPUT
+        (features of its fields) or CNN_TARGET (its fields as the target)."""
         (lo, hi) = box
-        n = [h - l for l, h in zip(lo, hi)]
-        V = n[0] * n[1] * n[2]
-        x = torch.empty((V, 16), dtype=torch.bfloat16, device="cuda")
-        f = torch.empty((V, 3), dtype=torch.float32, device="cuda")
-        b = mpm_box()
-        b.lo[:] = lo
-        b.hi[:] = hi
+        bx = mpm_box()
+        bx.lo[:] = [int(v) for v in lo]
+        bx.hi[:] = [int(v) for v in hi]
         ls = lat.struct()
-        self.ctx._check(self.ctx.lib.mpm_cnn_features(self.ctx.ptr, C.byref(ls), C.byref(prm.struct), C.byref(b),
-                                                      C.c_void_p(x.data_ptr()), C.c_void_p(f.data_ptr()),
-                                                      _stream_ptr(stream)), "mpm_cnn_features")
-        return x, f
+        self.ctx._check(self.ctx.lib.mpm_cnn_load_image(self.ctx.ptr, self.h, int(b), C.byref(ls),
+                                                        C.byref(prm.struct), C.byref(bx), int(what),
+                                                        _stream_ptr(stream)), "mpm_cnn_load_image")
 
-    def forward(self, x, fields, dims, batch: int = 1, stream=None):
+    def export_features(self, nimg: int = 1, stream=None):
+        """(x [nimg * voxels][16] bf16, mask [nimg * voxels] uint8) as loaded."""
         import torch
-        pred = torch.empty((x.shape[0], 3), dtype=torch.float32, device="cuda")
-        d = (C.c_int32 * 3)(*dims)
-        self.ctx._check(self.ctx.lib.mpm_cnn_forward(self.ctx.ptr, self.h, C.c_void_p(x.data_ptr()),
-                                                     C.c_void_p(fields.data_ptr()), d, batch,
-                                                     C.c_void_p(pred.data_ptr()), _stream_ptr(stream)),
-                        "mpm_cnn_forward")
+        x = torch.zeros((nimg * self.V, 16), dtype=torch.bfloat16, device="cuda")
+        m = torch.zeros(nimg * self.V, dtype=torch.uint8, device="cuda")
+        self.ctx._check(self.ctx.lib.mpm_cnn_export_features(self.ctx.ptr, self.h, int(nimg), C.c_void_p(x.data_ptr()),
+                                                             C.c_void_p(m.data_ptr()), _stream_ptr(stream)),
+                        "mpm_cnn_export_features")
+        return x, m
+
+    def export_preact(self, layer: int, nimg: int = 1, stream=None):
+        """FP32 pre-activations of `layer` (1..5) from the last train_step, [nimg * voxels][24]."""
+        import torch
+        z = torch.zeros((nimg * self.V, 24), dtype=torch.float32, device="cuda")
+        self.ctx._check(self.ctx.lib.mpm_cnn_export_preact(self.ctx.ptr, self.h, int(layer), int(nimg),
+                                                           C.c_void_p(z.data_ptr()), _stream_ptr(stream)),
+                        "mpm_cnn_export_preact")
+        return z
+
+    def forward(self, nimg: int = 1, pred=None, stream=None):
+        """pred [nimg * image voxels][3] FP32 (written at the active voxels)."""
+        import torch
+        if pred is None:
+            pred = torch.zeros((nimg * self.V, 3), dtype=torch.float32, device="cuda")
+        self.ctx._check(self.ctx.lib.mpm_cnn_forward(self.ctx.ptr, self.h, int(nimg), C.c_void_p(pred.data_ptr()),
+                                                     _stream_ptr(stream)), "mpm_cnn_forward")
         return pred
 
-    def train_step(self, x, fields, target, dims, batch: int, lr: float, apply: bool = True, stream=None) -> float:
-        d = (C.c_int32 * 3)(*dims)
+    def train_step(self, nimg: int, lr: float, apply: bool = True, stream=None) -> float:
         loss = C.c_double(0)
-        self.ctx._check(self.ctx.lib.mpm_cnn_train_step(self.ctx.ptr, self.h, C.c_void_p(x.data_ptr()),
-                                                        C.c_void_p(fields.data_ptr()), C.c_void_p(target.data_ptr()),
-                                                        d, batch, C.c_float(lr), int(apply), C.byref(loss),
-                                                        _stream_ptr(stream)), "mpm_cnn_train_step")
+        self.ctx._check(self.ctx.lib.mpm_cnn_train_step(self.ctx.ptr, self.h, int(nimg), C.c_float(lr), int(apply),
+                                                        C.byref(loss), _stream_ptr(stream)), "mpm_cnn_train_step")
         return float(loss.value)
 
     def guess(self, sub: Subgrid, lat: DeviceLattice, prm: DeviceParams, stream=None):
