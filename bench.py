@@ -3,19 +3,27 @@
 
 Metric: species-voxel-steps/s at 1e-6 relative residual (sum over steps and
 species of the in-mask voxels of the box, per second), plain FP64 GMRES against
-the FP32-in-FP64-refinement path, on the 256^3 three-species pleural-shell
-workload (2000 Voronoi tumour cells in a 128x128x96 region of the shell, bbox
-margin 4, D = (1, 0.5, 0.2), dt = 0.05, 20 steps).
+the learned + mixed-precision form (the network's guess, then FP32 GMRES inside
+FP64 refinement), on the full growing tumour: a 512x384x384 int32 CPM lattice
+with a pleural-shell mask whose tumour grows so the bounding box (margin 4)
+expands from ~61^3 to 302x264x264 voxels over 200 steps, re-extracted every
+step, 3 species.
 
 One bench step = one implicit-Euler step of the whole hot path through the C
-ABI (mpm_step / mpm_step_enqueue: one kernel per step): bounding box, tile
-compaction, gather + assembly, GMRES for the three species and the scatter
-onto the mask.  The lattice is resident in HBM; L2 is flushed (256 MB write)
-before every timed step.  `e2e` repeats the steps through mpm_step_host with
-the lattice in pinned host memory: the cell ids copied in and the step's box
-of the fields copied out inside the timed region.
+ABI (mpm_step_enqueue): bounding box, tile compaction, gather + assembly, [the
+network's guess,] GMRES for the three species and the scatter onto the mask,
+all in one CUDA graph.  The K timed steps are sampled evenly over the 200-step
+growth (t = 0, 200/K, ...); the tumour of step t is set on the device before
+the step, outside the timing.  The lattice is resident in HBM (2.2 GB, larger
+than L2) and L2 is flushed (256 MB write) before every timed step; every timed
+step's report is checked (status, true FP64 residual <= 1e-6 ||b||).  `e2e`
+repeats sampled steps through mpm_step_host with the lattice in pinned host
+memory.  The network is trained first, on the trajectory of another instance
+of the geometry (seed 6), by the library's own kernels.
 
---impl reference times the CPU oracle (single thread) on the same workload.
+--impl reference times the CPU oracle (single thread) on the first K steps of
+the same workload (a bounded sample: the late steps' boxes take the oracle
+seconds each).
 """
 from __future__ import annotations
 
@@ -35,9 +43,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "species-voxel-steps/s at 1e-6 rel. residual: plain FP64 GMRES vs learned+mixed"
-WORKLOAD = ("shell256: 256^3 int32 CPM lattice, pleural-shell mask (ellipsoids 110/90/120 and 100/80/110), "
-            "2000 Voronoi tumour cells in a 128x128x96 shell region, bbox+4, 3 species, D=(1,0.5,0.2), "
-            "dt=0.05, per-cell rates U[0.01,0.1], 20 implicit-Euler steps, rtol 1e-6")
 
 
 def _peaks():
@@ -264,36 +269,108 @@ def bench_patches64(mpm, W, ctx, stream, flush, warmup, steps=50):
             "mask_voxels": sum(r["mask_voxels"] for r in reps)}
 
 
-def bench_growth512(mpm, W, ctx, stream, flush, sample=range(0, 201, 20)):
-    """512x384x384 growing tumour: at sampled steps t the Voronoi cells whose seed
-    lies in the growth box are tumour (a device-side update outside the timing),
-    then one timed step re-extracts the box and solves 3 species."""
+C5_STEPS = 200
+CNN_FLOPS_PER_VOXEL = 2 * 27 * (9 * 24 + 4 * 24 * 24 + 24 * 3)   # 139 968: the network's convolutions
+
+
+def c5_schedule(K):
+    """The K sampled steps of the 200-step growth."""
+    return [int(k * C5_STEPS // K) for k in range(K)]
+
+
+def c5_workload(K):
+    ts = c5_schedule(K)
+    return ("growth512: 512x384x384 int32 CPM lattice, pleural-shell mask (ellipsoids 230/175/175 and "
+            "215/160/160), ~9.8k Voronoi tumour cells growing so the bbox+4 expands from 61x87x83 to "
+            f"302x264x264 over 200 steps, re-extracted every step; {K} steps sampled at t = "
+            f"{ts[0]}, {ts[1] if K > 1 else ts[0]}, ..., {ts[-1]} (every {C5_STEPS / K:g}); 3 species, "
+            "D=(1,0.5,0.2), dt=0.05, per-cell rates U[0.01,0.1], rtol 1e-6")
+
+
+class Growth:
+    """The growing tumour and its device-side tumour update."""
+
+    def __init__(self, W):
+        import torch
+        self.W = W
+        self.wl, self.extra = W.growth512()
+        self.cand = torch.from_numpy(self.extra["cand"]).cuda()
+        self.labels = torch.from_numpy(self.extra["labels"].astype(np.int64)).cuda()
+
+    def set_tumour(self, lat, t):
+        import torch
+        lo, hi = self.W.growth_box(t, self.wl.steps)
+        inside = np.all((self.extra["seeds"] >= lo) & (self.extra["seeds"] < hi), axis=1)
+        ids = torch.from_numpy(np.where(inside, np.arange(1, len(inside) + 1), 0).astype(np.int32)).cuda()
+        lat.cell_id.view(-1)[self.cand] = ids[self.labels]
+
+
+def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=None):
+    """K sampled steps of the growing tumour on one path, every report checked."""
     import torch
-    wl, extra = W.growth512()
-    cand = torch.from_numpy(extra["cand"]).cuda()
-    labels = torch.from_numpy(extra["labels"].astype(np.int64)).cuda()
-    out = {}
-    for name, extra_o in (("fp64", dict(precision=0)), ("mixed", dict(precision=1, inner_rtol=1e-6))):
-        lat = mpm.DeviceLattice(wl.lattice)
-        solver = mpm.StepSolver(ctx, lat, mpm.DeviceParams(wl.params), wl.margin)
-        opts = mpm.make_opts(rtol=wl.rtol, restart=8, maxit=1000, **extra_o)
-        ms, units, boxes = 0.0, 0, []
-        for i, t in enumerate(sample):
-            lo, hi = W.growth_box(t, wl.steps)
-            inside = np.all((extra["seeds"] >= lo) & (extra["seeds"] < hi), axis=1)
-            ids = torch.from_numpy(np.where(inside, np.arange(1, len(inside) + 1), 0).astype(np.int32)).cuda()
-            lat.cell_id.view(-1)[cand] = ids[labels]
-            if i == 0:
-                solver.step(opts)   # warm-up at the first sampled state
-            rep, dt = _timed_queued(solver, opts, stream, flush, i)
-            assert rep["status_code"] == mpm.OK, rep
-            ms += dt
-            units += rep["mask_voxels"] * 3
-            boxes.append(rep["box_voxels"])
-        out[name] = {"value": units / (ms / 1e3), "ms_per_step": ms / len(sample)}
-    return {"value": out["mixed"]["value"], "unit": "species-voxel-steps/s", "paths": out,
-            "sample": f"steps {list(sample)[0]}..{list(sample)[-1]} every {list(sample)[1] - list(sample)[0]}",
-            "box_voxels_first_last": [boxes[0], boxes[-1]]}
+    wl = g.wl
+    lat = mpm.DeviceLattice(wl.lattice)
+    init = lat.fields.clone()
+    prm = mpm.DeviceParams(wl.params)
+    solver = mpm.StepSolver(ctx, lat, prm, wl.margin)
+    if cnn is not None:
+        solver.set_network(cnn)
+    g.set_tumour(lat, 0)
+    for _ in range(warmup):
+        solver.step(opts)
+    lat.fields.copy_(init)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    l0 = ctx.launches()
+    ms, units, reps, its = 0.0, 0, [], []
+    kbytes = kops = 0
+    bT = 4 if opts.precision else 8
+    L = wl.lattice.cell_id.size
+    for i, t in enumerate(c5_schedule(K)):
+        g.set_tumour(lat, t)
+        rep, dt = _timed_queued(solver, opts, stream, flush, i)
+        assert rep["status_code"] == mpm.OK, (t, rep)
+        assert all(r <= wl.rtol * b for r, b in zip(rep["res"], rep["bnorm"])), (t, rep)
+        ms += dt
+        units += rep["mask_voxels"] * wl.params.nspecies
+        kbytes += step_bytes(rep, L, wl.params.nspecies, bT)
+        kops += solver_fp64_ops(rep, rep["mask_voxels"], bool(opts.precision))
+        reps.append(rep)
+        its.append(sum(rep["iters"]) / len(rep["iters"]))
+    launches = ctx.launches() - l0
+    clocks = sampler.stop() if sampler else None
+    out = {"value": units / (ms / 1e3), "ms_per_step": ms / K, "steps_checked": len(reps),
+           "arnoldi_steps_per_species_step": float(np.mean(its)), "kernel_ms": ms, "kernel_bytes": kbytes,
+           "kernel_fp64_ops": kops, "units": units, "launches": launches,
+           "box_voxels_first_last": [reps[0]["box_voxels"], reps[-1]["box_voxels"]],
+           "mask_voxels_first_last": [reps[0]["mask_voxels"], reps[-1]["mask_voxels"]],
+           "max_rel_res": max(r / b for rep in reps for r, b in zip(rep["res"], rep["bnorm"]))}
+    return out, clocks, (solver, lat, prm, init)
+
+
+def fp64_peak_instr(sm_mhz, nsm=152):
+    """FP64 thread-instructions per second the SMs can issue: 2 per clock per SM
+    (GB300's FP64 rate, 1.25 TFLOP/s counting an FMA as 2 flops, at 2.07 GHz)."""
+    return 2.0 * nsm * sm_mhz * 1e6
+
+
+def cnn_guess_time(mpm, ctx, cnn, solver, stream, flush, reps=3):
+    """Device time of the network's guess alone (plan, features, six
+    convolutions) on the subgrid's current extraction: mpm_cnn_guess bracketed
+    by CUDA events after an L2 flush, median of `reps`."""
+    import torch
+    ts = []
+    for i in range(reps + 1):
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cnn.guess(solver.sub, solver.lat, solver.prm)
+        b.record(stream)
+        b.synchronize()
+        if i:
+            ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
 
 
 def bench_learned(mpm, ctx, samples=20000):
@@ -323,49 +400,92 @@ def bench_learned(mpm, ctx, samples=20000):
     return out
 
 
-def cpu_baseline(wl, nsteps):
+def oracle_c5_steps(W, nsteps):
+    """The oracle on the first nsteps steps of the growing tumour (t = 0, 1, ...)."""
     import oracle
-    lat = wl.lattice.copy()
-    oracle.step(lat.copy(), wl.params, wl.margin, rtol=1e-6)       # load/build outside the timing
+    wl, extra = W.growth512()
+    lat = wl.lattice
     units = 0
-    t0 = time.perf_counter()
-    for _ in range(nsteps):
+    dt = 0.0
+    for t in range(nsteps):
+        W.grow(wl, t, extra)
+        t0 = time.perf_counter()
         rep = oracle.step(lat, wl.params, wl.margin, rtol=wl.rtol, restart=wl.restart)
+        dt += time.perf_counter() - t0
         units += rep["mask_voxels"] * wl.params.nspecies
-    dt = time.perf_counter() - t0
+    return units, dt
+
+
+def cpu_baseline(W, nsteps):
+    import oracle
+    oracle.build()
+    units, dt = oracle_c5_steps(W, nsteps)
     return {"value": units / dt, "unit": "species-voxel-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {nsteps} implicit-Euler steps of shell256 (all 3 species, every in-mask voxel), "
-                      f"single-threaded C/numpy oracle, GMRES(30) to 1e-6, {dt:.2f} s"}
+            "sample": f"the first {nsteps} implicit-Euler steps (t = 0..{nsteps - 1}) of growth512 (all 3 species, "
+                      f"every in-mask voxel of the box), single-threaded C/NumPy oracle (gcc "
+                      f"{' '.join(oracle.BUILD_FLAGS)}), GMRES(30) to 1e-6, {dt:.2f} s"}
 
 
 def run_reference(args, rank, world):
-    import numpy as np  # noqa: F401
     if rank != 0:
         return 0
     from paper_2505_03067_gb300 import workloads as W
     import oracle
     oracle.build()
-    wl = W.shell256()
-    lat = wl.lattice.copy()
-    for _ in range(args.warmup):
-        oracle.step(lat, wl.params, wl.margin, rtol=wl.rtol, restart=wl.restart)
-    lat = wl.lattice.copy()
-    units = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        rep = oracle.step(lat, wl.params, wl.margin, rtol=wl.rtol, restart=wl.restart)
-        units += rep["mask_voxels"] * wl.params.nspecies
-    dt = time.perf_counter() - t0
+    units, _ = oracle_c5_steps(W, min(args.warmup, 2))   # warm-up (loads, first touches)
+    units, dt = oracle_c5_steps(W, args.steps)
     v = units / dt
     line = {"metric": METRIC, "value": v, "unit": "species-voxel-steps/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "path": "CPU oracle, FP64 MGS-GMRES(30)"},
+            "config": {"workload": c5_workload(args.steps),
+                       "path": "CPU oracle, FP64 MGS-GMRES(30)",
+                       "sample": f"the first {args.steps} steps of the 200-step growth (t = 0..{args.steps - 1}): "
+                                 "the bounded sample of the same workload"},
             "cpu_baseline": {"value": v, "unit": "species-voxel-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full implicit-Euler steps of shell256 (single-threaded oracle)"},
+                             "sample": f"first {args.steps} implicit-Euler steps of growth512 (single-threaded "
+                                       f"oracle, gcc {' '.join(oracle.BUILD_FLAGS)})"},
             "e2e": {"value": v, "unit": "species-voxel-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_shell256(mpm, W, ctx, stream, flush, K, warmup):
+    """The 256^3 pleural shell (2000 Voronoi tumour cells, 20 steps): plain
+    FP64 against FP32 GMRES(8) inside FP64 refinement, and the same with the
+    box cadence of Sec. 2.3 (a full extraction every 50 steps, a 2-voxel
+    guard band; this tumour does not move, so every timed step keeps the box).
+    Every step's report is checked."""
+    wl = W.shell256()
+    S = wl.params.nspecies
+    out = {}
+    for name, extra in (("fp64", dict(precision=0)), ("mixed", dict(precision=1, inner_rtol=1e-6)),
+                        ("mixed_cadence50", dict(precision=1, inner_rtol=1e-6, box_every=50, box_guard=2))):
+        opts = mpm.make_opts(rtol=wl.rtol, restart=8, maxit=1000, **extra)
+        lat = mpm.DeviceLattice(wl.lattice)
+        init = lat.fields.clone()
+        solver = mpm.StepSolver(ctx, lat, mpm.DeviceParams(wl.params), wl.margin)
+        for _ in range(warmup):
+            solver.step(opts)
+        lat.fields.copy_(init)
+        ms, units, kbytes, kops = 0.0, 0, 0, 0
+        bT = 4 if extra["precision"] else 8
+        for i in range(K):
+            rep, t = _timed_queued(solver, opts, stream, flush, i)
+            assert rep["status_code"] == mpm.OK, rep
+            assert all(r <= wl.rtol * b for r, b in zip(rep["res"], rep["bnorm"])), rep
+            ms += t
+            units += rep["mask_voxels"] * S
+            kbytes += step_bytes(rep, wl.lattice.cell_id.size, S, bT)
+            kops += solver_fp64_ops(rep, rep["mask_voxels"], bool(extra["precision"]))
+        out[name] = {"value": units / (ms / 1e3), "ms_per_step": ms / K, "steps_checked": K,
+                     "iters_last_step": rep["iters"], "box_voxels": rep["box_voxels"],
+                     "mask_voxels": rep["mask_voxels"], "stored_voxels": rep["stored_voxels"],
+                     "achieved_gbs": kbytes / (ms / 1e3) / 1e9, "fp64_tinstr": kops / (ms / 1e3) / 1e12}
+        del solver, lat
+    return {"unit": "species-voxel-steps/s", "paths": out,
+            "workload": "shell256: 256^3 lattice, pleural shell (110/90/120, 100/80/110), 2000 Voronoi tumour "
+                        f"cells in a 128x128x96 region, bbox+4, 3 species, dt=0.05, {K} implicit-Euler steps, rtol 1e-6"}
 
 
 def main():
@@ -377,8 +497,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--restart", type=int, default=8)
+    ap.add_argument("--c5-epochs", type=int, default=3, help="passes over the training trajectory (200 steps each)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-workloads", action="store_true", help="skip the 32^3, 64-patch and 512x384x384 lines")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the 256^3, 32^3, 64-patch sub-lines")
     ap.add_argument("--train-samples", type=int, default=20000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -389,10 +510,9 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2505_03067_gb300 import mpm
+    from paper_2505_03067_gb300 import learned, mpm
     from paper_2505_03067_gb300 import workloads as W
 
     torch.cuda.set_device(local)
@@ -404,146 +524,143 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    wl = W.shell256()
     ctx = mpm.Context()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    S = wl.params.nspecies
-    # mixed_cadence50: the same FP32 path with Sec. 2.3's box cadence (a full
-    # extraction every 50 steps, a 2-voxel guard band); the tumour of this
-    # workload does not move, so every timed step keeps the box
-    paths = {"fp64": dict(precision=0), "mixed": dict(precision=1, inner_rtol=1e-6),
-             "mixed_cadence50": dict(precision=1, inner_rtol=1e-6, box_every=50, box_guard=2)}
-    results = {}
-    clocks = None
-    for name, extra in paths.items():
-        opts = mpm.make_opts(rtol=wl.rtol, restart=args.restart, maxit=1000, **extra)
-        lat = mpm.DeviceLattice(wl.lattice)
-        init = lat.fields.clone()
-        prm = mpm.DeviceParams(wl.params)
-        solver = mpm.StepSolver(ctx, lat, prm, wl.margin)
-        for _ in range(args.warmup):
-            solver.step(opts)
-        lat.fields.copy_(init)
-        check = solver.step(opts)   # one checked step from c^0 before the timing
-        assert check["status_code"] == mpm.OK, check
-        lat.fields.copy_(init)
-        headline = name == "mixed"
-        sampler = ClockSampler(local) if headline else None
+    K = args.steps
+    g = Growth(W)
+    S = g.wl.params.nspecies
+
+    # ---- the network of the learned form: trained on another instance of the
+    # geometry (seed 6, cut to its growth region) by the library's kernels
+    cnn_t, hist = learned.train_growth(ctx, epochs=args.c5_epochs)
+    params, s_out = cnn_t.get(0), cnn_t.s_out
+    cnn_t.close()
+    torch.cuda.empty_cache()
+    cnn = mpm.CNN(ctx, g.wl.lattice.dims, 1, params, s_out=s_out)
+    training = {"trajectory": "growth_crop seed 6: the growth geometry with other cells and rates, 324x264x264 crop "
+                              "of its growth region, 200 steps per epoch of the FP64 solver at rtol 1e-10",
+                "epochs": args.c5_epochs, "adam_steps": hist["samples"], "seconds": hist["seconds"],
+                "loss_first_last": [float(np.mean(hist["loss"][:10])), float(np.mean(hist["loss"][-20:]))]}
+
+    # ---- the three paths on the same sampled steps
+    peak, src = _peaks()
+    mixed = dict(precision=1, inner_rtol=1e-6)
+    plan = (("fp64", dict(precision=0), None), ("mixed", mixed, None), ("learned_mixed", mixed, cnn))
+    results, clocks, keep = {}, None, None
+    for name, extra, net in plan:
+        opts = mpm.make_opts(rtol=g.wl.rtol, restart=args.restart, maxit=1000, **extra)
+        headline = name == "learned_mixed"
         barrier()
-        if sampler:
-            sampler.start()
-        l0 = ctx.launches()
-        # each step queued behind its L2 flush (68 us of device work, longer
-        # than the host needs to queue the step) and bracketed by its own
-        # events, so the host's work stays off the device timeline; then waited
-        # for, and its report checked: every timed step must reach the tolerance
-        ms, units, checked = 0.0, 0, 0
-        for i in range(args.steps):
-            last, t = _timed_queued(solver, opts, stream, flush, i)
-            assert last["status_code"] == mpm.OK, last
-            assert all(res <= wl.rtol * b for res, b in zip(last["res"], last["bnorm"])), last
-            checked += 1
-            ms += t
-            units += last["mask_voxels"] * S
+        res, clk, kp = run_c5_path(mpm, g, ctx, stream, flush, opts, K, args.warmup, net,
+                                   ClockSampler(local) if headline else None)
         barrier()
-        launches = ctx.launches() - l0
-        if sampler:
-            clocks = sampler.stop()
-        _, ms_max = replica_value(units, ms, world, "cuda")
-        assert check["status_code"] == mpm.OK, check
-        bT = 4 if extra["precision"] else 8
-        L = wl.lattice.cell_id.size
-        kbytes = args.steps * step_bytes(last, L, S, bT)
-        sbytes = args.steps * solver_bytes(last, last["mask_voxels"], last["stored_voxels"], bT)
-        kops = args.steps * solver_fp64_ops(last, last["mask_voxels"], bool(extra["precision"]))
-        results[name] = {"value": replica_value(units, ms_max, 1)[0] * world, "ms_per_step": ms_max / args.steps,
-                         "steps_checked": checked,
-                         "solver_ms_last_step": last["solve_ms"], "kernel_bytes": kbytes, "solver_bytes": sbytes,
-                         "kernel_fp64_ops": kops, "kernel_ms": ms, "launches": launches,
-                         "iters_last_step": last["iters"], "box_voxels": last["box_voxels"],
-                         "mask_voxels": last["mask_voxels"], "stored_voxels": last["stored_voxels"]}
+        _, ms_max = replica_value(res["units"], res["kernel_ms"], world, "cuda")
+        res["value"] = replica_value(res["units"], ms_max, world)[0]
         if headline:
-            results[name]["solver"] = solver
-            results[name]["opts"] = opts
-            results[name]["lat"] = lat
-            results[name]["init"] = init
+            clocks, keep = clk, (kp, opts)
+            res["cnn_ms_last_step"] = cnn_guess_time(mpm, ctx, net, kp[0], stream, flush)
+        else:
+            del kp
+        results[name] = res
+        torch.cuda.empty_cache()
+
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    for name, r in results.items():
+        sec = r["kernel_ms"] / 1e3
+        if name == "learned_mixed":
+            # the network alone, timed on the last (largest) state; the rest of the step is the two step launches
+            last_mask = r["mask_voxels_first_last"][1]
+            t_cnn = r["cnn_ms_last_step"] / 1e3
+            r["roofline_cnn"] = {"bound": "tensor", "kernel": "the network's guess on the last sampled state: plan, "
+                                 "features and six tcgen05 convolutions (k_conv_tc)",
+                                 "achieved": last_mask * CNN_FLOPS_PER_VOXEL / t_cnn / 1e12,
+                                 "peak": 1980.0, "unit": "TFLOP/s", "peak_source": "measured bf16 burst "
+                                 "(MEASURED_PEAKS.json bf16_tflops)",
+                                 "flops_per_launch": last_mask * CNN_FLOPS_PER_VOXEL, "ms": r["cnn_ms_last_step"]}
+            r["roofline_cnn"]["frac"] = r["roofline_cnn"]["achieved"] / 1980.0
+        r["roofline_hbm"] = {"bound": "hbm", "achieved": r["kernel_bytes"] / sec / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": r["kernel_bytes"] / sec / 1e9 / peak,
+                             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                             "note": "algorithmic bytes of the step launches (extraction, solve, scatter) over the "
+                                     "whole step's time" + (" including the network's" if name == "learned_mixed" else "")}
+        pk = fp64_peak_instr(sm_mhz)
+        r["roofline_fp64"] = {"bound": "alu", "unit": "T FP64 instr/s", "achieved": r["kernel_fp64_ops"] / sec / 1e12,
+                              "peak": pk / 1e12, "frac": r["kernel_fp64_ops"] / sec / pk,
+                              "peak_source": "2 FP64 thread-instructions per clock per SM x 152 SMs at the median "
+                                             "SM clock under load"}
+
+    head = results["learned_mixed"]
+    # the dominant kernel of the headline step: the network's convolutions
+    # against the two step launches (their time = step time - network time)
+    t_step_last = head["kernel_ms"] / K
+    if head["cnn_ms_last_step"] >= 0.5 * t_step_last:
+        roofline = dict(head["roofline_cnn"])
+    else:
+        roofline = dict(head["roofline_hbm"])
+    roofline["traffic"] = None
 
     # ---- end to end through the public API with host buffers (mpm_step_host)
-    head = results["mixed"]
-    lat, init, solver, opts = head["lat"], head["init"], head["solver"], head["opts"]
-    h_cell = lat.cell_id.cpu().pin_memory()
+    (solver, lat, prm, init), opts = keep
+    wl, extra = g.wl, g.extra
+    W.grow(wl, 0, extra)
+    h_cell = torch.from_numpy(wl.lattice.cell_id).pin_memory()
     h_mask = lat.mask.cpu().pin_memory()
     h_fields = init.cpu().pin_memory()
-    ne = max(1, min(args.e2e_steps, args.steps))
-    # the first call brings the whole state in (mask and fields); every timed
-    # step then moves the step's input, the cell-id lattice, in and the step's
-    # box of the three fields out
     solver.step_host(h_cell, h_fields, opts, mask=h_mask, fields_in=True)
     barrier()
-    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne)]
-    bo = 0
-    for i in range(ne):
+    ne = max(1, min(args.e2e_steps, K))
+    e_ms, e_units, bo = 0.0, 0, 0
+    for i, t in enumerate(c5_schedule(ne)):
+        W.grow(wl, t, extra)
+        h_cell.numpy()[...] = wl.lattice.cell_id
         flush.fill_(i & 255)
-        eev[i][0].record(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         erep = solver.step_host(h_cell, h_fields, opts)
-        eev[i][1].record(stream)
+        b.record(stream)
+        b.synchronize()
+        assert erep["status_code"] == mpm.OK, erep
+        assert all(r <= wl.rtol * bb for r, bb in zip(erep["res"], erep["bnorm"])), erep
+        e_ms += a.elapsed_time(b)
+        e_units += erep["mask_voxels"] * S
         (x0, y0, z0), (x1, y1, z1) = erep["box"]
         bo += S * 8 * (x1 - x0) * (y1 - y0) * (z1 - z0)
-    torch.cuda.synchronize()
     barrier()
-    assert erep["status_code"] == mpm.OK, erep
-    assert all(res <= wl.rtol * b for res, b in zip(erep["res"], erep["bnorm"])), erep
-    e2e_ms = sum(a.elapsed_time(b) for a, b in eev)
-    units = erep["mask_voxels"] * S * ne
-    e2e_value, _ = replica_value(units, e2e_ms, world, "cuda")
-    bi = h_cell.numel() * 4
-    e2e = {"value": e2e_value, "unit": "species-voxel-steps/s",
-           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo // ne,
-           "note": "mpm_step_host per step (one synchronous C-ABI call): the 256^3 int32 cell-id lattice copied in "
-                   "from pinned host memory, the step, and the step's box of the 3 FP64 fields copied back to the "
-                   "pinned host fields (a step changes no voxel outside its box); the mask and the initial fields "
-                   "went in once before the timed steps"}
+    e2e_value, _ = replica_value(e_units, e_ms, world, "cuda")
+    e2e = {"value": e2e_value, "unit": "species-voxel-steps/s", "h2d_bytes_per_step": h_cell.numel() * 4,
+           "d2h_bytes_per_step": bo // ne, "steps": ne,
+           "note": f"mpm_step_host per step (one synchronous C-ABI call, learned + mixed path) at {ne} steps sampled "
+                   "over the growth: the 512x384x384 int32 cell-id lattice copied in from pinned host memory, the "
+                   "step, and the step's box of the 3 FP64 fields copied back to the pinned host fields; the mask "
+                   "and the initial fields went in once before the timed steps"}
+    del solver, lat
 
-    # ---- roofline of the dominant kernel (the persistent GMRES solver)
-    peak, src = _peaks()
-    ach = head["kernel_bytes"] / (head["kernel_ms"] / 1e3) / 1e9
-    fp64_rate = head["kernel_fp64_ops"] / (head["kernel_ms"] / 1e3) / 1e12
-    rec = _traffic_record("shell256_mixed_step")
-    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "of fallback",
-                "kernel": "k_step<float,8,1,1,512> (the whole step in one cooperative kernel: extraction, "
-                          "assembly, persistent GMRES with FP32 Krylov + FP64 residual, scatter)",
-                "duration": "CUDA events around each step's graph launch (one kernel per graph)",
-                "traffic": rec["dram_bytes_per_launch"] if rec else None,
-                "algorithmic_bytes_per_launch": head["kernel_bytes"] / args.steps,
-                "solver_share_of_bytes": head["solver_bytes"] / head["kernel_bytes"],
-                "fp64_tops_achieved": fp64_rate}
-    fp = results["fp64"]
-    fp_ach = fp["kernel_bytes"] / (fp["kernel_ms"] / 1e3) / 1e9
+    keys = ("value", "ms_per_step", "steps_checked", "arnoldi_steps_per_species_step", "max_rel_res",
+            "box_voxels_first_last", "mask_voxels_first_last", "roofline_hbm", "roofline_fp64")
+    paths = {k: {kk: v[kk] for kk in keys} for k, v in results.items()}
+    paths["learned_mixed"]["roofline_cnn"] = head["roofline_cnn"]
+    paths["learned_mixed"]["cnn_ms_last_step"] = head["cnn_ms_last_step"]
     line = {"metric": METRIC, "value": head["value"], "unit": "species-voxel-steps/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "steps": K, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 + bf16 network",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "path": "mixed: FP32 GMRES(8) inside FP64 refinement, inner cycle to max(tol/4, 1e-6 ||r||)",
-                       "step": "mpm_step: one CUDA graph per step (cooperative extraction + assembly, persistent GMRES, scatter)",
-                       "l2": "flushed (256 MB write) before every timed step; lattice (486 MB) > L2",
-                       "box_voxels": head["box_voxels"], "mask_voxels": head["mask_voxels"],
-                       "stored_voxels": head["stored_voxels"], "parallelism": f"replicas x{world}"},
-            "paths": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "solver_ms_last_step", "iters_last_step",
-                                               "steps_checked")}
-                      for k, v in results.items()},
-            "fp64_path_roofline": {"achieved_gbs": fp_ach, "frac_hbm": fp_ach / peak,
-                                   "fp64_tops": fp["kernel_fp64_ops"] / (fp["kernel_ms"] / 1e3) / 1e12,
-                                   "fp64_peak_tops_nominal": 1.25},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": head["launches"], "clocks": clocks}
+            "config": {"workload": c5_workload(K),
+                       "path": "learned_mixed: the network's guess (trained on seed 6), then FP32 GMRES(8) inside "
+                               "FP64 refinement (inner cycle to max(tol/4, 1e-6 ||r||)); compared with plain FP64 "
+                               "GMRES(8) (paths.fp64) and FP32-in-FP64 from c^n (paths.mixed) on the same steps",
+                       "step": "mpm_step_enqueue: one CUDA graph per step (extraction + assembly launch, the network, "
+                               "persistent GMRES + scatter launch)",
+                       "l2": "flushed (256 MB write) before every timed step; lattice (2.2 GB) > L2",
+                       "network_training": training, "parallelism": f"replicas x{world}"},
+            "paths": paths, "roofline": roofline, "e2e": e2e, "gpu_launches": head["launches"], "clocks": clocks}
     if not args.no_workloads:
-        line["workloads"] = {"sphere32": bench_sphere32(mpm, W, ctx, stream, flush, args.warmup),
+        line["workloads"] = {"shell256": bench_shell256(mpm, W, ctx, stream, flush, 20, args.warmup),
+                             "sphere32": bench_sphere32(mpm, W, ctx, stream, flush, args.warmup),
                              "patches64": bench_patches64(mpm, W, ctx, stream, flush, args.warmup),
-                             "growth512": bench_growth512(mpm, W, ctx, stream, flush),
                              "learned_sphere32": bench_learned(mpm, ctx, args.train_samples)}
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(W, args.cpu_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -48,6 +48,7 @@ typedef enum {
 
 typedef struct mpm_ctx mpm_ctx;
 typedef struct mpm_subgrid mpm_subgrid;
+typedef struct mpm_cnn mpm_cnn;       /* the learned warm start's network (see mpm_cnn_create) */
 
 /* Bounding box: lo inclusive, hi exclusive, per axis (x, y, z). */
 typedef struct { int32_t lo[3], hi[3]; } mpm_box;
@@ -280,6 +281,21 @@ mpm_status mpm_step_enqueue(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *l
                             int32_t margin, const int32_t tile[3], const mpm_opts *opt, void *stream);
 mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, void *stream);
 
+/*
+ * The learned form of the device-resident step (the paper has no network):
+ * attach a network (mpm_cnn_* below; its image dims must be the lattice's)
+ * and every later mpm_step / mpm_step_enqueue / mpm_step_host on `sub` starts
+ * its solve from the network's prediction of c^{n+1} instead of c^n -- in
+ * the same CUDA graph, between the extraction and the solve, with no host
+ * round trip: features of the step's box, the network on the box's masked
+ * voxels, the prediction into the iterate (c^n where it is not finite).  The
+ * solve and its stopping rule are unchanged: GMRES judges the guess.  cnn =
+ * NULL detaches.  The network must outlive its use; the graph keeps its
+ * buffers.  MPM_ERR_ARG while a step is pending; dims are checked at the
+ * next step.
+ */
+mpm_status mpm_step_set_network(mpm_ctx *ctx, mpm_subgrid *sub, mpm_cnn *cnn);
+
 /* The inputs of a step in host memory, for mpm_step_host (page-locked memory
  * lets the copies run at the link's full speed; pageable memory also works). */
 typedef struct {
@@ -357,7 +373,6 @@ mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys,
  * that lattice in place (mpm_cnn_guess, the learned mpm_step).  Device
  * memory: about 82 bytes per image voxel for inference, 500 for training.
  */
-typedef struct mpm_cnn mpm_cnn;
 #define MPM_CNN_INPUT 0     /* mpm_cnn_load_image: features of the lattice's fields (c^n) */
 #define MPM_CNN_TARGET 1    /* mpm_cnn_load_image: the lattice's fields as the training target */
 /* train: 0 inference only, 1 also training (keeps activations, gradients, Adam state).

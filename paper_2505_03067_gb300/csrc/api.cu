@@ -251,6 +251,13 @@ mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_bo
     return mpm_step_wait_impl(ctx, sub, rep, out_box, (cudaStream_t)stream);
 }
 
+mpm_status mpm_step_set_network(mpm_ctx *ctx, mpm_subgrid *sub, mpm_cnn *cnn)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    return mpm_step_set_network_impl(ctx, sub, cnn);
+}
+
 mpm_status mpm_step_host(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_host_lattice *host, const mpm_lattice *dev,
                          const mpm_params *prm, int32_t margin, const int32_t tile[3], const mpm_opts *opt,
                          int32_t flags, mpm_report *rep, mpm_box *out_box, void *stream)

@@ -591,7 +591,7 @@ mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t
     A.work = c->counters + slot;
     A.err = c->d_err;
     A.timeout_ns = ctx->timeout_ns;
-    tc::k_conv_tc<CI, NO, EPI><<<ctx->num_sms, tc::kThreads, smem, st>>>(A);
+    tc::k_conv_tc<CI, NO, EPI><<<ctx->num_sms, tc::kConvThreads, smem, st>>>(A);
     ctx->launches += 1;
     return mpm_cuda_check(ctx, cudaGetLastError(), "cnn convolution");
 }
@@ -1019,7 +1019,7 @@ mpm_status mpm_cnn_enqueue_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, con
     FU.units = c->units;
     FU.nunits = c->counters;
     FU.x = c->x;
-    k_feat_units<<<ctx->num_sms * 2, 256, 0, st>>>(FU);
+    k_feat_units<<<ctx->num_sms * 8, 256, 0, st>>>(FU);
     ctx->launches += 2;
     MPM_CU(cudaGetLastError());
     tc::ConvArgs O;
@@ -1034,11 +1034,14 @@ mpm_status mpm_cnn_enqueue_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, con
     return forward_layers(ctx, c, lat->mask, false, O, st);
 }
 
-mpm_status mpm_cnn_check(mpm_ctx *ctx, mpm_cnn *c, const mpm_subgrid *sub, const mpm_lattice *lat,
-                         const mpm_params *prm)
+// A network used by a device-resident step: its image dims must be the
+// lattice's, and it predicts 3 species at most.
+mpm_status mpm_cnn_check(mpm_ctx *ctx, mpm_cnn *c, const mpm_lattice *lat, const mpm_params *prm)
 {
-    mpm_status r = solver_mode_check(ctx, c, sub, lat, prm, "learned step");
-    if (r != MPM_OK) return r;
+    for (int d = 0; d < 3; ++d)
+        if (lat->dims[d] != c->L[d])
+            return mpm_fail(ctx, MPM_ERR_ARG, "learned step: lattice dims differ from the network's image dims");
+    if (prm->nspecies > 3) return mpm_fail(ctx, MPM_ERR_ARG, "learned step: the network predicts 3 species");
     return check_err(ctx, c);
 }
 
@@ -1096,7 +1099,7 @@ mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, cons
     FU.s = s;
     FU.geo = c->geo;
     FU.tile_index = sub->tile_index;
-    k_feat_units<<<ctx->num_sms * 2, 256, 0, st>>>(FU);
+    k_feat_units<<<ctx->num_sms * 8, 256, 0, st>>>(FU);
     ctx->launches += 3;
     MPM_CU(cudaGetLastError());
     // image-mode output (pred = field channels + s_out z6) on the lattice-indexed buffer
@@ -1117,7 +1120,7 @@ mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, cons
     P.vscale = d_scale;
     P.s = s;
     P.z = z;
-    k_pc_scatter<<<ctx->num_sms * 2, 256, 0, st>>>(P);
+    k_pc_scatter<<<ctx->num_sms * 8, 256, 0, st>>>(P);
     ctx->launches += 1;
     return mpm_cuda_check(ctx, cudaGetLastError(), "cnn preconditioner output");
 }

@@ -50,7 +50,9 @@ namespace tc {
 constexpr int kSlabX = 8, kSlabY = 16, kZSeg = 8;
 constexpr int kHaloX = kSlabX + 2, kHaloY = kSlabY + 2;
 constexpr int kSlots = 6;               // halo depths in the shared-memory ring
-constexpr int kThreads = 256;           // 8 warps
+constexpr int kThreads = 256;           // weight-gradient kernel: 8 warps
+constexpr int kEpiWarps = 16;           // forward kernel: 16 epilogue / loader warps ...
+constexpr int kConvThreads = 32 * (kEpiWarps + 1);   // ... and one warp that issues the MMAs
 constexpr int kMaxImages = 16;
 
 // Device-side description of the images a network application covers.
@@ -274,6 +276,7 @@ __device__ __forceinline__ bool in_box(const CnnDom &D, int b, int x, int y, int
 // Active bytes of a unit's halo region (depths z0-1 .. z0+kZSeg, rows
 // oy-1 .. oy+16, columns ox-1 .. ox+8) into smem; returns per-slab activity
 // in the low kZSeg bits (through *slab_bits, all threads).
+template <int NTHR>
 __device__ __forceinline__ void load_unit_act(const CnnDom &D, const uint8_t *__restrict__ mask, const Unit &u,
                                               uint8_t *act, uint32_t *slab_bits)
 {
@@ -281,7 +284,7 @@ __device__ __forceinline__ void load_unit_act(const CnnDom &D, const uint8_t *__
     __syncthreads();
     constexpr int N = (kZSeg + 2) * kHaloY * kHaloX;
     uint32_t mine = 0u;
-    for (int i = threadIdx.x; i < N; i += kThreads) {
+    for (int i = threadIdx.x; i < N; i += NTHR) {
         const int xh = i % kHaloX, r = i / kHaloX;
         const int yh = r % kHaloY, j = r / kHaloY;
         const int x = u.ox - 1 + xh, y = u.oy - 1 + yh, z = u.z0 - 1 + j;
@@ -294,51 +297,83 @@ __device__ __forceinline__ void load_unit_act(const CnnDom &D, const uint8_t *__
     __syncthreads();
 }
 
+// The 16-byte copies of one halo depth handled by one loader thread, fixed for
+// a launch: the k-th covers item tid + k NL of the depth (halo row yh, copy c,
+// x row, channel chunk kc); `rel` is its source offset in elements from the
+// depth's halo origin, `dst` its shared offset in the slot, `act` its index in
+// a depth of the unit's activity bytes (act < 0: no item).
+template <int CI, int NL>
+struct HaloItems {
+    static constexpr int N = kHaloY * 3 * kSlabX * (CI / 8);
+    static constexpr int K = (N + NL - 1) / NL;
+    int32_t rel[K], dst[K], act[K];
+    __device__ __forceinline__ void init(int tid, int L0)
+    {
+        using H = Halo<CI>;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = tid + k * NL;
+            const int kc = i % H::KC;
+            int r = i / H::KC;
+            const int x = r % kSlabX;
+            r /= kSlabX;
+            const int c = r % 3, yh = r / 3;
+            const int xh = x + c;
+            rel[k] = (yh * L0 + xh) * CI + kc * 8;
+            dst[k] = yh * H::GS + (c * H::KC + kc) * 128 + x * 16;
+            act[k] = i < N ? yh * kHaloX + xh : -1;
+        }
+    }
+};
+
 // cp.async the halo depth j (image depth z0 - 1 + j) of unit u into slot base
-// `dst` (3 x-shifted copies, zero-filled where inactive).
-template <int CI>
-__device__ __forceinline__ void load_halo_depth(const CnnDom &D, const __nv_bfloat16 *__restrict__ in, const Unit &u,
-                                                const uint8_t *act, int j, uint32_t dst)
+// `dst` (3 x-shifted copies, zero-filled where inactive), with the items of
+// this thread (it.act < 0: none).
+template <int CI, int NL>
+__device__ __forceinline__ void load_halo_depth_items(const CnnDom &D, const __nv_bfloat16 *__restrict__ in,
+                                                      const Unit &u, const uint8_t *act, int j, uint32_t dst,
+                                                      const HaloItems<CI, NL> &it)
 {
-    using H = Halo<CI>;
-    constexpr int N = kHaloY * 3 * kSlabX * H::KC;
     const uint8_t *aj = act + j * kHaloY * kHaloX;
-    const int z = u.z0 - 1 + j;
-    for (int i = threadIdx.x; i < N; i += kThreads) {
-        const int kc = i % H::KC;
-        int r = i / H::KC;
-        const int x = r % kSlabX;
-        r /= kSlabX;
-        const int c = r % 3, yh = r / 3;
-        const int xh = x + c;
-        const bool ok = aj[yh * kHaloX + xh] != 0;
-        const __nv_bfloat16 *src = in;
-        if (ok) src = in + vox_index(D, u.b, u.ox - 1 + xh, u.oy - 1 + yh, z) * CI + kc * 8;
-        cp_async16(dst + yh * H::GS + (c * H::KC + kc) * 128 + x * 16, src, ok ? 16u : 0u);
+    // the halo origin (ox - 1, oy - 1) of this depth; items inside the box only
+    // are read (inactive or outside: zero-filled, source unused)
+    const int64_t base = (((int64_t)u.b * D.L[2] + (u.z0 - 1 + j)) * D.L[1] + (u.oy - 1)) * (int64_t)D.L[0] + (u.ox - 1);
+#pragma unroll
+    for (int k = 0; k < HaloItems<CI, NL>::K; ++k) {
+        if (it.act[k] < 0) continue;
+        const bool ok = aj[it.act[k]] != 0;
+        const __nv_bfloat16 *src = ok ? in + (base * CI + it.rel[k]) : in;
+        cp_async16(dst + (uint32_t)it.dst[k], src, ok ? 16u : 0u);
     }
 }
 
 // ---------------------------------------------------------------- forward / input-gradient convolution
 // One persistent CTA per SM; units are taken from the plan's list through an
-// atomic counter.  NO: MMA N (output channels padded to 16 or 32).
+// atomic counter.  NO: MMA N (output channels padded to 16 or 32).  Warps
+// 0..15 load the halo depths and run the epilogue (warp w: TMEM lane quarter
+// w & 3, channels 6 (w >> 2) .. 6 (w >> 2) + 5); warp 16 issues the MMAs, so
+// a slab's MMAs overlap the previous slab's epilogue.
 template <int CI, int NO, int EPI>
-__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__ ConvArgs A)
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ ConvArgs A)
 {
     using H = Halo<CI>;
     using S = ConvSmem<CI, NO>;
+    constexpr int NG = WImg<CI, NO>::NG;
+    constexpr int NL = 32 * kEpiWarps;            // loader / epilogue threads
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t s_tmem, s_bits;
     __shared__ int32_t s_unit;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);   // [0], [1]: MMA done per accumulator
     uint8_t *act = sm + S::ACT_OFF;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == kEpiWarps;
     const CnnDom &D = *A.dom;
     const uint32_t wbase = smem_u32(sm + S::W_OFF), rbase = smem_u32(sm + S::RING_OFF);
 
     // weights into shared memory; zero the ring (pad K-columns stay zero)
-    for (int i = tid; i < WImg<CI, NO>::BYTES / 16; i += kThreads)
+    for (int i = tid; i < WImg<CI, NO>::BYTES / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(sm + S::W_OFF)[i] = __ldg(reinterpret_cast<const uint4 *>(A.wimg) + i);
-    for (int i = tid; i < (S::RING_BYTES + 2048) / 16; i += kThreads)
+    for (int i = tid; i < (S::RING_BYTES + 2048) / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(sm + S::RING_OFF)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (warp == 0) tmem_alloc(&s_tmem, 64);
     if (tid == 0) {
@@ -351,23 +386,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
     tc_after_sync();
     const uint32_t tmem = s_tmem;
     constexpr uint32_t kIdesc = idesc_bf16(128, NO, false, false);
-    // epilogue role: lane quarter and column half of this warp
-    const int lq = warp & 3, half = warp >> 2;
+    // descriptors of the ring and weight bases; a tap's operands are these
+    // plus an offset (start-address field in 16-byte units)
+    const uint64_t adesc0 = sdesc(rbase, 128u, H::GS), bdesc0 = sdesc(wbase, NG * 128u, 128u);
+    // epilogue role
+    const int lq = warp & 3, wq = (warp >> 2) & 3;
     const int row = lq * 32 + lane;               // voxel (row & 7, row >> 3) of the slab
     const int ex = row & 7, ey = row >> 3;
-    float bias[16];
+    const int c0 = 6 * wq;                        // first channel of this thread
+    const bool epi = !mma_warp && (EPI != EPI_OUT || wq == 0);
+    HaloItems<CI, NL> items;
+    items.init(mma_warp ? 0 : tid, D.L[0]);
+    float bias[6];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) bias[i] = 0.0f;
-    if (A.bias) {
-        if (EPI == EPI_OUT) {
+    for (int i = 0; i < 6; ++i) bias[i] = 0.0f;
+    if (A.bias && EPI != EPI_DGRAD) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) bias[i] = A.bias[i];
-        } else if (EPI == EPI_GELU) {
-#pragma unroll
-            for (int i = 0; i < 12; ++i) bias[i] = A.bias[half * 12 + i];
-        }
+        for (int i = 0; i < 6; ++i)
+            if (EPI != EPI_OUT || i < 3) bias[i] = A.bias[c0 + i];
     }
-    uint32_t nmma = 0;                            // MMAs groups issued (accumulator = nmma & 1)
+    uint32_t nmma = 0;                            // MMA groups issued (accumulator = nmma & 1)
     const int nunits = *A.nunits;
     bool dead = false;
     for (;;) {
@@ -376,13 +414,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
         const int ui = s_unit;
         if (ui >= nunits || dead) break;
         const Unit u = A.units[ui];
-        load_unit_act(D, A.mask, u, act, &s_bits);
+        load_unit_act<kConvThreads>(D, A.mask, u, act, &s_bits);
         const uint32_t bits = s_bits;
         // depths 0 .. u.nz + 1; prefetch the first kSlots
         const int ndep = u.nz + 2;
         int issued = 0;
         for (; issued < ndep && issued < kSlots; ++issued) {
-            load_halo_depth<CI>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT);
+            if (!mma_warp) load_halo_depth_items<CI, NL>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT, items);
             cp_async_commit();
         }
         int prev_k = -1;                          // slab whose epilogue is pending
@@ -396,20 +434,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                 tc_before_sync();
                 __syncthreads();
                 tc_after_sync();
-                if (have && tid == 0) {
+                if (have && mma_warp && lane == 0) {
                     const uint32_t dt = tmem + (nmma & 1u) * 32u;
-#pragma unroll 1
+#pragma unroll
                     for (int p = 0; p < 9; ++p) {
                         const int dy = p % 3 - 1, dz = p / 3 - 1;
                         const uint32_t slot = (uint32_t)((k + 1 + dz) % kSlots);
-                        const uint32_t a0 = rbase + slot * H::SLOT + (uint32_t)(dy + 1) * H::GS;
-                        const uint32_t b0 = wbase + (uint32_t)p * H::QP * WImg<CI, NO>::NG * 128;
+                        const uint64_t a = adesc0 + ((slot * H::SLOT + (uint32_t)(dy + 1) * H::GS) >> 4);
+                        const uint64_t b = bdesc0 + ((uint32_t)p * H::QP * NG * 128u >> 4);
 #pragma unroll
-                        for (int s = 0; s < H::NKS; ++s) {
-                            const uint64_t ad = sdesc(a0 + 2u * s * 128u, 128u, H::GS);
-                            const uint64_t bd = sdesc(b0 + 2u * s * WImg<CI, NO>::NG * 128u, WImg<CI, NO>::NG * 128u, 128u);
-                            mma_bf16(dt, ad, bd, kIdesc, (p | s) != 0);
-                        }
+                        for (int s2 = 0; s2 < H::NKS; ++s2)
+                            mma_bf16(dt, a + (uint64_t)(s2 * 16), b + (uint64_t)(s2 * NG * 16), kIdesc,
+                                     (p | s2) != 0);
                     }
                     mma_commit(&bars[nmma & 1u]);
                 }
@@ -417,109 +453,100 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
             // epilogue of the previous active slab
             if (prev_k >= 0) {
                 const uint32_t buf = prev_m & 1u, par = (prev_m >> 1) & 1u;
-                // a wait that gave up in any thread ends the whole CTA's work
-                dead = !__syncthreads_and(mbar_wait(&bars[buf], par, A.timeout_ns, A.err));
-                tc_after_sync();
-                if (!dead) {
-                    const int z = u.z0 + prev_k;
-                    const int x = u.ox + ex, y = u.oy + ey;
-                    const bool on = act[((prev_k + 1) * kHaloY + ey + 1) * kHaloX + ex + 1] != 0;
-                    const uint32_t ta = tmem + buf * 32u + ((uint32_t)(lq * 32) << 16);
-                    const int64_t v = vox_index(D, u.b, x, y, z);
-                    if (EPI == EPI_OUT) {
-                        if (half == 0) {   // 3 channels: the first warp of each lane quarter
-                            float d[8];
-                            tmem_ld8(ta, d);
-                            tc_wait_ld();
-                            if (on) {
-                                if (A.pred) {
+                const int z = u.z0 + prev_k;
+                const int x = u.ox + ex, y = u.oy + ey;
+                const bool on = epi && act[((prev_k + 1) * kHaloY + ey + 1) * kHaloX + ex + 1] != 0;
+                const int64_t v = on ? vox_index(D, u.b, x, y, z) : 0;
+                // operands that do not depend on the MMAs: loaded before the wait
+                float pre[6];
+                int64_t e = -1;
+                double cn[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-                                    for (int c = 0; c < 3; ++c)
-                                        A.pred[v * 3 + c] = A.f32[v * 3 + c] + A.s_out * (d[c] + bias[c]);
-                                } else {
-                                    // solver mode: the element of (x, y, z) in the subgrid
-                                    const BoxGeo &g = *A.geo;
-                                    const int bx = x - g.lo[0], by = y - g.lo[1], bz = z - g.lo[2];
-                                    const int32_t t = __ldg(A.tile_index + ((int64_t)(bz >> g.lt[2]) * g.nt[1] +
-                                                                             (by >> g.lt[1])) * g.nt[0] + (bx >> g.lt[0]));
-                                    if (t >= 0) {
-                                        const int ix = bx & ((1 << g.lt[0]) - 1), iy = by & ((1 << g.lt[1]) - 1),
-                                                  iz = bz & ((1 << g.lt[2]) - 1);
-                                        const int64_t e = ((int64_t)t << (g.lt[0] + g.lt[1] + g.lt[2])) + ix +
-                                                          ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
-                                        for (int c = 0; c < A.nspecies && c < 3; ++c) {
-                                            const double cn = A.field[c][v];
-                                            const double p = cn + (double)(A.s_out * (d[c] + bias[c]));
-                                            A.xs[c][e] = isfinite(p) ? p : cn;   // a non-finite guess falls back to c^n
-                                        }
-                                    }
-                                }
+                for (int i = 0; i < 6; ++i) pre[i] = 0.0f;
+                if (on) {
+                    if (EPI == EPI_DGRAD) {
+                        const float2 *zp = reinterpret_cast<const float2 *>(A.zprev + v * 24 + c0);
+                        const float2 q0 = zp[0], q1 = zp[1], q2 = zp[2];
+                        pre[0] = q0.x; pre[1] = q0.y; pre[2] = q1.x; pre[3] = q1.y; pre[4] = q2.x; pre[5] = q2.y;
+                    } else if (EPI == EPI_OUT) {
+                        if (A.pred) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) pre[c] = A.f32[v * 3 + c];
+                        } else {
+                            const BoxGeo &g = *A.geo;
+                            const int bx = x - g.lo[0], by = y - g.lo[1], bz = z - g.lo[2];
+                            const int32_t t = __ldg(A.tile_index + ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) *
+                                                                       g.nt[0] + (bx >> g.lt[0]));
+                            if (t >= 0) {
+                                const int ix = bx & ((1 << g.lt[0]) - 1), iy = by & ((1 << g.lt[1]) - 1),
+                                          iz = bz & ((1 << g.lt[2]) - 1);
+                                e = ((int64_t)t << (g.lt[0] + g.lt[1] + g.lt[2])) + ix +
+                                    ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
+                                for (int c = 0; c < A.nspecies && c < 3; ++c) cn[c] = A.field[c][v];
                             }
                         }
-                    } else {
-                        // 12 channels per warp half: half 0 columns 0..11, half 1 columns 12..23
-                        float d[12];
-                        if (half == 0) {
-                            float t16[16];
-                            tmem_ld16(ta, t16);
-                            tc_wait_ld();
+                    }
+                }
+                // one thread waits for the MMAs (the others sleep at the barrier);
+                // a wait that gave up ends the whole CTA's work
+                bool okw = true;
+                if (mma_warp && lane == 0) okw = mbar_wait(&bars[buf], par, A.timeout_ns, A.err);
+                dead = !__syncthreads_and(okw);
+                tc_after_sync();
+                if (!dead && !mma_warp && (EPI != EPI_OUT || wq == 0)) {
+                    // columns lo .. lo + 15 of this lane quarter hold channels c0 .. c0 + 5
+                    const int lo = c0 & ~7;
+                    const uint32_t ta = tmem + buf * 32u + (uint32_t)lo + ((uint32_t)(lq * 32) << 16);
+                    float t0[8], t1[8];
+                    tmem_ld8(ta, t0);
+                    tmem_ld8(ta + 8u, t1);
+                    tc_wait_ld();
+                    float d[6];
+                    switch (wq) {   // warp-uniform: constant register indices in every case
+                    case 0: d[0] = t0[0]; d[1] = t0[1]; d[2] = t0[2]; d[3] = t0[3]; d[4] = t0[4]; d[5] = t0[5]; break;
+                    case 1: d[0] = t0[6]; d[1] = t0[7]; d[2] = t1[0]; d[3] = t1[1]; d[4] = t1[2]; d[5] = t1[3]; break;
+                    case 2: d[0] = t0[4]; d[1] = t0[5]; d[2] = t0[6]; d[3] = t0[7]; d[4] = t1[0]; d[5] = t1[1]; break;
+                    default: d[0] = t0[2]; d[1] = t0[3]; d[2] = t0[4]; d[3] = t0[5]; d[4] = t0[6]; d[5] = t0[7]; break;
+                    }
+                    if (on) {
+                        if (EPI == EPI_OUT) {
+                            if (A.pred) {
 #pragma unroll
-                            for (int c = 0; c < 12; ++c) d[c] = t16[c];
+                                for (int c = 0; c < 3; ++c) A.pred[v * 3 + c] = pre[c] + A.s_out * (d[c] + bias[c]);
+                            } else if (e >= 0) {
+                                for (int c = 0; c < A.nspecies && c < 3; ++c) {
+                                    const double p = cn[c] + (double)(A.s_out * (d[c] + bias[c]));
+                                    A.xs[c][e] = isfinite(p) ? p : cn[c];   // a non-finite guess falls back to c^n
+                                }
+                            }
                         } else {
-                            float t8a[8], t8b[8];
-                            tmem_ld8(ta + 8u, t8a);
-                            tmem_ld8(ta + 16u, t8b);
-                            tc_wait_ld();
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) d[c] = t8a[4 + c];
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) d[4 + c] = t8b[c];
-                        }
-                        const int c0 = half * 12;
-                        if (on) {
-                            uint32_t o[6];
+                            uint32_t o[3];
                             if (EPI == EPI_GELU) {
-                                float zz[12];
+                                float zz[6];
 #pragma unroll
-                                for (int c = 0; c < 12; ++c) zz[c] = d[c] + bias[c];
+                                for (int c = 0; c < 6; ++c) zz[c] = d[c] + bias[c];
                                 if (A.z_out) {
-                                    float4 *zp = reinterpret_cast<float4 *>(A.z_out + v * 24 + c0);
-                                    zp[0] = make_float4(zz[0], zz[1], zz[2], zz[3]);
-                                    zp[1] = make_float4(zz[4], zz[5], zz[6], zz[7]);
-                                    zp[2] = make_float4(zz[8], zz[9], zz[10], zz[11]);
+                                    float2 *zp = reinterpret_cast<float2 *>(A.z_out + v * 24 + c0);
+                                    zp[0] = make_float2(zz[0], zz[1]);
+                                    zp[1] = make_float2(zz[2], zz[3]);
+                                    zp[2] = make_float2(zz[4], zz[5]);
                                 }
 #pragma unroll
-                                for (int c = 0; c < 6; ++c) {
+                                for (int c = 0; c < 3; ++c) {
                                     __nv_bfloat162 h = __floats2bfloat162_rn(gelu(zz[2 * c]), gelu(zz[2 * c + 1]));
                                     o[c] = *reinterpret_cast<uint32_t *>(&h);
                                 }
-                                __nv_bfloat16 *ap = A.a_out + v * 24 + c0;
-                                if (half == 0) {
-                                    *reinterpret_cast<uint4 *>(ap) = make_uint4(o[0], o[1], o[2], o[3]);
-                                    *reinterpret_cast<uint2 *>(ap + 8) = make_uint2(o[4], o[5]);
-                                } else {
-                                    *reinterpret_cast<uint2 *>(ap) = make_uint2(o[0], o[1]);
-                                    *reinterpret_cast<uint4 *>(ap + 4) = make_uint4(o[2], o[3], o[4], o[5]);
-                                }
+                                uint32_t *ap = reinterpret_cast<uint32_t *>(A.a_out + v * 24 + c0);
+                                ap[0] = o[0]; ap[1] = o[1]; ap[2] = o[2];
                             } else {   // EPI_DGRAD
-                                const float4 *zp = reinterpret_cast<const float4 *>(A.zprev + v * 24 + c0);
-                                const float4 q0 = zp[0], q1 = zp[1], q2 = zp[2];
-                                const float zq[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
-                                                      q2.x, q2.y, q2.z, q2.w};
 #pragma unroll
-                                for (int c = 0; c < 6; ++c) {
-                                    __nv_bfloat162 h = __floats2bfloat162_rn(d[2 * c] * gelu_grad(zq[2 * c]),
-                                                                             d[2 * c + 1] * gelu_grad(zq[2 * c + 1]));
+                                for (int c = 0; c < 3; ++c) {
+                                    __nv_bfloat162 h = __floats2bfloat162_rn(d[2 * c] * gelu_grad(pre[2 * c]),
+                                                                             d[2 * c + 1] * gelu_grad(pre[2 * c + 1]));
                                     o[c] = *reinterpret_cast<uint32_t *>(&h);
                                 }
-                                __nv_bfloat16 *gp = A.g_out + v * 24 + c0;
-                                if (half == 0) {
-                                    *reinterpret_cast<uint4 *>(gp) = make_uint4(o[0], o[1], o[2], o[3]);
-                                    *reinterpret_cast<uint2 *>(gp + 8) = make_uint2(o[4], o[5]);
-                                } else {
-                                    *reinterpret_cast<uint2 *>(gp) = make_uint2(o[0], o[1]);
-                                    *reinterpret_cast<uint4 *>(gp + 4) = make_uint4(o[2], o[3], o[4], o[5]);
-                                }
+                                uint32_t *gp = reinterpret_cast<uint32_t *>(A.g_out + v * 24 + c0);
+                                gp[0] = o[0]; gp[1] = o[1]; gp[2] = o[2];
                             }
                         }
                     }
@@ -532,11 +559,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                 prev_m = nmma;
                 nmma += 1;
             }
-            // the slot of depth k-1 (read by slabs k-2 .. k, all complete or
-            // issued before the wait above) -- refill it with depth k-1+kSlots
-            // (every MMA of slabs < k has been waited for by every thread)
+            // the slot of depth k-1 (read by slabs k-2 .. k-1, whose MMAs every
+            // thread has waited for) is refilled with depth k-1+kSlots
             if (!dead && k >= 1 && issued < ndep && issued == k - 1 + kSlots) {
-                load_halo_depth<CI>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT);
+                if (!mma_warp) load_halo_depth_items<CI, NL>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT, items);
                 cp_async_commit();
                 ++issued;
             }
@@ -627,22 +653,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
     uint32_t nmma = 0;
     bool ok = true;
     const int nunits = *A.nunits;
+    HaloItems<CI, kThreads> items;
+    items.init(tid, D.L[0]);
     const int gch = A.gc / 8;                     // real 8-channel chunks of g
     for (int ui = blockIdx.x; ui < nunits && ok; ui += gridDim.x) {
         const Unit u = A.units[ui];
-        load_unit_act(D, A.mask, u, act, &s_bits);
+        load_unit_act<kThreads>(D, A.mask, u, act, &s_bits);
         const uint32_t bits = s_bits;
         const int ndep = u.nz + 2;
         int issued = 0;
         for (; issued < ndep && issued < kSlots; ++issued) {
-            load_halo_depth<CI>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT);
+            load_halo_depth_items<CI, kThreads>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT, items);
             cp_async_commit();
         }
         for (int k = 0; k < u.nz && ok; ++k) {
             if ((bits >> k) & 1u) {
                 const uint32_t m = nmma, buf = m & 1u;
                 // the gradient tile buffer was last read by MMA group m - 2
-                if (m >= 2) ok = mbar_wait(&bars[buf], ((m - 2) >> 1) & 1u, A.timeout_ns, A.err);
+                if (m >= 2 && tid == 0) ok = mbar_wait(&bars[buf], ((m - 2) >> 1) & 1u, A.timeout_ns, A.err);
                 ok = __syncthreads_and(ok);
                 if (!ok) break;
                 // gradient tile of slab k: [y][ng][x][8 channels], zero where inactive
@@ -680,14 +708,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
                 nmma = m + 1;
                 // every MMA of slabs < k is complete once group m - 1 is: the
                 // ring slot of depth k - 1 may then be refilled
-                if (m >= 1) ok = mbar_wait(&bars[(m - 1) & 1u], ((m - 1) >> 1) & 1u, A.timeout_ns, A.err);
+                if (m >= 1 && tid == 0) ok = mbar_wait(&bars[(m - 1) & 1u], ((m - 1) >> 1) & 1u, A.timeout_ns, A.err);
                 ok = __syncthreads_and(ok);
             } else if (nmma >= 1) {
-                ok = mbar_wait(&bars[(nmma - 1) & 1u], ((nmma - 1) >> 1) & 1u, A.timeout_ns, A.err);
+                if (tid == 0) ok = mbar_wait(&bars[(nmma - 1) & 1u], ((nmma - 1) >> 1) & 1u, A.timeout_ns, A.err);
                 ok = __syncthreads_and(ok);
             }
             if (ok && k >= 1 && issued < ndep && issued == k - 1 + kSlots) {
-                load_halo_depth<CI>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT);
+                load_halo_depth_items<CI, kThreads>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT, items);
                 cp_async_commit();
                 ++issued;
             }
@@ -696,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
         __syncthreads();
     }
     // the last group, then the accumulators to this CTA's partial sums
-    if (ok && nmma >= 1) ok = mbar_wait(&bars[(nmma - 1) & 1u], ((nmma - 1) >> 1) & 1u, A.timeout_ns, A.err);
+    if (ok && nmma >= 1 && tid == 0) ok = mbar_wait(&bars[(nmma - 1) & 1u], ((nmma - 1) >> 1) & 1u, A.timeout_ns, A.err);
     ok = __syncthreads_and(ok);
     tc_after_sync();
     const int lq = warp & 3, half = warp >> 2;

@@ -524,6 +524,7 @@ mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat,
 mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
                                  int32_t margin, const int32_t tile[3], const mpm_opts *opt, cudaStream_t st);
 mpm_status mpm_step_wait_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_box *out_box, cudaStream_t st);
+mpm_status mpm_step_set_network_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_cnn *cnn);
 mpm_status mpm_solve_fgmres_impl(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
                                  const mpm_params *prm, const mpm_lattice *scatter_to, const mpm_opts *opt,
                                  mpm_report *rep, cudaStream_t st);

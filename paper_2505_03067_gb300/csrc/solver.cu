@@ -686,6 +686,7 @@ struct StepGraph {
     int32_t margin = 0, lt[3] = {2, 2, 2}, ldims[3] = {0, 0, 0};
     int gmax_key[3] = {-1, -1, -1};  // (precision, restart bucket, variant) of the cached grid limit
     int gmax = 0;
+    mpm_cnn *cnn = nullptr;          // the network whose prediction starts each solve (null: c^n)
 };
 
 static constexpr size_t kOutBox = 0, kOutCount = 64, kOutAbort = 128, kOutRep = 256;
@@ -750,7 +751,13 @@ static BatchSys step_sys(mpm_subgrid *sub, const mpm_lattice *lat, const mpm_par
     return S;
 }
 
-// One step on stream cs (captured or eager): the whole-step kernel.
+mpm_status mpm_cnn_enqueue_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                                 const mpm_params *prm, const BoxGeo *d_geo, cudaStream_t st);
+mpm_status mpm_cnn_check(mpm_ctx *ctx, mpm_cnn *c, const mpm_lattice *lat, const mpm_params *prm);
+
+// One step on stream cs (captured or eager): the whole-step kernel, or, with
+// a network attached, its extraction launch, the network's guess written
+// into the iterate, and its solve launch.
 static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, const mpm_lattice *lat,
                                const mpm_params *prm, int32_t margin, const mpm_opts *opt, cudaStream_t cs)
 {
@@ -817,8 +824,19 @@ static mpm_status enqueue_step(mpm_ctx *ctx, StepGraph *T, mpm_subgrid *sub, con
     A.o.exit_count = (uint32_t *)(T->d_xscr + (size_t)nb * 48 + 256);
     if (ctx->phase_prof) MPM_CU(cudaMemsetAsync(ctx->d_prof, 0, kProfSlots * sizeof(unsigned long long), cs));
     void *kargs[] = {&A};
-    MPM_CU(cudaLaunchCooperativeKernel((const void *)P.stepfn, dim3(nb), dim3(P.nt), kargs, P.smem, cs));
-    ctx->launches += 1;
+    if (!T->cnn) {
+        A.mode = STEP_WHOLE;
+        MPM_CU(cudaLaunchCooperativeKernel((const void *)P.stepfn, dim3(nb), dim3(P.nt), kargs, P.smem, cs));
+        ctx->launches += 1;
+    } else {
+        A.mode = STEP_EXTRACT;
+        MPM_CU(cudaLaunchCooperativeKernel((const void *)P.stepfn, dim3(nb), dim3(P.nt), kargs, P.smem, cs));
+        mpm_status r = mpm_cnn_enqueue_guess(ctx, T->cnn, sub, lat, prm, &d_dyn->g, cs);
+        if (r != MPM_OK) return r;
+        A.mode = STEP_SOLVE;
+        MPM_CU(cudaLaunchCooperativeKernel((const void *)P.stepfn, dim3(nb), dim3(P.nt), kargs, P.smem, cs));
+        ctx->launches += 2;
+    }
     if (ctx->phase_prof)
         MPM_CU(cudaMemcpyAsync(ctx->h_prof, ctx->d_prof, kProfSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
     return MPM_OK;
@@ -851,6 +869,10 @@ mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_latti
     if (r != MPM_OK) return r;
     if (!sub->step) sub->step = new StepGraph();
     StepGraph *T = (StepGraph *)sub->step;
+    if (T->cnn) {
+        r = mpm_cnn_check(ctx, T->cnn, lat, prm);
+        if (r != MPM_OK) return r;
+    }
     const int S = prm->nspecies;
     // buffers for the whole lattice (pointers move only when they grow)
     const void *old_geo = sub->geo, *old_elem = sub->elem;
@@ -896,6 +918,7 @@ mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_latti
         put(&sub->geo, sizeof(void *));
         put(&sub->elem, sizeof(void *));
         put(&sub->krylov, sizeof(void *));
+        put(&T->cnn, sizeof(void *));
     };
     std::vector<unsigned char> key;
     make_key(key);
@@ -1050,6 +1073,18 @@ mpm_status mpm_step_wait_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, m
     r = finish_solve(ctx, T->plan, &sub, (const SysReport *)(T->h_out + kOutRep), timed_out, ms, rep, nullptr, st);
     sub->x_fresh = false;
     return r;
+}
+
+// Attach (or detach, cnn = null) the network whose prediction starts the
+// solves of this subgrid's device-resident steps.
+mpm_status mpm_step_set_network_impl(mpm_ctx *ctx, mpm_subgrid *sub, mpm_cnn *cnn)
+{
+    if (!sub) return mpm_fail(ctx, MPM_ERR_ARG, "step_set_network: null subgrid");
+    if (!sub->step) sub->step = new StepGraph();
+    StepGraph *T = (StepGraph *)sub->step;
+    if (T->pending) return mpm_fail(ctx, MPM_ERR_ARG, "step_set_network: a step is pending (call mpm_step_wait)");
+    T->cnn = cnn;
+    return MPM_OK;
 }
 
 mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,

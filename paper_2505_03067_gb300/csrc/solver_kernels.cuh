@@ -1044,11 +1044,18 @@ struct StepOut {
     uint32_t *exit_count;          // CTAs that left; the last one copies and resets
 };
 
+// What one launch of the whole-step kernel does: the whole step, or (for a
+// step whose solve starts from another kernel's initial guess, written
+// between the two launches) its first half -- the extraction -- or its
+// second half -- the solve, the scatter and the step's results.
+enum { STEP_WHOLE = 0, STEP_EXTRACT = 1, STEP_SOLVE = 2 };
+
 struct StepArgs {
     SolveArgs sa;
     ExtractArgs xa;                // xa.bar: the grid barrier; xa.xabort == sa.abort_flag
     BatchSys S;
     StepOut o;
+    int32_t mode;                  // STEP_WHOLE, STEP_EXTRACT or STEP_SOLVE
 };
 
 // One implicit-Euler step of one lattice: the extraction phases A-E (bbox,
@@ -1069,10 +1076,21 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     // the box cadence: a full extraction unless the previous step let this one
     // keep the box (its last CTA decided; see the end of this kernel)
     const bool full = P.xa.box_every <= 1 || *(const volatile uint32_t *)&P.xa.cad->refresh_ok == 0u;
-    if (b != P.sa.skip_block) {                     // fault injection: this CTA never arrives
+    if (b != P.sa.skip_block && P.mode == STEP_EXTRACT) {
+        // the extraction alone; the kernel boundary orders it before the guess
         uint32_t epoch = 0;
-        bool ok = full ? extract_phases<NT>(P.xa, P.S, b, nb, epoch) : refresh_phases<NT>(P.xa, P.S, b, nb, epoch);
-        ok = ok && team_barrier(P.xa.bar, epoch, nb, P.xa.xabort, P.xa.timeout_ns);
+        if (full) extract_phases<NT>(P.xa, P.S, b, nb, epoch);
+        else refresh_phases<NT>(P.xa, P.S, b, nb, epoch);
+        if (prof) P.sa.prof[8] += globaltimer_ns() - t0;
+    } else if (b != P.sa.skip_block) {              // fault injection: this CTA never arrives
+        uint32_t epoch = 0;
+        bool ok = true;
+        if (P.mode == STEP_WHOLE) {
+            ok = full ? extract_phases<NT>(P.xa, P.S, b, nb, epoch) : refresh_phases<NT>(P.xa, P.S, b, nb, epoch);
+            ok = ok && team_barrier(P.xa.bar, epoch, nb, P.xa.xabort, P.xa.timeout_ns);
+        } else {
+            ok = *(volatile int32_t *)P.xa.xabort == 0;   // the extraction launch gave up
+        }
         if (prof) {
             const uint64_t t = globaltimer_ns();
             P.sa.prof[8] += t - t0;
@@ -1101,6 +1119,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     }
     __syncthreads();
     if (!s_last) return;
+    if (P.mode == STEP_EXTRACT) {
+        // the solve launch reuses the grid barrier and the exit counter
+        if (tid == 0) {
+            *P.xa.bar = 0u;
+            *P.o.exit_count = 0u;
+        }
+        return;
+    }
     int32_t *hb = reinterpret_cast<int32_t *>(P.o.host);
     unsigned long long *hc = reinterpret_cast<unsigned long long *>(P.o.host + 64);
     uint32_t *hr = reinterpret_cast<uint32_t *>(P.o.host + 256);

@@ -124,3 +124,54 @@ def evaluate_fgmres_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, steps: i
                                                        "ms_per_step": ms / steps, "max_rel_res": float(max(res)),
                                                        "final": lat.fields_numpy()}
     return out
+
+
+def train_growth(ctx: mpm.Context, wl=None, extra=None, epochs: int = 4, lr: float = 2e-3, seed: int = 7,
+                 params=None, rtol: float = 1e-10, log_every: int = 0, s_out: float = 0.01):
+    """Train a network for the growing tumour on the trajectory of another
+    instance of its geometry (workloads.growth_crop, seed 6 by default):
+    `epochs` passes over its 200 steps; every step the tumour grows, the
+    step's box (the allocation-free bounding box) and the features of c^n
+    are loaded, the FP64 solver advances the lattice to c^{n+1} (rtol 1e-10,
+    the target) and one Adam step follows.  Returns (CNN, history)."""
+    import torch
+    if wl is None:
+        wl, extra = W.growth_crop()
+    lat = mpm.DeviceLattice(wl.lattice)
+    prm = mpm.DeviceParams(wl.params)
+    init = lat.fields.clone()
+    cand = torch.from_numpy(np.ascontiguousarray(extra["cand"])).cuda()
+    labels = torch.from_numpy(extra["labels"].astype(np.int64)).cuda()
+    cnn = mpm.CNN(ctx, wl.lattice.dims, 1, mpm.cnn_init_params(seed) if params is None else params, s_out=s_out,
+                  train=True)
+    solver = mpm.StepSolver(ctx, lat, prm, wl.margin)
+    opts = mpm.make_opts(rtol=rtol, restart=16, maxit=500)
+    out_box = torch.zeros(8, dtype=torch.int32, device="cuda")
+    hist = []
+    t0 = time.time()
+    n_total = epochs * wl.steps
+    it = 0
+    for ep in range(epochs):
+        lat.fields.copy_(init)
+        for t in range(wl.steps):
+            lo, hi = W.growth_box(t, wl.steps)
+            lo, hi = lo - np.array(extra["origin"], float), hi - np.array(extra["origin"], float)
+            inside = np.all((extra["seeds"] >= lo) & (extra["seeds"] < hi), axis=1)
+            ids = torch.from_numpy(np.where(inside, np.arange(1, len(inside) + 1), 0).astype(np.int32)).cuda()
+            lat.cell_id.view(-1)[cand] = ids[labels]
+            st = mpm.mpm_box_bounds_noalloc(lat.cell_id, wl.margin, out_box)
+            if st != mpm.OK:
+                raise mpm.MpmError(st, "mpm_box_bounds_noalloc failed")
+            o = out_box.cpu().numpy().tolist()
+            if not o[6]:
+                continue
+            box = (tuple(o[0:3]), tuple(o[3:6]))
+            cnn.load_image(0, lat, prm, box, mpm.CNN_INPUT)
+            solver.step(opts)
+            cnn.load_image(0, lat, prm, box, mpm.CNN_TARGET)
+            lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * it / n_total))
+            hist.append(cnn.train_step(1, lr_t))
+            it += 1
+            if log_every and it % log_every == 0:
+                print(f"epoch {ep} step {t} loss {hist[-1]:.3e} ({time.time() - t0:.1f} s)", flush=True)
+    return cnn, {"loss": hist, "seconds": time.time() - t0, "samples": it}

@@ -33,7 +33,7 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
            "mpm_cnn_get_params", "mpm_cnn_load_image", "mpm_cnn_export_features", "mpm_cnn_export_preact", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
            "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond",
-           "mpm_step_host", "mpm_debug_convert"]
+           "mpm_step_host", "mpm_debug_convert", "mpm_step_set_network"]
 
 
 class mpm_box(C.Structure):
@@ -151,6 +151,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_counter_get": [P, C.c_int32, C.POINTER(C.c_int64)],
         "mpm_box_bounds_noalloc": [P, C.POINTER(C.c_int32), C.c_int32, P, P],
         "mpm_debug_convert": [P, P, P, P, P, P, C.c_int64, P],
+        "mpm_step_set_network": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -567,6 +568,13 @@ class StepSolver:
         self.ctx, self.lat, self.prm, self.margin, self.tile = ctx, lat, prm, margin, tile
         self.fused = fused
         self.sub = ctx.subgrid_create()
+
+    def set_network(self, cnn: "CNN | None"):
+        """Start every later device-resident step's solve from the network's
+        prediction (mpm_step_set_network); None: from c^n."""
+        self.cnn = cnn
+        self.ctx._check(self.ctx.lib.mpm_step_set_network(self.ctx.ptr, self.sub.h, cnn.h if cnn is not None else None),
+                        "mpm_step_set_network")
 
     def step_async(self, opts: mpm_opts, stream=None):
         """Queue one device-resident step (read the result with wait())."""

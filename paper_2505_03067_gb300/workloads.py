@@ -289,9 +289,38 @@ def growth512(seed: int = 5, mean_cell: float = 200.0, dims=GROWTH_DIMS):
     return wl, extra
 
 
+def growth_crop(seed: int = 6, mean_cell: float = 200.0):
+    """Another instance of the growing-tumour geometry (another seed: other
+    Voronoi cells and rates) cut to its final growth region plus the margin,
+    324x264x264 voxels: every step's bounding box lies inside the crop and is
+    the full 512x384x384 lattice's box moved by the crop origin (the tumour
+    never comes nearer a crop face than the margin, except at the lattice's
+    own +x face, which the crop keeps).  Returns (workload, extra) like
+    growth512; extra["cand"] indexes the crop.  This is the learned warm
+    start's training trajectory for the growing tumour."""
+    wl, extra = growth512(seed=seed, mean_cell=mean_cell)
+    (fx, fy, fz), (sx, sy, sz) = GROWTH_FINAL
+    m = wl.margin
+    lx, ly, lz = GROWTH_DIMS
+    lo = (max(0, fx - m), max(0, fy - m), max(0, fz - m))
+    hi = (min(lx, fx + sx + m), min(ly, fy + sy + m), min(lz, fz + sz + m))
+    sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    lat = wl.lattice
+    crop = Lattice(np.ascontiguousarray(lat.cell_id[sl]), np.ascontiguousarray(lat.mask[sl]),
+                   np.ascontiguousarray(lat.fields[(slice(None),) + sl]))
+    zz, yy, xx = np.unravel_index(extra["cand"], lat.cell_id.shape)
+    nx, ny = hi[0] - lo[0], hi[1] - lo[1]
+    cand = ((zz - lo[2]) * ny + (yy - lo[1])) * nx + (xx - lo[0])
+    seeds = extra["seeds"] - np.array(lo, float)
+    cw = Workload("growth_crop", crop, wl.params, margin=m, steps=wl.steps, rtol=wl.rtol, restart=wl.restart)
+    return cw, {"seeds": seeds, "labels": extra["labels"], "cand": cand, "origin": lo}
+
+
 def grow(wl: Workload, t: int, extra) -> None:
     """Mark as tumour (id = cell index + 1) every cell whose seed lies in growth_box(t)."""
     lo, hi = growth_box(t, wl.steps)
+    if "origin" in extra:
+        lo, hi = lo - np.array(extra["origin"], float), hi - np.array(extra["origin"], float)
     s = extra["seeds"]
     inside = np.all((s >= lo) & (s < hi), axis=1)
     ids = np.where(inside, np.arange(1, len(s) + 1, dtype=np.int32), 0).astype(np.int32)
