@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -547,6 +548,8 @@ struct mpm_cnn {
     float *partials = nullptr;
     CnnDom *dom = nullptr;
     Unit *units = nullptr;
+    uint8_t *uact = nullptr;         // [units][kActStride] activity bytes of each listed unit
+    uint32_t *ubits = nullptr;       // [units] its active slabs
     long long max_units = 0;
     uint8_t *flags = nullptr;
     int32_t *counters = nullptr;     // [0] listed units, [1..15] work counters
@@ -582,18 +585,33 @@ mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t
     static bool attr = false;
     constexpr int smem = tc::ConvSmem<CI, NO>::BYTES;
     if (!attr) {
-        cudaFuncSetAttribute(tc::k_conv_tc<CI, NO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const cudaError_t e =
+            cudaFuncSetAttribute(tc::k_conv_tc<CI, NO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return mpm_cuda_check(ctx, e, "cnn convolution: shared-memory attribute");
         attr = true;
     }
     A.dom = c->dom;
     A.units = c->units;
     A.nunits = c->counters;
+    A.uact = c->uact;
+    A.ubits = c->ubits;
     A.work = c->counters + slot;
     A.err = c->d_err;
     A.timeout_ns = ctx->timeout_ns;
     tc::k_conv_tc<CI, NO, EPI><<<ctx->num_sms, tc::kConvThreads, smem, st>>>(A);
     ctx->launches += 1;
-    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn convolution");
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFuncAttributes fa;
+        memset(&fa, 0, sizeof(fa));
+        cudaFuncGetAttributes(&fa, tc::k_conv_tc<CI, NO, EPI>);
+        char msg[256];
+        snprintf(msg, sizeof(msg), "cnn convolution (%d threads, %d B shared; kernel: max %d threads, %d registers, "
+                 "%zu B static shared, %d B dynamic allowed)", tc::kConvThreads, smem, fa.maxThreadsPerBlock,
+                 fa.numRegs, fa.sharedSizeBytes, fa.maxDynamicSharedSizeBytes);
+        return mpm_cuda_check(ctx, e, msg);
+    }
+    return MPM_OK;
 }
 
 template <int CI, int NO>
@@ -615,6 +633,8 @@ mpm_status wgrad(mpm_ctx *ctx, mpm_cnn *c, const __nv_bfloat16 *in, const __nv_b
     A.dom = c->dom;
     A.units = c->units;
     A.nunits = c->counters;
+    A.uact = c->uact;
+    A.ubits = c->ubits;
     A.partials = c->partials;
     A.err = c->d_err;
     A.timeout_ns = ctx->timeout_ns;
@@ -649,6 +669,15 @@ mpm_status check_err(mpm_ctx *ctx, mpm_cnn *c)
     return MPM_OK;
 }
 
+// The listed units' activity bytes and slab masks (once per application,
+// for all six layers and the backward pass).
+mpm_status unit_act(mpm_ctx *ctx, mpm_cnn *c, const uint8_t *mask, cudaStream_t st)
+{
+    tc::k_unit_act<<<ctx->num_sms * 4, 256, 0, st>>>(c->dom, mask, c->units, c->counters, c->uact, c->ubits);
+    ctx->launches += 1;
+    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn unit activity");
+}
+
 // Image mode plan over images 0..nimg-1 (their boxes as loaded).
 mpm_status plan_images(mpm_ctx *ctx, mpm_cnn *c, int nimg, cudaStream_t st)
 {
@@ -659,7 +688,8 @@ mpm_status plan_images(mpm_ctx *ctx, mpm_cnn *c, int nimg, cudaStream_t st)
     k_plan_flags<<<ctx->num_sms * 4, 256, 0, st>>>(D, c->mask, ncand, c->flags);
     k_plan_compact<<<1, 1024, 0, st>>>(D, c->flags, ncand, c->units, c->counters, c->dom);
     ctx->launches += 2;
-    return mpm_cuda_check(ctx, cudaGetLastError(), "cnn plan");
+    MPM_CU(cudaGetLastError());
+    return unit_act(ctx, c, c->mask, st);
 }
 
 // The six layers.  Inference (train = false): activations ping-pong in a[0],
@@ -779,6 +809,8 @@ extern "C" mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **out, const int32_t 
     }
     A((void **)&c->dom, sizeof(CnnDom));
     A((void **)&c->units, (size_t)c->max_units * sizeof(Unit));
+    A((void **)&c->uact, (size_t)c->max_units * tc::kActStride);
+    A((void **)&c->ubits, (size_t)c->max_units * sizeof(uint32_t));
     A((void **)&c->flags, (size_t)c->max_units);
     A((void **)&c->counters, 64 * sizeof(int32_t));
     A((void **)&c->geo, 256);
@@ -1011,6 +1043,9 @@ mpm_status mpm_cnn_enqueue_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, con
     MPM_CU(cudaMemsetAsync(c->counters, 0, 16 * sizeof(int32_t), st));
     k_plan_box<<<ctx->num_sms, 256, 0, st>>>(d_geo, sub->tile_index, lat->dims[0], lat->dims[1], lat->dims[2], c->units,
                                              c->counters, c->dom);
+    ctx->launches += 1;
+    mpm_status ra = unit_act(ctx, c, lat->mask, st);
+    if (ra != MPM_OK) return ra;
     FeatUnits FU;
     memset(&FU, 0, sizeof(FU));
     FU.F = feat_src(lat, prm);
@@ -1020,7 +1055,7 @@ mpm_status mpm_cnn_enqueue_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, con
     FU.nunits = c->counters;
     FU.x = c->x;
     k_feat_units<<<ctx->num_sms * 8, 256, 0, st>>>(FU);
-    ctx->launches += 2;
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
     tc::ConvArgs O;
     memset(&O, 0, sizeof(O));
@@ -1085,6 +1120,9 @@ mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, cons
     MPM_CU(cudaMemsetAsync(c->counters, 0, 16 * sizeof(int32_t), st));
     k_plan_box<<<ctx->num_sms, 256, 0, st>>>(c->geo, sub->tile_index, lat->dims[0], lat->dims[1], lat->dims[2],
                                              c->units, c->counters, c->dom);
+    ctx->launches += 1;
+    r = unit_act(ctx, c, lat->mask, st);
+    if (r != MPM_OK) return r;
     FeatUnits FU;
     memset(&FU, 0, sizeof(FU));
     FU.F = feat_src(lat, prm);
@@ -1100,7 +1138,7 @@ mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, cons
     FU.geo = c->geo;
     FU.tile_index = sub->tile_index;
     k_feat_units<<<ctx->num_sms * 8, 256, 0, st>>>(FU);
-    ctx->launches += 3;
+    ctx->launches += 2;
     MPM_CU(cudaGetLastError());
     // image-mode output (pred = field channels + s_out z6) on the lattice-indexed buffer
     tc::ConvArgs O;

@@ -51,9 +51,20 @@ constexpr int kSlabX = 8, kSlabY = 16, kZSeg = 8;
 constexpr int kHaloX = kSlabX + 2, kHaloY = kSlabY + 2;
 constexpr int kSlots = 6;               // halo depths in the shared-memory ring
 constexpr int kThreads = 256;           // weight-gradient kernel: 8 warps
-constexpr int kEpiWarps = 16;           // forward kernel: 16 epilogue / loader warps ...
-constexpr int kConvThreads = 32 * (kEpiWarps + 1);   // ... and one warp that issues the MMAs
+// forward kernel: 12 epilogue warps, 4 loader warps and one warp that issues the
+// MMAs (17 warps: at most 5 on each SM sub-partition, whose register file
+// holds 16 Ki registers)
+constexpr int kEpiWarps = 12, kLoadWarps = 4;
+constexpr int kConvThreads = 32 * (kEpiWarps + kLoadWarps + 1);
+constexpr int kFwdSlots = 7;            // halo depths in the forward kernel's ring
+constexpr int kAcc = 4;                 // TMEM accumulators (32 columns each)
 constexpr int kMaxImages = 16;
+// Activity bytes of a unit's halo region (depths z0-1 .. z0+kZSeg, rows
+// oy-1 .. oy+16, columns ox-1 .. ox+8: in its image's box and mask set),
+// kActStride bytes per unit, and the unit's active slabs (bit k: slab z0+k),
+// computed once per network application by k_unit_act.
+constexpr int kActBytes = (kZSeg + 2) * kHaloY * kHaloX;
+constexpr int kActStride = (kActBytes + 15) & ~15;
 
 // Device-side description of the images a network application covers.
 struct CnnDom {
@@ -112,6 +123,18 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                  : "=r"(ok)
                  : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about `ns` nanoseconds passed, instead of spinning.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
                  : "memory");
     return ok != 0;
 }
@@ -225,11 +248,14 @@ template <int CI, int NO>
 struct ConvSmem {
     static constexpr int W_OFF = 0;
     static constexpr int RING_OFF = (WImg<CI, NO>::BYTES + 1023) & ~1023;
-    static constexpr int RING_BYTES = kSlots * Halo<CI>::SLOT;
-    static constexpr int ACT_OFF = RING_OFF + RING_BYTES + 2048;   // 2 KB guard after the ring
-    static constexpr int ACT_BYTES = (kZSeg + 2) * kHaloY * kHaloX;
-    static constexpr int BAR_OFF = (ACT_OFF + ACT_BYTES + 15) & ~15;
-    static constexpr int BYTES = BAR_OFF + 64;
+    static constexpr int RING_BYTES = kFwdSlots * Halo<CI>::SLOT;
+    static constexpr int ACT_BYTES = kActStride;
+    static constexpr int ACT_OFF = RING_OFF + RING_BYTES;          // two units' activity bytes
+    static constexpr int UNIT_OFF = (ACT_OFF + 2 * ACT_BYTES + 15) & ~15;   // two Units + two slab masks
+    // mbarriers: full[slots], empty[slots], acc_full[kAcc], acc_empty[kAcc], unit_full[2], unit_empty[2]
+    static constexpr int BAR_OFF = (UNIT_OFF + 2 * 32 + 2 * 4 + 15) & ~15;
+    static constexpr int NBAR = 2 * kFwdSlots + 2 * kAcc + 4;
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
 };
 
 enum { EPI_GELU = 0, EPI_OUT = 1, EPI_DGRAD = 2 };
@@ -240,6 +266,8 @@ struct ConvArgs {
     const CnnDom *dom;
     const Unit *units;
     const int32_t *nunits;
+    const uint8_t *uact;            // [units][kActStride]
+    const uint32_t *ubits;          // [units]
     int32_t *work;                  // dynamic scheduling counter (reset by the plan)
     const unsigned char *wimg;      // weight image (WImg layout)
     const float *bias;              // [NO] (null: none)
@@ -273,43 +301,22 @@ __device__ __forceinline__ bool in_box(const CnnDom &D, int b, int x, int y, int
            z >= D.lo[b][2] && z < D.lo[b][2] + D.n[b][2];
 }
 
-// Active bytes of a unit's halo region (depths z0-1 .. z0+kZSeg, rows
-// oy-1 .. oy+16, columns ox-1 .. ox+8) into smem; returns per-slab activity
-// in the low kZSeg bits (through *slab_bits, all threads).
-template <int NTHR>
-__device__ __forceinline__ void load_unit_act(const CnnDom &D, const uint8_t *__restrict__ mask, const Unit &u,
-                                              uint8_t *act, uint32_t *slab_bits)
-{
-    if (threadIdx.x == 0) *slab_bits = 0u;
-    __syncthreads();
-    constexpr int N = (kZSeg + 2) * kHaloY * kHaloX;
-    uint32_t mine = 0u;
-    for (int i = threadIdx.x; i < N; i += NTHR) {
-        const int xh = i % kHaloX, r = i / kHaloX;
-        const int yh = r % kHaloY, j = r / kHaloY;
-        const int x = u.ox - 1 + xh, y = u.oy - 1 + yh, z = u.z0 - 1 + j;
-        uint8_t a = 0;
-        if (in_box(D, u.b, x, y, z)) a = __ldg(mask + vox_index(D, u.b, x, y, z)) != 0;
-        act[i] = a;
-        if (a && xh >= 1 && xh <= kSlabX && yh >= 1 && yh <= kSlabY && j >= 1 && j <= u.nz) mine |= 1u << (j - 1);
-    }
-    if (mine) atomicOr(slab_bits, mine);
-    __syncthreads();
-}
-
 // The 16-byte copies of one halo depth handled by one loader thread, fixed for
 // a launch: the k-th covers item tid + k NL of the depth (halo row yh, copy c,
 // x row, channel chunk kc); `rel` is its source offset in elements from the
-// depth's halo origin, `dst` its shared offset in the slot, `act` its index in
-// a depth of the unit's activity bytes (act < 0: no item).
+// depth's halo origin; `da` packs its shared offset in the slot (low 16 bits)
+// and its index in a depth of the unit's activity bytes (bits 16..23; 255: no
+// item).
 template <int CI, int NL>
 struct HaloItems {
     static constexpr int N = kHaloY * 3 * kSlabX * (CI / 8);
     static constexpr int K = (N + NL - 1) / NL;
-    int32_t rel[K], dst[K], act[K];
+    int32_t rel[K];
+    uint32_t da[K];
     __device__ __forceinline__ void init(int tid, int L0)
     {
         using H = Halo<CI>;
+        static_assert(kHaloY * kHaloX < 255 && Halo<CI>::SLOT < 65536, "packed halo item");
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int i = tid + k * NL;
@@ -320,8 +327,8 @@ struct HaloItems {
             const int c = r % 3, yh = r / 3;
             const int xh = x + c;
             rel[k] = (yh * L0 + xh) * CI + kc * 8;
-            dst[k] = yh * H::GS + (c * H::KC + kc) * 128 + x * 16;
-            act[k] = i < N ? yh * kHaloX + xh : -1;
+            const uint32_t dst = (uint32_t)(yh * H::GS + (c * H::KC + kc) * 128 + x * 16);
+            da[k] = dst | ((i < N ? (uint32_t)(yh * kHaloX + xh) : 255u) << 16);
         }
     }
 };
@@ -340,134 +347,296 @@ __device__ __forceinline__ void load_halo_depth_items(const CnnDom &D, const __n
     const int64_t base = (((int64_t)u.b * D.L[2] + (u.z0 - 1 + j)) * D.L[1] + (u.oy - 1)) * (int64_t)D.L[0] + (u.ox - 1);
 #pragma unroll
     for (int k = 0; k < HaloItems<CI, NL>::K; ++k) {
-        if (it.act[k] < 0) continue;
-        const bool ok = aj[it.act[k]] != 0;
+        const uint32_t ai = it.da[k] >> 16;
+        if (ai == 255u) continue;
+        const bool ok = aj[ai] != 0;
         const __nv_bfloat16 *src = ok ? in + (base * CI + it.rel[k]) : in;
-        cp_async16(dst + (uint32_t)it.dst[k], src, ok ? 16u : 0u);
+        cp_async16(dst + (it.da[k] & 0xFFFFu), src, ok ? 16u : 0u);
     }
 }
 
+// One CTA per listed unit (grid-strided): its activity bytes and slab mask.
+__global__ void __launch_bounds__(256) k_unit_act(const CnnDom *__restrict__ dom, const uint8_t *__restrict__ mask,
+                                                  const Unit *__restrict__ units, const int32_t *__restrict__ nunits,
+                                                  uint8_t *__restrict__ uact, uint32_t *__restrict__ ubits)
+{
+    __shared__ uint32_t s_bits;
+    const CnnDom &D = *dom;
+    const int nu = *nunits;
+    for (int ui = blockIdx.x; ui < nu; ui += gridDim.x) {
+        if (threadIdx.x == 0) s_bits = 0u;
+        __syncthreads();
+        const Unit u = units[ui];
+        uint32_t mine = 0u;
+        for (int i = threadIdx.x; i < kActStride; i += blockDim.x) {
+            uint8_t a = 0;
+            if (i < kActBytes) {
+                const int xh = i % kHaloX, r = i / kHaloX;
+                const int yh = r % kHaloY, j = r / kHaloY;
+                const int x = u.ox - 1 + xh, y = u.oy - 1 + yh, z = u.z0 - 1 + j;
+                if (in_box(D, u.b, x, y, z)) a = __ldg(mask + vox_index(D, u.b, x, y, z)) != 0;
+                if (a && xh >= 1 && xh <= kSlabX && yh >= 1 && yh <= kSlabY && j >= 1 && j <= u.nz)
+                    mine |= 1u << (j - 1);
+            }
+            uact[(size_t)ui * kActStride + i] = a;
+        }
+        if (mine) atomicOr(&s_bits, mine);
+        __syncthreads();
+        if (threadIdx.x == 0) ubits[ui] = s_bits;
+    }
+}
+
+// Copy a unit's activity bytes into shared memory (threads 0..NT-1 of the
+// caller's group, one 16-byte load each at most); the caller syncs.
+template <int NT>
+__device__ __forceinline__ void copy_unit_act(const uint8_t *__restrict__ uact, int ui, uint8_t *act, int t)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(uact + (size_t)ui * kActStride);
+    for (int i = t; i < kActStride / 16; i += NT) reinterpret_cast<uint4 *>(act)[i] = __ldg(src + i);
+}
+
 // ---------------------------------------------------------------- forward / input-gradient convolution
-// One persistent CTA per SM; units are taken from the plan's list through an
-// atomic counter.  NO: MMA N (output channels padded to 16 or 32).  Warps
-// 0..15 load the halo depths and run the epilogue (warp w: TMEM lane quarter
-// w & 3, channels 6 (w >> 2) .. 6 (w >> 2) + 5); warp 16 issues the MMAs, so
-// a slab's MMAs overlap the previous slab's epilogue.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Arrive on an mbarrier once every cp.async this thread issued so far has
+// landed (the arrival counts toward the phase's expected count).
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Bounded wait that also gives up once another role of the CTA gave up (*abort).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, uint64_t timeout_ns, int32_t *err,
+                                                   volatile int32_t *abort)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_sleep(bar, parity, 20000u)) return true;
+        if (*abort) return false;
+        if (globaltimer_ns() - t0 > timeout_ns) {
+            if (err) atomicExch(err, 1);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// One persistent CTA per SM over the units i = blockIdx, blockIdx + gridDim,
+// ... of the plan's list, as a pipeline of three roles that meet only at
+// mbarriers (no CTA-wide barrier in the steady state):
+//  - 4 LOADER warps stage, per unit, its activity bytes and slab mask (one of
+//    two unit buffers) and then its halo depths into a ring of kFwdSlots
+//    slots (cp.async; a slot's mbarrier completes when every loader's copies
+//    into it have landed; a slot is refilled once the MMAs that read it
+//    completed);
+//  - 1 MMA warp (one thread) issues, per active slab, 9 taps x (K/16) MMAs
+//    into one of kAcc TMEM accumulators and commits them; it releases a ring
+//    slot by a commit once the last slab reading it was issued;
+//  - 12 EPILOGUE warps (warp w: TMEM lane quarter w & 3, channels
+//    8 (w >> 2) .. 8 (w >> 2) + 7) drain each accumulator through the
+//    epilogue and hand it back.
+// NO: MMA N (output channels padded to 16 or 32).
 template <int CI, int NO, int EPI>
-__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ ConvArgs A)
+__global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
 {
     using H = Halo<CI>;
     using S = ConvSmem<CI, NO>;
     constexpr int NG = WImg<CI, NO>::NG;
-    constexpr int NL = 32 * kEpiWarps;            // loader / epilogue threads
+    constexpr int NE = 32 * kEpiWarps;            // epilogue threads: 0 .. NE-1
+    constexpr int NLD = 32 * kLoadWarps;          // loader threads: NE .. NE+NLD-1
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint32_t s_tmem, s_bits;
-    __shared__ int32_t s_unit;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);   // [0], [1]: MMA done per accumulator
-    uint8_t *act = sm + S::ACT_OFF;
+    __shared__ uint32_t s_tmem;
+    __shared__ int32_t s_abort, s_lstop;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);
+    uint64_t *full = bar, *empty = bar + kFwdSlots, *accf = bar + 2 * kFwdSlots, *acce = accf + kAcc;
+    uint64_t *unitf = acce + kAcc, *unite = unitf + 2;
+    Unit *urec = reinterpret_cast<Unit *>(sm + S::UNIT_OFF);
+    uint32_t *ubits = reinterpret_cast<uint32_t *>(sm + S::UNIT_OFF + 64);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool mma_warp = warp == kEpiWarps;
     const CnnDom &D = *A.dom;
     const uint32_t wbase = smem_u32(sm + S::W_OFF), rbase = smem_u32(sm + S::RING_OFF);
+    volatile int32_t *abort = &s_abort;
 
     // weights into shared memory; zero the ring (pad K-columns stay zero)
     for (int i = tid; i < WImg<CI, NO>::BYTES / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(sm + S::W_OFF)[i] = __ldg(reinterpret_cast<const uint4 *>(A.wimg) + i);
-    for (int i = tid; i < (S::RING_BYTES + 2048) / 16; i += kConvThreads)
+    for (int i = tid; i < S::RING_BYTES / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(sm + S::RING_OFF)[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (warp == 0) tmem_alloc(&s_tmem, 64);
+    if (warp == 0) tmem_alloc(&s_tmem, 128);
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        s_abort = 0;
+        s_lstop = 0;
+        for (int i = 0; i < kFwdSlots; ++i) {
+            mbar_init(&full[i], NLD);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < kAcc; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], kEpiWarps);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&unitf[i], 1);
+            mbar_init(&unite[i], kEpiWarps + 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = s_tmem;
-    constexpr uint32_t kIdesc = idesc_bf16(128, NO, false, false);
-    // descriptors of the ring and weight bases; a tap's operands are these
-    // plus an offset (start-address field in 16-byte units)
-    const uint64_t adesc0 = sdesc(rbase, 128u, H::GS), bdesc0 = sdesc(wbase, NG * 128u, 128u);
-    // epilogue role
-    const int lq = warp & 3, wq = (warp >> 2) & 3;
-    const int row = lq * 32 + lane;               // voxel (row & 7, row >> 3) of the slab
-    const int ex = row & 7, ey = row >> 3;
-    const int c0 = 6 * wq;                        // first channel of this thread
-    const bool epi = !mma_warp && (EPI != EPI_OUT || wq == 0);
-    HaloItems<CI, NL> items;
-    items.init(mma_warp ? 0 : tid, D.L[0]);
-    float bias[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) bias[i] = 0.0f;
-    if (A.bias && EPI != EPI_DGRAD) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-            if (EPI != EPI_OUT || i < 3) bias[i] = A.bias[c0 + i];
-    }
-    uint32_t nmma = 0;                            // MMA groups issued (accumulator = nmma & 1)
     const int nunits = *A.nunits;
-    bool dead = false;
-    for (;;) {
-        if (tid == 0) s_unit = atomicAdd(A.work, 1);
-        __syncthreads();
-        const int ui = s_unit;
-        if (ui >= nunits || dead) break;
-        const Unit u = A.units[ui];
-        load_unit_act<kConvThreads>(D, A.mask, u, act, &s_bits);
-        const uint32_t bits = s_bits;
-        // depths 0 .. u.nz + 1; prefetch the first kSlots
-        const int ndep = u.nz + 2;
-        int issued = 0;
-        for (; issued < ndep && issued < kSlots; ++issued) {
-            if (!mma_warp) load_halo_depth_items<CI, NL>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT, items);
-            cp_async_commit();
-        }
-        int prev_k = -1;                          // slab whose epilogue is pending
-        uint32_t prev_m = 0;
-        for (int k = 0; k <= u.nz && !dead; ++k) {
-            const bool have = k < u.nz && ((bits >> k) & 1u);
-            if (k < u.nz) {
-                // depths k, k+1, k+2 (slices z-1, z, z+1) must have landed
-                cp_async_wait(issued - (k + 3) < 0 ? 0 : issued - (k + 3));
-                fence_async_smem();
-                tc_before_sync();
-                __syncthreads();
-                tc_after_sync();
-                if (have && mma_warp && lane == 0) {
-                    const uint32_t dt = tmem + (nmma & 1u) * 32u;
-#pragma unroll
-                    for (int p = 0; p < 9; ++p) {
-                        const int dy = p % 3 - 1, dz = p / 3 - 1;
-                        const uint32_t slot = (uint32_t)((k + 1 + dz) % kSlots);
-                        const uint64_t a = adesc0 + ((slot * H::SLOT + (uint32_t)(dy + 1) * H::GS) >> 4);
-                        const uint64_t b = bdesc0 + ((uint32_t)p * H::QP * NG * 128u >> 4);
-#pragma unroll
-                        for (int s2 = 0; s2 < H::NKS; ++s2)
-                            mma_bf16(dt, a + (uint64_t)(s2 * 16), b + (uint64_t)(s2 * NG * 16), kIdesc,
-                                     (p | s2) != 0);
-                    }
-                    mma_commit(&bars[nmma & 1u]);
-                }
+    const uint64_t T = A.timeout_ns;
+
+    if (tid >= NE && tid < NE + NLD) {
+        // ------------------------------------------------------------ loaders
+        // Loader thread 0 alone waits on the mbarriers and publishes the
+        // outcome (s_lstop) before a named barrier, so every decision of the
+        // loader warps is uniform.
+        const int lt = tid - NE;
+        HaloItems<CI, NLD> items;
+        items.init(lt, D.L[0]);
+        uint32_t dseq = 0;                        // depths issued
+        for (int n = 0;; ++n) {
+            const int ui = blockIdx.x + n * gridDim.x;
+            if (ui >= nunits) break;
+            const int ub = n & 1;
+            if (lt == 0) {
+                const bool w = n < 2 || mbar_wait_or_abort(&unite[ub], ((n >> 1) - 1) & 1, T, A.err, abort);
+                if (!w || *abort) s_lstop = 1;
             }
-            // epilogue of the previous active slab
-            if (prev_k >= 0) {
-                const uint32_t buf = prev_m & 1u, par = (prev_m >> 1) & 1u;
-                const int z = u.z0 + prev_k;
-                const int x = u.ox + ex, y = u.oy + ey;
-                const bool on = epi && act[((prev_k + 1) * kHaloY + ey + 1) * kHaloX + ex + 1] != 0;
+            named_sync(1, NLD);
+            if (s_lstop) break;
+            const Unit u = A.units[ui];
+            uint8_t *act = sm + S::ACT_OFF + ub * S::ACT_BYTES;
+            copy_unit_act<NLD>(A.uact, ui, act, lt);
+            if (lt == 0) ubits[ub] = A.ubits[ui];
+            named_sync(1, NLD);
+            if (lt == 0) {
+                urec[ub] = u;
+                mbar_arrive(&unitf[ub]);
+            }
+            for (int j = 0; j < u.nz + 2; ++j) {
+                const uint32_t slot = dseq % kFwdSlots, use = dseq / kFwdSlots;
+                if (lt == 0 && use >= 1 && !mbar_wait_or_abort(&empty[slot], (use - 1) & 1, T, A.err, abort))
+                    s_lstop = 1;
+                named_sync(1, NLD);
+                if (s_lstop) break;
+                load_halo_depth_items<CI, NLD>(D, A.in, u, act, j, rbase + slot * H::SLOT, items);
+                cp_async_arrive(&full[slot]);   // completes the slot's phase once the copies land
+                ++dseq;
+            }
+            if (s_lstop) break;
+        }
+        cp_async_wait(0);
+    } else if (warp == kEpiWarps + kLoadWarps) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            constexpr uint32_t kIdesc = idesc_bf16(128, NO, false, false);
+            const uint64_t adesc0 = sdesc(rbase, 128u, H::GS), bdesc0 = sdesc(wbase, NG * 128u, 128u);
+            uint32_t dbase = 0, m = 0;
+            bool ok = true;
+            for (int n = 0; ok; ++n) {
+                const int ui = blockIdx.x + n * gridDim.x;
+                if (ui >= nunits) break;
+                const int ub = n & 1;
+                ok = mbar_wait_or_abort(&unitf[ub], (n >> 1) & 1, T, A.err, abort);
+                if (!ok) break;
+                const int nz = urec[ub].nz;
+                const uint32_t bits = ubits[ub];
+                for (int k = 0; k < nz && ok; ++k) {
+                    // slab k reads depths k, k+1, k+2; k+2 is the newest
+                    for (int j = (k == 0 ? 0 : k + 2); j <= k + 2 && ok; ++j) {
+                        const uint32_t d = dbase + j;
+                        ok = mbar_wait_or_abort(&full[d % kFwdSlots], (d / kFwdSlots) & 1, T, A.err, abort);
+                    }
+                    if (!ok) break;
+                    fence_async_smem();
+                    if ((bits >> k) & 1u) {
+                        const uint32_t b = m % kAcc, use = m / kAcc;
+                        if (use >= 1) ok = mbar_wait_or_abort(&acce[b], (use - 1) & 1, T, A.err, abort);
+                        if (!ok) break;
+                        tc_after_sync();
+                        const uint32_t dt = tmem + b * 32u;
+#pragma unroll
+                        for (int p = 0; p < 9; ++p) {
+                            const int dy = p % 3 - 1, dz = p / 3 - 1;
+                            const uint32_t slot = (dbase + k + 1 + dz) % kFwdSlots;
+                            const uint64_t a = adesc0 + ((slot * H::SLOT + (uint32_t)(dy + 1) * H::GS) >> 4);
+                            const uint64_t bb = bdesc0 + ((uint32_t)p * H::QP * NG * 128u >> 4);
+#pragma unroll
+                            for (int s2 = 0; s2 < H::NKS; ++s2)
+                                mma_bf16(dt, a + (uint64_t)(s2 * 16), bb + (uint64_t)(s2 * NG * 16), kIdesc,
+                                         (p | s2) != 0);
+                        }
+                        mma_commit(&accf[b]);
+                        ++m;
+                    }
+                    // depth k is read by no later slab of the unit
+                    mma_commit(&empty[(dbase + k) % kFwdSlots]);
+                }
+                if (!ok) break;
+                mma_commit(&empty[(dbase + nz) % kFwdSlots]);
+                mma_commit(&empty[(dbase + nz + 1) % kFwdSlots]);
+                dbase += nz + 2;
+                mbar_arrive(&unite[ub]);
+            }
+        }
+        __syncwarp();
+    } else if (tid < NE) {
+        // ------------------------------------------------------------ epilogue
+        const int lq = warp & 3, wq = warp >> 2;
+        const int row = lq * 32 + lane;           // voxel (row & 7, row >> 3) of the slab
+        const int ex = row & 7, ey = row >> 3;
+        const int c0 = 8 * wq;                    // first channel of this thread
+        const bool reads = EPI != EPI_OUT || wq == 0;
+        float bias[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bias[i] = 0.0f;
+        if (A.bias && EPI != EPI_DGRAD) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (EPI != EPI_OUT || i < 3) bias[i] = A.bias[c0 + i];
+        }
+        uint32_t m = 0;
+        bool ok = true;
+        for (int n = 0; ok; ++n) {
+            const int ui = blockIdx.x + n * gridDim.x;
+            if (ui >= nunits) break;
+            const int ub = n & 1;
+            if (lane == 0) ok = mbar_wait_or_abort(&unitf[ub], (n >> 1) & 1, T, A.err, abort);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            const Unit u = urec[ub];
+            const uint32_t bits = ubits[ub];
+            const uint8_t *act = sm + S::ACT_OFF + ub * S::ACT_BYTES;
+            for (int k = 0; k < u.nz && ok; ++k) {
+                if (!((bits >> k) & 1u)) continue;
+                const uint32_t b = m % kAcc, use = m / kAcc;
+                const int z = u.z0 + k, x = u.ox + ex, y = u.oy + ey;
+                const bool on = reads && act[((k + 1) * kHaloY + ey + 1) * kHaloX + ex + 1] != 0;
                 const int64_t v = on ? vox_index(D, u.b, x, y, z) : 0;
                 // operands that do not depend on the MMAs: loaded before the wait
-                float pre[6];
+                float pre[8];
                 int64_t e = -1;
                 double cn[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-                for (int i = 0; i < 6; ++i) pre[i] = 0.0f;
+                for (int i = 0; i < 8; ++i) pre[i] = 0.0f;
                 if (on) {
                     if (EPI == EPI_DGRAD) {
-                        const float2 *zp = reinterpret_cast<const float2 *>(A.zprev + v * 24 + c0);
-                        const float2 q0 = zp[0], q1 = zp[1], q2 = zp[2];
-                        pre[0] = q0.x; pre[1] = q0.y; pre[2] = q1.x; pre[3] = q1.y; pre[4] = q2.x; pre[5] = q2.y;
+                        const float4 *zp = reinterpret_cast<const float4 *>(A.zprev + v * 24 + c0);
+                        const float4 q0 = zp[0], q1 = zp[1];
+                        pre[0] = q0.x; pre[1] = q0.y; pre[2] = q0.z; pre[3] = q0.w;
+                        pre[4] = q1.x; pre[5] = q1.y; pre[6] = q1.z; pre[7] = q1.w;
                     } else if (EPI == EPI_OUT) {
                         if (A.pred) {
 #pragma unroll
@@ -487,95 +656,70 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
                         }
                     }
                 }
-                // one thread waits for the MMAs (the others sleep at the barrier);
-                // a wait that gave up ends the whole CTA's work
-                bool okw = true;
-                if (mma_warp && lane == 0) okw = mbar_wait(&bars[buf], par, A.timeout_ns, A.err);
-                dead = !__syncthreads_and(okw);
+                if (lane == 0) ok = mbar_wait_or_abort(&accf[b], use & 1, T, A.err, abort);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
                 tc_after_sync();
-                if (!dead && !mma_warp && (EPI != EPI_OUT || wq == 0)) {
-                    // columns lo .. lo + 15 of this lane quarter hold channels c0 .. c0 + 5
-                    const int lo = c0 & ~7;
-                    const uint32_t ta = tmem + buf * 32u + (uint32_t)lo + ((uint32_t)(lq * 32) << 16);
-                    float t0[8], t1[8];
-                    tmem_ld8(ta, t0);
-                    tmem_ld8(ta + 8u, t1);
+                float d[8];
+                if (reads) {
+                    tmem_ld8(tmem + b * 32u + (uint32_t)c0 + ((uint32_t)(lq * 32) << 16), d);
                     tc_wait_ld();
-                    float d[6];
-                    switch (wq) {   // warp-uniform: constant register indices in every case
-                    case 0: d[0] = t0[0]; d[1] = t0[1]; d[2] = t0[2]; d[3] = t0[3]; d[4] = t0[4]; d[5] = t0[5]; break;
-                    case 1: d[0] = t0[6]; d[1] = t0[7]; d[2] = t1[0]; d[3] = t1[1]; d[4] = t1[2]; d[5] = t1[3]; break;
-                    case 2: d[0] = t0[4]; d[1] = t0[5]; d[2] = t0[6]; d[3] = t0[7]; d[4] = t1[0]; d[5] = t1[1]; break;
-                    default: d[0] = t0[2]; d[1] = t0[3]; d[2] = t0[4]; d[3] = t0[5]; d[4] = t0[6]; d[5] = t0[7]; break;
-                    }
-                    if (on) {
-                        if (EPI == EPI_OUT) {
-                            if (A.pred) {
+                }
+                // the accumulator is free again once every warp has read it
+                tc_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[b]);
+                ++m;
+                if (on) {
+                    if (EPI == EPI_OUT) {
+                        if (A.pred) {
 #pragma unroll
-                                for (int c = 0; c < 3; ++c) A.pred[v * 3 + c] = pre[c] + A.s_out * (d[c] + bias[c]);
-                            } else if (e >= 0) {
-                                for (int c = 0; c < A.nspecies && c < 3; ++c) {
-                                    const double p = cn[c] + (double)(A.s_out * (d[c] + bias[c]));
-                                    A.xs[c][e] = isfinite(p) ? p : cn[c];   // a non-finite guess falls back to c^n
-                                }
+                            for (int c = 0; c < 3; ++c) A.pred[v * 3 + c] = pre[c] + A.s_out * (d[c] + bias[c]);
+                        } else if (e >= 0) {
+                            for (int c = 0; c < A.nspecies && c < 3; ++c) {
+                                const double p = cn[c] + (double)(A.s_out * (d[c] + bias[c]));
+                                A.xs[c][e] = isfinite(p) ? p : cn[c];   // a non-finite guess falls back to c^n
                             }
-                        } else {
-                            uint32_t o[3];
-                            if (EPI == EPI_GELU) {
-                                float zz[6];
+                        }
+                    } else {
+                        uint32_t o[4];
+                        if (EPI == EPI_GELU) {
+                            float zz[8];
 #pragma unroll
-                                for (int c = 0; c < 6; ++c) zz[c] = d[c] + bias[c];
-                                if (A.z_out) {
-                                    float2 *zp = reinterpret_cast<float2 *>(A.z_out + v * 24 + c0);
-                                    zp[0] = make_float2(zz[0], zz[1]);
-                                    zp[1] = make_float2(zz[2], zz[3]);
-                                    zp[2] = make_float2(zz[4], zz[5]);
-                                }
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) {
-                                    __nv_bfloat162 h = __floats2bfloat162_rn(gelu(zz[2 * c]), gelu(zz[2 * c + 1]));
-                                    o[c] = *reinterpret_cast<uint32_t *>(&h);
-                                }
-                                uint32_t *ap = reinterpret_cast<uint32_t *>(A.a_out + v * 24 + c0);
-                                ap[0] = o[0]; ap[1] = o[1]; ap[2] = o[2];
-                            } else {   // EPI_DGRAD
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) {
-                                    __nv_bfloat162 h = __floats2bfloat162_rn(d[2 * c] * gelu_grad(pre[2 * c]),
-                                                                             d[2 * c + 1] * gelu_grad(pre[2 * c + 1]));
-                                    o[c] = *reinterpret_cast<uint32_t *>(&h);
-                                }
-                                uint32_t *gp = reinterpret_cast<uint32_t *>(A.g_out + v * 24 + c0);
-                                gp[0] = o[0]; gp[1] = o[1]; gp[2] = o[2];
+                            for (int c = 0; c < 8; ++c) zz[c] = d[c] + bias[c];
+                            if (A.z_out) {
+                                float4 *zp = reinterpret_cast<float4 *>(A.z_out + v * 24 + c0);
+                                zp[0] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+                                zp[1] = make_float4(zz[4], zz[5], zz[6], zz[7]);
                             }
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                __nv_bfloat162 h = __floats2bfloat162_rn(gelu(zz[2 * c]), gelu(zz[2 * c + 1]));
+                                o[c] = *reinterpret_cast<uint32_t *>(&h);
+                            }
+                            *reinterpret_cast<uint4 *>(A.a_out + v * 24 + c0) = make_uint4(o[0], o[1], o[2], o[3]);
+                        } else {   // EPI_DGRAD
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                __nv_bfloat162 h = __floats2bfloat162_rn(d[2 * c] * gelu_grad(pre[2 * c]),
+                                                                         d[2 * c + 1] * gelu_grad(pre[2 * c + 1]));
+                                o[c] = *reinterpret_cast<uint32_t *>(&h);
+                            }
+                            *reinterpret_cast<uint4 *>(A.g_out + v * 24 + c0) = make_uint4(o[0], o[1], o[2], o[3]);
                         }
                     }
                 }
-                tc_before_sync();
-                prev_k = -1;
             }
-            if (have) {
-                prev_k = k;
-                prev_m = nmma;
-                nmma += 1;
-            }
-            // the slot of depth k-1 (read by slabs k-2 .. k-1, whose MMAs every
-            // thread has waited for) is refilled with depth k-1+kSlots
-            if (!dead && k >= 1 && issued < ndep && issued == k - 1 + kSlots) {
-                if (!mma_warp) load_halo_depth_items<CI, NL>(D, A.in, u, act, issued, rbase + (issued % kSlots) * H::SLOT, items);
-                cp_async_commit();
-                ++issued;
-            }
+            // this warp is done with the unit's activity bytes and records
+            __syncwarp();
+            if (ok && lane == 0) mbar_arrive(&unite[ub]);
         }
-        cp_async_wait(0);
-        __syncthreads();
     }
-    // leave: all MMAs were waited for (or a wait gave up); free TMEM
-    cp_async_wait(0);
+    // leave: every role finished (or gave up); free TMEM
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (warp == 0) tmem_dealloc(tmem, 64);
+    if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -590,7 +734,7 @@ struct WgSmem {
     static constexpr int G_OFF = RING_OFF + RING_BYTES + 2048;
     static constexpr int G_BYTES = kSlabY * NG * 128;
     static constexpr int ACT_OFF = G_OFF + 2 * G_BYTES;
-    static constexpr int ACT_BYTES = (kZSeg + 2) * kHaloY * kHaloX;
+    static constexpr int ACT_BYTES = kActStride;
     static constexpr int BAR_OFF = (ACT_OFF + ACT_BYTES + 15) & ~15;
     // more than half an SM's shared memory: one CTA per SM, so a CTA's TMEM
     // allocation never waits for another's
@@ -606,6 +750,8 @@ struct WgradArgs {
     const CnnDom *dom;
     const Unit *units;
     const int32_t *nunits;
+    const uint8_t *uact;            // [units][kActStride]
+    const uint32_t *ubits;          // [units]
     float *partials;                // [gridDim][9][128][NO]
     int32_t *err;
     uint64_t timeout_ns;
@@ -622,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
     using H = Halo<CI>;
     using S = WgSmem<CI, NO>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint32_t s_tmem, s_bits;
+    __shared__ uint32_t s_tmem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);
     uint8_t *act = sm + S::ACT_OFF;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -658,8 +804,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
     const int gch = A.gc / 8;                     // real 8-channel chunks of g
     for (int ui = blockIdx.x; ui < nunits && ok; ui += gridDim.x) {
         const Unit u = A.units[ui];
-        load_unit_act<kThreads>(D, A.mask, u, act, &s_bits);
-        const uint32_t bits = s_bits;
+        copy_unit_act<kThreads>(A.uact, ui, act, tid);
+        __syncthreads();
+        const uint32_t bits = A.ubits[ui];
         const int ndep = u.nz + 2;
         int issued = 0;
         for (; issued < ndep && issued < kSlots; ++issued) {
