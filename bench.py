@@ -166,7 +166,7 @@ def _traffic_record(kernel_key):
     except Exception:
         return None
     h = hashlib.sha256()
-    for f in ("solver_kernels.cuh", "solver_f32.cu", "mpm_internal.cuh", "step_kernels.cuh"):
+    for f in ("solver_kernels.cuh", "solver_inst_f32a.cu", "mpm_internal.cuh", "step_kernels.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2505_03067_gb300", "csrc", f), "rb").read())
     rec = d.get(kernel_key)
     if not rec or rec.get("source_sha256") != h.hexdigest():

@@ -115,6 +115,9 @@ typedef struct {
     double item_ms[MPM_MAX_SPECIES];    /* device time of each species' work item inside the
                                            persistent launch */
     int32_t reorth[MPM_MAX_SPECIES];    /* Arnoldi steps that took the second Gram-Schmidt pass */
+    int32_t fallback[MPM_MAX_SPECIES];  /* mpm_solve_fgmres_cnn: 1 when a cycle preconditioned by the
+                                           network failed to reduce the FP64 true residual and the
+                                           solve went on as plain GMRES (0 elsewhere) */
 } mpm_report;
 
 /* Shape of an extracted subgrid (host struct filled by mpm_subgrid_info). */
@@ -424,14 +427,25 @@ mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm
  * (m = max |v|), the network's inputs being v in the field channel of s, the
  * other fields and the source map at zero, and the lattice's cell ids, uptake
  * maps and mask over the box (the homogeneous problem, whose solution operator
- * is A^-1).  Modified Gram-Schmidt, Givens rotations, the update from the
- * preconditioned directions, restarts from the true FP64 residual; stopping
- * rule and statuses as mpm_solve_step, in FP64 (opt->precision is ignored).
- * x0 is c^n, or the iterate as it stands with opt->x0_given = 1 (for
- * instance after mpm_cnn_guess).  scatter_to (nullable) receives the result
- * as in mpm_solve_step.  The box must fit the network (mpm_cnn_create's
- * max_voxels); species 0..2 only.  Synchronises `stream` once per Arnoldi
- * step: this is the learned solver's reference path, not the fast one.
+ * is A^-1).  Each cycle starts from the FP64 true residual r = b - A x and
+ * ends with the FP64 update x + Z y (iterative refinement around one flexible
+ * GMRES cycle); opt->precision 1 holds the Krylov vectors, the directions z
+ * and the operator in FP32 and ends a cycle when its residual estimate falls
+ * to max(tol / 4, opt->inner_rtol * ||r||), precision 0 holds them in FP64
+ * and ends it at tol.  Classical Gram-Schmidt in two passes, Givens rotations
+ * and the least-squares solve in FP64 on the device: the solve is one CUDA
+ * graph (conditional WHILE nodes) and the host waits once, for the report.
+ * Fallback: a cycle whose true residual is not below the one it started from
+ * (or not finite) is discarded and the rest of the solve is plain GMRES
+ * (z = v); rep->fallback[s] = 1 records it, and the status is that of the
+ * whole solve (a discarded plain cycle ends it: MPM_ERR_NOCONV unless the
+ * tolerance is met).  Stopping rule tol = max(rtol ||b_mask||, atol) on the
+ * true residual, statuses as mpm_solve_step; rep->reorth counts every Arnoldi
+ * step (both passes are always taken).  x0 is c^n, or the iterate as it
+ * stands with opt->x0_given = 1 (for instance after mpm_cnn_guess).
+ * scatter_to (nullable) receives the result as in mpm_solve_step.  The
+ * lattice dims must be the network's image dims; species 0..2 only.
+ * MPM_ERR_TIMEOUT: a bounded wait in a network kernel gave up.
  */
 /* The preconditioner of mpm_solve_fgmres_cnn applied to one box-dense FP64
  * vector v of species s (device, nx*ny*nz): z (device, box-dense) = the

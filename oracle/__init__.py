@@ -401,6 +401,109 @@ def fgmres(A: CSR, b, x0, M, restart: int = 30, tol_abs: float = 1e-12, maxit: i
     return x, {"status": status, "iters": it, "cycles": cyc, "res": float(np.sqrt(r @ r))}
 
 
+def fgmres_refined(A: CSR, b, x0, M, restart: int = 8, tol_abs: float = 1e-12, maxit: int = 10000,
+                   inner=np.float32, inner_rtol: float = 0.0):
+    """Flexible GMRES inside iterative refinement, with the fallback to plain
+    GMRES: the solver of the learned path (the network as the right
+    preconditioner of a flexible Krylov method; mixed precision as iterative
+    refinement around a low-precision inner solve).  Plain NumPy.
+
+    Each refinement step takes the FP64 true residual r = b - A x, beta =
+    ||r||, and runs ONE flexible GMRES(m) cycle on A d = r: the Krylov vectors
+    v_j, the directions z_j = M(v_j) and w = A z_j are stored in `inner`
+    precision (for FP32 with A's coefficients rounded to FP32), Gram-Schmidt is
+    classical in two passes, the Hessenberg matrix, Givens rotations and the
+    least-squares solve are FP64.  The cycle ends when the residual estimate
+    |g_{j+1}| falls to max(tol / 4, inner_rtol * beta) (FP32; tol for FP64),
+    after m steps, at maxit steps in all, or on a zero or non-finite
+    h_{j+1,j} / estimate.  The trial x_t = x + Z y (FP64) replaces x when
+    ||b - A x_t|| < beta; otherwise it is dropped and the solve continues
+    with M = identity (plain GMRES), or, already plain, stops (stagnation).
+    Returns x and {status, iters, cycles, res, fallback}."""
+    with np.errstate(all="ignore"):          # a failing preconditioner may return inf / NaN
+        return _fgmres_refined(A, b, x0, M, restart, tol_abs, maxit, inner, inner_rtol)
+
+
+def _fgmres_refined(A, b, x0, M, restart, tol_abs, maxit, inner, inner_rtol):
+    b = np.asarray(b, np.float64).reshape(-1)
+    x = np.array(x0, np.float64).reshape(-1).copy()
+    f32 = np.dtype(inner) == np.float32
+    if f32:
+        q = lambda u: np.asarray(u, np.float64).astype(np.float32).astype(np.float64)
+        A_in = dataclasses.replace(A, val=q(A.val))
+    else:
+        q = lambda u: np.asarray(u, np.float64)
+        A_in = A
+    m = restart
+    r = b - A.matvec(x)
+    beta = float(np.sqrt(r @ r))
+    it = cyc = 0
+    fallback = False
+    if not np.isfinite(beta):
+        return x, {"status": ERR_BREAKDOWN, "iters": 0, "cycles": 0, "res": beta, "fallback": False}
+    if beta <= tol_abs:
+        return x, {"status": OK, "iters": 0, "cycles": 0, "res": beta, "fallback": False}
+    while True:
+        cyc += 1
+        tol_in = max(0.25 * tol_abs, inner_rtol * beta) if f32 else tol_abs
+        V = [q(r / beta)]
+        Z = []
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            z = V[j] if fallback else q(M(V[j]))
+            Z.append(z)
+            w = q(A_in.matvec(z))
+            col = np.zeros(j + 1)
+            for _ in range(2):                       # classical Gram-Schmidt, two passes
+                c = np.array([w @ V[i] for i in range(j + 1)])
+                w = q(w - sum(c[i] * V[i] for i in range(j + 1)))
+                col += c
+            hn = float(np.sqrt(w @ w))
+            H[:j + 1, j] = col
+            for i in range(j):
+                t0, t1 = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * t0 + sn[i] * t1
+                H[i + 1, j] = -sn[i] * t0 + cs[i] * t1
+            den = float(np.hypot(H[j, j], hn))
+            cs[j], sn[j] = (1.0, 0.0) if den == 0.0 else (H[j, j] / den, hn / den)
+            H[j, j] = cs[j] * H[j, j] + sn[j] * hn
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            k = j + 1
+            if hn > 0.0 and np.isfinite(hn):
+                V.append(q(w / hn))
+            if not np.isfinite(g[j + 1]) or abs(g[j + 1]) <= tol_in or it >= maxit or hn == 0.0:
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        xt = x.copy()
+        for i in range(k):
+            xt = xt + y[i] * Z[i]
+        rt = b - A.matvec(xt)
+        bt = float(np.sqrt(rt @ rt))
+        stall = False
+        if np.isfinite(bt) and bt < beta:
+            x, r, beta = xt, rt, bt
+        elif not fallback:
+            fallback = True
+        else:
+            stall = True
+        if beta <= tol_abs:
+            status = OK
+            break
+        if it >= maxit or stall:
+            status = ERR_NOCONV
+            break
+    return x, {"status": status, "iters": it, "cycles": cyc, "res": beta, "fallback": fallback}
+
+
 def cnn_precond_inputs(v_box, s, cell_box, mask_box, params):
     """Inputs of the network used as a preconditioner for species s: the
     network's nine channels with the field of species s set to v (scaled as

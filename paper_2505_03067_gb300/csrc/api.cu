@@ -121,6 +121,7 @@ mpm_status mpm_destroy(mpm_ctx *ctx)
 {
     if (!ctx) return MPM_ERR_ARG;
     mpm_batch_graph_free(ctx);
+    mpm_fgmres_release(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_box);
     cudaFree(ctx->d_count);

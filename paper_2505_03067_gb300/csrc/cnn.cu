@@ -22,6 +22,7 @@
 // the tensor cores read them from shared memory.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -376,8 +377,10 @@ __device__ __forceinline__ int64_t elem_of(const BoxGeo &g, const int32_t *__res
 
 // Solver mode: features of the active voxels of every listed unit (B = 1, the
 // lattice itself).  vin == null: c^n from the lattice (the guess); otherwise
-// the field channel of species s carries vin / m (compact vector of the
-// subgrid, m = *vscale), the other fields and the source map are zero (the
+// the field channel of species s carries v / m (v: compact vector of the
+// subgrid, FP32 or FP64, at vin + (*vj) * vstride elements when vj is set --
+// the Krylov vector whose index the solver keeps in device memory; m =
+// *vscale), the other fields and the source map are zero (the
 // preconditioner's homogeneous problem), and f32 receives the field channels.
 struct FeatUnits {
     FeatSrc F;
@@ -387,7 +390,10 @@ struct FeatUnits {
     const int32_t *nunits;
     __nv_bfloat16 *x;
     float *f32;
-    const double *vin;
+    const void *vin;
+    int32_t vin_f32;
+    int64_t vstride;
+    const int32_t *vj;
     const double *vscale;
     int s;
     const BoxGeo *geo;
@@ -399,6 +405,7 @@ __global__ void k_feat_units(const __grid_constant__ FeatUnits A)
     const CnnDom &D = *A.dom;
     const int nu = *A.nunits;
     const double m = A.vin ? *A.vscale : 1.0;
+    const int64_t voff = A.vin && A.vj ? (int64_t)*A.vj * A.vstride : 0;
     for (int ui = blockIdx.x; ui < nu; ui += gridDim.x) {
         const Unit u = A.units[ui];
         for (int i = threadIdx.x; i < tc::kSlabX * tc::kSlabY * u.nz; i += blockDim.x) {
@@ -412,7 +419,11 @@ __global__ void k_feat_units(const __grid_constant__ FeatUnits A)
             } else {
                 if (m > 0.0) {
                     const int64_t e = elem_of(*A.geo, A.tile_index, x, y, z);
-                    if (e >= 0) fld[A.s] = (float)(A.vin[e] / m);
+                    if (e >= 0) {
+                        const double ve = A.vin_f32 ? (double)static_cast<const float *>(A.vin)[voff + e]
+                                                    : static_cast<const double *>(A.vin)[voff + e];
+                        fld[A.s] = (float)(ve / m);
+                    }
                 }
                 for (int s = 0; s < 3; ++s) A.f32[L * 3 + s] = fld[s];
             }
@@ -501,7 +512,8 @@ struct PcOut {
     const int32_t *tile_index;
     const double *vscale;
     int s;
-    double *z;
+    void *z;                      // FP32 (z_f32) or FP64 compact vector
+    int32_t z_f32;
 };
 
 __global__ void k_pc_scatter(const __grid_constant__ PcOut P)
@@ -518,7 +530,11 @@ __global__ void k_pc_scatter(const __grid_constant__ PcOut P)
             const int64_t L = tc::vox_index(D, 0, x, y, z);
             if (!P.lmask[L]) continue;
             const int64_t e = elem_of(*P.geo, P.tile_index, x, y, z);
-            if (e >= 0) P.z[e] = m * (double)P.pred[L * 3 + P.s];
+            if (e >= 0) {
+                const double z = m * (double)P.pred[L * 3 + P.s];
+                if (P.z_f32) static_cast<float *>(P.z)[e] = (float)z;
+                else static_cast<double *>(P.z)[e] = z;
+            }
         }
     }
 }
@@ -528,6 +544,7 @@ __global__ void k_pc_scatter(const __grid_constant__ PcOut P)
 using namespace mpm;
 
 struct mpm_cnn {
+    uint64_t serial = 0;             // distinct for every network of the process (graph caches)
     int32_t L[3] = {0, 0, 0};
     int32_t maxB = 0;
     long long V = 0;                 // voxels per image
@@ -579,17 +596,28 @@ mpm_status cnn_alloc(mpm_ctx *ctx, mpm_cnn *c, void **p, size_t bytes)
 
 // One forward / input-gradient convolution over the listed units; `slot` is
 // its work counter.
+// The dynamic shared-memory size of a convolution instance, set once per
+// process (outside any stream capture: mpm_cnn_create sets the forward ones).
 template <int CI, int NO, int EPI>
-mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t st)
+mpm_status conv_attr(mpm_ctx *ctx)
 {
     static bool attr = false;
-    constexpr int smem = tc::ConvSmem<CI, NO>::BYTES;
     if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(tc::k_conv_tc<CI, NO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const cudaError_t e = cudaFuncSetAttribute(tc::k_conv_tc<CI, NO, EPI>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)tc::ConvSmem<CI, NO>::BYTES);
         if (e != cudaSuccess) return mpm_cuda_check(ctx, e, "cnn convolution: shared-memory attribute");
         attr = true;
     }
+    return MPM_OK;
+}
+
+template <int CI, int NO, int EPI>
+mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t st)
+{
+    constexpr int smem = tc::ConvSmem<CI, NO>::BYTES;
+    const mpm_status ra = conv_attr<CI, NO, EPI>(ctx);
+    if (ra != MPM_OK) return ra;
     A.dom = c->dom;
     A.units = c->units;
     A.nunits = c->counters;
@@ -765,7 +793,9 @@ extern "C" mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **out, const int32_t 
         if (image_dims[d] < 1) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_create: bad image dims");
     const long long V = (long long)image_dims[0] * image_dims[1] * image_dims[2];
     if (V * max_images >= (1LL << 31)) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_create: more than 2^31 voxels");
+    static std::atomic<uint64_t> serials{0};
     mpm_cnn *c = new mpm_cnn();
+    c->serial = ++serials;
     for (int d = 0; d < 3; ++d) c->L[d] = image_dims[d];
     c->maxB = max_images;
     c->V = V;
@@ -832,6 +862,11 @@ extern "C" mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **out, const int32_t 
         cudaMemset(c->counters, 0, 64 * sizeof(int32_t));
         if (cudaDeviceSynchronize() != cudaSuccess) r = mpm_cuda_check(ctx, cudaGetLastError(), "cnn_create");
     }
+    // the forward convolutions run inside captured graphs (learned step,
+    // flexible GMRES): their attributes are set here, outside any capture
+    if (r == MPM_OK) r = conv_attr<kXC, 32, tc::EPI_GELU>(ctx);
+    if (r == MPM_OK) r = conv_attr<kHC, 32, tc::EPI_GELU>(ctx);
+    if (r == MPM_OK) r = conv_attr<kHC, 16, tc::EPI_OUT>(ctx);
     if (r != MPM_OK) {
         mpm_cnn_destroy(ctx, c);
         return r;
@@ -1099,30 +1134,47 @@ extern "C" mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, 
 }
 
 // ---------------------------------------------------------------- the network as a preconditioner
-// Row a13: flexible GMRES applies z = m * net(v / m) to a vector v of one
-// species (m = max |v|, which puts v in the range the network was trained
+// Row a13: flexible GMRES applies z = m * net(v / m) to a Krylov vector v of
+// one species (m = max |v|, which puts v in the range the network was trained
 // on), with the other fields and the source map at zero (the homogeneous
-// problem), and keeps z on the in-mask voxels only.  z = d_scale-scaled
-// network output on compact FP64 vectors of species s of sub; d_scale: one
-// device double of scratch.  Stream work only.
-mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
-                                const mpm_params *prm, int s, const double *v, double *z, double *d_scale,
-                                cudaStream_t st)
+// problem), and keeps z on the in-mask voxels only.
+//
+// The plan (box geometry, listed units, per-unit activity) depends on the
+// subgrid alone: mpm_cnn_pc_plan computes it once per solve and keeps the
+// unit count twice, in counters[0] (read by every network kernel) and in
+// counters[kUnitsSaved] (from which a solver restores it: a solver that has
+// abandoned the network sets counters[0] = 0, and every network kernel then
+// has nothing to do).  Stream work only.
+constexpr int kUnitsSaved = 32;
+
+mpm_status mpm_cnn_pc_plan(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,
+                           cudaStream_t st, int32_t **units_out)
 {
     mpm_status r = solver_mode_check(ctx, c, sub, lat, prm, "cnn_precond");
     if (r != MPM_OK) return r;
-    if (s < 0 || s > 2) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: the network covers species 0..2");
+    r = check_err(ctx, c);
+    if (r != MPM_OK) return r;
     const BoxGeo g = make_geo(sub, lat->dims);
     MPM_CU(cudaMemcpyAsync(c->geo, &g, sizeof(g), cudaMemcpyHostToDevice, st));
-    MPM_CU(cudaMemsetAsync(z, 0, (size_t)(sub->NE > 0 ? sub->NE : 1) * sizeof(double), st));
-    if (sub->NE == 0) return MPM_OK;
-    k_pc_amax<<<1, 1024, 0, st>>>(v, sub->NE, d_scale);
     MPM_CU(cudaMemsetAsync(c->counters, 0, 16 * sizeof(int32_t), st));
     k_plan_box<<<ctx->num_sms, 256, 0, st>>>(c->geo, sub->tile_index, lat->dims[0], lat->dims[1], lat->dims[2],
                                              c->units, c->counters, c->dom);
     ctx->launches += 1;
     r = unit_act(ctx, c, lat->mask, st);
     if (r != MPM_OK) return r;
+    MPM_CU(cudaMemcpyAsync(c->counters + kUnitsSaved, c->counters, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    if (units_out) *units_out = c->counters;
+    return MPM_OK;
+}
+
+// z = m * net(v / m)[s] on the in-mask stored elements of the planned units
+// (elements elsewhere untouched).  v at v + (*vj) * vstride elements (vj null:
+// at v), FP32 or FP64 (f32); m = *vscale (device); z of the same type.  Kernel
+// launches only (capturable into a graph body).
+mpm_status mpm_cnn_pc_apply(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                            const mpm_params *prm, int s, const void *v, bool f32, int64_t vstride,
+                            const int32_t *vj, const double *vscale, void *z, cudaStream_t st)
+{
     FeatUnits FU;
     memset(&FU, 0, sizeof(FU));
     FU.F = feat_src(lat, prm);
@@ -1133,19 +1185,22 @@ mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, cons
     FU.x = c->x;
     FU.f32 = c->f32;
     FU.vin = v;
-    FU.vscale = d_scale;
+    FU.vin_f32 = f32 ? 1 : 0;
+    FU.vstride = vstride;
+    FU.vj = vj;
+    FU.vscale = vscale;
     FU.s = s;
     FU.geo = c->geo;
     FU.tile_index = sub->tile_index;
     k_feat_units<<<ctx->num_sms * 8, 256, 0, st>>>(FU);
-    ctx->launches += 2;
+    ctx->launches += 1;
     MPM_CU(cudaGetLastError());
     // image-mode output (pred = field channels + s_out z6) on the lattice-indexed buffer
     tc::ConvArgs O;
     memset(&O, 0, sizeof(O));
     O.pred = c->pred;
     O.f32 = c->f32;
-    r = forward_layers(ctx, c, lat->mask, false, O, st);
+    mpm_status r = forward_layers(ctx, c, lat->mask, false, O, st);
     if (r != MPM_OK) return r;
     PcOut P;
     P.dom = c->dom;
@@ -1155,12 +1210,36 @@ mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, cons
     P.pred = c->pred;
     P.geo = c->geo;
     P.tile_index = sub->tile_index;
-    P.vscale = d_scale;
+    P.vscale = vscale;
     P.s = s;
     P.z = z;
+    P.z_f32 = f32 ? 1 : 0;
     k_pc_scatter<<<ctx->num_sms * 8, 256, 0, st>>>(P);
     ctx->launches += 1;
     return mpm_cuda_check(ctx, cudaGetLastError(), "cnn preconditioner output");
+}
+
+uint64_t mpm_cnn_serial(const mpm_cnn *c) { return c->serial; }
+
+// Kernels one mpm_cnn_pc_apply launches.
+int mpm_cnn_pc_launches() { return 2 + kLayers; }
+
+mpm_status mpm_cnn_check_err(mpm_ctx *ctx, mpm_cnn *c) { return check_err(ctx, c); }
+
+// One application on compact FP64 vectors (z = 0 off the mask); d_scale: one
+// device double of scratch.  Stream work only.
+mpm_status mpm_cnn_precond_impl(mpm_ctx *ctx, mpm_cnn *c, mpm_subgrid *sub, const mpm_lattice *lat,
+                                const mpm_params *prm, int s, const double *v, double *z, double *d_scale,
+                                cudaStream_t st)
+{
+    if (s < 0 || s > 2) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_precond: the network covers species 0..2");
+    MPM_CU(cudaMemsetAsync(z, 0, (size_t)(sub->NE > 0 ? sub->NE : 1) * sizeof(double), st));
+    if (sub->NE == 0) return MPM_OK;
+    mpm_status r = mpm_cnn_pc_plan(ctx, c, sub, lat, prm, st, nullptr);
+    if (r != MPM_OK) return r;
+    k_pc_amax<<<1, 1024, 0, st>>>(v, sub->NE, d_scale);
+    ctx->launches += 1;
+    return mpm_cnn_pc_apply(ctx, c, sub, lat, prm, s, v, false, 0, nullptr, d_scale, z, st);
 }
 
 mpm_status mpm_dense_to_elems(mpm_ctx *ctx, const mpm_subgrid *sub, const double *src, double *dst, cudaStream_t st);

@@ -418,6 +418,8 @@ struct mpm_ctx {
     int32_t solver_variant = 0;  // solver kernel variant (tuning)
     void *batch_graph = nullptr; // captured batched step (solver.cu)
     cudaStream_t cap_stream = nullptr;  // stream used only for graph capture
+    cudaStream_t fg_cs[3] = {};  // capture streams of the flexible GMRES graph (fgmres.cu)
+    void *fg_cache = nullptr;    // its last graph
     void *d_tune = nullptr;      // tuner scratch tables
     size_t tune_cap = 0;
     unsigned long long *d_prof = nullptr;
@@ -519,6 +521,7 @@ mpm_status mpm_batch_step_impl(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm
                                const mpm_params *const *prms, int32_t nsys, const mpm_opts *opt, mpm_report *reps,
                                cudaStream_t st);
 void mpm_batch_graph_free(mpm_ctx *ctx);
+void mpm_fgmres_release(mpm_ctx *ctx);   // fgmres.cu: its graph and capture streams
 mpm_status mpm_step_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm, int32_t margin,
                          const int32_t tile[3], const mpm_opts *opt, mpm_report *rep, mpm_box *out_box, cudaStream_t st);
 mpm_status mpm_step_enqueue_impl(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_lattice *lat, const mpm_params *prm,

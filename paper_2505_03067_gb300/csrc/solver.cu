@@ -19,11 +19,32 @@ namespace mpm {
 // elements at one CTA/SM of 512, 1: one element at two CTAs/SM, 2: one
 // element at one CTA/SM of 1024, 3: one element at one CTA/SM of 768, 4: two
 // elements at one CTA/SM of 768, 5: one element at one CTA/SM of 512.
+// The instances live in the solver_inst_*.cu translation units.
 static Variant pick(int prec, int maxm, int variant)
 {
-    if (prec != 0) return pick_f32(maxm, variant);
-    if (maxm == 8 && (variant == 0 || variant == 1 || variant == 5 || variant > 5)) return pick_f64(maxm, variant);
-    return pick_f64x(maxm, variant);
+    if (prec != 0) {
+        if (maxm == 16) return inst_f32_16_1_1_512();
+        if (maxm == 32) return inst_f32_32_1_1_512();
+        switch (variant) {
+        case 1: return inst_f32_8_1_1_768();
+        case 2: return inst_f32_8_2_2_512();
+        case 3: return inst_f32_8_2_1_512();
+        case 4: return inst_f32_8_1_1_1024();
+        case 5: return inst_f32_8_1_2_512();
+        case 6: return inst_f32_8_1_1_640();
+        default: return inst_f32_8_1_1_512();
+        }
+    }
+    if (maxm == 16) return inst_f64_16_1_1_512();
+    if (maxm == 32) return inst_f64_32_1_1_512();
+    switch (variant) {
+    case 1: return inst_f64_8_1_2_512();
+    case 2: return inst_f64_8_1_1_1024();
+    case 3: return inst_f64_8_1_1_768();
+    case 4: return inst_f64_8_2_1_768();
+    case 5: return inst_f64_8_1_1_512();
+    default: return inst_f64_8_2_1_512();
+    }
 }
 
 }  // namespace mpm

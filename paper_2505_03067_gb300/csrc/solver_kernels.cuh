@@ -1,7 +1,7 @@
 // solver_kernels.cuh -- restarted GMRES (Saad & Schultz 1986, the solver named
 // in Sec. 2.4) for the box systems, as ONE persistent cooperative kernel: the
-// device code and its instantiation helper (the instantiations themselves
-// live in solver_f32.cu, solver_f64.cu and solver_f64x.cu, compiled in
+// device code and its instantiation helper (the instances themselves live
+// in the solver_inst_*.cu translation units, two each, compiled in
 // parallel).
 //
 // Structure of a launch.  The grid is split into teams of co-resident CTAs;
@@ -1171,9 +1171,24 @@ static Variant var_of()
     return Variant{k_gmres<T, MAXM, U, MINB, NT>, k_step<T, MAXM, U, MINB, NT>, sizeof(Smem<MAXM, T, NT>), NT};
 }
 
-// Kernel variant tables, one per translation unit (see solver.cu's pick).
-Variant pick_f32(int maxm, int variant);
-Variant pick_f64(int maxm, int variant);    // m <= 8: variants 0, 1, 5
-Variant pick_f64x(int maxm, int variant);   // m <= 8: variants 2, 3, 4; m > 8
+// Kernel instances <type, restart bucket, elements per thread, CTAs per SM,
+// threads>, defined in the solver_inst_*.cu translation units.
+Variant inst_f32_8_1_1_512();
+Variant inst_f32_8_1_1_768();
+Variant inst_f32_8_2_2_512();
+Variant inst_f32_8_2_1_512();
+Variant inst_f32_8_1_1_1024();
+Variant inst_f32_8_1_2_512();
+Variant inst_f32_8_1_1_640();
+Variant inst_f32_16_1_1_512();
+Variant inst_f32_32_1_1_512();
+Variant inst_f64_8_2_1_512();
+Variant inst_f64_8_1_2_512();
+Variant inst_f64_8_1_1_512();
+Variant inst_f64_8_1_1_1024();
+Variant inst_f64_8_1_1_768();
+Variant inst_f64_8_2_1_768();
+Variant inst_f64_16_1_1_512();
+Variant inst_f64_32_1_1_512();
 
 }  // namespace mpm

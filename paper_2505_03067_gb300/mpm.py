@@ -74,7 +74,7 @@ class mpm_report(C.Structure):
                 ("res", C.c_double * MAX_SPECIES),
                 ("bnorm", C.c_double * MAX_SPECIES), ("box_voxels", C.c_int64), ("mask_voxels", C.c_int64),
                 ("stored_voxels", C.c_int64), ("solve_ms", C.c_double), ("item_ms", C.c_double * MAX_SPECIES),
-                ("reorth", C.c_int32 * MAX_SPECIES)]
+                ("reorth", C.c_int32 * MAX_SPECIES), ("fallback", C.c_int32 * MAX_SPECIES)]
 
     def as_dict(self, nspecies):
         return {"iters": list(self.iters[:nspecies]), "cycles": list(self.cycles[:nspecies]),
@@ -82,7 +82,8 @@ class mpm_report(C.Structure):
                 "res": list(self.res[:nspecies]),
                 "bnorm": list(self.bnorm[:nspecies]), "box_voxels": self.box_voxels,
                 "mask_voxels": self.mask_voxels, "stored_voxels": self.stored_voxels, "solve_ms": self.solve_ms,
-                "item_ms": list(self.item_ms[:nspecies]), "reorth": list(self.reorth[:nspecies])}
+                "item_ms": list(self.item_ms[:nspecies]), "reorth": list(self.reorth[:nspecies]),
+                "fallback": list(self.fallback[:nspecies])}
 
 
 class mpm_subgrid_desc(C.Structure):

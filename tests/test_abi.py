@@ -52,8 +52,8 @@ def test_binding_structs_match_header_sizes(libpath):
 int main(void){
  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mpm_lattice), sizeof(mpm_params), sizeof(mpm_opts),
         sizeof(mpm_report), sizeof(mpm_subgrid_desc), sizeof(mpm_box));
- printf("%zu %zu %zu %zu\n", offsetof(mpm_params,k_cell), offsetof(mpm_opts,inner_rtol),
-        offsetof(mpm_report,box_voxels), offsetof(mpm_subgrid_desc,stored_voxels));
+ printf("%zu %zu %zu %zu %zu\n", offsetof(mpm_params,k_cell), offsetof(mpm_opts,inner_rtol),
+        offsetof(mpm_report,box_voxels), offsetof(mpm_subgrid_desc,stored_voxels), offsetof(mpm_report,fallback));
  return 0; }'''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
@@ -66,7 +66,8 @@ int main(void){
     assert sizes[:6] == [C.sizeof(mpm.mpm_lattice), C.sizeof(mpm.mpm_params), C.sizeof(mpm.mpm_opts),
                          C.sizeof(mpm.mpm_report), C.sizeof(mpm.mpm_subgrid_desc), C.sizeof(mpm.mpm_box)]
     assert sizes[6:] == [mpm.mpm_params.k_cell.offset, mpm.mpm_opts.inner_rtol.offset,
-                         mpm.mpm_report.box_voxels.offset, mpm.mpm_subgrid_desc.stored_voxels.offset]
+                         mpm.mpm_report.box_voxels.offset, mpm.mpm_subgrid_desc.stored_voxels.offset,
+                         mpm.mpm_report.fallback.offset]
 
 
 def test_product_path_does_not_import_the_oracle():

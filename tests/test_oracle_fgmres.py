@@ -139,3 +139,78 @@ def test_network_preconditioned_fgmres_reaches_the_solution():
     # the preconditioner only acts on the mask: identity rows keep c^n
     out = lat.mask.reshape(-1) == 0
     assert np.array_equal(x[out], c[out])
+
+
+# ---------------------------------------------------------------- refined FGMRES with the fallback
+# Pins of oracle.fgmres_refined: in FP64 with every cycle accepted it is the
+# restarted (F)GMRES of oracle.gmres / oracle.fgmres cycle for cycle (a wrong
+# rotation, update or Gram-Schmidt pass changes the iteration count or the
+# solution); in FP32 the refinement still reaches an FP64 tolerance; a
+# preconditioner that returns non-finite or zero directions is dropped after
+# one cycle, and the rest of the solve is then plain GMRES step for step.
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_refined_fp64_identity_is_restarted_gmres(seed):
+    wl, A, b, c = _system(seed)
+    tol = 1e-11 * np.linalg.norm(b)
+    xg, ig = oracle.gmres(A, b, c, 8, tol, 500)
+    xr, ir = oracle.fgmres_refined(A, b, c, lambda v: v, 8, tol, 500, inner=np.float64)
+    assert ig["status"] == ir["status"] == oracle.OK and not ir["fallback"]
+    assert ig["iters"] == ir["iters"] and ig["cycles"] == ir["cycles"]
+    assert np.max(np.abs(xr - xg)) <= 1e-12 * np.max(np.abs(xg))
+
+
+def test_refined_fp64_jacobi_is_fgmres():
+    wl, A, b, c = _system(6, dfac=True)
+    d = A.dense().diagonal()
+    tol = 1e-11 * np.linalg.norm(b)
+    xf, inf = oracle.fgmres(A, b, c, lambda v: v / d, 5, tol, 500)
+    xr, ir = oracle.fgmres_refined(A, b, c, lambda v: v / d, 5, tol, 500, inner=np.float64)
+    assert inf["iters"] == ir["iters"] and inf["cycles"] == ir["cycles"] and not ir["fallback"]
+    assert np.max(np.abs(xr - xf)) <= 1e-12 * np.max(np.abs(xf))
+
+
+@pytest.mark.parametrize("seed,dfac", [(7, False), (8, True)])
+def test_refined_fp32_reaches_fp64_tolerance(seed, dfac):
+    """FP32 cycles inside FP64 refinement meet a tolerance far below FP32's
+    precision; the cycles end early (inner_rtol), so there are several."""
+    wl, A, b, c = _system(seed, dfac=dfac)
+    xs = oracle.dense_solve(A, b)
+    d = A.dense().diagonal()
+    tol = 1e-11 * np.linalg.norm(b)
+    for M in (lambda v: v, lambda v: v / d, lambda v: np.tanh(v) + 0.1 * v):
+        x, info = oracle.fgmres_refined(A, b, c, M, 8, tol, 2000, inner=np.float32, inner_rtol=1e-4)
+        assert info["status"] == oracle.OK and not info["fallback"], info
+        assert info["res"] <= tol and info["cycles"] >= 2
+        r = b - A.matvec(x)
+        assert abs(np.linalg.norm(r) - info["res"]) <= 1e-3 * info["res"]
+        assert np.linalg.norm(x - xs) <= info["res"] + 1e-13
+
+
+@pytest.mark.parametrize("inner", [np.float32, np.float64])
+@pytest.mark.parametrize("bad", ["nan", "zero"])
+def test_failing_preconditioner_falls_back_to_plain_gmres(inner, bad):
+    """The failed cycle costs one Arnoldi step (its estimate or h_{1,0} ends it)
+    and leaves x and r as they were: the result is the plain solve's, bit for
+    bit, one cycle and one step later."""
+    wl, A, b, c = _system(9)
+    tol = 1e-10 * np.linalg.norm(b)
+    M = (lambda v: np.full_like(v, np.nan)) if bad == "nan" else (lambda v: np.zeros_like(v))
+    xp, ip = oracle.fgmres_refined(A, b, c, lambda v: v, 8, tol, 500, inner=inner, inner_rtol=1e-4)
+    xb, ib = oracle.fgmres_refined(A, b, c, M, 8, tol, 500, inner=inner, inner_rtol=1e-4)
+    assert ip["status"] == ib["status"] == oracle.OK
+    assert not ip["fallback"] and ib["fallback"]
+    assert ib["iters"] == ip["iters"] + 1 and ib["cycles"] == ip["cycles"] + 1
+    assert np.array_equal(xb, xp)
+
+
+def test_refined_stagnation_stops_before_maxit():
+    """With tolerance 0 the refinement reaches the rounding floor, where a
+    cycle no longer reduces the FP64 residual: the solver drops the
+    preconditioner once, stalls on the next failure and returns NOCONV long
+    before maxit."""
+    wl, A, b, c = _system(10)
+    x, info = oracle.fgmres_refined(A, b, c, lambda v: v, 8, 0.0, 100000, inner=np.float32, inner_rtol=1e-4)
+    assert info["status"] == oracle.ERR_NOCONV and info["fallback"]
+    assert info["iters"] < 1000
+    assert info["res"] <= 1e-13 * np.linalg.norm(b)
