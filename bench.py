@@ -264,6 +264,12 @@ def bench_patches64(mpm, W, ctx, stream, flush, warmup, steps=50):
             "systems": 3 * len(ps), "tuned": {"restart": m, "variant": var,
                                               "tiles": sorted(set(map(tuple, bs.tiles)))},
             "graph": bs.graph_active(), "stored_voxels": stored,
+            "team_model": {"f_per_tuning_round": bs.team_tuning["f"],
+                           "fixed_F1_F_per_round": bs.team_tuning["fixed_per_round"],
+                           "kept_F1_F": bs.team_tuning["fixed"],
+                           "note": "mpm_tune_teams: item cost it (F1 + NE) on one CTA, it (F + NE / c) on c > 1, "
+                                   "F1 and F fitted to measured item times, it from the previous solve; round 0 is "
+                                   "the unmeasured model"},
             "imbalance_f": {"mean": float(np.mean(imb)), "max": float(np.max(imb)),
                             "definition": "t_max/<t> - 1 over the CTA teams of the persistent launch"},
             "mask_voxels": sum(r["mask_voxels"] for r in reps)}
@@ -340,13 +346,123 @@ def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=N
         its.append(sum(rep["iters"]) / len(rep["iters"]))
     launches = ctx.launches() - l0
     clocks = sampler.stop() if sampler else None
+    # after the timed steps: one more step on the last state with the phase
+    # timers on (CTA 0's split of the step: extraction, the solver's passes and
+    # its waits), not part of any timed figure
+    ctx.debug_set(mpm.DEBUG_PHASE_TIMES, 1)
+    prep = solver.step(opts)
+    phases = {k: round(v, 1) for k, v in ctx.phase_times_us().items()}
+    phases["iters"] = prep["iters"]
+    ctx.debug_set(mpm.DEBUG_PHASE_TIMES, 0)
     out = {"value": units / (ms / 1e3), "ms_per_step": ms / K, "steps_checked": len(reps),
+           "phase_us_last_state": phases,
            "arnoldi_steps_per_species_step": float(np.mean(its)), "kernel_ms": ms, "kernel_bytes": kbytes,
            "kernel_fp64_ops": kops, "units": units, "launches": launches,
            "box_voxels_first_last": [reps[0]["box_voxels"], reps[-1]["box_voxels"]],
            "mask_voxels_first_last": [reps[0]["mask_voxels"], reps[-1]["mask_voxels"]],
            "max_rel_res": max(r / b for rep in reps for r, b in zip(rep["res"], rep["bnorm"]))}
     return out, clocks, (solver, lat, prm, init)
+
+
+def run_c5_fgmres(mpm, g, ctx, stream, flush, okw, K, warmup, cnn):
+    """K sampled steps of the growing tumour by flexible GMRES with the network
+    as the right preconditioner from its guess (mpm_solve_fgmres_cnn, one
+    graph per solve): extraction, assembly, guess, solve and scatter per step,
+    timed by CUDA events around the step (the solve's one host wait for its
+    report included), every report checked."""
+    import torch
+    wl = g.wl
+    lat = mpm.DeviceLattice(wl.lattice)
+    init = lat.fields.clone()
+    prm = mpm.DeviceParams(wl.params)
+    sub = ctx.subgrid_create()
+    S = wl.params.nspecies
+    opts = mpm.make_opts(x0_given=1, **okw)
+
+    def one():
+        sub.mpm_box_extract(lat, S, wl.margin)
+        sub.mpm_assemble_coeffs(prm)
+        cnn.guess(sub, lat, prm)
+        return cnn.solve_fgmres(sub, lat, prm, opts, scatter_to=lat)
+
+    g.set_tumour(lat, 0)
+    for _ in range(warmup):
+        one()
+    lat.fields.copy_(init)
+    torch.cuda.synchronize()
+    l0 = ctx.launches()
+    ms, units, its, fb, mx = 0.0, 0, [], 0, 0.0
+    for i, t in enumerate(c5_schedule(K)):
+        g.set_tumour(lat, t)
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rep = one()
+        b.record(stream)
+        b.synchronize()
+        assert rep["status_code"] == mpm.OK, (t, rep)
+        assert all(r <= wl.rtol * bb for r, bb in zip(rep["res"], rep["bnorm"])), (t, rep)
+        ms += a.elapsed_time(b)
+        units += rep["mask_voxels"] * S
+        its.append(sum(rep["iters"]) / S)
+        fb += sum(rep["fallback"])
+        mx = max(mx, max(r / bb for r, bb in zip(rep["res"], rep["bnorm"])))
+    out = {"value": units / (ms / 1e3), "ms_per_step": ms / K, "steps_checked": K,
+           "arnoldi_steps_per_species_step": float(np.mean(its)),
+           "network_applications_per_step": float(np.mean(its)) * S + 1,
+           "fallback_solves": fb, "solves": K * S, "max_rel_res": mx, "launches": ctx.launches() - l0}
+    sub.destroy()
+    del lat
+    return out
+
+
+def bench_growth_cpm(mpm, W, ctx, stream, flush, K, warmup):
+    """The 512x384x384 tumour grown by the device growth driver instead of the
+    script: from the scripted initial tumour (t = 0), K steps of (growth +
+    mitosis launches, then the device-resident FP32-in-FP64 step with the box
+    re-extracted), both queued on one stream between CUDA events; every step's
+    report checked."""
+    import torch
+    wl, extra = W.growth512()
+    W.grow(wl, 0, extra)
+    ncell0 = wl.params.ncell
+    wl.params = W.with_capacity(wl.params, 8 * ncell0)
+    lat = mpm.DeviceLattice(wl.lattice)
+    prm = mpm.DeviceParams(wl.params)
+    drv = mpm.GrowthDriver(ctx, lat, prm, ncell0, p_grow=0.6, K_o2=0.2, K_nut=0.3, o2_min=0.05, v_div=400, seed=2026)
+    solver = mpm.StepSolver(ctx, lat, prm, wl.margin)
+    opts = mpm.make_opts(rtol=wl.rtol, restart=8, maxit=1000, precision=1, inner_rtol=1e-6)
+    for _ in range(warmup):
+        solver.step(opts)
+    ms_cpm = ms_pde = 0.0
+    units = 0
+    boxes = []
+    for i in range(K):
+        flush.fill_(i & 255)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        drv.step(stream=stream)
+        b.record(stream)
+        solver.step_async(opts)
+        c.record(stream)
+        rep = solver.wait()
+        c.synchronize()
+        assert rep["status_code"] == mpm.OK, (i, rep)
+        assert all(r <= wl.rtol * bb for r, bb in zip(rep["res"], rep["bnorm"])), (i, rep)
+        ms_cpm += a.elapsed_time(b)
+        ms_pde += b.elapsed_time(c)
+        units += rep["mask_voxels"] * wl.params.nspecies
+        boxes.append(rep["box_voxels"])
+    cnt = drv.counts()
+    out = {"value": units / (ms_pde / 1e3), "unit": "species-voxel-steps/s", "pde_ms_per_step": ms_pde / K,
+           "growth_ms_per_step": ms_cpm / K, "steps_checked": K, "box_voxels_first_last": [boxes[0], boxes[-1]],
+           "cells_first_last": [ncell0 - 1, cnt["ncell"] - 1], "grown_voxels": cnt["grown"],
+           "divisions": cnt["divisions"],
+           "driver": "mpm_cpm_step: growth into the mask with p = 0.6 c_O/(0.2 + c_O) c_n/(0.3 + c_n) (0 below "
+                     "c_O = 0.05), mitosis at 400 voxels, SplitMix64 counter draws (seed 2026)",
+           "path": "FP32 GMRES(8) inside FP64 refinement, device-resident step, rtol 1e-6"}
+    del solver, drv, lat
+    return out
 
 
 def fp64_peak_instr(sm_mhz, nsm=152):
@@ -390,12 +506,15 @@ def bench_learned(mpm, ctx, samples=20000):
             e = ev[k]
             out[f"{name}_{k}"] = {"value": 32 ** 3 / (e["ms_per_step"] / 1e3), "ms_per_step": e["ms_per_step"],
                                   "iters_per_step": e["iters_per_step"], "max_rel_res": e["max_rel_res"]}
-    # row a13: flexible GMRES with the network as the right preconditioner (FP64)
-    ev = learned.evaluate_fgmres_sphere32(ctx, cnn, rtol=1e-6)
-    for k in ("fgmres", "guess_fgmres"):
-        e = ev[k]
-        out[f"fp64_{k}"] = {"value": 32 ** 3 / (e["ms_per_step"] / 1e3), "ms_per_step": e["ms_per_step"],
-                            "iters_per_step": e["iters_per_step"], "max_rel_res": e["max_rel_res"]}
+    # row a13: flexible GMRES with the network as the right preconditioner,
+    # device-resident (one graph per solve), FP64 and FP32 cycles in FP64 refinement
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        ev = learned.evaluate_fgmres_sphere32(ctx, cnn, rtol=1e-6, precision=prec)
+        for k in ("fgmres", "guess_fgmres"):
+            e = ev[k]
+            out[f"{name}_{k}"] = {"value": 32 ** 3 / (e["ms_per_step"] / 1e3), "ms_per_step": e["ms_per_step"],
+                                  "iters_per_step": e["iters_per_step"], "max_rel_res": e["max_rel_res"],
+                                  "fallback_steps": e["fallback_steps"]}
     cnn.close()
     return out
 
@@ -488,6 +607,44 @@ def bench_shell256(mpm, W, ctx, stream, flush, K, warmup):
                         f"cells in a 128x128x96 region, bbox+4, 3 species, dt=0.05, {K} implicit-Euler steps, rtol 1e-6"}
 
 
+def cnn_only(args):
+    """The network alone: the guess (plan, features, six tcgen05 convolutions)
+    on the growing tumour's training crop (324x264x264, about 4 GB on the
+    device) at its last, largest step, `--steps` launches after `--warmup`,
+    each timed by CUDA events after an L2 flush.  Prints one JSON line (not
+    the benchmark's line): a small case to profile the convolution kernels."""
+    import torch
+    from paper_2505_03067_gb300 import mpm
+    from paper_2505_03067_gb300 import workloads as W
+    wl, extra = W.growth_crop()
+    W.grow(wl, wl.steps - 1, extra)
+    ctx = mpm.Context()
+    lat = mpm.DeviceLattice(wl.lattice)
+    prm = mpm.DeviceParams(wl.params)
+    sub = ctx.subgrid_create()
+    sub.mpm_box_extract(lat, wl.params.nspecies, wl.margin)
+    sub.mpm_assemble_coeffs(prm)
+    act = sub.info()["mask_voxels"]
+    cnn = mpm.CNN(ctx, wl.lattice.dims, 1, mpm.cnn_init_params(7), s_out=0.01)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ts = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cnn.guess(sub, lat, prm)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    print(json.dumps({"mode": "cnn_only", "workload": "growth_crop seed 6 at t = 199 (324x264x264 lattice)",
+                      "active_voxels": act, "ms_per_guess_median": ms, "launches_timed": args.steps,
+                      "tflops": act * CNN_FLOPS_PER_VOXEL / (ms / 1e3) / 1e12}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,8 +658,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="skip the 256^3, 32^3, 64-patch sub-lines")
     ap.add_argument("--train-samples", type=int, default=20000)
+    ap.add_argument("--cnn-only", action="store_true", help="time the network alone on a small case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.cnn_only:
+        return cnn_only(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -585,10 +745,10 @@ def main():
                              "note": "algorithmic bytes of the step launches (extraction, solve, scatter) over the "
                                      "whole step's time" + (" including the network's" if name == "learned_mixed" else "")}
         pk = fp64_peak_instr(sm_mhz)
-        r["roofline_fp64"] = {"bound": "alu", "unit": "T FP64 instr/s", "achieved": r["kernel_fp64_ops"] / sec / 1e12,
+        r["roofline_fp64"] = {"bound": "fp64", "unit": "T FP64 instr/s", "achieved": r["kernel_fp64_ops"] / sec / 1e12,
                               "peak": pk / 1e12, "frac": r["kernel_fp64_ops"] / sec / pk,
                               "peak_source": "2 FP64 thread-instructions per clock per SM x 152 SMs at the median "
-                                             "SM clock under load"}
+                                             "SM clock under load (the FP64 pipe: an ALU bound)"}
 
     head = results["learned_mixed"]
     # the dominant kernel of the headline step: the network's convolutions
@@ -637,10 +797,18 @@ def main():
     del solver, lat
 
     keys = ("value", "ms_per_step", "steps_checked", "arnoldi_steps_per_species_step", "max_rel_res",
-            "box_voxels_first_last", "mask_voxels_first_last", "roofline_hbm", "roofline_fp64")
+            "box_voxels_first_last", "mask_voxels_first_last", "roofline_hbm", "roofline_fp64",
+            "phase_us_last_state")
     paths = {k: {kk: v[kk] for kk in keys} for k, v in results.items()}
     paths["learned_mixed"]["roofline_cnn"] = head["roofline_cnn"]
     paths["learned_mixed"]["cnn_ms_last_step"] = head["cnn_ms_last_step"]
+    # row a13 on the same steps: the network as the right preconditioner of
+    # FP32 flexible GMRES inside FP64 refinement, from its guess
+    barrier()
+    paths["learned_fgmres_mixed"] = run_c5_fgmres(
+        mpm, g, ctx, stream, flush, dict(rtol=g.wl.rtol, restart=args.restart, maxit=1000, **mixed), K,
+        args.warmup, cnn)
+    barrier()
     line = {"metric": METRIC, "value": head["value"], "unit": "species-voxel-steps/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 + bf16 network",
@@ -655,7 +823,8 @@ def main():
                        "network_training": training, "parallelism": f"replicas x{world}"},
             "paths": paths, "roofline": roofline, "e2e": e2e, "gpu_launches": head["launches"], "clocks": clocks}
     if not args.no_workloads:
-        line["workloads"] = {"shell256": bench_shell256(mpm, W, ctx, stream, flush, 20, args.warmup),
+        line["workloads"] = {"growth512_cpm": bench_growth_cpm(mpm, W, ctx, stream, flush, 50, args.warmup),
+                             "shell256": bench_shell256(mpm, W, ctx, stream, flush, 20, args.warmup),
                              "sphere32": bench_sphere32(mpm, W, ctx, stream, flush, args.warmup),
                              "patches64": bench_patches64(mpm, W, ctx, stream, flush, args.warmup),
                              "learned_sphere32": bench_learned(mpm, ctx, args.train_samples)}

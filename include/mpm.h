@@ -292,7 +292,7 @@ mpm_status mpm_step_wait(mpm_ctx *ctx, mpm_subgrid *sub, mpm_report *rep, mpm_bo
  * the same CUDA graph, between the extraction and the solve, with no host
  * round trip: features of the step's box, the network on the box's masked
  * voxels, the prediction into the iterate (c^n where it is not finite).  The
- * solve and its stopping rule are unchanged: GMRES judges the guess.  cnn =
+ * solve and its stopping rule are unchanged: GMRES corrects the guess.  cnn =
  * NULL detaches.  The network must outlive its use; the graph keeps its
  * buffers.  MPM_ERR_ARG while a step is pending; dims are checked at the
  * next step.
@@ -355,6 +355,29 @@ mpm_status mpm_tune_tile(mpm_ctx *ctx, const mpm_lattice *lat, int32_t margin, i
  */
 mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys, mpm_opts *opt,
                            int32_t *out_variant, const char *cache_path, void *stream);
+
+/*
+ * Team planner model of the batched solve (the load imbalance of Sec. 2.5):
+ * the persistent launch splits its CTAs into teams, and an item (one species
+ * of one system) is planned to cost it (F1 + NE) element-equivalents on a
+ * one-CTA team and it (F + NE / c) on a team of c > 1 CTAs, it its Arnoldi
+ * steps and NE its stored elements.  Each round solves the batch from c^n,
+ * fits F1 and F to the measured item times (least squares of the time per
+ * Arnoldi step against NE / c, one intercept per regime, every round pooled),
+ * takes every item's Arnoldi steps from the solve just measured, and plans
+ * again; the round with the smallest imbalance f = t_max / <t> over the teams
+ * minus 1 is kept as the context's model (round 0: the unmeasured model;
+ * rounds 1..64; it stops early once f has not fallen for two rounds).  Later
+ * solves and captured batch steps of a batch with the same item count plan
+ * with it.  history (nullable, 3 (rounds + 1) doubles) gets f, F1 and F per
+ * round (-1 for rounds not run), out_fixed (nullable, 2 doubles) the kept F1
+ * and F.  cache_path as mpm_tune_solver (a hit restores the model; a miss
+ * appends F1, F, f, the per-item steps and the per-team times).  The
+ * iterates are left at c^n.
+ */
+mpm_status mpm_tune_teams(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys, const mpm_opts *opt,
+                          int32_t rounds, const char *cache_path, double *history, double *out_fixed,
+                          void *stream);
 
 /*
  * Learned warm start (a small 3D CNN; the paper has no network).  Six 3x3x3
@@ -455,6 +478,45 @@ mpm_status mpm_cnn_precond(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const m
 mpm_status mpm_solve_fgmres_cnn(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
                                 const mpm_params *prm, const mpm_lattice *scatter_to, const mpm_opts *opt,
                                 mpm_report *rep, void *stream);
+
+/*
+ * Growth driver (the CPM of Sec. 2.1 with its mitosis Steppable, Sec. 2.4;
+ * the paper gives no Hamiltonian, so this is one simple rule coupled to the
+ * fields).  One step, on the device, stream-ordered:
+ *  1. growth: every medium voxel (id 0) of the mask with k >= 1 tumour
+ *     neighbours (6-neighbourhood; off-lattice neighbours are medium) is taken
+ *     over with probability p = p_grow * c_O/(K_o2 + c_O) * c_n/(K_nut + c_n)
+ *     (c_O, c_n: field[0], field[1] at the voxel; p = 0 where c_O < o2_min) by
+ *     the j-th of its tumour neighbours in the order -x, +x, -y, +y, -z, +z;
+ *     every voxel reads the lattice as it was before the step;
+ *  2. mitosis: every cell of at least v_div voxels divides, in increasing id
+ *     order while the tables have room: the daughter takes id *ncell_dev (then
+ *     incremented), the parent's rates (k_cell, q_cell entries written), and
+ *     the parent's voxels strictly above its centroid along an axis drawn per
+ *     cell (integer test coord * volume > sum of coords).
+ * Random numbers: SplitMix64's output function of seed + (c + 1) *
+ * 0x9E3779B97F4A7C15, c = ((4 step + stream) mod 2^24) << 40 | index; growth
+ * u = (word >> 11) * 2^-53 < p (stream 0, voxel index), neighbour j =
+ * ((word >> 32) * k) >> 32 (stream 1), axis = ((word >> 32) * 3) >> 32
+ * (stream 2, cell id): the result does not depend on the launch shape.
+ * lat: device lattice (cell ids updated in place; mask, field[0], field[1]
+ * read).  prm: its rate tables (device, [nspecies][ncell], ncell = capacity;
+ * nspecies >= 2) are written for the daughters.  ncell_dev: device int32, the
+ * ids in use (medium included), read and updated.  stats_dev: device int64[3]
+ * accumulating grown voxels, divisions, and voxels whose id lies outside
+ * [0, capacity) (left unchanged).  MPM_ERR_ARG on a null or inconsistent
+ * argument, p_grow, K_o2 or K_nut negative or NaN, v_div < 2, step < 0.
+ */
+typedef struct {
+    double p_grow;      /* growth probability at saturating O2 and nutrient */
+    double K_o2;        /* half-saturation concentration of O2 (species 0) */
+    double K_nut;       /* half-saturation concentration of the nutrient (species 1) */
+    double o2_min;      /* no growth into a voxel whose O2 is below this */
+    int32_t v_div;      /* a cell of at least v_div voxels divides */
+    int32_t reserved;
+} mpm_cpm_params;
+mpm_status mpm_cpm_step(mpm_ctx *ctx, const mpm_lattice *lat, const mpm_params *prm, const mpm_cpm_params *cp,
+                        uint64_t seed, int64_t step, int32_t *ncell_dev, int64_t *stats_dev, void *stream);
 
 /* Copy `what` of species s from the subgrid into dst (device, box-dense,
  * nx*ny*nz elements of the export type).  Voxels of tiles that hold no

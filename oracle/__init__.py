@@ -540,3 +540,180 @@ def cnn_precond(v_box, s, cell_box, mask_box, params, net_params, s_out):
     x, f = cnn_precond_inputs(v / m, s, cell_box, mask_box, params)
     pred, _ = cnn_forward(x, f, bf16(np.asarray(net_params, np.float64)), s_out)
     return np.where(mask_box > 0, m * pred[..., s], 0.0)
+
+
+# ---------------------------------------------------------------- growth driver (a reading of Sec. 2.1 / 2.4)
+# The paper drives the fields from CompuCell3D's CPM (proliferation, mitosis,
+# death through Steppables) and gives no Hamiltonian.  This is the simple
+# growth / mitosis rule the GPU driver implements, written out plainly:
+#
+# 1. Growth.  Every medium voxel (cell id 0) inside the pleural mask with at
+#    least one tumour neighbour (6-neighbourhood, lattice faces closed) is
+#    taken over with probability p = p_grow * c_O/(K_O + c_O) * c_n/(K_n + c_n)
+#    (O2 = species 0, nutrient = species 1 at that voxel; p = 0 where
+#    c_O < o2_min), by the j-th of its k tumour neighbours in the order
+#    -x, +x, -y, +y, -z, +z.  All voxels read the lattice as it was before
+#    the step (synchronous update).
+# 2. Mitosis.  After growth every cell with at least v_div voxels divides, in
+#    increasing id order while the rate tables have room: the daughter gets
+#    the next free id and the parent's rates, and takes the parent's voxels
+#    strictly above the parent's centroid along an axis drawn per cell
+#    (coord * volume > sum of coords, exact integers).
+#
+# Random numbers: one counter-based generator on both sides, the SplitMix64
+# output function (Steele, Lea and Flood, OOPSLA 2014) applied to
+# seed + (c + 1) * 0x9E3779B97F4A7C15 with the counter c = (4 step + stream)
+# << 40 | index: stream 0 (growth draw u = top 53 bits / 2^53), 1 (neighbour
+# choice j = (top 32 bits * k) >> 32) per voxel, 2 (axis = (top 32 bits * 3)
+# >> 32) per cell.
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_out(z):
+    """The SplitMix64 output (mix) function of 64-bit words (NumPy uint64)."""
+    z = np.asarray(z, np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def cpm_draw(seed: int, step: int, stream: int, idx):
+    """64 random bits for (seed, step, stream, index), index an integer array."""
+    idx = np.asarray(idx, np.uint64)
+    c = (np.uint64((4 * step + stream) & ((1 << 24) - 1)) << np.uint64(40)) | idx
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _M64) + (c + np.uint64(1)) * np.uint64(SPLITMIX_GAMMA)
+    return splitmix64_out(z)
+
+
+def _nbr_ids(cell):
+    """[6, Lz, Ly, Lx] ids of the -x, +x, -y, +y, -z, +z neighbours (0 off the lattice)."""
+    p = np.pad(cell, 1)
+    Lz, Ly, Lx = cell.shape
+    c = (slice(1, Lz + 1), slice(1, Ly + 1), slice(1, Lx + 1))
+    return np.stack([p[c[0], c[1], 0:Lx], p[c[0], c[1], 2:Lx + 2], p[c[0], 0:Ly, c[2]], p[c[0], 2:Ly + 2, c[2]],
+                     p[0:Lz, c[1], c[2]], p[2:Lz + 2, c[1], c[2]]])
+
+
+def cpm_step(cell_id, mask, o2, nut, k_cell, q_cell, ncell: int, cp: dict, seed: int, step: int):
+    """One growth + mitosis step (rules above).  cell_id (Lz, Ly, Lx) int32,
+    o2 / nut float64 of the same shape, k_cell / q_cell [S][capacity] float64,
+    ncell ids in use.  Returns (cell_id, k_cell, q_cell, ncell, stats) with
+    stats = {grown, divisions}; the inputs are not modified."""
+    cell = np.asarray(cell_id, np.int32)
+    Lz, Ly, Lx = cell.shape
+    v = np.arange(cell.size, dtype=np.uint64).reshape(cell.shape)
+    nb = _nbr_ids(cell)
+    tum = nb > 0
+    k = tum.sum(axis=0)
+    cand = (cell == 0) & (np.asarray(mask) > 0) & (k > 0)
+    c0 = np.asarray(o2, np.float64)
+    c1 = np.asarray(nut, np.float64)
+    with np.errstate(all="ignore"):
+        p = cp["p_grow"] * (c0 / (cp["K_o2"] + c0)) * (c1 / (cp["K_nut"] + c1))
+    p = np.where(c0 < cp["o2_min"], 0.0, p)
+    u = (cpm_draw(seed, step, 0, v) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    grow = cand & (u < p)
+    h2 = cpm_draw(seed, step, 1, v) >> np.uint64(32)
+    j = ((h2 * k.astype(np.uint64)) >> np.uint64(32)).astype(np.int64)
+    # the j-th tumour neighbour: position of the (j+1)-th True along axis 0
+    rank = np.cumsum(tum, axis=0) - 1
+    pick = np.argmax(tum & (rank == j[None]), axis=0)
+    chosen = np.take_along_axis(nb, pick[None], axis=0)[0]
+    new = np.where(grow, chosen, cell).astype(np.int32)
+    # mitosis
+    cap = k_cell.shape[1]
+    ids = new.reshape(-1)
+    zz, yy, xx = np.indices(new.shape)
+    coords = [xx.reshape(-1).astype(np.int64), yy.reshape(-1).astype(np.int64), zz.reshape(-1).astype(np.int64)]
+    vol = np.bincount(ids, minlength=cap).astype(np.int64)
+    sums = [np.zeros(cap, np.int64) for _ in range(3)]
+    for a in range(3):
+        np.add.at(sums[a], ids, coords[a])
+    k_new = np.array(k_cell, np.float64, copy=True)
+    q_new = np.array(q_cell, np.float64, copy=True)
+    daughter = np.full(cap, -1, np.int64)
+    axis = np.zeros(cap, np.int64)
+    nc = ncell
+    for cid in range(1, ncell):
+        if vol[cid] >= cp["v_div"] and nc < cap:
+            daughter[cid] = nc
+            h3 = int(cpm_draw(seed, step, 2, np.array([cid]))[0]) >> 32
+            axis[cid] = (h3 * 3) >> 32
+            k_new[:, nc] = k_new[:, cid]
+            q_new[:, nc] = q_new[:, cid]
+            nc += 1
+    d = daughter[ids]
+    a = axis[ids]
+    cpos = np.where(a == 0, coords[0], np.where(a == 1, coords[1], coords[2]))
+    spos = np.where(a == 0, sums[0][ids], np.where(a == 1, sums[1][ids], sums[2][ids]))
+    move = (ids > 0) & (d >= 0) & (cpos * vol[ids] > spos)
+    out = np.where(move, d, ids).astype(np.int32).reshape(new.shape)
+    return out, k_new, q_new, nc, {"grown": int(grow.sum()), "divisions": int(nc - ncell)}
+
+
+def cpm_step_loops(cell_id, mask, o2, nut, k_cell, q_cell, ncell: int, cp: dict, seed: int, step: int):
+    """cpm_step written voxel by voxel in plain Python (tiny lattices only):
+    the rules above, literally."""
+    cell = np.asarray(cell_id, np.int32)
+    Lz, Ly, Lx = cell.shape
+    new = cell.copy()
+    grown = 0
+    for z in range(Lz):
+        for y in range(Ly):
+            for x in range(Lx):
+                if cell[z, y, x] != 0 or not mask[z, y, x]:
+                    continue
+                nbrs = []
+                for dz, dy, dx in ((0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)):
+                    zz, yy, xx = z + dz, y + dy, x + dx
+                    if 0 <= zz < Lz and 0 <= yy < Ly and 0 <= xx < Lx and cell[zz, yy, xx] > 0:
+                        nbrs.append(int(cell[zz, yy, xx]))
+                if not nbrs:
+                    continue
+                c0, c1 = float(o2[z, y, x]), float(nut[z, y, x])
+                if c0 < cp["o2_min"]:
+                    continue
+                p = cp["p_grow"] * (c0 / (cp["K_o2"] + c0)) * (c1 / (cp["K_nut"] + c1))
+                vi = x + Lx * (y + Ly * z)
+                u = (int(cpm_draw(seed, step, 0, np.array([vi]))[0]) >> 11) * 2.0 ** -53
+                if u < p:
+                    h2 = int(cpm_draw(seed, step, 1, np.array([vi]))[0]) >> 32
+                    new[z, y, x] = nbrs[(h2 * len(nbrs)) >> 32]
+                    grown += 1
+    cap = k_cell.shape[1]
+    k_new = np.array(k_cell, np.float64, copy=True)
+    q_new = np.array(q_cell, np.float64, copy=True)
+    vol = {}
+    sums = {}
+    for z in range(Lz):
+        for y in range(Ly):
+            for x in range(Lx):
+                c = int(new[z, y, x])
+                if c > 0:
+                    vol[c] = vol.get(c, 0) + 1
+                    s = sums.setdefault(c, [0, 0, 0])
+                    s[0] += x
+                    s[1] += y
+                    s[2] += z
+    plan = {}
+    nc = ncell
+    for cid in range(1, ncell):
+        if vol.get(cid, 0) >= cp["v_div"] and nc < cap:
+            h3 = int(cpm_draw(seed, step, 2, np.array([cid]))[0]) >> 32
+            plan[cid] = (nc, (h3 * 3) >> 32)
+            k_new[:, nc] = k_new[:, cid]
+            q_new[:, nc] = q_new[:, cid]
+            nc += 1
+    out = new.copy()
+    for z in range(Lz):
+        for y in range(Ly):
+            for x in range(Lx):
+                c = int(new[z, y, x])
+                if c in plan:
+                    d, a = plan[c]
+                    if (x, y, z)[a] * vol[c] > sums[c][a]:
+                        out[z, y, x] = d
+    return out, k_new, q_new, nc, {"grown": grown, "divisions": nc - ncell}

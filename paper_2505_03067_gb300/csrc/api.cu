@@ -132,6 +132,7 @@ mpm_status mpm_destroy(mpm_ctx *ctx)
     cudaFree(ctx->d_args);
     cudaFree(ctx->d_tmp);
     cudaFree(ctx->d_fg);
+    cudaFree(ctx->d_cpm);
     cudaFree(ctx->d_prof);
     cudaFree(ctx->d_tune);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);

@@ -420,11 +420,24 @@ struct mpm_ctx {
     cudaStream_t cap_stream = nullptr;  // stream used only for graph capture
     cudaStream_t fg_cs[3] = {};  // capture streams of the flexible GMRES graph (fgmres.cu)
     void *fg_cache = nullptr;    // its last graph
+    void *d_cpm = nullptr;       // growth driver scratch (cpm.cu)
+    size_t cpm_cap = 0;
     void *d_tune = nullptr;      // tuner scratch tables
     size_t tune_cap = 0;
     unsigned long long *d_prof = nullptr;
     unsigned long long h_prof[16] = {};   // phase timer slots (kProfSlots used)
     double last_imbalance = 0.0; // t_max / <t> - 1 over the teams of the last solve
+    // team planning of the batched solve (solver.cu); the model is measured
+    // by mpm_tune_teams (tune.cu)
+    double team_fixed = 3000.0;         // per-pass fixed cost of an item on a team of several CTAs
+    double team_fixed1 = 3000.0;        //   and on a one-CTA team (no grid barrier), element-equivalents
+    int32_t team_use_iters = 0;         // weight items by their Arnoldi steps in item_iters
+    uint64_t team_gen = 0;              // bumped when the model changes (captured plans are redone)
+    std::vector<double> item_iters;     // per work item of the last solve: Arnoldi steps
+    std::vector<double> item_ne;        //   stored elements
+    std::vector<double> item_cta;       //   CTAs of its team
+    std::vector<double> item_ns;        //   device time (its team's CTA 0)
+    std::vector<double> team_ns;        // per team of the last solve: device time
     int64_t step_nfull = 0;      // mpm_step: full extractions so far (MPM_COUNTER_STEP_FULL_EXTRACTIONS)
     // test hooks
     uint64_t timeout_ns = 2000000000ull;

@@ -102,17 +102,24 @@ int mpm_solver_variants(int prec, int m)
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Team plan of the batched form, with the paper's load-imbalance concern
-// (Sec. 2.5) in mind.  A pass of item i on a team of c CTAs costs about
-// kPassFixed + work_i / c element-equivalents: the fixed part is the per-pass
-// synchronisation (team barrier, reduction, least squares; the constant was
-// set by timing the 64-patch batch), the rest the streaming work.  For a
-// candidate makespan T, items whose cost on one CTA fits in T are packed
-// first-fit-decreasing onto single-CTA teams of capacity T; larger items get
-// ceil(work / (T - fixed)) CTAs of their own.  The smallest T that fits in G
-// CTAs is kept (binary search), and the spare CTAs go to the largest teams.
-static constexpr double kPassFixed = 3000.0;
+// (Sec. 2.5) in mind.  Item i costs it_i (F1 + NE_i) element-equivalents on a
+// one-CTA team and it_i (F + NE_i / c) on a team of c > 1 CTAs: it_i Arnoldi
+// passes, each a fixed part (F1: block barriers and the least squares; F:
+// grid barriers among the team's CTAs as well) and a streaming part.  Without
+// a measured model it_i = 1 and F1 = F = 3000 (set by timing the 64-patch
+// batch); mpm_tune_teams fits F1 and F to measured item times and takes it_i
+// from the previous solve.  For a candidate makespan T, items whose one-CTA
+// cost fits in T are packed first-fit-decreasing onto one-CTA teams of
+// capacity T; larger items get ceil(work_i / (T - fix_i)) CTAs of their own.
+// The smallest T that fits in G CTAs is kept (binary search), and the spare
+// CTAs go to the teams with the most streaming work per CTA.
+struct ItemCost {
+    double one;      // on one CTA
+    double fix;      // fixed part on a team of several CTAs
+    double work;     // streaming part (divided by the team's CTAs)
+};
 
-static bool try_plan(const std::vector<double> &work, const std::vector<int> &idx, int G, double T,
+static bool try_plan(const std::vector<ItemCost> &ic, const std::vector<int> &idx, int G, double T,
                      std::vector<std::vector<int>> &members, std::vector<int> &nbk)
 {
     members.clear();
@@ -120,10 +127,10 @@ static bool try_plan(const std::vector<double> &work, const std::vector<int> &id
     std::vector<double> load;
     int used = 0;
     for (int i : idx) {
-        const double one = kPassFixed + work[i];
+        const double one = ic[i].one;
         if (one > T) {
-            if (T <= kPassFixed * 1.05) return false;
-            const int c = (int)std::ceil(work[i] / (T - kPassFixed));
+            if (T <= ic[i].fix * 1.05) return false;
+            const int c = std::max(2, (int)std::ceil(ic[i].work / (T - ic[i].fix)));
             members.push_back({i});
             nbk.push_back(c);
             load.push_back(-1.0);
@@ -147,42 +154,44 @@ static bool try_plan(const std::vector<double> &work, const std::vector<int> &id
     return used <= G;
 }
 
-static void plan_teams(const std::vector<double> &work, int G, std::vector<TeamDesc> &teams,
+static void plan_teams(const std::vector<ItemCost> &ic, int G, std::vector<TeamDesc> &teams,
                        std::vector<int32_t> &order, std::vector<int32_t> &block_team)
 {
-    const int nsys = (int)work.size();
+    const int nsys = (int)ic.size();
     std::vector<int> idx(nsys);
     for (int i = 0; i < nsys; ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return ic[a].one > ic[b].one; });
     std::vector<std::vector<int>> members;
     std::vector<int> nbk;
     if (nsys == 1) {
         members = {{0}};
         nbk = {G};
     } else {
-        double hi = 1.0;   // everything on one CTA
-        for (int i = 0; i < nsys; ++i) hi += kPassFixed + work[i];
-        double lo = kPassFixed * 1.05;
+        double hi = 1.0, lo = 0.0;   // hi: everything on one CTA
+        for (int i = 0; i < nsys; ++i) {
+            hi += ic[i].one;
+            lo = std::max(lo, std::min(ic[i].one, ic[i].fix * 1.05));
+        }
         for (int it = 0; it < 60; ++it) {
             const double mid = 0.5 * (lo + hi);
             std::vector<std::vector<int>> m2;
             std::vector<int> n2;
-            if (try_plan(work, idx, G, mid, m2, n2)) hi = mid;
+            if (try_plan(ic, idx, G, mid, m2, n2)) hi = mid;
             else lo = mid;
         }
-        if (!try_plan(work, idx, G, hi, members, nbk)) {   // cannot happen for G >= 1; keep a valid plan
+        if (!try_plan(ic, idx, G, hi, members, nbk)) {   // cannot happen for G >= 1; keep a valid plan
             members = {idx};
             nbk = {G};
         }
         int used = 0;
         for (int c : nbk) used += c;
-        // spare CTAs to the teams with the most work per CTA
+        // spare CTAs to the teams with the most streaming work per CTA
         while (used < G) {
             int best = 0;
             double bw = -1.0;
             for (size_t t = 0; t < members.size(); ++t) {
                 double w = 0.0;
-                for (int i : members[t]) w += work[i];
+                for (int i : members[t]) w += ic[i].work;
                 if (w / nbk[t] > bw) { bw = w / nbk[t]; best = (int)t; }
             }
             nbk[best] += 1;
@@ -320,7 +329,19 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
         P.G = (int)std::min<double>(gmax, std::max(1.0, want));
         P.G = std::max(P.G, std::min(P.nitem, gmax));
     }
-    plan_teams(work, P.G, P.teams, P.order, P.block_team);
+    {
+        // the cost model: measured Arnoldi steps per item when the context has
+        // them for a batch of this many items, else one pass each
+        const bool iters = ctx->team_use_iters && (int)ctx->item_iters.size() == P.nitem;
+        std::vector<ItemCost> ic(P.nitem);
+        for (int i = 0; i < P.nitem; ++i) {
+            const double it = iters ? std::max(1.0, ctx->item_iters[i]) : 1.0;
+            ic[i].one = it * (ctx->team_fixed1 + work[i]);
+            ic[i].fix = it * ctx->team_fixed;
+            ic[i].work = it * work[i];
+        }
+        plan_teams(ic, P.G, P.teams, P.order, P.block_team);
+    }
     P.nteam = (int)P.teams.size();
     P.o_sys = 0;
     P.o_team = a256(P.o_sys + sizeof(SysDev) * P.nitem);
@@ -409,11 +430,24 @@ static mpm_status finish_solve(mpm_ctx *ctx, const SolvePlan &P, mpm_subgrid *co
         R[i].stored_voxels = sub->NE;
         R[i].solve_ms = ms;
     }
-    // the paper's load imbalance f = t_max / <t> - 1 (Sec. 2.5), over CTA teams
+    // the paper's load imbalance f = t_max / <t> - 1 (Sec. 2.5), over CTA
+    // teams; the per-item measurements feed the team planner's model
     {
         std::vector<double> tt(P.nteam, 0.0);
+        ctx->item_iters.assign(P.nitem, 0.0);
+        ctx->item_ne.assign(P.nitem, 0.0);
+        ctx->item_cta.assign(P.nitem, 1.0);
+        ctx->item_ns.assign(P.nitem, 0.0);
         for (int t = 0; t < P.nteam; ++t)
-            for (int k = P.teams[t].sys_begin; k < P.teams[t].sys_end; ++k) tt[t] += (double)hrep[P.order[k]].t_ns;
+            for (int k = P.teams[t].sys_begin; k < P.teams[t].sys_end; ++k) {
+                const int it = P.order[k];
+                tt[t] += (double)hrep[it].t_ns;
+                ctx->item_iters[it] = (double)hrep[it].iters[0];
+                ctx->item_ne[it] = (double)subs[P.item_sys[it]]->NE;
+                ctx->item_cta[it] = (double)P.teams[t].nblocks;
+                ctx->item_ns[it] = (double)hrep[it].t_ns;
+            }
+        ctx->team_ns = tt;
         double mx = 0.0, mean = 0.0;
         for (double v : tt) { mx = std::max(mx, v); mean += v; }
         mean /= std::max(1, P.nteam);
@@ -534,6 +568,7 @@ static void batch_key(mpm_ctx *ctx, mpm_subgrid *const *subs, const mpm_lattice 
     put(&ctx->solver_variant, sizeof(int32_t));
     put(&ctx->timeout_ns, sizeof(uint64_t));
     put(&ctx->skip_block, sizeof(int32_t));
+    put(&ctx->team_gen, sizeof(uint64_t));
     for (int i = 0; i < nsys; ++i) {
         put(&subs[i], sizeof(void *));
         put(&subs[i]->gen, sizeof(subs[i]->gen));

@@ -11,6 +11,7 @@
 // on-disk cache, one line per key: the GPU name, precision, tolerance, and
 // for every system its species count with bucketed box dims
 // (nearest power of two) and mask occupancy (tenths).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -172,6 +173,232 @@ extern "C" mpm_status mpm_tune_solver(mpm_ctx *ctx, mpm_subgrid *const *subs, in
     *out_variant = best_v;
     ctx->solver_variant = best_v;
     cache_store(cache_path, key, best_m, best_v);
+    // leave the iterates at c^n for the caller's own solve
+    for (int i = 0; i < nsys; ++i) {
+        mpm_subgrid *sub = subs[i];
+        for (int s = 0; s < sub->nspecies; ++s)
+            MPM_CU(cudaMemcpyAsync(sub->x[s], sub->cn[s], (size_t)sub->NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        sub->x_fresh = true;
+    }
+    return MPM_OK;
+}
+
+// ------------------------------------------------------------------ team model
+// The team planner's model of the batched solve (Sec. 2.5's load imbalance):
+// item i costs it_i (F1 + NE_i) element-equivalents on one CTA and
+// it_i (F + NE_i / c) on c > 1 CTAs.  Each round solves the batch from c^n,
+// fits F1 and F to the measured item times (least squares of the time per
+// Arnoldi step against NE_i / c_i with one intercept per regime, all rounds'
+// items pooled), takes it_i from the solve just measured, and plans again;
+// the round with the smallest imbalance f = t_max / <t> - 1 over the teams
+// wins.  Stops after `rounds` rounds or when f has not fallen for two.
+namespace {
+
+// Least squares of y = beta x + alpha1 [one CTA] + alpha [several CTAs] over
+// the measured items (x = NE / c, y = time per Arnoldi step): F1 =
+// alpha1 / beta, F = alpha / beta.  A regime without items keeps its value.
+bool fit_fixed(const std::vector<double> &x, const std::vector<double> &y, const std::vector<int> &one, double &F1,
+               double &F)
+{
+    // normal equations of the three unknowns (beta, alpha1, alpha)
+    double a[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, r[3] = {0, 0, 0};
+    int n1 = 0, nm = 0;
+    for (size_t i = 0; i < x.size(); ++i) {
+        const double f[3] = {x[i], one[i] ? 1.0 : 0.0, one[i] ? 0.0 : 1.0};
+        n1 += one[i] ? 1 : 0;
+        nm += one[i] ? 0 : 1;
+        for (int p = 0; p < 3; ++p) {
+            r[p] += f[p] * y[i];
+            for (int q = 0; q < 3; ++q) a[p][q] += f[p] * f[q];
+        }
+    }
+    if (n1 + nm < 3) return false;
+    // drop a regime without measurements
+    int keep[3], nk = 0;
+    for (int p = 0; p < 3; ++p)
+        if (a[p][p] > 0.0) keep[nk++] = p;
+    if (nk < 2 || keep[0] != 0) return false;
+    double m[3][4];
+    for (int p = 0; p < nk; ++p) {
+        for (int q = 0; q < nk; ++q) m[p][q] = a[keep[p]][keep[q]];
+        m[p][nk] = r[keep[p]];
+    }
+    for (int c = 0; c < nk; ++c) {   // Gaussian elimination with partial pivoting
+        int piv = c;
+        for (int p = c + 1; p < nk; ++p)
+            if (std::fabs(m[p][c]) > std::fabs(m[piv][c])) piv = p;
+        if (!(std::fabs(m[piv][c]) > 0.0)) return false;
+        for (int q = 0; q <= nk; ++q) std::swap(m[c][q], m[piv][q]);
+        for (int p = 0; p < nk; ++p) {
+            if (p == c) continue;
+            const double f = m[p][c] / m[c][c];
+            for (int q = c; q <= nk; ++q) m[p][q] -= f * m[c][q];
+        }
+    }
+    double sol[3] = {0, -1, -1};
+    for (int p = 0; p < nk; ++p) sol[keep[p]] = m[p][nk] / m[p][p];
+    const double beta = sol[0];
+    if (!(beta > 0.0)) return false;
+    auto clampF = [](double v) { return std::min(1e7, std::max(0.0, v)); };
+    if (a[1][1] > 0.0 && sol[1] >= 0.0) F1 = clampF(sol[1] / beta);
+    if (a[2][2] > 0.0 && sol[2] >= 0.0) F = clampF(sol[2] / beta);
+    return true;
+}
+
+std::string teams_key(const std::string &k) { return k + ";teams"; }
+
+bool teams_lookup(const char *path, const std::string &key, double &F1, double &F, double &f, int &use,
+                  std::vector<double> &iters)
+{
+    if (!path) return false;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return false;
+    std::vector<char> line(1 << 20);
+    bool found = false;
+    while (fgets(line.data(), (int)line.size(), fp)) {
+        std::string s(line.data());
+        if (s.compare(0, key.size(), key) != 0 || s.size() <= key.size() || s[key.size()] != ' ') continue;
+        // key F1 F f use nitem it_0 .. it_{n-1} | team times (ns)
+        const char *p = s.c_str() + key.size();
+        char *e = nullptr;
+        const double F1_ = strtod(p, &e);
+        const double F_ = strtod(e, &e);
+        const double f_ = strtod(e, &e);
+        const long u = strtol(e, &e, 10);
+        const long n = strtol(e, &e, 10);
+        if (n < 0 || n > (1 << 20)) continue;
+        std::vector<double> it(n);
+        bool ok = true;
+        for (long i = 0; i < n && ok; ++i) {
+            char *e2 = nullptr;
+            it[i] = strtod(e, &e2);
+            ok = e2 != e;
+            e = e2;
+        }
+        if (!ok) continue;
+        F1 = F1_;
+        F = F_;
+        f = f_;
+        use = u != 0 ? 1 : 0;
+        iters = it;
+        found = true;
+    }
+    fclose(fp);
+    return found;
+}
+
+void teams_store(const char *path, const std::string &key, double F1, double F, double f, int use,
+                 const std::vector<double> &iters, const std::vector<double> &team_ns)
+{
+    if (!path) return;
+    FILE *fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s %.17g %.17g %.6g %d %zu", key.c_str(), F1, F, f, use, iters.size());
+    for (double v : iters) fprintf(fp, " %.0f", v);
+    fprintf(fp, " |");
+    for (double v : team_ns) fprintf(fp, " %.0f", v);
+    fprintf(fp, "\n");
+    fclose(fp);
+}
+
+}  // namespace
+
+extern "C" mpm_status mpm_tune_teams(mpm_ctx *ctx, mpm_subgrid *const *subs, int32_t nsys, const mpm_opts *opt,
+                                     int32_t rounds, const char *cache_path, double *history, double *out_fixed,
+                                     void *stream)
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!subs || nsys < 1 || !opt || rounds < 1 || rounds > 64)
+        return mpm_fail(ctx, MPM_ERR_ARG, "tune_teams: null argument or rounds out of [1, 64]");
+    for (int i = 0; i < nsys; ++i)
+        if (!subs[i] || !subs[i]->assembled) return mpm_fail(ctx, MPM_ERR_ARG, "tune_teams: subgrid not assembled");
+    const std::string key = teams_key(cache_key(ctx, subs, nsys, opt));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (history)
+        for (int r = 0; r <= rounds; ++r) history[3 * r] = history[3 * r + 1] = history[3 * r + 2] = -1.0;
+    {
+        double F1 = 0.0, F = 0.0, f = 0.0;
+        int use = 0;
+        std::vector<double> it;
+        if (teams_lookup(cache_path, key, F1, F, f, use, it)) {
+            ctx->team_fixed1 = F1;
+            ctx->team_fixed = F;
+            ctx->team_use_iters = use;
+            if (use) ctx->item_iters = it;
+            ctx->team_gen += 1;
+            if (history) {
+                history[0] = f;
+                history[1] = F1;
+                history[2] = F;
+            }
+            if (out_fixed) {
+                out_fixed[0] = F1;
+                out_fixed[1] = F;
+            }
+            return MPM_OK;
+        }
+    }
+    mpm_opts o = *opt;
+    o.x0_given = 0;
+    std::vector<mpm_report> reps(nsys);
+    std::vector<double> xs, ys;
+    std::vector<int> ones;
+    double best_f = 1e300, best_F1 = ctx->team_fixed1, best_F = ctx->team_fixed;
+    int best_use = 0;
+    std::vector<double> best_iters, best_team;
+    int since = 0;
+    for (int round = 0; round <= rounds; ++round) {
+        if (round > 0) {
+            double F1 = ctx->team_fixed1, F = ctx->team_fixed;
+            if (fit_fixed(xs, ys, ones, F1, F)) {
+                ctx->team_fixed1 = F1;
+                ctx->team_fixed = F;
+            }
+            ctx->team_use_iters = 1;   // item_iters: the solve just measured
+        } else {
+            ctx->team_use_iters = 0;
+        }
+        const double F1_used = ctx->team_fixed1, F_used = ctx->team_fixed;
+        const int use_used = ctx->team_use_iters;
+        const std::vector<double> iters_used = ctx->item_iters;
+        const mpm_status r = mpm_solve_impl(ctx, subs, nullptr, nsys, &o, reps.data(), st);
+        if (r != MPM_OK && r != MPM_ERR_NOCONV) return r;
+        const double f = ctx->last_imbalance;
+        if (history) {
+            history[3 * round] = f;
+            history[3 * round + 1] = F1_used;
+            history[3 * round + 2] = F_used;
+        }
+        for (size_t i = 0; i < ctx->item_ns.size(); ++i)
+            if (ctx->item_iters[i] > 0.0) {
+                xs.push_back((ctx->item_ne[i] + 1.0) / ctx->item_cta[i]);
+                ys.push_back(ctx->item_ns[i] / ctx->item_iters[i]);
+                ones.push_back(ctx->item_cta[i] <= 1.0 ? 1 : 0);
+            }
+        if (f < best_f) {
+            best_f = f;
+            best_F1 = F1_used;
+            best_F = F_used;
+            best_use = use_used;
+            best_iters = use_used ? iters_used : std::vector<double>();
+            best_team = ctx->team_ns;
+            since = 0;
+        } else if (++since >= 2) {
+            break;
+        }
+    }
+    ctx->err.clear();
+    ctx->team_fixed1 = best_F1;
+    ctx->team_fixed = best_F;
+    ctx->team_use_iters = best_use;
+    if (best_use) ctx->item_iters = best_iters;
+    ctx->team_gen += 1;
+    teams_store(cache_path, key, best_F1, best_F, best_f, best_use, best_iters, best_team);
+    if (out_fixed) {
+        out_fixed[0] = best_F1;
+        out_fixed[1] = best_F;
+    }
     // leave the iterates at c^n for the caller's own solve
     for (int i = 0; i < nsys; ++i) {
         mpm_subgrid *sub = subs[i];

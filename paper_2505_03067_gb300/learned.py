@@ -92,11 +92,14 @@ def evaluate_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, precision: int 
     return out
 
 
-def evaluate_fgmres_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, steps: int = 10, restart: int = 8):
+def evaluate_fgmres_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, steps: int = 10, restart: int = 8,
+                             precision: int = 0, inner_rtol: float = 1e-6):
     """The 32^3 sphere workload advanced `steps` steps by flexible GMRES with the
-    network as the right preconditioner (mpm_solve_fgmres_cnn, FP64), from
-    x0 = c^n and from the learned guess.  Returns Arnoldi steps and device time
-    per step (extraction and assembly excluded, as in evaluate_sphere32)."""
+    network as the right preconditioner (mpm_solve_fgmres_cnn; precision 1:
+    FP32 cycles inside FP64 refinement), from x0 = c^n and from the learned
+    guess.  Returns Arnoldi steps, the steps whose solve fell back to plain
+    GMRES, and device time per step (extraction and assembly excluded, as in
+    evaluate_sphere32)."""
     import torch
     wl = W.sphere32()
     out = {}
@@ -104,7 +107,7 @@ def evaluate_fgmres_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, steps: i
         lat = mpm.DeviceLattice(wl.lattice)
         prm = mpm.DeviceParams(wl.params)
         sub = ctx.subgrid_create()
-        its, ms, res = [], 0.0, []
+        its, ms, res, fb = [], 0.0, [], 0
         stream = torch.cuda.current_stream()
         for _ in range(steps):
             sub.mpm_box_extract(lat, 1, wl.margin)
@@ -114,15 +117,17 @@ def evaluate_fgmres_sphere32(ctx: mpm.Context, cnn, rtol: float = 1e-6, steps: i
             if guess:
                 cnn.guess(sub, lat, prm)
             rep = cnn.solve_fgmres(sub, lat, prm, mpm.make_opts(rtol=rtol, restart=restart, maxit=500,
+                                                                precision=precision, inner_rtol=inner_rtol,
                                                                 x0_given=int(guess)), scatter_to=lat)
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
             its.append(rep["iters"][0])
             res.append(rep["res"][0] / rep["bnorm"][0])
+            fb += rep["fallback"][0]
         out["guess_fgmres" if guess else "fgmres"] = {"iters_per_step": float(np.mean(its)),
                                                        "ms_per_step": ms / steps, "max_rel_res": float(max(res)),
-                                                       "final": lat.fields_numpy()}
+                                                       "fallback_steps": fb, "final": lat.fields_numpy()}
     return out
 
 

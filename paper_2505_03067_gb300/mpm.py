@@ -30,10 +30,10 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_subgrid_info", "mpm_box_extract", "mpm_assemble_coeffs", "mpm_solve_step", "mpm_solve_batch",
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
-           "mpm_tune_tile", "mpm_tune_solver", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
+           "mpm_tune_tile", "mpm_tune_solver", "mpm_tune_teams", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
            "mpm_cnn_get_params", "mpm_cnn_load_image", "mpm_cnn_export_features", "mpm_cnn_export_preact", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
            "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond",
-           "mpm_step_host", "mpm_debug_convert", "mpm_step_set_network"]
+           "mpm_step_host", "mpm_debug_convert", "mpm_step_set_network", "mpm_cpm_step"]
 
 
 class mpm_box(C.Structure):
@@ -86,6 +86,11 @@ class mpm_report(C.Structure):
                 "fallback": list(self.fallback[:nspecies])}
 
 
+class mpm_cpm_params(C.Structure):
+    _fields_ = [("p_grow", C.c_double), ("K_o2", C.c_double), ("K_nut", C.c_double), ("o2_min", C.c_double),
+                ("v_div", C.c_int32), ("reserved", C.c_int32)]
+
+
 class mpm_subgrid_desc(C.Structure):
     _fields_ = [("box", mpm_box), ("n", C.c_int32 * 3), ("tile", C.c_int32 * 3), ("ntiles", C.c_int32),
                 ("nactive", C.c_int32), ("stored_voxels", C.c_int64), ("mask_voxels", C.c_int64),
@@ -131,6 +136,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_cnn_precond": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, P, P, P],
         "mpm_tune_tile": [P, C.POINTER(mpm_lattice), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), P],
         "mpm_tune_solver": [P, C.POINTER(P), C.c_int32, C.POINTER(mpm_opts), C.POINTER(C.c_int32), C.c_char_p, P],
+        "mpm_tune_teams": [P, C.POINTER(P), C.c_int32, C.POINTER(mpm_opts), C.c_int32, C.c_char_p, P, P, P],
         "mpm_batch_step": [P, C.POINTER(P), C.POINTER(C.POINTER(mpm_lattice)), C.POINTER(C.POINTER(mpm_params)),
                            C.c_int32, C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
         "mpm_solve_step": [P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
@@ -152,6 +158,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_counter_get": [P, C.c_int32, C.POINTER(C.c_int64)],
         "mpm_box_bounds_noalloc": [P, C.POINTER(C.c_int32), C.c_int32, P, P],
         "mpm_debug_convert": [P, P, P, P, P, P, C.c_int64, P],
+        "mpm_cpm_step": [P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_cpm_params), C.c_uint64,
+                         C.c_int64, P, P, P],
         "mpm_step_set_network": [P, P, P],
     }
     for name, args in sig.items():
@@ -302,6 +310,20 @@ class Context:
         self._check(self.lib.mpm_tune_solver(self.ptr, hs, n, C.byref(opts), C.byref(v), cp, _stream_ptr(stream)),
                     "mpm_tune_solver")
         return int(opts.restart), int(v.value)
+
+    def mpm_tune_teams(self, subs, opts: "mpm_opts", rounds: int = 6, cache_path=None, stream=None):
+        """The team planner's measured model (mpm_tune_teams): returns the
+        imbalance f of every round run and the kept per-pass fixed cost F."""
+        n = len(subs)
+        hs = (C.c_void_p * n)(*[s.h.value for s in subs])
+        hist = (C.c_double * (3 * (rounds + 1)))()
+        F = (C.c_double * 2)()
+        cp = cache_path.encode() if cache_path else None
+        self._check(self.lib.mpm_tune_teams(self.ptr, hs, n, C.byref(opts), rounds, cp, hist, F,
+                                            _stream_ptr(stream)), "mpm_tune_teams")
+        h = [tuple(hist[3 * r:3 * r + 3]) for r in range(rounds + 1) if hist[3 * r] >= 0.0]
+        return {"f": [v[0] for v in h], "fixed_per_round": [(v[1], v[2]) for v in h],
+                "fixed": (float(F[0]), float(F[1]))}
 
     def subgrid_create(self) -> "Subgrid":
         h = C.c_void_p()
@@ -544,9 +566,15 @@ class BatchStepper:
         for sub, prm in zip(self.subs, self.prms):
             sub.mpm_assemble_coeffs(prm)
 
-    def tune(self, opts: mpm_opts, cache_path=None):
-        """Restart length and kernel variant for this batch (mpm_tune_solver)."""
-        return self.ctx.mpm_tune_solver(self.subs, opts, cache_path)
+    def tune(self, opts: mpm_opts, cache_path=None, team_rounds: int = 6):
+        """Restart length and kernel variant for this batch (mpm_tune_solver),
+        then the team planner's measured model (mpm_tune_teams; team_rounds 0
+        skips it).  Returns (restart, variant); the team rounds' imbalances
+        are kept in self.team_tuning."""
+        m, var = self.ctx.mpm_tune_solver(self.subs, opts, cache_path)
+        self.team_tuning = (self.ctx.mpm_tune_teams(self.subs, opts, team_rounds, cache_path)
+                            if team_rounds > 0 else None)
+        return m, var
 
     def step(self, opts: mpm_opts, stream=None, allow=(ERR_NOCONV,)):
         n = len(self.subs)
@@ -617,6 +645,35 @@ def cnn_init_params(seed: int = 0, last_scale: float = 0.1):
             w *= last_scale
         out += [w, np.zeros(co)]
     return np.concatenate(out).astype(np.float32)
+
+
+class GrowthDriver:
+    """The device growth driver (mpm_cpm_step) on a device lattice: tumour
+    growth into the mask driven by O2 and nutrient, and mitosis.  The rate
+    tables of `prm` must have room for the daughters (capacity = their
+    ncell); `ncell` is the number of ids in use at the start."""
+
+    def __init__(self, ctx: Context, lat: DeviceLattice, prm: DeviceParams, ncell: int, p_grow: float = 0.6,
+                 K_o2: float = 0.2, K_nut: float = 0.3, o2_min: float = 0.05, v_div: int = 400, seed: int = 1):
+        import torch
+        self.ctx, self.lat, self.prm, self.seed = ctx, lat, prm, seed
+        self.cp = mpm_cpm_params(p_grow, K_o2, K_nut, o2_min, v_div, 0)
+        self.ncell = torch.tensor([ncell], dtype=torch.int32, device="cuda")
+        self.stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+        self.t = 0
+
+    def step(self, stream=None):
+        """One growth + mitosis step (queued on `stream`)."""
+        ls = self.lat.struct()
+        st = self.ctx.lib.mpm_cpm_step(self.ctx.ptr, C.byref(ls), C.byref(self.prm.struct), C.byref(self.cp),
+                                       C.c_uint64(self.seed), self.t, C.c_void_p(self.ncell.data_ptr()),
+                                       C.c_void_p(self.stats.data_ptr()), _stream_ptr(stream))
+        self.ctx._check(st, "mpm_cpm_step")
+        self.t += 1
+
+    def counts(self) -> dict:
+        s = self.stats.cpu().tolist()
+        return {"ncell": int(self.ncell.item()), "grown": s[0], "divisions": s[1], "bad_ids": s[2]}
 
 
 class CNN:

@@ -409,3 +409,16 @@ def sphere_training_case(rng, n: int = 32, three_species=None, homogeneous: bool
         params = Params(3, params.dt, params.h, params.D, params.mu, np.zeros(3), params.k_cell, np.zeros_like(q))
     return Workload("sphere_train", Lattice(cell_id, np.ones(x.shape, np.uint8), fields), params, margin=n,
                     steps=10, rtol=1e-10, restart=30)
+
+
+def with_capacity(params: Params, capacity: int) -> Params:
+    """The same parameters with rate tables of `capacity` entries per species
+    (new entries zero): room for the daughters of the growth driver."""
+    S, n = params.k_cell.shape
+    if capacity < n:
+        raise ValueError("capacity below the current table size")
+    k = np.zeros((S, capacity))
+    q = np.zeros((S, capacity))
+    k[:, :n] = params.k_cell
+    q[:, :n] = params.q_cell
+    return dataclasses.replace(params, k_cell=k, q_cell=q)

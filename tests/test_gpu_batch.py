@@ -136,3 +136,44 @@ def test_batch_step_flags_only_the_system_with_a_bad_cell_id(M):
     st, reps = bs.step(M.make_opts(rtol=1e-10, restart=8, maxit=500), allow=(M.ERR_NOCONV, M.ERR_ARG))
     assert st == M.ERR_ARG
     assert [set(r["status"]) for r in reps] == [{M.OK}, {M.ERR_ARG}, {M.OK}]
+
+
+def test_team_model_replanning_keeps_results_within_the_residual_bound(M, tmp_path):
+    """NEXT-3: the team planner's measured model (mpm_tune_teams) re-plans the
+    64-patch batch; every plan's solution meets the tolerance, and two plans'
+    solutions differ by no more than the sum of their residual bounds
+    (||x - x*|| <= ||r|| since A's eigenvalues are >= 1).  The kept round's f
+    is the smallest measured, a cache hit restores the same model, and the
+    captured batch step plans with it."""
+    ps = W.patches()
+    ctx = M.Context()
+    opts = M.make_opts(rtol=1e-9, restart=8, maxit=800, precision=1, inner_rtol=1e-6)
+    lats = [M.DeviceLattice(p.lattice) for p in ps]
+    subs = []
+    for p, lat in zip(ps, lats):
+        sub = ctx.subgrid_create()
+        sub.mpm_box_extract(lat, 3, p.margin)
+        sub.mpm_assemble_coeffs(M.DeviceParams(p.params))
+        subs.append(sub)
+    st, reps0 = M.mpm_solve_batch(ctx, subs, opts)
+    assert st == M.OK
+    x0 = [[sub.mpm_subgrid_export(M.EXPORT_X, s).cpu().numpy() for s in range(3)] for sub in subs]
+    cache = str(tmp_path / "tune.txt")
+    tt = ctx.mpm_tune_teams(subs, opts, 6, cache)
+    assert len(tt["f"]) >= 3 and min(tt["fixed"]) >= 0.0
+    st, reps1 = M.mpm_solve_batch(ctx, subs, opts)
+    assert st == M.OK
+    f_new = ctx.imbalance()
+    for i, sub in enumerate(subs):
+        for s in range(3):
+            r0, r1 = reps0[i]["res"][s], reps1[i]["res"][s]
+            assert r1 <= 1e-9 * reps1[i]["bnorm"][s]
+            x1 = sub.mpm_subgrid_export(M.EXPORT_X, s).cpu().numpy()
+            assert np.linalg.norm(x1 - x0[i][s]) <= r0 + r1 + 1e-14
+    assert min(tt["f"]) <= tt["f"][0]
+    # the cache restores the model without timing
+    ctx2 = M.Context()
+    tt2 = ctx2.mpm_tune_teams(subs, opts, 6, cache)
+    assert tt2["fixed"] == tt["fixed"] and len(tt2["f"]) == 1
+    print("team tuning f per round", tt["f"], "F1, F per round", tt["fixed_per_round"], "f of the next solve",
+          f_new)
