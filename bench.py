@@ -156,24 +156,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_record(kernel_key):
-    """Per-launch DRAM bytes of the whole-step kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged (hash recorded
-    with it)."""
-    p = os.path.join(ROOT, "profiles", "k_step_traffic.json")
-    try:
-        d = json.load(open(p))
-    except Exception:
-        return None
-    h = hashlib.sha256()
-    for f in ("solver_kernels.cuh", "solver_inst_f32a.cu", "mpm_internal.cuh", "step_kernels.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2505_03067_gb300", "csrc", f), "rb").read())
-    rec = d.get(kernel_key)
-    if not rec or rec.get("source_sha256") != h.hexdigest():
-        return None
-    return rec
-
-
 def replica_value(units: float, ms_local: float, world: int, device=None):
     """Whole-job throughput of N independent replicas: every rank processed
     `units` in `ms_local` ms; the job time is the maximum over ranks (one
@@ -354,6 +336,20 @@ def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=N
     phases = {k: round(v, 1) for k, v in ctx.phase_times_us().items()}
     phases["iters"] = prep["iters"]
     ctx.debug_set(mpm.DEBUG_PHASE_TIMES, 0)
+    # the solver phase alone on the last state (CTA 0's team time "work"; the
+    # three species' teams run side by side): its FP64 instructions per the
+    # pass model over the in-mask unknowns (algorithmic) and over every stored
+    # element (what the passes execute), and its algorithmic bytes, against
+    # the whole GPU's FP64 issue rate at 2070 MHz and the measured HBM peak
+    sec = phases["work"] * 1e-6
+    fp32 = bool(opts.precision)
+    if sec > 0:
+        pk = fp64_peak_instr(2070.0)
+        phases["solver_fp64_frac_algorithmic"] = solver_fp64_ops(prep, prep["mask_voxels"], fp32) / sec / pk
+        phases["solver_fp64_frac_executed"] = solver_fp64_ops(prep, prep["stored_voxels"], fp32) / sec / pk
+        phases["solver_hbm_frac"] = (solver_bytes(prep, prep["mask_voxels"], prep["stored_voxels"], 4 if fp32 else 8)
+                                     / sec / 1e9 / _peaks()[0])
+        phases["stored_mask_box"] = [prep["stored_voxels"], prep["mask_voxels"], prep["box_voxels"]]
     out = {"value": units / (ms / 1e3), "ms_per_step": ms / K, "steps_checked": len(reps),
            "phase_us_last_state": phases,
            "arnoldi_steps_per_species_step": float(np.mean(its)), "kernel_ms": ms, "kernel_bytes": kbytes,
@@ -487,6 +483,50 @@ def cnn_guess_time(mpm, ctx, cnn, solver, stream, flush, reps=3):
         if i:
             ts.append(a.elapsed_time(b))
     return float(np.median(ts))
+
+
+def cnn_layer_roofline(mpm, ctx, cnn, solver, stream, flush, active, reps=5):
+    """Roofline of the headline's dominant kernel, the hidden-layer convolution
+    k_conv_tc<24, 32, 0> (four of the guess's six launches): CUDA events around
+    each convolution launch of the guess on the last state (the library records
+    them on the guess's stream, MPM_DEBUG_CNN_LAYER_TIMES), median over `reps`
+    guesses after L2 flushes; algorithmic flops per launch = active voxels x 27 x
+    24 x 24 x 2.  DRAM traffic per launch: the committed ncu record of that
+    kernel (a capture on the crop's largest state) scaled by the active voxels,
+    valid while the kernel sources are unchanged."""
+    import torch
+    ctx.debug_set(mpm.DEBUG_CNN_LAYER_TIMES, 1)
+    per = []
+    for i in range(reps):
+        flush.fill_(i & 255)
+        cnn.guess(solver.sub, solver.lat, solver.prm)
+        per.append(cnn.layer_times())
+    ctx.debug_set(mpm.DEBUG_CNN_LAYER_TIMES, 0)
+    med = [float(np.median([p[l] for p in per])) for l in range(6)]
+    hid = float(np.mean(med[1:5]))
+    flops = active * 27 * 24 * 24 * 2
+    achieved = flops / (hid / 1e3) / 1e12
+    rec = _traffic_record_cnn()
+    traffic = rec["dram_bytes_per_launch"] * active / rec["active_voxels"] if rec else None
+    return {"bound": "tensor", "kernel": "k_conv_tc<24, 32, 0> (hidden-layer 3x3x3 convolution, tcgen05)",
+            "achieved": achieved, "peak": 1980.0, "unit": "TFLOP/s", "frac": achieved / 1980.0,
+            "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": hid, "layer_ms": med,
+            "peak_source": "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops)",
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on the "
+                               "growth crop's largest state, scaled by active voxels (profiles/conv_tc_traffic.json)"
+                               if rec else "no record for the current kernel sources")}
+
+
+def _traffic_record_cnn():
+    p = os.path.join(ROOT, "profiles", "conv_tc_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in ("cnn_tc.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_2505_03067_gb300", "csrc", f), "rb").read())
+    return d if d.get("source_sha256") == h.hexdigest() else None
 
 
 def bench_learned(mpm, ctx, samples=20000):
@@ -651,7 +691,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--restart", type=int, default=8)
     ap.add_argument("--c5-epochs", type=int, default=3, help="passes over the training trajectory (200 steps each)")
@@ -659,10 +699,21 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the 256^3, 32^3, 64-patch sub-lines")
     ap.add_argument("--train-samples", type=int, default=20000)
     ap.add_argument("--cnn-only", action="store_true", help="time the network alone on a small case (profiling)")
+    ap.add_argument("--shell256-only", action="store_true",
+                    help="the 256^3 shell sub-line alone (FP64, mixed, cadence paths; a few GB: profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.cnn_only:
         return cnn_only(args)
+    if args.shell256_only:
+        import torch
+        from paper_2505_03067_gb300 import mpm
+        from paper_2505_03067_gb300 import workloads as W
+        ctx = mpm.Context()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        print(json.dumps({"mode": "shell256_only", **bench_shell256(mpm, W, ctx, torch.cuda.current_stream(), flush,
+                                                                     args.steps, args.warmup)}), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -720,6 +771,8 @@ def main():
         if headline:
             clocks, keep = clk, (kp, opts)
             res["cnn_ms_last_step"] = cnn_guess_time(mpm, ctx, net, kp[0], stream, flush)
+            res["roofline_conv"] = cnn_layer_roofline(mpm, ctx, net, kp[0], stream, flush,
+                                                      res["mask_voxels_first_last"][1])
         else:
             del kp
         results[name] = res
@@ -751,14 +804,15 @@ def main():
                                              "SM clock under load (the FP64 pipe: an ALU bound)"}
 
     head = results["learned_mixed"]
-    # the dominant kernel of the headline step: the network's convolutions
-    # against the two step launches (their time = step time - network time)
+    # the dominant kernel of the headline step: the hidden-layer convolution
+    # (four of the network's six launches) when the network takes at least
+    # half the step, else the step launches' HBM roofline
     t_step_last = head["kernel_ms"] / K
     if head["cnn_ms_last_step"] >= 0.5 * t_step_last:
-        roofline = dict(head["roofline_cnn"])
+        roofline = dict(head["roofline_conv"])
     else:
         roofline = dict(head["roofline_hbm"])
-    roofline["traffic"] = None
+        roofline["traffic"] = None
 
     # ---- end to end through the public API with host buffers (mpm_step_host)
     (solver, lat, prm, init), opts = keep
@@ -801,6 +855,7 @@ def main():
             "phase_us_last_state")
     paths = {k: {kk: v[kk] for kk in keys} for k, v in results.items()}
     paths["learned_mixed"]["roofline_cnn"] = head["roofline_cnn"]
+    paths["learned_mixed"]["roofline_conv"] = head["roofline_conv"]
     paths["learned_mixed"]["cnn_ms_last_step"] = head["cnn_ms_last_step"]
     # row a13 on the same steps: the network as the right preconditioner of
     # FP32 flexible GMRES inside FP64 refinement, from its guess

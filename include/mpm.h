@@ -442,6 +442,10 @@ mpm_status mpm_cnn_train_step(mpm_ctx *ctx, mpm_cnn *cnn, int32_t nimg, float lr
  * solve with x0_given = 1).  A non-finite prediction leaves c^n.  Queued on `stream`. */
 mpm_status mpm_cnn_guess(mpm_ctx *ctx, mpm_cnn *cnn, mpm_subgrid *sub, const mpm_lattice *lat,
                          const mpm_params *prm, void *stream);
+/* Test hook: device milliseconds of the six convolution launches of the network's last
+ * application recorded with MPM_DEBUG_CNN_LAYER_TIMES on (waits for them).  MPM_ERR_ARG when
+ * none was recorded. */
+mpm_status mpm_cnn_layer_times(mpm_ctx *ctx, mpm_cnn *cnn, float ms[6]);
 
 /*
  * Solve every species of an assembled subgrid by right-preconditioned
@@ -548,11 +552,16 @@ mpm_status mpm_scatter(mpm_ctx *ctx, const mpm_subgrid *sub, const mpm_lattice *
  *  MPM_DEBUG_SOLVER_VARIANT  solver kernel variant 0..6 (elements in flight per
  *                        thread, CTAs per SM, threads per CTA; 0 = default;
  *                        a bucket without the variant uses its default), for
- *                        tuning. */
+ *                        tuning.
+ *  MPM_DEBUG_CNN_LAYER_TIMES 1: every later network application outside a
+ *                        graph capture records CUDA events around each of its
+ *                        six convolution launches (read with
+ *                        mpm_cnn_layer_times). */
 #define MPM_DEBUG_TIMEOUT_NS 1
 #define MPM_DEBUG_SKIP_BLOCK 2
 #define MPM_DEBUG_PHASE_TIMES 3
 #define MPM_DEBUG_SOLVER_VARIANT 4
+#define MPM_DEBUG_CNN_LAYER_TIMES 5
 mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value);
 
 /* Test hook: the FP32 Krylov path's bit-level conversions applied to n

@@ -366,6 +366,9 @@ mpm_status mpm_debug_set(mpm_ctx *ctx, int32_t key, int64_t value)
         if (value < 0 || value > 6) return mpm_fail(ctx, MPM_ERR_ARG, "debug: solver variant out of [0, 6]");
         ctx->solver_variant = (int32_t)value;
         return MPM_OK;
+    case MPM_DEBUG_CNN_LAYER_TIMES:
+        ctx->cnn_layer_prof = value != 0;
+        return MPM_OK;
     default:
         return mpm_fail(ctx, MPM_ERR_ARG, "debug: unknown key");
     }

@@ -545,6 +545,8 @@ using namespace mpm;
 
 struct mpm_cnn {
     uint64_t serial = 0;             // distinct for every network of the process (graph caches)
+    cudaEvent_t lev[kLayers + 1] = {};   // around the convolutions (MPM_DEBUG_CNN_LAYER_TIMES)
+    bool lev_recorded = false;
     int32_t L[3] = {0, 0, 0};
     int32_t maxB = 0;
     long long V = 0;                 // voxels per image
@@ -727,6 +729,15 @@ mpm_status plan_images(mpm_ctx *ctx, mpm_cnn *c, int nimg, cudaStream_t st)
 mpm_status forward_layers(mpm_ctx *ctx, mpm_cnn *c, const uint8_t *mask, bool train, const tc::ConvArgs &out_args,
                           cudaStream_t st)
 {
+    bool timed = false;
+    if (ctx->cnn_layer_prof) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        timed = cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+        for (int i = 0; i <= kLayers && timed; ++i)
+            if (!c->lev[i]) timed = cudaEventCreate(&c->lev[i]) == cudaSuccess;
+        cudaGetLastError();
+        if (timed) MPM_CU(cudaEventRecord(c->lev[0], st));
+    }
     for (int l = 0; l < kLayers; ++l) {
         tc::ConvArgs A;
         memset(&A, 0, sizeof(A));
@@ -750,7 +761,9 @@ mpm_status forward_layers(mpm_ctx *ctx, mpm_cnn *c, const uint8_t *mask, bool tr
             r = conv<kHC, 16, tc::EPI_OUT>(ctx, c, O, 1 + l, st);
         }
         if (r != MPM_OK) return r;
+        if (timed) MPM_CU(cudaEventRecord(c->lev[l + 1], st));
     }
+    if (timed) c->lev_recorded = true;
     return MPM_OK;
 }
 
@@ -875,10 +888,23 @@ extern "C" mpm_status mpm_cnn_create(mpm_ctx *ctx, mpm_cnn **out, const int32_t 
     return MPM_OK;
 }
 
+extern "C" mpm_status mpm_cnn_layer_times(mpm_ctx *ctx, mpm_cnn *c, float ms[6])
+{
+    if (!ctx) return MPM_ERR_ARG;
+    ctx->err.clear();
+    if (!c || !ms) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_layer_times: null argument");
+    if (!c->lev_recorded) return mpm_fail(ctx, MPM_ERR_ARG, "cnn_layer_times: no timed application");
+    MPM_CU(cudaEventSynchronize(c->lev[kLayers]));
+    for (int l = 0; l < kLayers; ++l) MPM_CU(cudaEventElapsedTime(&ms[l], c->lev[l], c->lev[l + 1]));
+    return MPM_OK;
+}
+
 extern "C" mpm_status mpm_cnn_destroy(mpm_ctx *ctx, mpm_cnn *c)
 {
     (void)ctx;
     if (!c) return MPM_ERR_ARG;
+    for (int i = 0; i <= kLayers; ++i)
+        if (c->lev[i]) cudaEventDestroy(c->lev[i]);
     for (void *p : c->allocs) cudaFree(p);
     if (c->h_err) cudaFreeHost(c->h_err);
     delete c;

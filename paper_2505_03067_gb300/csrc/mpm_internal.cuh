@@ -415,6 +415,7 @@ struct mpm_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t launches = 0;        // kernels launched by this context
     int32_t phase_prof = 0;      // record the solver's phase times (test/tuning hook)
+    int32_t cnn_layer_prof = 0;  // record CUDA events around the network's convolutions (test hook)
     int32_t solver_variant = 0;  // solver kernel variant (tuning)
     void *batch_graph = nullptr; // captured batched step (solver.cu)
     cudaStream_t cap_stream = nullptr;  // stream used only for graph capture
@@ -431,7 +432,8 @@ struct mpm_ctx {
     // by mpm_tune_teams (tune.cu)
     double team_fixed = 3000.0;         // per-pass fixed cost of an item on a team of several CTAs
     double team_fixed1 = 3000.0;        //   and on a one-CTA team (no grid barrier), element-equivalents
-    int32_t team_use_iters = 0;         // weight items by their Arnoldi steps in item_iters
+    int32_t team_use_iters = 0;         // 1: weight items by item_iters; 2: plan from the measured item times
+    double team_beta = 0.0;             // fitted device time per stored element and Arnoldi step (ns)
     uint64_t team_gen = 0;              // bumped when the model changes (captured plans are redone)
     std::vector<double> item_iters;     // per work item of the last solve: Arnoldi steps
     std::vector<double> item_ne;        //   stored elements

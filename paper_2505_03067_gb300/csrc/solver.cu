@@ -333,12 +333,26 @@ static mpm_status plan_solve(mpm_ctx *ctx, mpm_subgrid *const *subs, int nsys, c
         // the cost model: measured Arnoldi steps per item when the context has
         // them for a batch of this many items, else one pass each
         const bool iters = ctx->team_use_iters && (int)ctx->item_iters.size() == P.nitem;
+        const bool timed = ctx->team_use_iters == 2 && iters && (int)ctx->item_ns.size() == P.nitem &&
+                           ctx->team_beta > 0.0;
         std::vector<ItemCost> ic(P.nitem);
         for (int i = 0; i < P.nitem; ++i) {
             const double it = iters ? std::max(1.0, ctx->item_iters[i]) : 1.0;
-            ic[i].one = it * (ctx->team_fixed1 + work[i]);
-            ic[i].fix = it * ctx->team_fixed;
-            ic[i].work = it * work[i];
+            if (timed) {
+                // the measured time of the item on its c CTAs, split into the
+                // fixed part (fitted per Arnoldi step) and the streaming part
+                // (which c CTAs divided), in ns
+                const double a1 = ctx->team_fixed1 * ctx->team_beta, a = ctx->team_fixed * ctx->team_beta;
+                const double c = std::max(1.0, ctx->item_cta[i]), t = ctx->item_ns[i];
+                const double stream = std::max(0.0, t - it * (c > 1.0 ? a : a1)) * c;
+                ic[i].one = it * a1 + stream;
+                ic[i].fix = it * a;
+                ic[i].work = stream;
+            } else {
+                ic[i].one = it * (ctx->team_fixed1 + work[i]);
+                ic[i].fix = it * ctx->team_fixed;
+                ic[i].work = it * work[i];
+            }
         }
         plan_teams(ic, P.G, P.teams, P.order, P.block_team);
     }

@@ -198,7 +198,7 @@ namespace {
 // the measured items (x = NE / c, y = time per Arnoldi step): F1 =
 // alpha1 / beta, F = alpha / beta.  A regime without items keeps its value.
 bool fit_fixed(const std::vector<double> &x, const std::vector<double> &y, const std::vector<int> &one, double &F1,
-               double &F)
+               double &F, double &beta_out)
 {
     // normal equations of the three unknowns (beta, alpha1, alpha)
     double a[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, r[3] = {0, 0, 0};
@@ -239,6 +239,7 @@ bool fit_fixed(const std::vector<double> &x, const std::vector<double> &y, const
     for (int p = 0; p < nk; ++p) sol[keep[p]] = m[p][nk] / m[p][p];
     const double beta = sol[0];
     if (!(beta > 0.0)) return false;
+    beta_out = beta;
     auto clampF = [](double v) { return std::min(1e7, std::max(0.0, v)); };
     if (a[1][1] > 0.0 && sol[1] >= 0.0) F1 = clampF(sol[1] / beta);
     if (a[2][2] > 0.0 && sol[2] >= 0.0) F = clampF(sol[2] / beta);
@@ -247,54 +248,93 @@ bool fit_fixed(const std::vector<double> &x, const std::vector<double> &y, const
 
 std::string teams_key(const std::string &k) { return k + ";teams"; }
 
-bool teams_lookup(const char *path, const std::string &key, double &F1, double &F, double &f, int &use,
-                  std::vector<double> &iters)
+// The team planner's inputs (the context's model fields).
+struct TeamModel {
+    double F1 = 3000.0, F = 3000.0, beta = 0.0;
+    int use = 0;
+    std::vector<double> iters, ns, cta;
+    static TeamModel of(const mpm_ctx *c)
+    {
+        TeamModel m;
+        m.F1 = c->team_fixed1;
+        m.F = c->team_fixed;
+        m.beta = c->team_beta;
+        m.use = c->team_use_iters;
+        m.iters = c->item_iters;
+        m.ns = c->item_ns;
+        m.cta = c->item_cta;
+        return m;
+    }
+    void apply(mpm_ctx *c) const
+    {
+        c->team_fixed1 = F1;
+        c->team_fixed = F;
+        c->team_beta = beta;
+        c->team_use_iters = use;
+        if (use) {
+            c->item_iters = iters;
+            c->item_ns = ns;
+            c->item_cta = cta;
+        }
+        c->team_gen += 1;
+    }
+};
+
+// One line per tuning: key F1 F beta f use n, then n Arnoldi steps, n times
+// (ns) and n CTA counts of the plan's input, then "|" and the kept plan's
+// per-team times (ns).
+bool teams_lookup(const char *path, const std::string &key, TeamModel &m, double &f)
 {
     if (!path) return false;
     FILE *fp = fopen(path, "r");
     if (!fp) return false;
-    std::vector<char> line(1 << 20);
+    std::vector<char> line(1 << 22);
     bool found = false;
     while (fgets(line.data(), (int)line.size(), fp)) {
         std::string s(line.data());
         if (s.compare(0, key.size(), key) != 0 || s.size() <= key.size() || s[key.size()] != ' ') continue;
-        // key F1 F f use nitem it_0 .. it_{n-1} | team times (ns)
         const char *p = s.c_str() + key.size();
         char *e = nullptr;
-        const double F1_ = strtod(p, &e);
-        const double F_ = strtod(e, &e);
+        TeamModel t;
+        t.F1 = strtod(p, &e);
+        t.F = strtod(e, &e);
+        t.beta = strtod(e, &e);
         const double f_ = strtod(e, &e);
-        const long u = strtol(e, &e, 10);
+        t.use = (int)strtol(e, &e, 10);
         const long n = strtol(e, &e, 10);
         if (n < 0 || n > (1 << 20)) continue;
-        std::vector<double> it(n);
         bool ok = true;
-        for (long i = 0; i < n && ok; ++i) {
-            char *e2 = nullptr;
-            it[i] = strtod(e, &e2);
-            ok = e2 != e;
-            e = e2;
+        for (std::vector<double> *v : {&t.iters, &t.ns, &t.cta}) {
+            v->resize(n);
+            for (long i = 0; i < n && ok; ++i) {
+                char *e2 = nullptr;
+                (*v)[i] = strtod(e, &e2);
+                ok = e2 != e;
+                e = e2;
+            }
         }
         if (!ok) continue;
-        F1 = F1_;
-        F = F_;
+        m = t;
         f = f_;
-        use = u != 0 ? 1 : 0;
-        iters = it;
         found = true;
     }
     fclose(fp);
     return found;
 }
 
-void teams_store(const char *path, const std::string &key, double F1, double F, double f, int use,
-                 const std::vector<double> &iters, const std::vector<double> &team_ns)
+void teams_store(const char *path, const std::string &key, const TeamModel &m, double f,
+                 const std::vector<double> &team_ns)
 {
     if (!path) return;
     FILE *fp = fopen(path, "a");
     if (!fp) return;
-    fprintf(fp, "%s %.17g %.17g %.6g %d %zu", key.c_str(), F1, F, f, use, iters.size());
-    for (double v : iters) fprintf(fp, " %.0f", v);
+    const size_t n = m.iters.size();
+    const bool full = m.ns.size() == n && m.cta.size() == n;
+    fprintf(fp, "%s %.17g %.17g %.17g %.6g %d %zu", key.c_str(), m.F1, m.F, m.beta, f, full ? m.use : 0,
+            full ? n : (size_t)0);
+    if (full)
+        for (const std::vector<double> *v : {&m.iters, &m.ns, &m.cta})
+            for (double x : *v) fprintf(fp, " %.17g", x);
     fprintf(fp, " |");
     for (double v : team_ns) fprintf(fp, " %.0f", v);
     fprintf(fp, "\n");
@@ -318,23 +358,18 @@ extern "C" mpm_status mpm_tune_teams(mpm_ctx *ctx, mpm_subgrid *const *subs, int
     if (history)
         for (int r = 0; r <= rounds; ++r) history[3 * r] = history[3 * r + 1] = history[3 * r + 2] = -1.0;
     {
-        double F1 = 0.0, F = 0.0, f = 0.0;
-        int use = 0;
-        std::vector<double> it;
-        if (teams_lookup(cache_path, key, F1, F, f, use, it)) {
-            ctx->team_fixed1 = F1;
-            ctx->team_fixed = F;
-            ctx->team_use_iters = use;
-            if (use) ctx->item_iters = it;
-            ctx->team_gen += 1;
+        TeamModel m;
+        double f = 0.0;
+        if (teams_lookup(cache_path, key, m, f)) {
+            m.apply(ctx);
             if (history) {
                 history[0] = f;
-                history[1] = F1;
-                history[2] = F;
+                history[1] = m.F1;
+                history[2] = m.F;
             }
             if (out_fixed) {
-                out_fixed[0] = F1;
-                out_fixed[1] = F;
+                out_fixed[0] = m.F1;
+                out_fixed[1] = m.F;
             }
             return MPM_OK;
         }
@@ -344,31 +379,32 @@ extern "C" mpm_status mpm_tune_teams(mpm_ctx *ctx, mpm_subgrid *const *subs, int
     std::vector<mpm_report> reps(nsys);
     std::vector<double> xs, ys;
     std::vector<int> ones;
-    double best_f = 1e300, best_F1 = ctx->team_fixed1, best_F = ctx->team_fixed;
-    int best_use = 0;
-    std::vector<double> best_iters, best_team;
+    double best_f = 1e300;
+    TeamModel best;
+    std::vector<double> best_team;
     int since = 0;
     for (int round = 0; round <= rounds; ++round) {
         if (round > 0) {
-            double F1 = ctx->team_fixed1, F = ctx->team_fixed;
-            if (fit_fixed(xs, ys, ones, F1, F)) {
+            double F1 = ctx->team_fixed1, F = ctx->team_fixed, beta = 0.0;
+            if (fit_fixed(xs, ys, ones, F1, F, beta)) {
                 ctx->team_fixed1 = F1;
                 ctx->team_fixed = F;
+                ctx->team_beta = beta;
             }
-            ctx->team_use_iters = 1;   // item_iters: the solve just measured
+            // odd rounds weight the items by their Arnoldi steps, even rounds
+            // plan from their measured times (both from the solve just run)
+            ctx->team_use_iters = (round & 1) ? 1 : 2;
         } else {
             ctx->team_use_iters = 0;
         }
-        const double F1_used = ctx->team_fixed1, F_used = ctx->team_fixed;
-        const int use_used = ctx->team_use_iters;
-        const std::vector<double> iters_used = ctx->item_iters;
+        const TeamModel used = TeamModel::of(ctx);
         const mpm_status r = mpm_solve_impl(ctx, subs, nullptr, nsys, &o, reps.data(), st);
         if (r != MPM_OK && r != MPM_ERR_NOCONV) return r;
         const double f = ctx->last_imbalance;
         if (history) {
             history[3 * round] = f;
-            history[3 * round + 1] = F1_used;
-            history[3 * round + 2] = F_used;
+            history[3 * round + 1] = used.F1;
+            history[3 * round + 2] = used.F;
         }
         for (size_t i = 0; i < ctx->item_ns.size(); ++i)
             if (ctx->item_iters[i] > 0.0) {
@@ -378,26 +414,19 @@ extern "C" mpm_status mpm_tune_teams(mpm_ctx *ctx, mpm_subgrid *const *subs, int
             }
         if (f < best_f) {
             best_f = f;
-            best_F1 = F1_used;
-            best_F = F_used;
-            best_use = use_used;
-            best_iters = use_used ? iters_used : std::vector<double>();
+            best = used;
             best_team = ctx->team_ns;
             since = 0;
-        } else if (++since >= 2) {
+        } else if (++since >= 2 && round >= 2) {
             break;
         }
     }
     ctx->err.clear();
-    ctx->team_fixed1 = best_F1;
-    ctx->team_fixed = best_F;
-    ctx->team_use_iters = best_use;
-    if (best_use) ctx->item_iters = best_iters;
-    ctx->team_gen += 1;
-    teams_store(cache_path, key, best_F1, best_F, best_f, best_use, best_iters, best_team);
+    best.apply(ctx);
+    teams_store(cache_path, key, best, best_f, best_team);
     if (out_fixed) {
-        out_fixed[0] = best_F1;
-        out_fixed[1] = best_F;
+        out_fixed[0] = best.F1;
+        out_fixed[1] = best.F;
     }
     // leave the iterates at c^n for the caller's own solve
     for (int i = 0; i < nsys; ++i) {

@@ -18,7 +18,7 @@ NOALLOC_MAX_SLABS = 4096
 OK, ERR_ARG, ERR_EMPTY, ERR_NOCONV, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(8)
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_EMPTY", "ERR_NOCONV", "ERR_BREAKDOWN", "ERR_TIMEOUT", "ERR_CUDA", "ERR_NOMEM"]
 EXPORT_X, EXPORT_RHS, EXPORT_DIAG, EXPORT_FLAGS, EXPORT_CELL = range(5)
-DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK, DEBUG_PHASE_TIMES, DEBUG_SOLVER_VARIANT = 1, 2, 3, 4
+DEBUG_TIMEOUT_NS, DEBUG_SKIP_BLOCK, DEBUG_PHASE_TIMES, DEBUG_SOLVER_VARIANT, DEBUG_CNN_LAYER_TIMES = 1, 2, 3, 4, 5
 COUNTER_STEP_FULL_EXTRACTIONS = 19
 CNN_INPUT, CNN_TARGET = 0, 1
 
@@ -31,7 +31,7 @@ SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_subgrid_create", 
            "mpm_subgrid_export", "mpm_subgrid_import", "mpm_apply_operator", "mpm_scatter", "mpm_debug_set",
            "mpm_counter_get", "mpm_box_bounds_noalloc", "mpm_subgrid_refresh", "mpm_batch_step",
            "mpm_tune_tile", "mpm_tune_solver", "mpm_tune_teams", "mpm_cnn_create", "mpm_cnn_destroy", "mpm_cnn_set_params",
-           "mpm_cnn_get_params", "mpm_cnn_load_image", "mpm_cnn_export_features", "mpm_cnn_export_preact", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess",
+           "mpm_cnn_get_params", "mpm_cnn_load_image", "mpm_cnn_export_features", "mpm_cnn_export_preact", "mpm_cnn_forward", "mpm_cnn_train_step", "mpm_cnn_guess", "mpm_cnn_layer_times",
            "mpm_step", "mpm_step_enqueue", "mpm_step_wait", "mpm_solve_fgmres_cnn", "mpm_cnn_precond",
            "mpm_step_host", "mpm_debug_convert", "mpm_step_set_network", "mpm_cpm_step"]
 
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mpm_cnn_export_preact": [P, P, C.c_int32, C.c_int32, P, P],
         "mpm_cnn_train_step": [P, P, C.c_int32, C.c_float, C.c_int32, C.POINTER(C.c_double), P],
         "mpm_cnn_guess": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), P],
+        "mpm_cnn_layer_times": [P, P, P],
         "mpm_solve_fgmres_cnn": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.POINTER(mpm_lattice),
                                  C.POINTER(mpm_opts), C.POINTER(mpm_report), P],
         "mpm_cnn_precond": [P, P, P, C.POINTER(mpm_lattice), C.POINTER(mpm_params), C.c_int32, P, P, P],
@@ -760,6 +761,13 @@ class CNN:
         ls = lat.struct()
         self.ctx._check(self.ctx.lib.mpm_cnn_guess(self.ctx.ptr, self.h, sub.h, C.byref(ls), C.byref(prm.struct),
                                                    _stream_ptr(stream)), "mpm_cnn_guess")
+
+    def layer_times(self):
+        """Device ms of the six convolutions of the last application timed with
+        DEBUG_CNN_LAYER_TIMES on (mpm_cnn_layer_times)."""
+        ms = (C.c_float * 6)()
+        self.ctx._check(self.ctx.lib.mpm_cnn_layer_times(self.ctx.ptr, self.h, ms), "mpm_cnn_layer_times")
+        return list(ms)
 
     def precond(self, sub: Subgrid, lat: DeviceLattice, prm: DeviceParams, s: int, v, stream=None):
         """The FGMRES preconditioner on a box-dense FP64 tensor v (mpm_cnn_precond)."""
