@@ -701,10 +701,25 @@ def main():
     ap.add_argument("--cnn-only", action="store_true", help="time the network alone on a small case (profiling)")
     ap.add_argument("--shell256-only", action="store_true",
                     help="the 256^3 shell sub-line alone (FP64, mixed, cadence paths; a few GB: profiling)")
+    ap.add_argument("--c5-only", choices=["fp64", "mixed"], default=None,
+                    help="one path of the growing tumour alone, no network (profiling the step kernel)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.cnn_only:
         return cnn_only(args)
+    if args.c5_only:
+        import torch
+        from paper_2505_03067_gb300 import mpm
+        from paper_2505_03067_gb300 import workloads as W
+        ctx = mpm.Context()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        extra = dict(precision=0) if args.c5_only == "fp64" else dict(precision=1, inner_rtol=1e-6)
+        g = Growth(W)
+        opts = mpm.make_opts(rtol=g.wl.rtol, restart=args.restart, maxit=1000, **extra)
+        res, _, _ = run_c5_path(mpm, g, ctx, torch.cuda.current_stream(), flush, opts, args.steps, args.warmup)
+        keys = ("value", "ms_per_step", "steps_checked", "arnoldi_steps_per_species_step", "phase_us_last_state")
+        print(json.dumps({"mode": "c5_only", "path": args.c5_only, **{k: res[k] for k in keys}}), flush=True)
+        return 0
     if args.shell256_only:
         import torch
         from paper_2505_03067_gb300 import mpm

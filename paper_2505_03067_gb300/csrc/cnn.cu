@@ -626,6 +626,7 @@ mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t
     A.uact = c->uact;
     A.ubits = c->ubits;
     A.work = c->counters + slot;
+    A.done = c->counters + 16 + slot;
     A.err = c->d_err;
     A.timeout_ns = ctx->timeout_ns;
     tc::k_conv_tc<CI, NO, EPI><<<ctx->num_sms, tc::kConvThreads, smem, st>>>(A);

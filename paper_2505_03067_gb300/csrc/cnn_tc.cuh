@@ -268,7 +268,8 @@ struct ConvArgs {
     const int32_t *nunits;
     const uint8_t *uact;            // [units][kActStride]
     const uint32_t *ubits;          // [units]
-    int32_t *work;                  // dynamic scheduling counter (reset by the plan)
+    int32_t *work;                  // dynamic scheduling: the next unit (reset by the launch's last CTA)
+    int32_t *done;                  //   CTAs finished (reset with it)
     const unsigned char *wimg;      // weight image (WImg layout)
     const float *bias;              // [NO] (null: none)
     // EPI_GELU: a_out = bf16(gelu(z)) at active voxels, z_out (nullable) = z
@@ -303,10 +304,12 @@ __device__ __forceinline__ bool in_box(const CnnDom &D, int b, int x, int y, int
 
 // The 16-byte copies of one halo depth handled by one loader thread, fixed for
 // a launch: the k-th covers item tid + k NL of the depth (halo row yh, copy c,
-// x row, channel chunk kc); `rel` is its source offset in elements from the
-// depth's halo origin; `da` packs its shared offset in the slot (low 16 bits)
-// and its index in a depth of the unit's activity bytes (bits 16..23; 255: no
-// item).
+// channel chunk kc, x row; x fastest, so the eight lanes that fill one core
+// matrix write its 128 contiguous bytes -- one shared-memory wavefront, no
+// bank conflict -- while a warp still reads the same sectors of the source
+// rows); `rel` is its source offset in elements from the depth's halo origin;
+// `da` packs its shared offset in the slot (low 16 bits) and its index in a
+// depth of the unit's activity bytes (bits 16..23; 255: no item).
 template <int CI, int NL>
 struct HaloItems {
     static constexpr int N = kHaloY * 3 * kSlabX * (CI / 8);
@@ -320,10 +323,10 @@ struct HaloItems {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int i = tid + k * NL;
-            const int kc = i % H::KC;
-            int r = i / H::KC;
-            const int x = r % kSlabX;
-            r /= kSlabX;
+            const int x = i % kSlabX;
+            int r = i / kSlabX;
+            const int kc = r % H::KC;
+            r /= H::KC;
             const int c = r % 3, yh = r / 3;
             const int xh = x + c;
             rel[k] = (yh * L0 + xh) * CI + kc * 8;
@@ -455,7 +458,7 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
     constexpr int NLD = 32 * kLoadWarps;          // loader threads: NE .. NE+NLD-1
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t s_tmem;
-    __shared__ int32_t s_abort, s_lstop;
+    __shared__ int32_t s_abort, s_lstop, s_ui;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);
     uint64_t *full = bar, *empty = bar + kFwdSlots, *accf = bar + 2 * kFwdSlots, *acce = accf + kAcc;
     uint64_t *unitf = acce + kAcc, *unite = unitf + 2;
@@ -507,15 +510,29 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
         items.init(lt, D.L[0]);
         uint32_t dseq = 0;                        // depths issued
         for (int n = 0;; ++n) {
-            const int ui = blockIdx.x + n * gridDim.x;
-            if (ui >= nunits) break;
+            // units are taken from a counter shared by the CTAs (units hold 1..8
+            // active slabs, so a fixed assignment leaves CTAs unequally loaded);
+            // a unit index past the list is published as the stop record
             const int ub = n & 1;
             if (lt == 0) {
                 const bool w = n < 2 || mbar_wait_or_abort(&unite[ub], ((n >> 1) - 1) & 1, T, A.err, abort);
                 if (!w || *abort) s_lstop = 1;
+                else s_ui = atomicAdd(A.work, 1);
             }
             named_sync(1, NLD);
             if (s_lstop) break;
+            const int ui = s_ui;
+            if (ui >= nunits) {
+                if (lt == 0) {
+                    Unit stop;
+                    stop.b = stop.ox = stop.oy = stop.z0 = 0;
+                    stop.nz = -1;
+                    stop.pad0 = stop.pad1 = stop.pad2 = 0;
+                    urec[ub] = stop;
+                    mbar_arrive(&unitf[ub]);
+                }
+                break;
+            }
             const Unit u = A.units[ui];
             uint8_t *act = sm + S::ACT_OFF + ub * S::ACT_BYTES;
             copy_unit_act<NLD>(A.uact, ui, act, lt);
@@ -546,12 +563,11 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
             uint32_t dbase = 0, m = 0;
             bool ok = true;
             for (int n = 0; ok; ++n) {
-                const int ui = blockIdx.x + n * gridDim.x;
-                if (ui >= nunits) break;
                 const int ub = n & 1;
                 ok = mbar_wait_or_abort(&unitf[ub], (n >> 1) & 1, T, A.err, abort);
                 if (!ok) break;
                 const int nz = urec[ub].nz;
+                if (nz < 0) break;                // the stop record
                 const uint32_t bits = ubits[ub];
                 for (int k = 0; k < nz && ok; ++k) {
                     // slab k reads depths k, k+1, k+2; k+2 is the newest
@@ -610,13 +626,12 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
         uint32_t m = 0;
         bool ok = true;
         for (int n = 0; ok; ++n) {
-            const int ui = blockIdx.x + n * gridDim.x;
-            if (ui >= nunits) break;
             const int ub = n & 1;
             if (lane == 0) ok = mbar_wait_or_abort(&unitf[ub], (n >> 1) & 1, T, A.err, abort);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             const Unit u = urec[ub];
+            if (u.nz < 0) break;                  // the stop record
             const uint32_t bits = ubits[ub];
             const uint8_t *act = sm + S::ACT_OFF + ub * S::ACT_BYTES;
             for (int k = 0; k < u.nz && ok; ++k) {
@@ -720,6 +735,15 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
     __syncthreads();
     tc_after_sync();
     if (warp == 0) tmem_dealloc(tmem, 128);
+    // the launch's last CTA resets the unit counter for the next launch
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
+            *A.work = 0;
+            *A.done = 0;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------- weight gradient
