@@ -293,14 +293,24 @@ class Growth:
         lat.cell_id.view(-1)[self.cand] = ids[self.labels]
 
 
-def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=None):
+def c5_tile(mpm, g, ctx):
+    """The tile of the growing tumour's steps: the tuner's pick (the tile
+    storing the fewest voxels, mpm_tune_tile) on the largest, last state."""
+    lat = mpm.DeviceLattice(g.wl.lattice)
+    g.set_tumour(lat, C5_STEPS - 1)
+    tile, stored = ctx.mpm_tune_tile(lat, g.wl.margin)
+    del lat
+    return tile, stored
+
+
+def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=None, tile=None):
     """K sampled steps of the growing tumour on one path, every report checked."""
     import torch
     wl = g.wl
     lat = mpm.DeviceLattice(wl.lattice)
     init = lat.fields.clone()
     prm = mpm.DeviceParams(wl.params)
-    solver = mpm.StepSolver(ctx, lat, prm, wl.margin)
+    solver = mpm.StepSolver(ctx, lat, prm, wl.margin, tile=tile)
     if cnn is not None:
         solver.set_network(cnn)
     g.set_tumour(lat, 0)
@@ -322,7 +332,7 @@ def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=N
         assert all(r <= wl.rtol * b for r, b in zip(rep["res"], rep["bnorm"])), (t, rep)
         ms += dt
         units += rep["mask_voxels"] * wl.params.nspecies
-        kbytes += step_bytes(rep, L, wl.params.nspecies, bT)
+        kbytes += step_bytes(rep, L, wl.params.nspecies, bT, int(np.prod(tile)) if tile else 64)
         kops += solver_fp64_ops(rep, rep["mask_voxels"], bool(opts.precision))
         reps.append(rep)
         its.append(sum(rep["iters"]) / len(rep["iters"]))
@@ -360,7 +370,7 @@ def run_c5_path(mpm, g, ctx, stream, flush, opts, K, warmup, cnn=None, sampler=N
     return out, clocks, (solver, lat, prm, init)
 
 
-def run_c5_fgmres(mpm, g, ctx, stream, flush, okw, K, warmup, cnn):
+def run_c5_fgmres(mpm, g, ctx, stream, flush, okw, K, warmup, cnn, tile=None):
     """K sampled steps of the growing tumour by flexible GMRES with the network
     as the right preconditioner from its guess (mpm_solve_fgmres_cnn, one
     graph per solve): extraction, assembly, guess, solve and scatter per step,
@@ -376,7 +386,7 @@ def run_c5_fgmres(mpm, g, ctx, stream, flush, okw, K, warmup, cnn):
     opts = mpm.make_opts(x0_given=1, **okw)
 
     def one():
-        sub.mpm_box_extract(lat, S, wl.margin)
+        sub.mpm_box_extract(lat, S, wl.margin, tile=tile)
         sub.mpm_assemble_coeffs(prm)
         cnn.guess(sub, lat, prm)
         return cnn.solve_fgmres(sub, lat, prm, opts, scatter_to=lat)
@@ -703,6 +713,8 @@ def main():
                     help="the 256^3 shell sub-line alone (FP64, mixed, cadence paths; a few GB: profiling)")
     ap.add_argument("--c5-only", choices=["fp64", "mixed"], default=None,
                     help="one path of the growing tumour alone, no network (profiling the step kernel)")
+    ap.add_argument("--c5-tile", choices=["tuned", "default"], default="tuned",
+                    help="tile of the growing tumour's steps: the tuner's pick on the last state, or 4x4x4")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.cnn_only:
@@ -716,9 +728,12 @@ def main():
         extra = dict(precision=0) if args.c5_only == "fp64" else dict(precision=1, inner_rtol=1e-6)
         g = Growth(W)
         opts = mpm.make_opts(rtol=g.wl.rtol, restart=args.restart, maxit=1000, **extra)
-        res, _, _ = run_c5_path(mpm, g, ctx, torch.cuda.current_stream(), flush, opts, args.steps, args.warmup)
+        tile = c5_tile(mpm, g, ctx)[0] if args.c5_tile == "tuned" else None
+        res, _, _ = run_c5_path(mpm, g, ctx, torch.cuda.current_stream(), flush, opts, args.steps, args.warmup,
+                                tile=tile)
         keys = ("value", "ms_per_step", "steps_checked", "arnoldi_steps_per_species_step", "phase_us_last_state")
-        print(json.dumps({"mode": "c5_only", "path": args.c5_only, **{k: res[k] for k in keys}}), flush=True)
+        print(json.dumps({"mode": "c5_only", "path": args.c5_only, "tile": tile, **{k: res[k] for k in keys}}),
+              flush=True)
         return 0
     if args.shell256_only:
         import torch
@@ -769,6 +784,9 @@ def main():
                 "epochs": args.c5_epochs, "adam_steps": hist["samples"], "seconds": hist["seconds"],
                 "loss_first_last": [float(np.mean(hist["loss"][:10])), float(np.mean(hist["loss"][-20:]))]}
 
+    # ---- the tile of every path: the tuner's pick on the largest state
+    tile, tile_stored = c5_tile(mpm, g, ctx) if args.c5_tile == "tuned" else (None, None)
+
     # ---- the three paths on the same sampled steps
     peak, src = _peaks()
     mixed = dict(precision=1, inner_rtol=1e-6)
@@ -779,7 +797,7 @@ def main():
         headline = name == "learned_mixed"
         barrier()
         res, clk, kp = run_c5_path(mpm, g, ctx, stream, flush, opts, K, args.warmup, net,
-                                   ClockSampler(local) if headline else None)
+                                   ClockSampler(local) if headline else None, tile=tile)
         barrier()
         _, ms_max = replica_value(res["units"], res["kernel_ms"], world, "cuda")
         res["value"] = replica_value(res["units"], ms_max, world)[0]
@@ -877,7 +895,7 @@ def main():
     barrier()
     paths["learned_fgmres_mixed"] = run_c5_fgmres(
         mpm, g, ctx, stream, flush, dict(rtol=g.wl.rtol, restart=args.restart, maxit=1000, **mixed), K,
-        args.warmup, cnn)
+        args.warmup, cnn, tile=tile)
     barrier()
     line = {"metric": METRIC, "value": head["value"], "unit": "species-voxel-steps/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -889,6 +907,8 @@ def main():
                                "GMRES(8) (paths.fp64) and FP32-in-FP64 from c^n (paths.mixed) on the same steps",
                        "step": "mpm_step_enqueue: one CUDA graph per step (extraction + assembly launch, the network, "
                                "persistent GMRES + scatter launch)",
+                       "tile": {"xyz": tile or [4, 4, 4], "source": ("mpm_tune_tile on the last state (fewest stored "
+                                                                       f"voxels: {tile_stored})") if tile else "default"},
                        "l2": "flushed (256 MB write) before every timed step; lattice (2.2 GB) > L2",
                        "network_training": training, "parallelism": f"replicas x{world}"},
             "paths": paths, "roofline": roofline, "e2e": e2e, "gpu_launches": head["launches"], "clocks": clocks}
