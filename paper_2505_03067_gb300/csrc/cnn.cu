@@ -62,18 +62,19 @@ struct PrepArgs {
 };
 
 // Entry e (a bf16 element) of a weight image with input channels CI and N =
-// NO: core matrix cm = e / 64 at ((p * QP + q) * NG + ng), row r, column j.
-// Forward: value W[t][ci][co]; input gradient: W[26 - t][co][ci] (the tap
-// mirrored, input and output channels exchanged).
+// NO: core matrix cm = e / 64 at ((dy+1) * QP + q) * 3 NG + (dz+1) * NG + ng,
+// row r, column j.  Forward: value W[t][ci][co]; input gradient:
+// W[26 - t][co][ci] (the tap mirrored, input and output channels exchanged).
 __device__ float wimg_value(const float *W, int Ci, int Co, int CI, int NO, int e, bool dgrad)
 {
     const int KC = CI / 8, QC = 3 * KC, QP = QC + (QC & 1), NG = NO / 8;
     const int cm = e >> 6, w = e & 63, r = w >> 3, j = w & 7;
-    const int ng = cm % NG, rest = cm / NG;
-    const int q = rest % QP, p = rest / QP;
+    const int nn = cm % (3 * NG), rest = cm / (3 * NG);
+    const int q = rest % QP, dyi = rest / QP;
+    const int dzi = nn / NG, ng = nn % NG;
     if (q >= QC) return 0.0f;
     const int c = q / KC, kc = q % KC;
-    const int dx = c - 1, dy = p % 3 - 1, dz = p / 3 - 1;
+    const int dx = c - 1, dy = dyi - 1, dz = dzi - 1;
     const int t = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
     const int n = ng * 8 + r, k = kc * 8 + j;   // output, input channel of this convolution
     if (!dgrad) return (k < Ci && n < Co) ? W[((long long)t * Ci + k) * Co + n] : 0.0f;

@@ -57,7 +57,10 @@ constexpr int kThreads = 256;           // weight-gradient kernel: 8 warps
 constexpr int kEpiWarps = 12, kLoadWarps = 4;
 constexpr int kConvThreads = 32 * (kEpiWarps + kLoadWarps + 1);
 constexpr int kFwdSlots = 7;            // halo depths in the forward kernel's ring
-constexpr int kAcc = 4;                 // TMEM accumulators (32 columns each)
+// TMEM of the forward kernel: two unit buffers of 256 columns, slab k of a
+// unit (k < kZSeg) accumulating in columns NO * (kZSeg - 1 - k) .. + NO of its
+// buffer (descending, so the slabs one input depth feeds are adjacent)
+constexpr int kTmemBuf = 256;
 constexpr int kMaxImages = 16;
 // Activity bytes of a unit's halo region (depths z0-1 .. z0+kZSeg, rows
 // oy-1 .. oy+16, columns ox-1 .. ox+8: in its image's box and mask set),
@@ -234,9 +237,11 @@ struct Halo {
     static constexpr int NKS = QP / 2;             // MMAs of K = 16 per tap
 };
 
-// Weight image of one layer for the forward kernel: for tap pair p = (dy+1) +
-// 3 (dz+1), K-column q and output-channel group ng, the 8 x 8 core matrix
-// (rows n = ng*8 + r, columns k = q*8 + j) at ((p * QP + q) * NG + ng) * 128 bytes.
+// Weight image of one layer for the forward kernel: for tap row dy, K-column
+// q, tap depth dz and output-channel group ng, the 8 x 8 core matrix (rows n =
+// ng*8 + r, columns k = q*8 + j) at (((dy+1) * QP + q) * 3 NG + (dz+1) * NG +
+// ng) * 128 bytes: the three depths' N blocks are adjacent, so one MMA of N =
+// 3 NO applies the taps dz = -1, 0, +1 of an input depth to three output slabs.
 template <int CI, int NO>
 struct WImg {
     static constexpr int NG = NO / 8;
@@ -252,10 +257,13 @@ struct ConvSmem {
     static constexpr int ACT_BYTES = kActStride;
     static constexpr int ACT_OFF = RING_OFF + RING_BYTES;          // two units' activity bytes
     static constexpr int UNIT_OFF = (ACT_OFF + 2 * ACT_BYTES + 15) & ~15;   // two Units + two slab masks
-    // mbarriers: full[slots], empty[slots], acc_full[kAcc], acc_empty[kAcc], unit_full[2], unit_empty[2]
+    // mbarriers: full[slots], empty[slots], slab_done[2][kZSeg], tmem_free[2], unit_full[2], unit_empty[2]
     static constexpr int BAR_OFF = (UNIT_OFF + 2 * 32 + 2 * 4 + 15) & ~15;
-    static constexpr int NBAR = 2 * kFwdSlots + 2 * kAcc + 4;
-    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int NBAR = 2 * kFwdSlots + 2 * kZSeg + 2 + 4;
+    // more than half an SM's shared memory: one CTA per SM, so its 512-column
+    // TMEM allocation never waits for another CTA's
+    static constexpr int BYTES0 = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int BYTES = BYTES0 > 120 * 1024 ? BYTES0 : 120 * 1024;
 };
 
 enum { EPI_GELU = 0, EPI_OUT = 1, EPI_DGRAD = 2 };
@@ -441,12 +449,15 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parit
 //    slots (cp.async; a slot's mbarrier completes when every loader's copies
 //    into it have landed; a slot is refilled once the MMAs that read it
 //    completed);
-//  - 1 MMA warp (one thread) issues, per active slab, 9 taps x (K/16) MMAs
-//    into one of kAcc TMEM accumulators and commits them; it releases a ring
-//    slot by a commit once the last slab reading it was issued;
+//  - 1 MMA warp (one thread) issues, per input depth, 3 tap rows (dy) x (K/16)
+//    MMAs of N = up to 3 NO: the depth's halo (the A operand, read once) times
+//    the weights of its three tap depths dz, into the accumulators of the
+//    (active) output slabs it feeds, which lie side by side in TMEM; the
+//    first MMA into a slab overwrites it.  A commit releases the depth's ring
+//    slot, and one marks slab j - 2 complete after depth j;
 //  - 12 EPILOGUE warps (warp w: TMEM lane quarter w & 3, channels
-//    8 (w >> 2) .. 8 (w >> 2) + 7) drain each accumulator through the
-//    epilogue and hand it back.
+//    8 (w >> 2) .. 8 (w >> 2) + 7) drain each complete slab through the
+//    epilogue and hand the unit's TMEM buffer back.
 // NO: MMA N (output channels padded to 16 or 32).
 template <int CI, int NO, int EPI>
 __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
@@ -460,8 +471,8 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
     __shared__ uint32_t s_tmem;
     __shared__ int32_t s_abort, s_lstop, s_ui;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);
-    uint64_t *full = bar, *empty = bar + kFwdSlots, *accf = bar + 2 * kFwdSlots, *acce = accf + kAcc;
-    uint64_t *unitf = acce + kAcc, *unite = unitf + 2;
+    uint64_t *full = bar, *empty = bar + kFwdSlots, *accf = bar + 2 * kFwdSlots, *accu = accf + 2 * kZSeg;
+    uint64_t *unitf = accu + 2, *unite = unitf + 2;
     Unit *urec = reinterpret_cast<Unit *>(sm + S::UNIT_OFF);
     uint32_t *ubits = reinterpret_cast<uint32_t *>(sm + S::UNIT_OFF + 64);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -474,7 +485,7 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
         reinterpret_cast<uint4 *>(sm + S::W_OFF)[i] = __ldg(reinterpret_cast<const uint4 *>(A.wimg) + i);
     for (int i = tid; i < S::RING_BYTES / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(sm + S::RING_OFF)[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (warp == 0) tmem_alloc(&s_tmem, 128);
+    if (warp == 0) tmem_alloc(&s_tmem, 2 * kTmemBuf);
     if (tid == 0) {
         s_abort = 0;
         s_lstop = 0;
@@ -482,10 +493,8 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
             mbar_init(&full[i], NLD);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < kAcc; ++i) {
-            mbar_init(&accf[i], 1);
-            mbar_init(&acce[i], kEpiWarps);
-        }
+        for (int i = 0; i < 2 * kZSeg; ++i) mbar_init(&accf[i], 1);
+        for (int i = 0; i < 2; ++i) mbar_init(&accu[i], kEpiWarps);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&unitf[i], 1);
             mbar_init(&unite[i], kEpiWarps + 1);
@@ -558,9 +567,8 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
     } else if (warp == kEpiWarps + kLoadWarps) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
-            constexpr uint32_t kIdesc = idesc_bf16(128, NO, false, false);
-            const uint64_t adesc0 = sdesc(rbase, 128u, H::GS), bdesc0 = sdesc(wbase, NG * 128u, 128u);
-            uint32_t dbase = 0, m = 0;
+            const uint64_t adesc0 = sdesc(rbase, 128u, H::GS), bdesc0 = sdesc(wbase, 3u * NG * 128u, 128u);
+            uint32_t dbase = 0;
             bool ok = true;
             for (int n = 0; ok; ++n) {
                 const int ub = n & 1;
@@ -569,40 +577,56 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                 const int nz = urec[ub].nz;
                 if (nz < 0) break;                // the stop record
                 const uint32_t bits = ubits[ub];
-                for (int k = 0; k < nz && ok; ++k) {
-                    // slab k reads depths k, k+1, k+2; k+2 is the newest
-                    for (int j = (k == 0 ? 0 : k + 2); j <= k + 2 && ok; ++j) {
-                        const uint32_t d = dbase + j;
-                        ok = mbar_wait_or_abort(&full[d % kFwdSlots], (d / kFwdSlots) & 1, T, A.err, abort);
-                    }
+                // the unit's TMEM buffer is free once the epilogue drained unit n - 2
+                if (n >= 2) ok = mbar_wait_or_abort(&accu[ub], ((n >> 1) - 1) & 1, T, A.err, abort);
+                if (!ok) break;
+                tc_after_sync();
+                const uint32_t cbuf = tmem + (uint32_t)ub * kTmemBuf;
+                for (int j = 0; j < nz + 2 && ok; ++j) {
+                    const uint32_t d = dbase + j, slot = d % kFwdSlots;
+                    ok = mbar_wait_or_abort(&full[slot], (d / kFwdSlots) & 1, T, A.err, abort);
                     if (!ok) break;
                     fence_async_smem();
-                    if ((bits >> k) & 1u) {
-                        const uint32_t b = m % kAcc, use = m / kAcc;
-                        if (use >= 1) ok = mbar_wait_or_abort(&acce[b], (use - 1) & 1, T, A.err, abort);
-                        if (!ok) break;
-                        tc_after_sync();
-                        const uint32_t dt = tmem + b * 32u;
-#pragma unroll
-                        for (int p = 0; p < 9; ++p) {
-                            const int dy = p % 3 - 1, dz = p / 3 - 1;
-                            const uint32_t slot = (dbase + k + 1 + dz) % kFwdSlots;
-                            const uint64_t a = adesc0 + ((slot * H::SLOT + (uint32_t)(dy + 1) * H::GS) >> 4);
-                            const uint64_t bb = bdesc0 + ((uint32_t)p * H::QP * NG * 128u >> 4);
-#pragma unroll
-                            for (int s2 = 0; s2 < H::NKS; ++s2)
-                                mma_bf16(dt, a + (uint64_t)(s2 * 16), bb + (uint64_t)(s2 * NG * 16), kIdesc,
-                                         (p | s2) != 0);
+                    tc_after_sync();
+                    // depth j feeds slabs j (tap dz = -1), j - 1 (dz = 0), j - 2 (dz = +1):
+                    // the active ones among them, hi .. lo (descending)
+                    int hi = -1, lo = kZSeg;
+                    for (int k = (j >= 2 ? j - 2 : 0); k <= j && k < nz; ++k)
+                        if ((bits >> k) & 1u) {
+                            hi = k > hi ? k : hi;
+                            lo = k < lo ? k : lo;
                         }
-                        mma_commit(&accf[b]);
-                        ++m;
+                    if (hi >= 0) {
+                        const bool fresh = hi == j;       // slab j's first MMA: it overwrites
+                        const uint32_t ahalo = slot * H::SLOT;
+#pragma unroll
+                        for (int dyi = 0; dyi < 3; ++dyi) {
+                            const uint64_t a = adesc0 + ((ahalo + (uint32_t)dyi * H::GS) >> 4);
+#pragma unroll
+                            for (int s2 = 0; s2 < H::NKS; ++s2) {
+                                const uint64_t aa = a + (uint64_t)(s2 * 16);
+                                // B: core matrix (dy, q = 2 s2, dz block j - k, ng 0) of the first slab k
+                                const uint32_t bq = (uint32_t)(dyi * H::QP + 2 * s2) * 3u * NG;
+                                if (dyi == 0 && s2 == 0 && fresh) {
+                                    mma_bf16(cbuf + NO * (kZSeg - 1 - j), aa, bdesc0 + (uint64_t)(bq * 8u),
+                                             idesc_bf16(128, NO, false, false), 0u);
+                                    if (lo < hi)
+                                        mma_bf16(cbuf + NO * (kZSeg - hi), aa, bdesc0 + (uint64_t)((bq + NG) * 8u),
+                                                 idesc_bf16(128, NO * (hi - lo), false, false), 1u);
+                                } else {
+                                    mma_bf16(cbuf + NO * (kZSeg - 1 - hi), aa,
+                                             bdesc0 + (uint64_t)((bq + (uint32_t)(j - hi) * NG) * 8u),
+                                             idesc_bf16(128, NO * (hi - lo + 1), false, false), 1u);
+                                }
+                            }
+                        }
                     }
-                    // depth k is read by no later slab of the unit
-                    mma_commit(&empty[(dbase + k) % kFwdSlots]);
+                    mma_commit(&empty[slot]);            // no later MMA reads this depth
+                    if (j >= 2 && j - 2 < nz) mma_commit(&accf[ub * kZSeg + (j - 2)]);   // slab j - 2 complete
                 }
                 if (!ok) break;
-                mma_commit(&empty[(dbase + nz) % kFwdSlots]);
-                mma_commit(&empty[(dbase + nz + 1) % kFwdSlots]);
+                // one completion per buffer use for every slab barrier
+                for (int k = nz; k < kZSeg; ++k) mma_commit(&accf[ub * kZSeg + k]);
                 dbase += nz + 2;
                 mbar_arrive(&unite[ub]);
             }
@@ -623,7 +647,6 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
             for (int i = 0; i < 8; ++i)
                 if (EPI != EPI_OUT || i < 3) bias[i] = A.bias[c0 + i];
         }
-        uint32_t m = 0;
         bool ok = true;
         for (int n = 0; ok; ++n) {
             const int ub = n & 1;
@@ -636,7 +659,6 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
             const uint8_t *act = sm + S::ACT_OFF + ub * S::ACT_BYTES;
             for (int k = 0; k < u.nz && ok; ++k) {
                 if (!((bits >> k) & 1u)) continue;
-                const uint32_t b = m % kAcc, use = m / kAcc;
                 const int z = u.z0 + k, x = u.ox + ex, y = u.oy + ey;
                 const bool on = reads && act[((k + 1) * kHaloY + ey + 1) * kHaloX + ex + 1] != 0;
                 const int64_t v = on ? vox_index(D, u.b, x, y, z) : 0;
@@ -671,20 +693,16 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                         }
                     }
                 }
-                if (lane == 0) ok = mbar_wait_or_abort(&accf[b], use & 1, T, A.err, abort);
+                if (lane == 0) ok = mbar_wait_or_abort(&accf[ub * kZSeg + k], (n >> 1) & 1, T, A.err, abort);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) break;
                 tc_after_sync();
                 float d[8];
                 if (reads) {
-                    tmem_ld8(tmem + b * 32u + (uint32_t)c0 + ((uint32_t)(lq * 32) << 16), d);
+                    tmem_ld8(tmem + (uint32_t)ub * kTmemBuf + (uint32_t)(NO * (kZSeg - 1 - k)) + (uint32_t)c0 +
+                                 ((uint32_t)(lq * 32) << 16), d);
                     tc_wait_ld();
                 }
-                // the accumulator is free again once every warp has read it
-                tc_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[b]);
-                ++m;
                 if (on) {
                     if (EPI == EPI_OUT) {
                         if (A.pred) {
@@ -725,16 +743,20 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                     }
                 }
             }
-            // this warp is done with the unit's activity bytes and records
+            // this warp is done with the unit's TMEM buffer, activity bytes and records
+            tc_before_sync();
             __syncwarp();
-            if (ok && lane == 0) mbar_arrive(&unite[ub]);
+            if (ok && lane == 0) {
+                mbar_arrive(&accu[ub]);
+                mbar_arrive(&unite[ub]);
+            }
         }
     }
     // leave: every role finished (or gave up); free TMEM
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (warp == 0) tmem_dealloc(tmem, 2 * kTmemBuf);
     // the launch's last CTA resets the unit counter for the next launch
     if (tid == 0) {
         __threadfence();
