@@ -517,40 +517,67 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
         const int lt = tid - NE;
         HaloItems<CI, NLD> items;
         items.init(lt, D.L[0]);
+        // Units are taken from a counter shared by the CTAs (units hold 1..8
+        // active slabs, so a fixed assignment leaves CTAs unequally loaded).
+        // The next unit's index, activity bytes (one 16-byte share per
+        // thread), record and slab mask are fetched a unit ahead, so a unit's
+        // start waits on no global round trip; an index past the list is
+        // published as the stop record.
+        constexpr int kAct16 = kActStride / 16;
+        static_assert(kAct16 <= NLD, "one activity share per loader thread");
+        const uint4 *uact4 = reinterpret_cast<const uint4 *>(A.uact);
+        uint4 actq = make_uint4(0u, 0u, 0u, 0u);
+        Unit urow;
+        urow.b = urow.ox = urow.oy = urow.z0 = urow.nz = urow.pad0 = urow.pad1 = urow.pad2 = 0;
+        uint32_t ubit = 0u;
+        if (lt == 0) s_ui = atomicAdd(A.work, 1);
+        named_sync(1, NLD);
+        int ui = s_ui;
+        if (ui < nunits) {
+            if (lt < kAct16) actq = __ldg(uact4 + (size_t)ui * kAct16 + lt);
+            if (lt == 0) {
+                urow = A.units[ui];
+                ubit = A.ubits[ui];
+            }
+        }
         uint32_t dseq = 0;                        // depths issued
         for (int n = 0;; ++n) {
-            // units are taken from a counter shared by the CTAs (units hold 1..8
-            // active slabs, so a fixed assignment leaves CTAs unequally loaded);
-            // a unit index past the list is published as the stop record
             const int ub = n & 1;
+            named_sync(1, NLD);                   // every loader read s_ui
             if (lt == 0) {
+                s_ui = ui < nunits ? atomicAdd(A.work, 1) : nunits;
                 const bool w = n < 2 || mbar_wait_or_abort(&unite[ub], ((n >> 1) - 1) & 1, T, A.err, abort);
                 if (!w || *abort) s_lstop = 1;
-                else s_ui = atomicAdd(A.work, 1);
             }
             named_sync(1, NLD);
             if (s_lstop) break;
-            const int ui = s_ui;
+            const int ui_next = s_ui;
             if (ui >= nunits) {
                 if (lt == 0) {
-                    Unit stop;
-                    stop.b = stop.ox = stop.oy = stop.z0 = 0;
+                    Unit stop = urow;
                     stop.nz = -1;
-                    stop.pad0 = stop.pad1 = stop.pad2 = 0;
                     urec[ub] = stop;
                     mbar_arrive(&unitf[ub]);
                 }
                 break;
             }
-            const Unit u = A.units[ui];
             uint8_t *act = sm + S::ACT_OFF + ub * S::ACT_BYTES;
-            copy_unit_act<NLD>(A.uact, ui, act, lt);
-            if (lt == 0) ubits[ub] = A.ubits[ui];
-            named_sync(1, NLD);
+            if (lt < kAct16) reinterpret_cast<uint4 *>(act)[lt] = actq;
             if (lt == 0) {
-                urec[ub] = u;
-                mbar_arrive(&unitf[ub]);
+                ubits[ub] = ubit;
+                urec[ub] = urow;
             }
+            named_sync(1, NLD);
+            if (lt == 0) mbar_arrive(&unitf[ub]);
+            const Unit u = urec[ub];
+            if (ui_next < nunits) {
+                if (lt < kAct16) actq = __ldg(uact4 + (size_t)ui_next * kAct16 + lt);
+                if (lt == 0) {
+                    urow = A.units[ui_next];
+                    ubit = A.ubits[ui_next];
+                }
+            }
+            ui = ui_next;
             for (int j = 0; j < u.nz + 2; ++j) {
                 const uint32_t slot = dseq % kFwdSlots, use = dseq / kFwdSlots;
                 if (lt == 0 && use >= 1 && !mbar_wait_or_abort(&empty[slot], (use - 1) & 1, T, A.err, abort))
