@@ -782,7 +782,8 @@ def main():
     training = {"trajectory": "growth_crop seed 6: the growth geometry with other cells and rates, 324x264x264 crop "
                               "of its growth region, 200 steps per epoch of the FP64 solver at rtol 1e-10",
                 "epochs": args.c5_epochs, "adam_steps": hist["samples"], "seconds": hist["seconds"],
-                "loss_first_last": [float(np.mean(hist["loss"][:10])), float(np.mean(hist["loss"][-20:]))]}
+                "loss_first_last": ([float(np.mean(hist["loss"][:10])), float(np.mean(hist["loss"][-20:]))]
+                                    if hist["loss"] else None)}
 
     # ---- the tile of every path: the tuner's pick on the largest state
     tile, tile_stored = c5_tile(mpm, g, ctx) if args.c5_tile == "tuned" else (None, None)
