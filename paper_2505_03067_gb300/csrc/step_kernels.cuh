@@ -587,32 +587,36 @@ __device__ __forceinline__ bool extract_phases(const ExtractArgs &A, const Batch
         __syncthreads();
         unsigned long long cnt = 0;
         if (g.n[0] > 0) {
-            // one row per warp and iteration; the first four 32-voxel chunks of
-            // the row have their mask bytes in flight together
+            // one row of tiles (TY x TZ box rows) per warp and iteration: for
+            // each 32-voxel chunk the mask bytes of those rows are in flight
+            // together and OR-ed, and the chunk's active tiles are written
+            // once, by the first lane of each tile (the rows of a tile would
+            // otherwise store the same activity bytes again and again)
             const int64_t gw = (int64_t)b * (NT / 32) + warp, nw = (int64_t)nb * (NT / 32);
-            const int64_t nrows = (int64_t)g.n[1] * g.n[2];
-            for (int64_t row = gw; row < nrows; row += nw) {
-                const int by = (int)(row % g.n[1]), bz = (int)(row / g.n[1]);
-                const int64_t L0 = (int64_t)g.lo[0] + (int64_t)g.Lx * ((int64_t)(g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
-                const int64_t trow = ((int64_t)(bz >> g.lt[2]) * g.nt[1] + (by >> g.lt[1])) * g.nt[0];
-                uint32_t m[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int bx = c * 32 + lane;
-                    m[c] = bx < g.n[0] ? __ldg(A.mask + L0 + bx) : 0u;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (m[c]) {
-                        ++cnt;
-                        A.active[trow + ((c * 32 + lane) >> g.lt[0])] = 1;
+            const int TX = 1 << g.lt[0], TY = 1 << g.lt[1], TZ = 1 << g.lt[2];
+            const int64_t ngroups = (int64_t)g.nt[1] * g.nt[2];
+            for (int64_t grp = gw; grp < ngroups; grp += nw) {
+                const int ty = (int)(grp % g.nt[1]), tz = (int)(grp / g.nt[1]);
+                const int64_t trow = ((int64_t)tz * g.nt[1] + ty) * g.nt[0];
+                const int y1 = min(TY, g.n[1] - ty * TY), z1 = min(TZ, g.n[2] - tz * TZ);
+                const int nr = y1 * z1;
+                for (int c0 = 0; c0 < g.n[0]; c0 += 32) {
+                    const int bx = c0 + lane;
+                    uint32_t any = 0u;
+                    if (bx < g.n[0]) {
+#pragma unroll 4
+                        for (int r = 0; r < nr; ++r) {
+                            const int by = ty * TY + r % y1, bz = tz * TZ + r / y1;
+                            const int64_t L0 = (int64_t)g.lo[0] +
+                                               (int64_t)g.Lx * ((int64_t)(g.lo[1] + by) + (int64_t)g.Ly * (g.lo[2] + bz));
+                            const uint32_t m = __ldg(A.mask + L0 + bx);
+                            cnt += m != 0u ? 1u : 0u;
+                            any |= m;
+                        }
                     }
-                }
-                for (int bx = 128 + lane; bx < g.n[0]; bx += 32) {
-                    if (__ldg(A.mask + L0 + bx)) {
-                        ++cnt;
+                    const unsigned bal = __ballot_sync(0xffffffffu, any != 0u);
+                    if ((lane & (TX - 1)) == 0 && ((bal >> lane) & ((TX >= 32) ? 0xffffffffu : ((1u << TX) - 1u))))
                         A.active[trow + (bx >> g.lt[0])] = 1;
-                    }
                 }
             }
         }
