@@ -109,6 +109,33 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
                  "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
+// The same issued by a converged warp: every lane executes it with the same
+// (warp-uniform) operands and one elected lane issues.  Descriptors come as
+// their two 32-bit words (the start address and LBO in the low word), so a
+// tile offset is one 32-bit add.
+__device__ __forceinline__ void mma_bf16_warp(uint32_t d_tmem, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                              uint32_t idesc, uint32_t accum)
+{
+    asm volatile("{\n.reg .pred p, e;\n.reg .b64 a, b;\nelect.sync _|e, 0xffffffff;\nsetp.ne.b32 p, %6, 0;\n"
+                 "mov.b64 a, {%1, %2};\nmov.b64 b, {%3, %4};\n"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %5, p;\n}" ::"r"(d_tmem),
+                 "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit_warp(uint64_t *bar)
+{
+    asm volatile("{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Low and high words of a no-swizzle shared-memory descriptor (see sdesc).
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr, uint32_t lbo)
+{
+    return ((addr & 0x3FFFFu) >> 4) | (((lbo >> 4) & 0x3FFFu) << 16);
+}
+__host__ __device__ constexpr uint32_t sdesc_hi(uint32_t sbo) { return ((sbo >> 4) & 0x3FFFu) | (1u << 14); }
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -177,6 +204,13 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 
 // 32 lanes x 32 bit, N consecutive columns: thread t of the warp receives
 // columns [col, col + N) of lane (warp's lane quarter) * 32 + t.
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr)
+{
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 {
     uint32_t r[8];
@@ -199,10 +233,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 16-byte asynchronous global -> shared copy; src_bytes 0 writes zeros.
+// 16-byte asynchronous global -> shared copy; src_bytes 0 writes zeros.  The
+// copy allocates in L1 (.ca): the three x-shifted halo copies read each
+// 16-byte source chunk three times, and the second and third reads hit L1.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // Wait until at most n of this thread's committed groups are pending.
@@ -218,7 +254,22 @@ __device__ __forceinline__ void cp_async_wait(int n)
     }
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the
+// rational-exponential approximation of Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26 (|error| <= 1.5e-7 for x >= 0):
+// erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2), t = 1 / (1 + p x).
+// For z < 0, Phi(z) = (1 - erf(|z| / sqrt 2)) / 2.  Far below the bf16 rounding
+// of the stored activation (2^-9 relative).
+__device__ __forceinline__ float gelu(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.0f));
+    const float e = exp2f(-1.4426950408889634f * x * x);
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float half_tail = 0.5f * poly * e;   // (1 - erf(x)) / 2
+    return z * (z >= 0.0f ? 1.0f - half_tail : half_tail);
+}
 __device__ __forceinline__ float gelu_grad(float z)
 {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
@@ -441,6 +492,24 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parit
     }
 }
 
+// Warp-level bounded wait for phase `parity`: every lane tests the barrier
+// (non-blocking) and the warp agrees by a vote, so a phase that is already
+// complete costs no divergent branch and no broadcast; otherwise lane 0 waits
+// (mbar_wait_or_abort) and broadcasts the outcome.  The whole warp calls it.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, uint64_t timeout_ns, int32_t *err,
+                                               volatile int32_t *abort)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    if (__all_sync(0xffffffffu, ok)) return true;
+    int w = 1;
+    if ((threadIdx.x & 31) == 0) w = mbar_wait_or_abort(bar, parity, timeout_ns, err, abort) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, w, 0) != 0;
+}
+
 // One persistent CTA per SM over the units i = blockIdx, blockIdx + gridDim,
 // ... of the plan's list, as a pipeline of three roles that meet only at
 // mbarriers (no CTA-wide barrier in the steady state):
@@ -593,70 +662,71 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
         cp_async_wait(0);
     } else if (warp == kEpiWarps + kLoadWarps) {
         // ------------------------------------------------------------ MMA issue
-        if (lane == 0) {
-            const uint64_t adesc0 = sdesc(rbase, 128u, H::GS), bdesc0 = sdesc(wbase, 3u * NG * 128u, 128u);
-            uint32_t dbase = 0;
-            bool ok = true;
-            for (int n = 0; ok; ++n) {
-                const int ub = n & 1;
-                ok = mbar_wait_or_abort(&unitf[ub], (n >> 1) & 1, T, A.err, abort);
+        // The whole warp runs this loop on warp-uniform values (shared-memory
+        // reads broadcast from lane 0), and one elected lane issues each
+        // tcgen05 instruction: operands the compiler can keep in uniform
+        // registers let the MMAs issue back to back.
+        constexpr uint32_t kId1 = idesc_bf16(128, NO, false, false), kId2 = idesc_bf16(128, 2 * NO, false, false),
+                           kId3 = idesc_bf16(128, 3 * NO, false, false);
+        const uint32_t tm = __shfl_sync(0xffffffffu, tmem, 0);
+        const uint32_t alo0 = sdesc_lo(rbase, 128u), blo0 = sdesc_lo(wbase, 3u * NG * 128u);
+        constexpr uint32_t ahi = sdesc_hi(H::GS), bhi = sdesc_hi(128u);
+        uint32_t dbase = 0;
+        bool ok = true;
+        for (int n = 0; ok; ++n) {
+            const int ub = n & 1;
+            ok = mbar_wait_warp(&unitf[ub], (n >> 1) & 1, T, A.err, abort);
+            if (!ok) break;
+            const int nz = __shfl_sync(0xffffffffu, urec[ub].nz, 0);
+            if (nz < 0) break;                    // the stop record
+            const uint32_t bits = __shfl_sync(0xffffffffu, ubits[ub], 0);
+            // the unit's TMEM buffer is free once the epilogue drained unit n - 2
+            ok = n < 2 || mbar_wait_warp(&accu[ub], ((n >> 1) - 1) & 1, T, A.err, abort);
+            if (!ok) break;
+            tc_after_sync();
+            const uint32_t cbuf = tm + (uint32_t)ub * kTmemBuf;
+            for (int j = 0; j < nz + 2; ++j) {
+                const uint32_t d = dbase + j, slot = d % kFwdSlots;
+                ok = mbar_wait_warp(&full[slot], (d / kFwdSlots) & 1, T, A.err, abort);
                 if (!ok) break;
-                const int nz = urec[ub].nz;
-                if (nz < 0) break;                // the stop record
-                const uint32_t bits = ubits[ub];
-                // the unit's TMEM buffer is free once the epilogue drained unit n - 2
-                if (n >= 2) ok = mbar_wait_or_abort(&accu[ub], ((n >> 1) - 1) & 1, T, A.err, abort);
-                if (!ok) break;
+                fence_async_smem();
                 tc_after_sync();
-                const uint32_t cbuf = tmem + (uint32_t)ub * kTmemBuf;
-                for (int j = 0; j < nz + 2 && ok; ++j) {
-                    const uint32_t d = dbase + j, slot = d % kFwdSlots;
-                    ok = mbar_wait_or_abort(&full[slot], (d / kFwdSlots) & 1, T, A.err, abort);
-                    if (!ok) break;
-                    fence_async_smem();
-                    tc_after_sync();
-                    // depth j feeds slabs j (tap dz = -1), j - 1 (dz = 0), j - 2 (dz = +1):
-                    // the active ones among them, hi .. lo (descending)
-                    int hi = -1, lo = kZSeg;
-                    for (int k = (j >= 2 ? j - 2 : 0); k <= j && k < nz; ++k)
-                        if ((bits >> k) & 1u) {
-                            hi = k > hi ? k : hi;
-                            lo = k < lo ? k : lo;
-                        }
-                    if (hi >= 0) {
-                        const bool fresh = hi == j;       // slab j's first MMA: it overwrites
-                        const uint32_t ahalo = slot * H::SLOT;
-#pragma unroll
-                        for (int dyi = 0; dyi < 3; ++dyi) {
-                            const uint64_t a = adesc0 + ((ahalo + (uint32_t)dyi * H::GS) >> 4);
-#pragma unroll
-                            for (int s2 = 0; s2 < H::NKS; ++s2) {
-                                const uint64_t aa = a + (uint64_t)(s2 * 16);
-                                // B: core matrix (dy, q = 2 s2, dz block j - k, ng 0) of the first slab k
-                                const uint32_t bq = (uint32_t)(dyi * H::QP + 2 * s2) * 3u * NG;
-                                if (dyi == 0 && s2 == 0 && fresh) {
-                                    mma_bf16(cbuf + NO * (kZSeg - 1 - j), aa, bdesc0 + (uint64_t)(bq * 8u),
-                                             idesc_bf16(128, NO, false, false), 0u);
-                                    if (lo < hi)
-                                        mma_bf16(cbuf + NO * (kZSeg - hi), aa, bdesc0 + (uint64_t)((bq + NG) * 8u),
-                                                 idesc_bf16(128, NO * (hi - lo), false, false), 1u);
-                                } else {
-                                    mma_bf16(cbuf + NO * (kZSeg - 1 - hi), aa,
-                                             bdesc0 + (uint64_t)((bq + (uint32_t)(j - hi) * NG) * 8u),
-                                             idesc_bf16(128, NO * (hi - lo + 1), false, false), 1u);
-                                }
-                            }
-                        }
+                // depth j feeds slabs j (tap dz = -1), j - 1 (dz = 0), j - 2 (dz = +1):
+                // the active ones among them, hi .. lo (descending)
+                const uint32_t win = (bits & ((1u << nz) - 1u)) >> (j >= 2 ? j - 2 : 0);
+                const uint32_t sel = win & (j >= 2 ? 7u : (j == 1 ? 3u : 1u));
+                if (sel) {
+                    const int base = j >= 2 ? j - 2 : 0;
+                    const int hi = base + 31 - __clz(sel), lo = base + __ffs(sel) - 1;
+                    const int nsl = hi - lo + 1;
+                    const uint32_t idn = nsl == 3 ? kId3 : (nsl == 2 ? kId2 : kId1);
+                    const uint32_t dacc = cbuf + (uint32_t)(NO * (kZSeg - 1 - hi));
+                    const uint32_t alo = alo0 + slot * (uint32_t)(H::SLOT >> 4);
+                    const uint32_t blo = blo0 + (uint32_t)((j - hi) * NG * 8);
+                    // first tap: the first MMA into slab j (hi == j) overwrites it
+                    if (hi == j) {
+                        mma_bf16_warp(dacc, alo, ahi, blo, bhi, kId1, 0u);
+                        if (lo < hi) mma_bf16_warp(dacc + NO, alo, ahi, blo + NG * 8, bhi, nsl == 3 ? kId2 : kId1, 1u);
+                    } else {
+                        mma_bf16_warp(dacc, alo, ahi, blo, bhi, idn, 1u);
                     }
-                    mma_commit(&empty[slot]);            // no later MMA reads this depth
-                    if (j >= 2 && j - 2 < nz) mma_commit(&accf[ub * kZSeg + (j - 2)]);   // slab j - 2 complete
+#pragma unroll
+                    for (int t = 1; t < 3 * H::NKS; ++t) {
+                        const int dyi = t / H::NKS, s2 = t % H::NKS;
+                        // A: halo row dyi, K-columns 2 s2 .. 2 s2 + 1; B: core matrix (dy, q = 2 s2, dz block j - hi, ng 0)
+                        mma_bf16_warp(dacc, alo + (uint32_t)((dyi * H::GS) >> 4) + (uint32_t)(s2 * 16), ahi,
+                                      blo + (uint32_t)((dyi * H::QP + 2 * s2) * 3 * NG * 8), bhi, idn, 1u);
+                    }
                 }
-                if (!ok) break;
-                // one completion per buffer use for every slab barrier
-                for (int k = nz; k < kZSeg; ++k) mma_commit(&accf[ub * kZSeg + k]);
-                dbase += nz + 2;
-                mbar_arrive(&unite[ub]);
+                mma_commit_warp(&empty[slot]);          // no later MMA reads this depth
+                if (j >= 2 && j - 2 < nz) mma_commit_warp(&accf[ub * kZSeg + (j - 2)]);   // slab j - 2 complete
             }
+            if (!ok) break;
+            // one completion per buffer use for every slab barrier
+            for (int k = nz; k < kZSeg; ++k) mma_commit_warp(&accf[ub * kZSeg + k]);
+            dbase += nz + 2;
+            if (lane == 0) mbar_arrive(&unite[ub]);
+            __syncwarp();
         }
         __syncwarp();
     } else if (tid < NE) {
@@ -664,15 +734,18 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
         const int lq = warp & 3, wq = warp >> 2;
         const int row = lq * 32 + lane;           // voxel (row & 7, row >> 3) of the slab
         const int ex = row & 7, ey = row >> 3;
-        const int c0 = 8 * wq;                    // first channel of this thread
-        const bool reads = EPI != EPI_OUT || wq == 0;
+        // first channel of this thread: 8 channels per warp group; the output
+        // layer's three channels go one to each warp group (channel wq)
+        const int c0 = EPI == EPI_OUT ? wq : 8 * wq;
+        // (image mode writes all three predicted channels, solver mode the species')
+        const bool reads = EPI != EPI_OUT || wq < (A.pred ? 3 : (A.nspecies < 3 ? A.nspecies : 3));
         float bias[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) bias[i] = 0.0f;
         if (A.bias && EPI != EPI_DGRAD) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                if (EPI != EPI_OUT || i < 3) bias[i] = A.bias[c0 + i];
+                if (EPI != EPI_OUT || i == 0) bias[i] = A.bias[c0 + i];
         }
         bool ok = true;
         for (int n = 0; ok; ++n) {
@@ -703,8 +776,7 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                         pre[4] = q1.x; pre[5] = q1.y; pre[6] = q1.z; pre[7] = q1.w;
                     } else if (EPI == EPI_OUT) {
                         if (A.pred) {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) pre[c] = A.f32[v * 3 + c];
+                            pre[0] = A.f32[v * 3 + c0];
                         } else {
                             const BoxGeo &g = *A.geo;
                             const int bx = x - g.lo[0], by = y - g.lo[1], bz = z - g.lo[2];
@@ -715,31 +787,31 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                                           iz = bz & ((1 << g.lt[2]) - 1);
                                 e = ((int64_t)t << (g.lt[0] + g.lt[1] + g.lt[2])) + ix +
                                     ((int64_t)(iy + (iz << g.lt[1])) << g.lt[0]);
-                                for (int c = 0; c < A.nspecies && c < 3; ++c) cn[c] = A.field[c][v];
+                                cn[0] = A.field[c0][v];
                             }
                         }
                     }
                 }
-                if (lane == 0) ok = mbar_wait_or_abort(&accf[ub * kZSeg + k], (n >> 1) & 1, T, A.err, abort);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                ok = mbar_wait_warp(&accf[ub * kZSeg + k], (n >> 1) & 1, T, A.err, abort);
                 if (!ok) break;
                 tc_after_sync();
                 float d[8];
                 if (reads) {
-                    tmem_ld8(tmem + (uint32_t)ub * kTmemBuf + (uint32_t)(NO * (kZSeg - 1 - k)) + (uint32_t)c0 +
-                                 ((uint32_t)(lq * 32) << 16), d);
+                    const uint32_t ta = tmem + (uint32_t)ub * kTmemBuf + (uint32_t)(NO * (kZSeg - 1 - k)) + (uint32_t)c0 +
+                                        ((uint32_t)(lq * 32) << 16);
+                    if (EPI == EPI_OUT)
+                        d[0] = tmem_ld1(ta);
+                    else
+                        tmem_ld8(ta, d);
                     tc_wait_ld();
                 }
                 if (on) {
                     if (EPI == EPI_OUT) {
                         if (A.pred) {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) A.pred[v * 3 + c] = pre[c] + A.s_out * (d[c] + bias[c]);
+                            A.pred[v * 3 + c0] = pre[0] + A.s_out * (d[0] + bias[0]);
                         } else if (e >= 0) {
-                            for (int c = 0; c < A.nspecies && c < 3; ++c) {
-                                const double p = cn[c] + (double)(A.s_out * (d[c] + bias[c]));
-                                A.xs[c][e] = isfinite(p) ? p : cn[c];   // a non-finite guess falls back to c^n
-                            }
+                            const double p = cn[0] + (double)(A.s_out * (d[0] + bias[0]));
+                            A.xs[c0][e] = isfinite(p) ? p : cn[0];   // a non-finite guess falls back to c^n
                         }
                     } else {
                         uint32_t o[4];
