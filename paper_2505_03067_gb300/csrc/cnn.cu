@@ -630,9 +630,23 @@ mpm_status conv(mpm_ctx *ctx, mpm_cnn *c, tc::ConvArgs A, int slot, cudaStream_t
     A.done = c->counters + 16 + slot;
     A.err = c->d_err;
     A.timeout_ns = ctx->timeout_ns;
-    tc::k_conv_tc<CI, NO, EPI><<<ctx->num_sms, tc::kConvThreads, smem, st>>>(A);
+    // programmatic dependent launch: the next layer's CTAs start their
+    // prologue (weights into shared memory, TMEM) on the SMs this launch has
+    // left, and wait (griddepcontrol.wait) for it to complete before reading
+    // its output
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctx->num_sms);
+    cfg.blockDim = dim3((unsigned)tc::kConvThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tc::k_conv_tc<CI, NO, EPI>, A);
     ctx->launches += 1;
-    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         cudaFuncAttributes fa;
         memset(&fa, 0, sizeof(fa));

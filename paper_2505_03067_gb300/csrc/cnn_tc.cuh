@@ -51,10 +51,12 @@ constexpr int kSlabX = 8, kSlabY = 16, kZSeg = 8;
 constexpr int kHaloX = kSlabX + 2, kHaloY = kSlabY + 2;
 constexpr int kSlots = 6;               // halo depths in the shared-memory ring
 constexpr int kThreads = 256;           // weight-gradient kernel: 8 warps
-// forward kernel: 12 epilogue warps, 4 loader warps and one warp that issues the
-// MMAs (17 warps: at most 5 on each SM sub-partition, whose register file
-// holds 16 Ki registers)
-constexpr int kEpiWarps = 12, kLoadWarps = 4;
+// forward kernel: 12 epilogue warps, 6 loader warps and one warp that issues the
+// MMAs (19 warps, at most 5 on each SM sub-partition; 96 registers a thread).
+// With six loader warps a thread issues 7 halo copies per depth instead of
+// 11 with four, whose issue latency held the pipeline back (seven warps gain
+// nothing more, five less).
+constexpr int kEpiWarps = 12, kLoadWarps = 6;
 constexpr int kConvThreads = 32 * (kEpiWarps + kLoadWarps + 1);
 constexpr int kFwdSlots = 7;            // halo depths in the forward kernel's ring
 // TMEM of the forward kernel: two unit buffers of 256 columns, slab k of a
@@ -204,6 +206,18 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 
 // 32 lanes x 32 bit, N consecutive columns: thread t of the warp receives
 // columns [col, col + N) of lane (warp's lane quarter) * 32 + t.
+// Zeros into N consecutive columns of the warp's 32 lanes (tcgen05.st).
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(0u)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_zero1(uint32_t taddr)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(0u) : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ float tmem_ld1(uint32_t taddr)
 {
     uint32_t r;
@@ -513,20 +527,21 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, u
 // One persistent CTA per SM over the units i = blockIdx, blockIdx + gridDim,
 // ... of the plan's list, as a pipeline of three roles that meet only at
 // mbarriers (no CTA-wide barrier in the steady state):
-//  - 4 LOADER warps stage, per unit, its activity bytes and slab mask (one of
+//  - 6 LOADER warps stage, per unit, its activity bytes and slab mask (one of
 //    two unit buffers) and then its halo depths into a ring of kFwdSlots
 //    slots (cp.async; a slot's mbarrier completes when every loader's copies
 //    into it have landed; a slot is refilled once the MMAs that read it
 //    completed);
-//  - 1 MMA warp (one thread) issues, per input depth, 3 tap rows (dy) x (K/16)
-//    MMAs of N = up to 3 NO: the depth's halo (the A operand, read once) times
-//    the weights of its three tap depths dz, into the accumulators of the
-//    (active) output slabs it feeds, which lie side by side in TMEM; the
-//    first MMA into a slab overwrites it.  A commit releases the depth's ring
+//  - 1 MMA warp (one elected lane) issues, per input depth, 3 tap rows (dy) x
+//    (K/16) MMAs of N = up to 3 NO: the depth's halo (the A operand, read
+//    once) times the weights of its three tap depths dz, accumulating into
+//    the accumulators of the (active) output slabs it feeds, which lie side
+//    by side in TMEM and start at zero.  A commit releases the depth's ring
 //    slot, and one marks slab j - 2 complete after depth j;
 //  - 12 EPILOGUE warps (warp w: TMEM lane quarter w & 3, channels
-//    8 (w >> 2) .. 8 (w >> 2) + 7) drain each complete slab through the
-//    epilogue and hand the unit's TMEM buffer back.
+//    8 (w >> 2) .. 8 (w >> 2) + 7; the output layer: channel w >> 2) drain
+//    each complete slab through the epilogue, zero their columns of the
+//    unit's TMEM buffer and hand it back.
 // NO: MMA N (output channels padded to 16 or 32).
 template <int CI, int NO, int EPI>
 __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
@@ -575,6 +590,21 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = s_tmem;
+    // every accumulator starts at zero: the MMAs always accumulate, and the
+    // epilogue zeroes the columns it drained before it hands a buffer back
+    if (warp < 4) {
+        for (uint32_t c = 0; c < 2 * kTmemBuf; c += 8) tmem_zero8(tmem + c + ((uint32_t)(warp * 32) << 16));
+        tc_wait_st();
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    // launched as a programmatic dependent of the previous launch (the layer
+    // before): let the next one start its prologue as SMs free up, then wait
+    // for the previous one's completion and memory before touching any
+    // global data it writes or reads (activations, unit lists, counters)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nunits = *A.nunits;
     const uint64_t T = A.timeout_ns;
 
@@ -703,15 +733,9 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                     const uint32_t dacc = cbuf + (uint32_t)(NO * (kZSeg - 1 - hi));
                     const uint32_t alo = alo0 + slot * (uint32_t)(H::SLOT >> 4);
                     const uint32_t blo = blo0 + (uint32_t)((j - hi) * NG * 8);
-                    // first tap: the first MMA into slab j (hi == j) overwrites it
-                    if (hi == j) {
-                        mma_bf16_warp(dacc, alo, ahi, blo, bhi, kId1, 0u);
-                        if (lo < hi) mma_bf16_warp(dacc + NO, alo, ahi, blo + NG * 8, bhi, nsl == 3 ? kId2 : kId1, 1u);
-                    } else {
-                        mma_bf16_warp(dacc, alo, ahi, blo, bhi, idn, 1u);
-                    }
+                    // the accumulators start at zero (see the epilogue), so every MMA accumulates
 #pragma unroll
-                    for (int t = 1; t < 3 * H::NKS; ++t) {
+                    for (int t = 0; t < 3 * H::NKS; ++t) {
                         const int dyi = t / H::NKS, s2 = t % H::NKS;
                         // A: halo row dyi, K-columns 2 s2 .. 2 s2 + 1; B: core matrix (dy, q = 2 s2, dz block j - hi, ng 0)
                         mma_bf16_warp(dacc, alo + (uint32_t)((dyi * H::GS) >> 4) + (uint32_t)(s2 * 16), ahi,
@@ -841,6 +865,20 @@ __global__ void __maxnreg__(96) k_conv_tc(const __grid_constant__ ConvArgs A)
                         }
                     }
                 }
+            }
+            // zero this warp's accumulator columns of every slab of the buffer
+            // (every MMA accumulates; unit n + 2 starts from these zeros): all
+            // MMAs into the buffer completed with its last active slab
+            if (ok) {
+                const uint32_t tq = tmem + (uint32_t)ub * kTmemBuf + (uint32_t)c0 + ((uint32_t)(lq * 32) << 16);
+#pragma unroll
+                for (int k = 0; k < kZSeg; ++k) {
+                    if (EPI == EPI_OUT)
+                        tmem_zero1(tq + (uint32_t)(NO * (kZSeg - 1 - k)));
+                    else
+                        tmem_zero8(tq + (uint32_t)(NO * (kZSeg - 1 - k)));
+                }
+                tc_wait_st();
             }
             // this warp is done with the unit's TMEM buffer, activity bytes and records
             tc_before_sync();
