@@ -872,15 +872,16 @@ def main():
         assert all(r <= wl.rtol * bb for r, bb in zip(erep["res"], erep["bnorm"])), erep
         e_ms += a.elapsed_time(b)
         e_units += erep["mask_voxels"] * S
-        (x0, y0, z0), (x1, y1, z1) = erep["box"]
-        bo += S * 8 * (x1 - x0) * (y1 - y0) * (z1 - z0)
+        # pinned host fields: the step's in-mask voxels come back (8 B per species each)
+        bo += S * 8 * erep["mask_voxels"]
     barrier()
     e2e_value, _ = replica_value(e_units, e_ms, world, "cuda")
     e2e = {"value": e2e_value, "unit": "species-voxel-steps/s", "h2d_bytes_per_step": h_cell.numel() * 4,
            "d2h_bytes_per_step": bo // ne, "steps": ne,
            "note": f"mpm_step_host per step (one synchronous C-ABI call, learned + mixed path) at {ne} steps sampled "
                    "over the growth: the 512x384x384 int32 cell-id lattice copied in from pinned host memory, the "
-                   "step, and the step's box of the 3 FP64 fields copied back to the pinned host fields; the mask "
+                   "step, and the voxels the step updated (the in-mask voxels of its box) of the 3 FP64 fields written back "
+                   "to the pinned host fields by a kernel; the mask "
                    "and the initial fields went in once before the timed steps"}
     del solver, lat
 

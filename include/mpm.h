@@ -305,7 +305,7 @@ typedef struct {
     const int32_t *cell_id;             /* nullable: the device lattice's cell ids are current */
     const uint8_t *mask;                /* nullable: the device mask is current */
     double *field[MPM_MAX_SPECIES];     /* nullable per species: read with MPM_HOST_FIELDS_IN;
-                                           receives the step's box of the device field */
+                                           receives the voxels the step updated */
 } mpm_host_lattice;
 
 #define MPM_HOST_FIELDS_IN 1            /* mpm_step_host: copy the host fields in before the step */
@@ -315,12 +315,15 @@ typedef struct {
  * copies host->cell_id and host->mask (when not NULL) and, with
  * MPM_HOST_FIELDS_IN, every non-NULL host field into the device lattice `dev`
  * (whose buffers the call overwrites), runs mpm_step on `dev`, waits for it,
- * and copies the step's box of every device field into the host field of the
- * same species (one 3-D copy per species, box rows only).  A step changes no
- * voxel outside its box, so a host field that equalled the device field
- * before the step equals it afterwards: a caller that keeps the fields in
- * step (MPM_HOST_FIELDS_IN on the first call and after changing them on the
- * host) moves the cell ids in and the box out per step.  The fields are
+ * and copies the voxels the step updated back into the host field of the
+ * same species: a page-locked host field (one the device can address)
+ * receives the in-mask voxels of the step's box, written by a kernel; any
+ * other host field the whole box (one 3-D copy per species, box rows only).
+ * A step changes no voxel outside its box nor outside the mask, so a host
+ * field that equalled the device field before the step equals it
+ * afterwards: a caller that keeps the fields in step (MPM_HOST_FIELDS_IN on
+ * the first call and after changing them on the host) moves the cell ids in
+ * and the step's results out per step.  The fields are
  * copied back for every status that lets the step write them (MPM_OK,
  * MPM_ERR_NOCONV, MPM_ERR_BREAKDOWN) and left alone otherwise.
  *   dev   : device lattice (as for mpm_step), dims give the size of every copy.

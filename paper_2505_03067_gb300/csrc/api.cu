@@ -82,6 +82,31 @@ __global__ void k_debug_convert(const double *__restrict__ in64, float *__restri
         ref64[i] = (double)in32[i];
     }
 }
+
+// The voxels a step updated -- the in-mask voxels of its box -- of every
+// field into host fields the device addresses directly (page-locked host
+// memory): one box row per CTA iteration, the row's in-mask voxels only.
+struct HostBack {
+    const double *src[MPM_MAX_SPECIES];
+    double *dst[MPM_MAX_SPECIES];
+    int32_t n;
+};
+
+__global__ void __launch_bounds__(256) k_box_mask_to_host(const uint8_t *__restrict__ mask, HostBack o, int64_t nx,
+                                                          int64_t ny, int32_t x0, int32_t y0, int32_t z0, int32_t bx,
+                                                          int32_t by, int32_t bz)
+{
+    const int64_t rows = (int64_t)by * bz;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t y = y0 + r % by, z = z0 + r / by;
+        const int64_t off = (z * ny + y) * nx + x0;
+        for (int32_t i = threadIdx.x; i < bx; i += blockDim.x) {
+            if (!mask[off + i]) continue;
+            for (int s = 0; s < o.n; ++s)
+                if (o.dst[s]) o.dst[s][off + i] = o.src[s][off + i];
+        }
+    }
+}
 }  // namespace mpm
 
 extern "C" {
@@ -292,10 +317,39 @@ mpm_status mpm_step_host(mpm_ctx *ctx, mpm_subgrid *sub, const mpm_host_lattice 
     const mpm_status r = mpm_step_impl(ctx, sub, dev, prm, margin, tile, opt, rep, &box, st);
     if (out_box && (r == MPM_OK || r == MPM_ERR_NOCONV || r == MPM_ERR_BREAKDOWN)) *out_box = box;
     if (r != MPM_OK && r != MPM_ERR_NOCONV && r != MPM_ERR_BREAKDOWN) return r;
-    // the box of every field back to the host: rows of nx doubles, pitch nx
-    for (int s = 0; s < prm->nspecies; ++s) {
+    // the step's results back to the host.  A host field the device can
+    // address (page-locked) receives the in-mask voxels of the box from a
+    // kernel -- the only voxels the step wrote, a tenth of the box on a thin
+    // shell -- any other one the whole box by a 3-D copy (rows of nx doubles).
+    const bool has_box = box.hi[0] > box.lo[0] && box.hi[1] > box.lo[1] && box.hi[2] > box.lo[2];
+    mpm::HostBack hb;
+    memset(&hb, 0, sizeof(hb));
+    hb.n = prm->nspecies;
+    bool pageable[MPM_MAX_SPECIES] = {};
+    bool any_mapped = false;
+    for (int s = 0; s < prm->nspecies && has_box; ++s) {
         if (!host->field[s] || !dev->field[s]) continue;
-        if (box.hi[0] <= box.lo[0] || box.hi[1] <= box.lo[1] || box.hi[2] <= box.lo[2]) break;
+        cudaPointerAttributes pa;
+        memset(&pa, 0, sizeof(pa));
+        if (cudaPointerGetAttributes(&pa, host->field[s]) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            hb.src[s] = dev->field[s];
+            hb.dst[s] = (double *)pa.devicePointer;
+            any_mapped = true;
+        } else {
+            cudaGetLastError();
+            pageable[s] = true;
+        }
+    }
+    if (any_mapped) {
+        const int32_t bx = box.hi[0] - box.lo[0], by = box.hi[1] - box.lo[1], bz = box.hi[2] - box.lo[2];
+        mpm::k_box_mask_to_host<<<ctx->num_sms * 8, 256, 0, st>>>(dev->mask, hb, (int64_t)nx, (int64_t)ny, box.lo[0],
+                                                                 box.lo[1], box.lo[2], bx, by, bz);
+        ctx->launches += 1;
+        MPM_CU(cudaGetLastError());
+    }
+    for (int s = 0; s < prm->nspecies; ++s) {
+        if (!pageable[s]) continue;
         cudaMemcpy3DParms p = {};
         p.srcPtr = make_cudaPitchedPtr(dev->field[s], nx * sizeof(double), nx, ny);
         p.dstPtr = make_cudaPitchedPtr(host->field[s], nx * sizeof(double), nx, ny);

@@ -407,7 +407,8 @@ class Subgrid:
         """mpm_step with the inputs in host memory: `cell_id` (int32), `mask`
         (uint8) and `fields` ([S, Lz, Ly, Lx] float64) are contiguous CPU
         tensors (None: the device copy is current); `fields` receives the
-        step's box of every field."""
+        voxels the step updated (the in-mask voxels of its box when `fields`
+        is pinned, else the whole box)."""
         h = mpm_host_lattice()
         for name, t in (("cell_id", cell_id), ("mask", mask)):
             if t is not None:
@@ -616,7 +617,7 @@ class StepSolver:
     def step_host(self, cell_id, fields, opts: mpm_opts, mask=None, fields_in=False, stream=None,
                   allow=(ERR_NOCONV,)):
         """One step from host buffers (mpm_step_host): the cell ids (and the
-        mask, and with fields_in the fields) in, the step's box of the fields out."""
+        mask, and with fields_in the fields) in, the step's results out."""
         return self.sub.mpm_step_host(cell_id, mask, fields, self.lat, self.prm, self.margin, opts, fields_in,
                                       self.tile, stream, allow)
 

@@ -544,12 +544,15 @@ def test_reorth_flag_out_of_range_is_an_argument_error(M, ctx):
 
 
 # ---------------------------------------------------------------- host buffers (mpm_step_host)
-def test_step_from_host_buffers_follows_a_moving_tumour(M, ctx):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_from_host_buffers_follows_a_moving_tumour(M, ctx, pinned):
     """mpm_step_host: the host's cell ids (and on the first call its mask and
-    fields) go in, the step's box of every field comes back; the device
-    lattice starts out wrong (zero cell ids, mask and fields), so the answer
-    can only come from the copies.  Each step meets the oracle's step, and
-    after each the host fields equal the device fields bit for bit."""
+    fields) go in, the step's results come back (page-locked host fields: the
+    in-mask voxels of the box, by a kernel; pageable ones: the whole box, by a
+    3-D copy); the device lattice starts out wrong (zero cell ids, mask and
+    fields), so the answer can only come from the copies.  Each step meets
+    the oracle's step, and after each the host fields equal the device fields
+    bit for bit."""
     import torch
     wl = W.random_case(23, (40, 36, 30), nspecies=3, ncell=9)
     ref = wl.lattice.copy()
@@ -561,7 +564,10 @@ def test_step_from_host_buffers_follows_a_moving_tumour(M, ctx):
     prm = M.DeviceParams(wl.params)
     solver = M.StepSolver(ctx, lat, prm, wl.margin, (4, 4, 4))
     h_mask = torch.from_numpy(np.ascontiguousarray(wl.lattice.mask, np.uint8)).pin_memory()
-    h_fields = torch.from_numpy(np.ascontiguousarray(wl.lattice.fields)).pin_memory()
+    h_fields = torch.from_numpy(np.ascontiguousarray(wl.lattice.fields))
+    if pinned:
+        h_fields = h_fields.pin_memory()
+    assert h_fields.is_pinned() == pinned
     opts = M.make_opts(rtol=0.0, atol=1e-13, restart=8, maxit=2000)
     for k, (r, c) in enumerate([(3, (8, 9, 10)), (6, (12, 12, 12)), (4, (25, 20, 16)), (9, (20, 18, 15))]):
         cid = _grow_cells(wl, r, c)
