@@ -162,3 +162,57 @@ def test_learned_mixed_growth512_steps_meet_tolerance(M):
         outside[oracle.box_slices(box)] = False
         outside |= before.mask == 0
         assert np.array_equal(after[:, outside], before.fields[:, outside])
+
+
+def test_growth512_guess_matches_oracle_on_sampled_voxels(M):
+    """The network's guess at full size, in the launch configuration the
+    benchmark times (the learned step graph on the 512x384x384 growing tumour
+    at its last, largest state): a tolerance of 1e3 ||b|| stops every species
+    at its first residual, so the fields the step scatters are the prediction.  Sampled
+    in-mask voxels of the box are checked one by one against the oracle's
+    network on the voxel's receptive field (radius 6 for six 3x3x3 layers,
+    clipped to the box: the network sees the box only), at the bound of the
+    whole-box test."""
+    import torch
+    from types import SimpleNamespace
+    wl, extra = W.growth512()
+    W.grow(wl, wl.steps - 1, extra)
+    ctx = M.Context()
+    lat = M.DeviceLattice(wl.lattice)
+    prm = M.DeviceParams(wl.params)
+    solver = M.StepSolver(ctx, lat, prm, wl.margin)
+    s_out = 0.05
+    cnn, params = _net(M, ctx, wl.lattice.dims, seed=5, last_scale=0.3, s_out=s_out)
+    solver.set_network(cnn)
+    rep = solver.step(M.make_opts(rtol=1e3, restart=8, maxit=50))
+    assert rep["status_code"] == M.OK and rep["iters"] == [0, 0, 0]
+    box = rep["box"]
+    assert box == oracle.bbox(wl.lattice.cell_id, wl.margin)
+    (lx, ly, lz), (hx, hy, hz) = box
+    got = [lat.fields[s].cpu().numpy() for s in range(3)]
+    P = oracle.bf16(params.astype(np.float64))
+    rng = np.random.default_rng(11)
+    mz, my, mx = np.nonzero(wl.lattice.mask[lz:hz, ly:hy, lx:hx])
+    pick = rng.choice(len(mx), size=24, replace=False)
+    z6g, z6o = [], []
+    for i in pick:
+        x, y, z = lx + mx[i], ly + my[i], lz + mz[i]
+        x0, x1 = max(lx, x - 6), min(hx, x + 7)
+        y0, y1 = max(ly, y - 6), min(hy, y + 7)
+        z0, z1 = max(lz, z - 6), min(hz, z + 7)
+        sl = (slice(z0, z1), slice(y0, y1), slice(x0, x1))
+        sub = SimpleNamespace(cell_id=wl.lattice.cell_id[sl], mask=wl.lattice.mask[sl],
+                              fields=wl.lattice.fields[(slice(None),) + sl])
+        X = _features_np(sub, wl.params)
+        F = np.moveaxis(sub.fields.astype(np.float32).astype(np.float64), 0, -1)
+        p_o, _ = oracle.cnn_forward(X, F, P, s_out)
+        c = (z - z0, y - y0, x - x0)
+        for s in range(3):
+            z6o.append((p_o[c + (s,)] - F[c + (s,)]) / s_out)
+            z6g.append((got[s][z, y, x] - wl.lattice.fields[s][z, y, x]) / s_out)
+    z6g, z6o = np.array(z6g), np.array(z6o)
+    assert np.max(np.abs(z6g - z6o)) <= 1e-2 * np.max(np.abs(z6o)) + 1e-6
+    # voxels of the box outside the mask keep c^n
+    outside = wl.lattice.mask[lz:hz, ly:hy, lx:hx] == 0
+    for s in range(3):
+        assert np.array_equal(got[s][lz:hz, ly:hy, lx:hx][outside], wl.lattice.fields[s][lz:hz, ly:hy, lx:hx][outside])
