@@ -26,11 +26,13 @@
 // MMAs per slab read the staged halo in place, with no per-tap copy.  The
 // weights of all taps are staged once per CTA in the matching B layout.
 //
-// Pipeline per CTA.  Halo depths are copied with cp.async (16 B, zero-filled
-// for inactive voxels) into a ring of kSlots slots, two depths ahead; one
-// thread issues the slab's MMAs into one of two TMEM accumulators and commits
-// them to an mbarrier; all eight warps drain the other accumulator (tcgen05.ld)
-// through the epilogue while the tensor cores run.
+// Pipeline per CTA (forward kernel).  Loader warps copy halo depths with
+// cp.async (16 B, zero-filled for inactive voxels) into a ring of depth
+// slots; one warp issues each depth's MMAs (the tap depths folded into N)
+// into the accumulators of the slabs it feeds and commits them to
+// mbarriers; epilogue warps drain complete slabs (tcgen05.ld) while the
+// tensor cores run on.  The weight-gradient kernel runs its own, simpler
+// pipeline (kSlots slots, eight warps).
 //
 // Weight gradient.  dW[(dx,dy,dz)][ci][co] = sum_v in[v + off][ci] g[v][co] is
 // a GEMM over voxels with the halo buffer read as an MN-major A operand
